@@ -1,0 +1,254 @@
+"""FP64 CPU oracle for the IFGF-accelerated CFIE apply (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
+reference legs use this package.  It shares no code with
+``paper_2112_06316_gb300`` (the CUDA library) and never imports it.
+
+* ``direct`` / ``direct_adjoint``: the plain O(N^2) combined-field sum of
+  Eq. field1 (kernel of Eq. GreenFunction / Eq. double_layer, identity term of
+  Eq. CombLayIE) and its conjugate transpose, on all rows or a row subset.
+* ``ifgf``: Algorithm 1 written loop by loop in FP64 (``oracle.c``).
+* ``mie``: closed-form sound-soft sphere solutions (module ``oracle.mie``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIBDIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+MAXD = 20
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc (FP64, OpenMP) into ``oracle/_build``."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
+               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OracleParams(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_double), ("eta", ctypes.c_double),
+        ("Ps", ctypes.c_int), ("Pang", ctypes.c_int), ("nC0", ctypes.c_int), ("nS0", ctypes.c_int),
+        ("levels", ctypes.c_int), ("leaf_target", ctypes.c_double),
+        ("cone_rule", ctypes.c_int), ("factor_mode", ctypes.c_int),
+        ("identity_coef", ctypes.c_double),
+        ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+    ]
+
+
+class OracleInfo(ctypes.Structure):
+    _fields_ = [
+        ("D", ctypes.c_int),
+        ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+        ("nbox", ctypes.c_int * (MAXD + 1)), ("ns", ctypes.c_int * (MAXD + 1)),
+        ("nC", ctypes.c_int * (MAXD + 1)), ("split", ctypes.c_int * (MAXD + 1)),
+        ("nrc", ctypes.c_int64 * (MAXD + 1)),
+        ("cousin_evals", ctypes.c_int64 * (MAXD + 1)),
+        ("prop_evals", ctypes.c_int64 * (MAXD + 1)),
+        ("leaf_evals", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        _lib.oracle_direct_rows.restype = ctypes.c_int
+        _lib.oracle_direct_adjoint_rows.restype = ctypes.c_int
+        _lib.oracle_ifgf.restype = ctypes.c_int
+        _lib.oracle_cheb_interp_1d.restype = ctypes.c_double
+        _lib.oracle_cheb_interp_1d.argtypes = [ctypes.c_int, dp, ctypes.c_double]
+        _lib.oracle_num_threads.restype = ctypes.c_int
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+@dataclass
+class IFGFParams:
+    """Parameters of the IFGF apply (same meaning as the library's ifgf_params)."""
+
+    k: float
+    eta: float | None = None
+    Ps: int = 3
+    Pang: int = 5
+    nC0: int = 2
+    nS0: int = 1
+    levels: int = 0
+    leaf_target: float = 64.0
+    cone_rule: int = 0
+    factor_mode: int = 0
+    identity_coef: float = 0.0
+    root_center: tuple = (0.0, 0.0, 0.0)
+    root_side: float = 0.0
+
+    def to_c(self) -> OracleParams:
+        p = OracleParams()
+        p.k = self.k
+        p.eta = self.k if self.eta is None else self.eta
+        p.Ps, p.Pang, p.nC0, p.nS0, p.levels = self.Ps, self.Pang, self.nC0, self.nS0, self.levels
+        p.leaf_target = self.leaf_target
+        p.cone_rule, p.factor_mode = self.cone_rule, self.factor_mode
+        p.identity_coef = self.identity_coef
+        for a in range(3):
+            p.root_center[a] = self.root_center[a]
+        p.root_side = self.root_side
+        return p
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _geom(points, normals, weights):
+    x = np.ascontiguousarray(points, dtype=np.float64)
+    n = np.ascontiguousarray(normals, dtype=np.float64)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    return x, n, w
+
+
+def _dens(sigma, N):
+    s = np.asarray(sigma)
+    if s.ndim == 1:
+        s = s[None, :]
+    if s.shape[1] != N:
+        raise ValueError("density must be (nrhs, N)")
+    return np.ascontiguousarray(s, dtype=np.complex128)
+
+
+def direct(points, normals, weights, k, eta, sigma, cI=0.0, rows=None) -> np.ndarray:
+    """y_l = cI sigma_l + sum_{m != l} K(x_l, x_m) w_m sigma_m for l in rows (all if None).
+
+    sigma: (nrhs, N) complex; returns (nrhs, len(rows)) complex128.
+    """
+    x, n, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(sigma, N)
+    nrhs = s.shape[0]
+    if rows is None:
+        r = None
+        nrows = N
+    else:
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        nrows = r.shape[0]
+    out = np.zeros((nrhs, nrows), dtype=np.complex128)
+    cI = complex(cI)
+    rc = lib().oracle_direct_rows(
+        ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
+        ctypes.c_double(cI.real), ctypes.c_double(cI.imag), ctypes.c_int(nrhs),
+        s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_int64(nrows),
+        None if r is None else r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise RuntimeError(f"oracle_direct_rows failed ({rc})")
+    return out
+
+
+def direct_adjoint(points, normals, weights, k, eta, g, cI=0.0, rows=None) -> np.ndarray:
+    """(A^H g)_m = conj(cI) g_m + w_m sum_{l != m} conj(K(x_l, x_m)) g_l for m in rows."""
+    x, n, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(g, N)
+    nrhs = s.shape[0]
+    if rows is None:
+        r = None
+        nrows = N
+    else:
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        nrows = r.shape[0]
+    out = np.zeros((nrhs, nrows), dtype=np.complex128)
+    cI = complex(cI)
+    rc = lib().oracle_direct_adjoint_rows(
+        ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
+        ctypes.c_double(cI.real), ctypes.c_double(cI.imag), ctypes.c_int(nrhs),
+        s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_int64(nrows),
+        None if r is None else r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise RuntimeError(f"oracle_direct_adjoint_rows failed ({rc})")
+    return out
+
+
+def ifgf(points, normals, weights, params: IFGFParams, sigma):
+    """Algorithm 1 in FP64.  Returns (y (nrhs, N) complex128, info dict)."""
+    x, n, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(sigma, N)
+    nrhs = s.shape[0]
+    out = np.zeros((nrhs, N), dtype=np.complex128)
+    info = OracleInfo()
+    p = params.to_c()
+    rc = lib().oracle_ifgf(ctypes.byref(p), ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_int(nrhs),
+                           s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(info))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ifgf failed ({rc})")
+    D = info.D
+    d = {
+        "D": D,
+        "root_center": tuple(info.root_center),
+        "root_side": info.root_side,
+        "nbox": [info.nbox[i] for i in range(D + 1)],
+        "ns": [info.ns[i] for i in range(D + 1)],
+        "nC": [info.nC[i] for i in range(D + 1)],
+        "split": [info.split[i] for i in range(D + 1)],
+        "nrc": [info.nrc[i] for i in range(D + 1)],
+        "cousin_evals": [info.cousin_evals[i] for i in range(D + 1)],
+        "prop_evals": [info.prop_evals[i] for i in range(D + 1)],
+        "leaf_evals": info.leaf_evals,
+        "near_pairs": info.near_pairs,
+    }
+    return out, d
+
+
+def auto_levels(points, leaf_target=64.0) -> int:
+    x = np.ascontiguousarray(points, dtype=np.float64)
+    return int(lib().oracle_auto_levels(ctypes.c_int64(x.shape[0]), _dptr(x), ctypes.c_double(leaf_target)))
+
+
+def kernel(k, eta, x, y, ny) -> complex:
+    o = np.zeros(2)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, ny)]
+    lib().oracle_kernel(ctypes.c_double(k), ctypes.c_double(eta), _dptr(a[0]), _dptr(a[1]), _dptr(a[2]), _dptr(o))
+    return complex(o[0], o[1])
+
+
+def layer_kernels(k, x, y, ny):
+    """(Phi(x, y), dPhi/dnu(y)) of Eq. GreenFunction and Eq. double_layer."""
+    o = np.zeros(4)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, ny)]
+    lib().oracle_layer_kernels(ctypes.c_double(k), _dptr(a[0]), _dptr(a[1]), _dptr(a[2]), _dptr(o))
+    return complex(o[0], o[1]), complex(o[2], o[3])
+
+
+def wfactors(k, eta, x, y0, h, y, ny, split: bool, literal: bool = False):
+    """Analytic factors (W_C,) or (W2, W13) at x for source y of the box (y0, h)."""
+    o = np.zeros(4)
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y0, y, ny)]
+    lib().oracle_wfactors(ctypes.c_double(k), ctypes.c_double(eta), _dptr(a[0]), _dptr(a[1]), ctypes.c_double(h),
+                          _dptr(a[2]), _dptr(a[3]), ctypes.c_int(int(split)), ctypes.c_int(int(literal)), _dptr(o))
+    return (complex(o[0], o[1]), complex(o[2], o[3])) if split else (complex(o[0], o[1]),)
+
+
+def cheb_interp_1d(values, t) -> float:
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    return float(lib().oracle_cheb_interp_1d(ctypes.c_int(v.shape[0]), _dptr(v), ctypes.c_double(t)))

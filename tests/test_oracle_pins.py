@@ -1,0 +1,202 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a finite
+difference, a symmetry, a textbook integral, a brute-force loop over the
+oracle's single-pair kernel, polynomial exactness, the paper's printed level
+counts, or convergence of the IFGF approximation to the direct sum.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from workloads import cube_sphere, fejer_nodes, fejer_weights, random_density, sphere_workload
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+# ---------------------------------------------------------------- quadrature inputs (Section 4)
+def test_fejer_exactness():
+    """Fejer's first rule (Eq. FejersWeights) integrates x^j exactly for j < J."""
+    for J in (5, 8, 26):
+        x, w = fejer_nodes(J), fejer_weights(J)
+        assert abs(w.sum() - 2.0) < 1e-14
+        for j in range(J):
+            exact = 0.0 if j % 2 else 2.0 / (j + 1)
+            assert abs((w * x ** j).sum() - exact) < 1e-13
+
+
+def test_sphere_area_weights():
+    """Equiangular cube-sphere area weights sum to 4 pi (unit sphere)."""
+    for n, m in ((26, 26), (64, 8)):
+        s = cube_sphere(n, m)
+        assert abs(s.weights.sum() - 4 * math.pi) < 1e-12
+        assert np.allclose(np.linalg.norm(s.points, axis=1), 1.0, atol=1e-15)
+
+
+# ---------------------------------------------------------------- kernel (Eq. GreenFunction, Eq. double_layer)
+def test_kernel_reciprocity_and_normal_derivative(oracle_lib):
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        k = rng.uniform(0.5, 30)
+        x, y = rng.normal(size=3), rng.normal(size=3)
+        nu = rng.normal(size=3)
+        nu /= np.linalg.norm(nu)
+        phi_xy, dphi = oracle_lib.layer_kernels(k, x, y, nu)
+        phi_yx, _ = oracle_lib.layer_kernels(k, y, x, nu)
+        assert abs(phi_xy - phi_yx) <= 1e-14 * abs(phi_xy)
+        # d/dnu(y) by a central difference of Phi along nu at y
+        h = 1e-5
+        fp, _ = oracle_lib.layer_kernels(k, x, y + h * nu, nu)
+        fm, _ = oracle_lib.layer_kernels(k, x, y - h * nu, nu)
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - dphi) <= 1e-7 * max(1.0, abs(dphi))
+        # combined kernel = dPhi/dnu - i eta Phi
+        eta = rng.uniform(0, 40)
+        K = oracle_lib.kernel(k, eta, x, y, nu)
+        assert abs(K - (dphi - 1j * eta * phi_xy)) <= 1e-13 * abs(K)
+
+
+def test_gauss_and_shell_potential_static_limit(oracle_lib):
+    """k -> 0 on the unit sphere: the double layer of 1 is -1/2 (Gauss) and the single
+    layer of 1 is 1 (uniform shell); the plain quadrature without singular correction
+    is only O(h) accurate, so the bound is loose.  Pins sign and 4 pi normalisation."""
+    s = cube_sphere(26)
+    one = np.ones((1, s.N), complex)
+    ydl = oracle_lib.direct(s.points, s.normals, s.weights, 1e-9, 0.0, one)
+    assert abs(np.median(ydl.real) + 0.5) < 2e-2
+    ysl = oracle_lib.direct(s.points, s.normals, s.weights, 1e-9, 1.0, one)  # -i * S[1]
+    assert abs(np.median(-ysl.imag) - 1.0) < 5e-2
+
+
+def test_direct_sum_brute_force(oracle_lib):
+    """Assembly of Eq. field1 (m != l, weights, identity term, multiple rhs, row subset)
+    against a Python loop over the single-pair kernel."""
+    rng = np.random.default_rng(3)
+    N, k, eta, cI = 37, 4.0, 2.5, 0.5
+    x = rng.normal(size=(N, 3))
+    nu = rng.normal(size=(N, 3))
+    nu /= np.linalg.norm(nu, axis=1, keepdims=True)
+    w = rng.uniform(0.1, 1.0, N)
+    sig = random_density(N, 2, 11)
+    ref = np.zeros((2, N), complex)
+    for l in range(N):
+        for m in range(N):
+            if m != l:
+                ref[:, l] += oracle_lib.kernel(k, eta, x[l], x[m], nu[m]) * w[m] * sig[:, m]
+    ref += cI * sig
+    got = oracle_lib.direct(x, nu, w, k, eta, sig, cI=cI)
+    assert rel(got, ref) < 1e-14
+    rows = np.array([5, 0, 36, 17])
+    assert rel(oracle_lib.direct(x, nu, w, k, eta, sig, cI=cI, rows=rows), ref[:, rows]) < 1e-14
+    # conjugate transpose: <A s, g> = <s, A^H g>
+    g = random_density(N, 2, 12)
+    lhs = np.vdot(g, got)
+    rhs = np.vdot(oracle_lib.direct_adjoint(x, nu, w, k, eta, g, cI=cI), sig)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ---------------------------------------------------------------- Chebyshev (Eq. ChebyPoly, ChebyNodes)
+def test_chebyshev_exact_for_low_degree(oracle_lib):
+    rng = np.random.default_rng(5)
+    for n in (3, 5, 7, 9):
+        xk = np.cos((2 * np.arange(n) + 1) * np.pi / (2 * n))
+        for deg in range(n):
+            c = rng.normal(size=deg + 1)
+            vals = np.polyval(c, xk)
+            for t in rng.uniform(-1, 1, 5):
+                assert abs(oracle_lib.cheb_interp_1d(vals, t) - np.polyval(c, t)) < 1e-12
+        # degree n is not reproduced (the interpolant has degree n-1)
+        vals = xk ** n
+        errs = [abs(oracle_lib.cheb_interp_1d(vals, t) - t ** n) for t in (0.3, 0.77)]
+        assert max(errs) > 1e-6
+
+
+# ---------------------------------------------------------------- factorisation (Eq. hgn2, double_layer_fact, w23)
+def test_factorisation_identity(oracle_lib):
+    """E(x; y0) * W(x, y; y0) reproduces K(x, y) for both factor modes; the
+    cancellation-free phase equals the literal phase."""
+    rng = np.random.default_rng(9)
+    for _ in range(30):
+        k, eta, H = rng.uniform(1, 60), rng.uniform(0, 60), rng.uniform(0.05, 2)
+        y0 = rng.normal(size=3)
+        h = math.sqrt(3) / 2 * H
+        y = y0 + rng.uniform(-H / 2, H / 2, 3)
+        nu = rng.normal(size=3)
+        nu /= np.linalg.norm(nu)
+        d = rng.normal(size=3)
+        x = y0 + d / np.linalg.norm(d) * rng.uniform(1.5 * H, 40 * H)
+        r = np.linalg.norm(x - y0)
+        E1 = np.exp(1j * k * r) / (4 * math.pi * r)
+        E2 = E1 / r
+        K = oracle_lib.kernel(k, eta, x, y, nu)
+        (Wc,) = oracle_lib.wfactors(k, eta, x, y0, h, y, nu, split=False)
+        W2, W13 = oracle_lib.wfactors(k, eta, x, y0, h, y, nu, split=True)
+        assert abs(E1 * Wc - K) < 1e-11 * abs(K)
+        assert abs(E2 * W2 + E1 * W13 - K) < 1e-11 * abs(K)
+        (Wl,) = oracle_lib.wfactors(k, eta, x, y0, h, y, nu, split=False, literal=True)
+        assert abs(Wl - Wc) < 1e-8 * abs(Wc)
+
+
+# ---------------------------------------------------------------- IFGF oracle (Algorithm 1)
+@pytest.fixture(scope="module")
+def sphere1():
+    s = cube_sphere(26)
+    k = math.pi
+    sig = random_density(s.N, 1, 1)
+    return s, k, sig
+
+
+def test_ifgf_oracle_counts_config1(oracle_lib, sphere1):
+    s, k, sig = sphere1
+    _, info = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k, levels=3), sig)
+    assert info["nbox"][3] == 56
+    assert info["nrc"][3] == 344
+    assert info["cousin_evals"][3] == 184224
+    assert info["leaf_evals"] == 1819800
+
+
+def test_ifgf_oracle_converges_to_direct(oracle_lib, sphere1):
+    s, k, sig = sphere1
+    yd = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5)
+    errs = []
+    for ps, pa in ((3, 5), (5, 7), (7, 9), (9, 11)):
+        p = oracle_lib.IFGFParams(k=k, levels=3, Ps=ps, Pang=pa, identity_coef=0.5)
+        yi, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, p, sig)
+        errs.append(rel(yi, yd))
+    assert errs[0] < 3e-3
+    assert all(errs[i + 1] < 0.3 * errs[i] for i in range(3)), errs
+    assert errs[-1] < 2e-6
+
+
+def test_ifgf_oracle_multilevel_all_modes(oracle_lib):
+    """4-wavelength sphere (N = 13,824, D = 4 as in Table 1): two levels of recursion,
+    propagation through split and combined factors; all modes converge to the direct sum."""
+    s, k = sphere_workload(48, 6, 4.0)
+    sig = random_density(s.N, 2, 4)
+    rows = np.random.default_rng(0).choice(s.N, 600, replace=False)
+    yd = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, rows=rows)
+    for fm in (0, 1, 2):
+        e = []
+        for ps, pa in ((3, 5), (6, 8)):
+            p = oracle_lib.IFGFParams(k=k, levels=4, Ps=ps, Pang=pa, factor_mode=fm)
+            yi, info = oracle_lib.ifgf(s.points, s.normals, s.weights, p, sig)
+            e.append(rel(yi[:, rows], yd))
+        assert e[0] < 5e-3 and e[1] < 1e-4, (fm, e)
+    assert info["nrc"][3] > 0 and info["prop_evals"][3] > 0
+
+
+def test_ifgf_oracle_levels_match_table1(oracle_lib):
+    """Automatic level count reproduces Table 1's levels for the sphere sizes there."""
+    rows = json.load(open(os.path.join(HERE, "golden", "paper_table1_spheres.json")))["rows"]
+    for r in rows[:3]:
+        n = int(round(math.sqrt(r["N"] / 6)))
+        s, k = sphere_workload(n, 8 if n % 8 == 0 else 6, float(r["diameter_wavelengths"]))
+        assert s.N == r["N"]
+        assert oracle_lib.auto_levels(s.points) == r["levels"], r

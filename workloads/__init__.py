@@ -1,0 +1,16 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the bench.
+
+This package holds no arithmetic of the IFGF method: it only produces surface
+discretisations (points, outward unit normals, quadrature area weights) and
+seeded complex densities.  See ``workloads.geometry``.
+"""
+from .geometry import (  # noqa: F401
+    fejer_nodes,
+    fejer_weights,
+    cube_sphere,
+    ellipsoid,
+    star_body,
+    sphere_workload,
+    random_density,
+    Surface,
+)
