@@ -252,3 +252,18 @@ def wfactors(k, eta, x, y0, h, y, ny, split: bool, literal: bool = False):
 def cheb_interp_1d(values, t) -> float:
     v = np.ascontiguousarray(values, dtype=np.float64)
     return float(lib().oracle_cheb_interp_1d(ctypes.c_int(v.shape[0]), _dptr(v), ctypes.c_double(t)))
+
+
+def csr_apply(rowptr, col, val, sigma) -> np.ndarray:
+    """Plain sparse product (C sigma)_l = sum_{j in row l} val_j sigma_{col_j}, per rhs."""
+    s = np.asarray(sigma, dtype=np.complex128)
+    if s.ndim == 1:
+        s = s[None, :]
+    rp = np.asarray(rowptr, dtype=np.int64)
+    cl = np.asarray(col, dtype=np.int64)
+    v = np.asarray(val, dtype=np.complex128)
+    out = np.zeros((s.shape[0], rp.shape[0] - 1), dtype=np.complex128)
+    for l in range(rp.shape[0] - 1):
+        j0, j1 = rp[l], rp[l + 1]
+        out[:, l] = s[:, cl[j0:j1]] @ v[j0:j1]
+    return out

@@ -34,6 +34,7 @@
  *   - The phase k (h/s)(|u - v s| - 1) of Eq. V3 is evaluated in the algebraically identical
  *     cancellation-free form k (s |y - y0|^2 / h - 2 u.(y - y0)) / (|u - v s| + 1).
  *   - Cone indices are clamped (min(floor(.), n - 1)); phi in [0, 2 pi); theta from atan2.
+ *     A point on a cone boundary (within 1e-12 relative) belongs to the upper interval.
  *   - Pairs closer than 1e-14 L (L the root box side) are dropped (Section 4.2 end).
  *   - Root box: centre = AABB midpoint, side = max AABB extent * (1 + 2^-30).
  *   - Automatic level count: D = argmin_{d >= 3} |log(N / #relevant level-d boxes / leaf_target)|.
@@ -365,6 +366,11 @@ static void build_cousins(otree *T, int d) {
 /* ------------------------------------------------------------------------- */
 /* cone segments (Eq. deltas, Eq. ConeIntervals, Eq. ConeSegmentSet)          */
 
+static double snap_boundary(double u) {
+    double r = nearbyint(u);
+    return fabs(u - r) <= 1e-12 * (fabs(u) > 1.0 ? fabs(u) : 1.0) ? r : u;
+}
+
 /* Classify x in the cone grid of box b (level d): returns cone id and the local
  * interpolation coordinates t in [-1, 1]^3 (s, theta, phi). */
 static int classify(const otree *T, int d, int b, const double *x, double *t3) {
@@ -378,7 +384,10 @@ static int classify(const otree *T, int d, int b, const double *x, double *t3) {
     double ph = atan2(dy, dx);
     if (ph < 0) ph += 2.0 * OR_PI;
     if (ph >= 2.0 * OR_PI) ph = 0.0;
-    int is = (int)floor(s / L->ds), it = (int)floor(th / L->dth), ip = (int)floor(ph / L->dph);
+    /* a coordinate within 1e-12 (relative) of a cone boundary is placed on it, so the
+     * interval owning a boundary point (the upper one) does not depend on last-bit rounding */
+    double us = snap_boundary(s / L->ds), ut = snap_boundary(th / L->dth), up = snap_boundary(ph / L->dph);
+    int is = (int)floor(us), it = (int)floor(ut), ip = (int)floor(up);
     if (is > L->ns - 1) is = L->ns - 1;
     if (it > L->nC - 1) it = L->nC - 1;
     if (ip > L->nph - 1) ip = L->nph - 1;
@@ -386,9 +395,9 @@ static int classify(const otree *T, int d, int b, const double *x, double *t3) {
     if (it < 0) it = 0;
     if (ip < 0) ip = 0;
     if (t3) {
-        t3[0] = 2.0 * (s / L->ds - is) - 1.0;
-        t3[1] = 2.0 * (th / L->dth - it) - 1.0;
-        t3[2] = 2.0 * (ph / L->dph - ip) - 1.0;
+        t3[0] = 2.0 * (us - is) - 1.0;
+        t3[1] = 2.0 * (ut - it) - 1.0;
+        t3[2] = 2.0 * (up - ip) - 1.0;
     }
     return (is * L->nC + it) * L->nph + ip;
 }
