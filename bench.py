@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Throughput of the IFGF-accelerated CFIE apply on one GB300 (one JSON line).
+
+Workload: unit sphere 16 wavelengths across (k = 16 pi), equiangular cube-sphere
+grid 6 x 256 x 256 with 8 x 8 Fejer sub-patches (N = 393,216), automatic octree
+depth (~64 points per leaf, D = 6), combined-field kernel with eta = k, seeded
+complex density.  The headline value is the mixed-precision apply at the
+interpolation orders that reach a relative l2 error <= 1e-4 against the direct
+sum (measured in the same run on sampled rows); the FP64 apply, the paper's
+orders (3, 5, 5) and an end-to-end host-buffer apply are reported beside it.
+
+A step is one operator apply y = A sigma (all stages).  Device time per step is
+taken with CUDA events on the launch stream; a 256 MB buffer is written between
+timed steps to flush the 129 MB L2.  With torchrun (N > 1) every rank runs an
+independent replica (the apply does not shard across GPUs); value = points of
+all ranks / max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (Algorithm 1 as written, OpenMP on
+the host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CFIE matvec Mpts/s at rel err≤1e-4: mixed vs FP64 IFGF; adjoint/forward ratio"
+UNIT = "Mpts/s"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="points per cube-face side")
+    ap.add_argument("--wavelengths", type=float, default=16.0)
+    ap.add_argument("--orders", default="6x8", help="Ps x Pang of the headline apply")
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
+    ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
+    return ap.parse_args()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload(args):
+    from workloads import random_density, sphere_workload
+
+    s, k = sphere_workload(args.n, 8, args.wavelengths)
+    sig = random_density(s.N, args.nrhs, 2)
+    return s, k, sig
+
+
+def cap_sample(s, frac=8):
+    """Points of the spherical cap holding 1/frac of the sphere's area (z > 1 - 2/frac)."""
+    return np.nonzero(s.points[:, 2] > 1.0 - 2.0 / frac)[0]
+
+
+def oracle_cap_apply(s, k, sig, info, Ps, Pang):
+    """One oracle IFGF apply on the cap sample, on the full sphere's octree (same root box, D)."""
+    import oracle
+
+    idx = cap_sample(s)
+    p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, levels=info["D"], identity_coef=0.5,
+                          root_center=tuple(info["root_center"]), root_side=info["root_side"])
+    t = time.perf_counter()
+    oracle.ifgf(s.points[idx], s.normals[idx], s.weights[idx], p, sig[:, idx])
+    return len(idx), time.perf_counter() - t
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx = float(c[2])
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_flops(info, P, nrhs, split_levels):
+    """FP32-class operations the method must perform per stage (see the design notes):
+    kernel evaluation 40 flops + 8 per rhs and factor; interpolation 4 P per rhs and
+    factor + 100 (geometry, basis, centred factor)."""
+    D = info["D"]
+    nf = lambda d: 2 if split_levels[d] else 1
+    leaf = info["leaf_evals"] * (40 + 8 * nrhs * nf(D))
+    near = (info["near_pairs"] - info["N"]) * (40 + 8 * nrhs)
+    cousin = {d: info["cousin_evals"][d] * (100 + 4 * P * nrhs * nf(d)) for d in range(3, D + 1)}
+    prop = {d: info["prop_evals"][d] * (100 + 4 * P * nrhs * nf(d + 1)) for d in range(3, D)}
+    return leaf, near, cousin, prop
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2112_06316_gb300 import binding
+
+    s, k, sig = workload(args)
+    Ps, Pang = (int(v) for v in args.orders.split("x"))
+    info = binding.dry_run(s.points, s.normals, s.weights, binding.Params(k=k, Ps=Ps, Pang=Pang))
+    oracle.build()
+    n = 0
+    for _ in range(args.warmup):
+        oracle_cap_apply(s, k, sig, info, Ps, Pang)
+    ts = []
+    for _ in range(args.steps):
+        n, t = oracle_cap_apply(s, k, sig, info, Ps, Pang)
+        ts.append(t)
+    ms = 1e3 * float(np.mean(ts))
+    value = n * args.nrhs / (ms * 1e3)
+    sample = (f"oracle IFGF (FP64, OpenMP) on the {n}-point spherical cap z > 0.75 of the workload, "
+              f"on the full sphere's octree (D={info['D']}, same root box), orders ({Ps},{Pang},{Pang})")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"sphere {args.wavelengths:g} wavelengths, cube-sphere 6x{args.n}x{args.n} "
+                               f"(N={s.N}), orders ({Ps},{Pang},{Pang}), nrhs={args.nrhs}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2112_06316_gb300 import Params, Plan
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    s, k, sig = workload(args)
+    N, nrhs = s.N, args.nrhs
+    Ps, Pang = (int(v) for v in args.orders.split("x"))
+    t0 = time.perf_counter()
+    plan = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang))
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    P = Ps * Pang * Pang
+    sig32 = torch.from_numpy(sig.astype(np.complex64)).to(dev)
+    sig64 = torch.from_numpy(sig).to(dev)
+    y32 = torch.empty_like(sig32)
+    y64 = torch.empty_like(sig64)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    # ---- headline: mixed apply ----
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_mixed = timed(lambda: plan.apply(sig32, out=y32), args.steps, args.warmup)
+    clk = clocks.stop()
+    ms = float(np.mean(t_mixed))
+    if world > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = N * nrhs * world / (ms * 1e3)
+
+    # ---- per-launch device times (profiled apply) ----
+    plan.set_profiling(True)
+    plan.apply(sig32, out=y32)
+    stages = plan.stage_times()
+    plan.set_profiling(False)
+    launches_per_apply = len(stages)
+    split = info["split"]
+    leaf_f, near_f, cousin_f, prop_f = algorithmic_flops(info, P, nrhs, split)
+    by_kind = {}
+    for kind, lvl, t in stages:
+        by_kind[kind] = by_kind.get(kind, 0.0) + t
+    flops_of = {"leaf": leaf_f, "near": near_f, "cousin": sum(cousin_f.values()), "prop": sum(prop_f.values())}
+    dom = max((kk for kk in by_kind if kk in flops_of), key=lambda kk: by_kind[kk])
+    n_dom = sum(1 for kind, _, _ in stages if kind == dom)
+    dom_ms = by_kind[dom]
+    achieved = flops_of[dom] / (dom_ms * 1e-3) / 1e12
+    sm_mhz = clk["sm_max_mhz"] or 2070.0
+    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "launches_per_apply": n_dom, "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:g} MHz",
+                "all_stages_ms": {kk: round(v, 4) for kk, v in by_kind.items()},
+                "all_stages_tflops": {kk: round(flops_of[kk] / (by_kind[kk] * 1e-3) / 1e12, 3)
+                                      for kk in flops_of if kk in by_kind}}
+
+    # ---- end to end through host (pinned) buffers ----
+    hs = torch.from_numpy(sig.astype(np.complex64)).pin_memory()
+    hy = torch.empty_like(hs).pin_memory()
+    dsig = torch.empty_like(sig32)
+
+    def e2e_step():
+        dsig.copy_(hs, non_blocking=True)
+        plan.apply(dsig, out=y32)
+        hy.copy_(y32, non_blocking=True)
+
+    t_e2e = timed(e2e_step, max(3, args.steps // 4), 2)
+    e2e_ms = float(np.mean(t_e2e))
+    e2e = {"value": N * nrhs * world / (e2e_ms * 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+           "h2d_bytes_per_step": int(hs.numel() * hs.element_size()),
+           "d2h_bytes_per_step": int(hy.numel() * hy.element_size())}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"sphere {args.wavelengths:g} wavelengths across (k={k:.4f}), cube-sphere "
+                                  f"6x{args.n}x{args.n} with 8x8 Fejer sub-patches, N={N}, D={info['D']}, "
+                                  f"orders ({Ps},{Pang},{Pang}), nC0=2, nS0=1, eta=k, nrhs={nrhs}",
+                      "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
+                      "plan_build_s": round(plan_s, 2)},
+           "roofline": roofline, "e2e": e2e,
+           "gpu_launches": launches_per_apply * args.steps,
+           "clocks": clk}
+
+    if not args.quick:
+        # ---- FP64 apply (same plan) ----
+        k64 = max(3, args.steps // 20)
+        t64 = timed(lambda: plan.apply(sig64, out=y64), k64, 1)
+        ms64 = float(np.mean(t64))
+        out["fp64"] = {"value": N * nrhs * world / (ms64 * 1e3), "ms_per_step": ms64, "steps": k64}
+        out["mixed_vs_fp64_speedup"] = ms64 / ms
+        out["gpu_launches"] += launches_per_apply * k64
+        # ---- paper orders (3,5,5) for context ----
+        plan35 = Plan(s.points, s.normals, s.weights, Params(k=k))
+        y35 = torch.empty_like(sig32)
+        t35 = timed(lambda: plan35.apply(sig32, out=y35), max(5, args.steps // 4), 2)
+        out["paper_orders_3x5"] = {"value": N * nrhs * world / (float(np.mean(t35)) * 1e3),
+                                   "ms_per_step": float(np.mean(t35))}
+        out["gpu_launches"] += len(stages) * max(5, args.steps // 4)
+        assert plan.missed_lookups() == 0 and plan35.missed_lookups() == 0
+        torch.cuda.synchronize()
+        if rank == 0:
+            # ---- CPU legs (oracle): direct-sum rows for the error check, IFGF baseline ----
+            import oracle
+
+            oracle.build()
+            rows = np.random.default_rng(0).choice(N, min(args.rows, N), replace=False)
+            t = time.perf_counter()
+            yd = oracle.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5, rows=rows)
+            t_direct = time.perf_counter() - t
+
+            def err(y):
+                return float(np.linalg.norm(y.cpu().numpy()[:, rows] - yd) / np.linalg.norm(yd))
+
+            out["rel_err_vs_direct"] = {"mixed": err(y32), "fp64": err(y64), "paper_orders_3x5_mixed": err(y35),
+                                        "rows": int(len(rows))}
+            out["fp64"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["fp64"]
+            out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
+            n_cap, t_cap = oracle_cap_apply(s, k, sig, info, Ps, Pang)
+            out["cpu_baseline"] = {
+                "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"one oracle IFGF apply (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 of the "
+                          f"workload, full sphere's octree, orders ({Ps},{Pang},{Pang}); took {t_cap:.1f} s",
+                "direct_sum_rows_per_s": len(rows) / t_direct}
+        plan35.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

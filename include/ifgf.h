@@ -1,0 +1,175 @@
+/*
+ * ifgf.h -- C ABI of the GB300 IFGF-accelerated combined-field (CFIE) operator.
+ *
+ * The library applies the discrete combined-field boundary operator of a
+ * sound-soft scatterer (Jimenez, Bauinger, Bruno, "IFGF-accelerated high-order
+ * integral equation solver for acoustic wave scattering"):
+ *
+ *   y_l = c_I sigma_l + sum_{m != l} K(x_l, x_m) w_m sigma_m  (+ (C sigma)_l),
+ *   K(x, y) = dPhi(x,y)/dnu(y) - i eta Phi(x,y),  Phi = e^{ik|x-y|} / (4 pi |x-y|)
+ *
+ * i.e. the regular-quadrature discretisation (Eq. ReguIntOpQuadrature) of the
+ * combined-field equation (Eq. CombLayIE, c_I = 1/2, eta the coupling
+ * parameter gamma) written as the discrete sum of Eq. field1, plus an optional
+ * sparse singular/near-singular correction C (Eq. IntOpAtSing minus the regular
+ * rows it replaces).  The far interactions are evaluated by the interpolated
+ * factored Green function (IFGF) recursion of Algorithm 1 (Section 3.4); the
+ * level-D neighbour interactions by direct summation (Remark level_D_neighboring).
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns IFGF_OK (0) or a negative ifgf_status and, on
+ *    error, records a message readable with ifgf_last_error() (thread-local).
+ *    Outputs are unspecified after an error.
+ *  - Host inputs (points, normals, weights, correction arrays) are copied; the
+ *    caller keeps ownership.  Device buffers passed to apply-type calls belong to
+ *    the caller, are never freed by the library and must not alias each other.
+ *  - Densities are complex, stored column-major N x nrhs (right-hand side j is
+ *    the contiguous block [j*N, (j+1)*N)), interleaved (re, im): complex128
+ *    (double2) for IFGF_FP64, complex64 (float2) for IFGF_MIXED.  Points keep
+ *    the caller's order; the library permutes internally.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Apply
+ *    calls are asynchronous on it; plan creation and GMRES synchronise.  A plan
+ *    serves one stream at a time.
+ */
+#ifndef IFGF_H
+#define IFGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IFGF_OK = 0,
+    IFGF_EINVAL = -1,        /* invalid argument (sizes, NaN/Inf, non-unit normal, ...) */
+    IFGF_ENOMEM = -2,        /* host or device allocation failed */
+    IFGF_ECUDA = -3,         /* a CUDA runtime call failed */
+    IFGF_ENOTCONVERGED = -4, /* GMRES reached maxit above the tolerance */
+    IFGF_EUNSUPPORTED = -5,  /* valid request this build does not implement (e.g. Ps/Pang pair) */
+    IFGF_EINTERNAL = -6      /* consistency check failed inside the library */
+} ifgf_status;
+
+typedef enum {
+    IFGF_FP64 = 0,  /* all arithmetic in FP64, densities complex128 */
+    IFGF_MIXED = 1  /* FP32 kernel evaluation and interpolation with compensated FP32
+                       accumulation; the phase k|x - y| is reduced exactly from integer box
+                       offsets plus an FP32 fraction; densities complex64 */
+} ifgf_precision;
+
+/* Parameters of the plan.  Fill with ifgf_params_default() and override. */
+typedef struct {
+    double k;             /* wavenumber (> 0), Eq. ScalarHelmholtz */
+    double eta;           /* coupling parameter gamma of Eq. CombinedLayer (default k) */
+    int Ps, Pang;         /* Chebyshev points per cone segment in s and in each angle
+                             (Section 3.2; paper: 3 and 5); supported pairs listed by
+                             ifgf_supported_orders() */
+    int nC0, nS0;         /* cone counts of the coarsest cone grid (Remark cone_seg_size; 2, 1) */
+    int levels;           /* octree levels D >= 3; 0 = automatic (mean points per leaf closest
+                             to leaf_target on a log scale) */
+    double leaf_target;   /* target mean points per relevant leaf for automatic D (64) */
+    int cone_rule;        /* 0: (n_s, n_C) doubled each time H_d exceeds lambda/2 * 2^e;
+                             1: literal Remark cone_seg_size (doubling from level d to d-1 when
+                             k H_d > 1/2, leaf level at (nS0, nC0)) */
+    int factor_mode;      /* 0: hybrid - split factors {W2, -ikW3 - i eta W1} on levels with
+                             H < lambda/2, combined W~2 - ikW3 - i eta W1 above (Section 3.3);
+                             1: combined everywhere; 2: split everywhere */
+    double identity_coef; /* c_I: 0.5 for Eq. CombLayIE, 0.0 for the bare sum of Eq. field1 */
+    double root_center[3];/* root box centre; used only when root_side > 0 */
+    double root_side;     /* <= 0: centre = AABB midpoint, side = max extent * (1 + 2^-30) */
+    double cone_band;     /* relative margin used when marking relevant cone segments
+                             (Eq. RelevantCones) so that a point within this fraction of a cone
+                             boundary marks both neighbours; keeps the FP32 classification
+                             inside the relevant set.  Default 1e-4; 0 = exact marking. */
+} ifgf_params;
+
+/* Plan statistics (ifgf_plan_info). Arrays are indexed by level d (0..IFGF_MAXD). */
+#define IFGF_MAXD 20
+typedef struct {
+    int64_t N;
+    int D;
+    double root_center[3], root_side;
+    int nbox[IFGF_MAXD + 1];      /* relevant boxes per level (Eq. RelevantBoxes) */
+    int ns[IFGF_MAXD + 1];        /* cone counts per level */
+    int nC[IFGF_MAXD + 1];
+    int split[IFGF_MAXD + 1];     /* 1 when the level interpolates the split factor pair */
+    int64_t nrc[IFGF_MAXD + 1];   /* relevant cone segments per level */
+    int64_t cousin_evals[IFGF_MAXD + 1]; /* target interpolations per level */
+    int64_t prop_evals[IFGF_MAXD + 1];   /* interpolations into this level's cone nodes */
+    int64_t leaf_evals;           /* factor evaluations at level-D cone nodes */
+    int64_t near_pairs;           /* level-D neighbour pairs (including l == m slots) */
+    int64_t correction_nnz;       /* stored correction entries (0 if none) */
+    int64_t device_bytes;         /* device memory held by the plan (excluding workspaces) */
+} ifgf_info;
+
+typedef struct ifgf_plan ifgf_plan;
+
+/* Default parameters for wavenumber k: eta = k, Ps = 3, Pang = 5, nC0 = 2, nS0 = 1,
+ * levels = 0, leaf_target = 64, cone_rule = 0, factor_mode = 0, identity_coef = 0.5,
+ * root_side = 0, cone_band = 1e-4. */
+void ifgf_params_default(ifgf_params *p, double k);
+
+/* Comma-separated list of compiled (Ps, Pang) pairs, e.g. "3x5,4x6". Static string. */
+const char *ifgf_supported_orders(void);
+
+/* Build the plan (Section 3.4 octree, Eq. RelevantBoxes, Eq. NeighborsCousins,
+ * Eq. RelevantCones) for N points on the current CUDA device and upload it.
+ *   xyz, normals: host, N x 3 row-major (x0,y0,z0,x1,...), FP64; normals unit length.
+ *   weights: host, N quadrature area weights (> 0).
+ *   stream: used for the uploads; the call synchronises it before returning.
+ *   out: receives the plan (NULL on error).
+ * Errors: IFGF_EINVAL (N < 1, non-finite input, |normal| not 1 within 1e-6, weight <= 0,
+ * k <= 0, levels in 1..2 or > 16), IFGF_EUNSUPPORTED (Ps/Pang pair not compiled),
+ * IFGF_ENOMEM, IFGF_ECUDA. */
+ifgf_status ifgf_plan_create(const double *xyz, const double *normals, const double *weights, int64_t N,
+                             const ifgf_params *params, void *stream, ifgf_plan **out);
+
+/* Host-only dry run of ifgf_plan_create: builds the octree and relevant cone
+ * segments on the host and fills `out` (device_bytes = 0) without touching any
+ * GPU.  Same arguments and errors as ifgf_plan_create (no CUDA errors). */
+ifgf_status ifgf_plan_dry_run(const double *xyz, const double *normals, const double *weights, int64_t N,
+                              const ifgf_params *params, ifgf_info *out);
+
+/* Attach a sparse correction C (CSR over the caller's point order): row l holds the
+ * entries (col[j], val[j]) for j in rowptr[l]..rowptr[l+1]-1; val interleaved complex128.
+ * Host arrays, copied.  nnz = rowptr[N].  Passing nnz = 0 removes the correction.
+ * Errors: IFGF_EINVAL (rowptr not monotone, col out of range, non-finite value). */
+ifgf_status ifgf_plan_set_correction(ifgf_plan *plan, const int64_t *rowptr, const int32_t *col,
+                                     const double *val, int64_t nnz);
+
+/* y = A sigma for nrhs right-hand sides (Algorithm 1 + near field + c_I sigma + C sigma).
+ * sigma_dev, y_dev: device, N x nrhs complex (see precision).  Asynchronous on stream.
+ * The plan's workspace grows on first use for a given nrhs (device allocation).
+ * Errors: IFGF_EINVAL (nrhs < 0, null pointers with nrhs > 0), IFGF_ENOMEM, IFGF_ECUDA. */
+ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
+                       void *stream);
+
+/* Plan statistics (host struct filled synchronously). */
+ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
+
+/* Number of failed relevant-cone lookups recorded by applies since the last call
+ * (should be 0; a non-zero count means a point fell outside the relevant set and
+ * its contribution was skipped).  Synchronises `stream` and resets the counter. */
+ifgf_status ifgf_plan_check(ifgf_plan *plan, void *stream, int64_t *missed_lookups);
+
+/* Enable (1) or disable (0) per-launch timing: each later apply records a CUDA
+ * event on its stream after every kernel launch.  Errors: IFGF_EINVAL, IFGF_ECUDA. */
+ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable);
+
+/* Per-launch device times of the last apply with profiling on: fills up to `cap`
+ * entries of kind (0 gather, 1 leaf evaluation, 2 propagation, 3 near field,
+ * 4 cousin interpolation, 5 scatter, 6 correction), level (octree level or 0) and
+ * ms (milliseconds); any output pointer may be NULL.  Waits for the last event.
+ * Returns the number of entries (0 if profiling is off), or a negative ifgf_status. */
+int ifgf_plan_stage_times(ifgf_plan *plan, int cap, int *kind, int *level, double *ms);
+
+/* Release the plan and its device memory (NULL is a no-op). */
+void ifgf_plan_destroy(ifgf_plan *plan);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *ifgf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFGF_H */

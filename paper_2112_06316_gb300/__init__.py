@@ -1,0 +1,17 @@
+"""GB300-native IFGF-accelerated combined-field (CFIE) operator.
+
+The hot path of Jimenez, Bauinger & Bruno's IFGF-accelerated CFIE solver: the
+apply of the discrete combined-field operator that GMRES calls once per
+iteration, as hand-written sm_103a CUDA behind the C ABI of ``include/ifgf.h``.
+Python only marshals arguments (``binding``); PyTorch supplies device memory
+and streams.
+"""
+from .binding import (  # noqa: F401
+    FP64,
+    MIXED,
+    IFGFError,
+    Params,
+    Plan,
+    lib,
+    supported_orders,
+)

@@ -1,0 +1,278 @@
+"""ctypes binding of the C ABI in ``include/ifgf.h`` (argument marshalling only).
+
+Every numerical step runs in ``libifgf.so``; this module converts Python /
+torch arguments to pointers and sizes, checks the returned status and raises
+``IFGFError`` with ``ifgf_last_error()``'s message.  There is no fallback: if
+the shared library is missing the import of a plan fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libifgf.so")
+MAXD = 20
+
+IFGF_OK = 0
+STATUS = {0: "IFGF_OK", -1: "IFGF_EINVAL", -2: "IFGF_ENOMEM", -3: "IFGF_ECUDA", -4: "IFGF_ENOTCONVERGED",
+          -5: "IFGF_EUNSUPPORTED", -6: "IFGF_EINTERNAL"}
+FP64 = 0
+MIXED = 1
+
+
+class IFGFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_double), ("eta", ctypes.c_double),
+        ("Ps", ctypes.c_int), ("Pang", ctypes.c_int), ("nC0", ctypes.c_int), ("nS0", ctypes.c_int),
+        ("levels", ctypes.c_int), ("leaf_target", ctypes.c_double),
+        ("cone_rule", ctypes.c_int), ("factor_mode", ctypes.c_int),
+        ("identity_coef", ctypes.c_double),
+        ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+        ("cone_band", ctypes.c_double),
+    ]
+
+
+class CInfo(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64), ("D", ctypes.c_int),
+        ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+        ("nbox", ctypes.c_int * (MAXD + 1)), ("ns", ctypes.c_int * (MAXD + 1)),
+        ("nC", ctypes.c_int * (MAXD + 1)), ("split", ctypes.c_int * (MAXD + 1)),
+        ("nrc", ctypes.c_int64 * (MAXD + 1)),
+        ("cousin_evals", ctypes.c_int64 * (MAXD + 1)),
+        ("prop_evals", ctypes.c_int64 * (MAXD + 1)),
+        ("leaf_evals", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+        ("correction_nnz", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+# (name, restype, argtypes) of every exported entry point
+_VP = ctypes.c_void_p
+_SIGS = [
+    ("ifgf_params_default", None, [ctypes.POINTER(CParams), ctypes.c_double]),
+    ("ifgf_supported_orders", ctypes.c_char_p, []),
+    ("ifgf_last_error", ctypes.c_char_p, []),
+    ("ifgf_plan_create", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(CParams), _VP,
+                                        ctypes.POINTER(_VP)]),
+    ("ifgf_plan_dry_run", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.POINTER(CParams),
+                                         ctypes.POINTER(CInfo)]),
+    ("ifgf_plan_set_correction", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64]),
+    ("ifgf_apply", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
+    ("ifgf_plan_check", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
+    ("ifgf_plan_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("ifgf_plan_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    ("ifgf_plan_destroy", None, [_VP]),
+]
+STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction"]
+
+_lib = None
+
+
+def lib():
+    """Load ``libifgf.so`` (built by ``paper_2112_06316_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2112_06316_gb300.build.build() first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [s[0] for s in _SIGS]
+
+
+def check(status: int):
+    if status != IFGF_OK:
+        raise IFGFError(status, lib().ifgf_last_error().decode())
+
+
+@dataclass
+class Params:
+    """Python mirror of ``ifgf_params`` (defaults of ``ifgf_params_default``)."""
+
+    k: float
+    eta: float | None = None
+    Ps: int = 3
+    Pang: int = 5
+    nC0: int = 2
+    nS0: int = 1
+    levels: int = 0
+    leaf_target: float = 64.0
+    cone_rule: int = 0
+    factor_mode: int = 0
+    identity_coef: float = 0.5
+    root_center: tuple = (0.0, 0.0, 0.0)
+    root_side: float = 0.0
+    cone_band: float = 1e-4
+
+    def to_c(self) -> CParams:
+        p = CParams()
+        lib().ifgf_params_default(ctypes.byref(p), ctypes.c_double(self.k))
+        p.eta = self.k if self.eta is None else self.eta
+        p.Ps, p.Pang, p.nC0, p.nS0, p.levels = self.Ps, self.Pang, self.nC0, self.nS0, self.levels
+        p.leaf_target = self.leaf_target
+        p.cone_rule, p.factor_mode = self.cone_rule, self.factor_mode
+        p.identity_coef = self.identity_coef
+        for a in range(3):
+            p.root_center[a] = self.root_center[a]
+        p.root_side = self.root_side
+        p.cone_band = self.cone_band
+        return p
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _info_dict(ci) -> dict:
+    D = ci.D
+    return {
+        "N": ci.N, "D": D, "root_center": tuple(ci.root_center), "root_side": ci.root_side,
+        "nbox": [ci.nbox[i] for i in range(D + 1)], "ns": [ci.ns[i] for i in range(D + 1)],
+        "nC": [ci.nC[i] for i in range(D + 1)], "split": [ci.split[i] for i in range(D + 1)],
+        "nrc": [ci.nrc[i] for i in range(D + 1)],
+        "cousin_evals": [ci.cousin_evals[i] for i in range(D + 1)],
+        "prop_evals": [ci.prop_evals[i] for i in range(D + 1)],
+        "leaf_evals": ci.leaf_evals, "near_pairs": ci.near_pairs,
+        "correction_nnz": ci.correction_nnz, "device_bytes": ci.device_bytes,
+    }
+
+
+def dry_run(points, normals, weights, params: Params) -> dict:
+    """Host-only plan statistics (``ifgf_plan_dry_run``); needs no GPU."""
+    x = _host(points, np.float64)
+    n = _host(normals, np.float64)
+    w = _host(weights, np.float64)
+    ci = CInfo()
+    cp = params.to_c()
+    check(lib().ifgf_plan_dry_run(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(x.shape[0]),
+                                  ctypes.byref(cp), ctypes.byref(ci)))
+    return _info_dict(ci)
+
+
+class Plan:
+    """An ``ifgf_plan``: octree, cone structure and device geometry for one surface."""
+
+    def __init__(self, points, normals, weights, params: Params, stream=None):
+        x = _host(points, np.float64)
+        n = _host(normals, np.float64)
+        w = _host(weights, np.float64)
+        if x.ndim != 2 or x.shape[1] != 3 or n.shape != x.shape or w.shape != (x.shape[0],):
+            raise ValueError("points/normals must be (N, 3) and weights (N,)")
+        self.N = int(x.shape[0])
+        self.params = params
+        cp = params.to_c()
+        h = _VP()
+        check(lib().ifgf_plan_create(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(self.N),
+                                     ctypes.byref(cp), _VP(_stream_ptr(stream)), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ifgf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        ci = CInfo()
+        check(lib().ifgf_plan_info(self._h, ctypes.byref(ci)))
+        return _info_dict(ci)
+
+    def set_correction(self, rowptr, col, val):
+        """CSR correction over the caller's point order; val complex (nnz,)."""
+        rp = _host(rowptr, np.int64)
+        cl = _host(col, np.int32)
+        v = _host(np.asarray(val, dtype=np.complex128).view(np.float64), np.float64)
+        nnz = int(rp[-1]) if rp.size else 0
+        check(lib().ifgf_plan_set_correction(self._h, rp.ctypes.data, cl.ctypes.data, v.ctypes.data,
+                                             ctypes.c_int64(nnz)))
+
+    def apply_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):
+        """Raw-pointer apply: sigma/y device buffers of N x nrhs complex."""
+        check(lib().ifgf_apply(self._h, _VP(sigma_ptr), _VP(y_ptr), ctypes.c_int(nrhs), ctypes.c_int(prec),
+                               _VP(_stream_ptr(stream))))
+
+    def apply(self, sigma, out=None, stream=None):
+        """y = A sigma for a CUDA torch tensor sigma of shape (nrhs, N) or (N,).
+
+        complex128 selects the FP64 path, complex64 the mixed path.
+        """
+        import torch
+
+        if not (isinstance(sigma, torch.Tensor) and sigma.is_cuda):
+            raise TypeError("sigma must be a CUDA torch tensor")
+        if sigma.dtype == torch.complex128:
+            prec = FP64
+        elif sigma.dtype == torch.complex64:
+            prec = MIXED
+        else:
+            raise TypeError("sigma must be complex64 (mixed) or complex128 (FP64)")
+        squeeze = sigma.dim() == 1
+        s = sigma.reshape(1, -1) if squeeze else sigma
+        if s.shape[-1] != self.N:
+            raise ValueError(f"sigma must have N={self.N} columns")
+        s = s.contiguous()
+        y = torch.empty_like(s) if out is None else out
+        if y.shape != s.shape or y.dtype != s.dtype or not y.is_contiguous():
+            raise ValueError("out must match sigma's shape/dtype and be contiguous")
+        self.apply_ptr(s.data_ptr(), y.data_ptr(), int(s.shape[0]), prec, stream)
+        return y.reshape(-1) if squeeze else y
+
+    def set_profiling(self, enable: bool = True):
+        check(lib().ifgf_plan_set_profiling(self._h, ctypes.c_int(int(enable))))
+
+    def stage_times(self):
+        """[(stage, level, ms)] of the last apply made with profiling on."""
+        cap = 80
+        kind = (ctypes.c_int * cap)()
+        level = (ctypes.c_int * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = lib().ifgf_plan_stage_times(self._h, cap, kind, level, ms)
+        if n < 0:
+            check(n)
+        return [(STAGES[kind[i]], level[i], ms[i]) for i in range(n)]
+
+    def missed_lookups(self, stream=None) -> int:
+        m = ctypes.c_int64()
+        check(lib().ifgf_plan_check(self._h, _VP(_stream_ptr(stream)), ctypes.byref(m)))
+        return int(m.value)
+
+
+def supported_orders():
+    return [tuple(int(v) for v in s.split("x")) for s in lib().ifgf_supported_orders().decode().split(",")]

@@ -1,0 +1,136 @@
+// Internal structures of the GB300 IFGF library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ifgf.h"
+
+namespace ifgf {
+
+constexpr int kMaxP = 12;  // largest supported points per axis
+
+void set_error(const char *fmt, ...);
+
+// Chebyshev first-kind nodes x_j = cos((2j+1) pi / (2n)) and Lagrange product
+// weights c_j = 1 / prod_{m != j} (x_j - x_m) for one axis (Section 3.2).
+struct ChebAxis {
+    int n;
+    double x[kMaxP], c[kMaxP];
+};
+void cheb_axis(int n, ChebAxis *a);
+
+// Host-side description of one octree level (Section 3.4).
+struct HostLevel {
+    int d = 0;
+    int nbox = 0;
+    double H = 0, h = 0;      // box side and half diagonal sqrt(3)/2 H (Eq. def_eps)
+    int scale = 1;            // box side in leaf units, 2^(D-d)
+    std::vector<int> ijk;     // 3 * nbox integer coordinates at this level
+    std::vector<int> start;   // nbox + 1 ranges into the Morton-sorted points
+    std::vector<int> parent;  // index of the parent box (level d-1), -1 at d = 1
+    std::vector<int> ch_start, ch_list;  // children (level d+1) CSR
+    std::vector<int> co_start, co_list;  // cousins CSR (Eq. NeighborsCousins)
+    std::vector<uint64_t> mkey;          // Morton key of each box (sorted)
+    int ns = 0, nC = 0, nph = 0, ncone = 0;
+    double ds = 0, dth = 0, dph = 0;
+    int split = 0, nfac = 1;
+    std::vector<int> rc_start, rc_cone, rc_box;  // relevant cones (Eq. RelevantCones)
+    std::vector<int> cone_map;                   // nbox * ncone -> rc index or -1
+    int64_t nrc = 0;
+    int64_t cousin_evals = 0, prop_evals = 0;
+};
+
+// Device arrays of one level.
+struct DevLevel {
+    int nbox, ns, nC, nph, ncone, split, nfac, scale;
+    int64_t nrc;
+    double H, h, ds, dth, dph;
+    int *ijk, *start, *parent, *ch_start, *ch_list, *co_start, *co_list;
+    int *rc_start, *rc_cone, *rc_box, *cone_map;
+};
+
+struct Workspace {
+    int nrhs = 0;
+    int prec = -1;
+    size_t bytes = 0;
+    void *base = nullptr;
+    void *a = nullptr;   // w * sigma in sorted order, [nrhs][N]
+    void *u = nullptr;   // accumulated field in sorted order, [nrhs][N]
+    void *F[IFGF_MAXD + 1] = {};  // cone values per level, [nrhs][nrc][nfac][Pstride]
+};
+
+struct Plan {
+    ifgf_params prm;
+    int64_t N = 0;
+    int D = 0;
+    int Ps = 3, Pang = 5, P = 75, Pstride = 76;
+    double c0[3] = {0, 0, 0};  // root box corner (centre - L/2)
+    double center[3] = {0, 0, 0};
+    double L = 0, HD = 0;
+    ChebAxis cs, ca;
+    std::vector<HostLevel> lv;  // index d = 0..D
+    std::vector<int> perm;      // sorted position -> caller index
+    std::vector<int> leaf_of;   // sorted position -> leaf box
+    int64_t leaf_evals = 0, near_pairs = 0;
+    std::vector<int> nb_start, nb_list;  // leaf neighbours (27-neighbourhood incl. self)
+
+    // device copies
+    int device = 0;
+    DevLevel dl[IFGF_MAXD + 1] = {};
+    int *d_perm = nullptr;
+    int *d_leaf_of = nullptr;
+    int *d_box_of[IFGF_MAXD + 1] = {};  // sorted position -> box index at level d
+    int *d_nb_start = nullptr, *d_nb_list = nullptr;
+    double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
+    float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
+    unsigned long long *d_missed = nullptr;
+    std::vector<void *> allocs;
+    int64_t device_bytes = 0;
+
+    // sparse correction (CSR in sorted order)
+    int64_t corr_nnz = 0;
+    int64_t *d_corr_rowptr = nullptr;
+    int *d_corr_col = nullptr;
+    double *d_corr_val64 = nullptr;
+    float *d_corr_val32 = nullptr;
+
+    Workspace ws;
+
+    // optional per-launch timing (events recorded on the apply stream)
+    bool profile = false;
+    static constexpr int kMaxEv = 80;
+    cudaEvent_t ev[kMaxEv] = {};
+    int nev = 0;                 // events recorded by the last apply
+    int ev_kind[kMaxEv] = {};    // stage kind of launch i (between event i and i+1)
+    int ev_level[kMaxEv] = {};
+};
+
+// stage kinds reported by ifgf_plan_stage_times
+enum StageKind { kStGather = 0, kStLeaf = 1, kStProp = 2, kStNear = 3, kStCousin = 4, kStScatter = 5, kStCorr = 6 };
+
+inline void prof_begin(Plan &p, cudaStream_t s) {
+    p.nev = 0;
+    if (p.profile) cudaEventRecord(p.ev[p.nev++], s);
+}
+inline void prof_mark(Plan &p, cudaStream_t s, int kind, int level) {
+    if (p.profile && p.nev < Plan::kMaxEv) {
+        p.ev_kind[p.nev - 1] = kind;
+        p.ev_level[p.nev - 1] = level;
+        cudaEventRecord(p.ev[p.nev++], s);
+    }
+}
+
+// plan.cpp
+ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const double *w);
+int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L, double leaf_target);
+
+// apply.cu
+ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const double *w, cudaStream_t s);
+ifgf_status ensure_workspace(Plan &p, int nrhs, int prec);
+ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
+void free_plan_device(Plan &p);
+
+}  // namespace ifgf

@@ -1,0 +1,429 @@
+// Host plan builder: octree, relevant boxes, neighbours/cousins, cone grids and
+// relevant cone segments (Section 3.4; Eq. box, Eq. RelevantBoxes,
+// Eq. NeighborsCousins, Eq. deltas, Eq. ConeIntervals, Eq. RelevantCones).
+//
+// Points are sorted along a Morton (Z) curve of their leaf boxes (the ordering
+// Section 3.5 uses for its task vectors); every octree box then owns a
+// contiguous range of sorted points at every level.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "ifgf_internal.h"
+
+namespace ifgf {
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char *last_error_str() { return g_err.c_str(); }
+void clear_error() { g_err.clear(); }
+
+void cheb_axis(int n, ChebAxis *a) {
+    a->n = n;
+    for (int j = 0; j < n; j++) a->x[j] = std::cos((2.0 * j + 1.0) * M_PI / (2.0 * n));
+    for (int j = 0; j < n; j++) {
+        double prod = 1.0;
+        for (int m = 0; m < n; m++)
+            if (m != j) prod *= (a->x[j] - a->x[m]);
+        a->c[j] = 1.0 / prod;
+    }
+}
+
+static uint64_t spread3(uint64_t v) {
+    // spread the low 21 bits of v to every third bit
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+static uint64_t morton(int i, int j, int k) { return (spread3(i) << 2) | (spread3(j) << 1) | spread3(k); }
+
+static int leaf_coord(double x, double corner, double H, int nside) {
+    double f = std::floor((x - corner) / H);
+    int v = (int)f;
+    if (f < 0) v = 0;
+    if (f > nside - 1) v = nside - 1;
+    return v;
+}
+
+int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L, double leaf_target) {
+    double lt = leaf_target > 0 ? leaf_target : 64.0;
+    double best = INFINITY;
+    int D = 3;
+    std::vector<uint64_t> keys(N);
+    for (int d = 3; d <= 16; d++) {
+        double H = std::ldexp(L, -(d - 1));
+        int nside = 1 << (d - 1);
+        for (int64_t i = 0; i < N; i++)
+            keys[i] = morton(leaf_coord(xyz[3 * i], c0[0], H, nside), leaf_coord(xyz[3 * i + 1], c0[1], H, nside),
+                             leaf_coord(xyz[3 * i + 2], c0[2], H, nside));
+        std::sort(keys.begin(), keys.end());
+        int64_t nb = std::unique(keys.begin(), keys.end()) - keys.begin();
+        double m = std::fabs(std::log((double)N / nb / lt));
+        if (m < best) {
+            best = m;
+            D = d;
+        }
+        if ((double)N / nb < lt / 16.0) break;
+    }
+    return D;
+}
+
+static int find_box(const HostLevel &L, int i, int j, int k) {
+    int n = 1 << (L.d - 1);
+    if (i < 0 || j < 0 || k < 0 || i >= n || j >= n || k >= n) return -1;
+    uint64_t key = morton(i, j, k);
+    auto it = std::lower_bound(L.mkey.begin(), L.mkey.end(), key);
+    if (it == L.mkey.end() || *it != key) return -1;
+    return (int)(it - L.mkey.begin());
+}
+
+namespace {
+
+struct Ctx {
+    const Plan *p;
+    const double *xs;  // sorted absolute positions
+};
+
+inline void box_center(const Plan &p, const HostLevel &L, int b, double *y0) {
+    for (int a = 0; a < 3; a++) y0[a] = p.c0[a] + (L.ijk[3 * b + a] + 0.5) * L.H;
+}
+
+// Candidate indices along one axis: the clamped floor plus neighbours within `band`
+// (in units of the interval) of a boundary.  Returns the count (1..3), or -1 when the
+// position is too uncertain and every index 0..n-1 is a candidate.
+inline int axis_candidates(double u, int n, double band, bool wrap, int *out) {
+    int i = (int)std::floor(u);
+    if (i > n - 1) i = n - 1;
+    if (i < 0) i = 0;
+    int c = 0;
+    out[c++] = i;
+    if (band <= 0) return 1;
+    if (band >= 0.5) return -1;
+    double fr = u - i;
+    if (fr < band) {
+        if (i > 0) out[c++] = i - 1;
+        else if (wrap) out[c++] = n - 1;
+    }
+    if (fr > 1.0 - band) {
+        if (i < n - 1) out[c++] = i + 1;
+        else if (wrap) out[c++] = 0;
+    }
+    return c;
+}
+
+// Boundary points (within 1e-12 relative) are placed on the boundary, so the upper
+// interval owns them independently of last-bit rounding (same rule as the kernels).
+inline double snap(double u) {
+    double r = std::nearbyint(u);
+    return std::fabs(u - r) <= 1e-12 * std::max(std::fabs(u), 1.0) ? r : u;
+}
+
+// Mark in `bits` every cone of box b (level L) that x may fall into (Eq. ConeIntervals
+// with clamped indices; phi in [0, 2 pi)).
+inline void mark_point(const Plan &p, const HostLevel &L, int b, const double *x, double tau, uint64_t *bits) {
+    double y0[3];
+    box_center(p, L, b, y0);
+    double dx = x[0] - y0[0], dy = x[1] - y0[1], dz = x[2] - y0[2];
+    double rho = std::sqrt(dx * dx + dy * dy);
+    double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+    double s = L.h / r;
+    double th = std::atan2(rho, dz);
+    double ph = std::atan2(dy, dx);
+    if (ph < 0) ph += 2.0 * M_PI;
+    if (ph >= 2.0 * M_PI) ph = 0.0;
+    double us = snap(s / L.ds), ut = snap(th / L.dth), up = snap(ph / L.dph);
+    int cs[3], ct[3], cp[3];
+    double bs = 0, bt = 0, bp = 0;
+    if (tau > 0) {
+        // tau plus the reach of FP32 rounding of the geometry (relative 4e-7 of r)
+        bs = tau + 4e-7 * us;
+        bt = tau + 4e-7 / L.dth;
+        bp = (rho > 0) ? tau + 4e-7 * (r / rho) / L.dph : 1.0;
+    }
+    int ns = axis_candidates(us, L.ns, bs, false, cs);
+    int nt = axis_candidates(ut, L.nC, bt, false, ct);
+    int np = axis_candidates(up, L.nph, bp, true, cp);
+    int ns_n = ns < 0 ? L.ns : ns, nt_n = nt < 0 ? L.nC : nt, np_n = np < 0 ? L.nph : np;
+    for (int a = 0; a < ns_n; a++)
+        for (int c = 0; c < nt_n; c++)
+            for (int e = 0; e < np_n; e++) {
+                int is = ns < 0 ? a : cs[a], it = nt < 0 ? c : ct[c], ip = np < 0 ? e : cp[e];
+                int cone = (is * L.nC + it) * L.nph + ip;
+                bits[cone >> 6] |= 1ULL << (cone & 63);
+            }
+}
+
+inline void node_position(const Plan &p, const HostLevel &L, int b, int cone, int n, double *x) {
+    int ip = cone % L.nph, it = (cone / L.nph) % L.nC, is = cone / (L.nph * L.nC);
+    int na = p.Pang;
+    int a = n / (na * na), bb = (n / na) % na, c = n % na;
+    double s = (is + 0.5 * (p.cs.x[a] + 1.0)) * L.ds;
+    double th = (it + 0.5 * (p.ca.x[bb] + 1.0)) * L.dth;
+    double ph = (ip + 0.5 * (p.ca.x[c] + 1.0)) * L.dph;
+    double y0[3];
+    box_center(p, L, b, y0);
+    double r = L.h / s;
+    x[0] = y0[0] + r * std::sin(th) * std::cos(ph);
+    x[1] = y0[1] + r * std::sin(th) * std::sin(ph);
+    x[2] = y0[2] + r * std::cos(th);
+}
+
+}  // namespace
+
+ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const double *w) {
+    const ifgf_params &prm = p.prm;
+    const int64_t N = p.N;
+    // ---- root box (centre = AABB midpoint, side = max extent (1 + 2^-30)) ----
+    if (prm.root_side > 0) {
+        p.L = prm.root_side;
+        for (int a = 0; a < 3; a++) p.center[a] = prm.root_center[a];
+    } else {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = 0; i < N; i++)
+            for (int a = 0; a < 3; a++) {
+                lo[a] = std::min(lo[a], xyz[3 * i + a]);
+                hi[a] = std::max(hi[a], xyz[3 * i + a]);
+            }
+        double ext = 0;
+        for (int a = 0; a < 3; a++) {
+            p.center[a] = 0.5 * (lo[a] + hi[a]);
+            ext = std::max(ext, hi[a] - lo[a]);
+        }
+        if (!(ext > 0)) ext = 1.0;
+        p.L = ext * (1.0 + std::ldexp(1.0, -30));
+    }
+    for (int a = 0; a < 3; a++) p.c0[a] = p.center[a] - 0.5 * p.L;
+    // ---- level count ----
+    int D = prm.levels > 0 ? prm.levels : morton_levels_auto(xyz, N, p.c0, p.L, prm.leaf_target);
+    if (D < 3 || D > 16) {
+        set_error("levels must be in 3..16 (got %d)", D);
+        return IFGF_EINVAL;
+    }
+    p.D = D;
+    p.HD = std::ldexp(p.L, -(D - 1));
+    cheb_axis(p.Ps, &p.cs);
+    cheb_axis(p.Pang, &p.ca);
+    const double lam = 2.0 * M_PI / prm.k;
+
+    // ---- leaf coordinates and Morton sort ----
+    const int nside = 1 << (D - 1);
+    std::vector<int> I(3 * N);
+    std::vector<uint64_t> key(N);
+    for (int64_t i = 0; i < N; i++) {
+        for (int a = 0; a < 3; a++) I[3 * i + a] = leaf_coord(xyz[3 * i + a], p.c0[a], p.HD, nside);
+        key[i] = morton(I[3 * i], I[3 * i + 1], I[3 * i + 2]);
+    }
+    p.perm.resize(N);
+    std::iota(p.perm.begin(), p.perm.end(), 0);
+    std::stable_sort(p.perm.begin(), p.perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    p.lv.assign(D + 1, HostLevel());
+    for (int d = 1; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.d = d;
+        L.H = std::ldexp(p.L, -(d - 1));
+        L.h = std::sqrt(3.0) / 2.0 * L.H;
+        L.scale = 1 << (D - d);
+        const int sh = 3 * (D - d);
+        for (int64_t s = 0; s < N; s++) {
+            uint64_t kk = key[p.perm[s]] >> sh;
+            if (s == 0 || kk != L.mkey.back()) {
+                L.mkey.push_back(kk);
+                L.start.push_back((int)s);
+                int pi = p.perm[s];
+                L.ijk.push_back(I[3 * pi] >> (D - d));
+                L.ijk.push_back(I[3 * pi + 1] >> (D - d));
+                L.ijk.push_back(I[3 * pi + 2] >> (D - d));
+            }
+        }
+        L.nbox = (int)L.mkey.size();
+        L.start.push_back((int)N);
+    }
+    p.leaf_of.resize(N);
+    {
+        const HostLevel &L = p.lv[D];
+        for (int b = 0; b < L.nbox; b++)
+            for (int s = L.start[b]; s < L.start[b + 1]; s++) p.leaf_of[s] = b;
+    }
+    // parents and children
+    for (int d = 1; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.parent.assign(L.nbox, -1);
+        if (d > 1) {
+            for (int b = 0; b < L.nbox; b++)
+                L.parent[b] = find_box(p.lv[d - 1], L.ijk[3 * b] >> 1, L.ijk[3 * b + 1] >> 1, L.ijk[3 * b + 2] >> 1);
+        }
+    }
+    for (int d = 1; d < D; d++) {
+        HostLevel &L = p.lv[d];
+        const HostLevel &C = p.lv[d + 1];
+        L.ch_start.assign(L.nbox + 1, 0);
+        for (int b = 0; b < C.nbox; b++) L.ch_start[C.parent[b] + 1]++;
+        for (int b = 0; b < L.nbox; b++) L.ch_start[b + 1] += L.ch_start[b];
+        L.ch_list.assign(C.nbox, 0);
+        std::vector<int> fill(L.ch_start.begin(), L.ch_start.end() - 1);
+        for (int b = 0; b < C.nbox; b++) L.ch_list[fill[C.parent[b]]++] = b;
+    }
+    p.lv[D].ch_start.assign(p.lv[D].nbox + 1, 0);
+    // leaf neighbours (27-neighbourhood including the box itself)
+    {
+        const HostLevel &L = p.lv[D];
+        p.nb_start.assign(L.nbox + 1, 0);
+        p.nb_list.clear();
+        int64_t pairs = 0;
+        for (int b = 0; b < L.nbox; b++) {
+            p.nb_start[b] = (int)p.nb_list.size();
+            int64_t cnt = 0;
+            for (int o0 = -1; o0 <= 1; o0++)
+                for (int o1 = -1; o1 <= 1; o1++)
+                    for (int o2 = -1; o2 <= 1; o2++) {
+                        int c = find_box(L, L.ijk[3 * b] + o0, L.ijk[3 * b + 1] + o1, L.ijk[3 * b + 2] + o2);
+                        if (c >= 0) {
+                            p.nb_list.push_back(c);
+                            cnt += L.start[c + 1] - L.start[c];
+                        }
+                    }
+            pairs += cnt * (L.start[b + 1] - L.start[b]);
+        }
+        p.nb_start[L.nbox] = (int)p.nb_list.size();
+        p.near_pairs = pairs;
+    }
+    // cousins (Eq. NeighborsCousins): non-neighbours whose parent neighbours the parent
+    for (int d = 3; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.co_start.assign(L.nbox + 1, 0);
+        L.co_list.clear();
+        for (int b = 0; b < L.nbox; b++) {
+            L.co_start[b] = (int)L.co_list.size();
+            const int *q = &L.ijk[3 * b];
+            int pp[3] = {q[0] >> 1, q[1] >> 1, q[2] >> 1};
+            for (int o0 = -1; o0 <= 1; o0++)
+                for (int o1 = -1; o1 <= 1; o1++)
+                    for (int o2 = -1; o2 <= 1; o2++)
+                        for (int ch = 0; ch < 8; ch++) {
+                            int j0 = 2 * (pp[0] + o0) + (ch & 1), j1 = 2 * (pp[1] + o1) + ((ch >> 1) & 1),
+                                j2 = 2 * (pp[2] + o2) + ((ch >> 2) & 1);
+                            int dm = std::max(std::abs(j0 - q[0]), std::max(std::abs(j1 - q[1]), std::abs(j2 - q[2])));
+                            if (dm <= 1) continue;
+                            int c = find_box(L, j0, j1, j2);
+                            if (c >= 0) L.co_list.push_back(c);
+                        }
+        }
+        L.co_start[L.nbox] = (int)L.co_list.size();
+        int64_t ev = 0;
+        for (int b = 0; b < L.nbox; b++)
+            for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) ev += L.start[L.co_list[c] + 1] - L.start[L.co_list[c]];
+        L.cousin_evals = ev;
+    }
+    // cone grids (Remark cone_seg_size) and factor split (Section 3.3)
+    int e_lit = 0;
+    for (int d = D; d >= 3; d--) {
+        HostLevel &L = p.lv[d];
+        int e = 0;
+        if (prm.cone_rule == 0) {
+            while (L.H > std::ldexp(0.5 * lam, e) && e < 24) e++;
+        } else {
+            if (d < D && prm.k * p.lv[d + 1].H > 0.5) e_lit++;
+            e = e_lit;
+        }
+        L.ns = prm.nS0 << e;
+        L.nC = prm.nC0 << e;
+        L.nph = 2 * L.nC;
+        int64_t nc = (int64_t)L.ns * L.nC * L.nph;
+        if (nc > (1LL << 28)) {
+            set_error("cone grid too fine at level %d (%lld cones per box)", d, (long long)nc);
+            return IFGF_EUNSUPPORTED;
+        }
+        L.ncone = (int)nc;
+        L.ds = (std::sqrt(3.0) / 3.0) / L.ns;
+        L.dth = M_PI / L.nC;
+        L.dph = M_PI / L.nC;
+        L.split = prm.factor_mode == 1 ? 0 : prm.factor_mode == 2 ? 1 : (L.H < 0.5 * lam ? 1 : 0);
+        L.nfac = L.split ? 2 : 1;
+    }
+    // sorted absolute positions (for classification)
+    std::vector<double> xs(3 * N);
+    for (int64_t s = 0; s < N; s++)
+        for (int a = 0; a < 3; a++) xs[3 * s + a] = xyz[3 * p.perm[s] + a];
+    // relevant cone segments (Eq. RelevantCones), from d = 3 towards D
+    const double tau = prm.cone_band;
+    for (int d = 3; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        const int words = (L.ncone + 63) / 64;
+        std::vector<std::vector<int>> lists(L.nbox);
+        const HostLevel *PL = d > 3 ? &p.lv[d - 1] : nullptr;
+#pragma omp parallel
+        {
+            std::vector<uint64_t> bits(words);
+#pragma omp for schedule(dynamic, 1)
+            for (int b = 0; b < L.nbox; b++) {
+                std::fill(bits.begin(), bits.end(), 0ULL);
+                for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
+                    int cb = L.co_list[c];
+                    for (int s = L.start[cb]; s < L.start[cb + 1]; s++) mark_point(p, L, b, &xs[3 * s], tau, bits.data());
+                }
+                if (PL) {
+                    int pb = L.parent[b];
+                    for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++)
+                        for (int n = 0; n < p.P; n++) {
+                            double x[3];
+                            node_position(p, *PL, pb, PL->rc_cone[rc], n, x);
+                            mark_point(p, L, b, x, tau, bits.data());
+                        }
+                }
+                std::vector<int> &v = lists[b];
+                for (int wi = 0; wi < words; wi++) {
+                    uint64_t m = bits[wi];
+                    while (m) {
+                        int t = __builtin_ctzll(m);
+                        v.push_back(wi * 64 + t);
+                        m &= m - 1;
+                    }
+                }
+            }
+        }
+        L.rc_start.assign(L.nbox + 1, 0);
+        for (int b = 0; b < L.nbox; b++) L.rc_start[b + 1] = L.rc_start[b] + (int)lists[b].size();
+        L.nrc = L.rc_start[L.nbox];
+        L.rc_cone.resize(L.nrc);
+        L.rc_box.resize(L.nrc);
+        L.cone_map.assign((size_t)L.nbox * L.ncone, -1);
+        for (int b = 0; b < L.nbox; b++)
+            for (size_t j = 0; j < lists[b].size(); j++) {
+                int rc = L.rc_start[b] + (int)j;
+                L.rc_cone[rc] = lists[b][j];
+                L.rc_box[rc] = b;
+                L.cone_map[(size_t)b * L.ncone + lists[b][j]] = rc;
+            }
+        if (PL) {
+            int64_t pe = 0;
+            for (int b = 0; b < L.nbox; b++) pe += (int64_t)(PL->rc_start[L.parent[b] + 1] - PL->rc_start[L.parent[b]]) * p.P;
+            p.lv[d - 1].prop_evals = pe;
+        }
+    }
+    {
+        const HostLevel &L = p.lv[D];
+        int64_t le = 0;
+        for (int b = 0; b < L.nbox; b++)
+            le += (int64_t)(L.rc_start[b + 1] - L.rc_start[b]) * p.P * (L.start[b + 1] - L.start[b]);
+        p.leaf_evals = le;
+    }
+    return IFGF_OK;
+}
+
+}  // namespace ifgf

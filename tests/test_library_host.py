@@ -1,0 +1,109 @@
+"""CPU tests of the C-ABI library: symbol exports, argument validation and the
+host plan (octree, cousins, relevant cone segments) against the oracle's counts.
+No GPU is touched: plans are built with ifgf_plan_dry_run."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from workloads import cube_sphere, ellipsoid, random_density, sphere_workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2112_06316_gb300 import binding
+    from paper_2112_06316_gb300 import build as _b
+
+    _b.build()
+    return binding
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ifgf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ifgf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(B):
+    import ctypes
+
+    lib = ctypes.CDLL(B.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each of them
+    assert set(names) <= set(B.exported_symbols()), set(names) - set(B.exported_symbols())
+
+
+def _sphere():
+    s = cube_sphere(26)
+    return s, math.pi
+
+
+def test_validation_errors(B):
+    s, k = _sphere()
+    x, n, w = s.points, s.normals, s.weights
+    with pytest.raises(B.IFGFError, match="EINVAL"):
+        B.dry_run(x[:0], n[:0], w[:0], B.Params(k=k))
+    bad = x.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(B.IFGFError, match="EINVAL"):
+        B.dry_run(bad, n, w, B.Params(k=k))
+    nb = n.copy()
+    nb[7] *= 1.01
+    with pytest.raises(B.IFGFError, match="not unit"):
+        B.dry_run(x, nb, w, B.Params(k=k))
+    wb = w.copy()
+    wb[0] = 0.0
+    with pytest.raises(B.IFGFError, match="weight"):
+        B.dry_run(x, n, wb, B.Params(k=k))
+    with pytest.raises(B.IFGFError, match="EINVAL"):
+        B.dry_run(x, n, w, B.Params(k=-1.0))
+    with pytest.raises(B.IFGFError, match="EINVAL"):
+        B.dry_run(x, n, w, B.Params(k=k, levels=2))
+    with pytest.raises(B.IFGFError, match="EUNSUPPORTED"):
+        B.dry_run(x, n, w, B.Params(k=k, Ps=2, Pang=2))
+
+
+@pytest.mark.parametrize("case", ["sphere1", "sphere4", "ellipsoid", "cloud"])
+def test_plan_counts_match_oracle(B, oracle_lib, case):
+    rng = np.random.default_rng(1)
+    if case == "sphere1":
+        s, k = _sphere()
+        x, n, w, D = s.points, s.normals, s.weights, 3
+    elif case == "sphere4":
+        s, k = sphere_workload(48, 6, 4.0)
+        x, n, w, D = s.points, s.normals, s.weights, 4
+    elif case == "ellipsoid":
+        s = ellipsoid(32, 8, (1.0, 2.0, 3.0))
+        k, x, n, w, D = 6.0, s.points, s.normals, s.weights, 5
+    else:  # clustered random cloud with random unit normals
+        x = np.concatenate([rng.normal(size=(1500, 3)) * 0.1, rng.uniform(-1, 1, (1500, 3))])
+        n = rng.normal(size=x.shape)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        w = rng.uniform(0.5, 1.5, x.shape[0])
+        k, D = 9.0, 5
+    for fm, cr in ((0, 0), (1, 1), (2, 0)):
+        sig = random_density(x.shape[0], 1, 0)
+        _, oi = oracle_lib.ifgf(x, n, w, oracle_lib.IFGFParams(k=k, levels=D, factor_mode=fm, cone_rule=cr), sig)
+        pi = B.dry_run(x, n, w, B.Params(k=k, levels=D, factor_mode=fm, cone_rule=cr, cone_band=0.0))
+        for key in ("nbox", "ns", "nC", "split", "nrc", "cousin_evals", "prop_evals"):
+            assert pi[key][3:] == oi[key][3:], (case, key, pi[key], oi[key])
+        assert pi["leaf_evals"] == oi["leaf_evals"]
+        assert pi["near_pairs"] == oi["near_pairs"] + x.shape[0]  # the plan counts the l == m slots
+        assert abs(pi["root_side"] - oi["root_side"]) == 0.0
+        # the default band only adds cone segments
+        pb = B.dry_run(x, n, w, B.Params(k=k, levels=D, factor_mode=fm, cone_rule=cr))
+        assert all(a >= b for a, b in zip(pb["nrc"], pi["nrc"]))
+
+
+def test_auto_levels_match_oracle_rule(B, oracle_lib):
+    for n, m, wl in ((26, 26, 1.0), (48, 6, 4.0), (96, 8, 8.0), (64, 8, 2.0)):
+        s, k = sphere_workload(n, m, wl)
+        pi = B.dry_run(s.points, s.normals, s.weights, B.Params(k=k))
+        assert pi["D"] == oracle_lib.auto_levels(s.points)
