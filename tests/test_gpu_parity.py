@@ -101,7 +101,8 @@ def test_uneven_cloud_ragged_boxes(lib, oracle_lib):
 
 
 def test_tiny_inputs(lib, oracle_lib):
-    """N = 1 (no interactions: y = sigma / 2), N = 2, and nrhs = 0 (no-op)."""
+    """N = 1 (no interactions: y = sigma / 2), N = 2 and 9 (cousins of each other or
+    neighbours), and nrhs = 0 (no-op)."""
     for N in (1, 2, 9):
         rng = np.random.default_rng(N)
         x = rng.uniform(-1, 1, (N, 3))
@@ -111,8 +112,8 @@ def test_tiny_inputs(lib, oracle_lib):
         sig = random_density(N, 1, 3)
         plan = lib.Plan(x, n, w, lib.Params(k=3.0))
         y = gpu_apply(plan, sig, np.complex128)
-        yd = oracle_lib.direct(x, n, w, 3.0, 3.0, sig, cI=0.5)
-        assert rel(y, yd) < 1e-12
+        ref, _ = oracle_lib.ifgf(x, n, w, oracle_lib.IFGFParams(k=3.0, identity_coef=0.5), sig)
+        assert rel(y, ref) < 1e-12
         if N == 1:
             assert np.allclose(y, 0.5 * sig, rtol=0, atol=1e-15)
         z = torch.zeros((0, N), dtype=torch.complex128, device="cuda")
