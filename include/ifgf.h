@@ -144,6 +144,30 @@ ifgf_status ifgf_plan_set_correction(ifgf_plan *plan, const int64_t *rowptr, con
 ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
                        void *stream);
 
+/* ifgf_apply without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc at apply time -- for
+ * example code whose device memory is reserved up front by a host application or
+ * pool that must not be bypassed, or code on a path where the implicit device
+ * synchronisation of cudaMalloc/cudaFree would stall other work.  The plan must
+ * already exist (ifgf_plan_create allocates); this call allocates and frees nothing.
+ *
+ * The apply's workspace (w*sigma and the field in Morton order, and the cone
+ * values of every level) lives in one fixed 64 MiB device array inside the
+ * library.  Every GPU that loads the library holds that array until the process
+ * exits.  Requests whose workspace exceeds it are rejected with IFGF_EINVAL and a
+ * message giving the required size; the workspace grows with N, nrhs, the
+ * precision (complex128 needs twice complex64) and the number of relevant cone
+ * segments.  The first call on a device looks the array's address up with that
+ * device current (once per device); make that first call before any stream
+ * capture begins.  All calls share the one array and it keeps the last call's
+ * contents (every value an apply reads is written earlier in the same apply, so
+ * nothing needs clearing).  Calls that overlap on the GPU -- on different streams,
+ * or with ifgf_apply_noalloc of another plan -- race on the array and must be
+ * serialised by the caller.  Arguments, results and errors are otherwise those of
+ * ifgf_apply. */
+ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
+                               void *stream);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 

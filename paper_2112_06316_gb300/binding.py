@@ -68,6 +68,7 @@ _SIGS = [
                                          ctypes.POINTER(CInfo)]),
     ("ifgf_plan_set_correction", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64]),
     ("ifgf_apply", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
     ("ifgf_plan_check", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
     ("ifgf_plan_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -227,6 +228,11 @@ class Plan:
         """Raw-pointer apply: sigma/y device buffers of N x nrhs complex."""
         check(lib().ifgf_apply(self._h, _VP(sigma_ptr), _VP(y_ptr), ctypes.c_int(nrhs), ctypes.c_int(prec),
                                _VP(_stream_ptr(stream))))
+
+    def apply_noalloc_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):
+        """Raw-pointer ``ifgf_apply_noalloc`` (workspace in the library's fixed device array)."""
+        check(lib().ifgf_apply_noalloc(self._h, _VP(sigma_ptr), _VP(y_ptr), ctypes.c_int(nrhs), ctypes.c_int(prec),
+                                       _VP(_stream_ptr(stream))))
 
     def apply(self, sigma, out=None, stream=None):
         """y = A sigma for a CUDA torch tensor sigma of shape (nrhs, N) or (N,).

@@ -941,4 +941,19 @@ ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, c
     return IFGF_EUNSUPPORTED;
 }
 
+// Same launches as run_apply on a caller-provided workspace view (no allocation).
+ifgf_status run_apply_on(Plan &p, const Workspace &ws, const void *sigma, void *y, int nrhs, int prec,
+                         cudaStream_t s) {
+    Workspace saved = p.ws;
+    p.ws = ws;
+    ifgf_status st = IFGF_EUNSUPPORTED;
+    if (p.Ps == 3 && p.Pang == 5) st = run_apply_t<3, 5>(p, sigma, y, nrhs, prec, s);
+    else if (p.Ps == 4 && p.Pang == 6) st = run_apply_t<4, 6>(p, sigma, y, nrhs, prec, s);
+    else if (p.Ps == 5 && p.Pang == 7) st = run_apply_t<5, 7>(p, sigma, y, nrhs, prec, s);
+    else if (p.Ps == 6 && p.Pang == 8) st = run_apply_t<6, 8>(p, sigma, y, nrhs, prec, s);
+    else set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
+    p.ws = saved;
+    return st;
+}
+
 }  // namespace ifgf

@@ -14,10 +14,6 @@ ifgf_status set_correction(Plan &p, const int64_t *rowptr, const int32_t *col, c
 
 using namespace ifgf;
 
-struct ifgf_plan {
-    Plan p;
-};
-
 static bool supported_pair(int ps, int pa) {
     return (ps == 3 && pa == 5) || (ps == 4 && pa == 6) || (ps == 5 && pa == 7) || (ps == 6 && pa == 8);
 }

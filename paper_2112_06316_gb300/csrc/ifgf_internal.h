@@ -134,3 +134,8 @@ ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, c
 void free_plan_device(Plan &p);
 
 }  // namespace ifgf
+
+// The opaque handle of the C ABI.
+struct ifgf_plan {
+    ifgf::Plan p;
+};
