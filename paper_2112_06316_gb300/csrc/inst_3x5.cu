@@ -1,0 +1,6 @@
+// Forward apply kernels instantiated for interpolation orders Ps = 3, Pang = 5.
+#include "fwd_kernels.cuh"
+
+namespace ifgf {
+template ifgf_status run_apply_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t);
+}  // namespace ifgf

@@ -1,0 +1,6 @@
+// Forward apply kernels instantiated for interpolation orders Ps = 5, Pang = 7.
+#include "fwd_kernels.cuh"
+
+namespace ifgf {
+template ifgf_status run_apply_t<5, 7>(Plan &, const void *, void *, int, int, cudaStream_t);
+}  // namespace ifgf
