@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="points per cube-face side")
     ap.add_argument("--wavelengths", type=float, default=16.0)
-    ap.add_argument("--orders", default="6x8", help="Ps x Pang of the headline apply")
+    ap.add_argument("--orders", default="5x8", help="Ps x Pang of the headline apply")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
@@ -71,13 +71,22 @@ def cap_sample(s, frac=8):
     return np.nonzero(s.points[:, 2] > 1.0 - 2.0 / frac)[0]
 
 
-def oracle_cap_apply(s, k, sig, info, Ps, Pang):
+def full_octree(s):
+    """Root box (AABB midpoint, max extent * (1 + 2^-30)) and level count of the whole surface."""
+    import oracle
+
+    lo, hi = s.points.min(0), s.points.max(0)
+    return {"root_center": tuple(0.5 * (lo + hi)), "root_side": float((hi - lo).max() * (1 + 2.0 ** -30)),
+            "D": oracle.auto_levels(s.points)}
+
+
+def oracle_cap_apply(s, k, sig, tree, Ps, Pang):
     """One oracle IFGF apply on the cap sample, on the full sphere's octree (same root box, D)."""
     import oracle
 
     idx = cap_sample(s)
-    p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, levels=info["D"], identity_coef=0.5,
-                          root_center=tuple(info["root_center"]), root_side=info["root_side"])
+    p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, levels=tree["D"], identity_coef=0.5,
+                          root_center=tree["root_center"], root_side=tree["root_side"])
     t = time.perf_counter()
     oracle.ifgf(s.points[idx], s.normals[idx], s.weights[idx], p, sig[:, idx])
     return len(idx), time.perf_counter() - t
@@ -143,12 +152,11 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    from paper_2112_06316_gb300 import binding
 
     s, k, sig = workload(args)
     Ps, Pang = (int(v) for v in args.orders.split("x"))
-    info = binding.dry_run(s.points, s.normals, s.weights, binding.Params(k=k, Ps=Ps, Pang=Pang))
     oracle.build()
+    info = full_octree(s)
     n = 0
     for _ in range(args.warmup):
         oracle_cap_apply(s, k, sig, info, Ps, Pang)
@@ -322,7 +330,7 @@ def run_ours(args):
                                         "rows": int(len(rows))}
             out["fp64"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["fp64"]
             out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
-            n_cap, t_cap = oracle_cap_apply(s, k, sig, info, Ps, Pang)
+            n_cap, t_cap = oracle_cap_apply(s, k, sig, full_octree(s), Ps, Pang)
             out["cpu_baseline"] = {
                 "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                 "sample": f"one oracle IFGF apply (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 of the "

@@ -23,6 +23,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
 extern template ifgf_status run_apply_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t);
 extern template ifgf_status run_apply_t<4, 6>(Plan &, const void *, void *, int, int, cudaStream_t);
 extern template ifgf_status run_apply_t<5, 7>(Plan &, const void *, void *, int, int, cudaStream_t);
+extern template ifgf_status run_apply_t<5, 8>(Plan &, const void *, void *, int, int, cudaStream_t);
 extern template ifgf_status run_apply_t<6, 8>(Plan &, const void *, void *, int, int, cudaStream_t);
 
 template <typename T>
@@ -169,6 +170,7 @@ ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, c
     IFGF_CASE(3, 5)
     IFGF_CASE(4, 6)
     IFGF_CASE(5, 7)
+    IFGF_CASE(5, 8)
     IFGF_CASE(6, 8)
 #undef IFGF_CASE
     set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
@@ -184,6 +186,7 @@ ifgf_status run_apply_on(Plan &p, const Workspace &ws, const void *sigma, void *
     if (p.Ps == 3 && p.Pang == 5) st = run_apply_t<3, 5>(p, sigma, y, nrhs, prec, s);
     else if (p.Ps == 4 && p.Pang == 6) st = run_apply_t<4, 6>(p, sigma, y, nrhs, prec, s);
     else if (p.Ps == 5 && p.Pang == 7) st = run_apply_t<5, 7>(p, sigma, y, nrhs, prec, s);
+    else if (p.Ps == 5 && p.Pang == 8) st = run_apply_t<5, 8>(p, sigma, y, nrhs, prec, s);
     else if (p.Ps == 6 && p.Pang == 8) st = run_apply_t<6, 8>(p, sigma, y, nrhs, prec, s);
     else set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
     p.ws = saved;

@@ -15,7 +15,7 @@ ifgf_status set_correction(Plan &p, const int64_t *rowptr, const int32_t *col, c
 using namespace ifgf;
 
 static bool supported_pair(int ps, int pa) {
-    return (ps == 3 && pa == 5) || (ps == 4 && pa == 6) || (ps == 5 && pa == 7) || (ps == 6 && pa == 8);
+    return (ps == 3 && pa == 5) || (ps == 4 && pa == 6) || (ps == 5 && pa == 7) || (ps == 5 && pa == 8) || (ps == 6 && pa == 8);
 }
 
 extern "C" {
@@ -37,7 +37,7 @@ void ifgf_params_default(ifgf_params *p, double k) {
     p->cone_band = 1e-4;
 }
 
-const char *ifgf_supported_orders(void) { return "3x5,4x6,5x7,6x8"; }
+const char *ifgf_supported_orders(void) { return "3x5,4x6,5x7,5x8,6x8"; }
 
 const char *ifgf_last_error(void) { return last_error_str(); }
 

@@ -1,0 +1,6 @@
+// Forward apply kernels instantiated for interpolation orders Ps = 5, Pang = 8.
+#include "fwd_kernels.cuh"
+
+namespace ifgf {
+template ifgf_status run_apply_t<5, 8>(Plan &, const void *, void *, int, int, cudaStream_t);
+}  // namespace ifgf

@@ -72,7 +72,7 @@ def test_multilevel_factor_modes(lib, oracle_lib, fm):
     run_case(lib, oracle_lib, s.points, s.normals, s.weights, k, {"levels": 4, "factor_mode": fm}, nrhs=2)
 
 
-@pytest.mark.parametrize("ps,pa", [(4, 6), (5, 7), (6, 8)])
+@pytest.mark.parametrize("ps,pa", [(4, 6), (5, 7), (5, 8), (6, 8)])
 def test_higher_orders(lib, oracle_lib, ps, pa):
     s, k = sphere_workload(32, 8, 3.0)
     run_case(lib, oracle_lib, s.points, s.normals, s.weights, k, {"levels": 4, "Ps": ps, "Pang": pa})
@@ -169,13 +169,13 @@ def test_config2_full_size(lib, oracle_lib):
 
 @pytest.mark.slow
 def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
-    """Orders (6, 8, 8) on the 16-wavelength sphere reach <= 1e-4 against the direct sum
+    """Orders (5, 8, 8) on the 16-wavelength sphere reach <= 1e-4 against the direct sum
     (sampled rows), in FP64 and in mixed precision."""
     s, k = sphere_workload(256, 8, 16.0)
     sig = random_density(s.N, 1, 2)
     rows = np.random.default_rng(0).choice(s.N, 2000, replace=False)
     yd = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5, rows=rows)
-    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, Ps=6, Pang=8))
+    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, Ps=5, Pang=8))
     y64 = gpu_apply(plan, sig, np.complex128)
     y32 = gpu_apply(plan, sig, np.complex64)
     assert plan.missed_lookups() == 0
