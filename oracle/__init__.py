@@ -13,6 +13,7 @@ reference legs use this package.  It shares no code with
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -21,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "rp.c")]
 _LIBDIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 MAXD = 20
@@ -29,10 +31,10 @@ MAXD = 20
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` with gcc (FP64, OpenMP) into ``oracle/_build``."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+               "-ffp-contract=off", *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -252,6 +254,55 @@ def wfactors(k, eta, x, y0, h, y, ny, split: bool, literal: bool = False):
 def cheb_interp_1d(values, t) -> float:
     v = np.ascontiguousarray(values, dtype=np.float64)
     return float(lib().oracle_cheb_interp_1d(ctypes.c_int(v.shape[0]), _dptr(v), ctypes.c_double(t)))
+
+
+def cube_sphere_patches(n: int, m: int):
+    """Patch id, node index and node -> point map of the cube-sphere ordering of
+    ``workloads.cube_sphere(n, m)`` (faces, then 'ij' meshgrid of face parameters)."""
+    P = n // m
+    idx = np.arange(6 * n * n)
+    f = idx // (n * n)
+    loc = idx % (n * n)
+    iu, iv = loc // n, loc % n
+    q = f * P * P + (iu // m) * P + (iv // m)
+    nd = (iu % m) * m + (iv % m)
+    node_of = np.empty(6 * P * P * m * m, dtype=np.int32)
+    node_of[q * m * m + nd] = idx
+    return q.astype(np.int32), nd.astype(np.int32), node_of
+
+
+def rp_correction_sphere(points, normals, weights, n: int, m: int, radius: float, k: float, eta: float,
+                         delta: float | None = None, Nbeta: int = 48, dgrade: float = 5.0):
+    """Rectangular-polar correction C (rows = targets) for a cube-sphere surface.
+
+    Returns (rowptr int64 (N+1,), col int32 (nnz,), val complex128 (nnz,)).  delta defaults
+    to the nominal sub-patch side pi R / (2P)."""
+    x, nu, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    P = n // m
+    q, nd, node_of = cube_sphere_patches(n, m)
+    if delta is None:
+        delta = math.pi * radius / (2 * P)
+    lo, hi = x.min(0), x.max(0)
+    L = float((hi - lo).max() * (1 + 2.0 ** -30))
+    rp = ctypes.POINTER(ctypes.c_int64)()
+    cp = ctypes.POINTER(ctypes.c_int32)()
+    vp = ctypes.POINTER(ctypes.c_double)()
+    ip = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    rc = lib().oracle_rp_correction(ctypes.c_int64(N), _dptr(x), _dptr(nu), _dptr(w), ip(q), ip(nd), ip(node_of),
+                                    ctypes.c_double(radius), ctypes.c_int(P), ctypes.c_int(m), ctypes.c_double(k),
+                                    ctypes.c_double(eta), ctypes.c_double(delta), ctypes.c_int(Nbeta),
+                                    ctypes.c_double(dgrade), ctypes.c_double(1e-14 * L), ctypes.byref(rp),
+                                    ctypes.byref(cp), ctypes.byref(vp))
+    if rc != 0:
+        raise RuntimeError(f"oracle_rp_correction failed ({rc})")
+    rowptr = np.ctypeslib.as_array(rp, shape=(N + 1,)).copy()
+    nnz = int(rowptr[-1])
+    col = np.ctypeslib.as_array(cp, shape=(max(nnz, 1),))[:nnz].copy()
+    val = np.ctypeslib.as_array(vp, shape=(max(2 * nnz, 2),))[:2 * nnz].copy().view(np.complex128)
+    for ptr in (rp, cp, vp):
+        lib().oracle_rp_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return rowptr, col, val
 
 
 def csr_apply(rowptr, col, val, sigma) -> np.ndarray:
