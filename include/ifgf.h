@@ -168,6 +168,24 @@ ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int 
 ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
                                void *stream);
 
+/* Restarted GMRES(restart) for A x = b with the plan's operator (Section 5: GMRES
+ * of Saad & Schultz applied to Eq. CombLayIE).  Arnoldi in FP64 with classical
+ * Gram-Schmidt applied twice on the device; the operator apply inside runs in
+ * `apply_prec` (IFGF_MIXED rounds each Krylov vector to complex64 for the apply).
+ *   rhs_dev: device, N complex128.  x_dev: device, N complex128; initial guess on
+ *            entry, solution on exit (must not alias rhs_dev).
+ *   restart >= 1, maxit >= 0 (operator applies inside the Arnoldi loops), tol >= 0
+ *   on the relative residual |b - A x| / |b|.
+ *   iters: receives the iterations done; resid_hist: host array of maxit + 1
+ *   doubles receiving the relative residual before each iteration (entry 0 = the
+ *   initial guess's true residual; later entries are the Arnoldi estimates).
+ * Allocates its Krylov basis ((restart + 1) x N complex128) for the duration of the
+ * call and synchronises `stream` every iteration.
+ * Returns IFGF_OK when converged, IFGF_ENOTCONVERGED when maxit is reached (x holds
+ * the last iterate), or IFGF_EINVAL / IFGF_ENOMEM / IFGF_ECUDA. */
+ifgf_status ifgf_gmres(ifgf_plan *plan, const void *rhs_dev, void *x_dev, int restart, int maxit, double tol,
+                       ifgf_precision apply_prec, int *iters, double *resid_hist, void *stream);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 

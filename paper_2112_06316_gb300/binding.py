@@ -69,6 +69,8 @@ _SIGS = [
     ("ifgf_plan_set_correction", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64]),
     ("ifgf_apply", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
     ("ifgf_plan_check", ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]),
     ("ifgf_plan_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -259,6 +261,28 @@ class Plan:
             raise ValueError("out must match sigma's shape/dtype and be contiguous")
         self.apply_ptr(s.data_ptr(), y.data_ptr(), int(s.shape[0]), prec, stream)
         return y.reshape(-1) if squeeze else y
+
+    def gmres(self, rhs, x0=None, restart: int = 50, maxit: int = 200, tol: float = 1e-6,
+              precision: int = FP64, stream=None):
+        """Solve A x = rhs (complex128 CUDA vector of length N) with ``ifgf_gmres``.
+
+        Returns (x, converged, iterations, relative-residual history)."""
+        import torch
+
+        if not (isinstance(rhs, torch.Tensor) and rhs.is_cuda and rhs.dtype == torch.complex128):
+            raise TypeError("rhs must be a complex128 CUDA tensor")
+        b = rhs.reshape(-1).contiguous()
+        if b.numel() != self.N:
+            raise ValueError("rhs must have N entries")
+        x = torch.zeros_like(b) if x0 is None else x0.reshape(-1).to(torch.complex128).clone().contiguous()
+        it = ctypes.c_int(0)
+        hist = np.zeros(maxit + 1)
+        st = lib().ifgf_gmres(self._h, _VP(b.data_ptr()), _VP(x.data_ptr()), ctypes.c_int(restart), ctypes.c_int(maxit),
+                              ctypes.c_double(tol), ctypes.c_int(precision), ctypes.byref(it), _VP(hist.ctypes.data),
+                              _VP(_stream_ptr(stream)))
+        if st not in (IFGF_OK, -4):
+            check(st)
+        return x, st == IFGF_OK, int(it.value), hist[: it.value + 1]
 
     def set_profiling(self, enable: bool = True):
         check(lib().ifgf_plan_set_profiling(self._h, ctypes.c_int(int(enable))))
