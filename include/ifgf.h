@@ -144,6 +144,20 @@ ifgf_status ifgf_plan_set_correction(ifgf_plan *plan, const int64_t *rowptr, con
 ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
                        void *stream);
 
+/* out = A^H g: the conjugate transpose of the operator applied by ifgf_apply
+ * (every stage of Algorithm 1 transposed and run in reverse order: anterpolation
+ * from cousin targets and parent cone nodes into each level's cone values, level
+ * by level from d = 3 down to D, then the transposed leaf evaluation, the
+ * transposed near field, conj(c_I) g and C^H g).  The paper has no adjoint; it is
+ * the exact transpose of the discrete FP64 operator (up to rounding) and of the
+ * mixed operator up to FP32 rounding of the cone assignment near cone boundaries.
+ * Same layout, precision and error conventions as ifgf_apply.  The first call
+ * builds the anterpolation lists on the host (synchronous; memory ~ 4 bytes per
+ * cousin interpolation and per propagation evaluation); its workspace grows like
+ * ifgf_apply's. */
+ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev, int nrhs, ifgf_precision prec,
+                               void *stream);
+
 /* ifgf_apply without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc at apply time -- for
  * example code whose device memory is reserved up front by a host application or

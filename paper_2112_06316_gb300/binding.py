@@ -68,6 +68,7 @@ _SIGS = [
                                          ctypes.POINTER(CInfo)]),
     ("ifgf_plan_set_correction", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64]),
     ("ifgf_apply", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), _VP, _VP]),
@@ -230,6 +231,24 @@ class Plan:
         """Raw-pointer apply: sigma/y device buffers of N x nrhs complex."""
         check(lib().ifgf_apply(self._h, _VP(sigma_ptr), _VP(y_ptr), ctypes.c_int(nrhs), ctypes.c_int(prec),
                                _VP(_stream_ptr(stream))))
+
+    def adjoint(self, g, out=None, stream=None):
+        """out = A^H g for a CUDA tensor g of shape (nrhs, N) or (N,); dtype selects the precision."""
+        import torch
+
+        if not (isinstance(g, torch.Tensor) and g.is_cuda):
+            raise TypeError("g must be a CUDA torch tensor")
+        prec = FP64 if g.dtype == torch.complex128 else MIXED if g.dtype == torch.complex64 else None
+        if prec is None:
+            raise TypeError("g must be complex64 or complex128")
+        squeeze = g.dim() == 1
+        gg = (g.reshape(1, -1) if squeeze else g).contiguous()
+        if gg.shape[-1] != self.N:
+            raise ValueError(f"g must have N={self.N} columns")
+        y = torch.empty_like(gg) if out is None else out
+        check(lib().ifgf_apply_adjoint(self._h, _VP(gg.data_ptr()), _VP(y.data_ptr()), ctypes.c_int(gg.shape[0]),
+                                       ctypes.c_int(prec), _VP(_stream_ptr(stream))))
+        return y.reshape(-1) if squeeze else y
 
     def apply_noalloc_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):
         """Raw-pointer ``ifgf_apply_noalloc`` (workspace in the library's fixed device array)."""

@@ -120,6 +120,9 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
 }
 
 void free_plan_device(Plan &p) {
+    if (p.adj_ws) cudaFree(p.adj_ws);
+    p.adj_ws = nullptr;
+    p.adj_ws_bytes = 0;
     for (int i = 0; i < Plan::kMaxEv; i++)
         if (p.ev[i]) {
             cudaEventDestroy(p.ev[i]);

@@ -43,6 +43,12 @@ __global__ void k_spmv(int N, int nrhs, const long long *__restrict__ rowptr, co
 }
 
 static void free_correction(Plan &p) {
+    for (void *q : {(void *)p.d_corrT_rowptr, (void *)p.d_corrT_col, (void *)p.d_corrT_val64, (void *)p.d_corrT_val32})
+        if (q) cudaFree(q);
+    p.d_corrT_rowptr = nullptr;
+    p.d_corrT_col = nullptr;
+    p.d_corrT_val64 = nullptr;
+    p.d_corrT_val32 = nullptr;
     if (p.d_corr_rowptr) cudaFree(p.d_corr_rowptr);
     if (p.d_corr_col) cudaFree(p.d_corr_col);
     if (p.d_corr_val64) cudaFree(p.d_corr_val64);
@@ -95,12 +101,59 @@ ifgf_status set_correction(Plan &p, const int64_t *rowptr, const int32_t *col, c
     if (e == cudaSuccess) e = cudaMemcpy(p.d_corr_col, col, sizeof(int) * nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_corr_val64, val, sizeof(double) * 2 * nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p.d_corr_val32, v32.data(), sizeof(float) * 2 * nnz, cudaMemcpyHostToDevice);
+    // conjugate transpose for the adjoint: row j of C^H holds conj(C[i][j]) at column i
+    std::vector<int64_t> trp(N + 1, 0);
+    for (int64_t j = 0; j < nnz; j++) trp[col[j] + 1]++;
+    for (int64_t i = 0; i < N; i++) trp[i + 1] += trp[i];
+    std::vector<int> tcol(nnz);
+    std::vector<double> tv64(2 * nnz);
+    std::vector<float> tv32(2 * nnz);
+    {
+        std::vector<int64_t> fill(trp.begin(), trp.end() - 1);
+        for (int64_t i = 0; i < N; i++)
+            for (int64_t j = rowptr[i]; j < rowptr[i + 1]; j++) {
+                int64_t o = fill[col[j]]++;
+                tcol[o] = (int)i;
+                tv64[2 * o] = val[2 * j];
+                tv64[2 * o + 1] = -val[2 * j + 1];
+                tv32[2 * o] = (float)val[2 * j];
+                tv32[2 * o + 1] = -(float)val[2 * j + 1];
+            }
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_corrT_rowptr, sizeof(int64_t) * (N + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_corrT_col, sizeof(int) * nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_corrT_val64, sizeof(double) * 2 * nnz);
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_corrT_val32, sizeof(float) * 2 * nnz);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_corrT_rowptr, trp.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_corrT_col, tcol.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_corrT_val64, tv64.data(), sizeof(double) * 2 * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p.d_corrT_val32, tv32.data(), sizeof(float) * 2 * nnz, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_correction(p);
         set_error("correction upload failed: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
     }
     p.corr_nnz = nnz;
+    return IFGF_OK;
+}
+
+// y += C^H g (conjugate-transposed correction)
+ifgf_status apply_correction_adjoint(Plan &p, const void *g, void *y, int nrhs, int prec, cudaStream_t s) {
+    if (p.corr_nnz == 0) return IFGF_OK;
+    const int N = (int)p.N;
+    const unsigned blocks = (unsigned)(((long long)N * 32 + 127) / 128);
+    if (prec == IFGF_FP64)
+        k_spmv<double><<<blocks, 128, 0, s>>>(N, nrhs, (const long long *)p.d_corrT_rowptr, p.d_corrT_col,
+                                              (const double2 *)p.d_corrT_val64, (const double2 *)g, (double2 *)y);
+    else
+        k_spmv<float><<<blocks, 128, 0, s>>>(N, nrhs, (const long long *)p.d_corrT_rowptr, p.d_corrT_col,
+                                             (const float2 *)p.d_corrT_val32, (const float2 *)g, (float2 *)y);
+    prof_mark(p, s, kStCorr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("correction-adjoint kernel launch failed: %s", cudaGetErrorString(e));
+        return IFGF_ECUDA;
+    }
     return IFGF_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "ifgf_internal.h"
 #include "kernels.cuh"
@@ -801,6 +802,380 @@ __global__ void __launch_bounds__(kBlock) k_cousin32(CommonArgs ca, LevelArgs L,
     }
 }
 
+
+// ============================================================================
+// Adjoint (conjugate transpose) kernels.  Same geometry as the forward kernels,
+// stages transposed and run in reverse order (all output-stationary).
+// ============================================================================
+template <typename T> struct CT;
+template <> struct CT<double> { typedef double2 c; };
+template <> struct CT<float> { typedef float2 c; };
+
+template <typename C>
+__device__ __forceinline__ C cconj_mul(C a, C b) {  // conj(a) * b
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.x * b.y - a.y * b.x;
+    return r;
+}
+
+// Per-entry data staged in shared memory by the anterpolation kernel.
+template <typename T, int PS, int PA>
+struct AntEntry {
+    T Ls[PS], Lt[PA], Lp[PA];
+    typename CT<T>::c v[2];
+};
+
+// Anterpolation into the relevant cones of level d (transpose of K2 and K3):
+// G_d[rc] = sum over its cousin targets of L(t) conj(E) g  +  sum over parent
+// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  One block per rc.
+template <int PS, int PA, bool MX>
+__global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD, int has_parent,
+                                              const long long *__restrict__ ad_start, const int *__restrict__ ad_list,
+                                              ChebTab tb, const void *gs_, const void *Gp_, void *Gc_) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    constexpr int P = PS * PA * PA, NROW = PS * PA;
+    const C *gs = (const C *)gs_;
+    const C *Gp = (const C *)Gp_;
+    C *Gc = (C *)Gc_;
+    __shared__ AntEntry<T, PS, PA> ent[128];
+    const int rc = blockIdx.x;
+    const int cbox = L.rc_box[rc];
+    const long long e0 = ad_start[rc], e1 = ad_start[rc + 1];
+    const int nfac = L.nfac;
+    const bool csplit = L.split != 0, psplit = has_parent && Pl.split != 0;
+    const int unit = threadIdx.x;
+    const bool active = unit < nfac * NROW;
+    const int fac = active ? unit / NROW : 0, row = active ? unit % NROW : 0;
+    const int ua = row / PA, ub = row % PA;
+    for (int q = 0; q < ca.nrhs; q++) {
+        C acc[PA];
+#pragma unroll
+        for (int c = 0; c < PA; c++) acc[c].x = acc[c].y = T(0);
+        for (long long base = e0; base < e1; base += 128) {
+            const long long e = base + threadIdx.x;
+            AntEntry<T, PS, PA> &me = ent[threadIdx.x];
+            T t3[3] = {T(0), T(0), T(0)};
+            C v0, v1;
+            v0.x = v0.y = v1.x = v1.y = T(0);
+            int cone_got = L.rc_cone[rc];
+            if (e < e1) {
+                const int ev = ad_list[e];
+                if (ev < ca.N) {  // cousin target
+                    const int i = ev;
+                    const C g = gs[(long long)q * ca.N + i];
+                    T Er, Ei, ir_abs;
+                    if constexpr (MX) {
+                        const int bl = ca.leaf_of[i];
+                        const float sc = (float)L.scale;
+                        const float M0 = LD.ijk[3 * bl] + 0.5f - (L.ijk[3 * cbox] + 0.5f) * sc;
+                        const float M1 = LD.ijk[3 * bl + 1] + 0.5f - (L.ijk[3 * cbox + 1] + 0.5f) * sc;
+                        const float M2 = LD.ijk[3 * bl + 2] + 0.5f - (L.ijk[3 * cbox + 2] + 0.5f) * sc;
+                        const float f0 = ca.f32[3 * i], f1 = ca.f32[3 * i + 1], f2 = ca.f32[3 * i + 2];
+                        float r;
+                        const float tph = phase_cycles_exact(M0, M1, M2, f0, f1, f2, ca.kappa_hi, ca.kappa_lo, r);
+                        float tt[3];
+                        cone_got = classify32(L, M0 + f0, M1 + f1, M2 + f2, r, tt);
+                        t3[0] = tt[0]; t3[1] = tt[1]; t3[2] = tt[2];
+                        float sn, cs;
+                        cis_cycles(tph, sn, cs);
+                        const float c4 = 1.f / (4.f * kPiF * ca.HDf * r);
+                        Er = c4 * cs;
+                        Ei = c4 * sn;
+                        ir_abs = 1.f / (r * ca.HDf);
+                    } else {
+                        double y0[3];
+                        center64(ca, L, cbox, y0);
+                        double r, tt[3];
+                        cone_got = classify64(L, ca.x64[3 * i] - y0[0], ca.x64[3 * i + 1] - y0[1], ca.x64[3 * i + 2] - y0[2],
+                                              r, tt);
+                        t3[0] = tt[0]; t3[1] = tt[1]; t3[2] = tt[2];
+                        double sn, cs;
+                        sincos(ca.k * r, &sn, &cs);
+                        const double c4 = 1.0 / (4.0 * kPi * r);
+                        Er = c4 * cs;
+                        Ei = c4 * sn;
+                        ir_abs = 1.0 / r;
+                    }
+                    C E;
+                    E.x = Er;
+                    E.y = Ei;
+                    if (csplit) {
+                        C E2;
+                        E2.x = Er * ir_abs;
+                        E2.y = Ei * ir_abs;
+                        v0 = cconj_mul(E2, g);
+                        v1 = cconj_mul(E, g);
+                    } else {
+                        v0 = cconj_mul(E, g);
+                    }
+                } else {  // parent cone node
+                    const int idx = ev - ca.N;
+                    const int rcp = idx / P, n = idx % P;
+                    const int pb = Pl.rc_box[rcp];
+                    T r1r, r1i, g1, irabs;
+                    if constexpr (MX) {
+                        float s, u[3];
+                        node32<PS, PA>(Pl, tb, Pl.rc_cone[rcp], n, s, u);
+                        const float rp = Pl.hu / s;
+                        const float nv[3] = {rp * u[0], rp * u[1], rp * u[2]};
+                        const float o0 = (L.ijk[3 * cbox] + 0.5f) * L.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+                        const float o1 = (L.ijk[3 * cbox + 1] + 0.5f) * L.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+                        const float o2 = (L.ijk[3 * cbox + 2] + 0.5f) * L.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+                        const float p0 = nv[0] - o0, p1 = nv[1] - o1, p2 = nv[2] - o2;
+                        const float rcv = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+                        float tt[3];
+                        cone_got = classify32(L, p0, p1, p2, rcv, tt);
+                        t3[0] = tt[0]; t3[1] = tt[1]; t3[2] = tt[2];
+                        const float oo = o0 * o0 + o1 * o1 + o2 * o2;
+                        const float no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+                        const float dr = (oo - 2.f * no) / (rcv + rp);
+                        float t = ca.kappa_hi * dr;
+                        t -= rintf(t);
+                        float sn, cs;
+                        cis_cycles(t, sn, cs);
+                        g1 = rp / rcv;
+                        r1r = cs * g1;
+                        r1i = sn * g1;
+                        irabs = 1.f / (rcv * ca.HDf);
+                    } else {
+                        double s, u[3];
+                        node64<PS, PA>(Pl, tb, Pl.rc_cone[rcp], n, s, u);
+                        double yp[3], yc[3];
+                        center64(ca, Pl, pb, yp);
+                        center64(ca, L, cbox, yc);
+                        const double rp = Pl.h / s;
+                        const double x[3] = {yp[0] + rp * u[0], yp[1] + rp * u[1], yp[2] + rp * u[2]};
+                        double rcv, tt[3];
+                        cone_got = classify64(L, x[0] - yc[0], x[1] - yc[1], x[2] - yc[2], rcv, tt);
+                        t3[0] = tt[0]; t3[1] = tt[1]; t3[2] = tt[2];
+                        double sn, cs;
+                        sincos(ca.k * (rcv - rp), &sn, &cs);
+                        g1 = rp / rcv;
+                        r1r = cs * g1;
+                        r1i = sn * g1;
+                        irabs = 1.0 / rcv;
+                    }
+                    C ratio1;
+                    ratio1.x = r1r;
+                    ratio1.y = r1i;
+                    const long long pbase = ((long long)q * Pl.nrc + rcp) * Pl.nfac;
+                    const C gp0 = Gp[pbase * ca.Pstride + n];
+                    if (csplit) {
+                        if (psplit) {
+                            C ratio2;
+                            ratio2.x = r1r * g1;
+                            ratio2.y = r1i * g1;
+                            const C gp1 = Gp[(pbase + 1) * ca.Pstride + n];
+                            v0 = cconj_mul(ratio2, gp0);
+                            v1 = cconj_mul(ratio1, gp1);
+                        } else {
+                            C rr;
+                            rr.x = r1r * irabs;
+                            rr.y = r1i * irabs;
+                            v0 = cconj_mul(rr, gp0);
+                            v1 = cconj_mul(ratio1, gp0);
+                        }
+                    } else {
+                        v0 = cconj_mul(ratio1, gp0);
+                    }
+                }
+                if (cone_got != L.rc_cone[rc] && q == 0) atomicAdd(ca.missed, 1ULL);
+            }
+            lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs,
+                            me.Ls);
+            lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca,
+                            me.Lt);
+            lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca,
+                            me.Lp);
+            me.v[0] = v0;
+            me.v[1] = v1;
+            __syncthreads();
+            if (active) {
+                const int cnt = (int)min((long long)128, e1 - base);
+                for (int t = 0; t < cnt; t++) {
+                    const AntEntry<T, PS, PA> &en = ent[t];
+                    const T w = en.Ls[ua] * en.Lt[ub];
+                    const C v = en.v[fac];
+#pragma unroll
+                    for (int c = 0; c < PA; c++) {
+                        const T wl = w * en.Lp[c];
+                        acc[c].x = fma(wl, v.x, acc[c].x);
+                        acc[c].y = fma(wl, v.y, acc[c].y);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (active) {
+            C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + row * PA;
+#pragma unroll
+            for (int c = 0; c < PA; c++) out[c] = acc[c];
+        }
+    }
+}
+
+// Transposed leaf evaluation: b_j += sum over the cone nodes of j's leaf box of
+// conj(W(x_n, y_j)) G_D (transpose of K1).
+template <int PS, int PA, bool MX>
+__global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, ChebTab tb, const void *G_, void *b_) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    constexpr int P = PS * PA * PA;
+    const C *G = (const C *)G_;
+    C *bo = (C *)b_;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ca.N) return;
+    const int b = ca.leaf_of[j];
+    const bool split = L.split != 0;
+    for (int q = 0; q < ca.nrhs; q++) {
+        T ar = T(0), ai = T(0);
+        for (int rc = L.rc_start[b]; rc < L.rc_start[b + 1]; rc++) {
+            const int cone = L.rc_cone[rc];
+            const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
+            for (int n = 0; n < P; n++) {
+                T W0r, W0i, W1r = T(0), W1i = T(0);
+                if constexpr (MX) {
+                    float s, u[3];
+                    node32<PS, PA>(L, tb, cone, n, s, u);
+                    const float hu = L.hu, ir = s / hu, kap = ca.kappa_hi, soh = s / (hu * ca.HDf);
+                    const float f0 = ca.f32[3 * j], f1 = ca.f32[3 * j + 1], f2 = ca.f32[3 * j + 2];
+                    const float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
+                    const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
+                    const float ia = rsqrtf(a2), am = a2 * ia;
+                    const float yy = f0 * f0 + f1 * f1 + f2 * f2, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
+                    float t = kap * (s * yy / hu - 2.f * uy) / (am + 1.f);
+                    t -= rintf(t);
+                    float sn, cs;
+                    cis_cycles(t, sn, cs);
+                    const float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
+                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = ca.kf * w3 + ca.etaf * ia;
+                    if (split) {
+                        W0r = cs * w2; W0i = sn * w2; W1r = sn * g; W1i = -cs * g;
+                    } else {
+                        W0r = cs * soh * w2 + sn * g; W0i = sn * soh * w2 - cs * g;
+                    }
+                } else {
+                    double s, u[3], y0[3];
+                    node64<PS, PA>(L, tb, cone, n, s, u);
+                    center64(ca, L, b, y0);
+                    const double r = L.h / s, soh = s / L.h;
+                    const double yv[3] = {ca.x64[3 * j] - y0[0], ca.x64[3 * j + 1] - y0[1], ca.x64[3 * j + 2] - y0[2]};
+                    const double dv[3] = {u[0] - yv[0] / r, u[1] - yv[1] / r, u[2] - yv[2] / r};
+                    const double am = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+                    const double yy = yv[0] * yv[0] + yv[1] * yv[1] + yv[2] * yv[2];
+                    const double uy = u[0] * yv[0] + u[1] * yv[1] + u[2] * yv[2];
+                    const double psi = ca.k * (s * yy / L.h - 2.0 * uy) / (am + 1.0);
+                    double sn, cs;
+                    sincos(psi, &sn, &cs);
+                    const double dn = dv[0] * ca.n64[3 * j] + dv[1] * ca.n64[3 * j + 1] + dv[2] * ca.n64[3 * j + 2];
+                    const double ia = 1.0 / am, w3 = dn * ia * ia, w2 = w3 * ia, g = ca.k * w3 + ca.eta * ia;
+                    if (split) {
+                        W0r = cs * w2; W0i = sn * w2; W1r = sn * g; W1i = -cs * g;
+                    } else {
+                        W0r = cs * soh * w2 + sn * g; W0i = sn * soh * w2 - cs * g;
+                    }
+                }
+                const C g0 = G[gb * ca.Pstride + n];
+                ar += W0r * g0.x + W0i * g0.y;  // conj(W) * G
+                ai += W0r * g0.y - W0i * g0.x;
+                if (split) {
+                    const C g1 = G[(gb + 1) * ca.Pstride + n];
+                    ar += W1r * g1.x + W1i * g1.y;
+                    ai += W1r * g1.y - W1i * g1.x;
+                }
+            }
+        }
+        C v = bo[(long long)q * ca.N + j];
+        v.x += ar;
+        v.y += ai;
+        bo[(long long)q * ca.N + j] = v;
+    }
+}
+
+// Transposed near field: b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i.
+template <bool MX>
+__global__ void __launch_bounds__(128) k_near_adj(CommonArgs ca, LevelArgs L, const void *gs_, void *b_) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    const C *gs = (const C *)gs_;
+    C *bo = (C *)b_;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ca.N) return;
+    const int b = ca.leaf_of[j];
+    for (int q = 0; q < ca.nrhs; q++) {
+        T ar = T(0), ai = T(0);
+        for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
+            const int c = ca.nb_list[nb];
+            for (int i = L.start[c]; i < L.start[c + 1]; i++) {
+                if (i == j) continue;
+                T Kr, Ki;
+                if constexpr (MX) {
+                    const float d0 = (float)(L.ijk[3 * c] - L.ijk[3 * b]) + ca.f32[3 * i] - ca.f32[3 * j];
+                    const float d1 = (float)(L.ijk[3 * c + 1] - L.ijk[3 * b + 1]) + ca.f32[3 * i + 1] - ca.f32[3 * j + 1];
+                    const float d2 = (float)(L.ijk[3 * c + 2] - L.ijk[3 * b + 2]) + ca.f32[3 * i + 2] - ca.f32[3 * j + 2];
+                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2, ir = rsqrtf(r2), r = r2 * ir;
+                    if (!(r >= (float)(ca.tol / ca.HD))) continue;
+                    float t = ca.kappa_hi * r;
+                    t -= rintf(t);
+                    float sn, cs;
+                    cis_cycles(t, sn, cs);
+                    const float dn = d0 * ca.n32[3 * j] + d1 * ca.n32[3 * j + 1] + d2 * ca.n32[3 * j + 2];
+                    const float A = dn * ir * ir / ca.HDf, Bv = -(ca.kf * dn * ir + ca.etaf);
+                    const float amp = ir / (4.f * kPiF * ca.HDf);
+                    Kr = amp * (cs * A - sn * Bv);
+                    Ki = amp * (sn * A + cs * Bv);
+                } else {
+                    const double d0 = ca.x64[3 * i] - ca.x64[3 * j], d1 = ca.x64[3 * i + 1] - ca.x64[3 * j + 1],
+                                 d2 = ca.x64[3 * i + 2] - ca.x64[3 * j + 2];
+                    const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    if (r < ca.tol) continue;
+                    double sn, cs;
+                    sincos(ca.k * r, &sn, &cs);
+                    const double ir = 1.0 / r;
+                    const double dn = d0 * ca.n64[3 * j] + d1 * ca.n64[3 * j + 1] + d2 * ca.n64[3 * j + 2];
+                    const double A = dn * ir * ir, Bv = -(ca.k * dn * ir + ca.eta);
+                    const double amp = ir / (4.0 * kPi);
+                    Kr = amp * (cs * A - sn * Bv);
+                    Ki = amp * (sn * A + cs * Bv);
+                }
+                const C g = gs[(long long)q * ca.N + i];
+                ar += Kr * g.x + Ki * g.y;
+                ai += Kr * g.y - Ki * g.x;
+            }
+        }
+        C v;
+        v.x = ar;
+        v.y = ai;
+        bo[(long long)q * ca.N + j] = v;
+    }
+}
+
+// gs[q][s] = g[q][perm[s]]
+template <typename C>
+__global__ void k_gather_plain(int N, int nrhs, const int *__restrict__ perm, const C *__restrict__ g, C *__restrict__ gs) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)N * nrhs) return;
+    const int q = (int)(i / N), s = (int)(i % N);
+    gs[i] = g[(long long)q * N + perm[s]];
+}
+
+// out[q][perm[s]] = conj(cI) g[q][perm[s]] + w_s b[q][s]   (cI real)
+template <typename T>
+__global__ void k_scatter_adj(int N, int nrhs, const int *__restrict__ perm, double cI, const T *__restrict__ w,
+                              const typename CT<T>::c *__restrict__ g, const typename CT<T>::c *__restrict__ b,
+                              typename CT<T>::c *__restrict__ out) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)N * nrhs) return;
+    const int q = (int)(i / N), s = (int)(i % N);
+    const long long o = (long long)q * N + perm[s];
+    typename CT<T>::c gg = g[o], bb = b[i], r;
+    r.x = (T)cI * gg.x + w[s] * bb.x;
+    r.y = (T)cI * gg.y + w[s] * bb.y;
+    out[o] = r;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -909,6 +1284,64 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         }
         k_scatter<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const float2 *)sigma,
                                                       (const float2 *)p.ws.u, (float2 *)y);
+        prof_mark(p, s, kStScatter, 0);
+    }
+    CK(cudaGetLastError());
+    return IFGF_OK;
+}
+
+
+// ============================================================================
+// launch sequence of one adjoint apply (workspace prepared by the caller)
+// ============================================================================
+template <int PS, int PA>
+ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec, cudaStream_t s, void *gs, void *bws,
+                          void **G) {
+    const int D = p.D;
+    const int N = (int)p.N;
+    CommonArgs ca = common_args(p, nrhs);
+    ChebTab tb = cheb_tab(p);
+    LevelArgs L[IFGF_MAXD + 1];
+    for (int d = 3; d <= D; d++) L[d] = level_args(p, d, nullptr);
+    const long long NT = (long long)N * nrhs;
+    prof_begin(p, s);
+    if (prec == IFGF_FP64) {
+        k_gather_plain<double2><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, (const double2 *)g, (double2 *)gs);
+        prof_mark(p, s, kStGather, 0);
+        for (int d = 3; d <= D; d++)
+            if (L[d].nrc) {
+                k_ant<PS, PA, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
+                                                                       (const long long *)p.d_ad_start[d], p.d_ad_list[d],
+                                                                       tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
+                prof_mark(p, s, kStCousin, d);
+            }
+        k_near_adj<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
+        prof_mark(p, s, kStNear, D);
+        if (L[D].nrc) {
+            k_leaf_adj<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], tb, G[D], bws);
+            prof_mark(p, s, kStLeaf, D);
+        }
+        k_scatter_adj<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w64,
+                                                           (const double2 *)g, (const double2 *)bws, (double2 *)out);
+        prof_mark(p, s, kStScatter, 0);
+    } else {
+        k_gather_plain<float2><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, (const float2 *)g, (float2 *)gs);
+        prof_mark(p, s, kStGather, 0);
+        for (int d = 3; d <= D; d++)
+            if (L[d].nrc) {
+                k_ant<PS, PA, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
+                                                                      (const long long *)p.d_ad_start[d], p.d_ad_list[d],
+                                                                      tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
+                prof_mark(p, s, kStCousin, d);
+            }
+        k_near_adj<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
+        prof_mark(p, s, kStNear, D);
+        if (L[D].nrc) {
+            k_leaf_adj<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], tb, G[D], bws);
+            prof_mark(p, s, kStLeaf, D);
+        }
+        k_scatter_adj<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w32,
+                                                          (const float2 *)g, (const float2 *)bws, (float2 *)out);
         prof_mark(p, s, kStScatter, 0);
     }
     CK(cudaGetLastError());

@@ -40,6 +40,11 @@ struct HostLevel {
     std::vector<int> rc_start, rc_cone, rc_box;  // relevant cones (Eq. RelevantCones)
     std::vector<int> cone_map;                   // nbox * ncone -> rc index or -1
     int64_t nrc = 0;
+    // adjoint: for every relevant cone, the forward interpolations that read it:
+    // entries e < N are cousin targets (sorted positions); e >= N are parent cone
+    // nodes (e - N = parent rc * P + node)
+    std::vector<int64_t> ad_start;
+    std::vector<int> ad_list;
     int64_t cousin_evals = 0, prop_evals = 0;
 };
 
@@ -73,6 +78,7 @@ struct Plan {
     ChebAxis cs, ca;
     std::vector<HostLevel> lv;  // index d = 0..D
     std::vector<int> perm;      // sorted position -> caller index
+    std::vector<double> xs;     // sorted absolute positions (host copy)
     std::vector<int> leaf_of;   // sorted position -> leaf box
     int64_t leaf_evals = 0, near_pairs = 0;
     std::vector<int> nb_start, nb_list;  // leaf neighbours (27-neighbourhood incl. self)
@@ -98,6 +104,17 @@ struct Plan {
     float *d_corr_val32 = nullptr;
 
     Workspace ws;
+
+    // adjoint structures (built on the first adjoint apply)
+    bool adj_ready = false;
+    int64_t *d_ad_start[IFGF_MAXD + 1] = {};
+    int *d_ad_list[IFGF_MAXD + 1] = {};
+    int64_t *d_corrT_rowptr = nullptr;
+    int *d_corrT_col = nullptr;
+    double *d_corrT_val64 = nullptr;
+    float *d_corrT_val32 = nullptr;
+    void *adj_ws = nullptr;      // [nrhs][N] gathered g and accumulated b, plus per-level G
+    size_t adj_ws_bytes = 0;
 
     // optional per-launch timing (events recorded on the apply stream)
     bool profile = false;
@@ -125,6 +142,7 @@ inline void prof_mark(Plan &p, cudaStream_t s, int kind, int level) {
 
 // plan.cpp
 ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const double *w);
+ifgf_status build_adjoint_lists(Plan &p, const double *xs_sorted);
 int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L, double leaf_target);
 
 // apply.cu

@@ -3,4 +3,6 @@
 
 namespace ifgf {
 template ifgf_status run_apply_t<4, 6>(Plan &, const void *, void *, int, int, cudaStream_t);
+template ifgf_status run_adjoint_t<4, 6>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *,
+                                              void **);
 }  // namespace ifgf

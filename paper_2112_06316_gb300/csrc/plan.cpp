@@ -356,8 +356,9 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
         L.split = prm.factor_mode == 1 ? 0 : prm.factor_mode == 2 ? 1 : (L.H < 0.5 * lam ? 1 : 0);
         L.nfac = L.split ? 2 : 1;
     }
-    // sorted absolute positions (for classification)
-    std::vector<double> xs(3 * N);
+    // sorted absolute positions (for classification; kept for the adjoint lists)
+    p.xs.resize(3 * N);
+    std::vector<double> &xs = p.xs;
     for (int64_t s = 0; s < N; s++)
         for (int a = 0; a < 3; a++) xs[3 * s + a] = xyz[3 * p.perm[s] + a];
     // relevant cone segments (Eq. RelevantCones), from d = 3 towards D
@@ -422,6 +423,68 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
         for (int b = 0; b < L.nbox; b++)
             le += (int64_t)(L.rc_start[b + 1] - L.rc_start[b]) * p.P * (L.start[b + 1] - L.start[b]);
         p.leaf_evals = le;
+    }
+    return IFGF_OK;
+}
+
+// Adjoint lists: for every relevant cone of level d, the cousin targets and parent
+// cone nodes that the forward apply interpolates from it, classified with the same
+// rule as the kernels (no margin band).  Entry order is deterministic.
+static int classify_exact(const Plan &p, const HostLevel &L, int b, const double *x) {
+    double y0[3];
+    box_center(p, L, b, y0);
+    double dx = x[0] - y0[0], dy = x[1] - y0[1], dz = x[2] - y0[2];
+    double rho = std::sqrt(dx * dx + dy * dy);
+    double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+    double s = L.h / r;
+    double th = std::atan2(rho, dz);
+    double ph = std::atan2(dy, dx);
+    if (ph < 0) ph += 2.0 * M_PI;
+    if (ph >= 2.0 * M_PI) ph = 0.0;
+    double us = snap(s / L.ds), ut = snap(th / L.dth), up = snap(ph / L.dph);
+    int is = std::min(std::max((int)std::floor(us), 0), L.ns - 1);
+    int it = std::min(std::max((int)std::floor(ut), 0), L.nC - 1);
+    int ip = std::min(std::max((int)std::floor(up), 0), L.nph - 1);
+    return (is * L.nC + it) * L.nph + ip;
+}
+
+ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
+    const int64_t N = p.N;
+    for (int d = 3; d <= p.D; d++) {
+        HostLevel &L = p.lv[d];
+        const HostLevel *PL = d > 3 ? &p.lv[d - 1] : nullptr;
+        std::vector<std::vector<std::vector<int>>> per_box(L.nbox);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int b = 0; b < L.nbox; b++) {
+            const int r0 = L.rc_start[b], nr = L.rc_start[b + 1] - r0;
+            std::vector<std::vector<int>> &lists = per_box[b];
+            lists.assign(nr, std::vector<int>());
+            for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
+                int cb = L.co_list[c];
+                for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
+                    int rc = L.cone_map[(size_t)b * L.ncone + classify_exact(p, L, b, xs + 3 * si)];
+                    if (rc >= 0) lists[rc - r0].push_back(si);
+                }
+            }
+            if (PL) {
+                int pb = L.parent[b];
+                for (int rcp = PL->rc_start[pb]; rcp < PL->rc_start[pb + 1]; rcp++)
+                    for (int n = 0; n < p.P; n++) {
+                        double x[3];
+                        node_position(p, *PL, pb, PL->rc_cone[rcp], n, x);
+                        int rc = L.cone_map[(size_t)b * L.ncone + classify_exact(p, L, b, x)];
+                        if (rc >= 0) lists[rc - r0].push_back((int)(N + (int64_t)rcp * p.P + n));
+                    }
+            }
+        }
+        L.ad_start.assign(L.nrc + 1, 0);
+        for (int b = 0; b < L.nbox; b++)
+            for (size_t j = 0; j < per_box[b].size(); j++) L.ad_start[L.rc_start[b] + j + 1] = per_box[b][j].size();
+        for (int64_t r = 0; r < L.nrc; r++) L.ad_start[r + 1] += L.ad_start[r];
+        L.ad_list.resize(L.ad_start[L.nrc]);
+        for (int b = 0; b < L.nbox; b++)
+            for (size_t j = 0; j < per_box[b].size(); j++)
+                std::copy(per_box[b][j].begin(), per_box[b][j].end(), L.ad_list.begin() + L.ad_start[L.rc_start[b] + j]);
     }
     return IFGF_OK;
 }
