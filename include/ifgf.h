@@ -158,6 +158,21 @@ ifgf_status ifgf_apply(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int 
 ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev, int nrhs, ifgf_precision prec,
                                void *stream);
 
+/* Vector-Jacobian product of y = A(k) sigma for reverse-mode differentiation:
+ *   gsigma = A^H g                        (device, N x nrhs, same precision as sigma)
+ *   *dk    = Re sum_rhs <g, (dA/dk) sigma> (host double; may be NULL to skip)
+ * dA/dk is the derivative with the plan frozen (octree, cone grids and relevant
+ * cones fixed, which the piecewise-constant cone rule makes exact for small k
+ * changes), the coupling eta held fixed, and the correction C treated as a
+ * constant.  It is assembled from four fused reductions that pair the forward
+ * cone values with the adjoint cone values (near field, cousin interpolation,
+ * propagation ratios, leaf factors).  The paper has no adjoint or k-derivative.
+ * Runs one forward apply and one adjoint apply internally (gsigma is used as
+ * scratch for the forward output); synchronises `stream` when dk is requested.
+ * Errors as ifgf_apply; sigma, g and gsigma must be distinct. */
+ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g_dev, void *gsigma_dev, int nrhs,
+                           double *dk_host, ifgf_precision prec, void *stream);
+
 /* ifgf_apply without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc at apply time -- for
  * example code whose device memory is reserved up front by a host application or

@@ -15,3 +15,4 @@ from .binding import (  # noqa: F401
     lib,
     supported_orders,
 )
+from .autograd import IFGFApply, ifgf_apply  # noqa: F401

@@ -69,6 +69,8 @@ _SIGS = [
     ("ifgf_plan_set_correction", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64]),
     ("ifgf_apply", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_apply_vjp", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), _VP, _VP]),
@@ -249,6 +251,25 @@ class Plan:
         check(lib().ifgf_apply_adjoint(self._h, _VP(gg.data_ptr()), _VP(y.data_ptr()), ctypes.c_int(gg.shape[0]),
                                        ctypes.c_int(prec), _VP(_stream_ptr(stream))))
         return y.reshape(-1) if squeeze else y
+
+    def vjp(self, sigma, g, stream=None):
+        """(A^H g, Re <g, dA/dk sigma>) for CUDA tensors sigma, g of shape (nrhs, N) or (N,)."""
+        import torch
+
+        if sigma.dtype != g.dtype or sigma.shape != g.shape:
+            raise ValueError("sigma and g must have the same shape and dtype")
+        prec = FP64 if sigma.dtype == torch.complex128 else MIXED if sigma.dtype == torch.complex64 else None
+        if prec is None:
+            raise TypeError("complex64 or complex128 expected")
+        squeeze = sigma.dim() == 1
+        s_ = (sigma.reshape(1, -1) if squeeze else sigma).contiguous()
+        g_ = (g.reshape(1, -1) if squeeze else g).contiguous()
+        out = torch.empty_like(s_)
+        dk = ctypes.c_double(0.0)
+        check(lib().ifgf_apply_vjp(self._h, _VP(s_.data_ptr()), _VP(g_.data_ptr()), _VP(out.data_ptr()),
+                                   ctypes.c_int(s_.shape[0]), ctypes.byref(dk), ctypes.c_int(prec),
+                                   _VP(_stream_ptr(stream))))
+        return (out.reshape(-1) if squeeze else out), float(dk.value)
 
     def apply_noalloc_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):
         """Raw-pointer ``ifgf_apply_noalloc`` (workspace in the library's fixed device array)."""

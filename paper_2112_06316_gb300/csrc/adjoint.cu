@@ -1,7 +1,8 @@
 // Host side of the adjoint apply A^H g (conjugate transpose of the discrete
-// operator, including the correction): builds the anterpolation lists on the
-// first call, manages the adjoint workspace and dispatches over the compiled
-// interpolation orders (kernels in fwd_kernels.cuh).
+// operator, including the correction) and of the vector-Jacobian product
+// (A^H g, Re <g, dA/dk sigma>): builds the anterpolation lists on the first call,
+// manages the adjoint workspace and dispatches over the compiled interpolation
+// orders (kernels in fwd_kernels.cuh).
 #include <cmath>
 #include <vector>
 
@@ -12,24 +13,39 @@ namespace ifgf {
 template <int PS, int PA>
 ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec, cudaStream_t s, void *gs, void *bws,
                           void **G);
-extern template ifgf_status run_adjoint_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *, void **);
-extern template ifgf_status run_adjoint_t<4, 6>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *, void **);
-extern template ifgf_status run_adjoint_t<5, 7>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *, void **);
-extern template ifgf_status run_adjoint_t<5, 8>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *, void **);
-extern template ifgf_status run_adjoint_t<6, 8>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *, void **);
+template <int PS, int PA>
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+                     long long *nparts);
+#define IFGF_EXTERN(a, b)                                                                                           \
+    extern template ifgf_status run_adjoint_t<a, b>(Plan &, const void *, void *, int, int, cudaStream_t, void *,     \
+                                                    void *, void **);                                               \
+    extern template ifgf_status run_dk_t<a, b>(Plan &, int, int, cudaStream_t, const void *, void **, double *,       \
+                                               long long *);
+IFGF_EXTERN(3, 5)
+IFGF_EXTERN(4, 6)
+IFGF_EXTERN(5, 7)
+IFGF_EXTERN(5, 8)
+IFGF_EXTERN(6, 8)
+#undef IFGF_EXTERN
+
 ifgf_status apply_correction_adjoint(Plan &p, const void *g, void *y, int nrhs, int prec, cudaStream_t s);
+ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
 void clear_error();
 
-static ifgf_status cuda_fail(cudaError_t e, const char *what) {
+namespace {
+
+ifgf_status cuda_fail(cudaError_t e, const char *what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
 }
 
 // Anterpolation lists per level (host build, then upload); once per plan.
-static ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
+ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
     if (p.adj_ready) return IFGF_OK;
-    if ((int64_t)p.N + (int64_t)p.lv[p.D].nrc * p.P >= (int64_t)0x7fffffff) {
-        set_error("adjoint lists exceed 32-bit entry range");
+    int64_t maxe = p.N;
+    for (int d = 3; d < p.D; d++) maxe = std::max<int64_t>(maxe, p.N + p.lv[d].nrc * p.P);
+    if (maxe >= (int64_t)0x7fffffff) {
+        set_error("adjoint lists exceed the 32-bit entry range");
         return IFGF_EUNSUPPORTED;
     }
     ifgf_status st = build_adjoint_lists(p, p.xs.data());
@@ -39,7 +55,10 @@ static ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
         void *a = nullptr, *b = nullptr;
         cudaError_t e = cudaMalloc(&a, sizeof(int64_t) * L.ad_start.size());
         if (e == cudaSuccess) e = cudaMalloc(&b, sizeof(int) * (L.ad_list.size() + 1));
-        if (e != cudaSuccess) return cuda_fail(e, "adjoint list allocation");
+        if (e != cudaSuccess) {
+            if (a) cudaFree(a);
+            return cuda_fail(e, "adjoint list allocation");
+        }
         p.allocs.push_back(a);
         p.allocs.push_back(b);
         p.device_bytes += (int64_t)(sizeof(int64_t) * L.ad_start.size() + sizeof(int) * (L.ad_list.size() + 1));
@@ -57,40 +76,19 @@ static ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
     return IFGF_OK;
 }
 
-}  // namespace ifgf
-
-using namespace ifgf;
-
-extern "C" ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev, int nrhs,
-                                          ifgf_precision prec, void *stream) {
-    clear_error();
-    if (!plan) {
-        set_error("null plan");
-        return IFGF_EINVAL;
-    }
-    if (nrhs < 0 || (nrhs > 0 && (!g_dev || !out_dev))) {
-        set_error("invalid nrhs or null device pointer");
-        return IFGF_EINVAL;
-    }
-    if (prec != IFGF_FP64 && prec != IFGF_MIXED) {
-        set_error("unknown precision %d", (int)prec);
-        return IFGF_EINVAL;
-    }
-    if (nrhs == 0) return IFGF_OK;
-    if (g_dev == out_dev) {
-        set_error("g and out must not alias");
-        return IFGF_EINVAL;
-    }
-    Plan &p = plan->p;
-    cudaStream_t s = (cudaStream_t)stream;
+// A^H g into out (without the correction); leaves the gathered g and the cone
+// values G of every level in the adjoint workspace (returned through gs_out / G).
+ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, int prec, cudaStream_t s, void **gs_out,
+                         void **G) {
     ifgf_status st = ensure_adjoint_lists(p, s);
     if (st != IFGF_OK) return st;
-    // workspace: gs [nrhs][N], b [nrhs][N], G of levels 3..D
     const size_t cb = prec == IFGF_FP64 ? 16 : 8;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    size_t off = 0, ogs = 0, ob = 0, oG[IFGF_MAXD + 1] = {};
-    ogs = off; off += al(cb * p.N * nrhs);
-    ob = off; off += al(cb * p.N * nrhs);
+    size_t off = 0, oG[IFGF_MAXD + 1] = {};
+    const size_t ogs = off;
+    off += al(cb * p.N * nrhs);
+    const size_t ob = off;
+    off += al(cb * p.N * nrhs);
     for (int d = 3; d <= p.D; d++) {
         oG[d] = off;
         off += al(cb * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
@@ -104,18 +102,111 @@ extern "C" ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, vo
         p.adj_ws_bytes = off;
     }
     char *c = (char *)p.adj_ws;
-    void *G[IFGF_MAXD + 1] = {};
     for (int d = 3; d <= p.D; d++) G[d] = c + oG[d];
-#define IFGF_ADJ(a, b)                                                                                  \
-    else if (p.Ps == a && p.Pang == b) st = run_adjoint_t<a, b>(p, g_dev, out_dev, nrhs, (int)prec, s, c + ogs, c + ob, G);
-    if (false) {
+    *gs_out = c + ogs;
+#define IFGF_CASE(a, b) \
+    if (p.Ps == a && p.Pang == b) return run_adjoint_t<a, b>(p, g_dev, out_dev, nrhs, prec, s, c + ogs, c + ob, G);
+    IFGF_CASE(3, 5)
+    IFGF_CASE(4, 6)
+    IFGF_CASE(5, 7)
+    IFGF_CASE(5, 8)
+    IFGF_CASE(6, 8)
+#undef IFGF_CASE
+    set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
+    return IFGF_EUNSUPPORTED;
+}
+
+ifgf_status run_dk(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+                   long long *nparts) {
+#define IFGF_CASE(a, b) \
+    if (p.Ps == a && p.Pang == b) return run_dk_t<a, b>(p, nrhs, prec, s, gs, G, partials, nparts);
+    IFGF_CASE(3, 5)
+    IFGF_CASE(4, 6)
+    IFGF_CASE(5, 7)
+    IFGF_CASE(5, 8)
+    IFGF_CASE(6, 8)
+#undef IFGF_CASE
+    set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
+    return IFGF_EUNSUPPORTED;
+}
+
+ifgf_status check_args(ifgf_plan *plan, const void *a, void *b, int nrhs, ifgf_precision prec) {
+    if (!plan) {
+        set_error("null plan");
+        return IFGF_EINVAL;
     }
-    IFGF_ADJ(3, 5) IFGF_ADJ(4, 6) IFGF_ADJ(5, 7) IFGF_ADJ(5, 8) IFGF_ADJ(6, 8)
-    else {
-        set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
-        return IFGF_EUNSUPPORTED;
+    if (nrhs < 0 || (nrhs > 0 && (!a || !b))) {
+        set_error("invalid nrhs or null device pointer");
+        return IFGF_EINVAL;
     }
-#undef IFGF_ADJ
+    if (prec != IFGF_FP64 && prec != IFGF_MIXED) {
+        set_error("unknown precision %d", (int)prec);
+        return IFGF_EINVAL;
+    }
+    if (nrhs > 0 && a == b) {
+        set_error("input and output must not alias");
+        return IFGF_EINVAL;
+    }
+    return IFGF_OK;
+}
+
+}  // namespace
+}  // namespace ifgf
+
+using namespace ifgf;
+
+extern "C" ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev, int nrhs,
+                                          ifgf_precision prec, void *stream) {
+    clear_error();
+    ifgf_status st = check_args(plan, g_dev, out_dev, nrhs, prec);
+    if (st != IFGF_OK || nrhs == 0) return st;
+    Plan &p = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *gs = nullptr, *G[IFGF_MAXD + 1] = {};
+    st = adjoint_core(p, g_dev, out_dev, nrhs, (int)prec, s, &gs, G);
     if (st != IFGF_OK) return st;
     return apply_correction_adjoint(p, g_dev, out_dev, nrhs, (int)prec, s);
+}
+
+extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g_dev, void *gsigma_dev,
+                                      int nrhs, double *dk_host, ifgf_precision prec, void *stream) {
+    clear_error();
+    ifgf_status st = check_args(plan, g_dev, gsigma_dev, nrhs, prec);
+    if (st != IFGF_OK) return st;
+    if (nrhs > 0 && (!sigma_dev || sigma_dev == gsigma_dev || sigma_dev == g_dev)) {
+        set_error("sigma must be a distinct, non-null device buffer");
+        return IFGF_EINVAL;
+    }
+    if (dk_host) *dk_host = 0.0;
+    if (nrhs == 0) return IFGF_OK;
+    Plan &p = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    // forward state (a = w sigma, cone values F) in the plan workspace; gsigma is scratch here
+    st = run_apply(p, sigma_dev, gsigma_dev, nrhs, (int)prec, s);
+    if (st != IFGF_OK) return st;
+    void *gs = nullptr, *G[IFGF_MAXD + 1] = {};
+    st = adjoint_core(p, g_dev, gsigma_dev, nrhs, (int)prec, s, &gs, G);
+    if (st != IFGF_OK) return st;
+    st = apply_correction_adjoint(p, g_dev, gsigma_dev, nrhs, (int)prec, s);
+    if (st != IFGF_OK) return st;
+    if (!dk_host) return IFGF_OK;
+    long long need = (long long)((p.N + 127) / 128) * (p.D - 1);
+    for (int d = p.D; d >= 3; d--) need += (p.lv[d].nrc * p.P + 127) / 128;
+    double *partials = nullptr;
+    cudaError_t e = cudaMalloc(&partials, sizeof(double) * (need + 1));
+    if (e != cudaSuccess) return cuda_fail(e, "vjp partial sums");
+    long long np = 0;
+    st = run_dk(p, nrhs, (int)prec, s, gs, G, partials, &np);
+    std::vector<double> h(np > 0 ? np : 1, 0.0);
+    if (st == IFGF_OK && np > 0) {
+        e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "vjp partial copy");
+    }
+    cudaFree(partials);
+    if (st != IFGF_OK) return st;
+    double sum = 0.0;
+    for (long long i = 0; i < np; i++) sum += h[i];
+    *dk_host = sum;
+    return IFGF_OK;
 }

@@ -1176,6 +1176,338 @@ __global__ void k_scatter_adj(int N, int nrhs, const int *__restrict__ perm, dou
     out[o] = r;
 }
 
+
+// ============================================================================
+// k-derivative reductions:  Re <g, (dA/dk) sigma>  with the plan frozen and eta
+// fixed.  Each kernel mirrors a forward stage and reduces conj(cotangent) times
+// the k-derivative of that stage's output, using the forward cone values F and
+// the adjoint cone values G.  One double per block is written to `partials`.
+// ============================================================================
+__device__ __forceinline__ void block_sum_store(double v, double *partials) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) partials[blockIdx.x] = v;
+    }
+}
+
+// Re(conj(a) * b)
+template <typename C>
+__device__ __forceinline__ double re_conj_mul(C a, C b) {
+    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+
+// near field: sum_i conj(g_i) sum_j dK/dk(x_i, x_j) a_j,  dK/dk = i r K - i E1 dn / r
+template <bool MX>
+__global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, const void *a_, const void *gs_,
+                                                 double *partials) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    const C *a = (const C *)a_;
+    const C *gs = (const C *)gs_;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (i < ca.N) {
+        const int b = ca.leaf_of[i];
+        for (int q = 0; q < ca.nrhs; q++) {
+            T sr = T(0), si = T(0);
+            for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
+                const int c = ca.nb_list[nb];
+                for (int j = L.start[c]; j < L.start[c + 1]; j++) {
+                    if (j == i) continue;
+                    T Er, Ei, Br, Bi, R, dnr;
+                    if constexpr (MX) {
+                        const float d0 = (float)(L.ijk[3 * b] - L.ijk[3 * c]) + ca.f32[3 * i] - ca.f32[3 * j];
+                        const float d1 = (float)(L.ijk[3 * b + 1] - L.ijk[3 * c + 1]) + ca.f32[3 * i + 1] - ca.f32[3 * j + 1];
+                        const float d2 = (float)(L.ijk[3 * b + 2] - L.ijk[3 * c + 2]) + ca.f32[3 * i + 2] - ca.f32[3 * j + 2];
+                        const float r2 = d0 * d0 + d1 * d1 + d2 * d2, ir = rsqrtf(r2), r = r2 * ir;
+                        if (!(r >= (float)(ca.tol / ca.HD))) continue;
+                        float t = ca.kappa_hi * r;
+                        t -= rintf(t);
+                        float sn, cs;
+                        cis_cycles(t, sn, cs);
+                        const float dn = d0 * ca.n32[3 * j] + d1 * ca.n32[3 * j + 1] + d2 * ca.n32[3 * j + 2];
+                        const float amp = ir / (4.f * kPiF * ca.HDf);
+                        Er = amp * cs; Ei = amp * sn;
+                        Br = dn * ir * ir / ca.HDf; Bi = -(ca.kf * dn * ir + ca.etaf);
+                        R = r * ca.HDf;
+                        dnr = dn * ir;
+                    } else {
+                        const double d0 = ca.x64[3 * i] - ca.x64[3 * j], d1 = ca.x64[3 * i + 1] - ca.x64[3 * j + 1],
+                                     d2 = ca.x64[3 * i + 2] - ca.x64[3 * j + 2];
+                        const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                        if (r < ca.tol) continue;
+                        double sn, cs;
+                        sincos(ca.k * r, &sn, &cs);
+                        const double ir = 1.0 / r, dn = d0 * ca.n64[3 * j] + d1 * ca.n64[3 * j + 1] + d2 * ca.n64[3 * j + 2];
+                        Er = cs * ir / (4.0 * kPi); Ei = sn * ir / (4.0 * kPi);
+                        Br = dn * ir * ir; Bi = -(ca.k * dn * ir + ca.eta);
+                        R = r;
+                        dnr = dn * ir;
+                    }
+                    // K = E B; dK/dk = i R E B - i E dn/r
+                    const T Kr = Er * Br - Ei * Bi, Ki = Er * Bi + Ei * Br;
+                    const T dKr = -R * Ki + Ei * dnr, dKi = R * Kr - Er * dnr;
+                    const C aj = a[(long long)q * ca.N + j];
+                    sr += dKr * aj.x - dKi * aj.y;
+                    si += dKr * aj.y + dKi * aj.x;
+                }
+            }
+            C z;
+            z.x = sr;
+            z.y = si;
+            acc += re_conj_mul(gs[(long long)q * ca.N + i], z);
+        }
+    }
+    block_sum_store(acc, partials);
+}
+
+// cousin interpolation at level d: sum_i conj(g_i) sum_c i r E Interp(F_c)(x_i)
+template <int PS, int PA, bool MX>
+__global__ void __launch_bounds__(128) k_dk_cousin(CommonArgs ca, LevelArgs L, LevelArgs LD, const int *__restrict__ box_of,
+                                                   ChebTab tb, const void *F_, const void *gs_, double *partials) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    const C *F = (const C *)F_;
+    const C *gs = (const C *)gs_;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (i < ca.N) {
+        const int b = box_of[i];
+        for (int q = 0; q < ca.nrhs; q++) {
+            T sr = T(0), si = T(0);
+            for (int ci = L.co_start[b]; ci < L.co_start[b + 1]; ci++) {
+                const int c = L.co_list[ci];
+                T Er, Ei, irabs, t3[3];
+                int rc;
+                if constexpr (MX) {
+                    const int bl = ca.leaf_of[i];
+                    const float I0[3] = {LD.ijk[3 * bl] + 0.5f, LD.ijk[3 * bl + 1] + 0.5f, LD.ijk[3 * bl + 2] + 0.5f};
+                    const float f0[3] = {ca.f32[3 * i], ca.f32[3 * i + 1], ca.f32[3 * i + 2]};
+                    CousGeo g;
+                    cousin_geo32(ca, L, c, I0, f0, g);
+                    rc = g.rc;
+                    Er = g.E1r; Ei = g.E1i; irabs = g.irabs;
+                    t3[0] = g.t3[0]; t3[1] = g.t3[1]; t3[2] = g.t3[2];
+                } else {
+                    double y0[3], r;
+                    center64(ca, L, c, y0);
+                    const int cone = classify64(L, ca.x64[3 * i] - y0[0], ca.x64[3 * i + 1] - y0[1],
+                                                ca.x64[3 * i + 2] - y0[2], r, t3);
+                    rc = L.cone_map[(long long)c * L.ncone + cone];
+                    double sn, cs;
+                    sincos(ca.k * r, &sn, &cs);
+                    Er = cs / (4.0 * kPi * r); Ei = sn / (4.0 * kPi * r);
+                    irabs = 1.0 / r;
+                }
+                if (rc < 0) continue;
+                T Ls[PS], Lt[PA], Lp[PA];
+                lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs, Ls);
+                lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lt);
+                lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lp);
+                const long long base = ((long long)q * L.nrc + rc) * L.nfac;
+                T vr, vi;
+                interp3<PS, PA, T>(F + base * ca.Pstride, Ls, Lt, Lp, vr, vi);
+                if (L.split) {
+                    T wr, wi;
+                    interp3<PS, PA, T>(F + (base + 1) * ca.Pstride, Ls, Lt, Lp, wr, wi);
+                    vr = vr * irabs + wr;
+                    vi = vi * irabs + wi;
+                }
+                const T zr = Er * vr - Ei * vi, zi = Er * vi + Ei * vr;
+                const T rabs = T(1) / irabs;
+                sr += -rabs * zi;  // i r z
+                si += rabs * zr;
+            }
+            C z;
+            z.x = sr;
+            z.y = si;
+            acc += re_conj_mul(gs[(long long)q * ca.N + i], z);
+        }
+    }
+    block_sum_store(acc, partials);
+}
+
+// propagation into level d-1: sum_{rcp,n} conj(G_p[n]) sum_children i (r_c - r_p) ratio Interp(F_c)(x_n)
+template <int PS, int PA, bool MX>
+__global__ void __launch_bounds__(128) k_dk_prop(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb, const void *F_,
+                                                 const void *Gp_, double *partials) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c Cx;
+    constexpr int P = PS * PA * PA;
+    const Cx *FC = (const Cx *)F_;
+    const Cx *Gp = (const Cx *)Gp_;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (tid < Pl.nrc * P) {
+        const int rc = (int)(tid / P), n = (int)(tid % P);
+        const int pb = Pl.rc_box[rc];
+        for (int q = 0; q < ca.nrhs; q++) {
+            T s0r = T(0), s0i = T(0), s1r = T(0), s1i = T(0);  // per parent factor
+            for (int ci = Pl.ch_start[pb]; ci < Pl.ch_start[pb + 1]; ci++) {
+                const int cb = Pl.ch_list[ci];
+                T t3[3], r1r, r1i, g1, irabs, dr_abs;
+                int crc;
+                if constexpr (MX) {
+                    float s, u[3];
+                    node32<PS, PA>(Pl, tb, Pl.rc_cone[rc], n, s, u);
+                    const float rp = Pl.hu / s;
+                    const float nv[3] = {rp * u[0], rp * u[1], rp * u[2]};
+                    const float o0 = (C.ijk[3 * cb] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+                    const float o1 = (C.ijk[3 * cb + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+                    const float o2 = (C.ijk[3 * cb + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+                    PropGeo g;
+                    prop_geo32(ca, C, cb, nv, rp, o0, o1, o2, g);
+                    crc = g.crc;
+                    t3[0] = g.t3[0]; t3[1] = g.t3[1]; t3[2] = g.t3[2];
+                    r1r = g.r1r; r1i = g.r1i; g1 = g.g1; irabs = g.irabs;
+                    const float p0 = nv[0] - o0, p1 = nv[1] - o1, p2 = nv[2] - o2;
+                    const float rcv = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+                    const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+                    dr_abs = (oo - 2.f * no) / (rcv + rp) * ca.HDf;
+                } else {
+                    double s, u[3], yp[3], yc[3];
+                    node64<PS, PA>(Pl, tb, Pl.rc_cone[rc], n, s, u);
+                    center64(ca, Pl, pb, yp);
+                    center64(ca, C, cb, yc);
+                    const double rp = Pl.h / s;
+                    const double x[3] = {yp[0] + rp * u[0], yp[1] + rp * u[1], yp[2] + rp * u[2]};
+                    double rcv;
+                    const int cone = classify64(C, x[0] - yc[0], x[1] - yc[1], x[2] - yc[2], rcv, t3);
+                    crc = C.cone_map[(long long)cb * C.ncone + cone];
+                    double sn, cs;
+                    sincos(ca.k * (rcv - rp), &sn, &cs);
+                    g1 = rp / rcv;
+                    r1r = cs * g1; r1i = sn * g1;
+                    irabs = 1.0 / rcv;
+                    dr_abs = rcv - rp;
+                }
+                if (crc < 0) continue;
+                T Ls[PS], Lt[PA], Lp[PA];
+                lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs, Ls);
+                lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lt);
+                lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lp);
+                const long long base = ((long long)q * C.nrc + crc) * C.nfac;
+                T vr, vi, wr = T(0), wi = T(0);
+                interp3<PS, PA, T>(FC + base * ca.Pstride, Ls, Lt, Lp, vr, vi);
+                if (C.split) interp3<PS, PA, T>(FC + (base + 1) * ca.Pstride, Ls, Lt, Lp, wr, wi);
+                // contributions z0 (parent factor 0) and z1 (parent factor 1), then multiply by i dr
+                T z0r, z0i, z1r = T(0), z1i = T(0);
+                if (C.split && Pl.split) {
+                    const T r2r = r1r * g1, r2i = r1i * g1;
+                    z0r = vr * r2r - vi * r2i; z0i = vr * r2i + vi * r2r;
+                    z1r = wr * r1r - wi * r1i; z1i = wr * r1i + wi * r1r;
+                } else if (C.split) {
+                    const T xr = vr * irabs + wr, xi = vi * irabs + wi;
+                    z0r = xr * r1r - xi * r1i; z0i = xr * r1i + xi * r1r;
+                } else {
+                    z0r = vr * r1r - vi * r1i; z0i = vr * r1i + vi * r1r;
+                }
+                s0r += -dr_abs * z0i; s0i += dr_abs * z0r;
+                s1r += -dr_abs * z1i; s1i += dr_abs * z1r;
+            }
+            const long long pbase = ((long long)q * Pl.nrc + rc) * Pl.nfac;
+            Cx z0, z1;
+            z0.x = s0r; z0.y = s0i; z1.x = s1r; z1.y = s1i;
+            acc += re_conj_mul(Gp[pbase * ca.Pstride + n], z0);
+            if (Pl.split) acc += re_conj_mul(Gp[(pbase + 1) * ca.Pstride + n], z1);
+        }
+    }
+    block_sum_store(acc, partials);
+}
+
+// leaf evaluation: sum_{rc,n} conj(G_D[n]) sum_j dW/dk(x_n, y_j) a_j,
+// dW/dk = i phi0 W - i e w3 (combined or W13),  i phi0 W2 (split W2)
+template <int PS, int PA, bool MX>
+__global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, ChebTab tb, const void *a_, const void *G_,
+                                                 double *partials) {
+    typedef typename std::conditional<MX, float, double>::type T;
+    typedef typename CT<T>::c C;
+    constexpr int P = PS * PA * PA;
+    const C *a = (const C *)a_;
+    const C *G = (const C *)G_;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double acc = 0.0;
+    if (tid < L.nrc * P) {
+        const int rc = (int)(tid / P), n = (int)(tid % P);
+        const int b = L.rc_box[rc];
+        for (int q = 0; q < ca.nrhs; q++) {
+            T s0r = T(0), s0i = T(0), s1r = T(0), s1i = T(0);
+            for (int j = L.start[b]; j < L.start[b + 1]; j++) {
+                T cs, sn, w1, w2, w3, soh, ph0;
+                if constexpr (MX) {
+                    float s, u[3];
+                    node32<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
+                    const float hu = L.hu, ir = s / hu;
+                    const float f0 = ca.f32[3 * j], f1 = ca.f32[3 * j + 1], f2 = ca.f32[3 * j + 2];
+                    const float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
+                    const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2, ia = rsqrtf(a2), am = a2 * ia;
+                    const float yy = f0 * f0 + f1 * f1 + f2 * f2, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
+                    const float phl = (s * yy / hu - 2.f * uy) / (am + 1.f);  // leaf units
+                    float t = ca.kappa_hi * phl;
+                    t -= rintf(t);
+                    float snf, csf;
+                    cis_cycles(t, snf, csf);
+                    sn = snf; cs = csf;
+                    const float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
+                    w1 = ia; w3 = dn * ia * ia; w2 = w3 * ia;
+                    soh = s / (hu * ca.HDf);
+                    ph0 = phl * ca.HDf;
+                } else {
+                    double s, u[3], y0[3];
+                    node64<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
+                    center64(ca, L, b, y0);
+                    const double r = L.h / s;
+                    const double yv[3] = {ca.x64[3 * j] - y0[0], ca.x64[3 * j + 1] - y0[1], ca.x64[3 * j + 2] - y0[2]};
+                    const double dv[3] = {u[0] - yv[0] / r, u[1] - yv[1] / r, u[2] - yv[2] / r};
+                    const double am = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
+                    const double yy = yv[0] * yv[0] + yv[1] * yv[1] + yv[2] * yv[2];
+                    const double uy = u[0] * yv[0] + u[1] * yv[1] + u[2] * yv[2];
+                    ph0 = (s * yy / L.h - 2.0 * uy) / (am + 1.0);
+                    sincos(ca.k * ph0, &sn, &cs);
+                    const double dn = dv[0] * ca.n64[3 * j] + dv[1] * ca.n64[3 * j + 1] + dv[2] * ca.n64[3 * j + 2];
+                    const double ia = 1.0 / am;
+                    w1 = ia; w3 = dn * ia * ia; w2 = w3 * ia;
+                    soh = s / L.h;
+                }
+                const T kk = MX ? (T)ca.kf : (T)ca.k, ee = MX ? (T)ca.etaf : (T)ca.eta;
+                // W = e (A + i B): combined A = soh w2, B = -(k w3 + eta w1); split: W2 = e w2, W13 = e (-i (k w3 + eta w1))
+                T d0r, d0i, d1r = T(0), d1i = T(0);
+                if (L.split) {
+                    // dW2/dk = i ph0 e w2
+                    d0r = -ph0 * sn * w2; d0i = ph0 * cs * w2;
+                    // W13 = e * (0 - i g), g = k w3 + eta w1;  dW13 = i ph0 W13 - i e w3
+                    const T g = kk * w3 + ee * w1;
+                    const T W13r = sn * g, W13i = -cs * g;
+                    d1r = -ph0 * W13i + sn * w3;
+                    d1i = ph0 * W13r - cs * w3;
+                } else {
+                    const T g = kk * w3 + ee * w1;
+                    const T Wr = cs * soh * w2 + sn * g, Wi = sn * soh * w2 - cs * g;
+                    d0r = -ph0 * Wi + sn * w3;
+                    d0i = ph0 * Wr - cs * w3;
+                }
+                const C aj = a[(long long)q * ca.N + j];
+                s0r += d0r * aj.x - d0i * aj.y; s0i += d0r * aj.y + d0i * aj.x;
+                s1r += d1r * aj.x - d1i * aj.y; s1i += d1r * aj.y + d1i * aj.x;
+            }
+            const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
+            C z0, z1;
+            z0.x = s0r; z0.y = s0i; z1.x = s1r; z1.y = s1i;
+            acc += re_conj_mul(G[gb * ca.Pstride + n], z0);
+            if (L.split) acc += re_conj_mul(G[(gb + 1) * ca.Pstride + n], z1);
+        }
+    }
+    block_sum_store(acc, partials);
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1346,6 +1678,63 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
     }
     CK(cudaGetLastError());
     return IFGF_OK;
+}
+
+
+// ============================================================================
+// k-derivative reductions (forward state in p.ws, adjoint state gs / G)
+// ============================================================================
+template <int PS, int PA>
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+                     long long *nparts) {
+    constexpr int P = PS * PA * PA;
+    const int D = p.D;
+    const int N = (int)p.N;
+    CommonArgs ca = common_args(p, nrhs);
+    ChebTab tb = cheb_tab(p);
+    LevelArgs L[IFGF_MAXD + 1];
+    for (int d = 3; d <= D; d++) L[d] = level_args(p, d, p.ws.F[d]);
+    long long off = 0;
+    const bool mx = prec == IFGF_MIXED;
+    if (mx) k_dk_near<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
+    else k_dk_near<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
+    off += nblk(N);
+    for (int d = D; d >= 3; d--) {
+        if (mx) k_dk_cousin<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb, p.ws.F[d], gs,
+                                                                    partials + off);
+        else k_dk_cousin<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb, p.ws.F[d], gs,
+                                                                   partials + off);
+        off += nblk(N);
+    }
+    for (int d = D; d >= 4; d--) {
+        const long long nt = L[d - 1].nrc * P;
+        if (!nt) continue;
+        if (mx) k_dk_prop<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb, p.ws.F[d], G[d - 1],
+                                                                   partials + off);
+        else k_dk_prop<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb, p.ws.F[d], G[d - 1],
+                                                                  partials + off);
+        off += nblk(nt);
+    }
+    {
+        const long long nt = L[D].nrc * P;
+        if (nt) {
+            if (mx) k_dk_leaf<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, L[D], tb, p.ws.a, G[D], partials + off);
+            else k_dk_leaf<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, L[D], tb, p.ws.a, G[D], partials + off);
+            off += nblk(nt);
+        }
+    }
+    *nparts = off;
+    CK(cudaGetLastError());
+    return IFGF_OK;
+}
+
+// number of partial sums run_dk_t writes
+inline long long dk_partials_needed(const Plan &p) {
+    const long long nN = nblk(p.N);
+    long long n = nN * (1 + (p.D - 2));
+    for (int d = p.D; d >= 4; d--) n += nblk(p.lv[d - 1].nrc * p.P);
+    n += nblk(p.lv[p.D].nrc * p.P);
+    return n;
 }
 
 }  // namespace ifgf
