@@ -215,6 +215,38 @@ ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev, void *y_d
 ifgf_status ifgf_gmres(ifgf_plan *plan, const void *rhs_dev, void *x_dev, int restart, int maxit, double tol,
                        ifgf_precision apply_prec, int *iters, double *resid_hist, void *stream);
 
+/* ---- batched applies over many plans (one CUDA graph) ----------------------
+ * A group applies several plans (e.g. many scatterers of uneven size, each with
+ * its own right-hand sides) as one captured CUDA graph.  The first
+ * ifgf_group_apply captures the launch sequences of all plans (largest first,
+ * round-robin over `nstreams` forked capture streams so that independent plans
+ * overlap), instantiates the graph and launches it on `stream`; later calls with
+ * the same buffers, nrhs and precision replay it with one cudaGraphLaunch.  A
+ * change of buffers, nrhs, precision, stream count, or of a plan's workspace or
+ * correction triggers a new capture.  The group references the plans (they must
+ * outlive it) and each plan may appear once.  The paper has no batched apply. */
+typedef struct ifgf_group ifgf_group;
+
+/* Create a group over nplans >= 1 distinct plans.  Errors: IFGF_EINVAL. */
+ifgf_status ifgf_group_create(ifgf_plan *const *plans, int nplans, ifgf_group **out);
+
+/* Number of concurrent capture streams (1..64, default 4). */
+ifgf_status ifgf_group_set_streams(ifgf_group *group, int nstreams);
+
+/* y[i] = A_i sigma[i] for every plan i (device buffers as in ifgf_apply, nrhs[i] >= 0
+ * right-hand sides each, one precision for all).  Asynchronous on `stream`.  Errors
+ * as ifgf_apply; capture failures return IFGF_ECUDA. */
+ifgf_status ifgf_group_apply(ifgf_group *group, const void *const *sigma, void *const *y, const int *nrhs,
+                             ifgf_precision prec, void *stream);
+
+/* Release the group and its graph (not the plans). NULL is a no-op. */
+void ifgf_group_destroy(ifgf_group *group);
+
+/* Tunable: right-hand sides per register block in the mixed interpolation kernels
+ * (4 = share geometry and basis weights across 4 right-hand sides, 1 = recompute
+ * them per right-hand side with fewer registers).  Errors: IFGF_EINVAL. */
+ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 

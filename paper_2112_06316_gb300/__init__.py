@@ -9,6 +9,7 @@ and streams.
 from .binding import (  # noqa: F401
     FP64,
     MIXED,
+    Group,
     IFGFError,
     Params,
     Plan,

@@ -79,6 +79,11 @@ _SIGS = [
     ("ifgf_plan_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_plan_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     ("ifgf_plan_destroy", None, [_VP]),
+    ("ifgf_plan_set_rhs_block", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("ifgf_group_create", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    ("ifgf_group_destroy", None, [_VP]),
 ]
 STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction"]
 
@@ -338,6 +343,9 @@ class Plan:
             check(n)
         return [(STAGES[kind[i]], level[i], ms[i]) for i in range(n)]
 
+    def set_rhs_block(self, rhs_block: int):
+        check(lib().ifgf_plan_set_rhs_block(self._h, ctypes.c_int(rhs_block)))
+
     def missed_lookups(self, stream=None) -> int:
         m = ctypes.c_int64()
         check(lib().ifgf_plan_check(self._h, _VP(_stream_ptr(stream)), ctypes.byref(m)))
@@ -346,3 +354,43 @@ class Plan:
 
 def supported_orders():
     return [tuple(int(v) for v in s.split("x")) for s in lib().ifgf_supported_orders().decode().split(",")]
+
+
+class Group:
+    """``ifgf_group``: one CUDA-graph apply over several plans (each with its own rhs)."""
+
+    def __init__(self, plans, nstreams: int = 4):
+        self.plans = list(plans)
+        arr = (_VP * len(self.plans))(*[p.handle for p in self.plans])
+        h = _VP()
+        check(lib().ifgf_group_create(arr, ctypes.c_int(len(self.plans)), ctypes.byref(h)))
+        self._h = h
+        self.set_streams(nstreams)
+
+    def set_streams(self, nstreams: int):
+        check(lib().ifgf_group_set_streams(self._h, ctypes.c_int(nstreams)))
+        self.nstreams = nstreams
+
+    def apply(self, sigmas, outs, stream=None):
+        """outs[i] = A_i sigmas[i]; tensors of shape (nrhs_i, N_i), one complex dtype for all."""
+        import torch
+
+        dt = sigmas[0].dtype
+        prec = FP64 if dt == torch.complex128 else MIXED
+        n = len(self.plans)
+        sp = (_VP * n)(*[s.data_ptr() for s in sigmas])
+        yp = (_VP * n)(*[y.data_ptr() for y in outs])
+        nr = (ctypes.c_int * n)(*[int(s.shape[0]) if s.dim() == 2 else 1 for s in sigmas])
+        check(lib().ifgf_group_apply(self._h, sp, yp, nr, ctypes.c_int(prec), _VP(_stream_ptr(stream))))
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ifgf_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -148,6 +148,7 @@ ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {
     }
     if (p.ws.base) cudaFree(p.ws.base);
     p.ws = Workspace();
+    p.gen++;
     void *base = nullptr;
     cudaError_t e = cudaMalloc(&base, off);
     if (e != cudaSuccess) {

@@ -255,6 +255,16 @@ ifgf_status ifgf_plan_check(ifgf_plan *plan, void *stream, int64_t *missed_looku
     return IFGF_OK;
 }
 
+ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block) {
+    clear_error();
+    if (!plan || (rhs_block != 1 && rhs_block != 4)) {
+        set_error("rhs_block must be 1 or 4");
+        return IFGF_EINVAL;
+    }
+    plan->p.rhs_block = rhs_block;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable) {
     clear_error();
     if (!plan) {

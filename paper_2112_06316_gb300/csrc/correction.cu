@@ -61,6 +61,7 @@ static void free_correction(Plan &p) {
 }
 
 ifgf_status set_correction(Plan &p, const int64_t *rowptr, const int32_t *col, const double *val, int64_t nnz) {
+    p.gen++;
     if (nnz == 0) {
         free_correction(p);
         return IFGF_OK;

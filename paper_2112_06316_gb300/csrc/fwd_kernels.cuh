@@ -1599,14 +1599,14 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         for (int d = D; d >= 4; d--)
             if (L[d - 1].nrc) {
                 const long long nth = L[d - 1].nrc * ((P + 1) / 2);
-                if (nrhs == 1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
+                if (nrhs == 1 || p.rhs_block == 1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 else k_prop32<PS, PA, kRB><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
         k_near32<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
         prof_mark(p, s, kStNear, D);
         for (int d = D; d >= 3; d--) {
-            if (nrhs == 1)
+            if (nrhs == 1 || p.rhs_block == 1)
                 k_cousin32<PS, PA, 1><<<nblk((N + 1) / 2), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb,
                                                                           (float2 *)p.ws.u);
             else

@@ -116,6 +116,11 @@ struct Plan {
     void *adj_ws = nullptr;      // [nrhs][N] gathered g and accumulated b, plus per-level G
     size_t adj_ws_bytes = 0;
 
+    // bumped whenever device buffers baked into a captured graph may change
+    uint64_t gen = 0;
+    // tunable: right-hand sides per register block in the mixed interpolation kernels (1 or 4)
+    int rhs_block = 4;
+
     // optional per-launch timing (events recorded on the apply stream)
     bool profile = false;
     static constexpr int kMaxEv = 80;

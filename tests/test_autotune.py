@@ -1,0 +1,45 @@
+"""Host logic of the autotuner: candidate selection, medians, JSON cache, keys."""
+import json
+
+from paper_2112_06316_gb300.autotune import DEFAULT_CANDIDATES, Autotuner, tune_key
+
+
+def test_picks_fastest_and_caches(tmp_path):
+    calls = []
+
+    def run(cfg):
+        calls.append(cfg)
+        # fake cost: 4 streams and rhs_block 4 are best
+        return 10.0 + abs(cfg["nstreams"] - 4) + (0 if cfg["rhs_block"] == 4 else 3)
+
+    t = Autotuner(str(tmp_path / "tune.json"))
+    key = tune_key("GB300", "mixed", 3_854_976, 4)
+    r = t.tune(key, run, reps=3)
+    assert r.config == {"nstreams": 4, "rhs_block": 4} and not r.cached
+    assert len(calls) == 3 * len(DEFAULT_CANDIDATES)
+    db = json.load(open(tmp_path / "tune.json"))
+    assert db[key]["config"] == r.config
+    # a second tuner reads the cache and does not time again
+    calls.clear()
+    r2 = Autotuner(str(tmp_path / "tune.json")).tune(key, run)
+    assert r2.cached and r2.config == r.config and not calls
+    r3 = Autotuner(str(tmp_path / "tune.json")).tune(key, run, force=True, candidates=[{"nstreams": 1, "rhs_block": 1}])
+    assert r3.config == {"nstreams": 1, "rhs_block": 1} and not r3.cached
+
+
+def test_median_of_reps(tmp_path):
+    seq = iter([5.0, 100.0, 6.0, 1.0, 9.0, 8.0])
+
+    def run(cfg):
+        return next(seq)
+
+    r = Autotuner(str(tmp_path / "t.json")).tune("k", run, reps=3,
+                                                 candidates=[{"nstreams": 1, "rhs_block": 1}, {"nstreams": 2, "rhs_block": 1}])
+    # medians: (5, 100, 6) -> 6 and (1, 9, 8) -> 8
+    assert r.config["nstreams"] == 1 and r.ms == 6.0
+
+
+def test_key_buckets():
+    assert tune_key("d", "fp64", 1000, 1) == tune_key("d", "fp64", 1024, 1)
+    assert tune_key("d", "fp64", 1025, 1) != tune_key("d", "fp64", 1024, 1)
+    assert tune_key("d", "mixed", 1000, 4) != tune_key("d", "fp64", 1000, 4)

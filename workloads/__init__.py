@@ -12,5 +12,6 @@ from .geometry import (  # noqa: F401
     star_body,
     sphere_workload,
     random_density,
+    scatterer_batch,
     Surface,
 )

@@ -238,3 +238,23 @@ def random_density(N: int, nrhs: int, seed: int) -> np.ndarray:
     re = rng.standard_normal((nrhs, N))
     im = rng.standard_normal((nrhs, N))
     return re + 1j * im
+
+
+def scatterer_batch(seed: int = 3, count: int = 24, n_min: int = 64, n_max: int = 256, d_min: float = 2.0,
+                    d_max: float = 24.0):
+    """Uneven batch of scatterers: spheres (even index) and ellipsoids with axis ratios
+    from U[1, 3] (odd index); diameters D_i ~ U[d_min, d_max] wavelengths; points
+    N_i ~ 20k + 380k (D_i^2 - 4) / 572 rounded to 6 n^2 with n a multiple of 8 in
+    [n_min, n_max].  Returns a list of (surface, k) with k = 2 pi D_i / diameter."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        dw = rng.uniform(d_min, d_max)
+        nt = 20000 + 380000 * (dw * dw - 4) / 572
+        n = int(np.clip(round(math.sqrt(max(nt, 1) / 6) / 8) * 8, n_min, n_max))
+        if i % 2 == 0:
+            s = cube_sphere(n, 8)
+        else:
+            s = ellipsoid(n, 8, (1.0, rng.uniform(1, 3), rng.uniform(1, 3)))
+        out.append((s, 2 * math.pi * dw / s.diameter()))
+    return out
