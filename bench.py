@@ -51,11 +51,18 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
+    ap.add_argument("--batch", action="store_true", help="also time the 24-scatterer graph apply")
     return ap.parse_args()
 
 
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def random_density_like(sig, seed):
+    from workloads import random_density
+
+    return random_density(sig.shape[1], sig.shape[0], seed)
 
 
 def workload(args):
@@ -268,6 +275,22 @@ def run_ours(args):
                 "all_stages_tflops": {kk: round(flops_of[kk] / (by_kind[kk] * 1e-3) / 1e12, 3)
                                       for kk in flops_of if kk in by_kind}}
 
+    # ---- adjoint (mixed) and vector-Jacobian product on the same plan ----
+    g32 = torch.from_numpy(random_density_like(sig, 7).astype(np.complex64)).to(dev)
+    a32 = torch.empty_like(g32)
+    plan.adjoint(g32, out=a32)  # builds the anterpolation lists once (host)
+    t_adj = timed(lambda: plan.adjoint(g32, out=a32), max(3, args.steps // 4), 2)
+    adj_ms = float(np.mean(t_adj))
+    plan.set_profiling(True)
+    plan.adjoint(g32, out=a32)
+    adj_stages = plan.stage_times()
+    plan.set_profiling(False)
+    t_vjp = timed(lambda: plan.vjp(sig32, g32), 3, 1)
+    adjoint = {"ms_per_step": adj_ms, "adjoint_forward_ratio": adj_ms / ms,
+               "vjp_ms_per_step": float(np.mean(t_vjp)), "vjp_forward_ratio": float(np.mean(t_vjp)) / ms,
+               "stages_ms": {kk: round(sum(t for k2, _, t in adj_stages if k2 == kk), 4)
+                             for kk in {k2 for k2, _, _ in adj_stages}}}
+
     # ---- end to end through host (pinned) buffers ----
     hs = torch.from_numpy(sig.astype(np.complex64)).pin_memory()
     hy = torch.empty_like(hs).pin_memory()
@@ -292,8 +315,9 @@ def run_ours(args):
                                   f"orders ({Ps},{Pang},{Pang}), nC0=2, nS0=1, eta=k, nrhs={nrhs}",
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
-           "roofline": roofline, "e2e": e2e,
-           "gpu_launches": launches_per_apply * args.steps,
+           "roofline": roofline, "e2e": e2e, "adjoint": adjoint,
+           "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
+           "gpu_launches": launches_per_apply * args.steps + len(adj_stages) * max(3, args.steps // 4),
            "clocks": clk}
 
     if not args.quick:
@@ -337,6 +361,25 @@ def run_ours(args):
                           f"workload, full sphere's octree, orders ({Ps},{Pang},{Pang}); took {t_cap:.1f} s",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
+    if args.batch:
+        from paper_2112_06316_gb300 import Group
+        from workloads import random_density as _rd, scatterer_batch
+
+        bodies = scatterer_batch(seed=3)
+        t0 = time.perf_counter()
+        bplans = [Plan(b.points, b.normals, b.weights, Params(k=kb)) for b, kb in bodies]
+        bsig = [torch.from_numpy(_rd(b.N, 4, 300 + i).astype(np.complex64)).to(dev) for i, (b, _) in enumerate(bodies)]
+        bout = [torch.empty_like(x) for x in bsig]
+        build_s = time.perf_counter() - t0
+        grp = Group(bplans)
+        tb = timed(lambda: grp.apply(bsig, bout), max(3, args.steps // 10), 2)
+        npts = sum(b.N for b, _ in bodies) * 4
+        out["batch_24_scatterers"] = {"value": npts / (float(np.mean(tb)) * 1e3), "unit": UNIT,
+                                      "ms_per_step": float(np.mean(tb)), "points_x_rhs": npts,
+                                      "orders": "3x5", "plan_build_s": round(build_s, 1)}
+        grp.close()
+        for bp in bplans:
+            bp.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     plan.close()

@@ -981,7 +981,21 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
                         v0 = cconj_mul(ratio1, gp0);
                     }
                 }
-                if (cone_got != L.rc_cone[rc] && q == 0) atomicAdd(ca.missed, 1ULL);
+                // express the local coordinates in the list's cone (an FP32 classification can land
+                // in a neighbouring cone near a boundary): t' = t + 2 (i_got - i_list), phi wrapping
+                const int cl = L.rc_cone[rc];
+                if (cone_got != cl) {
+                    const int ipg = cone_got % L.nph, itg = (cone_got / L.nph) % L.nC, isg = cone_got / (L.nph * L.nC);
+                    const int ipl = cl % L.nph, itl = (cl / L.nph) % L.nC, isl = cl / (L.nph * L.nC);
+                    int dp = ipg - ipl;
+                    if (dp > L.nph / 2) dp -= L.nph;
+                    if (dp < -L.nph / 2) dp += L.nph;
+                    t3[0] += T(2 * (isg - isl));
+                    t3[1] += T(2 * (itg - itl));
+                    t3[2] += T(2 * dp);
+                    const T lim = T(1.02);
+                    if (q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
+                }
             }
             lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs,
                             me.Ls);
