@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="points per cube-face side")
     ap.add_argument("--wavelengths", type=float, default=16.0)
     ap.add_argument("--orders", default="5x8", help="Ps x Pang of the headline apply")
+    ap.add_argument("--nc0", type=int, default=2, help="coarsest angular cone count n_C0")
+    ap.add_argument("--ns0", type=int, default=1, help="coarsest radial cone count n_S0")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
@@ -92,7 +94,8 @@ def oracle_cap_apply(s, k, sig, tree, Ps, Pang):
     import oracle
 
     idx = cap_sample(s)
-    p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, levels=tree["D"], identity_coef=0.5,
+    p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, nC0=tree.get("nC0", 2), nS0=tree.get("nS0", 1), levels=tree["D"],
+                          identity_coef=0.5,
                           root_center=tree["root_center"], root_side=tree["root_side"])
     t = time.perf_counter()
     oracle.ifgf(s.points[idx], s.normals[idx], s.weights[idx], p, sig[:, idx])
@@ -164,6 +167,7 @@ def run_reference(args):
     Ps, Pang = (int(v) for v in args.orders.split("x"))
     oracle.build()
     info = full_octree(s)
+    info.update(nC0=args.nc0, nS0=args.ns0)
     n = 0
     for _ in range(args.warmup):
         oracle_cap_apply(s, k, sig, info, Ps, Pang)
@@ -174,7 +178,8 @@ def run_reference(args):
     ms = 1e3 * float(np.mean(ts))
     value = n * args.nrhs / (ms * 1e3)
     sample = (f"oracle IFGF (FP64, OpenMP) on the {n}-point spherical cap z > 0.75 of the workload, "
-              f"on the full sphere's octree (D={info['D']}, same root box), orders ({Ps},{Pang},{Pang})")
+              f"on the full sphere's octree (D={info['D']}, same root box), orders ({Ps},{Pang},{Pang}), "
+              f"nC0={args.nc0}, nS0={args.ns0}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -211,7 +216,7 @@ def run_ours(args):
     N, nrhs = s.N, args.nrhs
     Ps, Pang = (int(v) for v in args.orders.split("x"))
     t0 = time.perf_counter()
-    plan = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang))
+    plan = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0))
     plan_s = time.perf_counter() - t0
     info = plan.info()
     P = Ps * Pang * Pang
@@ -312,7 +317,7 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"sphere {args.wavelengths:g} wavelengths across (k={k:.4f}), cube-sphere "
                                   f"6x{args.n}x{args.n} with 8x8 Fejer sub-patches, N={N}, D={info['D']}, "
-                                  f"orders ({Ps},{Pang},{Pang}), nC0=2, nS0=1, eta=k, nrhs={nrhs}",
+                                  f"orders ({Ps},{Pang},{Pang}), nC0={args.nc0}, nS0={args.ns0}, eta=k, nrhs={nrhs}",
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
            "roofline": roofline, "e2e": e2e, "adjoint": adjoint,
@@ -354,7 +359,9 @@ def run_ours(args):
                                         "rows": int(len(rows))}
             out["fp64"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["fp64"]
             out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
-            n_cap, t_cap = oracle_cap_apply(s, k, sig, full_octree(s), Ps, Pang)
+            tree = full_octree(s)
+            tree.update(nC0=args.nc0, nS0=args.ns0)
+            n_cap, t_cap = oracle_cap_apply(s, k, sig, tree, Ps, Pang)
             out["cpu_baseline"] = {
                 "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                 "sample": f"one oracle IFGF apply (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 of the "
