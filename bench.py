@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--nc0", type=int, default=2, help="coarsest angular cone count n_C0")
     ap.add_argument("--ns0", type=int, default=1, help="coarsest radial cone count n_S0")
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--tc-fill", type=float, default=None, help="tensor-core propagation fill threshold")
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
     ap.add_argument("--batch", action="store_true", help="also time the 24-scatterer graph apply")
@@ -218,6 +219,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     plan = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0))
     plan_s = time.perf_counter() - t0
+    if args.tc_fill is not None:
+        plan.set_tc_fill(args.tc_fill)
     info = plan.info()
     P = Ps * Pang * Pang
     sig32 = torch.from_numpy(sig.astype(np.complex64)).to(dev)
@@ -277,6 +280,7 @@ def run_ours(args):
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_basis": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:g} MHz",
                 "all_stages_ms": {kk: round(v, 4) for kk, v in by_kind.items()},
+                "per_launch_ms": [[kk, lvl, round(t, 4)] for kk, lvl, t in stages],
                 "all_stages_tflops": {kk: round(flops_of[kk] / (by_kind[kk] * 1e-3) / 1e12, 3)
                                       for kk in flops_of if kk in by_kind}}
 

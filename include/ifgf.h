@@ -247,6 +247,12 @@ void ifgf_group_destroy(ifgf_group *group);
  * them per right-hand side with fewer registers).  Errors: IFGF_EINVAL. */
 ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block);
 
+/* Tunable: the mixed propagation from a level uses the tensor-core contraction
+ * (orders with Pang = 8) when the fraction of filled pair slots in its tiles is at
+ * least min_fill (default 0.6; 0 = always, > 1 = never), else the CUDA-core kernel.
+ * Errors: IFGF_EINVAL. */
+ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 

@@ -80,6 +80,7 @@ _SIGS = [
     ("ifgf_plan_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     ("ifgf_plan_destroy", None, [_VP]),
     ("ifgf_plan_set_rhs_block", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("ifgf_plan_set_tc_fill", ctypes.c_int, [_VP, ctypes.c_double]),
     ("ifgf_group_create", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
     ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -342,6 +343,9 @@ class Plan:
         if n < 0:
             check(n)
         return [(STAGES[kind[i]], level[i], ms[i]) for i in range(n)]
+
+    def set_tc_fill(self, min_fill: float):
+        check(lib().ifgf_plan_set_tc_fill(self._h, ctypes.c_double(min_fill)))
 
     def set_rhs_block(self, rhs_block: int):
         check(lib().ifgf_plan_set_rhs_block(self._h, ctypes.c_int(rhs_block)))

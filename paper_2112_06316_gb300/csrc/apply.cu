@@ -106,6 +106,59 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
             for (int si = L.start[b]; si < L.start[b + 1]; si++) box_of[si] = b;
         UP(p.d_box_of[d], box_of);
     }
+    // tensor-core propagation tables (orders with Pang = 8)
+    if (p.Pang == 8) {
+        p.use_tc = true;
+        for (int d = D; d >= 4; d--) {
+            const HostLevel &Cl = p.lv[d], &Pl = p.lv[d - 1];
+            // key = octant * ncone_parent + parent cone id
+            std::vector<std::pair<long long, std::pair<int, int>>> pairs;  // (key, (rcp, cb))
+            for (int pb = 0; pb < Pl.nbox; pb++)
+                for (int ci = Pl.ch_start[pb]; ci < Pl.ch_start[pb + 1]; ci++) {
+                    const int cb = Pl.ch_list[ci];
+                    const int o = (Cl.ijk[3 * cb] & 1) + 2 * (Cl.ijk[3 * cb + 1] & 1) + 4 * (Cl.ijk[3 * cb + 2] & 1);
+                    for (int rc = Pl.rc_start[pb]; rc < Pl.rc_start[pb + 1]; rc++)
+                        pairs.push_back({(long long)o * Pl.ncone + Pl.rc_cone[rc], {rc, cb}});
+                }
+            std::stable_sort(pairs.begin(), pairs.end(),
+                             [](const auto &a, const auto &b) { return a.first < b.first; });
+            std::vector<int> tg, ts, tcnt, gg, gpb, gcb, prc, pcb;
+            TcLevel &T = p.tc[d];
+            int cur_oct = -1;
+            for (size_t i = 0; i < pairs.size();) {
+                size_t j = i;
+                while (j < pairs.size() && pairs[j].first == pairs[i].first) j++;
+                const int g = (int)gg.size();
+                const int oct = (int)(pairs[i].first / Pl.ncone);
+                while (cur_oct < oct) T.oct_tile_start[++cur_oct] = (int)tg.size();
+                gg.push_back((int)(pairs[i].first % Pl.ncone));
+                gpb.push_back(Pl.rc_box[pairs[i].second.first]);
+                gcb.push_back(pairs[i].second.second);
+                for (size_t t = i; t < j; t += kTcPairs) {
+                    tg.push_back(g);
+                    ts.push_back((int)(prc.size() + (t - i)));
+                    tcnt.push_back((int)std::min<size_t>(kTcPairs, j - t));
+                }
+                for (size_t t = i; t < j; t++) {
+                    prc.push_back(pairs[t].second.first);
+                    pcb.push_back(pairs[t].second.second);
+                }
+                i = j;
+            }
+            while (cur_oct < 8) T.oct_tile_start[++cur_oct] = (int)tg.size();
+            T.ntiles = (int)tg.size();
+            T.ngroups = (int)gg.size();
+            T.fill = T.ntiles ? (double)prc.size() / ((double)T.ntiles * kTcPairs) : 0.0;
+            UP(T.tile_group, tg);
+            UP(T.tile_start, ts);
+            UP(T.tile_count, tcnt);
+            UP(T.grp_gamma, gg);
+            UP(T.grp_pb, gpb);
+            UP(T.grp_cb, gcb);
+            UP(T.pair_rcp, prc);
+            UP(T.pair_cb, pcb);
+        }
+    }
     {
         cudaError_t err;
         p.d_missed = dalloc<unsigned long long>(p, 1, err);

@@ -265,6 +265,16 @@ ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block) {
     return IFGF_OK;
 }
 
+ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill) {
+    clear_error();
+    if (!plan || !(min_fill >= 0)) {
+        set_error("min_fill must be >= 0");
+        return IFGF_EINVAL;
+    }
+    plan->p.tc_min_fill = min_fill;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable) {
     clear_error();
     if (!plan) {

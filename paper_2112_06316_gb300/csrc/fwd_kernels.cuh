@@ -1522,6 +1522,335 @@ __global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, Che
     block_sum_store(acc, partials);
 }
 
+
+// ============================================================================
+// Tensor-core propagation (mixed path, Pang = 8).  For one group key (child
+// octant, parent cone id) the map from a child cone's node values to the parent
+// cone's node values is the same for every (parent cone, child box) pair of the
+// key, so a block evaluates it as a dense contraction
+//     D[node, pair] = sum_k W[node, k] F_child(pair)[k]      (M = P, K = P, N = pairs)
+// with warp-level mma.sync m16n8k8 TF32 and a three-term split (hi*hi + hi*lo +
+// lo*hi) that keeps FP32 accuracy; W[node, (a,b,c)] = Ls[a] Lt[b] Lp[c] at the
+// node's child coordinates is generated in the A fragments from per-node basis
+// values staged in shared memory.  The epilogue multiplies by the centred-factor
+// ratio and adds into the parent cone values (the caller zeroes them and launches
+// one octant at a time, so no parent cone is written twice by one launch).
+// ============================================================================
+__device__ __forceinline__ unsigned f2tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    hi = f2tf32(x);
+    lo = f2tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float *d, const unsigned *a, const unsigned *b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int kTcRows = 64;  // parent nodes per block (one m16 tile per warp)
+
+template <int PS>
+struct TcSmem {
+    float Ls[kTcRows][PS];
+    float Lt[kTcRows][12];  // row stride 12: the 32 lanes' (row, tig) reads hit 32 distinct banks
+    float Lp[kTcRows][12];
+    float rr[kTcRows], ri[kTcRows], g1[kTcRows], ir[kTcRows];
+    short perm[kTcRows];        // parent node of each block row (nodes sorted by child cone)
+    signed char slot[kTcRows];  // index of the row's child cone in `cones`, -1 if absent
+    int cones[16];
+    int ncones;
+    int present[16];
+    int jlist[16];  // slots present among the block's rows, ascending
+    int njp;
+    int crc[16][kTcPairs];
+    int rcp[kTcPairs], cb[kTcPairs];
+    // one K-chunk (64 child nodes) of the pairs' child values, split into TF32 hi / lo;
+    // column n = 2 * pair + (re, im); row stride 72 keeps the fragment reads conflict-free.
+    // Before the first chunk, bh holds the child cone of every parent node (P ints).
+    alignas(16) unsigned bh[64][72];
+    alignas(16) unsigned bl[64][72];
+};
+
+// Parent node n of cone gamma seen from the child: position relative to the child
+// centre (p), its distance (rcv) and the node's distance to the parent centre (rp).
+template <int PS>
+__device__ __forceinline__ int tc_child_cone(const LevelArgs &C, const LevelArgs &Pl, const ChebTab &tb, int gamma,
+                                             int n, float o0, float o1, float o2, float *nv, float &rp, float &rcv,
+                                             float *t3) {
+    float s, u[3];
+    node32<PS, 8>(Pl, tb, gamma, n, s, u);
+    rp = Pl.hu / s;
+    nv[0] = rp * u[0];
+    nv[1] = rp * u[1];
+    nv[2] = rp * u[2];
+    const float p0 = nv[0] - o0, p1 = nv[1] - o1, p2 = nv[2] - o2;
+    rcv = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+    return classify32(C, p0, p1, p2, rcv, t3);
+}
+
+// grid: (tiles of this octant) x (P / 64 row slices).  The parent nodes of the group
+// key are ordered by the child cone they fall in (ascending cone id, then node index),
+// so the 16 rows of a warp mostly share one child cone and the masked work of rows in
+// other cones stays small; block y takes rows [64 y, 64 y + 64) of that order.
+template <int PS>
+__global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb, TcLevel T,
+                                                 int tile0) {
+    constexpr int P = PS * 64, NT = kTcPairs / 4;
+    __shared__ TcSmem<PS> sm;
+    static_assert(P <= 64 * 72, "child cone table must fit in the staging buffer");
+    int *ccone = reinterpret_cast<int *>(&sm.bh[0][0]);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tig = lane & 3;
+    const int tile = tile0 + blockIdx.x;
+    const int row0 = blockIdx.y * kTcRows;  // first sorted row of this block
+    const int grp = T.tile_group[tile], p0 = T.tile_start[tile], np = T.tile_count[tile];
+    const int gamma = T.grp_gamma[grp], pb = T.grp_pb[grp], cb0 = T.grp_cb[grp];
+    if (tid < kTcPairs) {
+        sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
+        sm.cb[tid] = tid < np ? T.pair_cb[p0 + tid] : -1;
+    }
+    if (tid < 16) sm.present[tid] = 0;
+    // node geometry relative to the child (the same for every pair of the group)
+    const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+    const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+    const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+    for (int n = tid; n < P; n += blockDim.x) {
+        float nv[3], rp, rcv, t3[3];
+        ccone[n] = tc_child_cone<PS>(C, Pl, tb, gamma, n, o0, o1, o2, nv, rp, rcv, t3);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // distinct child cones, ascending (deterministic order)
+        int nc = 0;
+        for (int base = 0; base < P; base += 32) {
+            const int c = ccone[base + lane];
+            unsigned todo = 0xffffffffu;
+            while (todo) {
+                const int leader = __ffs(todo) - 1;
+                const int cl = __shfl_sync(0xffffffffu, c, leader);
+                const unsigned same = __ballot_sync(0xffffffffu, c == cl);
+                todo &= ~same;
+                bool seen = false;
+                for (int j = 0; j < nc; j++) seen |= sm.cones[j] == cl;
+                if (!seen && nc < 16) {
+                    if (lane == 0) sm.cones[nc] = cl;
+                    nc++;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            for (int i = 1; i < nc; i++)
+                for (int j = i; j > 0 && sm.cones[j - 1] > sm.cones[j]; j--) {
+                    const int t = sm.cones[j];
+                    sm.cones[j] = sm.cones[j - 1];
+                    sm.cones[j - 1] = t;
+                }
+            sm.ncones = nc;
+        }
+        __syncwarp();
+        // stable counting sort of the nodes by slot (slot nc collects nodes of no listed cone)
+        int cnt = 0;  // lane j: nodes in slot j
+        for (int base = 0; base < P; base += 32) {
+            const int c = ccone[base + lane];
+            int sl = 0;
+            while (sl < nc && sm.cones[sl] != c) sl++;
+            for (int j = 0; j <= nc; j++) {
+                const unsigned m = __ballot_sync(0xffffffffu, sl == j);
+                if (lane == j) cnt += __popc(m);
+            }
+        }
+        int start = cnt;  // exclusive prefix over lanes 0..nc
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, start, o);
+            if (lane >= o) start += v;
+        }
+        start -= cnt;
+        for (int base = 0; base < P; base += 32) {
+            const int c = ccone[base + lane];
+            int sl = 0;
+            while (sl < nc && sm.cones[sl] != c) sl++;
+            for (int j = 0; j <= nc; j++) {
+                const unsigned m = __ballot_sync(0xffffffffu, sl == j);
+                const int sj = __shfl_sync(0xffffffffu, start, j);
+                if (sl == j) {
+                    const int pos = sj + __popc(m & ((1u << lane) - 1u)) - row0;
+                    if (pos >= 0 && pos < kTcRows) sm.perm[pos] = (short)(base + lane);
+                }
+                if (lane == j) start += __popc(m);
+            }
+        }
+    }
+    __syncthreads();
+    const int nc = sm.ncones;
+    if (tid < kTcRows) {
+        const int n = sm.perm[tid];
+        float nv[3], rp, rcv, t3[3];
+        const int cone = tc_child_cone<PS>(C, Pl, tb, gamma, n, o0, o1, o2, nv, rp, rcv, t3);
+        int j = 0;
+        while (j < nc && sm.cones[j] != cone) j++;
+        sm.slot[tid] = (signed char)(j < nc ? j : -1);
+        if (j < nc) sm.present[j] = 1;
+        else atomicAdd(ca.missed, 1ULL);
+        const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+        float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
+        t -= rintf(t);
+        float sn, cs;
+        cis_cycles(t, sn, cs);
+        const float g1 = rp / rcv;
+        sm.rr[tid] = cs * g1;
+        sm.ri[tid] = sn * g1;
+        sm.g1[tid] = g1;
+        sm.ir[tid] = 1.f / (rcv * ca.HDf);
+        lagrange<PS, float>(t3[0], tb.fxs, tb.fcs, sm.Ls[tid]);
+        lagrange<8, float>(t3[1], tb.fxa, tb.fca, sm.Lt[tid]);
+        lagrange<8, float>(t3[2], tb.fxa, tb.fca, sm.Lp[tid]);
+    }
+    for (int idx = tid; idx < nc * kTcPairs; idx += blockDim.x) {
+        const int j = idx / kTcPairs, q = idx % kTcPairs;
+        const int cb = sm.cb[q];
+        int crc = -1;
+        if (cb >= 0) {
+            crc = C.cone_map[(long long)cb * C.ncone + sm.cones[j]];
+            if (crc < 0) atomicAdd(ca.missed, 1ULL);
+        }
+        sm.crc[j][q] = crc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int m = 0;
+        for (int j = 0; j < nc; j++)
+            if (sm.present[j]) sm.jlist[m++] = j;
+        sm.njp = m;
+    }
+    __syncthreads();
+    const bool csplit = C.split != 0, psplit = Pl.split != 0;
+    const int npass = (csplit && psplit) ? 2 : 1;
+    const float *FC = (const float *)C.F;
+    float2 *FP = (float2 *)Pl.F;
+    const int r0 = warp * 16 + g, r1 = r0 + 8;  // block-local rows of this lane
+    constexpr int NKC = P / 64;                  // K-chunks of 64 child nodes
+    constexpr int NIT = kTcPairs * 16 / 128;     // staging items per thread
+    const int njp = sm.njp;
+    for (int q = 0; q < ca.nrhs; q++) {
+        for (int pass = 0; pass < npass; pass++) {
+            const int cf_lo = (csplit && psplit) ? pass : 0, cf_hi = (csplit && psplit) ? pass : (csplit ? 1 : 0);
+            const int fp = (csplit && psplit) ? pass : 0;
+            const bool use_g1 = csplit && psplit && pass == 0;
+            const int ncf = cf_hi - cf_lo + 1;
+            const int nsteps = njp * ncf * NKC;  // flattened (cone slot, factor, K-chunk) steps
+            float d[NT][4];
+#pragma unroll
+            for (int nt = 0; nt < NT; nt++) d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.f;
+            float4 pre[NIT][2];  // next step's child values, fetched while the current step computes
+            auto fetch = [&](int st) {
+                const int kc = (st % NKC) * 64, t = st / NKC;
+                const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
+#pragma unroll
+                for (int i = 0; i < NIT; i++) {
+                    const int it = tid + 128 * i;
+                    const int pr = it % kTcPairs, k4 = (it / kTcPairs) * 4;
+                    const int crc = sm.crc[j][pr];
+                    pre[i][0] = pre[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (crc >= 0) {
+                        const float4 *src = reinterpret_cast<const float4 *>(
+                            FC + 2 * ((((long long)q * C.nrc + crc) * C.nfac + cf) * ca.Pstride + kc + k4));
+                        pre[i][0] = __ldg(src);
+                        pre[i][1] = __ldg(src + 1);
+                    }
+                }
+            };
+            if (nsteps > 0) fetch(0);
+            for (int st = 0; st < nsteps; st++) {
+                const int kc = (st % NKC) * 64, t = st / NKC;
+                const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
+                __syncthreads();  // the previous step's fragment reads are done
+#pragma unroll
+                for (int i = 0; i < NIT; i++) {
+                    // item = (pair, 4 consecutive nodes), pair fastest: a warp's stores cover 256 contiguous bytes
+                    const int it = tid + 128 * i;
+                    const int pr = it % kTcPairs, k4 = (it / kTcPairs) * 4;
+                    const float vals[8] = {pre[i][0].x, pre[i][0].y, pre[i][0].z, pre[i][0].w,
+                                           pre[i][1].x, pre[i][1].y, pre[i][1].z, pre[i][1].w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        uint2 h, l;
+                        split_tf32(vals[2 * e], h.x, l.x);
+                        split_tf32(vals[2 * e + 1], h.y, l.y);
+                        *reinterpret_cast<uint2 *>(&sm.bh[k4 + e][2 * pr]) = h;
+                        *reinterpret_cast<uint2 *>(&sm.bl[k4 + e][2 * pr]) = l;
+                    }
+                }
+                __syncthreads();
+                if (st + 1 < nsteps) fetch(st + 1);
+                const bool on0 = sm.slot[r0] == j, on1 = sm.slot[r1] == j;
+                if (!__any_sync(0xffffffffu, on0 || on1)) continue;  // every lane votes: warp-uniform
+                const float sc0 = (csplit && !psplit && cf == 0) ? sm.ir[r0] : 1.f;
+                const float sc1 = (csplit && !psplit && cf == 0) ? sm.ir[r1] : 1.f;
+                const float w0base = on0 ? sc0 : 0.f, w1base = on1 ? sc1 : 0.f;
+#pragma unroll 2
+                for (int kk = 0; kk < 64; kk += 8) {
+                    const int ks = (kc + kk) >> 3;
+                    const int a = ks >> 3, b = ks & 7;
+                    const float w0 = w0base * sm.Ls[r0][a] * sm.Lt[r0][b];
+                    const float w1 = w1base * sm.Ls[r1][a] * sm.Lt[r1][b];
+                    unsigned ah[4], al[4];
+                    split_tf32(w0 * sm.Lp[r0][tig], ah[0], al[0]);
+                    split_tf32(w1 * sm.Lp[r1][tig], ah[1], al[1]);
+                    split_tf32(w0 * sm.Lp[r0][tig + 4], ah[2], al[2]);
+                    split_tf32(w1 * sm.Lp[r1][tig + 4], ah[3], al[3]);
+                    unsigned bh[NT][2], bl[NT][2];
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++) {
+                        const int n = 8 * nt + g;
+                        bh[nt][0] = sm.bh[kk + tig][n];
+                        bh[nt][1] = sm.bh[kk + tig + 4][n];
+                        bl[nt][0] = sm.bl[kk + tig][n];
+                        bl[nt][1] = sm.bl[kk + tig + 4][n];
+                    }
+                    // the three split terms as three sweeps over the n-tiles: dependent MMAs are NT apart
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++) mma_tf32(d[nt], ah, bh[nt]);
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++) mma_tf32(d[nt], ah, bl[nt]);
+#pragma unroll
+                    for (int nt = 0; nt < NT; nt++) mma_tf32(d[nt], al, bh[nt]);
+                }
+            }
+            // epilogue: rows r0, r1; this lane holds pair 4 nt + tig (re, im)
+#pragma unroll
+            for (int nt = 0; nt < NT; nt++) {
+                const int pr = nt * 4 + tig;
+                const int rcp = sm.rcp[pr];
+                if (rcp < 0) continue;
+                const long long base = (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const int r = h ? r1 : r0;
+                    const float dr = d[nt][2 * h], di = d[nt][2 * h + 1];
+                    float rr = sm.rr[r], ri = sm.ri[r];
+                    if (use_g1) {
+                        rr *= sm.g1[r];
+                        ri *= sm.g1[r];
+                    }
+                    const int n = sm.perm[r];
+                    float2 v = FP[base + n];
+                    v.x += rr * dr - ri * di;
+                    v.y += rr * di + ri * dr;
+                    FP[base + n] = v;
+                }
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1611,7 +1940,16 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             prof_mark(p, s, kStLeaf, D);
         }
         for (int d = D; d >= 4; d--)
-            if (L[d - 1].nrc) {
+            if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].fill >= p.tc_min_fill) {
+                const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
+                CK(cudaMemsetAsync(L[d - 1].F, 0, bytes, s));
+                const TcLevel &T = p.tc[d];
+                for (int o = 0; o < 8; o++) {
+                    const int t0 = T.oct_tile_start[o], nt = T.oct_tile_start[o + 1] - t0;
+                    if (nt > 0) k_prop_tc<PS><<<dim3(nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
+                }
+                prof_mark(p, s, kStProp, d - 1);
+            } else if (L[d - 1].nrc) {
                 const long long nth = L[d - 1].nrc * ((P + 1) / 2);
                 if (nrhs == 1 || p.rhs_block == 1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 else k_prop32<PS, PA, kRB><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);

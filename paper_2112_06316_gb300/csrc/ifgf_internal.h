@@ -48,6 +48,21 @@ struct HostLevel {
     int64_t cousin_evals = 0, prop_evals = 0;
 };
 
+// Tensor-core propagation into level d-1 (mixed path, Pang = 8): pairs (parent
+// relevant cone, child box) grouped by (child octant, parent cone id) — the
+// propagation weights depend only on that key — and cut into tiles of up to
+// kTcPairs pairs; tiles are ordered by octant so one launch per octant never
+// writes the same parent cone twice.
+constexpr int kTcPairs = 32;
+struct TcLevel {
+    int ntiles = 0, ngroups = 0;
+    double fill = 0.0;  // pairs / (tiles * kTcPairs)
+    int oct_tile_start[9] = {};
+    int *tile_group = nullptr, *tile_start = nullptr, *tile_count = nullptr;
+    int *grp_gamma = nullptr, *grp_pb = nullptr, *grp_cb = nullptr;
+    int *pair_rcp = nullptr, *pair_cb = nullptr;
+};
+
 // Device arrays of one level.
 struct DevLevel {
     int nbox, ns, nC, nph, ncone, split, nfac, scale;
@@ -93,6 +108,10 @@ struct Plan {
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
     unsigned long long *d_missed = nullptr;
+    TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
+    bool use_tc = false;
+    // a level uses the tensor-core propagation when its tile fill reaches this value
+    double tc_min_fill = 0.6;
     std::vector<void *> allocs;
     int64_t device_bytes = 0;
 

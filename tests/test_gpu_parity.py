@@ -182,3 +182,46 @@ def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
     assert rel(y64[:, rows], yd) < 1e-4
     assert rel(y32[:, rows], yd) < 1e-4
     assert rel(y32, y64) < 1e-5
+
+
+@pytest.mark.parametrize("fm", [0, 1, 2])
+@pytest.mark.parametrize("ps", [5, 6])
+def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm):
+    """Orders with Pang = 8 propagate through the tensor-core (mma.sync TF32, three-term split)
+    contraction on the mixed path, forced on at every level (fill threshold 0); two
+    propagation levels (D = 5) in every factor-mode combination (split -> split,
+    split -> combined, combined -> combined), two right-hand sides.  The result matches the
+    oracle to the mixed bar and the CUDA-core propagation (threshold > 1) to 2e-6."""
+    s, k = sphere_workload(64, 8, 6.0)
+    sig = random_density(s.N, 2, 4)
+    ref, _ = oracle_lib.ifgf(s.points, s.normals, s.weights,
+                             oracle_lib.IFGFParams(k=k, identity_coef=0.5, levels=5, Ps=ps, Pang=8,
+                                                   factor_mode=fm), sig)
+    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, levels=5, Ps=ps, Pang=8, factor_mode=fm))
+    plan.set_tc_fill(0.0)
+    y_tc = gpu_apply(plan, sig, np.complex64)
+    assert plan.missed_lookups() == 0
+    plan.set_tc_fill(2.0)
+    y_cc = gpu_apply(plan, sig, np.complex64)
+    e_ref, e_cc = rel(y_tc, ref), rel(y_tc, y_cc)
+    assert e_ref <= 1e-5, e_ref
+    assert e_cc <= 2e-6, e_cc
+    plan.close()
+
+
+def test_tensor_core_propagation_full_size_level_choice(lib):
+    """16-wavelength sphere at orders (5, 8): the default fill threshold puts the fine
+    propagation levels on the tensor cores; the result equals the all-CUDA-core one to
+    2e-6 and the FP64 apply to 1e-5."""
+    s, k = sphere_workload(256, 8, 16.0)
+    sig = random_density(s.N, 1, 8)
+    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, Ps=5, Pang=8))
+    y_def = gpu_apply(plan, sig, np.complex64)
+    plan.set_tc_fill(2.0)
+    y_cc = gpu_apply(plan, sig, np.complex64)
+    y64 = gpu_apply(plan, sig, np.complex128)
+    assert plan.missed_lookups() == 0
+    e_cc, e64 = rel(y_def, y_cc), rel(y_def, y64)
+    assert e_cc <= 2e-6, e_cc
+    assert e64 <= 1e-5, e64
+    plan.close()
