@@ -80,6 +80,14 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     UP(p.d_f32, f32);
     UP(p.d_n32, n32);
     UP(p.d_w32, w32);
+    {
+        std::vector<float4> pn(2 * (size_t)N);
+        for (int64_t i = 0; i < N; i++) {
+            pn[2 * i] = make_float4(f32[3 * i], f32[3 * i + 1], f32[3 * i + 2], 0.f);
+            pn[2 * i + 1] = make_float4(n32[3 * i], n32[3 * i + 1], n32[3 * i + 2], 0.f);
+        }
+        UP(p.d_pn32, pn);
+    }
     UP(p.d_perm, p.perm);
     UP(p.d_leaf_of, p.leaf_of);
     UP(p.d_nb_start, p.nb_start);

@@ -374,14 +374,23 @@ __global__ void __launch_bounds__(kBlock) k_cousin64(CommonArgs ca, LevelArgs L,
 // Mixed kernels: FP32 arithmetic in leaf-box units, exact phase reduction,
 // compensated FP32 accumulation.
 // ============================================================================
+// Kahan-compensated complex accumulator (four adds per component, no compare):
+// the running correction c holds the negated low part lost by the last add.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 struct CAcc {
     float sr, cr, si, ci;
     __device__ __forceinline__ void zero() { sr = cr = si = ci = 0.f; }
     __device__ __forceinline__ void add(float re, float im) {
-        comp_add(sr, cr, re);
-        comp_add(si, ci, im);
+        kahan_add(sr, cr, re);
+        kahan_add(si, ci, im);
     }
-    __device__ __forceinline__ float2 get() const { return make_float2(sr + cr, si + ci); }
+    __device__ __forceinline__ float2 get() const { return make_float2(sr - cr, si - ci); }
 };
 
 template <int PS, int PA>
@@ -420,8 +429,9 @@ __device__ __forceinline__ int classify32(const LevelArgs &L, float px, float py
 // e^{2 pi i t} for |t| <= 1/2 (t already reduced)
 __device__ __forceinline__ void cis_cycles(float t, float &sn, float &cs) { __sincosf(2.f * kPiF * t, &sn, &cs); }
 
-// K1 (mixed)
-template <int PS, int PA>
+// K1 (mixed).  RB right-hand sides per pass; SPLIT = the level stores the two
+// factors {W2, W13} instead of the combined one.
+template <int PS, int PA, int RB, bool SPLIT>
 __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, ChebTab tb, const float2 *__restrict__ a) {
     constexpr int P = PS * PA * PA;
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -436,31 +446,33 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
     const float soh = s / (hu * ca.HDf);   // s / h (absolute)
     const float kf = ca.kf, etaf = ca.etaf;
     const int j0 = L.start[b], j1 = L.start[b + 1];
+    const float4 *pn = ca.pn32;
     float2 *F = (float2 *)L.F;
-    for (int q0 = 0; q0 < ca.nrhs; q0 += kRB) {
-        CAcc acc0[kRB], acc1[kRB];
+    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
+        CAcc acc0[RB], acc1[RB];
 #pragma unroll
-        for (int qq = 0; qq < kRB; qq++) {
+        for (int qq = 0; qq < RB; qq++) {
             acc0[qq].zero();
             acc1[qq].zero();
         }
         for (int j = j0; j < j1; j++) {
-            const float f0 = ca.f32[3 * j], f1 = ca.f32[3 * j + 1], f2 = ca.f32[3 * j + 2];
-            float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
+            const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
+            float dv0 = u[0] - fj.x * ir, dv1 = u[1] - fj.y * ir, dv2 = u[2] - fj.z * ir;
             float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
             float ia = rsqrtf(a2);
             float am = a2 * ia;
-            float yy = f0 * f0 + f1 * f1 + f2 * f2;
-            float uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
-            float t = kap * (s * yy / hu - 2.f * uy) / (am + 1.f);
+            float yy = fj.x * fj.x + fj.y * fj.y + fj.z * fj.z;
+            float uy = u[0] * fj.x + u[1] * fj.y + u[2] * fj.z;
+            // (|x - y| - |x|) / (h / s) in leaf units; am + 1 lies in [1, 3]: the fast divide is exact to 2 ulp
+            float t = kap * __fdividef(ir * yy - 2.f * uy, am + 1.f);
             t -= rintf(t);
             float sn, cs;
             cis_cycles(t, sn, cs);
-            float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
+            float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
             float w3 = dn * ia * ia, w2 = w3 * ia;
             float g = kf * w3 + etaf * ia;
             float W0r, W0i, W1r = 0.f, W1i = 0.f;
-            if (L.split) {
+            if (SPLIT) {
                 W0r = cs * w2;
                 W0i = sn * w2;
                 W1r = sn * g;
@@ -470,20 +482,20 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
                 W0i = sn * soh * w2 - cs * g;
             }
 #pragma unroll
-            for (int qq = 0; qq < kRB; qq++) {
-                if (q0 + qq < ca.nrhs) {
+            for (int qq = 0; qq < RB; qq++) {
+                if (RB == 1 || q0 + qq < ca.nrhs) {
                     float2 aj = a[(long long)(q0 + qq) * ca.N + j];
                     acc0[qq].add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
-                    if (L.split) acc1[qq].add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
+                    if (SPLIT) acc1[qq].add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
                 }
             }
         }
 #pragma unroll
-        for (int qq = 0; qq < kRB; qq++) {
-            if (q0 + qq < ca.nrhs) {
+        for (int qq = 0; qq < RB; qq++) {
+            if (RB == 1 || q0 + qq < ca.nrhs) {
                 long long base = ((long long)(q0 + qq) * L.nrc + rc) * L.nfac;
                 F[base * ca.Pstride + n] = acc0[qq].get();
-                if (L.split) F[(base + 1) * ca.Pstride + n] = acc1[qq].get();
+                if (SPLIT) F[(base + 1) * ca.Pstride + n] = acc1[qq].get();
             }
         }
     }
@@ -622,28 +634,31 @@ __global__ void __launch_bounds__(kBlock) k_prop32(CommonArgs ca, LevelArgs C, L
     }
 }
 
-// K4 (mixed)
+// K4 (mixed), RB right-hand sides per pass
+template <int RB>
 __global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, const float2 *__restrict__ a,
                                                    float2 *__restrict__ u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ca.N) return;
     int b = ca.leaf_of[i];
     const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
-    const float fx0 = ca.f32[3 * i], fx1 = ca.f32[3 * i + 1], fx2 = ca.f32[3 * i + 2];
+    const float4 *pn = ca.pn32;
+    const float4 fi = __ldg(pn + 2 * i);
     const float kf = ca.kf, etaf = ca.etaf, kap = ca.kappa_hi;
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
     const float tolu = (float)(ca.tol / ca.HD);
-    for (int q0 = 0; q0 < ca.nrhs; q0 += kRB) {
-        CAcc acc[kRB];
+    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
+        CAcc acc[RB];
 #pragma unroll
-        for (int qq = 0; qq < kRB; qq++) acc[qq].zero();
+        for (int qq = 0; qq < RB; qq++) acc[qq].zero();
         for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
             int c = ca.nb_list[nb];
-            const float D0 = (float)(bi0 - L.ijk[3 * c]) + fx0, D1 = (float)(bi1 - L.ijk[3 * c + 1]) + fx1,
-                        D2 = (float)(bi2 - L.ijk[3 * c + 2]) + fx2;
+            const float D0 = (float)(bi0 - L.ijk[3 * c]) + fi.x, D1 = (float)(bi1 - L.ijk[3 * c + 1]) + fi.y,
+                        D2 = (float)(bi2 - L.ijk[3 * c + 2]) + fi.z;
             for (int j = L.start[c]; j < L.start[c + 1]; j++) {
                 if (j == i) continue;
-                float d0 = D0 - ca.f32[3 * j], d1 = D1 - ca.f32[3 * j + 1], d2 = D2 - ca.f32[3 * j + 2];
+                const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
+                float d0 = D0 - fj.x, d1 = D1 - fj.y, d2 = D2 - fj.z;
                 float r2 = d0 * d0 + d1 * d1 + d2 * d2;
                 float ir = rsqrtf(r2);
                 float r = r2 * ir;
@@ -652,14 +667,14 @@ __global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, c
                 t -= rintf(t);
                 float sn, cs;
                 cis_cycles(t, sn, cs);
-                float dn = d0 * ca.n32[3 * j] + d1 * ca.n32[3 * j + 1] + d2 * ca.n32[3 * j + 2];
+                float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
                 // K = e^{ikR}/(4 pi R) [ dn_u / (r^2 HD) - i (k dn_u / r + eta) ],  R = r HD
                 float A = dn * ir * ir * iHD, B = -(kf * dn * ir + etaf);
                 float amp = c4 * ir;
                 float Kr = amp * (cs * A - sn * B), Ki = amp * (sn * A + cs * B);
 #pragma unroll
-                for (int qq = 0; qq < kRB; qq++) {
-                    if (q0 + qq < ca.nrhs) {
+                for (int qq = 0; qq < RB; qq++) {
+                    if (RB == 1 || q0 + qq < ca.nrhs) {
                         float2 aj = a[(long long)(q0 + qq) * ca.N + j];
                         acc[qq].add(Kr * aj.x - Ki * aj.y, Kr * aj.y + Ki * aj.x);
                     }
@@ -667,8 +682,8 @@ __global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, c
             }
         }
 #pragma unroll
-        for (int qq = 0; qq < kRB; qq++)
-            if (q0 + qq < ca.nrhs) u[(long long)(q0 + qq) * ca.N + i] = acc[qq].get();
+        for (int qq = 0; qq < RB; qq++)
+            if (RB == 1 || q0 + qq < ca.nrhs) u[(long long)(q0 + qq) * ca.N + i] = acc[qq].get();
     }
 }
 
@@ -1883,7 +1898,7 @@ static inline CommonArgs common_args(const Plan &p, int nrhs) {
     c.kappa_lo = (float)(kap - (double)c.kappa_hi);
     c.leaf_of = p.d_leaf_of; c.nb_start = p.d_nb_start; c.nb_list = p.d_nb_list;
     c.x64 = p.d_x64; c.n64 = p.d_n64; c.w64 = p.d_w64;
-    c.f32 = p.d_f32; c.n32 = p.d_n32; c.w32 = p.d_w32;
+    c.f32 = p.d_f32; c.n32 = p.d_n32; c.w32 = p.d_w32; c.pn32 = p.d_pn32;
     c.missed = p.d_missed;
     return c;
 }
@@ -1936,7 +1951,16 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         k_gather<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w32, (const float2 *)sigma, (float2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
         if (L[D].nrc) {
-            k_leaf32<PS, PA><<<nblk(L[D].nrc * P), kBlock, 0, s>>>(ca, L[D], tb, (const float2 *)p.ws.a);
+            const unsigned g = nblk(L[D].nrc * P);
+            const float2 *a32 = (const float2 *)p.ws.a;
+            const bool rb1 = nrhs == 1 || p.rhs_block == 1;
+            if (L[D].split) {
+                if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                else k_leaf32<PS, PA, kRB, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+            } else {
+                if (rb1) k_leaf32<PS, PA, 1, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                else k_leaf32<PS, PA, kRB, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+            }
             prof_mark(p, s, kStLeaf, D);
         }
         for (int d = D; d >= 4; d--)
@@ -1955,7 +1979,10 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 else k_prop32<PS, PA, kRB><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
-        k_near32<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
+        if (nrhs == 1 || p.rhs_block == 1)
+            k_near32<1><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
+        else
+            k_near32<kRB><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
         prof_mark(p, s, kStNear, D);
         for (int d = D; d >= 3; d--) {
             if (nrhs == 1 || p.rhs_block == 1)
