@@ -113,6 +113,18 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         for (int b = 0; b < L.nbox; b++)
             for (int si = L.start[b]; si < L.start[b + 1]; si++) box_of[si] = b;
         UP(p.d_box_of[d], box_of);
+        std::vector<int4> ch;
+        for (int b = 0; b < L.nbox; b++) {
+            const int n = L.start[b + 1] - L.start[b];
+            const int nch = (n + 31) / 32;
+            for (int k = 0; k < nch; k++) {
+                const int s0 = L.start[b] + (int)((int64_t)n * k / nch);
+                const int s1 = L.start[b] + (int)((int64_t)n * (k + 1) / nch);
+                ch.push_back(make_int4(b, s0, s1 - s0, 0));
+            }
+        }
+        p.ncchunk[d] = (int)ch.size();
+        UP(p.d_cchunk[d], ch);
     }
     // tensor-core propagation tables (orders with Pang = 8)
     if (p.Pang == 8) {

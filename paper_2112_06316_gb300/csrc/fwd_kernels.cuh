@@ -687,9 +687,7 @@ __global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, c
     }
 }
 
-// K2 (mixed).  One thread owns two consecutive (Morton-sorted) targets; when they
-// share their level-d box (almost always) they walk the same cousin list, and when
-// they fall in the same cone of a cousin box its node values are loaded once.
+// K2 (mixed): geometry of one (target, cousin box) pair.
 struct CousGeo {
     int rc;
     float t3[3];
@@ -723,94 +721,133 @@ __device__ __forceinline__ void cousin_add(CAcc &a, bool split, const CousGeo &g
     a.add(g.E1r * vr - g.E1i * vi, g.E1r * vi + g.E1i * vr);
 }
 
-template <int PS, int PA, int RB>
-__global__ void __launch_bounds__(kBlock) k_cousin32(CommonArgs ca, LevelArgs L, LevelArgs LD, const int *__restrict__ box_of,
-                                                     ChebTab tb, float2 *__restrict__ u) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int i0 = 2 * m, i1 = 2 * m + 1;
-    if (i0 >= ca.N) return;
-    const bool has1 = i1 < ca.N;
-    const int b0 = box_of[i0], b1 = has1 ? box_of[i1] : b0;
-    const int l0 = ca.leaf_of[i0], l1 = has1 ? ca.leaf_of[i1] : l0;
-    const float I0[3] = {LD.ijk[3 * l0] + 0.5f, LD.ijk[3 * l0 + 1] + 0.5f, LD.ijk[3 * l0 + 2] + 0.5f};
-    const float I1[3] = {LD.ijk[3 * l1] + 0.5f, LD.ijk[3 * l1 + 1] + 0.5f, LD.ijk[3 * l1 + 2] + 0.5f};
-    const int j1i = has1 ? i1 : i0;
-    const float f0[3] = {ca.f32[3 * i0], ca.f32[3 * i0 + 1], ca.f32[3 * i0 + 2]};
-    const float f1[3] = {ca.f32[3 * j1i], ca.f32[3 * j1i + 1], ca.f32[3 * j1i + 2]};
-    const float2 *F = (const float2 *)L.F;
-    const bool sp = L.split != 0;
-    const int nfac = L.nfac;
-    // both targets walk the cousin list of their level-d box; when the boxes differ
-    // (rare) each box's list is walked once with only its own target kept
-    const int nlist = (b0 == b1) ? 1 : 2;
-    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
-        CAcc acc0[RB], acc1[RB];
+// K2 (mixed), staged.  One warp owns a chunk of at most 32 targets of one level-d
+// box (one per lane) and walks the box's cousin list.  For every cousin, the
+// distinct cones its lanes fall into are taken one at a time: the warp copies that
+// cone's node values (all factors) into its shared-memory buffer with coalesced
+// 16-byte loads, and the lanes of that cone interpolate from shared memory (every
+// lane reads the same address: broadcasts).
+constexpr int kCwWarps = 4;
+
+// 16-byte global -> shared copy that bypasses the registers (cp.async, L2 only)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <int PS, int PA>
+__device__ __forceinline__ void interp3f_one(const float2 *f, const float *Ls, const float *Lt, const float *Lp,
+                                             float &r, float &i) {
+    r = i = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < PS; a++) {
+        const float2 *fa = f + a * PA * PA;
+        float ra = 0.f, ia = 0.f;
 #pragma unroll
-        for (int qq = 0; qq < RB; qq++) {
-            acc0[qq].zero();
-            acc1[qq].zero();
-        }
-#pragma unroll 1
-        for (int li = 0; li < nlist; li++) {
-            const int b = li == 0 ? b0 : b1;
-            const bool keep0 = li == 0, keep1 = has1 && (nlist == 1 || li == 1);
-            for (int ci = L.co_start[b]; ci < L.co_start[b + 1]; ci++) {
-                const int c = L.co_list[ci];
-                CousGeo g0, g1;
-                cousin_geo32(ca, L, c, I0, f0, g0);
-                cousin_geo32(ca, L, c, I1, f1, g1);
-                if (!keep0) g0.rc = -2;
-                if (!keep1) g1.rc = -2;
-                if (q0 == 0 && (g0.rc == -1 || g1.rc == -1)) atomicAdd(ca.missed, (g0.rc == -1) + (g1.rc == -1));
-                float Ls0[PS], Lt0[PA], Lp0[PA], Ls1[PS], Lt1[PA], Lp1[PA];
-                lagrange<PS, float>(g0.t3[0], tb.fxs, tb.fcs, Ls0);
-                lagrange<PA, float>(g0.t3[1], tb.fxa, tb.fca, Lt0);
-                lagrange<PA, float>(g0.t3[2], tb.fxa, tb.fca, Lp0);
-                lagrange<PS, float>(g1.t3[0], tb.fxs, tb.fcs, Ls1);
-                lagrange<PA, float>(g1.t3[1], tb.fxa, tb.fca, Lt1);
-                lagrange<PA, float>(g1.t3[2], tb.fxa, tb.fca, Lp1);
-                const int npass = (g0.rc == g1.rc || g1.rc < 0 || g0.rc < 0) ? 1 : 2;
-#pragma unroll 1
-                for (int pass = 0; pass < npass; pass++) {
-                    const int rc = (pass == 0) ? (g0.rc >= 0 ? g0.rc : g1.rc) : g1.rc;
-                    if (rc < 0) continue;
-                    const bool k0 = g0.rc == rc, k1 = g1.rc == rc;
+        for (int b = 0; b < PA; b++) {
+            float rb = 0.f, ib = 0.f;
+            const float2 *row = fa + b * PA;
+            if constexpr (PA % 2 == 0) {
 #pragma unroll
-                    for (int qq = 0; qq < RB; qq++) {
-                        if (q0 + qq >= ca.nrhs) continue;
-                        const long long base = ((long long)(q0 + qq) * L.nrc + rc) * nfac;
-                        float v0r = 0.f, v0i = 0.f, v1r = 0.f, v1i = 0.f, w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f;
-#pragma unroll 1
-                        for (int fac = 0; fac < nfac; fac++) {
-                            float x0r, x0i, x1r, x1i;
-                            interp3f_pair<PS, PA>(F + (base + fac) * ca.Pstride, Ls0, Lt0, Lp0, Ls1, Lt1, Lp1, x0r,
-                                                  x0i, x1r, x1i);
-                            if (fac == 0) {
-                                v0r = x0r; v0i = x0i; v1r = x1r; v1i = x1i;
-                            } else {
-                                w0r = x0r; w0i = x0i; w1r = x1r; w1i = x1i;
-                            }
-                        }
-                        if (k0) cousin_add(acc0[qq], sp, g0, v0r, v0i, w0r, w0i);
-                        if (k1) cousin_add(acc1[qq], sp, g1, v1r, v1i, w1r, w1i);
-                    }
+                for (int c = 0; c < PA; c += 2) {
+                    const float4 v = *reinterpret_cast<const float4 *>(row + c);
+                    rb = fmaf(Lp[c], v.x, rb);
+                    ib = fmaf(Lp[c], v.y, ib);
+                    rb = fmaf(Lp[c + 1], v.z, rb);
+                    ib = fmaf(Lp[c + 1], v.w, ib);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < PA; c++) {
+                    const float2 v = row[c];
+                    rb = fmaf(Lp[c], v.x, rb);
+                    ib = fmaf(Lp[c], v.y, ib);
                 }
             }
+            ra = fmaf(Lt[b], rb, ra);
+            ia = fmaf(Lt[b], ib, ia);
         }
+        const float la = pick<PS>(Ls, a);
+        r = fmaf(la, ra, r);
+        i = fmaf(la, ia, i);
+    }
+}
+
+template <int PS, int PA, int RB>
+__global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, LevelArgs L, LevelArgs LD,
+                                                            const int4 *__restrict__ chunks, int nchunk, ChebTab tb,
+                                                            float2 *__restrict__ u) {
+    constexpr int P = PS * PA * PA, PST = P + (P & 1);  // PST = node stride of one factor (the plan's Pstride)
+    constexpr int NL = (PST + 31) / 32;                  // float4 per lane to copy two factors
+    __shared__ __align__(16) float2 sF[kCwWarps][2 * PST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kCwWarps + warp;
+    if (ch >= nchunk) return;  // warp-uniform: no block-wide barrier below
+    const int4 cw = chunks[ch];
+    const int b = cw.x;
+    const bool act = lane < cw.z;
+    const int i = cw.y + (act ? lane : 0);
+    const int l = ca.leaf_of[i];
+    const float I[3] = {LD.ijk[3 * l] + 0.5f, LD.ijk[3 * l + 1] + 0.5f, LD.ijk[3 * l + 2] + 0.5f};
+    const float4 fi = __ldg(ca.pn32 + 2 * i);
+    const float f[3] = {fi.x, fi.y, fi.z};
+    const float2 *F = (const float2 *)L.F;
+    const bool sp = L.split != 0;
+    const int nv4 = L.nfac * PST / 2;  // float4 of one relevant cone (all factors)
+    float2 *buf = sF[warp];
+    float4 *dst = reinterpret_cast<float4 *>(buf);
+    const int c0 = L.co_start[b], c1 = L.co_start[b + 1];
+    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
+        CAcc acc[RB];
 #pragma unroll
-        for (int qq = 0; qq < RB; qq++) {
-            if (q0 + qq < ca.nrhs) {
-                long long o = (long long)(q0 + qq) * ca.N + i0;
-                float2 v = u[o], w = acc0[qq].get();
-                v.x += w.x;
-                v.y += w.y;
-                u[o] = v;
-                if (has1) {
-                    v = u[o + 1];
-                    w = acc1[qq].get();
+        for (int qq = 0; qq < RB; qq++) acc[qq].zero();
+        for (int ci = c0; ci < c1; ci++) {
+            const int c = L.co_list[ci];
+            CousGeo g;
+            cousin_geo32(ca, L, c, I, f, g);
+            if (!act) g.rc = -2;
+            if (q0 == 0 && g.rc == -1) atomicAdd(ca.missed, 1ULL);
+            float Ls[PS], Lt[PA], Lp[PA];
+            lagrange<PS, float>(g.t3[0], tb.fxs, tb.fcs, Ls);
+            lagrange<PA, float>(g.t3[1], tb.fxa, tb.fca, Lt);
+            lagrange<PA, float>(g.t3[2], tb.fxa, tb.fca, Lp);
+            bool pend = g.rc >= 0;
+            unsigned m;
+            while ((m = __ballot_sync(0xffffffffu, pend)) != 0u) {
+                const int rc = __shfl_sync(0xffffffffu, g.rc, __ffs(m) - 1);
+                const bool mine = pend && g.rc == rc;
+#pragma unroll
+                for (int qq = 0; qq < RB; qq++) {
+                    if (RB > 1 && q0 + qq >= ca.nrhs) break;  // warp-uniform
+                    const float4 *src = reinterpret_cast<const float4 *>(
+                        F + ((long long)(q0 + qq) * L.nrc + rc) * L.nfac * ca.Pstride);
+                    __syncwarp();  // the previous cone's readers are done
+#pragma unroll
+                    for (int k = 0; k < NL; k++)
+                        if (lane + 32 * k < nv4) cp_async16(dst + lane + 32 * k, src + lane + 32 * k);
+                    cp_async_wait_all();
+                    __syncwarp();
+                    if (mine) {
+                        float vr, vi, wr = 0.f, wi = 0.f;
+                        interp3f_one<PS, PA>(buf, Ls, Lt, Lp, vr, vi);
+                        if (sp) interp3f_one<PS, PA>(buf + PST, Ls, Lt, Lp, wr, wi);
+                        cousin_add(acc[qq], sp, g, vr, vi, wr, wi);
+                    }
+                }
+                pend = pend && !mine;
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int qq = 0; qq < RB; qq++) {
+                if (RB == 1 || q0 + qq < ca.nrhs) {
+                    const long long o = (long long)(q0 + qq) * ca.N + i;
+                    float2 v = u[o];
+                    const float2 w = acc[qq].get();
                     v.x += w.x;
                     v.y += w.y;
-                    u[o + 1] = v;
+                    u[o] = v;
                 }
             }
         }
@@ -1985,12 +2022,16 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             k_near32<kRB><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
         prof_mark(p, s, kStNear, D);
         for (int d = D; d >= 3; d--) {
-            if (nrhs == 1 || p.rhs_block == 1)
-                k_cousin32<PS, PA, 1><<<nblk((N + 1) / 2), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb,
-                                                                          (float2 *)p.ws.u);
-            else
-                k_cousin32<PS, PA, kRB><<<nblk((N + 1) / 2), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb,
-                                                                            (float2 *)p.ws.u);
+            const int nch = p.ncchunk[d];
+            if (nch > 0) {
+                const unsigned g = (unsigned)((nch + kCwWarps - 1) / kCwWarps);
+                if (nrhs == 1 || p.rhs_block == 1)
+                    k_cousin_w<PS, PA, 1><<<g, kCwWarps * 32, 0, s>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb,
+                                                                      (float2 *)p.ws.u);
+                else
+                    k_cousin_w<PS, PA, kRB><<<g, kCwWarps * 32, 0, s>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb,
+                                                                        (float2 *)p.ws.u);
+            }
             prof_mark(p, s, kStCousin, d);
         }
         k_scatter<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const float2 *)sigma,

@@ -104,6 +104,10 @@ struct Plan {
     int *d_perm = nullptr;
     int *d_leaf_of = nullptr;
     int *d_box_of[IFGF_MAXD + 1] = {};  // sorted position -> box index at level d
+    // cousin-interpolation work chunks of level d: (box, first sorted target, count <= 32, 0);
+    // the targets of every box split into near-equal runs of at most 32
+    int4 *d_cchunk[IFGF_MAXD + 1] = {};
+    int ncchunk[IFGF_MAXD + 1] = {};
     int *d_nb_start = nullptr, *d_nb_list = nullptr;
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
