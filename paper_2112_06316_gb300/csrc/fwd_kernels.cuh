@@ -1607,6 +1607,16 @@ __device__ __forceinline__ void mma_tf32(float *d, const unsigned *a, const unsi
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// four 8x8 b16 tiles from shared memory; with 32-bit elements, lane l receives word (l % 4)
+// of row (l / 4) of each tile — the m16n8k8 TF32 B fragment layout for an n-major tile
+__device__ __forceinline__ void ldmatrix_x4(const void *smem_row, unsigned &r0, unsigned &r1, unsigned &r2,
+                                            unsigned &r3) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 constexpr int kTcRows = 64;  // parent nodes per block (one m16 tile per warp)
 
 template <int PS>
@@ -1624,11 +1634,11 @@ struct TcSmem {
     int njp;
     int crc[16][kTcPairs];
     int rcp[kTcPairs], cb[kTcPairs];
-    // one K-chunk (64 child nodes) of the pairs' child values, split into TF32 hi / lo;
-    // column n = 2 * pair + (re, im); row stride 72 keeps the fragment reads conflict-free.
-    // Before the first chunk, bh holds the child cone of every parent node (P ints).
-    alignas(16) unsigned bh[64][72];
-    alignas(16) unsigned bl[64][72];
+    // one K-chunk (64 child nodes) of the pairs' child values, split into TF32 hi (bt[0]) and
+    // lo (bt[1]), stored n-major: bt[h][n][k] with n = 2 * pair + (re, im).  The row stride of
+    // 68 words (272 bytes) puts the 8 rows of an ldmatrix tile in 8 distinct 16-byte bank groups.
+    // Before the first chunk, bt holds the child cone of every parent node (P ints).
+    alignas(16) unsigned bt[2][64][68];
 };
 
 // Parent node n of cone gamma seen from the child: position relative to the child
@@ -1657,8 +1667,8 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                                                  int tile0) {
     constexpr int P = PS * 64, NT = kTcPairs / 4;
     __shared__ TcSmem<PS> sm;
-    static_assert(P <= 64 * 72, "child cone table must fit in the staging buffer");
-    int *ccone = reinterpret_cast<int *>(&sm.bh[0][0]);
+    static_assert(P <= 2 * 64 * 68, "child cone table must fit in the staging buffer");
+    int *ccone = reinterpret_cast<int *>(&sm.bt[0][0][0]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tig = lane & 3;
     const int tile = tile0 + blockIdx.x;
     const int row0 = blockIdx.y * kTcRows;  // first sorted row of this block
@@ -1808,7 +1818,7 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
 #pragma unroll
                 for (int i = 0; i < NIT; i++) {
                     const int it = tid + 128 * i;
-                    const int pr = it % kTcPairs, k4 = (it / kTcPairs) * 4;
+                    const int pr = it >> 4, k4 = (it & 15) * 4;
                     const int crc = sm.crc[j][pr];
                     pre[i][0] = pre[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (crc >= 0) {
@@ -1826,19 +1836,22 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                 __syncthreads();  // the previous step's fragment reads are done
 #pragma unroll
                 for (int i = 0; i < NIT; i++) {
-                    // item = (pair, 4 consecutive nodes), pair fastest: a warp's stores cover 256 contiguous bytes
+                    // item = (pair, 4 consecutive nodes), nodes fastest: 8 threads store 128 contiguous bytes
                     const int it = tid + 128 * i;
-                    const int pr = it % kTcPairs, k4 = (it / kTcPairs) * 4;
-                    const float vals[8] = {pre[i][0].x, pre[i][0].y, pre[i][0].z, pre[i][0].w,
-                                           pre[i][1].x, pre[i][1].y, pre[i][1].z, pre[i][1].w};
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        uint2 h, l;
-                        split_tf32(vals[2 * e], h.x, l.x);
-                        split_tf32(vals[2 * e + 1], h.y, l.y);
-                        *reinterpret_cast<uint2 *>(&sm.bh[k4 + e][2 * pr]) = h;
-                        *reinterpret_cast<uint2 *>(&sm.bl[k4 + e][2 * pr]) = l;
-                    }
+                    const int pr = it >> 4, k4 = (it & 15) * 4;
+                    uint4 hr, lr, hi_, li;
+                    split_tf32(pre[i][0].x, hr.x, lr.x);
+                    split_tf32(pre[i][0].z, hr.y, lr.y);
+                    split_tf32(pre[i][1].x, hr.z, lr.z);
+                    split_tf32(pre[i][1].z, hr.w, lr.w);
+                    split_tf32(pre[i][0].y, hi_.x, li.x);
+                    split_tf32(pre[i][0].w, hi_.y, li.y);
+                    split_tf32(pre[i][1].y, hi_.z, li.z);
+                    split_tf32(pre[i][1].w, hi_.w, li.w);
+                    *reinterpret_cast<uint4 *>(&sm.bt[0][2 * pr][k4]) = hr;
+                    *reinterpret_cast<uint4 *>(&sm.bt[1][2 * pr][k4]) = lr;
+                    *reinterpret_cast<uint4 *>(&sm.bt[0][2 * pr + 1][k4]) = hi_;
+                    *reinterpret_cast<uint4 *>(&sm.bt[1][2 * pr + 1][k4]) = li;
                 }
                 __syncthreads();
                 if (st + 1 < nsteps) fetch(st + 1);
@@ -1861,11 +1874,10 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                     unsigned bh[NT][2], bl[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; nt++) {
-                        const int n = 8 * nt + g;
-                        bh[nt][0] = sm.bh[kk + tig][n];
-                        bh[nt][1] = sm.bh[kk + tig + 4][n];
-                        bl[nt][0] = sm.bl[kk + tig][n];
-                        bl[nt][1] = sm.bl[kk + tig + 4][n];
+                        // lane supplies the row address of tile (lane / 8): hi k0-3, hi k4-7, lo k0-3, lo k4-7
+                        const int tl = lane >> 3;
+                        const unsigned *row = &sm.bt[tl >> 1][8 * nt + (lane & 7)][kk + 4 * (tl & 1)];
+                        ldmatrix_x4(row, bh[nt][0], bh[nt][1], bl[nt][0], bl[nt][1]);
                     }
                     // the three split terms as three sweeps over the n-tiles: dependent MMAs are NT apart
 #pragma unroll
