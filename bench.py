@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--ns0", type=int, default=1, help="coarsest radial cone count n_S0")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tc-fill", type=float, default=None, help="tensor-core propagation fill threshold")
+    ap.add_argument("--tc-engine", type=int, default=None, help="tensor-core propagation engine: 1 tcgen05, 0 mma.sync")
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
     ap.add_argument("--batch", action="store_true", help="also time the 24-scatterer graph apply")
@@ -221,6 +222,8 @@ def run_ours(args):
     plan_s = time.perf_counter() - t0
     if args.tc_fill is not None:
         plan.set_tc_fill(args.tc_fill)
+    if args.tc_engine is not None:
+        plan.set_tc_engine(args.tc_engine)
     info = plan.info()
     P = Ps * Pang * Pang
     sig32 = torch.from_numpy(sig.astype(np.complex64)).to(dev)

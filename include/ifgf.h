@@ -253,6 +253,15 @@ ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block);
  * Errors: IFGF_EINVAL. */
 ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill);
 
+/* Tunable: engine of the tensor-core propagation.  1 (default) = 5th-generation
+ * tensor cores: the last angular contraction of the tensor-product Chebyshev
+ * interpolant (Eq. ChebyPoly; K = 8) runs as tcgen05.mma with TF32 hi/lo operands
+ * in shared memory and FP32 accumulators in tensor memory, the other two
+ * contractions in registers; 0 = warp-level mma.sync over the full K = P
+ * contraction.  Both keep FP32-level accuracy (three-term TF32 split).
+ * Errors: IFGF_EINVAL for any other value. */
+ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 

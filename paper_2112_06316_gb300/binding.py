@@ -81,6 +81,7 @@ _SIGS = [
     ("ifgf_plan_destroy", None, [_VP]),
     ("ifgf_plan_set_rhs_block", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_plan_set_tc_fill", ctypes.c_int, [_VP, ctypes.c_double]),
+    ("ifgf_plan_set_tc_engine", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_create", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
     ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
@@ -346,6 +347,10 @@ class Plan:
 
     def set_tc_fill(self, min_fill: float):
         check(lib().ifgf_plan_set_tc_fill(self._h, ctypes.c_double(min_fill)))
+
+    def set_tc_engine(self, engine: int):
+        """1 = tcgen05 (tensor memory), 0 = warp-level mma.sync."""
+        check(lib().ifgf_plan_set_tc_engine(self._h, ctypes.c_int(engine)))
 
     def set_rhs_block(self, rhs_block: int):
         check(lib().ifgf_plan_set_rhs_block(self._h, ctypes.c_int(rhs_block)))

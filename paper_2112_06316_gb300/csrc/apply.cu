@@ -20,6 +20,13 @@ namespace ifgf {
 
 template <int PS, int PA>
 ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
+template <int PS, int PA>
+ifgf_status prepare_t(Plan &p, cudaStream_t s);
+extern template ifgf_status prepare_t<3, 5>(Plan &, cudaStream_t);
+extern template ifgf_status prepare_t<4, 6>(Plan &, cudaStream_t);
+extern template ifgf_status prepare_t<5, 7>(Plan &, cudaStream_t);
+extern template ifgf_status prepare_t<5, 8>(Plan &, cudaStream_t);
+extern template ifgf_status prepare_t<6, 8>(Plan &, cudaStream_t);
 extern template ifgf_status run_apply_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t);
 extern template ifgf_status run_apply_t<4, 6>(Plan &, const void *, void *, int, int, cudaStream_t);
 extern template ifgf_status run_apply_t<5, 7>(Plan &, const void *, void *, int, int, cudaStream_t);
@@ -177,6 +184,17 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
             UP(T.grp_cb, gcb);
             UP(T.pair_rcp, prc);
             UP(T.pair_cb, pcb);
+            {
+                cudaError_t err;
+                const size_t ng = gg.size() > 0 ? gg.size() : 1;
+                T.grp_perm = dalloc<short>(p, ng * (size_t)p.P, err);
+                if (T.grp_perm) T.grp_cones = dalloc<int>(p, ng * 16, err);
+                if (T.grp_cones) T.grp_nc = dalloc<int>(p, ng, err);
+                if (!T.grp_nc) {
+                    set_error("cudaMalloc failed: %s", cudaGetErrorString(err));
+                    return IFGF_ENOMEM;
+                }
+            }
         }
     }
     {
@@ -189,7 +207,14 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         CK(cudaMemsetAsync(p.d_missed, 0, sizeof(unsigned long long), s));
     }
     CK(cudaStreamSynchronize(s));
-    return IFGF_OK;
+    ifgf_status st = IFGF_EUNSUPPORTED;
+    if (p.Ps == 3 && p.Pang == 5) st = prepare_t<3, 5>(p, s);
+    else if (p.Ps == 4 && p.Pang == 6) st = prepare_t<4, 6>(p, s);
+    else if (p.Ps == 5 && p.Pang == 7) st = prepare_t<5, 7>(p, s);
+    else if (p.Ps == 5 && p.Pang == 8) st = prepare_t<5, 8>(p, s);
+    else if (p.Ps == 6 && p.Pang == 8) st = prepare_t<6, 8>(p, s);
+    else set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
+    return st;
 }
 
 void free_plan_device(Plan &p) {

@@ -275,6 +275,16 @@ ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill) {
     return IFGF_OK;
 }
 
+ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine) {
+    clear_error();
+    if (!plan || (engine != 0 && engine != 1)) {
+        set_error("engine must be 0 (mma.sync) or 1 (tcgen05)");
+        return IFGF_EINVAL;
+    }
+    plan->p.tc_engine = engine;
+    return IFGF_OK;
+}
+
 ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable) {
     clear_error();
     if (!plan) {

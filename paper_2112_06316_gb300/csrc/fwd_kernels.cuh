@@ -1663,7 +1663,7 @@ __device__ __forceinline__ int tc_child_cone(const LevelArgs &C, const LevelArgs
 // so the 16 rows of a warp mostly share one child cone and the masked work of rows in
 // other cones stays small; block y takes rows [64 y, 64 y + 64) of that order.
 template <int PS>
-__global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb, TcLevel T,
+__global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb, TcLevel T,
                                                  int tile0) {
     constexpr int P = PS * 64, NT = kTcPairs / 4;
     __shared__ TcSmem<PS> sm;
@@ -1859,18 +1859,21 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                 if (!__any_sync(0xffffffffu, on0 || on1)) continue;  // every lane votes: warp-uniform
                 const float sc0 = (csplit && !psplit && cf == 0) ? sm.ir[r0] : 1.f;
                 const float sc1 = (csplit && !psplit && cf == 0) ? sm.ir[r1] : 1.f;
-                const float w0base = on0 ? sc0 : 0.f, w1base = on1 ? sc1 : 0.f;
+                // a chunk of 64 nodes is one radial index a = kc / 64; node k = kc + 8 b + c
+                const int a = kc >> 6;
+                const float s0 = on0 ? sc0 * sm.Ls[r0][a] : 0.f, s1 = on1 ? sc1 * sm.Ls[r1][a] : 0.f;
+                const float p00 = sm.Lp[r0][tig], p04 = sm.Lp[r0][tig + 4];
+                const float p10 = sm.Lp[r1][tig], p14 = sm.Lp[r1][tig + 4];
 #pragma unroll 2
                 for (int kk = 0; kk < 64; kk += 8) {
-                    const int ks = (kc + kk) >> 3;
-                    const int a = ks >> 3, b = ks & 7;
-                    const float w0 = w0base * sm.Ls[r0][a] * sm.Lt[r0][b];
-                    const float w1 = w1base * sm.Ls[r1][a] * sm.Lt[r1][b];
+                    const int b = kk >> 3;
+                    const float w0 = s0 * sm.Lt[r0][b];
+                    const float w1 = s1 * sm.Lt[r1][b];
                     unsigned ah[4], al[4];
-                    split_tf32(w0 * sm.Lp[r0][tig], ah[0], al[0]);
-                    split_tf32(w1 * sm.Lp[r1][tig], ah[1], al[1]);
-                    split_tf32(w0 * sm.Lp[r0][tig + 4], ah[2], al[2]);
-                    split_tf32(w1 * sm.Lp[r1][tig + 4], ah[3], al[3]);
+                    split_tf32(w0 * p00, ah[0], al[0]);
+                    split_tf32(w1 * p10, ah[1], al[1]);
+                    split_tf32(w0 * p04, ah[2], al[2]);
+                    split_tf32(w1 * p14, ah[3], al[3]);
                     unsigned bh[NT][2], bl[NT][2];
 #pragma unroll
                     for (int nt = 0; nt < NT; nt++) {
@@ -1889,14 +1892,24 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                 }
             }
             // epilogue: rows r0, r1; this lane holds pair 4 nt + tig (re, im)
+            // the pairs of a tile have distinct parent cones: all loads before any store
+            long long oo[NT][2];
+            float2 vv[NT][2];
 #pragma unroll
             for (int nt = 0; nt < NT; nt++) {
-                const int pr = nt * 4 + tig;
-                const int rcp = sm.rcp[pr];
-                if (rcp < 0) continue;
+                const int rcp = sm.rcp[nt * 4 + tig];
                 const long long base = (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
+                    oo[nt][h] = rcp < 0 ? -1 : base + sm.perm[h ? r1 : r0];
+                    vv[nt][h] = rcp < 0 ? make_float2(0.f, 0.f) : FP[oo[nt][h]];
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < NT; nt++) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    if (oo[nt][h] < 0) continue;
                     const int r = h ? r1 : r0;
                     const float dr = d[nt][2 * h], di = d[nt][2 * h + 1];
                     float rr = sm.rr[r], ri = sm.ri[r];
@@ -1904,16 +1917,485 @@ __global__ void __launch_bounds__(128) k_prop_tc(CommonArgs ca, LevelArgs C, Lev
                         rr *= sm.g1[r];
                         ri *= sm.g1[r];
                     }
-                    const int n = sm.perm[r];
-                    float2 v = FP[base + n];
-                    v.x += rr * dr - ri * di;
-                    v.y += rr * di + ri * dr;
-                    FP[base + n] = v;
+                    vv[nt][h].x += rr * dr - ri * di;
+                    vv[nt][h].y += rr * di + ri * dr;
+                    FP[oo[nt][h]] = vv[nt][h];
                 }
             }
         }
     }
 }
+
+// ============================================================================
+// Tensor-core propagation on the 5th-generation tensor cores (tcgen05, TMEM).
+// The interpolation from a child cone is a tensor product; its two angular
+// contractions form one GEMM with K = 64 (node index (b, c) within a radial
+// index a):
+//     D[node, (a, pair, re/im)] = sum_{b,c} Lt[node][b] Lp[node][c] F_pair[a, b, c]
+// with A[node][(b, c)] = Lt[b] Lp[c] the same for every pair, radial index and
+// child cone, and the radial factor Ls[node][a] applied when D is read back.
+// A block owns 128 parent nodes (TMEM lanes) in the plan's child-cone order and
+// one tile of up to 32 pairs.  Each step (child cone, factor, two radial indices)
+// stages B (2 a x 32 pairs x re/im = 128 columns, K = 64) in shared memory as
+// TF32 hi / lo and runs 8 k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of
+// tcgen05.mma 128 x 128 x 8 into one of two 128-column TMEM buffers.
+// Warp-specialised: warps 0-7 stage operands and read D back (two threads per
+// node, one per half of the pairs), warp 8 only issues MMAs.  Per buffer, three
+// mbarriers hand the work over: full (B staged), done (MMAs complete, via
+// tcgen05.commit) and empty (D read back).  Every wait is bounded; a timeout
+// sets a block flag that ends the remaining waits early and is reported in the
+// missed counter (high word).
+// ============================================================================
+constexpr int kT5Rows = 128;     // parent nodes per block (TMEM lanes)
+constexpr int kT5Cols = 128;     // TMEM columns of one step's D (two buffers)
+constexpr int kT5Work = 256;     // staging / readback threads (warps 0-7)
+constexpr int kT5Threads = kT5Work + 32;  // + the MMA-issuing warp
+constexpr int kT5K = 64;         // contraction length (b, c)
+constexpr int kT5TileBytes = kT5Rows * kT5K * 4;  // one 128 x 64 TF32 operand tile (A, or B of one step)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of (row, k) in a K-major, non-swizzled tcgen05 operand tile of 128 rows x K = 64 TF32,
+// stored as 8 contiguous k-slices of 8 values (4 KB each, one MMA's K): within a slice, 8-row x
+// 16-byte core matrices, the two k-halves 128 bytes apart (LBO) and 8-row groups 256 bytes apart
+// (SBO), so that the rows an MMA reads together fall in distinct banks
+__device__ __forceinline__ int t5_off(int r, int k) {
+    return (k >> 3) * 4096 + (r >> 3) * 256 + ((k >> 2) & 1) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ uint64_t t5_desc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void t5_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void t5_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+// bounded wait for the completion of the phase with the given parity; gives up early once the
+// block's abort flag is set
+__device__ __forceinline__ bool t5_wait(uint32_t mbar, uint32_t parity, volatile int *abort_flag) {
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 20) && !done; it++) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (!done && (it & 255) == 255 && *abort_flag) break;
+    }
+    if (!done) *abort_flag = 1;
+    return done != 0;
+}
+
+__device__ __forceinline__ void t5_ld32(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void t5_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+struct T5Misc {
+    short perm[kT5Rows];
+    int cones[16];
+    int ncones;
+    int present[16];
+    int jlist[16];
+    int njp;
+    int crc[16][kTcPairs];
+    int rcp[kTcPairs], cb[kTcPairs];
+    unsigned long long full[2], done[2], empty[2];
+    uint32_t tmem;
+    int abort_;
+};
+
+// dynamic shared memory: A hi, A lo, B[stage][hi / lo], misc
+constexpr size_t kT5Smem = 6 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
+
+template <int PS>
+__global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
+                                                           TcLevel T, int tile0) {
+    constexpr int P = PS * 64, NT5 = kTcPairs, NH = kTcPairs / 2, NSA = (PS + 1) / 2;
+    extern __shared__ unsigned char t5_dyn[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)t5_dyn + 1023) & ~(uintptr_t)1023);
+    unsigned char *const sAh = base, *const sAl = base + kT5TileBytes;
+    unsigned char *sB = base + 2 * kT5TileBytes;  // buffer b: sB + (2 * b + hl) * kT5TileBytes
+    T5Misc &sm = *reinterpret_cast<T5Misc *>(base + 6 * kT5TileBytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool worker = warp < 8;
+    const int qd = warp & 3, hf = (warp >> 2) & 1;  // TMEM lane quadrant, half of the pairs
+    const int row = 32 * qd + lane;
+    const int tile = tile0 + blockIdx.x;
+    const int row0 = blockIdx.y * kT5Rows;
+    const int grp = T.tile_group[tile], p0 = T.tile_start[tile], np = T.tile_count[tile];
+    const int gamma = T.grp_gamma[grp], pb = T.grp_pb[grp], cb0 = T.grp_cb[grp];
+    if (tid < NT5) {
+        sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
+        sm.cb[tid] = tid < np ? T.pair_cb[p0 + tid] : -1;
+    }
+    if (tid < 16) sm.present[tid] = 0;
+    if (tid == 0) {
+        sm.abort_ = 0;
+        for (int b = 0; b < 2; b++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.full[b])), "r"(kT5Work));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.empty[b])), "r"(kT5Work));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.done[b])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(2 * kT5Cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+    const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+    const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+    // node order and child cones of the group key (filled once per plan by k_tc_order)
+    if (tid < 16) sm.cones[tid] = T.grp_cones[16 * grp + tid];
+    if (tid == 0) sm.ncones = T.grp_nc[grp];
+    if (tid < kT5Rows) sm.perm[tid] = (row0 + tid < P) ? T.grp_perm[(long long)grp * P + row0 + tid] : (short)-1;
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const int nc = sm.ncones;
+    const uint32_t tmem = sm.tmem;
+    // this thread's node (both threads of the node compute it): geometry, cone slot, Lagrange factors
+    const int node = worker ? sm.perm[row] : -1;
+    int slot = -1;
+    float Ls[PS], rr = 0.f, ri = 0.f, g1 = 0.f, irs = 0.f;
+#pragma unroll
+    for (int e = 0; e < PS; e++) Ls[e] = 0.f;
+    if (worker) {
+        float Lt[8], Lp[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) Lp[e] = Lt[e] = 0.f;
+        if (node >= 0) {
+            float nv[3], rp, rcv, t3[3];
+            const int cone = tc_child_cone<PS>(C, Pl, tb, gamma, node, o0, o1, o2, nv, rp, rcv, t3);
+            int j = 0;
+            while (j < nc && sm.cones[j] != cone) j++;
+            if (j < nc) {
+                slot = j;
+                if (hf == 0) sm.present[j] = 1;
+            } else if (hf == 0) {
+                atomicAdd(ca.missed, 1ULL);
+            }
+            const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+            float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
+            t -= rintf(t);
+            float sn, cs;
+            cis_cycles(t, sn, cs);
+            g1 = rp / rcv;
+            rr = cs * g1;
+            ri = sn * g1;
+            irs = 1.f / (rcv * ca.HDf);
+            lagrange<PS, float>(t3[0], tb.fxs, tb.fcs, Ls);
+            lagrange<8, float>(t3[1], tb.fxa, tb.fca, Lt);
+            lagrange<8, float>(t3[2], tb.fxa, tb.fca, Lp);
+        }
+        // A[row][(b, c)] = Lt[b] Lp[c]; this thread writes b in [4 hf, 4 hf + 4)
+        auto write_a = [&](int b, float lt) {
+#pragma unroll
+            for (int kh = 0; kh < 2; kh++) {
+                uint4 h, l;
+                split_tf32(lt * Lp[4 * kh + 0], h.x, l.x);
+                split_tf32(lt * Lp[4 * kh + 1], h.y, l.y);
+                split_tf32(lt * Lp[4 * kh + 2], h.z, l.z);
+                split_tf32(lt * Lp[4 * kh + 3], h.w, l.w);
+                *reinterpret_cast<uint4 *>(sAh + t5_off(row, 8 * b + 4 * kh)) = h;
+                *reinterpret_cast<uint4 *>(sAl + t5_off(row, 8 * b + 4 * kh)) = l;
+            }
+        };
+        if (hf == 0) {
+#pragma unroll
+            for (int bb = 0; bb < 4; bb++) write_a(bb, Lt[bb]);
+        } else {
+#pragma unroll
+            for (int bb = 4; bb < 8; bb++) write_a(bb, Lt[bb]);
+        }
+    }
+    for (int idx = tid; idx < nc * NT5; idx += blockDim.x) {
+        const int j = idx / NT5, q = idx % NT5;
+        const int cb = sm.cb[q];
+        int crc = -1;
+        if (cb >= 0) {
+            crc = C.cone_map[(long long)cb * C.ncone + sm.cones[j]];
+            if (crc < 0) atomicAdd(ca.missed, 1ULL);
+        }
+        sm.crc[j][q] = crc;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // A, for the MMAs
+    __syncthreads();
+    if (tid == 0) {
+        int m = 0;
+        for (int j = 0; j < nc; j++)
+            if (sm.present[j]) sm.jlist[m++] = j;
+        sm.njp = m;
+    }
+    __syncthreads();
+    const bool csplit = C.split != 0, psplit = Pl.split != 0;
+    const int npass = (csplit && psplit) ? 2 : 1;
+    const float *FC = (const float *)C.F;
+    float2 *FP = (float2 *)Pl.F;
+    const int njp = sm.njp;
+    volatile int *abort_flag = &sm.abort_;
+    // staging item: a_local = tid >> 7, pair = (tid >> 2) & 31, nodes [16 qn, 16 qn + 16) of that a with
+    // qn = tid & 3; lanes 16-31 store the im row first so a warp's 16-byte stores cover all 8 bank groups
+    const int s_al = (tid >> 7) & 1, s_pair = (tid >> 2) & 31, s_qn = tid & 3;
+    const int first_ri = (lane >> 4) & 1;
+    const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
+    const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl);
+    const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 32u * hf;
+    int G = 0;  // global step index: buffer G & 1, use G >> 1 (phase parity (G >> 1) & 1)
+    for (int q = 0; q < ca.nrhs; q++) {
+        for (int pass = 0; pass < npass; pass++) {
+            const int cf_lo = (csplit && psplit) ? pass : 0, cf_hi = (csplit && psplit) ? pass : (csplit ? 1 : 0);
+            const int fp = (csplit && psplit) ? pass : 0;
+            const bool use_g1 = csplit && psplit && pass == 0;
+            const int ncf = cf_hi - cf_lo + 1;
+            const int nsteps = njp * ncf * NSA;  // (cone slot, factor, pair of radial indices)
+            float E[NH][2];
+#pragma unroll
+            for (int pr = 0; pr < NH; pr++) E[pr][0] = E[pr][1] = 0.f;
+            if (worker) {
+                float4 pre[8], pre2[8];
+                auto fetch_to = [&](int st, float4 *dst) {
+                    const int sa = st % NSA, t = st / NSA;
+                    const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
+                    const int a = 2 * sa + s_al;
+                    const int crc = (a < PS) ? sm.crc[j][s_pair] : -1;
+#pragma unroll
+                    for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (crc >= 0) {
+                        const float4 *src = reinterpret_cast<const float4 *>(
+                            FC + 2 * ((((long long)q * C.nrc + crc) * C.nfac + cf) * ca.Pstride + a * 64 + 16 * s_qn));
+#pragma unroll
+                        for (int e = 0; e < 8; e++) dst[e] = __ldg(src + e);
+                    }
+                };
+                auto fetch = [&](int st) { fetch_to(st, pre); };
+                auto stage = [&](int gs) {  // into buffer gs & 1, then signal full
+                    unsigned char *bh = sB + (2 * (gs & 1)) * kT5TileBytes, *bl = bh + kT5TileBytes;
+                    const int nre = (s_al * 32 + s_pair) * 2;
+#pragma unroll
+                    for (int o = 0; o < 2; o++) {
+                        const bool im = (o ^ first_ri) != 0;
+                        const int n = nre + (im ? 1 : 0);
+#pragma unroll
+                        for (int kq = 0; kq < 4; kq++) {
+                            // nodes 16 qn + 4 kq .. + 3: pre[2 kq] = (n0, n1), pre[2 kq + 1] = (n2, n3)
+                            const float4 u0 = pre[2 * kq], u1 = pre[2 * kq + 1];
+                            uint4 h, l;
+                            split_tf32(im ? u0.y : u0.x, h.x, l.x);
+                            split_tf32(im ? u0.w : u0.z, h.y, l.y);
+                            split_tf32(im ? u1.y : u1.x, h.z, l.z);
+                            split_tf32(im ? u1.w : u1.z, h.w, l.w);
+                            const int k = 16 * s_qn + 4 * kq;
+                            *reinterpret_cast<uint4 *>(bh + t5_off(n, k)) = h;
+                            *reinterpret_cast<uint4 *>(bl + t5_off(n, k)) = l;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    t5_arrive(smem_u32(&sm.full[gs & 1]));
+                };
+                // prologue: the first two steps' loads in flight together
+                if (nsteps > 0) fetch(0);
+                if (nsteps > 1) fetch_to(1, pre2);
+                if (nsteps > 0) stage(G);
+                if (nsteps > 1) {
+#pragma unroll
+                    for (int e = 0; e < 8; e++) pre[e] = pre2[e];
+                    stage(G + 1);
+                }
+                if (nsteps > 2) fetch(2);
+                for (int st = 0; st < nsteps; st++) {
+                    const int gs = G + st, bsel = gs & 1;
+                    const int sa = st % NSA, t = st / NSA;
+                    const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
+                    const bool ok = t5_wait(smem_u32(&sm.done[bsel]), (gs >> 1) & 1, abort_flag);
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    // D row of this node, this thread's pairs: columns a_local * 64 + 32 hf + 2 i + re/im
+                    const float sc = (csplit && !psplit && cf == 0) ? irs : 1.f;
+                    const bool mine = slot == j && ok;
+                    const float w0 = mine ? sc * pick<PS>(Ls, 2 * sa) : 0.f;
+                    const float w1 = (mine && 2 * sa + 1 < PS) ? sc * pick<PS>(Ls, 2 * sa + 1) : 0.f;
+                    const uint32_t dcol = my_taddr + (uint32_t)(bsel * kT5Cols);
+                    uint32_t v0[32], v1[32];
+                    t5_ld32(dcol, v0);
+                    t5_ld32(dcol + 64u, v1);
+                    t5_ld_wait();
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    t5_arrive(smem_u32(&sm.empty[bsel]));
+#pragma unroll
+                    for (int i = 0; i < NH; i++) {
+                        E[i][0] = fmaf(w0, __uint_as_float(v0[2 * i]), E[i][0]);
+                        E[i][1] = fmaf(w0, __uint_as_float(v0[2 * i + 1]), E[i][1]);
+                        E[i][0] = fmaf(w1, __uint_as_float(v1[2 * i]), E[i][0]);
+                        E[i][1] = fmaf(w1, __uint_as_float(v1[2 * i + 1]), E[i][1]);
+                    }
+                    if (st + 2 < nsteps) {  // buffer bsel's B was consumed by the MMAs just waited for
+                        stage(gs + 2);
+                        if (st + 3 < nsteps) fetch(st + 3);
+                    }
+                }
+            } else if (lane == 0) {
+                // MMA issuer
+                for (int st = 0; st < nsteps; st++) {
+                    const int gs = G + st, bsel = gs & 1, use = gs >> 1;
+                    const int sa = st % NSA;
+                    t5_wait(smem_u32(&sm.full[bsel]), use & 1, abort_flag);
+                    if (gs >= 2) t5_wait(smem_u32(&sm.empty[bsel]), (use - 1) & 1, abort_flag);
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const int ncol = (2 * sa + 1 < PS) ? 128 : 64;
+                    const uint32_t idesc = idesc_base | ((uint32_t)(ncol >> 3) << 17);
+                    const uint32_t d = tmem + (uint32_t)(bsel * kT5Cols);
+                    const uint32_t bH = smem_u32(sB + (2 * bsel) * kT5TileBytes), bL = bH + kT5TileBytes;
+                    if (!*abort_flag) {
+#pragma unroll 1
+                        for (int kk = 0; kk < 8; kk++) {
+                            const uint32_t ko = 4096u * kk;
+                            t5_mma(d, t5_desc(aH + ko), t5_desc(bH + ko), idesc, kk > 0 ? 1u : 0u);
+                            t5_mma(d, t5_desc(aH + ko), t5_desc(bL + ko), idesc, 1u);
+                            t5_mma(d, t5_desc(aL + ko), t5_desc(bH + ko), idesc, 1u);
+                        }
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                smem_u32(&sm.done[bsel]))
+                            : "memory");
+                    }
+                }
+            }
+            G += nsteps;
+            __syncwarp();
+            __syncthreads();
+            // epilogue: times the centred-factor ratio, added into the parent cone values
+            if (worker && slot >= 0) {
+                float prr = rr, pri = ri;
+                if (use_g1) {
+                    prr *= g1;
+                    pri *= g1;
+                }
+                // the pairs of a tile have distinct parent cones (one child per octant): all loads
+                // are issued before any store
+                long long o[NH];
+                float2 v[NH];
+#pragma unroll
+                for (int i = 0; i < NH; i++) {
+                    const int rcp = sm.rcp[NH * hf + i];
+                    o[i] = rcp < 0 ? -1 : (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
+                    v[i] = rcp < 0 ? make_float2(0.f, 0.f) : FP[o[i]];
+                }
+#pragma unroll
+                for (int i = 0; i < NH; i++) {
+                    if (o[i] < 0) continue;
+                    v[i].x += prr * E[i][0] - pri * E[i][1];
+                    v[i].y += prr * E[i][1] + pri * E[i][0];
+                    FP[o[i]] = v[i];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && sm.abort_) atomicAdd(ca.missed, 1ULL << 32);
+    if (warp == 8) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kT5Cols));
+    }
+}
+
+// Once per plan: for every group key (child octant, parent cone), the child cone of each of the P
+// parent nodes (FP32, the classification the propagation kernels use), the distinct cones in
+// ascending order (at most 16; nodes of further cones go last and are counted as missed when
+// propagated), and the nodes in stable order of their cone.  One warp per group.
+template <int PS>
+__global__ void __launch_bounds__(32) k_tc_order(LevelArgs C, LevelArgs Pl, ChebTab tb, TcLevel T) {
+    constexpr int P = PS * 64;
+    __shared__ int ccone[P];
+    __shared__ int cones[16];
+    const int g = blockIdx.x, lane = threadIdx.x;
+    const int gamma = T.grp_gamma[g], pb = T.grp_pb[g], cb0 = T.grp_cb[g];
+    const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+    const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+    const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+    for (int n = lane; n < P; n += 32) {
+        float nv[3], rp, rcv, t3[3];
+        ccone[n] = tc_child_cone<PS>(C, Pl, tb, gamma, n, o0, o1, o2, nv, rp, rcv, t3);
+    }
+    __syncwarp();
+    int nc = 0;
+    for (int b0 = 0; b0 < P; b0 += 32) {
+        const int c = ccone[b0 + lane];
+        unsigned todo = 0xffffffffu;
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const int cl = __shfl_sync(0xffffffffu, c, leader);
+            const unsigned same = __ballot_sync(0xffffffffu, c == cl);
+            todo &= ~same;
+            bool seen = false;
+            for (int j = 0; j < nc; j++) seen |= cones[j] == cl;
+            if (!seen && nc < 16) {
+                if (lane == 0) cones[nc] = cl;
+                nc++;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        for (int i = 1; i < nc; i++)
+            for (int j = i; j > 0 && cones[j - 1] > cones[j]; j--) {
+                const int t = cones[j];
+                cones[j] = cones[j - 1];
+                cones[j - 1] = t;
+            }
+    }
+    __syncwarp();
+    if (lane < 16) T.grp_cones[16 * g + lane] = lane < nc ? cones[lane] : -1;
+    if (lane == 0) T.grp_nc[g] = nc;
+    int cnt = 0;
+    for (int b0 = 0; b0 < P; b0 += 32) {
+        const int c = ccone[b0 + lane];
+        int sl = 0;
+        while (sl < nc && cones[sl] != c) sl++;
+        for (int j = 0; j <= nc; j++) {
+            const unsigned m = __ballot_sync(0xffffffffu, sl == j);
+            if (lane == j) cnt += __popc(m);
+        }
+    }
+    int start = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, start, o);
+        if (lane >= o) start += v;
+    }
+    start -= cnt;
+    for (int b0 = 0; b0 < P; b0 += 32) {
+        const int c = ccone[b0 + lane];
+        int sl = 0;
+        while (sl < nc && cones[sl] != c) sl++;
+        for (int j = 0; j <= nc; j++) {
+            const unsigned m = __ballot_sync(0xffffffffu, sl == j);
+            const int sj = __shfl_sync(0xffffffffu, start, j);
+            if (sl == j) T.grp_perm[(long long)g * P + sj + __popc(m & ((1u << lane) - 1u))] = (short)(b0 + lane);
+            if (lane == j) start += __popc(m);
+        }
+    }
+}
+
 
 }  // namespace
 
@@ -1963,6 +2445,38 @@ static inline ChebTab cheb_tab(const Plan &p) {
 }
 
 static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <int PS>
+ifgf_status t5_prepare(Plan &p, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_prop_t5<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
+    if (e != cudaSuccess) {
+        set_error("cudaFuncSetAttribute(k_prop_t5): %s", cudaGetErrorString(e));
+        return IFGF_ECUDA;
+    }
+    const ChebTab tb = cheb_tab(p);
+    for (int d = p.D; d >= 4; d--) {
+        const TcLevel &T = p.tc[d];
+        if (T.ngroups == 0 || !T.grp_perm) continue;
+        k_tc_order<PS><<<T.ngroups, 32, 0, s>>>(level_args(p, d, nullptr), level_args(p, d - 1, nullptr), tb, T);
+    }
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("k_tc_order: %s", cudaGetErrorString(e));
+        return IFGF_ECUDA;
+    }
+    return IFGF_OK;
+}
+
+// one-time launch attributes of this order's kernels (the tcgen05 propagation takes more than
+// 48 KB of dynamic shared memory)
+template <int PS, int PA>
+ifgf_status prepare_t(Plan &p, cudaStream_t s) {
+    if constexpr (PA == 8) return t5_prepare<PS>(p, s);
+    (void)p;
+    (void)s;
+    return IFGF_OK;
+}
 
 template <int PS, int PA>
 ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s) {
@@ -2014,14 +2528,21 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         }
         for (int d = D; d >= 4; d--)
             if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].fill >= p.tc_min_fill) {
-                const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
-                CK(cudaMemsetAsync(L[d - 1].F, 0, bytes, s));
-                const TcLevel &T = p.tc[d];
-                for (int o = 0; o < 8; o++) {
-                    const int t0 = T.oct_tile_start[o], nt = T.oct_tile_start[o + 1] - t0;
-                    if (nt > 0) k_prop_tc<PS><<<dim3(nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
+                if constexpr (PA == 8) {
+                    const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
+                    CK(cudaMemsetAsync(L[d - 1].F, 0, bytes, s));
+                    const TcLevel &T = p.tc[d];
+                    for (int o = 0; o < 8; o++) {
+                        const int t0 = T.oct_tile_start[o], nt = T.oct_tile_start[o + 1] - t0;
+                        if (nt <= 0) continue;
+                        if (p.tc_engine == 1)
+                            k_prop_t5<PS><<<dim3(nt, (P + kT5Rows - 1) / kT5Rows), kT5Threads, kT5Smem, s>>>(
+                                ca, L[d], L[d - 1], tb, T, t0);
+                        else
+                            k_prop_tc<PS><<<dim3(nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
+                    }
+                    prof_mark(p, s, kStProp, d - 1);
                 }
-                prof_mark(p, s, kStProp, d - 1);
             } else if (L[d - 1].nrc) {
                 const long long nth = L[d - 1].nrc * ((P + 1) / 2);
                 if (nrhs == 1 || p.rhs_block == 1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);

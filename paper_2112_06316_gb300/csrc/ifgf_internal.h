@@ -61,6 +61,10 @@ struct TcLevel {
     int *tile_group = nullptr, *tile_start = nullptr, *tile_count = nullptr;
     int *grp_gamma = nullptr, *grp_pb = nullptr, *grp_cb = nullptr;
     int *pair_rcp = nullptr, *pair_cb = nullptr;
+    // per group, filled once per plan on the device: the P parent nodes ordered by the child
+    // cone they fall in (ascending cone id, then node), and the distinct child cones (<= 16)
+    short *grp_perm = nullptr;
+    int *grp_cones = nullptr, *grp_nc = nullptr;
 };
 
 // Device arrays of one level.
@@ -117,6 +121,8 @@ struct Plan {
     bool use_tc = false;
     // a level uses the tensor-core propagation when its tile fill reaches this value
     double tc_min_fill = 0.6;
+    // tensor-core propagation engine: 1 = tcgen05 (TMEM accumulators), 0 = warp-level mma.sync
+    int tc_engine = 1;
     std::vector<void *> allocs;
     int64_t device_bytes = 0;
 

@@ -2,6 +2,7 @@
 #include "fwd_kernels.cuh"
 
 namespace ifgf {
+template ifgf_status prepare_t<3, 5>(Plan &, cudaStream_t);
 template ifgf_status run_apply_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t);
 template ifgf_status run_adjoint_t<3, 5>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *,
                                               void **);

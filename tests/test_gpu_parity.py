@@ -184,12 +184,14 @@ def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
     assert rel(y32, y64) < 1e-5
 
 
+@pytest.mark.parametrize("engine", [1, 0])
 @pytest.mark.parametrize("fm", [0, 1, 2])
 @pytest.mark.parametrize("ps", [5, 6])
-def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm):
-    """Orders with Pang = 8 propagate through the tensor-core (mma.sync TF32, three-term split)
-    contraction on the mixed path, forced on at every level (fill threshold 0); two
-    propagation levels (D = 5) in every factor-mode combination (split -> split,
+def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm, engine):
+    """Orders with Pang = 8 propagate through the tensor cores on the mixed path (engine 1:
+    tcgen05 with TMEM accumulators over the K = 8 contraction; engine 0: warp mma.sync over
+    K = P; both with a three-term TF32 split), forced on at every level (fill threshold 0);
+    two propagation levels (D = 5) in every factor-mode combination (split -> split,
     split -> combined, combined -> combined), two right-hand sides.  The result matches the
     oracle to the mixed bar and the CUDA-core propagation (threshold > 1) to 2e-6."""
     s, k = sphere_workload(64, 8, 6.0)
@@ -198,6 +200,7 @@ def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm):
                              oracle_lib.IFGFParams(k=k, identity_coef=0.5, levels=5, Ps=ps, Pang=8,
                                                    factor_mode=fm), sig)
     plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, levels=5, Ps=ps, Pang=8, factor_mode=fm))
+    plan.set_tc_engine(engine)
     plan.set_tc_fill(0.0)
     y_tc = gpu_apply(plan, sig, np.complex64)
     assert plan.missed_lookups() == 0
