@@ -1933,12 +1933,15 @@ __global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, 
 // index a):
 //     D[node, (a, pair, re/im)] = sum_{b,c} Lt[node][b] Lp[node][c] F_pair[a, b, c]
 // with A[node][(b, c)] = Lt[b] Lp[c] the same for every pair, radial index and
-// child cone, and the radial factor Ls[node][a] applied when D is read back.
+// child cone (kept in tensor memory as TF32 hi / lo), and the radial factor
+// Ls[node][a] applied when D is read back.
 // A block owns 128 parent nodes (TMEM lanes) in the plan's child-cone order and
 // one tile of up to 32 pairs.  Each step (child cone, factor, two radial indices)
 // stages B (2 a x 32 pairs x re/im = 128 columns, K = 64) in shared memory as
 // TF32 hi / lo and runs 8 k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of
-// tcgen05.mma 128 x 128 x 8 into one of two 128-column TMEM buffers.
+// tcgen05.mma 128 x 128 x 8 (A from tensor memory, B from shared memory) into
+// one of two 128-column TMEM buffers.  TMEM columns: D0 0-127, D1 128-255,
+// A hi 256-319, A lo 320-383.
 // Warp-specialised: warps 0-7 stage operands and read D back (two threads per
 // node, one per half of the pairs), warp 8 only issues MMAs.  Per buffer, three
 // mbarriers hand the work over: full (B staged), done (MMAs complete, via
@@ -1951,7 +1954,8 @@ constexpr int kT5Cols = 128;     // TMEM columns of one step's D (two buffers)
 constexpr int kT5Work = 256;     // staging / readback threads (warps 0-7)
 constexpr int kT5Threads = kT5Work + 32;  // + the MMA-issuing warp
 constexpr int kT5K = 64;         // contraction length (b, c)
-constexpr int kT5TileBytes = kT5Rows * kT5K * 4;  // one 128 x 64 TF32 operand tile (A, or B of one step)
+constexpr int kT5TileBytes = kT5Rows * kT5K * 4;  // one 128 x 64 TF32 operand tile (B of one step)
+constexpr uint32_t kT5ColA = 256;  // TMEM column of A hi (A lo at + 64)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -1968,11 +1972,23 @@ __device__ __forceinline__ uint64_t t5_desc(uint32_t addr) {
            ((uint64_t)1 << 46);
 }
 
-__device__ __forceinline__ void t5_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+// D (TMEM) += A (TMEM, lane = row, 8 consecutive columns) x B (shared memory descriptor)
+__device__ __forceinline__ void t5_mma(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void t5_st32(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
         : "memory");
 }
 
@@ -2009,6 +2025,11 @@ __device__ __forceinline__ void t5_ld32(uint32_t taddr, uint32_t *r) {
 
 __device__ __forceinline__ void t5_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
+// TMEM address of lane 32 * quadrant, column 0 (a warp reaches the lanes of quadrant warp % 4)
+__device__ __forceinline__ uint32_t tmem_row_base(uint32_t tmem, int quadrant) {
+    return tmem + ((uint32_t)(32 * quadrant) << 16);
+}
+
 struct T5Misc {
     short perm[kT5Rows];
     int cones[16];
@@ -2023,8 +2044,8 @@ struct T5Misc {
     int abort_;
 };
 
-// dynamic shared memory: A hi, A lo, B[stage][hi / lo], misc
-constexpr size_t kT5Smem = 6 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
+// dynamic shared memory: B[stage][hi / lo], misc
+constexpr size_t kT5Smem = 4 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
 
 template <int PS>
 __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
@@ -2032,9 +2053,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     constexpr int P = PS * 64, NT5 = kTcPairs, NH = kTcPairs / 2, NSA = (PS + 1) / 2;
     extern __shared__ unsigned char t5_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)t5_dyn + 1023) & ~(uintptr_t)1023);
-    unsigned char *const sAh = base, *const sAl = base + kT5TileBytes;
-    unsigned char *sB = base + 2 * kT5TileBytes;  // buffer b: sB + (2 * b + hl) * kT5TileBytes
-    T5Misc &sm = *reinterpret_cast<T5Misc *>(base + 6 * kT5TileBytes);
+    unsigned char *sB = base;  // buffer b: sB + (2 * b + hl) * kT5TileBytes
+    T5Misc &sm = *reinterpret_cast<T5Misc *>(base + 4 * kT5TileBytes);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool worker = warp < 8;
     const int qd = warp & 3, hf = (warp >> 2) & 1;  // TMEM lane quadrant, half of the pairs
@@ -2059,7 +2079,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     }
     if (warp == 8) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
-                     "r"(2 * kT5Cols));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
@@ -2108,26 +2128,23 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             lagrange<8, float>(t3[1], tb.fxa, tb.fca, Lt);
             lagrange<8, float>(t3[2], tb.fxa, tb.fca, Lp);
         }
-        // A[row][(b, c)] = Lt[b] Lp[c]; this thread writes b in [4 hf, 4 hf + 4)
-        auto write_a = [&](int b, float lt) {
+        // A[row][(b, c)] = Lt[b] Lp[c] into TMEM lane `row`: this thread writes b in [4 hf, 4 hf + 4)
+        uint32_t ah[32], al[32];
+        auto fill_a = [&](int b, float lt) {
 #pragma unroll
-            for (int kh = 0; kh < 2; kh++) {
-                uint4 h, l;
-                split_tf32(lt * Lp[4 * kh + 0], h.x, l.x);
-                split_tf32(lt * Lp[4 * kh + 1], h.y, l.y);
-                split_tf32(lt * Lp[4 * kh + 2], h.z, l.z);
-                split_tf32(lt * Lp[4 * kh + 3], h.w, l.w);
-                *reinterpret_cast<uint4 *>(sAh + t5_off(row, 8 * b + 4 * kh)) = h;
-                *reinterpret_cast<uint4 *>(sAl + t5_off(row, 8 * b + 4 * kh)) = l;
-            }
+            for (int c = 0; c < 8; c++) split_tf32(lt * Lp[c], ah[8 * (b & 3) + c], al[8 * (b & 3) + c]);
         };
         if (hf == 0) {
 #pragma unroll
-            for (int bb = 0; bb < 4; bb++) write_a(bb, Lt[bb]);
+            for (int bb = 0; bb < 4; bb++) fill_a(bb, Lt[bb]);
         } else {
 #pragma unroll
-            for (int bb = 4; bb < 8; bb++) write_a(bb, Lt[bb]);
+            for (int bb = 4; bb < 8; bb++) fill_a(bb, Lt[bb]);
         }
+        const uint32_t lane_base = tmem_row_base(sm.tmem, qd);
+        t5_st32(lane_base + kT5ColA + 32u * hf, ah);
+        t5_st32(lane_base + kT5ColA + 64u + 32u * hf, al);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     }
     for (int idx = tid; idx < nc * NT5; idx += blockDim.x) {
         const int j = idx / NT5, q = idx % NT5;
@@ -2139,7 +2156,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
         }
         sm.crc[j][q] = crc;
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // A, for the MMAs
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");  // A in TMEM, for the MMAs
     __syncthreads();
     if (tid == 0) {
         int m = 0;
@@ -2159,7 +2176,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     const int s_al = (tid >> 7) & 1, s_pair = (tid >> 2) & 31, s_qn = tid & 3;
     const int first_ri = (lane >> 4) & 1;
     const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
-    const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl);
+    const uint32_t aH = tmem + kT5ColA, aL = tmem + kT5ColA + 64u;
     const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 32u * hf;
     int G = 0;  // global step index: buffer G & 1, use G >> 1 (phase parity (G >> 1) & 1)
     for (int q = 0; q < ca.nrhs; q++) {
@@ -2268,10 +2285,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                     if (!*abort_flag) {
 #pragma unroll 1
                         for (int kk = 0; kk < 8; kk++) {
-                            const uint32_t ko = 4096u * kk;
-                            t5_mma(d, t5_desc(aH + ko), t5_desc(bH + ko), idesc, kk > 0 ? 1u : 0u);
-                            t5_mma(d, t5_desc(aH + ko), t5_desc(bL + ko), idesc, 1u);
-                            t5_mma(d, t5_desc(aL + ko), t5_desc(bH + ko), idesc, 1u);
+                            const uint32_t ko = 4096u * kk, ka = 8u * kk;
+                            t5_mma(d, aH + ka, t5_desc(bH + ko), idesc, kk > 0 ? 1u : 0u);
+                            t5_mma(d, aH + ka, t5_desc(bL + ko), idesc, 1u);
+                            t5_mma(d, aL + ka, t5_desc(bH + ko), idesc, 1u);
                         }
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -2315,7 +2332,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     if (tid == 0 && sm.abort_) atomicAdd(ca.missed, 1ULL << 32);
     if (warp == 8) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * kT5Cols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
     }
 }
 
