@@ -249,16 +249,16 @@ ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block);
 
 /* Tunable: the mixed propagation from a level uses the tensor-core contraction
  * (orders with Pang = 8) when the fraction of filled pair slots in its tiles is at
- * least min_fill (default 0.6; 0 = always, > 1 = never), else the CUDA-core kernel.
+ * least min_fill (default 0.4; 0 = always, > 1 = never), else the CUDA-core kernel.
  * Errors: IFGF_EINVAL. */
 ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill);
 
 /* Tunable: engine of the tensor-core propagation.  1 (default) = 5th-generation
- * tensor cores: the last angular contraction of the tensor-product Chebyshev
- * interpolant (Eq. ChebyPoly; K = 8) runs as tcgen05.mma with TF32 hi/lo operands
- * in shared memory and FP32 accumulators in tensor memory, the other two
- * contractions in registers; 0 = warp-level mma.sync over the full K = P
- * contraction.  Both keep FP32-level accuracy (three-term TF32 split).
+ * tensor cores: the two angular contractions of the tensor-product Chebyshev
+ * interpolant (Eq. ChebyPoly; K = 64) run as tcgen05.mma with TF32 hi/lo operands
+ * (A in tensor memory, B in shared memory) and FP32 accumulators in tensor
+ * memory, the radial one in registers; 0 = warp-level mma.sync over the full
+ * K = P contraction.  Both keep FP32-level accuracy (three-term TF32 split).
  * Errors: IFGF_EINVAL for any other value. */
 ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine);
 

@@ -161,10 +161,10 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
                 gg.push_back((int)(pairs[i].first % Pl.ncone));
                 gpb.push_back(Pl.rc_box[pairs[i].second.first]);
                 gcb.push_back(pairs[i].second.second);
-                for (size_t t = i; t < j; t += kTcPairs) {
+                for (size_t t = i; t < j; t += kTcTile) {
                     tg.push_back(g);
                     ts.push_back((int)(prc.size() + (t - i)));
-                    tcnt.push_back((int)std::min<size_t>(kTcPairs, j - t));
+                    tcnt.push_back((int)std::min<size_t>(kTcTile, j - t));
                 }
                 for (size_t t = i; t < j; t++) {
                     prc.push_back(pairs[t].second.first);
@@ -175,7 +175,7 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
             while (cur_oct < 8) T.oct_tile_start[++cur_oct] = (int)tg.size();
             T.ntiles = (int)tg.size();
             T.ngroups = (int)gg.size();
-            T.fill = T.ntiles ? (double)prc.size() / ((double)T.ntiles * kTcPairs) : 0.0;
+            T.fill = T.ntiles ? (double)prc.size() / ((double)T.ntiles * kTcTile) : 0.0;
             UP(T.tile_group, tg);
             UP(T.tile_start, ts);
             UP(T.tile_count, tcnt);

@@ -1670,9 +1670,11 @@ __global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, 
     static_assert(P <= 2 * 64 * 68, "child cone table must fit in the staging buffer");
     int *ccone = reinterpret_cast<int *>(&sm.bt[0][0][0]);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, tig = lane & 3;
-    const int tile = tile0 + blockIdx.x;
+    const int tile = tile0 + (blockIdx.x >> 1), half = blockIdx.x & 1;  // a tile is two blocks of 32 pairs
     const int row0 = blockIdx.y * kTcRows;  // first sorted row of this block
-    const int grp = T.tile_group[tile], p0 = T.tile_start[tile], np = T.tile_count[tile];
+    const int grp = T.tile_group[tile], p0 = T.tile_start[tile] + kTcPairs * half;
+    const int np = min(kTcPairs, T.tile_count[tile] - kTcPairs * half);
+    if (np <= 0) return;  // block-uniform, before any barrier
     const int gamma = T.grp_gamma[grp], pb = T.grp_pb[grp], cb0 = T.grp_cb[grp];
     if (tid < kTcPairs) {
         sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
@@ -1936,8 +1938,8 @@ __global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, 
 // child cone (kept in tensor memory as TF32 hi / lo), and the radial factor
 // Ls[node][a] applied when D is read back.
 // A block owns 128 parent nodes (TMEM lanes) in the plan's child-cone order and
-// one tile of up to 32 pairs.  Each step (child cone, factor, two radial indices)
-// stages B (2 a x 32 pairs x re/im = 128 columns, K = 64) in shared memory as
+// one tile of up to 64 pairs.  Each step (child cone, factor, radial index a)
+// stages B (64 pairs x re/im = 128 columns, K = 64) in shared memory as
 // TF32 hi / lo and runs 8 k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of
 // tcgen05.mma 128 x 128 x 8 (A from tensor memory, B from shared memory) into
 // one of two 128-column TMEM buffers.  TMEM columns: D0 0-127, D1 128-255,
@@ -2037,8 +2039,8 @@ struct T5Misc {
     int present[16];
     int jlist[16];
     int njp;
-    int crc[16][kTcPairs];
-    int rcp[kTcPairs], cb[kTcPairs];
+    int crc[16][kTcTile];
+    int rcp[kTcTile], cb[kTcTile];
     unsigned long long full[2], done[2], empty[2];
     uint32_t tmem;
     int abort_;
@@ -2050,7 +2052,7 @@ constexpr size_t kT5Smem = 4 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
 template <int PS>
 __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
                                                            TcLevel T, int tile0) {
-    constexpr int P = PS * 64, NT5 = kTcPairs, NH = kTcPairs / 2, NSA = (PS + 1) / 2;
+    constexpr int P = PS * 64, NT5 = kTcTile, NH = kTcTile / 2;
     extern __shared__ unsigned char t5_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)t5_dyn + 1023) & ~(uintptr_t)1023);
     unsigned char *sB = base;  // buffer b: sB + (2 * b + hl) * kT5TileBytes
@@ -2171,13 +2173,13 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     float2 *FP = (float2 *)Pl.F;
     const int njp = sm.njp;
     volatile int *abort_flag = &sm.abort_;
-    // staging item: a_local = tid >> 7, pair = (tid >> 2) & 31, nodes [16 qn, 16 qn + 16) of that a with
-    // qn = tid & 3; lanes 16-31 store the im row first so a warp's 16-byte stores cover all 8 bank groups
-    const int s_al = (tid >> 7) & 1, s_pair = (tid >> 2) & 31, s_qn = tid & 3;
+    // staging item: pair = tid >> 2, nodes [16 qn, 16 qn + 16) of the step's radial index with qn = tid & 3;
+    // lanes 16-31 store the im row first so a warp's 16-byte stores cover all 8 bank groups
+    const int s_pair = (tid >> 2) & 63, s_qn = tid & 3;
     const int first_ri = (lane >> 4) & 1;
     const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
     const uint32_t aH = tmem + kT5ColA, aL = tmem + kT5ColA + 64u;
-    const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 32u * hf;
+    const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 64u * hf;  // pairs 32 hf .. 32 hf + 31
     int G = 0;  // global step index: buffer G & 1, use G >> 1 (phase parity (G >> 1) & 1)
     for (int q = 0; q < ca.nrhs; q++) {
         for (int pass = 0; pass < npass; pass++) {
@@ -2185,17 +2187,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             const int fp = (csplit && psplit) ? pass : 0;
             const bool use_g1 = csplit && psplit && pass == 0;
             const int ncf = cf_hi - cf_lo + 1;
-            const int nsteps = njp * ncf * NSA;  // (cone slot, factor, pair of radial indices)
+            const int nsteps = njp * ncf * PS;  // (cone slot, factor, radial index)
             float E[NH][2];
 #pragma unroll
             for (int pr = 0; pr < NH; pr++) E[pr][0] = E[pr][1] = 0.f;
             if (worker) {
                 float4 pre[8], pre2[8];
                 auto fetch_to = [&](int st, float4 *dst) {
-                    const int sa = st % NSA, t = st / NSA;
+                    const int a = st % PS, t = st / PS;
                     const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
-                    const int a = 2 * sa + s_al;
-                    const int crc = (a < PS) ? sm.crc[j][s_pair] : -1;
+                    const int crc = sm.crc[j][s_pair];
 #pragma unroll
                     for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (crc >= 0) {
@@ -2208,7 +2209,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 auto fetch = [&](int st) { fetch_to(st, pre); };
                 auto stage = [&](int gs) {  // into buffer gs & 1, then signal full
                     unsigned char *bh = sB + (2 * (gs & 1)) * kT5TileBytes, *bl = bh + kT5TileBytes;
-                    const int nre = (s_al * 32 + s_pair) * 2;
+                    const int nre = s_pair * 2;
 #pragma unroll
                     for (int o = 0; o < 2; o++) {
                         const bool im = (o ^ first_ri) != 0;
@@ -2242,28 +2243,26 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 if (nsteps > 2) fetch(2);
                 for (int st = 0; st < nsteps; st++) {
                     const int gs = G + st, bsel = gs & 1;
-                    const int sa = st % NSA, t = st / NSA;
+                    const int a = st % PS, t = st / PS;
                     const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
                     const bool ok = t5_wait(smem_u32(&sm.done[bsel]), (gs >> 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    // D row of this node, this thread's pairs: columns a_local * 64 + 32 hf + 2 i + re/im
+                    // D row of this node, this thread's pairs 32 hf .. 32 hf + 31: columns 64 hf + 2 i + re/im
                     const float sc = (csplit && !psplit && cf == 0) ? irs : 1.f;
-                    const bool mine = slot == j && ok;
-                    const float w0 = mine ? sc * pick<PS>(Ls, 2 * sa) : 0.f;
-                    const float w1 = (mine && 2 * sa + 1 < PS) ? sc * pick<PS>(Ls, 2 * sa + 1) : 0.f;
+                    const float w = (slot == j && ok) ? sc * pick<PS>(Ls, a) : 0.f;
                     const uint32_t dcol = my_taddr + (uint32_t)(bsel * kT5Cols);
                     uint32_t v0[32], v1[32];
                     t5_ld32(dcol, v0);
-                    t5_ld32(dcol + 64u, v1);
+                    t5_ld32(dcol + 32u, v1);
                     t5_ld_wait();
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                     t5_arrive(smem_u32(&sm.empty[bsel]));
 #pragma unroll
-                    for (int i = 0; i < NH; i++) {
-                        E[i][0] = fmaf(w0, __uint_as_float(v0[2 * i]), E[i][0]);
-                        E[i][1] = fmaf(w0, __uint_as_float(v0[2 * i + 1]), E[i][1]);
-                        E[i][0] = fmaf(w1, __uint_as_float(v1[2 * i]), E[i][0]);
-                        E[i][1] = fmaf(w1, __uint_as_float(v1[2 * i + 1]), E[i][1]);
+                    for (int i = 0; i < 16; i++) {
+                        E[i][0] = fmaf(w, __uint_as_float(v0[2 * i]), E[i][0]);
+                        E[i][1] = fmaf(w, __uint_as_float(v0[2 * i + 1]), E[i][1]);
+                        E[16 + i][0] = fmaf(w, __uint_as_float(v1[2 * i]), E[16 + i][0]);
+                        E[16 + i][1] = fmaf(w, __uint_as_float(v1[2 * i + 1]), E[16 + i][1]);
                     }
                     if (st + 2 < nsteps) {  // buffer bsel's B was consumed by the MMAs just waited for
                         stage(gs + 2);
@@ -2274,12 +2273,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 // MMA issuer
                 for (int st = 0; st < nsteps; st++) {
                     const int gs = G + st, bsel = gs & 1, use = gs >> 1;
-                    const int sa = st % NSA;
                     t5_wait(smem_u32(&sm.full[bsel]), use & 1, abort_flag);
                     if (gs >= 2) t5_wait(smem_u32(&sm.empty[bsel]), (use - 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const int ncol = (2 * sa + 1 < PS) ? 128 : 64;
-                    const uint32_t idesc = idesc_base | ((uint32_t)(ncol >> 3) << 17);
+                    const uint32_t idesc = idesc_base | ((uint32_t)(kT5Cols >> 3) << 17);
                     const uint32_t d = tmem + (uint32_t)(bsel * kT5Cols);
                     const uint32_t bH = smem_u32(sB + (2 * bsel) * kT5TileBytes), bL = bH + kT5TileBytes;
                     if (!*abort_flag) {
@@ -2307,22 +2304,25 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                     prr *= g1;
                     pri *= g1;
                 }
-                // the pairs of a tile have distinct parent cones (one child per octant): all loads
-                // are issued before any store
-                long long o[NH];
-                float2 v[NH];
+                // the pairs of a tile have distinct parent cones (one child per octant): loads are
+                // issued in batches of 16 before their stores
 #pragma unroll
-                for (int i = 0; i < NH; i++) {
-                    const int rcp = sm.rcp[NH * hf + i];
-                    o[i] = rcp < 0 ? -1 : (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
-                    v[i] = rcp < 0 ? make_float2(0.f, 0.f) : FP[o[i]];
-                }
+                for (int i0 = 0; i0 < NH; i0 += 16) {
+                    long long o[16];
+                    float2 v[16];
 #pragma unroll
-                for (int i = 0; i < NH; i++) {
-                    if (o[i] < 0) continue;
-                    v[i].x += prr * E[i][0] - pri * E[i][1];
-                    v[i].y += prr * E[i][1] + pri * E[i][0];
-                    FP[o[i]] = v[i];
+                    for (int i = 0; i < 16; i++) {
+                        const int rcp = sm.rcp[NH * hf + i0 + i];
+                        o[i] = rcp < 0 ? -1 : (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
+                        v[i] = rcp < 0 ? make_float2(0.f, 0.f) : FP[o[i]];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        if (o[i] < 0) continue;
+                        v[i].x += prr * E[i0 + i][0] - pri * E[i0 + i][1];
+                        v[i].y += prr * E[i0 + i][1] + pri * E[i0 + i][0];
+                        FP[o[i]] = v[i];
+                    }
                 }
             }
         }
@@ -2556,7 +2556,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                             k_prop_t5<PS><<<dim3(nt, (P + kT5Rows - 1) / kT5Rows), kT5Threads, kT5Smem, s>>>(
                                 ca, L[d], L[d - 1], tb, T, t0);
                         else
-                            k_prop_tc<PS><<<dim3(nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
+                            k_prop_tc<PS><<<dim3(2 * nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
                     }
                     prof_mark(p, s, kStProp, d - 1);
                 }

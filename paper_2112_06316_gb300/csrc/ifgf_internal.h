@@ -51,12 +51,13 @@ struct HostLevel {
 // Tensor-core propagation into level d-1 (mixed path, Pang = 8): pairs (parent
 // relevant cone, child box) grouped by (child octant, parent cone id) — the
 // propagation weights depend only on that key — and cut into tiles of up to
-// kTcPairs pairs; tiles are ordered by octant so one launch per octant never
+// kTcTile pairs; tiles are ordered by octant so one launch per octant never
 // writes the same parent cone twice.
-constexpr int kTcPairs = 32;
+constexpr int kTcTile = 64;   // pairs per tile
+constexpr int kTcPairs = 32;  // pairs per block of the warp-level (mma.sync) engine: a tile is two blocks
 struct TcLevel {
     int ntiles = 0, ngroups = 0;
-    double fill = 0.0;  // pairs / (tiles * kTcPairs)
+    double fill = 0.0;  // pairs / (tiles * kTcTile)
     int oct_tile_start[9] = {};
     int *tile_group = nullptr, *tile_start = nullptr, *tile_count = nullptr;
     int *grp_gamma = nullptr, *grp_pb = nullptr, *grp_cb = nullptr;
@@ -120,7 +121,7 @@ struct Plan {
     TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
     bool use_tc = false;
     // a level uses the tensor-core propagation when its tile fill reaches this value
-    double tc_min_fill = 0.6;
+    double tc_min_fill = 0.4;
     // tensor-core propagation engine: 1 = tcgen05 (TMEM accumulators), 0 = warp-level mma.sync
     int tc_engine = 1;
     std::vector<void *> allocs;

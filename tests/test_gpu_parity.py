@@ -189,8 +189,9 @@ def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
 @pytest.mark.parametrize("ps", [5, 6])
 def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm, engine):
     """Orders with Pang = 8 propagate through the tensor cores on the mixed path (engine 1:
-    tcgen05 with TMEM accumulators over the K = 8 contraction; engine 0: warp mma.sync over
-    K = P; both with a three-term TF32 split), forced on at every level (fill threshold 0);
+    tcgen05 with TMEM accumulators over the K = 64 angular contraction; engine 0: warp
+    mma.sync over K = P; both with a three-term TF32 split), forced on at every level (fill
+    threshold 0);
     two propagation levels (D = 5) in every factor-mode combination (split -> split,
     split -> combined, combined -> combined), two right-hand sides.  The result matches the
     oracle to the mixed bar and the CUDA-core propagation (threshold > 1) to 2e-6."""
