@@ -267,7 +267,9 @@ ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 
 /* Number of failed relevant-cone lookups recorded by applies since the last call
  * (should be 0; a non-zero count means a point fell outside the relevant set and
- * its contribution was skipped).  Synchronises `stream` and resets the counter. */
+ * its contribution was skipped).  A tensor-core propagation block whose bounded
+ * wait for its MMAs timed out adds 2^32 (its results are invalid).  Synchronises
+ * `stream` and resets the counter. */
 ifgf_status ifgf_plan_check(ifgf_plan *plan, void *stream, int64_t *missed_lookups);
 
 /* Enable (1) or disable (0) per-launch timing: each later apply records a CUDA
@@ -276,7 +278,8 @@ ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable);
 
 /* Per-launch device times of the last apply with profiling on: fills up to `cap`
  * entries of kind (0 gather, 1 leaf evaluation, 2 propagation, 3 near field,
- * 4 cousin interpolation, 5 scatter, 6 correction), level (octree level or 0) and
+ * 4 cousin interpolation, 5 scatter, 6 correction, 7 propagation on the tensor
+ * cores: one entry per level, all its octant launches), level (octree level or 0) and
  * ms (milliseconds); any output pointer may be NULL.  Waits for the last event.
  * Returns the number of entries (0 if profiling is off), or a negative ifgf_status. */
 int ifgf_plan_stage_times(ifgf_plan *plan, int cap, int *kind, int *level, double *ms);

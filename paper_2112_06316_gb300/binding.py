@@ -87,7 +87,7 @@ _SIGS = [
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("ifgf_group_destroy", None, [_VP]),
 ]
-STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction"]
+STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc"]
 
 _lib = None
 

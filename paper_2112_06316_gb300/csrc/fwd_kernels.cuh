@@ -2173,10 +2173,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     float2 *FP = (float2 *)Pl.F;
     const int njp = sm.njp;
     volatile int *abort_flag = &sm.abort_;
-    // staging item: pair = tid >> 2, nodes [16 qn, 16 qn + 16) of the step's radial index with qn = tid & 3;
-    // lanes 16-31 store the im row first so a warp's 16-byte stores cover all 8 bank groups
-    const int s_pair = (tid >> 2) & 63, s_qn = tid & 3;
-    const int first_ri = (lane >> 4) & 1;
+    // staging item: pair = 8 warp + (lane & 7), nodes [16 qn, 16 qn + 16) of the step's radial index with
+    // qn = lane >> 3.  16-byte shared stores are serviced 8 lanes at a time: lanes 0-3 and 4-7 of each
+    // group of 8 store the re / im rows in opposite order, so the 8 lanes cover all 8 bank groups
+    const int s_pair = 8 * (warp & 7) + (lane & 7), s_qn = lane >> 3;
+    const int first_ri = (lane >> 2) & 1;
     const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
     const uint32_t aH = tmem + kT5ColA, aL = tmem + kT5ColA + 64u;
     const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 64u * hf;  // pairs 32 hf .. 32 hf + 31
@@ -2558,7 +2559,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                         else
                             k_prop_tc<PS><<<dim3(2 * nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
                     }
-                    prof_mark(p, s, kStProp, d - 1);
+                    prof_mark(p, s, kStPropTc, d - 1);
                 }
             } else if (L[d - 1].nrc) {
                 const long long nth = L[d - 1].nrc * ((P + 1) / 2);

@@ -162,7 +162,10 @@ struct Plan {
 };
 
 // stage kinds reported by ifgf_plan_stage_times
-enum StageKind { kStGather = 0, kStLeaf = 1, kStProp = 2, kStNear = 3, kStCousin = 4, kStScatter = 5, kStCorr = 6 };
+enum StageKind {
+    kStGather = 0, kStLeaf = 1, kStProp = 2, kStNear = 3, kStCousin = 4, kStScatter = 5, kStCorr = 6,
+    kStPropTc = 7  // propagation on the tensor cores
+};
 
 inline void prof_begin(Plan &p, cudaStream_t s) {
     p.nev = 0;
