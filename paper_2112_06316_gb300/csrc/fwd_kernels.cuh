@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
                                               ChebTab tb, const void *gs_, const void *Gp_, void *Gc_) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
-    constexpr int P = PS * PA * PA, NROW = PS * PA;
+    constexpr int P = PS * PA * PA, PA2 = PA * PA;
     const C *gs = (const C *)gs_;
     const C *Gp = (const C *)Gp_;
     C *Gc = (C *)Gc_;
@@ -897,14 +897,15 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
     const long long e0 = ad_start[rc], e1 = ad_start[rc + 1];
     const int nfac = L.nfac;
     const bool csplit = L.split != 0, psplit = has_parent && Pl.split != 0;
+    // accumulation: thread = (factor, b, c) of the output cone, all PS radial nodes (a, b, c)
     const int unit = threadIdx.x;
-    const bool active = unit < nfac * NROW;
-    const int fac = active ? unit / NROW : 0, row = active ? unit % NROW : 0;
-    const int ua = row / PA, ub = row % PA;
+    const bool active = unit < nfac * PA2;
+    const int fac = active ? unit / PA2 : 0, bc = active ? unit % PA2 : 0;
+    const int ub = bc / PA, uc = bc % PA;
     for (int q = 0; q < ca.nrhs; q++) {
-        C acc[PA];
+        C acc[PS];
 #pragma unroll
-        for (int c = 0; c < PA; c++) acc[c].x = acc[c].y = T(0);
+        for (int a = 0; a < PS; a++) acc[a].x = acc[a].y = T(0);
         for (long long base = e0; base < e1; base += 128) {
             const long long e = base + threadIdx.x;
             AntEntry<T, PS, PA> &me = ent[threadIdx.x];
@@ -1062,22 +1063,22 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
                 const int cnt = (int)min((long long)128, e1 - base);
                 for (int t = 0; t < cnt; t++) {
                     const AntEntry<T, PS, PA> &en = ent[t];
-                    const T w = en.Ls[ua] * en.Lt[ub];
+                    const T w = en.Lt[ub] * en.Lp[uc];
                     const C v = en.v[fac];
+                    const T zr = w * v.x, zi = w * v.y;
 #pragma unroll
-                    for (int c = 0; c < PA; c++) {
-                        const T wl = w * en.Lp[c];
-                        acc[c].x = fma(wl, v.x, acc[c].x);
-                        acc[c].y = fma(wl, v.y, acc[c].y);
+                    for (int a = 0; a < PS; a++) {
+                        acc[a].x = fma(en.Ls[a], zr, acc[a].x);
+                        acc[a].y = fma(en.Ls[a], zi, acc[a].y);
                     }
                 }
             }
             __syncthreads();
         }
         if (active) {
-            C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + row * PA;
+            C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + bc;
 #pragma unroll
-            for (int c = 0; c < PA; c++) out[c] = acc[c];
+            for (int a = 0; a < PS; a++) out[a * PA2] = acc[a];
         }
     }
 }
