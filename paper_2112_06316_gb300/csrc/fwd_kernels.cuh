@@ -1161,6 +1161,80 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
     }
 }
 
+// Transposed leaf evaluation (mixed), warp-cooperative: one warp per chunk of at
+// most 32 sources of one leaf box (the level-D cousin chunks).  For 32 nodes of a
+// relevant cone at a time each lane computes one node's direction and loads its
+// cone values once; the warp then walks the 32 nodes with shuffles, every lane
+// evaluating conj(W(x_node, y_j)) G for its source.
+template <int PS, int PA, bool SPLIT>
+__global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, const int4 *__restrict__ chunks,
+                                                    int nchunk, ChebTab tb, const float2 *__restrict__ G,
+                                                    float2 *__restrict__ bo) {
+    constexpr int P = PS * PA * PA;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (ch >= nchunk) return;  // warp-uniform
+    const int4 cw = chunks[ch];
+    const int b = cw.x;
+    const bool act = lane < cw.z;
+    const int j = cw.y + (act ? lane : 0);
+    const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
+    const float hu = L.hu, kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, hd = ca.HDf;
+    const float yy = fj.x * fj.x + fj.y * fj.y + fj.z * fj.z;
+    const int r0 = L.rc_start[b], r1 = L.rc_start[b + 1];
+    for (int q = 0; q < ca.nrhs; q++) {
+        CAcc acc;
+        acc.zero();
+        for (int rc = r0; rc < r1; rc++) {
+            const int cone = L.rc_cone[rc];
+            const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
+            for (int n0 = 0; n0 < P; n0 += 32) {
+                const int n = min(n0 + lane, P - 1);
+                float sl, ul[3];
+                node32<PS, PA>(L, tb, cone, n, sl, ul);
+                const float2 gl0 = G[gb * ca.Pstride + n];
+                float2 gl1 = make_float2(0.f, 0.f);
+                if (SPLIT) gl1 = G[(gb + 1) * ca.Pstride + n];
+                const int cnt = min(32, P - n0);
+                for (int k = 0; k < cnt; k++) {
+                    const float s = __shfl_sync(0xffffffffu, sl, k);
+                    const float u0 = __shfl_sync(0xffffffffu, ul[0], k), u1 = __shfl_sync(0xffffffffu, ul[1], k),
+                                u2 = __shfl_sync(0xffffffffu, ul[2], k);
+                    const float g0x = __shfl_sync(0xffffffffu, gl0.x, k), g0y = __shfl_sync(0xffffffffu, gl0.y, k);
+                    const float ir = s / hu;  // 1 / r (leaf units)
+                    const float dv0 = u0 - fj.x * ir, dv1 = u1 - fj.y * ir, dv2 = u2 - fj.z * ir;
+                    const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
+                    const float ia = rsqrtf(a2), am = a2 * ia;
+                    const float uy = u0 * fj.x + u1 * fj.y + u2 * fj.z;
+                    float t = kap * __fdividef(ir * yy - 2.f * uy, am + 1.f);
+                    t -= rintf(t);
+                    float sn, cs;
+                    cis_cycles(t, sn, cs);
+                    const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
+                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
+                    if (SPLIT) {
+                        const float g1x = __shfl_sync(0xffffffffu, gl1.x, k), g1y = __shfl_sync(0xffffffffu, gl1.y, k);
+                        const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
+                        acc.add(W0r * g0x + W0i * g0y + W1r * g1x + W1i * g1y,
+                                W0r * g0y - W0i * g0x + W1r * g1y - W1i * g1x);
+                    } else {
+                        const float soh = ir / hd;  // s / h (absolute)
+                        const float W0r = cs * soh * w2 + sn * g, W0i = sn * soh * w2 - cs * g;
+                        acc.add(W0r * g0x + W0i * g0y, W0r * g0y - W0i * g0x);  // conj(W) G
+                    }
+                }
+            }
+        }
+        if (act) {
+            const float2 w = acc.get();
+            float2 v = bo[(long long)q * ca.N + j];
+            v.x += w.x;
+            v.y += w.y;
+            bo[(long long)q * ca.N + j] = v;
+        }
+    }
+}
+
 // Transposed near field: b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i.
 template <bool MX>
 __global__ void __launch_bounds__(128) k_near_adj(CommonArgs ca, LevelArgs L, const void *gs_, void *b_) {
@@ -2641,7 +2715,14 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         k_near_adj<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
         prof_mark(p, s, kStNear, D);
         if (L[D].nrc) {
-            k_leaf_adj<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], tb, G[D], bws);
+            const int nch = p.ncchunk[D];
+            const unsigned gw = (unsigned)((nch + 3) / 4);
+            if (L[D].split)
+                k_leaf_adj_w<PS, PA, true><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, (const float2 *)G[D],
+                                                              (float2 *)bws);
+            else
+                k_leaf_adj_w<PS, PA, false><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, (const float2 *)G[D],
+                                                               (float2 *)bws);
             prof_mark(p, s, kStLeaf, D);
         }
         k_scatter_adj<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w32,
