@@ -1235,6 +1235,48 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
     }
 }
 
+// Transposed near field (mixed): b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i,
+// packed point records, constants hoisted, Kahan-compensated sums.
+__global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, const float2 *__restrict__ gs,
+                                                    float2 *__restrict__ bo) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ca.N) return;
+    const int b = ca.leaf_of[j];
+    const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
+    const float4 *pn = ca.pn32;
+    const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
+    const float kf = ca.kf, etaf = ca.etaf, kap = ca.kappa_hi;
+    const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
+    const float tolu = (float)(ca.tol / ca.HD);
+    for (int q = 0; q < ca.nrhs; q++) {
+        CAcc acc;
+        acc.zero();
+        for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
+            const int c = ca.nb_list[nb];
+            const float D0 = (float)(L.ijk[3 * c] - bi0) - fj.x, D1 = (float)(L.ijk[3 * c + 1] - bi1) - fj.y,
+                        D2 = (float)(L.ijk[3 * c + 2] - bi2) - fj.z;
+            for (int i = L.start[c]; i < L.start[c + 1]; i++) {
+                if (i == j) continue;
+                const float4 fi = __ldg(pn + 2 * i);
+                const float d0 = D0 + fi.x, d1 = D1 + fi.y, d2 = D2 + fi.z;  // x_i - x_j (leaf units)
+                const float r2 = d0 * d0 + d1 * d1 + d2 * d2, ir = rsqrtf(r2), r = r2 * ir;
+                if (!(r >= tolu)) continue;
+                float t = kap * r;
+                t -= rintf(t);
+                float sn, cs;
+                cis_cycles(t, sn, cs);
+                const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
+                const float A = dn * ir * ir * iHD, Bv = -(kf * dn * ir + etaf);
+                const float amp = c4 * ir;
+                const float Kr = amp * (cs * A - sn * Bv), Ki = amp * (sn * A + cs * Bv);
+                const float2 g = gs[(long long)q * ca.N + i];
+                acc.add(Kr * g.x + Ki * g.y, Kr * g.y - Ki * g.x);  // conj(K) g
+            }
+        }
+        bo[(long long)q * ca.N + j] = acc.get();
+    }
+}
+
 // Transposed near field: b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i.
 template <bool MX>
 __global__ void __launch_bounds__(128) k_near_adj(CommonArgs ca, LevelArgs L, const void *gs_, void *b_) {
@@ -2712,7 +2754,7 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
                                                                       tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
                 prof_mark(p, s, kStCousin, d);
             }
-        k_near_adj<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
+        k_near_adj32<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)gs, (float2 *)bws);
         prof_mark(p, s, kStNear, D);
         if (L[D].nrc) {
             const int nch = p.ncchunk[D];
