@@ -207,6 +207,8 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         CK(cudaMemsetAsync(p.d_missed, 0, sizeof(unsigned long long), s));
     }
     CK(cudaStreamSynchronize(s));
+    CK(cudaStreamCreateWithFlags(&p.aux, cudaStreamNonBlocking));
+    for (int i = 0; i < Plan::kMaxDep; i++) CK(cudaEventCreateWithFlags(&p.dep[i], cudaEventDisableTiming));
     ifgf_status st = IFGF_EUNSUPPORTED;
     if (p.Ps == 3 && p.Pang == 5) st = prepare_t<3, 5>(p, s);
     else if (p.Ps == 4 && p.Pang == 6) st = prepare_t<4, 6>(p, s);
@@ -218,6 +220,13 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
 }
 
 void free_plan_device(Plan &p) {
+    for (int i = 0; i < Plan::kMaxDep; i++)
+        if (p.dep[i]) {
+            cudaEventDestroy(p.dep[i]);
+            p.dep[i] = nullptr;
+        }
+    if (p.aux) cudaStreamDestroy(p.aux);
+    p.aux = nullptr;
     if (p.adj_ws) cudaFree(p.adj_ws);
     p.adj_ws = nullptr;
     p.adj_ws_bytes = 0;

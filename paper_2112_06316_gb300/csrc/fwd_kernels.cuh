@@ -2624,34 +2624,71 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
     for (int d = 3; d <= D; d++) L[d] = level_args(p, d, p.ws.F[d]);
     const long long NT = (long long)N * nrhs;
     prof_begin(p, s);
+    // The near field and the cousin interpolation of level d depend only on the gathered density and
+    // on F_d: they run on the plan's auxiliary stream beside the leaf / propagation chain (fork after
+    // the gather, one event per finished level, join before the scatter).  The auxiliary stream runs
+    // near, then cousin D, ..., 3 in order, so the field u has one writer at a time.
+    const bool par = !p.profile && p.aux;
+    const cudaStream_t sb = par ? p.aux : s;
+    auto fork = [&](int slot) {
+        if (par) {
+            CK(cudaEventRecord(p.dep[slot], s));
+            CK(cudaStreamWaitEvent(sb, p.dep[slot], 0));
+        }
+    };
+    auto join = [&]() {
+        if (par) {
+            CK(cudaEventRecord(p.dep[Plan::kMaxDep - 1], sb));
+            CK(cudaStreamWaitEvent(s, p.dep[Plan::kMaxDep - 1], 0));
+        }
+    };
     if (prec == IFGF_FP64) {
         k_gather<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w64, (const double2 *)sigma, (double2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
+        fork(0);
+        k_near64<<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const double2 *)p.ws.a, (double2 *)p.ws.u);
+        prof_mark(p, sb, kStNear, D);
         if (L[D].nrc) {
             k_leaf64<PS, PA><<<nblk(L[D].nrc * P), kBlock, 0, s>>>(ca, L[D], tb, (const double2 *)p.ws.a);
             prof_mark(p, s, kStLeaf, D);
         }
-        for (int d = D; d >= 4; d--)
+        fork(1);
+        k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], p.d_box_of[D], tb, (double2 *)p.ws.u);
+        prof_mark(p, sb, kStCousin, D);
+        for (int d = D; d >= 4; d--) {
             if (L[d - 1].nrc) {
                 k_prop64<PS, PA><<<nblk(L[d - 1].nrc * P), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
-        k_near64<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const double2 *)p.ws.a, (double2 *)p.ws.u);
-        prof_mark(p, s, kStNear, D);
-        for (int d = D; d >= 3; d--) {
-            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, s>>>(ca, L[d], p.d_box_of[d], tb, (double2 *)p.ws.u);
-            prof_mark(p, s, kStCousin, d);
+            fork(2 + D - d);
+            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[d - 1], p.d_box_of[d - 1], tb, (double2 *)p.ws.u);
+            prof_mark(p, sb, kStCousin, d - 1);
         }
+        join();
         k_scatter<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const double2 *)sigma,
                                                        (const double2 *)p.ws.u, (double2 *)y);
         prof_mark(p, s, kStScatter, 0);
     } else {
+        const bool rb1 = nrhs == 1 || p.rhs_block == 1;
+        float2 *u32 = (float2 *)p.ws.u;
+        auto cousin = [&](int d) {
+            const int nch = p.ncchunk[d];
+            if (nch > 0) {
+                const unsigned g = (unsigned)((nch + kCwWarps - 1) / kCwWarps);
+                if (rb1) k_cousin_w<PS, PA, 1><<<g, kCwWarps * 32, 0, sb>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb, u32);
+                else k_cousin_w<PS, PA, kRB><<<g, kCwWarps * 32, 0, sb>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb, u32);
+            }
+            prof_mark(p, sb, kStCousin, d);
+        };
         k_gather<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w32, (const float2 *)sigma, (float2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
+        fork(0);
+        if (rb1) k_near32<1><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const float2 *)p.ws.a, u32);
+        else k_near32<kRB><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const float2 *)p.ws.a, u32);
+        prof_mark(p, sb, kStNear, D);
         if (L[D].nrc) {
             const unsigned g = nblk(L[D].nrc * P);
             const float2 *a32 = (const float2 *)p.ws.a;
-            const bool rb1 = nrhs == 1 || p.rhs_block == 1;
             if (L[D].split) {
                 if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
                 else k_leaf32<PS, PA, kRB, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
@@ -2661,7 +2698,9 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             }
             prof_mark(p, s, kStLeaf, D);
         }
-        for (int d = D; d >= 4; d--)
+        fork(1);
+        cousin(D);
+        for (int d = D; d >= 4; d--) {
             if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].fill >= p.tc_min_fill) {
                 if constexpr (PA == 8) {
                     const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
@@ -2680,28 +2719,14 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 }
             } else if (L[d - 1].nrc) {
                 const long long nth = L[d - 1].nrc * ((P + 1) / 2);
-                if (nrhs == 1 || p.rhs_block == 1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
+                if (rb1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 else k_prop32<PS, PA, kRB><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
-        if (nrhs == 1 || p.rhs_block == 1)
-            k_near32<1><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
-        else
-            k_near32<kRB><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)p.ws.a, (float2 *)p.ws.u);
-        prof_mark(p, s, kStNear, D);
-        for (int d = D; d >= 3; d--) {
-            const int nch = p.ncchunk[d];
-            if (nch > 0) {
-                const unsigned g = (unsigned)((nch + kCwWarps - 1) / kCwWarps);
-                if (nrhs == 1 || p.rhs_block == 1)
-                    k_cousin_w<PS, PA, 1><<<g, kCwWarps * 32, 0, s>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb,
-                                                                      (float2 *)p.ws.u);
-                else
-                    k_cousin_w<PS, PA, kRB><<<g, kCwWarps * 32, 0, s>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb,
-                                                                        (float2 *)p.ws.u);
-            }
-            prof_mark(p, s, kStCousin, d);
+            fork(2 + D - d);
+            cousin(d - 1);
         }
+        join();
         k_scatter<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const float2 *)sigma,
                                                       (const float2 *)p.ws.u, (float2 *)y);
         prof_mark(p, s, kStScatter, 0);

@@ -152,7 +152,14 @@ struct Plan {
     // tunable: right-hand sides per register block in the mixed interpolation kernels (1 or 4)
     int rhs_block = 4;
 
-    // optional per-launch timing (events recorded on the apply stream)
+    // concurrent stages: the near field and the cousin interpolation run on an auxiliary stream,
+    // ordered after the gather, the leaf evaluation and each propagation by the dep events
+    cudaStream_t aux = nullptr;
+    static constexpr int kMaxDep = IFGF_MAXD + 3;
+    cudaEvent_t dep[kMaxDep] = {};
+
+    // optional per-launch timing (events recorded on the apply stream; the apply then runs on
+    // that stream alone so that every launch has its own interval)
     bool profile = false;
     static constexpr int kMaxEv = 80;
     cudaEvent_t ev[kMaxEv] = {};
