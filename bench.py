@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--orders", default="5x8", help="Ps x Pang of the headline apply")
     ap.add_argument("--nc0", type=int, default=2, help="coarsest angular cone count n_C0")
     ap.add_argument("--ns0", type=int, default=1, help="coarsest radial cone count n_S0")
+    ap.add_argument("--factor-mode", type=int, default=1,
+                    help="0 hybrid (split factors below lambda/2), 1 combined factor on every level (the setting "
+                         "of the paper's experiments), 2 split everywhere")
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--tc-fill", type=float, default=None, help="tensor-core propagation fill threshold")
     ap.add_argument("--tc-engine", type=int, default=None, help="tensor-core propagation engine: 1 tcgen05, 0 mma.sync")
@@ -98,7 +101,7 @@ def oracle_cap_apply(s, k, sig, tree, Ps, Pang):
 
     idx = cap_sample(s)
     p = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, nC0=tree.get("nC0", 2), nS0=tree.get("nS0", 1), levels=tree["D"],
-                          identity_coef=0.5,
+                          identity_coef=0.5, factor_mode=tree.get("factor_mode", 0),
                           root_center=tree["root_center"], root_side=tree["root_side"])
     t = time.perf_counter()
     oracle.ifgf(s.points[idx], s.normals[idx], s.weights[idx], p, sig[:, idx])
@@ -179,7 +182,7 @@ def kernel_source_digest():
 def recorded_traffic(stage, launches, Ps, Pang, N, args):
     """DRAM bytes (read + write) per launch of the stage's kernel from the committed ncu summary,
     only when it was taken on this workload and on the current kernel sources; else None."""
-    if (Ps, Pang, N, args.nrhs) != (5, 8, 393216, 1):
+    if (Ps, Pang, N, args.nrhs, args.factor_mode, args.nc0, args.ns0) != (5, 8, 393216, 1, 1, 2, 1):
         return None
     try:
         with open(TRAFFIC_FILE) as f:
@@ -218,7 +221,7 @@ def run_reference(args):
     Ps, Pang = (int(v) for v in args.orders.split("x"))
     oracle.build()
     info = full_octree(s)
-    info.update(nC0=args.nc0, nS0=args.ns0)
+    info.update(nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode)
     n = 0
     for _ in range(args.warmup):
         oracle_cap_apply(s, k, sig, info, Ps, Pang)
@@ -230,13 +233,14 @@ def run_reference(args):
     value = n * args.nrhs / (ms * 1e3)
     sample = (f"oracle IFGF (FP64, OpenMP) on the {n}-point spherical cap z > 0.75 of the workload, "
               f"on the full sphere's octree (D={info['D']}, same root box), orders ({Ps},{Pang},{Pang}), "
-              f"nC0={args.nc0}, nS0={args.ns0}")
+              f"nC0={args.nc0}, nS0={args.ns0}, factor mode {args.factor_mode}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"sphere {args.wavelengths:g} wavelengths, cube-sphere 6x{args.n}x{args.n} "
-                               f"(N={s.N}), orders ({Ps},{Pang},{Pang}), nrhs={args.nrhs}"},
+                               f"(N={s.N}), orders ({Ps},{Pang},{Pang}), nC0={args.nc0}, nS0={args.ns0}, "
+                               f"factor mode {args.factor_mode}, nrhs={args.nrhs}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -267,7 +271,8 @@ def run_ours(args):
     N, nrhs = s.N, args.nrhs
     Ps, Pang = (int(v) for v in args.orders.split("x"))
     t0 = time.perf_counter()
-    plan = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0))
+    plan = Plan(s.points, s.normals, s.weights,
+                Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode))
     plan_s = time.perf_counter() - t0
     if args.tc_fill is not None:
         plan.set_tc_fill(args.tc_fill)
@@ -385,7 +390,9 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"sphere {args.wavelengths:g} wavelengths across (k={k:.4f}), cube-sphere "
                                   f"6x{args.n}x{args.n} with 8x8 Fejer sub-patches, N={N}, D={info['D']}, "
-                                  f"orders ({Ps},{Pang},{Pang}), nC0={args.nc0}, nS0={args.ns0}, eta=k, nrhs={nrhs}",
+                                  f"orders ({Ps},{Pang},{Pang}), nC0={args.nc0}, nS0={args.ns0}, "
+                                  f"factor mode {args.factor_mode} (1: combined factor on every level), eta=k, "
+                                  f"nrhs={nrhs}",
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
            "roofline": roofline, "e2e": e2e, "adjoint": adjoint,
@@ -402,7 +409,7 @@ def run_ours(args):
         out["mixed_vs_fp64_speedup"] = ms64 / ms
         out["gpu_launches"] += launches_per_apply * k64
         # ---- paper orders (3,5,5) for context ----
-        plan35 = Plan(s.points, s.normals, s.weights, Params(k=k))
+        plan35 = Plan(s.points, s.normals, s.weights, Params(k=k, factor_mode=args.factor_mode))
         y35 = torch.empty_like(sig32)
         t35 = timed(lambda: plan35.apply(sig32, out=y35), max(5, args.steps // 4), 2)
         out["paper_orders_3x5"] = {"value": N * nrhs * world / (float(np.mean(t35)) * 1e3),
@@ -428,7 +435,7 @@ def run_ours(args):
             out["fp64"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["fp64"]
             out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
             tree = full_octree(s)
-            tree.update(nC0=args.nc0, nS0=args.ns0)
+            tree.update(nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode)
             n_cap, t_cap = oracle_cap_apply(s, k, sig, tree, Ps, Pang)
             out["cpu_baseline"] = {
                 "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
