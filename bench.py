@@ -436,11 +436,21 @@ def run_ours(args):
             out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
             tree = full_octree(s)
             tree.update(nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode)
-            n_cap, t_cap = oracle_cap_apply(s, k, sig, tree, Ps, Pang)
+            # repeated oracle applies on the cap sample: about 10 s (at most 30 s) of CPU work
+            caps = []
+            t_all = time.perf_counter()
+            while True:
+                n_cap, t_cap = oracle_cap_apply(s, k, sig, tree, Ps, Pang)
+                caps.append(t_cap)
+                el = time.perf_counter() - t_all
+                if el >= 10.0 or el + t_cap > 30.0:
+                    break
+            t_cap = float(np.mean(caps))
             out["cpu_baseline"] = {
                 "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                "sample": f"one oracle IFGF apply (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 of the "
-                          f"workload, full sphere's octree, orders ({Ps},{Pang},{Pang}); took {t_cap:.1f} s",
+                "sample": f"{len(caps)} oracle IFGF applies (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 "
+                          f"of the workload, full sphere's octree, orders ({Ps},{Pang},{Pang}), factor mode "
+                          f"{args.factor_mode}; {t_cap:.2f} s each, {sum(caps):.1f} s in total",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
     if args.batch:
