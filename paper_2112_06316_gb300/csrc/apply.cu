@@ -190,7 +190,8 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
                 T.grp_perm = dalloc<short>(p, ng * (size_t)p.P, err);
                 if (T.grp_perm) T.grp_cones = dalloc<int>(p, ng * 16, err);
                 if (T.grp_cones) T.grp_nc = dalloc<int>(p, ng, err);
-                if (!T.grp_nc) {
+                if (T.grp_nc) T.grp_cnt = dalloc<int>(p, ng * 17, err);
+                if (!T.grp_cnt) {
                     set_error("cudaMalloc failed: %s", cudaGetErrorString(err));
                     return IFGF_ENOMEM;
                 }

@@ -2151,12 +2151,8 @@ __device__ __forceinline__ uint32_t tmem_row_base(uint32_t tmem, int quadrant) {
 
 struct T5Misc {
     short perm[kT5Rows];
-    int cones[16];
-    int ncones;
-    int present[16];
-    int jlist[16];
-    int njp;
-    int crc[16][kTcTile];
+    int cones[1];
+    int crc[1][kTcTile];
     int rcp[kTcTile], cb[kTcTile];
     unsigned long long full[2], done[2], empty[2];
     uint32_t tmem;
@@ -2168,7 +2164,7 @@ constexpr size_t kT5Smem = 4 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
 
 template <int PS>
 __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
-                                                           TcLevel T, int tile0) {
+                                                           TcLevel T, int item0) {
     constexpr int P = PS * 64, NT5 = kTcTile, NH = kTcTile / 2;
     extern __shared__ unsigned char t5_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)t5_dyn + 1023) & ~(uintptr_t)1023);
@@ -2178,15 +2174,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     const bool worker = warp < 8;
     const int qd = warp & 3, hf = (warp >> 2) & 1;  // TMEM lane quadrant, half of the pairs
     const int row = 32 * qd + lane;
-    const int tile = tile0 + blockIdx.x;
-    const int row0 = blockIdx.y * kT5Rows;
+    const int4 item = T.items[item0 + blockIdx.x];  // (tile, first row, rows, cone slot)
+    const int tile = item.x, row0 = item.y, nrows = item.z, jslot = item.w;
     const int grp = T.tile_group[tile], p0 = T.tile_start[tile], np = T.tile_count[tile];
     const int gamma = T.grp_gamma[grp], pb = T.grp_pb[grp], cb0 = T.grp_cb[grp];
     if (tid < NT5) {
         sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
         sm.cb[tid] = tid < np ? T.pair_cb[p0 + tid] : -1;
     }
-    if (tid < 16) sm.present[tid] = 0;
     if (tid == 0) {
         sm.abort_ = 0;
         for (int b = 0; b < 2; b++) {
@@ -2204,15 +2199,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
     const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
     const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
-    // node order and child cones of the group key (filled once per plan by k_tc_order)
-    if (tid < 16) sm.cones[tid] = T.grp_cones[16 * grp + tid];
-    if (tid == 0) sm.ncones = T.grp_nc[grp];
-    if (tid < kT5Rows) sm.perm[tid] = (row0 + tid < P) ? T.grp_perm[(long long)grp * P + row0 + tid] : (short)-1;
+    // the item's nodes (one child cone) in the plan's node order (k_tc_order)
+    if (tid < kT5Rows) sm.perm[tid] = tid < nrows ? T.grp_perm[(long long)grp * P + row0 + tid] : (short)-1;
+    if (tid == 0) sm.cones[0] = T.grp_cones[16 * grp + jslot];
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int nc = sm.ncones;
     const uint32_t tmem = sm.tmem;
+    const int ccone = sm.cones[0];
     // this thread's node (both threads of the node compute it): geometry, cone slot, Lagrange factors
     const int node = worker ? sm.perm[row] : -1;
     int slot = -1;
@@ -2226,14 +2220,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
         if (node >= 0) {
             float nv[3], rp, rcv, t3[3];
             const int cone = tc_child_cone<PS>(C, Pl, tb, gamma, node, o0, o1, o2, nv, rp, rcv, t3);
-            int j = 0;
-            while (j < nc && sm.cones[j] != cone) j++;
-            if (j < nc) {
-                slot = j;
-                if (hf == 0) sm.present[j] = 1;
-            } else if (hf == 0) {
-                atomicAdd(ca.missed, 1ULL);
-            }
+            if (cone == ccone) slot = 0;
+            else if (hf == 0) atomicAdd(ca.missed, 1ULL);  // the plan's order puts every node in its cone
             const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
             float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
             t -= rintf(t);
@@ -2265,30 +2253,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
         t5_st32(lane_base + kT5ColA + 64u + 32u * hf, al);
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     }
-    for (int idx = tid; idx < nc * NT5; idx += blockDim.x) {
-        const int j = idx / NT5, q = idx % NT5;
-        const int cb = sm.cb[q];
+    if (tid < NT5) {
+        const int cb = sm.cb[tid];
         int crc = -1;
         if (cb >= 0) {
-            crc = C.cone_map[(long long)cb * C.ncone + sm.cones[j]];
+            crc = C.cone_map[(long long)cb * C.ncone + ccone];
             if (crc < 0) atomicAdd(ca.missed, 1ULL);
         }
-        sm.crc[j][q] = crc;
+        sm.crc[0][tid] = crc;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");  // A in TMEM, for the MMAs
-    __syncthreads();
-    if (tid == 0) {
-        int m = 0;
-        for (int j = 0; j < nc; j++)
-            if (sm.present[j]) sm.jlist[m++] = j;
-        sm.njp = m;
-    }
     __syncthreads();
     const bool csplit = C.split != 0, psplit = Pl.split != 0;
     const int npass = (csplit && psplit) ? 2 : 1;
     const float *FC = (const float *)C.F;
     float2 *FP = (float2 *)Pl.F;
-    const int njp = sm.njp;
     volatile int *abort_flag = &sm.abort_;
     // staging item: pair = 8 warp + (lane & 7), nodes [16 qn, 16 qn + 16) of the step's radial index with
     // qn = lane >> 3.  16-byte shared stores are serviced 8 lanes at a time: lanes 0-3 and 4-7 of each
@@ -2305,16 +2284,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             const int fp = (csplit && psplit) ? pass : 0;
             const bool use_g1 = csplit && psplit && pass == 0;
             const int ncf = cf_hi - cf_lo + 1;
-            const int nsteps = njp * ncf * PS;  // (cone slot, factor, radial index)
+            const int nsteps = ncf * PS;  // (factor, radial index)
             float E[NH][2];
 #pragma unroll
             for (int pr = 0; pr < NH; pr++) E[pr][0] = E[pr][1] = 0.f;
             if (worker) {
                 float4 pre[8], pre2[8];
                 auto fetch_to = [&](int st, float4 *dst) {
-                    const int a = st % PS, t = st / PS;
-                    const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
-                    const int crc = sm.crc[j][s_pair];
+                    const int a = st % PS, cf = cf_lo + st / PS;
+                    const int crc = sm.crc[0][s_pair];
 #pragma unroll
                     for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (crc >= 0) {
@@ -2361,13 +2339,12 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 if (nsteps > 2) fetch(2);
                 for (int st = 0; st < nsteps; st++) {
                     const int gs = G + st, bsel = gs & 1;
-                    const int a = st % PS, t = st / PS;
-                    const int cf = cf_lo + t % ncf, j = sm.jlist[t / ncf];
+                    const int a = st % PS, cf = cf_lo + st / PS;
                     const bool ok = t5_wait(smem_u32(&sm.done[bsel]), (gs >> 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     // D row of this node, this thread's pairs 32 hf .. 32 hf + 31: columns 64 hf + 2 i + re/im
                     const float sc = (csplit && !psplit && cf == 0) ? irs : 1.f;
-                    const float w = (slot == j && ok) ? sc * pick<PS>(Ls, a) : 0.f;
+                    const float w = (slot == 0 && ok) ? sc * pick<PS>(Ls, a) : 0.f;
                     const uint32_t dcol = my_taddr + (uint32_t)(bsel * kT5Cols);
                     uint32_t v0[32], v1[32];
                     t5_ld32(dcol, v0);
@@ -2512,6 +2489,8 @@ __global__ void __launch_bounds__(32) k_tc_order(LevelArgs C, LevelArgs Pl, Cheb
             if (lane == j) cnt += __popc(m);
         }
     }
+    // lane j holds the nodes of slot j; slot nc (cones beyond the first 16) is empty unless nc = 16
+    if (lane <= 16) T.grp_cnt[17 * g + lane] = cnt;
     int start = cnt;
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, start, o);
@@ -2599,6 +2578,49 @@ ifgf_status t5_prepare(Plan &p, cudaStream_t s) {
     if (e != cudaSuccess) {
         set_error("k_tc_order: %s", cudaGetErrorString(e));
         return IFGF_ECUDA;
+    }
+    // work items of the tcgen05 engine: each tile's nodes split by child cone into runs of <= 128
+    for (int d = p.D; d >= 4; d--) {
+        TcLevel &T = p.tc[d];
+        if (T.ngroups == 0 || !T.grp_perm) continue;
+        std::vector<int> tg(T.ntiles), cnt(17 * (size_t)T.ngroups), nc(T.ngroups);
+        e = cudaMemcpy(tg.data(), T.tile_group, sizeof(int) * tg.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(cnt.data(), T.grp_cnt, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(nc.data(), T.grp_nc, sizeof(int) * nc.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error("tensor-core items: %s", cudaGetErrorString(e));
+            return IFGF_ECUDA;
+        }
+        bool ok = true;
+        std::vector<int4> items;
+        for (int o = 0; o < 8; o++) {
+            T.oct_item_start[o] = (int)items.size();
+            for (int t = T.oct_tile_start[o]; t < T.oct_tile_start[o + 1]; t++) {
+                const int g = tg[t];
+                ok = ok && cnt[17 * (size_t)g + 16] == 0;
+                int off = 0;
+                for (int j = 0; j < nc[g]; j++) {
+                    const int n = cnt[17 * (size_t)g + j];
+                    for (int r = 0; r < n; r += kT5Rows) items.push_back(make_int4(t, off + r, std::min(kT5Rows, n - r), j));
+                    off += n;
+                }
+            }
+        }
+        T.oct_item_start[8] = (int)items.size();
+        T.nitems = (int)items.size();
+        T.items_ok = ok;
+        void *ptr = nullptr;
+        e = cudaMalloc(&ptr, sizeof(int4) * (items.size() + 1));
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpy(ptr, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (ptr) cudaFree(ptr);
+            set_error("tensor-core items: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
+        }
+        p.allocs.push_back(ptr);
+        p.device_bytes += (int64_t)(sizeof(int4) * (items.size() + 1));
+        T.items = (int4 *)ptr;
     }
     return IFGF_OK;
 }
@@ -2701,7 +2723,8 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         fork(1);
         cousin(D);
         for (int d = D; d >= 4; d--) {
-            if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].fill >= p.tc_min_fill) {
+            if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].fill >= p.tc_min_fill &&
+                (p.tc_engine == 0 || p.tc[d].items_ok)) {
                 if constexpr (PA == 8) {
                     const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
                     CK(cudaMemsetAsync(L[d - 1].F, 0, bytes, s));
@@ -2709,11 +2732,13 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                     for (int o = 0; o < 8; o++) {
                         const int t0 = T.oct_tile_start[o], nt = T.oct_tile_start[o + 1] - t0;
                         if (nt <= 0) continue;
-                        if (p.tc_engine == 1)
-                            k_prop_t5<PS><<<dim3(nt, (P + kT5Rows - 1) / kT5Rows), kT5Threads, kT5Smem, s>>>(
-                                ca, L[d], L[d - 1], tb, T, t0);
-                        else
+                        if (p.tc_engine == 1) {
+                            const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
+                            if (ni > 0)
+                                k_prop_t5<PS><<<ni, kT5Threads, kT5Smem, s>>>(ca, L[d], L[d - 1], tb, T, i0);
+                        } else {
                             k_prop_tc<PS><<<dim3(2 * nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
+                        }
                     }
                     prof_mark(p, s, kStPropTc, d - 1);
                 }

@@ -66,6 +66,13 @@ struct TcLevel {
     // cone they fall in (ascending cone id, then node), and the distinct child cones (<= 16)
     short *grp_perm = nullptr;
     int *grp_cones = nullptr, *grp_nc = nullptr;
+    int *grp_cnt = nullptr;  // 17 per group: nodes per cone slot (slot 16: nodes of further cones)
+    // work items of the tcgen05 engine, ordered by octant: (tile, first row in the group's node
+    // order, rows <= 128, cone slot) -- every item's rows fall in one child cone
+    int4 *items = nullptr;
+    int nitems = 0;
+    int oct_item_start[9] = {};
+    bool items_ok = false;  // every group has at most 16 child cones
 };
 
 // Device arrays of one level.
