@@ -90,7 +90,8 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     {
         std::vector<float4> pn(2 * (size_t)N);
         for (int64_t i = 0; i < N; i++) {
-            pn[2 * i] = make_float4(f32[3 * i], f32[3 * i + 1], f32[3 * i + 2], 0.f);
+            const float fx = f32[3 * i], fy = f32[3 * i + 1], fz = f32[3 * i + 2];
+            pn[2 * i] = make_float4(fx, fy, fz, fx * fx + fy * fy + fz * fz);
             pn[2 * i + 1] = make_float4(n32[3 * i], n32[3 * i + 1], n32[3 * i + 2], 0.f);
         }
         UP(p.d_pn32, pn);

@@ -383,6 +383,18 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = t;
 }
 
+// plain FP32 complex sum (random-phase sums of comparable terms: the rounding error stays at the
+// level of one rounding of the result)
+struct PAcc {
+    float sr, si;
+    __device__ __forceinline__ void zero() { sr = si = 0.f; }
+    __device__ __forceinline__ void add(float re, float im) {
+        sr += re;
+        si += im;
+    }
+    __device__ __forceinline__ float2 get() const { return make_float2(sr, si); }
+};
+
 struct CAcc {
     float sr, cr, si, ci;
     __device__ __forceinline__ void zero() { sr = cr = si = ci = 0.f; }
@@ -449,7 +461,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
     const float4 *pn = ca.pn32;
     float2 *F = (float2 *)L.F;
     for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
-        CAcc acc0[RB], acc1[RB];
+        PAcc acc0[RB], acc1[RB];
 #pragma unroll
         for (int qq = 0; qq < RB; qq++) {
             acc0[qq].zero();
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
             float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
             float ia = rsqrtf(a2);
             float am = a2 * ia;
-            float yy = fj.x * fj.x + fj.y * fj.y + fj.z * fj.z;
+            const float yy = fj.w;  // |f|^2
             float uy = u[0] * fj.x + u[1] * fj.y + u[2] * fj.z;
             // (|x - y| - |x|) / (h / s) in leaf units; am + 1 lies in [1, 3]: the fast divide is exact to 2 ulp
             float t = kap * __fdividef(ir * yy - 2.f * uy, am + 1.f);
@@ -478,8 +490,9 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
                 W1r = sn * g;
                 W1i = -cs * g;
             } else {
-                W0r = cs * soh * w2 + sn * g;
-                W0i = sn * soh * w2 - cs * g;
+                const float w2s = soh * w2;
+                W0r = cs * w2s + sn * g;
+                W0i = sn * w2s - cs * g;
             }
 #pragma unroll
             for (int qq = 0; qq < RB; qq++) {
@@ -648,7 +661,7 @@ __global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, c
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
     const float tolu = (float)(ca.tol / ca.HD);
     for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
-        CAcc acc[RB];
+        PAcc acc[RB];
 #pragma unroll
         for (int qq = 0; qq < RB; qq++) acc[qq].zero();
         for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
@@ -1180,10 +1193,10 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
     const int j = cw.y + (act ? lane : 0);
     const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
     const float hu = L.hu, kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, hd = ca.HDf;
-    const float yy = fj.x * fj.x + fj.y * fj.y + fj.z * fj.z;
+    const float yy = fj.w;  // |f|^2
     const int r0 = L.rc_start[b], r1 = L.rc_start[b + 1];
     for (int q = 0; q < ca.nrhs; q++) {
-        CAcc acc;
+        PAcc acc;
         acc.zero();
         for (int rc = r0; rc < r1; rc++) {
             const int cone = L.rc_cone[rc];
@@ -1249,7 +1262,7 @@ __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, 
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
     const float tolu = (float)(ca.tol / ca.HD);
     for (int q = 0; q < ca.nrhs; q++) {
-        CAcc acc;
+        PAcc acc;
         acc.zero();
         for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
             const int c = ca.nb_list[nb];

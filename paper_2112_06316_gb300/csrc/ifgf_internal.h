@@ -123,7 +123,7 @@ struct Plan {
     int *d_nb_start = nullptr, *d_nb_list = nullptr;
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
-    float4 *d_pn32 = nullptr;                                      // sorted, (offset, 0), (normal, 0) per point
+    float4 *d_pn32 = nullptr;                                      // sorted, (offset, |offset|^2), (normal, 0)
     unsigned long long *d_missed = nullptr;
     TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
     bool use_tc = false;

@@ -32,7 +32,7 @@ struct CommonArgs {
     const int *leaf_of, *nb_start, *nb_list;
     const double *x64, *n64, *w64;
     const float *f32, *n32, *w32;
-    const float4 *pn32;  // per point: (leaf offset, 0), (normal, 0) — one 32-byte record
+    const float4 *pn32;  // per point: (leaf offset f, |f|^2), (normal, 0) — one 32-byte record
     unsigned long long *missed;
 };
 
