@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <type_traits>
 
 #include "ifgf_internal.h"
@@ -2072,22 +2073,24 @@ __global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, 
 // stages B (64 pairs x re/im = 128 columns, K = 64) in shared memory as
 // TF32 hi / lo and runs 8 k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of
 // tcgen05.mma 128 x 128 x 8 (A from tensor memory, B from shared memory) into
-// one of two 128-column TMEM buffers.  TMEM columns: D0 0-127, D1 128-255,
-// A hi 256-319, A lo 320-383.
+// one of three 128-column TMEM buffers.  TMEM columns: D0 0-127, D1 128-255,
+// D2 256-383, A hi 384-447, A lo 448-511.
 // Warp-specialised: warps 0-7 stage operands and read D back (two threads per
-// node, one per half of the pairs), warp 8 only issues MMAs.  Per buffer, three
-// mbarriers hand the work over: full (B staged), done (MMAs complete, via
-// tcgen05.commit) and empty (D read back).  Every wait is bounded; a timeout
+// node, one per half of the pairs), warp 8 only issues MMAs.  mbarriers hand the
+// work over: full (per B stage: B staged), done and empty (per D buffer: MMAs
+// complete via tcgen05.commit; D read back).  With three D buffers the workers
+// stage step s + 2 as soon as the MMAs of step s are done and before reading
+// D(s) back, so the MMAs of s + 2 wait for the staging only.  Every wait is bounded; a timeout
 // sets a block flag that ends the remaining waits early and is reported in the
 // missed counter (high word).
 // ============================================================================
 constexpr int kT5Rows = 128;     // parent nodes per block (TMEM lanes)
-constexpr int kT5Cols = 128;     // TMEM columns of one step's D (two buffers)
+constexpr int kT5Cols = 128;     // TMEM columns of one step's D (three buffers)
 constexpr int kT5Work = 256;     // staging / readback threads (warps 0-7)
 constexpr int kT5Threads = kT5Work + 32;  // + the MMA-issuing warp
 constexpr int kT5K = 64;         // contraction length (b, c)
 constexpr int kT5TileBytes = kT5Rows * kT5K * 4;  // one 128 x 64 TF32 operand tile (B of one step)
-constexpr uint32_t kT5ColA = 256;  // TMEM column of A hi (A lo at + 64)
+constexpr uint32_t kT5ColA = 384;  // TMEM column of A hi (A lo at + 64)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -2164,10 +2167,9 @@ __device__ __forceinline__ uint32_t tmem_row_base(uint32_t tmem, int quadrant) {
 
 struct T5Misc {
     short perm[kT5Rows];
-    int cones[1];
     int crc[1][kTcTile];
-    int rcp[kTcTile], cb[kTcTile];
-    unsigned long long full[2], done[2], empty[2];
+    int rcp[kTcTile];
+    unsigned long long full[2], done[3], empty[3];
     uint32_t tmem;
     int abort_;
 };
@@ -2187,18 +2189,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     const bool worker = warp < 8;
     const int qd = warp & 3, hf = (warp >> 2) & 1;  // TMEM lane quadrant, half of the pairs
     const int row = 32 * qd + lane;
-    const int4 item = T.items[item0 + blockIdx.x];  // (tile, first row, rows, cone slot)
-    const int tile = item.x, row0 = item.y, nrows = item.z, jslot = item.w;
-    const int grp = T.tile_group[tile], p0 = T.tile_start[tile], np = T.tile_count[tile];
-    const int gamma = T.grp_gamma[grp], pb = T.grp_pb[grp], cb0 = T.grp_cb[grp];
+    // item header (filled once per plan): nodes, group, child cone, pairs, child-centre offset
+    const long long it = item0 + blockIdx.x;
+    const int4 h0 = T.item_hdr[3 * it], h1 = T.item_hdr[3 * it + 1], h2 = T.item_hdr[3 * it + 2];
+    const int row0 = h0.x, nrows = h0.y, grp = h0.z, gamma = h0.w;
+    const int ccone = h1.x, p0 = h1.y, np = h1.z;
+    const float o0 = __int_as_float(h2.x), o1 = __int_as_float(h2.y), o2 = __int_as_float(h2.z);
     if (tid < NT5) {
         sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
-        sm.cb[tid] = tid < np ? T.pair_cb[p0 + tid] : -1;
+        sm.crc[0][tid] = T.item_crc[kTcTile * it + tid];
     }
     if (tid == 0) {
         sm.abort_ = 0;
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < 2; b++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.full[b])), "r"(kT5Work));
+        for (int b = 0; b < 3; b++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.empty[b])), "r"(kT5Work));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.done[b])));
         }
@@ -2209,17 +2214,34 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
-    const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
-    const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
     // the item's nodes (one child cone) in the plan's node order (k_tc_order)
     if (tid < kT5Rows) sm.perm[tid] = tid < nrows ? T.grp_perm[(long long)grp * P + row0 + tid] : (short)-1;
-    if (tid == 0) sm.cones[0] = T.grp_cones[16 * grp + jslot];
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = sm.tmem;
-    const int ccone = sm.cones[0];
+    const bool csplit = C.split != 0, psplit = Pl.split != 0;
+    const float *FC = (const float *)C.F;
+    // staging item: pair = 8 warp + (lane & 7), nodes [16 qn, 16 qn + 16) of the step's radial index with
+    // qn = lane >> 3.  16-byte shared stores are serviced 8 lanes at a time: lanes 0-3 and 4-7 of each
+    // group of 8 store the re / im rows in opposite order, so the 8 lanes cover all 8 bank groups
+    const int s_pair = 8 * (warp & 7) + (lane & 7), s_qn = lane >> 3;
+    // child values of step st (factor cf_lo + st / PS, radial index st % PS) of right-hand side q
+    auto fetch_to = [&](int q, int cf_lo, int st, float4 *dst) {
+        const int a = st % PS, cf = cf_lo + st / PS;
+        const int crc = sm.crc[0][s_pair];
+#pragma unroll
+        for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (crc >= 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(
+                FC + 2 * ((((long long)q * C.nrc + crc) * C.nfac + cf) * ca.Pstride + a * 64 + 16 * s_qn));
+#pragma unroll
+            for (int e = 0; e < 8; e++) dst[e] = __ldg(src + e);
+        }
+    };
+    // the first pipeline's first step is in flight while the node geometry is computed
+    float4 pre[8];
+    if (worker) fetch_to(0, 0, 0, pre);  // right-hand side 0, pass 0 (factor 0), step 0
     // this thread's node (both threads of the node compute it): geometry, cone slot, Lagrange factors
     const int node = worker ? sm.perm[row] : -1;
     int slot = -1;
@@ -2266,31 +2288,19 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
         t5_st32(lane_base + kT5ColA + 64u + 32u * hf, al);
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     }
-    if (tid < NT5) {
-        const int cb = sm.cb[tid];
-        int crc = -1;
-        if (cb >= 0) {
-            crc = C.cone_map[(long long)cb * C.ncone + ccone];
-            if (crc < 0) atomicAdd(ca.missed, 1ULL);
-        }
-        sm.crc[0][tid] = crc;
-    }
+    if (tid < NT5 && tid < np && sm.crc[0][tid] < 0) atomicAdd(ca.missed, 1ULL);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");  // A in TMEM, for the MMAs
     __syncthreads();
-    const bool csplit = C.split != 0, psplit = Pl.split != 0;
     const int npass = (csplit && psplit) ? 2 : 1;
-    const float *FC = (const float *)C.F;
     float2 *FP = (float2 *)Pl.F;
     volatile int *abort_flag = &sm.abort_;
-    // staging item: pair = 8 warp + (lane & 7), nodes [16 qn, 16 qn + 16) of the step's radial index with
-    // qn = lane >> 3.  16-byte shared stores are serviced 8 lanes at a time: lanes 0-3 and 4-7 of each
-    // group of 8 store the re / im rows in opposite order, so the 8 lanes cover all 8 bank groups
-    const int s_pair = 8 * (warp & 7) + (lane & 7), s_qn = lane >> 3;
     const int first_ri = (lane >> 2) & 1;
     const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
     const uint32_t aH = tmem + kT5ColA, aL = tmem + kT5ColA + 64u;
     const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 64u * hf;  // pairs 32 hf .. 32 hf + 31
-    int G = 0;  // global step index: buffer G & 1, use G >> 1 (phase parity (G >> 1) & 1)
+    // global step index G: B stage G & 1 (use G >> 1), D buffer G % 3 (use G / 3); a barrier's phase
+    // parity is its use count & 1
+    int G = 0;
     for (int q = 0; q < ca.nrhs; q++) {
         for (int pass = 0; pass < npass; pass++) {
             const int cf_lo = (csplit && psplit) ? pass : 0, cf_hi = (csplit && psplit) ? pass : (csplit ? 1 : 0);
@@ -2302,20 +2312,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
 #pragma unroll
             for (int pr = 0; pr < NH; pr++) E[pr][0] = E[pr][1] = 0.f;
             if (worker) {
-                float4 pre[8], pre2[8];
-                auto fetch_to = [&](int st, float4 *dst) {
-                    const int a = st % PS, cf = cf_lo + st / PS;
-                    const int crc = sm.crc[0][s_pair];
-#pragma unroll
-                    for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (crc >= 0) {
-                        const float4 *src = reinterpret_cast<const float4 *>(
-                            FC + 2 * ((((long long)q * C.nrc + crc) * C.nfac + cf) * ca.Pstride + a * 64 + 16 * s_qn));
-#pragma unroll
-                        for (int e = 0; e < 8; e++) dst[e] = __ldg(src + e);
-                    }
-                };
-                auto fetch = [&](int st) { fetch_to(st, pre); };
+                auto fetch = [&](int st) { fetch_to(q, cf_lo, st, pre); };
                 auto stage = [&](int gs) {  // into buffer gs & 1, then signal full
                     unsigned char *bh = sB + (2 * (gs & 1)) * kT5TileBytes, *bl = bh + kT5TileBytes;
                     const int nre = s_pair * 2;
@@ -2340,9 +2337,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                     t5_arrive(smem_u32(&sm.full[gs & 1]));
                 };
-                // prologue: the first two steps' loads in flight together
-                if (nsteps > 0) fetch(0);
-                if (nsteps > 1) fetch_to(1, pre2);
+                // prologue: the first two steps' loads in flight together (step 0 of the block's
+                // first pipeline was issued before the node geometry)
+                float4 pre2[8];
+                if ((q > 0 || pass > 0) && nsteps > 0) fetch(0);
+                if (nsteps > 1) fetch_to(q, cf_lo, 1, pre2);
                 if (nsteps > 0) stage(G);
                 if (nsteps > 1) {
 #pragma unroll
@@ -2351,20 +2350,24 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 }
                 if (nsteps > 2) fetch(2);
                 for (int st = 0; st < nsteps; st++) {
-                    const int gs = G + st, bsel = gs & 1;
+                    const int gs = G + st, dsel = gs % 3;
                     const int a = st % PS, cf = cf_lo + st / PS;
-                    const bool ok = t5_wait(smem_u32(&sm.done[bsel]), (gs >> 1) & 1, abort_flag);
+                    const bool ok = t5_wait(smem_u32(&sm.done[dsel]), (gs / 3) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    if (st + 2 < nsteps) {  // B stage gs & 1 was consumed by the MMAs just waited for
+                        stage(gs + 2);
+                        if (st + 3 < nsteps) fetch(st + 3);
+                    }
                     // D row of this node, this thread's pairs 32 hf .. 32 hf + 31: columns 64 hf + 2 i + re/im
                     const float sc = (csplit && !psplit && cf == 0) ? irs : 1.f;
                     const float w = (slot == 0 && ok) ? sc * pick<PS>(Ls, a) : 0.f;
-                    const uint32_t dcol = my_taddr + (uint32_t)(bsel * kT5Cols);
+                    const uint32_t dcol = my_taddr + (uint32_t)(dsel * kT5Cols);
                     uint32_t v0[32], v1[32];
                     t5_ld32(dcol, v0);
                     t5_ld32(dcol + 32u, v1);
                     t5_ld_wait();
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                    t5_arrive(smem_u32(&sm.empty[bsel]));
+                    t5_arrive(smem_u32(&sm.empty[dsel]));
 #pragma unroll
                     for (int i = 0; i < 16; i++) {
                         E[i][0] = fmaf(w, __uint_as_float(v0[2 * i]), E[i][0]);
@@ -2372,20 +2375,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                         E[16 + i][0] = fmaf(w, __uint_as_float(v1[2 * i]), E[16 + i][0]);
                         E[16 + i][1] = fmaf(w, __uint_as_float(v1[2 * i + 1]), E[16 + i][1]);
                     }
-                    if (st + 2 < nsteps) {  // buffer bsel's B was consumed by the MMAs just waited for
-                        stage(gs + 2);
-                        if (st + 3 < nsteps) fetch(st + 3);
-                    }
                 }
             } else if (lane == 0) {
                 // MMA issuer
                 for (int st = 0; st < nsteps; st++) {
-                    const int gs = G + st, bsel = gs & 1, use = gs >> 1;
-                    t5_wait(smem_u32(&sm.full[bsel]), use & 1, abort_flag);
-                    if (gs >= 2) t5_wait(smem_u32(&sm.empty[bsel]), (use - 1) & 1, abort_flag);
+                    const int gs = G + st, bsel = gs & 1, dsel = gs % 3;
+                    t5_wait(smem_u32(&sm.full[bsel]), (gs >> 1) & 1, abort_flag);
+                    if (gs >= 3) t5_wait(smem_u32(&sm.empty[dsel]), (gs / 3 - 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t idesc = idesc_base | ((uint32_t)(kT5Cols >> 3) << 17);
-                    const uint32_t d = tmem + (uint32_t)(bsel * kT5Cols);
+                    const uint32_t d = tmem + (uint32_t)(dsel * kT5Cols);
                     const uint32_t bH = smem_u32(sB + (2 * bsel) * kT5TileBytes), bL = bH + kT5TileBytes;
                     if (!*abort_flag) {
 #pragma unroll 1
@@ -2397,7 +2396,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                         }
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                smem_u32(&sm.done[bsel]))
+                                smem_u32(&sm.done[dsel]))
                             : "memory");
                     }
                 }
@@ -2412,25 +2411,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                     prr *= g1;
                     pri *= g1;
                 }
-                // the pairs of a tile have distinct parent cones (one child per octant): loads are
-                // issued in batches of 16 before their stores
+                // the pairs of a tile have distinct parent cones (one child per octant), so every
+                // parent value has one writer in this launch: reduction stores (no read round trip)
 #pragma unroll
-                for (int i0 = 0; i0 < NH; i0 += 16) {
-                    long long o[16];
-                    float2 v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        const int rcp = sm.rcp[NH * hf + i0 + i];
-                        o[i] = rcp < 0 ? -1 : (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
-                        v[i] = rcp < 0 ? make_float2(0.f, 0.f) : FP[o[i]];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 16; i++) {
-                        if (o[i] < 0) continue;
-                        v[i].x += prr * E[i0 + i][0] - pri * E[i0 + i][1];
-                        v[i].y += prr * E[i0 + i][1] + pri * E[i0 + i][0];
-                        FP[o[i]] = v[i];
-                    }
+                for (int i = 0; i < NH; i++) {
+                    const int rcp = sm.rcp[NH * hf + i];
+                    if (rcp < 0) continue;
+                    const long long o = (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
+                    atomicAdd(FP + o, make_float2(prr * E[i][0] - pri * E[i][1], prr * E[i][1] + pri * E[i][0]));
                 }
             }
         }
@@ -2573,6 +2561,12 @@ static inline ChebTab cheb_tab(const Plan &p) {
 
 static inline unsigned nblk(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
+static inline int __float_as_int_host(float f) {
+    int i;
+    std::memcpy(&i, &f, sizeof i);
+    return i;
+}
+
 template <int PS>
 ifgf_status t5_prepare(Plan &p, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_prop_t5<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kT5Smem);
@@ -2622,6 +2616,60 @@ ifgf_status t5_prepare(Plan &p, cudaStream_t s) {
         T.oct_item_start[8] = (int)items.size();
         T.nitems = (int)items.size();
         T.items_ok = ok;
+        // item headers and child-cone storage indices (host copies of the tile and group tables)
+        std::vector<int> ts(T.ntiles), tcn(T.ntiles), gg(T.ngroups), gpb(T.ngroups), gcb(T.ngroups),
+            gcones(16 * (size_t)T.ngroups), pcb;
+        int npairs = 0;
+        e = cudaMemcpy(ts.data(), T.tile_start, sizeof(int) * ts.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(tcn.data(), T.tile_count, sizeof(int) * tcn.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gg.data(), T.grp_gamma, sizeof(int) * gg.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gpb.data(), T.grp_pb, sizeof(int) * gpb.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(gcb.data(), T.grp_cb, sizeof(int) * gcb.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(gcones.data(), T.grp_cones, sizeof(int) * gcones.size(), cudaMemcpyDeviceToHost);
+        for (int t = 0; t < T.ntiles; t++) npairs = std::max(npairs, ts[t] + tcn[t]);
+        pcb.resize(npairs > 0 ? npairs : 1);
+        if (e == cudaSuccess && npairs > 0)
+            e = cudaMemcpy(pcb.data(), T.pair_cb, sizeof(int) * npairs, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error("tensor-core items: %s", cudaGetErrorString(e));
+            return IFGF_ECUDA;
+        }
+        const HostLevel &HC = p.lv[d], &HP = p.lv[d - 1];
+        std::vector<int4> hdr(3 * items.size() + 1);
+        std::vector<int> icrc(kTcTile * items.size() + 1, -1);
+        for (size_t i = 0; i < items.size(); i++) {
+            const int t = items[i].x, g = tg[t], cc = gcones[16 * (size_t)g + items[i].w];
+            const int pb = gpb[g], cb0 = gcb[g];
+            float o[3];
+            for (int a = 0; a < 3; a++)  // exact: integer box coordinates, power-of-two scales
+                o[a] = ((float)HC.ijk[3 * cb0 + a] + 0.5f) * (float)HC.scale -
+                       ((float)HP.ijk[3 * pb + a] + 0.5f) * (float)HP.scale;
+            hdr[3 * i] = make_int4(items[i].y, items[i].z, g, gg[g]);
+            hdr[3 * i + 1] = make_int4(cc, ts[t], tcn[t], 0);
+            hdr[3 * i + 2] = make_int4(__float_as_int_host(o[0]), __float_as_int_host(o[1]),
+                                       __float_as_int_host(o[2]), 0);
+            for (int q = 0; q < tcn[t]; q++) {
+                const int cb = pcb[ts[t] + q];
+                icrc[kTcTile * i + q] = HC.cone_map[(size_t)cb * HC.ncone + cc];
+            }
+        }
+        void *ph = nullptr, *pc = nullptr;
+        e = cudaMalloc(&ph, sizeof(int4) * hdr.size());
+        if (e == cudaSuccess) e = cudaMalloc(&pc, sizeof(int) * icrc.size());
+        if (e == cudaSuccess) e = cudaMemcpy(ph, hdr.data(), sizeof(int4) * hdr.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(pc, icrc.data(), sizeof(int) * icrc.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (ph) cudaFree(ph);
+            if (pc) cudaFree(pc);
+            set_error("tensor-core items: %s", cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
+        }
+        p.allocs.push_back(ph);
+        p.allocs.push_back(pc);
+        p.device_bytes += (int64_t)(sizeof(int4) * hdr.size() + sizeof(int) * icrc.size());
+        T.item_hdr = (int4 *)ph;
+        T.item_crc = (int *)pc;
         void *ptr = nullptr;
         e = cudaMalloc(&ptr, sizeof(int4) * (items.size() + 1));
         if (e == cudaSuccess && !items.empty())

@@ -71,6 +71,11 @@ struct TcLevel {
     // order, rows <= 128, cone slot) -- every item's rows fall in one child cone
     int4 *items = nullptr;
     int nitems = 0;
+    // per item, filled once per plan: header (row0, rows, group, gamma), (child cone id, first pair,
+    // pairs, 0), (child-centre offset from the parent centre, 0) and the pairs' child-cone storage
+    // indices (kTcTile ints, -1 beyond the tile's pairs)
+    int4 *item_hdr = nullptr;
+    int *item_crc = nullptr;
     int oct_item_start[9] = {};
     bool items_ok = false;  // every group has at most 16 child cones
 };
