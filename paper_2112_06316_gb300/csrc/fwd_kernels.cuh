@@ -515,6 +515,67 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
     }
 }
 
+// K1 (mixed), one right-hand side, two adjacent cone nodes per thread: every source record
+// (offset, |offset|^2, normal, weighted density) is loaded once for both nodes.
+template <int PS, int PA, bool SPLIT>
+__global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L, ChebTab tb,
+                                                     const float2 *__restrict__ a) {
+    constexpr int P = PS * PA * PA, PH = (P + 1) / 2;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= L.nrc * PH) return;
+    const int rc = (int)(tid / PH), m = (int)(tid % PH);
+    const int n0 = 2 * m, n1 = 2 * m + 1;
+    const bool has1 = n1 < P;
+    const int b = L.rc_box[rc];
+    float s0, u0[3], s1, u1[3];
+    node32<PS, PA>(L, tb, L.rc_cone[rc], n0, s0, u0);
+    node32<PS, PA>(L, tb, L.rc_cone[rc], has1 ? n1 : n0, s1, u1);
+    const float hu = L.hu;
+    const float ir0 = s0 / hu, ir1 = s1 / hu;  // 1 / r (leaf units)
+    const float soh0 = s0 / (hu * ca.HDf), soh1 = s1 / (hu * ca.HDf);
+    const float kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf;
+    const int j0 = L.start[b], j1 = L.start[b + 1];
+    const float4 *pn = ca.pn32;
+    PAcc p00, p01, p10, p11;  // [node][factor]
+    p00.zero(); p01.zero(); p10.zero(); p11.zero();
+    auto eval = [&](const float *u, float ir, float soh, const float4 &fj, const float4 &nj, const float2 &aj,
+                    PAcc &A0, PAcc &A1) {
+        const float dv0 = u[0] - fj.x * ir, dv1 = u[1] - fj.y * ir, dv2 = u[2] - fj.z * ir;
+        const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
+        const float ia = rsqrtf(a2), am = a2 * ia;
+        const float uy = u[0] * fj.x + u[1] * fj.y + u[2] * fj.z;
+        float t = kap * __fdividef(ir * fj.w - 2.f * uy, am + 1.f);
+        t -= rintf(t);
+        float sn, cs;
+        cis_cycles(t, sn, cs);
+        const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
+        const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
+        if (SPLIT) {
+            const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
+            A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
+            A1.add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
+        } else {
+            const float w2s = soh * w2;
+            const float W0r = cs * w2s + sn * g, W0i = sn * w2s - cs * g;
+            A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
+        }
+    };
+    for (int j = j0; j < j1; j++) {
+        const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
+        const float2 aj = a[j];
+        eval(u0, ir0, soh0, fj, nj, aj, p00, p01);
+        eval(u1, ir1, soh1, fj, nj, aj, p10, p11);
+    }
+    float2 *F = (float2 *)L.F;
+    const long long base = (long long)rc * L.nfac;
+    F[base * ca.Pstride + n0] = p00.get();
+    if (SPLIT) F[(base + 1) * ca.Pstride + n0] = p01.get();
+    if (has1) {
+        F[base * ca.Pstride + n1] = p10.get();
+        if (SPLIT) F[(base + 1) * ca.Pstride + n1] = p11.get();
+    }
+}
+
 // K3 (mixed).  One thread owns two adjacent nodes of a parent cone; when both
 // fall in the same child cone the child's node values are loaded once for both.
 struct PropGeo {
@@ -2772,11 +2833,14 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         if (L[D].nrc) {
             const unsigned g = nblk(L[D].nrc * P);
             const float2 *a32 = (const float2 *)p.ws.a;
+            const unsigned g2 = nblk(L[D].nrc * ((P + 1) / 2));
             if (L[D].split) {
-                if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                if (nrhs == 1) k_leaf32x2<PS, PA, true><<<g2, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                else if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
                 else k_leaf32<PS, PA, kRB, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
             } else {
-                if (rb1) k_leaf32<PS, PA, 1, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                if (nrhs == 1) k_leaf32x2<PS, PA, false><<<g2, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                else if (rb1) k_leaf32<PS, PA, 1, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
                 else k_leaf32<PS, PA, kRB, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
             }
             prof_mark(p, s, kStLeaf, D);
