@@ -967,15 +967,18 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
     const C *Gp = (const C *)Gp_;
     C *Gc = (C *)Gc_;
     __shared__ AntEntry<T, PS, PA> ent[128];
+    __shared__ C part[128][PS];  // partial sums of the entry groups
     const int rc = blockIdx.x;
     const int cbox = L.rc_box[rc];
     const long long e0 = ad_start[rc], e1 = ad_start[rc + 1];
     const int nfac = L.nfac;
     const bool csplit = L.split != 0, psplit = has_parent && Pl.split != 0;
-    // accumulation: thread = (factor, b, c) of the output cone, all PS radial nodes (a, b, c)
-    const int unit = threadIdx.x;
-    const bool active = unit < nfac * PA2;
-    const int fac = active ? unit / PA2 : 0, bc = active ? unit % PA2 : 0;
+    // accumulation: thread = (factor, b, c) of the output cone, all PS radial nodes (a, b, c); the
+    // ng = 128 / (nfac PA^2) groups of such threads take every ng-th entry and are summed at the end
+    const int unit = threadIdx.x, nout = nfac * PA2, ng = 128 / nout;
+    const int eg = unit / nout, uo = unit % nout;
+    const bool active = eg < ng;
+    const int fac = uo / PA2, bc = uo % PA2;
     const int ub = bc / PA, uc = bc % PA;
     for (int q = 0; q < ca.nrhs; q++) {
         C acc[PS];
@@ -1136,7 +1139,7 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
             __syncthreads();
             if (active) {
                 const int cnt = (int)min((long long)128, e1 - base);
-                for (int t = 0; t < cnt; t++) {
+                for (int t = eg; t < cnt; t += ng) {
                     const AntEntry<T, PS, PA> &en = ent[t];
                     const T w = en.Lt[ub] * en.Lp[uc];
                     const C v = en.v[fac];
@@ -1150,11 +1153,23 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
             }
             __syncthreads();
         }
-        if (active) {
+        if (active && eg > 0) {
+#pragma unroll
+            for (int a = 0; a < PS; a++) part[unit][a] = acc[a];
+        }
+        __syncthreads();
+        if (active && eg == 0) {
+            for (int g2 = 1; g2 < ng; g2++)
+#pragma unroll
+                for (int a = 0; a < PS; a++) {
+                    acc[a].x += part[g2 * nout + uo][a].x;
+                    acc[a].y += part[g2 * nout + uo][a].y;
+                }
             C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + bc;
 #pragma unroll
             for (int a = 0; a < PS; a++) out[a * PA2] = acc[a];
         }
+        __syncthreads();
     }
 }
 
