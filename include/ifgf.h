@@ -29,7 +29,10 @@
  *    the caller's order; the library permutes internally.
  *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Apply
  *    calls are asynchronous on it; plan creation and GMRES synchronise.  A plan
- *    serves one stream at a time.
+ *    serves one stream at a time.  Inside a forward apply the near field and the
+ *    cousin interpolation run on a stream owned by the plan, forked from and
+ *    joined back into `stream` by events, so every effect of the call is ordered
+ *    on `stream` (this also holds inside CUDA graph capture).
  */
 #ifndef IFGF_H
 #define IFGF_H
