@@ -576,8 +576,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L,
     }
 }
 
-// K3 (mixed).  One thread owns two adjacent nodes of a parent cone; when both
-// fall in the same child cone the child's node values are loaded once for both.
+// K3 (mixed): geometry of one (parent node, child box) pair.
 struct PropGeo {
     int crc;
     float t3[3];
@@ -618,94 +617,6 @@ __device__ __forceinline__ void prop_add(CAcc &a0, CAcc &a1, bool csplit, bool p
         }
     } else {
         a0.add(vr * g.r1r - vi * g.r1i, vr * g.r1i + vi * g.r1r);
-    }
-}
-
-template <int PS, int PA, int RB>
-__global__ void __launch_bounds__(kBlock) k_prop32(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb) {
-    constexpr int P = PS * PA * PA, PH = (P + 1) / 2;
-    long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= Pl.nrc * PH) return;
-    const int rc = (int)(tid / PH), m = (int)(tid % PH);
-    const int n0 = 2 * m, n1 = 2 * m + 1;
-    const bool has1 = n1 < P;
-    const int pb = Pl.rc_box[rc];
-    float s0, u0[3], s1, u1[3];
-    node32<PS, PA>(Pl, tb, Pl.rc_cone[rc], n0, s0, u0);
-    node32<PS, PA>(Pl, tb, Pl.rc_cone[rc], has1 ? n1 : n0, s1, u1);
-    const float rp0 = Pl.hu / s0, rp1 = Pl.hu / s1;  // leaf units
-    const float nv0[3] = {rp0 * u0[0], rp0 * u0[1], rp0 * u0[2]};
-    const float nv1[3] = {rp1 * u1[0], rp1 * u1[1], rp1 * u1[2]};
-    const float pc[3] = {(Pl.ijk[3 * pb] + 0.5f) * Pl.scale, (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale,
-                         (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale};
-    const float2 *FC = (const float2 *)C.F;
-    float2 *FP = (float2 *)Pl.F;
-    const bool cs_ = C.split != 0, ps_ = Pl.split != 0;
-    const int nfac = C.nfac;
-    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
-        CAcc a00[RB], a01[RB], a10[RB], a11[RB];  // [node][factor]
-#pragma unroll
-        for (int qq = 0; qq < RB; qq++) {
-            a00[qq].zero(); a01[qq].zero(); a10[qq].zero(); a11[qq].zero();
-        }
-        for (int ci = Pl.ch_start[pb]; ci < Pl.ch_start[pb + 1]; ci++) {
-            const int cb = Pl.ch_list[ci];
-            // child centre minus parent centre, exact in leaf units
-            const float o0 = (C.ijk[3 * cb] + 0.5f) * C.scale - pc[0];
-            const float o1 = (C.ijk[3 * cb + 1] + 0.5f) * C.scale - pc[1];
-            const float o2 = (C.ijk[3 * cb + 2] + 0.5f) * C.scale - pc[2];
-            PropGeo g0, g1;
-            prop_geo32(ca, C, cb, nv0, rp0, o0, o1, o2, g0);
-            prop_geo32(ca, C, cb, nv1, rp1, o0, o1, o2, g1);
-            if (!has1) g1.crc = -2;
-            if (q0 == 0 && (g0.crc < 0 || g1.crc == -1)) atomicAdd(ca.missed, (g0.crc < 0) + (g1.crc == -1));
-            float Ls0[PS], Lt0[PA], Lp0[PA], Ls1[PS], Lt1[PA], Lp1[PA];
-            lagrange<PS, float>(g0.t3[0], tb.fxs, tb.fcs, Ls0);
-            lagrange<PA, float>(g0.t3[1], tb.fxa, tb.fca, Lt0);
-            lagrange<PA, float>(g0.t3[2], tb.fxa, tb.fca, Lp0);
-            lagrange<PS, float>(g1.t3[0], tb.fxs, tb.fcs, Ls1);
-            lagrange<PA, float>(g1.t3[1], tb.fxa, tb.fca, Lt1);
-            lagrange<PA, float>(g1.t3[2], tb.fxa, tb.fca, Lp1);
-            // one pass when both nodes use the same child cone, else one pass per cone
-            const int npass = (g0.crc == g1.crc || g1.crc < 0 || g0.crc < 0) ? 1 : 2;
-#pragma unroll 1
-            for (int pass = 0; pass < npass; pass++) {
-                const int crc = (pass == 0) ? (g0.crc >= 0 ? g0.crc : g1.crc) : g1.crc;
-                if (crc < 0) continue;
-                const bool k0 = g0.crc == crc, k1 = g1.crc == crc;
-#pragma unroll
-                for (int qq = 0; qq < RB; qq++) {
-                    if (q0 + qq >= ca.nrhs) continue;
-                    const long long base = ((long long)(q0 + qq) * C.nrc + crc) * nfac;
-                    float v0r = 0.f, v0i = 0.f, v1r = 0.f, v1i = 0.f, w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f;
-#pragma unroll 1
-                    for (int fac = 0; fac < nfac; fac++) {
-                        float x0r, x0i, x1r, x1i;
-                        interp3f_pair<PS, PA>(FC + (base + fac) * ca.Pstride, Ls0, Lt0, Lp0, Ls1, Lt1, Lp1, x0r, x0i,
-                                              x1r, x1i);
-                        if (fac == 0) {
-                            v0r = x0r; v0i = x0i; v1r = x1r; v1i = x1i;
-                        } else {
-                            w0r = x0r; w0i = x0i; w1r = x1r; w1i = x1i;
-                        }
-                    }
-                    if (k0) prop_add(a00[qq], a01[qq], cs_, ps_, g0, v0r, v0i, w0r, w0i);
-                    if (k1) prop_add(a10[qq], a11[qq], cs_, ps_, g1, v1r, v1i, w1r, w1i);
-                }
-            }
-        }
-#pragma unroll
-        for (int qq = 0; qq < RB; qq++) {
-            if (q0 + qq < ca.nrhs) {
-                const long long base = ((long long)(q0 + qq) * Pl.nrc + rc) * Pl.nfac;
-                FP[base * ca.Pstride + n0] = a00[qq].get();
-                if (ps_) FP[(base + 1) * ca.Pstride + n0] = a01[qq].get();
-                if (has1) {
-                    FP[base * ca.Pstride + n1] = a10[qq].get();
-                    if (ps_) FP[(base + 1) * ca.Pstride + n1] = a11[qq].get();
-                }
-            }
-        }
     }
 }
 
@@ -923,6 +834,94 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
                     v.x += w.x;
                     v.y += w.y;
                     u[o] = v;
+                }
+            }
+        }
+    }
+}
+
+
+// K3 (mixed), staged: one warp owns 32 nodes of one parent relevant cone and walks the
+// parent box's children; for every distinct child cone its lanes fall into, the warp
+// copies that cone's node values (all factors) into shared memory with cp.async and the
+// lanes of that cone interpolate from there (the pattern of k_cousin_w).
+template <int PS, int PA, int RB>
+__global__ void __launch_bounds__(kCwWarps * 32) k_prop_w(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb) {
+    constexpr int P = PS * PA * PA, PST = P + (P & 1), NCH = (P + 31) / 32;
+    constexpr int NL = (PST + 31) / 32;
+    __shared__ __align__(16) float2 sF[kCwWarps][2 * PST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long unit = (long long)blockIdx.x * kCwWarps + warp;
+    if (unit >= Pl.nrc * (long long)NCH) return;  // warp-uniform: no block-wide barrier below
+    const int rc = (int)(unit / NCH), n = (int)(unit % NCH) * 32 + lane;
+    const bool act = n < P;
+    const int pb = Pl.rc_box[rc];
+    float s, uu[3];
+    node32<PS, PA>(Pl, tb, Pl.rc_cone[rc], act ? n : 0, s, uu);
+    const float rp = Pl.hu / s;  // leaf units
+    const float nv[3] = {rp * uu[0], rp * uu[1], rp * uu[2]};
+    const float pc[3] = {(Pl.ijk[3 * pb] + 0.5f) * Pl.scale, (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale,
+                         (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale};
+    const float2 *FC = (const float2 *)C.F;
+    float2 *FP = (float2 *)Pl.F;
+    const bool cs_ = C.split != 0, ps_ = Pl.split != 0;
+    const int nv4 = C.nfac * PST / 2;
+    float2 *buf = sF[warp];
+    float4 *dst = reinterpret_cast<float4 *>(buf);
+    const int c0 = Pl.ch_start[pb], c1 = Pl.ch_start[pb + 1];
+    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
+        CAcc a0[RB], a1[RB];  // parent factors
+#pragma unroll
+        for (int qq = 0; qq < RB; qq++) {
+            a0[qq].zero();
+            a1[qq].zero();
+        }
+        for (int ci = c0; ci < c1; ci++) {
+            const int cb = Pl.ch_list[ci];
+            const float o0 = (C.ijk[3 * cb] + 0.5f) * C.scale - pc[0];
+            const float o1 = (C.ijk[3 * cb + 1] + 0.5f) * C.scale - pc[1];
+            const float o2 = (C.ijk[3 * cb + 2] + 0.5f) * C.scale - pc[2];
+            PropGeo g;
+            prop_geo32(ca, C, cb, nv, rp, o0, o1, o2, g);
+            if (!act) g.crc = -2;
+            if (q0 == 0 && g.crc == -1) atomicAdd(ca.missed, 1ULL);
+            float Ls[PS], Lt[PA], Lp[PA];
+            lagrange<PS, float>(g.t3[0], tb.fxs, tb.fcs, Ls);
+            lagrange<PA, float>(g.t3[1], tb.fxa, tb.fca, Lt);
+            lagrange<PA, float>(g.t3[2], tb.fxa, tb.fca, Lp);
+            bool pend = g.crc >= 0;
+            unsigned m;
+            while ((m = __ballot_sync(0xffffffffu, pend)) != 0u) {
+                const int crc = __shfl_sync(0xffffffffu, g.crc, __ffs(m) - 1);
+                const bool mine = pend && g.crc == crc;
+#pragma unroll
+                for (int qq = 0; qq < RB; qq++) {
+                    if (RB > 1 && q0 + qq >= ca.nrhs) break;  // warp-uniform
+                    const float4 *src = reinterpret_cast<const float4 *>(
+                        FC + ((long long)(q0 + qq) * C.nrc + crc) * C.nfac * ca.Pstride);
+                    __syncwarp();  // the previous cone's readers are done
+#pragma unroll
+                    for (int k = 0; k < NL; k++)
+                        if (lane + 32 * k < nv4) cp_async16(dst + lane + 32 * k, src + lane + 32 * k);
+                    cp_async_wait_all();
+                    __syncwarp();
+                    if (mine) {
+                        float vr, vi, wr = 0.f, wi = 0.f;
+                        interp3f_one<PS, PA>(buf, Ls, Lt, Lp, vr, vi);
+                        if (cs_) interp3f_one<PS, PA>(buf + PST, Ls, Lt, Lp, wr, wi);
+                        prop_add(a0[qq], a1[qq], cs_, ps_, g, vr, vi, wr, wi);
+                    }
+                }
+                pend = pend && !mine;
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int qq = 0; qq < RB; qq++) {
+                if (RB == 1 || q0 + qq < ca.nrhs) {
+                    const long long base = ((long long)(q0 + qq) * Pl.nrc + rc) * Pl.nfac;
+                    FP[base * ca.Pstride + n] = a0[qq].get();
+                    if (ps_) FP[(base + 1) * ca.Pstride + n] = a1[qq].get();
                 }
             }
         }
@@ -2883,9 +2882,10 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                     prof_mark(p, s, kStPropTc, d - 1);
                 }
             } else if (L[d - 1].nrc) {
-                const long long nth = L[d - 1].nrc * ((P + 1) / 2);
-                if (rb1) k_prop32<PS, PA, 1><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
-                else k_prop32<PS, PA, kRB><<<nblk(nth), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
+                const long long nw = L[d - 1].nrc * (long long)((P + 31) / 32);
+                const unsigned gw = (unsigned)((nw + kCwWarps - 1) / kCwWarps);
+                if (rb1) k_prop_w<PS, PA, 1><<<gw, kCwWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb);
+                else k_prop_w<PS, PA, kRB><<<gw, kCwWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
             fork(2 + D - d);

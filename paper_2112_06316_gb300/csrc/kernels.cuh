@@ -106,59 +106,6 @@ __device__ __forceinline__ float pick(const float *L, int a) {
     return v;
 }
 
-// Two targets interpolated from the same cone in FP32: every node value loaded
-// feeds both targets (16-byte loads of two complex values when PA is even).  The
-// s-loop is kept rolled so that the body (PA*PA nodes) stays small in the
-// instruction cache.  Node order as interp3.
-template <int PS, int PA>
-__device__ __forceinline__ void interp3f_pair(const float2 *__restrict__ f, const float *Ls0, const float *Lt0,
-                                              const float *Lp0, const float *Ls1, const float *Lt1, const float *Lp1,
-                                              float &r0, float &i0, float &r1, float &i1) {
-    r0 = i0 = r1 = i1 = 0.f;
-#pragma unroll 1
-    for (int a = 0; a < PS; a++) {
-        const float la0 = pick<PS>(Ls0, a), la1 = pick<PS>(Ls1, a);
-        const float2 *fa = f + a * PA * PA;
-        float ra0 = 0.f, ia0 = 0.f, ra1 = 0.f, ia1 = 0.f;
-#pragma unroll
-        for (int b = 0; b < PA; b++) {
-            float rb0 = 0.f, ib0 = 0.f, rb1 = 0.f, ib1 = 0.f;
-            const float2 *row = fa + b * PA;
-            if constexpr (PA % 2 == 0) {
-#pragma unroll
-                for (int c = 0; c < PA; c += 2) {
-                    float4 v = __ldg(reinterpret_cast<const float4 *>(row + c));
-                    rb0 = fmaf(Lp0[c], v.x, rb0);
-                    ib0 = fmaf(Lp0[c], v.y, ib0);
-                    rb0 = fmaf(Lp0[c + 1], v.z, rb0);
-                    ib0 = fmaf(Lp0[c + 1], v.w, ib0);
-                    rb1 = fmaf(Lp1[c], v.x, rb1);
-                    ib1 = fmaf(Lp1[c], v.y, ib1);
-                    rb1 = fmaf(Lp1[c + 1], v.z, rb1);
-                    ib1 = fmaf(Lp1[c + 1], v.w, ib1);
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < PA; c++) {
-                    float2 v = __ldg(row + c);
-                    rb0 = fmaf(Lp0[c], v.x, rb0);
-                    ib0 = fmaf(Lp0[c], v.y, ib0);
-                    rb1 = fmaf(Lp1[c], v.x, rb1);
-                    ib1 = fmaf(Lp1[c], v.y, ib1);
-                }
-            }
-            ra0 = fmaf(Lt0[b], rb0, ra0);
-            ia0 = fmaf(Lt0[b], ib0, ia0);
-            ra1 = fmaf(Lt1[b], rb1, ra1);
-            ia1 = fmaf(Lt1[b], ib1, ia1);
-        }
-        r0 = fmaf(la0, ra0, r0);
-        i0 = fmaf(la0, ia0, i0);
-        r1 = fmaf(la1, ra1, r1);
-        i1 = fmaf(la1, ia1, i1);
-    }
-}
-
 // Phase (in cycles, reduced to [-1/2, 1/2]) of kappa * |M + f| where M has
 // half-integer components with |2M|^2 < 2^24 (so |M|^2 is exact in FP32) and f is
 // a small FP32 offset; kappa = kappa_hi + kappa_lo.  |M + f| = sqrt(S) + T / (r + sqrt(S))
