@@ -150,7 +150,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_OF_STAGE = {"leaf": "k_leaf32", "near": "k_near32", "cousin": "k_cousin_w", "prop": "k_prop_w",
+KERNEL_OF_STAGE = {"leaf": "k_leaf32x2", "near": "k_near32", "cousin": "k_cousin_w", "prop": "k_prop_w",
                    "prop_tc": "k_prop_t5"}
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "dram_traffic_sphere16lambda_5x8.txt")
