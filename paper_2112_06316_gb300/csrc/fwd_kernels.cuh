@@ -766,7 +766,11 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
                                                             float2 *__restrict__ u) {
     constexpr int P = PS * PA * PA, PST = P + (P & 1);  // PST = node stride of one factor (the plan's Pstride)
     constexpr int NL = (PST + 31) / 32;                  // float4 per lane to copy two factors
-    __shared__ __align__(16) float2 sF[kCwWarps][2 * PST];
+    // four slots of one factor each (slot k at k (PST + 2): 16 bytes of stagger per slot, so that lanes
+    // reading different cones at the same offset hit different bank groups); a pass stages up to
+    // 4 / nfac distinct cones, cone k in slots nfac k .. nfac k + nfac - 1
+    constexpr int SLOT = PST + 2;
+    __shared__ __align__(16) float2 sF[kCwWarps][4 * SLOT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x * kCwWarps + warp;
     if (ch >= nchunk) return;  // warp-uniform: no block-wide barrier below
@@ -780,9 +784,9 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
     const float f[3] = {fi.x, fi.y, fi.z};
     const float2 *F = (const float2 *)L.F;
     const bool sp = L.split != 0;
-    const int nv4 = L.nfac * PST / 2;  // float4 of one relevant cone (all factors)
+    const int nv4 = PST / 2;  // float4 of one factor of a relevant cone
+    const int nfac = L.nfac, kmax = 4 / nfac;  // cones per pass
     float2 *buf = sF[warp];
-    float4 *dst = reinterpret_cast<float4 *>(buf);
     const int c0 = L.co_start[b], c1 = L.co_start[b + 1];
     for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
         CAcc acc[RB];
@@ -799,25 +803,43 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
             lagrange<PA, float>(g.t3[1], tb.fxa, tb.fca, Lt);
             lagrange<PA, float>(g.t3[2], tb.fxa, tb.fca, Lp);
             bool pend = g.rc >= 0;
-            unsigned m;
-            while ((m = __ballot_sync(0xffffffffu, pend)) != 0u) {
-                const int rc = __shfl_sync(0xffffffffu, g.rc, __ffs(m) - 1);
-                const bool mine = pend && g.rc == rc;
+            while (__any_sync(0xffffffffu, pend)) {
+                // up to kmax distinct cones of the pending lanes (leaders in lane order)
+                int rcs[4] = {-1, -1, -1, -1};
+                int nk = 0, myk = -1;
+                bool left = pend;
+                for (int k = 0; k < kmax; k++) {
+                    const unsigned mk = __ballot_sync(0xffffffffu, left);
+                    if (!mk) break;
+                    const int rk = __shfl_sync(0xffffffffu, g.rc, __ffs(mk) - 1);
+                    if (left && g.rc == rk) {
+                        myk = k;
+                        left = false;
+                    }
+                    rcs[k] = rk;
+                    nk = k + 1;
+                }
+                const bool mine = myk >= 0;
+                const float2 *mybuf = buf + (mine ? myk * nfac : 0) * SLOT;
 #pragma unroll
                 for (int qq = 0; qq < RB; qq++) {
                     if (RB > 1 && q0 + qq >= ca.nrhs) break;  // warp-uniform
-                    const float4 *src = reinterpret_cast<const float4 *>(
-                        F + ((long long)(q0 + qq) * L.nrc + rc) * L.nfac * ca.Pstride);
-                    __syncwarp();  // the previous cone's readers are done
+                    __syncwarp();  // the previous cones' readers are done
+                    for (int k = 0; k < nk; k++)
+                        for (int fc = 0; fc < nfac; fc++) {
+                            const float4 *src = reinterpret_cast<const float4 *>(
+                                F + (((long long)(q0 + qq) * L.nrc + rcs[k]) * nfac + fc) * ca.Pstride);
+                            float4 *dk = reinterpret_cast<float4 *>(buf + (k * nfac + fc) * SLOT);
 #pragma unroll
-                    for (int k = 0; k < NL; k++)
-                        if (lane + 32 * k < nv4) cp_async16(dst + lane + 32 * k, src + lane + 32 * k);
+                            for (int v = 0; v < NL; v++)
+                                if (lane + 32 * v < nv4) cp_async16(dk + lane + 32 * v, src + lane + 32 * v);
+                        }
                     cp_async_wait_all();
                     __syncwarp();
                     if (mine) {
                         float vr, vi, wr = 0.f, wi = 0.f;
-                        interp3f_one<PS, PA>(buf, Ls, Lt, Lp, vr, vi);
-                        if (sp) interp3f_one<PS, PA>(buf + PST, Ls, Lt, Lp, wr, wi);
+                        interp3f_one<PS, PA>(mybuf, Ls, Lt, Lp, vr, vi);
+                        if (sp) interp3f_one<PS, PA>(mybuf + SLOT, Ls, Lt, Lp, wr, wi);
                         cousin_add(acc[qq], sp, g, vr, vi, wr, wi);
                     }
                 }
