@@ -871,7 +871,8 @@ template <int PS, int PA, int RB>
 __global__ void __launch_bounds__(kCwWarps * 32) k_prop_w(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb) {
     constexpr int P = PS * PA * PA, PST = P + (P & 1), NCH = (P + 31) / 32;
     constexpr int NL = (PST + 31) / 32;
-    __shared__ __align__(16) float2 sF[kCwWarps][2 * PST];
+    constexpr int SLOT = PST + 2;  // four 16-byte-staggered one-factor slots, as in k_cousin_w
+    __shared__ __align__(16) float2 sF[kCwWarps][4 * SLOT];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long unit = (long long)blockIdx.x * kCwWarps + warp;
     if (unit >= Pl.nrc * (long long)NCH) return;  // warp-uniform: no block-wide barrier below
@@ -887,9 +888,9 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_prop_w(CommonArgs ca, LevelAr
     const float2 *FC = (const float2 *)C.F;
     float2 *FP = (float2 *)Pl.F;
     const bool cs_ = C.split != 0, ps_ = Pl.split != 0;
-    const int nv4 = C.nfac * PST / 2;
+    const int nv4 = PST / 2;  // float4 of one factor of a child cone
+    const int nfac = C.nfac, kmax = 4 / nfac;  // child cones per pass
     float2 *buf = sF[warp];
-    float4 *dst = reinterpret_cast<float4 *>(buf);
     const int c0 = Pl.ch_start[pb], c1 = Pl.ch_start[pb + 1];
     for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
         CAcc a0[RB], a1[RB];  // parent factors
@@ -912,25 +913,43 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_prop_w(CommonArgs ca, LevelAr
             lagrange<PA, float>(g.t3[1], tb.fxa, tb.fca, Lt);
             lagrange<PA, float>(g.t3[2], tb.fxa, tb.fca, Lp);
             bool pend = g.crc >= 0;
-            unsigned m;
-            while ((m = __ballot_sync(0xffffffffu, pend)) != 0u) {
-                const int crc = __shfl_sync(0xffffffffu, g.crc, __ffs(m) - 1);
-                const bool mine = pend && g.crc == crc;
+            while (__any_sync(0xffffffffu, pend)) {
+                // up to kmax distinct child cones of the pending lanes (leaders in lane order)
+                int crcs[4] = {-1, -1, -1, -1};
+                int nk = 0, myk = -1;
+                bool left = pend;
+                for (int k = 0; k < kmax; k++) {
+                    const unsigned mk = __ballot_sync(0xffffffffu, left);
+                    if (!mk) break;
+                    const int ck = __shfl_sync(0xffffffffu, g.crc, __ffs(mk) - 1);
+                    if (left && g.crc == ck) {
+                        myk = k;
+                        left = false;
+                    }
+                    crcs[k] = ck;
+                    nk = k + 1;
+                }
+                const bool mine = myk >= 0;
+                const float2 *mybuf = buf + (mine ? myk * nfac : 0) * SLOT;
 #pragma unroll
                 for (int qq = 0; qq < RB; qq++) {
                     if (RB > 1 && q0 + qq >= ca.nrhs) break;  // warp-uniform
-                    const float4 *src = reinterpret_cast<const float4 *>(
-                        FC + ((long long)(q0 + qq) * C.nrc + crc) * C.nfac * ca.Pstride);
-                    __syncwarp();  // the previous cone's readers are done
+                    __syncwarp();  // the previous cones' readers are done
+                    for (int k = 0; k < nk; k++)
+                        for (int fc = 0; fc < nfac; fc++) {
+                            const float4 *src = reinterpret_cast<const float4 *>(
+                                FC + (((long long)(q0 + qq) * C.nrc + crcs[k]) * nfac + fc) * ca.Pstride);
+                            float4 *dk = reinterpret_cast<float4 *>(buf + (k * nfac + fc) * SLOT);
 #pragma unroll
-                    for (int k = 0; k < NL; k++)
-                        if (lane + 32 * k < nv4) cp_async16(dst + lane + 32 * k, src + lane + 32 * k);
+                            for (int v = 0; v < NL; v++)
+                                if (lane + 32 * v < nv4) cp_async16(dk + lane + 32 * v, src + lane + 32 * v);
+                        }
                     cp_async_wait_all();
                     __syncwarp();
                     if (mine) {
                         float vr, vi, wr = 0.f, wi = 0.f;
-                        interp3f_one<PS, PA>(buf, Ls, Lt, Lp, vr, vi);
-                        if (cs_) interp3f_one<PS, PA>(buf + PST, Ls, Lt, Lp, wr, wi);
+                        interp3f_one<PS, PA>(mybuf, Ls, Lt, Lp, vr, vi);
+                        if (cs_) interp3f_one<PS, PA>(mybuf + SLOT, Ls, Lt, Lp, wr, wi);
                         prop_add(a0[qq], a1[qq], cs_, ps_, g, vr, vi, wr, wi);
                     }
                 }
