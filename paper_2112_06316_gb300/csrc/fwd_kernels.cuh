@@ -986,18 +986,31 @@ __device__ __forceinline__ C cconj_mul(C a, C b) {  // conj(a) * b
     return r;
 }
 
-// Per-entry data staged in shared memory by the anterpolation kernel.
+// Per-entry data staged in shared memory by the anterpolation kernel: the angular
+// basis values and, per factor, the radial basis values times the entry's complex
+// weight (sv[f][a] = Ls[a] v_f).  Rows padded so that vector loads stay aligned.
 template <typename T, int PS, int PA>
-struct AntEntry {
-    T Ls[PS], Lt[PA], Lp[PA];
-    typename CT<T>::c v[2];
+struct __align__(16) AntEntry {
+    static constexpr int PAP = (PA + 3) & ~3, PSP = (PS + 1) & ~1;
+    T Lt[PAP], Lp[PAP];
+    typename CT<T>::c sv[2][PSP];
+};
+
+// Columns c of one output row (factor, b) that an anterpolation thread owns: four or
+// two consecutive ones in FP32 when Pang allows it, one otherwise.
+template <int PA, bool MX>
+struct AntCols {
+    static constexpr int CQ = !MX ? 1 : (PA % 4 == 0 ? 4 : (PA % 2 == 0 ? 2 : 1));
 };
 
 // Anterpolation into the relevant cones of level d (transpose of K2 and K3):
 // G_d[rc] = sum over its cousin targets of L(t) conj(E) g  +  sum over parent
-// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  One block per rc.
+// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  One block per rc.  The
+// FP32 version keeps six blocks per SM (at most 80 registers): the entry set-up
+// chases dependent loads, and that occupancy hides them better than the extra
+// registers of an uncapped build would pay back.
 template <int PS, int PA, bool MX>
-__global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD, int has_parent,
+__global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD, int has_parent,
                                               const long long *__restrict__ ad_start, const int *__restrict__ ad_list,
                                               ChebTab tb, const void *gs_, const void *Gp_, void *Gc_) {
     typedef typename std::conditional<MX, float, double>::type T;
@@ -1006,33 +1019,44 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
     const C *gs = (const C *)gs_;
     const C *Gp = (const C *)Gp_;
     C *Gc = (C *)Gc_;
-    __shared__ AntEntry<T, PS, PA> ent[128];
-    __shared__ C part[128][PS];  // partial sums of the entry groups
+    constexpr int CQ = AntCols<PA, MX>::CQ, PAQ = PA / CQ;
+    typedef AntEntry<T, PS, PA> Ent;
+    // the entries of one batch, and after the last batch the partial sums of the entry groups
+    union Stage {
+        Ent ent[128];
+        C part[128][CQ * PS];
+    };
+    __shared__ Stage sh;
     const int rc = blockIdx.x;
     const int cbox = L.rc_box[rc];
     const long long e0 = ad_start[rc], e1 = ad_start[rc + 1];
     const int nfac = L.nfac;
     const bool csplit = L.split != 0, psplit = has_parent && Pl.split != 0;
-    // accumulation: thread = (factor, b, c) of the output cone, all PS radial nodes (a, b, c); the
-    // ng = 128 / (nfac PA^2) groups of such threads take every ng-th entry and are summed at the end
-    const int unit = threadIdx.x, nout = nfac * PA2, ng = 128 / nout;
+    // accumulation: thread = (factor, b, CQ consecutive c) of the output cone, all PS radial nodes
+    // (a, b, c); the ng = 128 / (nfac PA PA / CQ) groups of such threads take every ng-th entry and
+    // are summed at the end
+    const int unit = threadIdx.x, nout = nfac * PA * PAQ, ng = 128 / nout;
     const int eg = unit / nout, uo = unit % nout;
     const bool active = eg < ng;
-    const int fac = uo / PA2, bc = uo % PA2;
-    const int ub = bc / PA, uc = bc % PA;
+    const int fac = uo / (PA * PAQ), rb = uo % (PA * PAQ);
+    const int ub = rb / PAQ, uc0 = (rb % PAQ) * CQ;
     for (int q = 0; q < ca.nrhs; q++) {
-        C acc[PS];
+        C acc[CQ][PS];
 #pragma unroll
-        for (int a = 0; a < PS; a++) acc[a].x = acc[a].y = T(0);
+        for (int j = 0; j < CQ; j++)
+#pragma unroll
+            for (int a = 0; a < PS; a++) acc[j][a].x = acc[j][a].y = T(0);
+        int ev_next = e0 + threadIdx.x < e1 ? ad_list[e0 + threadIdx.x] : 0;
         for (long long base = e0; base < e1; base += 128) {
             const long long e = base + threadIdx.x;
-            AntEntry<T, PS, PA> &me = ent[threadIdx.x];
+            const int ev = ev_next;
+            if (e + 128 < e1) ev_next = ad_list[e + 128];  // next batch's entry, in flight during this one
+            Ent &me = sh.ent[threadIdx.x];
             T t3[3] = {T(0), T(0), T(0)};
             C v0, v1;
             v0.x = v0.y = v1.x = v1.y = T(0);
             int cone_got = L.rc_cone[rc];
             if (e < e1) {
-                const int ev = ad_list[e];
                 if (ev < ca.N) {  // cousin target
                     const int i = ev;
                     const C g = gs[(long long)q * ca.N + i];
@@ -1168,46 +1192,85 @@ __global__ void __launch_bounds__(128) k_ant(CommonArgs ca, LevelArgs L, LevelAr
                     if (q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
                 }
             }
-            lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs,
-                            me.Ls);
-            lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca,
-                            me.Lt);
-            lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca,
-                            me.Lp);
-            me.v[0] = v0;
-            me.v[1] = v1;
+            {
+                T Ls[PS];
+                lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs,
+                                MX ? (const T *)tb.fcs : (const T *)tb.cs, Ls);
+                lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa,
+                                MX ? (const T *)tb.fca : (const T *)tb.ca, me.Lt);
+                lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa,
+                                MX ? (const T *)tb.fca : (const T *)tb.ca, me.Lp);
+#pragma unroll
+                for (int a = 0; a < PS; a++) {
+                    C z;
+                    z.x = Ls[a] * v0.x;
+                    z.y = Ls[a] * v0.y;
+                    me.sv[0][a] = z;
+                }
+                if (csplit) {
+#pragma unroll
+                    for (int a = 0; a < PS; a++) {
+                        C z;
+                        z.x = Ls[a] * v1.x;
+                        z.y = Ls[a] * v1.y;
+                        me.sv[1][a] = z;
+                    }
+                }
+            }
             __syncthreads();
             if (active) {
                 const int cnt = (int)min((long long)128, e1 - base);
                 for (int t = eg; t < cnt; t += ng) {
-                    const AntEntry<T, PS, PA> &en = ent[t];
-                    const T w = en.Lt[ub] * en.Lp[uc];
-                    const C v = en.v[fac];
-                    const T zr = w * v.x, zi = w * v.y;
+                    const Ent &en = sh.ent[t];
+                    const T lt = en.Lt[ub];
+                    T lp[CQ];
+                    if constexpr (CQ == 4) {
+                        const float4 l4 = *reinterpret_cast<const float4 *>(&en.Lp[uc0]);
+                        lp[0] = l4.x; lp[1] = l4.y; lp[2] = l4.z; lp[3] = l4.w;
+                    } else if constexpr (CQ == 2) {
+                        const float2 l2 = *reinterpret_cast<const float2 *>(&en.Lp[uc0]);
+                        lp[0] = l2.x; lp[1] = l2.y;
+                    } else {
+                        lp[0] = en.Lp[uc0];
+                    }
+                    C sv[PS];
 #pragma unroll
-                    for (int a = 0; a < PS; a++) {
-                        acc[a].x = fma(en.Ls[a], zr, acc[a].x);
-                        acc[a].y = fma(en.Ls[a], zi, acc[a].y);
+                    for (int a = 0; a < PS; a++) sv[a] = en.sv[fac][a];
+#pragma unroll
+                    for (int j = 0; j < CQ; j++) {
+                        const T w = lt * lp[j];
+#pragma unroll
+                        for (int a = 0; a < PS; a++) {
+                            acc[j][a].x = fma(w, sv[a].x, acc[j][a].x);
+                            acc[j][a].y = fma(w, sv[a].y, acc[j][a].y);
+                        }
                     }
                 }
             }
             __syncthreads();
         }
+        // the loop's last barrier ends every read of the entries: the union's partial sums reuse them
         if (active && eg > 0) {
 #pragma unroll
-            for (int a = 0; a < PS; a++) part[unit][a] = acc[a];
+            for (int j = 0; j < CQ; j++)
+#pragma unroll
+                for (int a = 0; a < PS; a++) sh.part[unit][j * PS + a] = acc[j][a];
         }
         __syncthreads();
         if (active && eg == 0) {
             for (int g2 = 1; g2 < ng; g2++)
 #pragma unroll
-                for (int a = 0; a < PS; a++) {
-                    acc[a].x += part[g2 * nout + uo][a].x;
-                    acc[a].y += part[g2 * nout + uo][a].y;
-                }
-            C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + bc;
+                for (int j = 0; j < CQ; j++)
 #pragma unroll
-            for (int a = 0; a < PS; a++) out[a * PA2] = acc[a];
+                    for (int a = 0; a < PS; a++) {
+                        acc[j][a].x += sh.part[g2 * nout + uo][j * PS + a].x;
+                        acc[j][a].y += sh.part[g2 * nout + uo][j * PS + a].y;
+                    }
+            C *out = Gc + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + ub * PA + uc0;
+#pragma unroll
+            for (int j = 0; j < CQ; j++)
+#pragma unroll
+                for (int a = 0; a < PS; a++) out[a * PA2 + j] = acc[j][a];
         }
         __syncthreads();
     }
@@ -1293,14 +1356,17 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
 
 // Transposed leaf evaluation (mixed), warp-cooperative: one warp per chunk of at
 // most 32 sources of one leaf box (the level-D cousin chunks).  For 32 nodes of a
-// relevant cone at a time each lane computes one node's direction and loads its
-// cone values once; the warp then walks the 32 nodes with shuffles, every lane
-// evaluating conj(W(x_node, y_j)) G for its source.
+// relevant cone at a time each lane computes one node's direction, 1/r and scale
+// and loads its cone values once into the warp's shared-memory slots; the warp
+// then walks the 32 nodes with broadcast loads, every lane evaluating
+// conj(W(x_node, y_j)) G for its source.
 template <int PS, int PA, bool SPLIT>
 __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, const int4 *__restrict__ chunks,
                                                     int nchunk, ChebTab tb, const float2 *__restrict__ G,
                                                     float2 *__restrict__ bo) {
     constexpr int P = PS * PA * PA;
+    __shared__ float4 s_dir[4][32];  // (u0, u1, u2, 1/r) per node, r in leaf units
+    __shared__ float4 s_g[4][32];    // (G0, G1) per node; G1 = (s/h, 0) when the factor is combined
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x * (blockDim.x >> 5) + warp;
     if (ch >= nchunk) return;  // warp-uniform
@@ -1320,18 +1386,26 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
             const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
             for (int n0 = 0; n0 < P; n0 += 32) {
                 const int n = min(n0 + lane, P - 1);
-                float sl, ul[3];
-                node32<PS, PA>(L, tb, cone, n, sl, ul);
-                const float2 gl0 = G[gb * ca.Pstride + n];
-                float2 gl1 = make_float2(0.f, 0.f);
-                if (SPLIT) gl1 = G[(gb + 1) * ca.Pstride + n];
+                {
+                    float sl, ul[3];
+                    node32<PS, PA>(L, tb, cone, n, sl, ul);
+                    const float2 gl0 = G[gb * ca.Pstride + n];
+                    const float irl = sl / hu;  // 1 / r (leaf units)
+                    float2 gl1;
+                    if (SPLIT)
+                        gl1 = G[(gb + 1) * ca.Pstride + n];
+                    else
+                        gl1 = make_float2(irl / hd, 0.f);  // s / h (absolute)
+                    __syncwarp();  // the previous batch's reads are done
+                    s_dir[warp][lane] = make_float4(ul[0], ul[1], ul[2], irl);
+                    s_g[warp][lane] = make_float4(gl0.x, gl0.y, gl1.x, gl1.y);
+                    __syncwarp();
+                }
                 const int cnt = min(32, P - n0);
                 for (int k = 0; k < cnt; k++) {
-                    const float s = __shfl_sync(0xffffffffu, sl, k);
-                    const float u0 = __shfl_sync(0xffffffffu, ul[0], k), u1 = __shfl_sync(0xffffffffu, ul[1], k),
-                                u2 = __shfl_sync(0xffffffffu, ul[2], k);
-                    const float g0x = __shfl_sync(0xffffffffu, gl0.x, k), g0y = __shfl_sync(0xffffffffu, gl0.y, k);
-                    const float ir = s / hu;  // 1 / r (leaf units)
+                    const float4 dk = s_dir[warp][k], gk = s_g[warp][k];
+                    const float u0 = dk.x, u1 = dk.y, u2 = dk.z, ir = dk.w;
+                    const float g0x = gk.x, g0y = gk.y;
                     const float dv0 = u0 - fj.x * ir, dv1 = u1 - fj.y * ir, dv2 = u2 - fj.z * ir;
                     const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
                     const float ia = rsqrtf(a2), am = a2 * ia;
@@ -1343,12 +1417,12 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
                     const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
                     const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
                     if (SPLIT) {
-                        const float g1x = __shfl_sync(0xffffffffu, gl1.x, k), g1y = __shfl_sync(0xffffffffu, gl1.y, k);
+                        const float g1x = gk.z, g1y = gk.w;
                         const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
                         acc.add(W0r * g0x + W0i * g0y + W1r * g1x + W1i * g1y,
                                 W0r * g0y - W0i * g0x + W1r * g1y - W1i * g1x);
                     } else {
-                        const float soh = ir / hd;  // s / h (absolute)
+                        const float soh = gk.z;
                         const float W0r = cs * soh * w2 + sn * g, W0i = sn * soh * w2 - cs * g;
                         acc.add(W0r * g0x + W0i * g0y, W0r * g0y - W0i * g0x);  // conj(W) G
                     }

@@ -60,6 +60,22 @@ def test_dot_product_identity_fp64(B, oracle_lib, fm):
     assert plan.missed_lookups() == 0
 
 
+@pytest.mark.parametrize("orders", [(3, 5), (4, 6), (5, 8)])
+@pytest.mark.parametrize("fm", [0, 1, 2])
+def test_mixed_adjoint_orders_and_factors(B, orders, fm):
+    """The FP32 anterpolation owns one (Pang odd), two (Pang = 6) or four (Pang = 8) output
+    columns per thread, with one or two factors per cone: each layout, two right-hand
+    sides, matches the FP64 adjoint (which the oracle pins above and below)."""
+    s, k = sphere_workload(48, 6, 4.0)
+    plan = B.Plan(s.points, s.normals, s.weights,
+                  B.Params(k=k, Ps=orders[0], Pang=orders[1], levels=4, factor_mode=fm))
+    g = random_density(s.N, 2, 4)
+    a64 = plan.adjoint(cu(g)).cpu().numpy()
+    a32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
+    assert rel(a32, a64) < 1e-5
+    assert plan.missed_lookups() == 0
+
+
 def test_adjoint_matches_oracle_matrix_transpose(B, oracle_lib):
     """Tiny 4-level surface: the oracle's Algorithm 1 applied to every unit vector gives
     the discrete IFGF matrix M; the GPU adjoint must equal M^H g."""
