@@ -14,13 +14,13 @@ template <int PS, int PA>
 ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec, cudaStream_t s, void *gs, void *bws,
                           void **G);
 template <int PS, int PA>
-ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
                      long long *nparts);
 #define IFGF_EXTERN(a, b)                                                                                           \
     extern template ifgf_status run_adjoint_t<a, b>(Plan &, const void *, void *, int, int, cudaStream_t, void *,     \
                                                     void *, void **);                                               \
-    extern template ifgf_status run_dk_t<a, b>(Plan &, int, int, cudaStream_t, const void *, void **, double *,       \
-                                               long long *);
+    extern template ifgf_status run_dk_t<a, b>(Plan &, int, int, cudaStream_t, const void *, void **, void *,         \
+                                               double *, long long *);
 IFGF_EXTERN(3, 5)
 IFGF_EXTERN(4, 6)
 IFGF_EXTERN(5, 7)
@@ -116,10 +116,10 @@ ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, in
     return IFGF_EUNSUPPORTED;
 }
 
-ifgf_status run_dk(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+ifgf_status run_dk(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
                    long long *nparts) {
 #define IFGF_CASE(a, b) \
-    if (p.Ps == a && p.Pang == b) return run_dk_t<a, b>(p, nrhs, prec, s, gs, G, partials, nparts);
+    if (p.Ps == a && p.Pang == b) return run_dk_t<a, b>(p, nrhs, prec, s, gs, G, H, partials, nparts);
     IFGF_CASE(3, 5)
     IFGF_CASE(4, 6)
     IFGF_CASE(5, 7)
@@ -190,20 +190,31 @@ extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, co
     st = apply_correction_adjoint(p, g_dev, gsigma_dev, nrhs, (int)prec, s);
     if (st != IFGF_OK) return st;
     if (!dk_host) return IFGF_OK;
-    long long need = (long long)((p.N + 127) / 128) * (p.D - 1);
-    for (int d = p.D; d >= 3; d--) need += (p.lv[d].nrc * p.P + 127) / 128;
-    double *partials = nullptr;
-    cudaError_t e = cudaMalloc(&partials, sizeof(double) * (need + 1));
-    if (e != cudaSuccess) return cuda_fail(e, "vjp partial sums");
+    // partial sums: near field, one reduction per level, leaf; scratch H for the largest level
+    long long need = (p.N + 127) / 128 + (long long)kDkDotBlocks * (p.D - 2) + (p.lv[p.D].nrc * p.P + 127) / 128;
+    size_t hbytes = 0;
+    for (int d = 3; d <= p.D; d++)
+        hbytes = std::max(hbytes, (prec == IFGF_FP64 ? 16 : 8) * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
+    hbytes = (hbytes + 255) & ~(size_t)255;
+    const size_t bytes = hbytes + sizeof(double) * (need + 1);
+    if (bytes > p.dk_ws_bytes) {
+        if (p.dk_ws) cudaFree(p.dk_ws);
+        p.dk_ws = nullptr;
+        p.dk_ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&p.dk_ws, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "k-gradient workspace");
+        p.dk_ws_bytes = bytes;
+    }
+    void *H = p.dk_ws;
+    double *partials = (double *)((char *)p.dk_ws + hbytes);
     long long np = 0;
-    st = run_dk(p, nrhs, (int)prec, s, gs, G, partials, &np);
+    st = run_dk(p, nrhs, (int)prec, s, gs, G, H, partials, &np);
     std::vector<double> h(np > 0 ? np : 1, 0.0);
     if (st == IFGF_OK && np > 0) {
-        e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "vjp partial copy");
     }
-    cudaFree(partials);
     if (st != IFGF_OK) return st;
     double sum = 0.0;
     for (long long i = 0; i < np; i++) sum += h[i];

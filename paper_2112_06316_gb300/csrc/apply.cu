@@ -232,6 +232,9 @@ void free_plan_device(Plan &p) {
     if (p.adj_ws) cudaFree(p.adj_ws);
     p.adj_ws = nullptr;
     p.adj_ws_bytes = 0;
+    if (p.dk_ws) cudaFree(p.dk_ws);
+    p.dk_ws = nullptr;
+    p.dk_ws_bytes = 0;
     for (int i = 0; i < Plan::kMaxEv; i++)
         if (p.ev[i]) {
             cudaEventDestroy(p.ev[i]);

@@ -1005,11 +1005,14 @@ struct AntCols {
 
 // Anterpolation into the relevant cones of level d (transpose of K2 and K3):
 // G_d[rc] = sum over its cousin targets of L(t) conj(E) g  +  sum over parent
-// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  One block per rc.  The
+// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  With DK every entry's
+// weight is scaled by -i rho, rho = r (cousin target) or r_c - r_p (parent node):
+// the k-derivative of E and of the ratio, so that Re <H_d, F_d> is the
+// k-derivative of the level's cousin and propagation terms.  One block per rc.  The
 // FP32 version keeps six blocks per SM (at most 80 registers): the entry set-up
 // chases dependent loads, and that occupancy hides them better than the extra
 // registers of an uncapped build would pay back.
-template <int PS, int PA, bool MX>
+template <int PS, int PA, bool MX, bool DK>
 __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD, int has_parent,
                                               const long long *__restrict__ ad_start, const int *__restrict__ ad_list,
                                               ChebTab tb, const void *gs_, const void *Gp_, void *Gc_) {
@@ -1056,6 +1059,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
             C v0, v1;
             v0.x = v0.y = v1.x = v1.y = T(0);
             int cone_got = L.rc_cone[rc];
+            T rho = T(0);  // k-derivative factor of the entry's weight (DK)
             if (e < e1) {
                 if (ev < ca.N) {  // cousin target
                     const int i = ev;
@@ -1079,6 +1083,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         Er = c4 * cs;
                         Ei = c4 * sn;
                         ir_abs = 1.f / (r * ca.HDf);
+                        rho = r * ca.HDf;
                     } else {
                         double y0[3];
                         center64(ca, L, cbox, y0);
@@ -1092,6 +1097,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         Er = c4 * cs;
                         Ei = c4 * sn;
                         ir_abs = 1.0 / r;
+                        rho = r;
                     }
                     C E;
                     E.x = Er;
@@ -1134,6 +1140,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         r1r = cs * g1;
                         r1i = sn * g1;
                         irabs = 1.f / (rcv * ca.HDf);
+                        rho = dr * ca.HDf;
                     } else {
                         double s, u[3];
                         node64<PS, PA>(Pl, tb, Pl.rc_cone[rcp], n, s, u);
@@ -1151,6 +1158,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         r1r = cs * g1;
                         r1i = sn * g1;
                         irabs = 1.0 / rcv;
+                        rho = rcv - rp;
                     }
                     C ratio1;
                     ratio1.x = r1r;
@@ -1176,6 +1184,13 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         v0 = cconj_mul(ratio1, gp0);
                     }
                 }
+                if constexpr (DK) {  // (-i rho) v
+                    const C w0 = v0, w1 = v1;
+                    v0.x = rho * w0.y;
+                    v0.y = -rho * w0.x;
+                    v1.x = rho * w1.y;
+                    v1.y = -rho * w1.x;
+                }
                 // express the local coordinates in the list's cone (an FP32 classification can land
                 // in a neighbouring cone near a boundary): t' = t + 2 (i_got - i_list), phi wrapping
                 const int cl = L.rc_cone[rc];
@@ -1189,7 +1204,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                     t3[1] += T(2 * (itg - itl));
                     t3[2] += T(2 * dp);
                     const T lim = T(1.02);
-                    if (q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
+                    if (!DK && q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
                 }
             }
             {
@@ -1591,6 +1606,22 @@ __device__ __forceinline__ double re_conj_mul(C a, C b) {
     return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
 }
 
+// Re <H, F> over the cone values of one level (both stored [nrhs][nrc][nfac][Pstride],
+// nodes n < P only); grid-stride over kDkDotBlocks blocks, one double per block.
+template <typename C>
+__global__ void __launch_bounds__(128) k_dot_re(const C *__restrict__ H, const C *__restrict__ F, long long rows,
+                                                int P, int Pstride, double *partials) {
+    double acc = 0.0;
+    const long long tot = rows * P;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / P, n = t % P;
+        const C h = H[row * Pstride + n], f = F[row * Pstride + n];
+        acc += (double)h.x * (double)f.x + (double)h.y * (double)f.y;
+    }
+    block_sum_store(acc, partials);
+}
+
 // near field: sum_i conj(g_i) sum_j dK/dk(x_i, x_j) a_j,  dK/dk = i r K - i E1 dn / r
 template <bool MX>
 __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, const void *a_, const void *gs_,
@@ -1651,160 +1682,6 @@ __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, con
             z.x = sr;
             z.y = si;
             acc += re_conj_mul(gs[(long long)q * ca.N + i], z);
-        }
-    }
-    block_sum_store(acc, partials);
-}
-
-// cousin interpolation at level d: sum_i conj(g_i) sum_c i r E Interp(F_c)(x_i)
-template <int PS, int PA, bool MX>
-__global__ void __launch_bounds__(128) k_dk_cousin(CommonArgs ca, LevelArgs L, LevelArgs LD, const int *__restrict__ box_of,
-                                                   ChebTab tb, const void *F_, const void *gs_, double *partials) {
-    typedef typename std::conditional<MX, float, double>::type T;
-    typedef typename CT<T>::c C;
-    const C *F = (const C *)F_;
-    const C *gs = (const C *)gs_;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc = 0.0;
-    if (i < ca.N) {
-        const int b = box_of[i];
-        for (int q = 0; q < ca.nrhs; q++) {
-            T sr = T(0), si = T(0);
-            for (int ci = L.co_start[b]; ci < L.co_start[b + 1]; ci++) {
-                const int c = L.co_list[ci];
-                T Er, Ei, irabs, t3[3];
-                int rc;
-                if constexpr (MX) {
-                    const int bl = ca.leaf_of[i];
-                    const float I0[3] = {LD.ijk[3 * bl] + 0.5f, LD.ijk[3 * bl + 1] + 0.5f, LD.ijk[3 * bl + 2] + 0.5f};
-                    const float f0[3] = {ca.f32[3 * i], ca.f32[3 * i + 1], ca.f32[3 * i + 2]};
-                    CousGeo g;
-                    cousin_geo32(ca, L, c, I0, f0, g);
-                    rc = g.rc;
-                    Er = g.E1r; Ei = g.E1i; irabs = g.irabs;
-                    t3[0] = g.t3[0]; t3[1] = g.t3[1]; t3[2] = g.t3[2];
-                } else {
-                    double y0[3], r;
-                    center64(ca, L, c, y0);
-                    const int cone = classify64(L, ca.x64[3 * i] - y0[0], ca.x64[3 * i + 1] - y0[1],
-                                                ca.x64[3 * i + 2] - y0[2], r, t3);
-                    rc = L.cone_map[(long long)c * L.ncone + cone];
-                    double sn, cs;
-                    sincos(ca.k * r, &sn, &cs);
-                    Er = cs / (4.0 * kPi * r); Ei = sn / (4.0 * kPi * r);
-                    irabs = 1.0 / r;
-                }
-                if (rc < 0) continue;
-                T Ls[PS], Lt[PA], Lp[PA];
-                lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs, Ls);
-                lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lt);
-                lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lp);
-                const long long base = ((long long)q * L.nrc + rc) * L.nfac;
-                T vr, vi;
-                interp3<PS, PA, T>(F + base * ca.Pstride, Ls, Lt, Lp, vr, vi);
-                if (L.split) {
-                    T wr, wi;
-                    interp3<PS, PA, T>(F + (base + 1) * ca.Pstride, Ls, Lt, Lp, wr, wi);
-                    vr = vr * irabs + wr;
-                    vi = vi * irabs + wi;
-                }
-                const T zr = Er * vr - Ei * vi, zi = Er * vi + Ei * vr;
-                const T rabs = T(1) / irabs;
-                sr += -rabs * zi;  // i r z
-                si += rabs * zr;
-            }
-            C z;
-            z.x = sr;
-            z.y = si;
-            acc += re_conj_mul(gs[(long long)q * ca.N + i], z);
-        }
-    }
-    block_sum_store(acc, partials);
-}
-
-// propagation into level d-1: sum_{rcp,n} conj(G_p[n]) sum_children i (r_c - r_p) ratio Interp(F_c)(x_n)
-template <int PS, int PA, bool MX>
-__global__ void __launch_bounds__(128) k_dk_prop(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb, const void *F_,
-                                                 const void *Gp_, double *partials) {
-    typedef typename std::conditional<MX, float, double>::type T;
-    typedef typename CT<T>::c Cx;
-    constexpr int P = PS * PA * PA;
-    const Cx *FC = (const Cx *)F_;
-    const Cx *Gp = (const Cx *)Gp_;
-    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    double acc = 0.0;
-    if (tid < Pl.nrc * P) {
-        const int rc = (int)(tid / P), n = (int)(tid % P);
-        const int pb = Pl.rc_box[rc];
-        for (int q = 0; q < ca.nrhs; q++) {
-            T s0r = T(0), s0i = T(0), s1r = T(0), s1i = T(0);  // per parent factor
-            for (int ci = Pl.ch_start[pb]; ci < Pl.ch_start[pb + 1]; ci++) {
-                const int cb = Pl.ch_list[ci];
-                T t3[3], r1r, r1i, g1, irabs, dr_abs;
-                int crc;
-                if constexpr (MX) {
-                    float s, u[3];
-                    node32<PS, PA>(Pl, tb, Pl.rc_cone[rc], n, s, u);
-                    const float rp = Pl.hu / s;
-                    const float nv[3] = {rp * u[0], rp * u[1], rp * u[2]};
-                    const float o0 = (C.ijk[3 * cb] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
-                    const float o1 = (C.ijk[3 * cb + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
-                    const float o2 = (C.ijk[3 * cb + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
-                    PropGeo g;
-                    prop_geo32(ca, C, cb, nv, rp, o0, o1, o2, g);
-                    crc = g.crc;
-                    t3[0] = g.t3[0]; t3[1] = g.t3[1]; t3[2] = g.t3[2];
-                    r1r = g.r1r; r1i = g.r1i; g1 = g.g1; irabs = g.irabs;
-                    const float p0 = nv[0] - o0, p1 = nv[1] - o1, p2 = nv[2] - o2;
-                    const float rcv = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
-                    const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
-                    dr_abs = (oo - 2.f * no) / (rcv + rp) * ca.HDf;
-                } else {
-                    double s, u[3], yp[3], yc[3];
-                    node64<PS, PA>(Pl, tb, Pl.rc_cone[rc], n, s, u);
-                    center64(ca, Pl, pb, yp);
-                    center64(ca, C, cb, yc);
-                    const double rp = Pl.h / s;
-                    const double x[3] = {yp[0] + rp * u[0], yp[1] + rp * u[1], yp[2] + rp * u[2]};
-                    double rcv;
-                    const int cone = classify64(C, x[0] - yc[0], x[1] - yc[1], x[2] - yc[2], rcv, t3);
-                    crc = C.cone_map[(long long)cb * C.ncone + cone];
-                    double sn, cs;
-                    sincos(ca.k * (rcv - rp), &sn, &cs);
-                    g1 = rp / rcv;
-                    r1r = cs * g1; r1i = sn * g1;
-                    irabs = 1.0 / rcv;
-                    dr_abs = rcv - rp;
-                }
-                if (crc < 0) continue;
-                T Ls[PS], Lt[PA], Lp[PA];
-                lagrange<PS, T>(t3[0], MX ? (const T *)tb.fxs : (const T *)tb.xs, MX ? (const T *)tb.fcs : (const T *)tb.cs, Ls);
-                lagrange<PA, T>(t3[1], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lt);
-                lagrange<PA, T>(t3[2], MX ? (const T *)tb.fxa : (const T *)tb.xa, MX ? (const T *)tb.fca : (const T *)tb.ca, Lp);
-                const long long base = ((long long)q * C.nrc + crc) * C.nfac;
-                T vr, vi, wr = T(0), wi = T(0);
-                interp3<PS, PA, T>(FC + base * ca.Pstride, Ls, Lt, Lp, vr, vi);
-                if (C.split) interp3<PS, PA, T>(FC + (base + 1) * ca.Pstride, Ls, Lt, Lp, wr, wi);
-                // contributions z0 (parent factor 0) and z1 (parent factor 1), then multiply by i dr
-                T z0r, z0i, z1r = T(0), z1i = T(0);
-                if (C.split && Pl.split) {
-                    const T r2r = r1r * g1, r2i = r1i * g1;
-                    z0r = vr * r2r - vi * r2i; z0i = vr * r2i + vi * r2r;
-                    z1r = wr * r1r - wi * r1i; z1i = wr * r1i + wi * r1r;
-                } else if (C.split) {
-                    const T xr = vr * irabs + wr, xi = vi * irabs + wi;
-                    z0r = xr * r1r - xi * r1i; z0i = xr * r1i + xi * r1r;
-                } else {
-                    z0r = vr * r1r - vi * r1i; z0i = vr * r1i + vi * r1r;
-                }
-                s0r += -dr_abs * z0i; s0i += dr_abs * z0r;
-                s1r += -dr_abs * z1i; s1i += dr_abs * z1r;
-            }
-            const long long pbase = ((long long)q * Pl.nrc + rc) * Pl.nfac;
-            Cx z0, z1;
-            z0.x = s0r; z0.y = s0i; z1.x = s1r; z1.y = s1i;
-            acc += re_conj_mul(Gp[pbase * ca.Pstride + n], z0);
-            if (Pl.split) acc += re_conj_mul(Gp[(pbase + 1) * ca.Pstride + n], z1);
         }
     }
     block_sum_store(acc, partials);
@@ -3035,7 +2912,7 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         prof_mark(p, s, kStGather, 0);
         for (int d = 3; d <= D; d++)
             if (L[d].nrc) {
-                k_ant<PS, PA, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
+                k_ant<PS, PA, false, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
                                                                        (const long long *)p.d_ad_start[d], p.d_ad_list[d],
                                                                        tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
                 prof_mark(p, s, kStCousin, d);
@@ -3054,7 +2931,7 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         prof_mark(p, s, kStGather, 0);
         for (int d = 3; d <= D; d++)
             if (L[d].nrc) {
-                k_ant<PS, PA, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
+                k_ant<PS, PA, true, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
                                                                       (const long long *)p.d_ad_start[d], p.d_ad_list[d],
                                                                       tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
                 prof_mark(p, s, kStCousin, d);
@@ -3085,7 +2962,7 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
 // k-derivative reductions (forward state in p.ws, adjoint state gs / G)
 // ============================================================================
 template <int PS, int PA>
-ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
                      long long *nparts) {
     constexpr int P = PS * PA * PA;
     const int D = p.D;
@@ -3099,21 +2976,25 @@ ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs
     if (mx) k_dk_near<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
     else k_dk_near<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
     off += nblk(N);
-    for (int d = D; d >= 3; d--) {
-        if (mx) k_dk_cousin<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb, p.ws.F[d], gs,
-                                                                    partials + off);
-        else k_dk_cousin<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[d], L[D], p.d_box_of[d], tb, p.ws.F[d], gs,
-                                                                   partials + off);
-        off += nblk(N);
-    }
-    for (int d = D; d >= 4; d--) {
-        const long long nt = L[d - 1].nrc * P;
-        if (!nt) continue;
-        if (mx) k_dk_prop<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb, p.ws.F[d], G[d - 1],
-                                                                   partials + off);
-        else k_dk_prop<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb, p.ws.F[d], G[d - 1],
-                                                                  partials + off);
-        off += nblk(nt);
+    // cousin interpolation and propagation of level d: anterpolation with k-derivative
+    // weights into H, then Re <H, F_d>
+    for (int d = 3; d <= D; d++) {
+        if (!L[d].nrc) continue;
+        const long long rows = (long long)nrhs * L[d].nrc * L[d].nfac;
+        if (mx) {
+            k_ant<PS, PA, true, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, (const long long *)p.d_ad_start[d], p.d_ad_list[d],
+                tb, gs, d > 3 ? G[d - 1] : nullptr, H);
+            k_dot_re<float2><<<kDkDotBlocks, kBlock, 0, s>>>((const float2 *)H, (const float2 *)p.ws.F[d], rows, P,
+                                                          p.Pstride, partials + off);
+        } else {
+            k_ant<PS, PA, false, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, (const long long *)p.d_ad_start[d], p.d_ad_list[d],
+                tb, gs, d > 3 ? G[d - 1] : nullptr, H);
+            k_dot_re<double2><<<kDkDotBlocks, kBlock, 0, s>>>((const double2 *)H, (const double2 *)p.ws.F[d], rows,
+                                                           P, p.Pstride, partials + off);
+        }
+        off += kDkDotBlocks;
     }
     {
         const long long nt = L[D].nrc * P;

@@ -53,6 +53,7 @@ struct HostLevel {
 // propagation weights depend only on that key — and cut into tiles of up to
 // kTcTile pairs; tiles are ordered by octant so one launch per octant never
 // writes the same parent cone twice.
+constexpr int kDkDotBlocks = 1216;  // blocks of each level's Re <H, F> reduction in the k-gradient (8 per SM)
 constexpr int kTcTile = 64;   // pairs per tile
 constexpr int kTcPairs = 32;  // pairs per block of the warp-level (mma.sync) engine: a tile is two blocks
 struct TcLevel {
@@ -158,6 +159,8 @@ struct Plan {
     float *d_corrT_val32 = nullptr;
     void *adj_ws = nullptr;      // [nrhs][N] gathered g and accumulated b, plus per-level G
     size_t adj_ws_bytes = 0;
+    void *dk_ws = nullptr;       // k-gradient: one level's anterpolated H plus the partial sums
+    size_t dk_ws_bytes = 0;
 
     // bumped whenever device buffers baked into a captured graph may change
     uint64_t gen = 0;

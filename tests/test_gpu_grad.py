@@ -62,9 +62,10 @@ def test_grad_sigma_and_k_vs_finite_differences(B, fm):
     assert abs(fdk - gk) <= 1e-6 * abs(gk), (fdk, gk)
 
 
-def test_vjp_density_part_is_the_adjoint(B):
+@pytest.mark.parametrize("orders", [(3, 5), (5, 8)])
+def test_vjp_density_part_is_the_adjoint(B, orders):
     s, k = sphere_workload(32, 8, 3.0)
-    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k))
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=orders[0], Pang=orders[1]))
     sig = torch.from_numpy(random_density(s.N, 2, 4)).cuda()
     g = torch.from_numpy(random_density(s.N, 2, 5)).cuda()
     gs, dk = plan.vjp(sig, g)
