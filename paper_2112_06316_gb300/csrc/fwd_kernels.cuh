@@ -722,42 +722,60 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Packed two-lane FP32 arithmetic (fma.rn.f32x2, sm_100 and later): one instruction
+// performs the real and imaginary FMAs of a complex value times a real weight, each
+// lane rounded exactly as fmaf.  Halves the issue slots of the interpolation sums.
+__device__ __forceinline__ unsigned long long f2pack(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+// acc += (w, w) * v, lane by lane
+__device__ __forceinline__ void f2fma(unsigned long long &acc, unsigned long long w, unsigned long long v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
+}
+
 template <int PS, int PA>
 __device__ __forceinline__ void interp3f_one(const float2 *f, const float *Ls, const float *Lt, const float *Lp,
                                              float &r, float &i) {
-    r = i = 0.f;
+    unsigned long long lp2[PA], lt2[PA];
+#pragma unroll
+    for (int c = 0; c < PA; c++) {
+        lp2[c] = f2pack(Lp[c], Lp[c]);
+        lt2[c] = f2pack(Lt[c], Lt[c]);
+    }
+    unsigned long long acc = 0ull;  // (0.f, 0.f)
 #pragma unroll 1
     for (int a = 0; a < PS; a++) {
         const float2 *fa = f + a * PA * PA;
-        float ra = 0.f, ia = 0.f;
+        unsigned long long acc_a = 0ull;
 #pragma unroll
         for (int b = 0; b < PA; b++) {
-            float rb = 0.f, ib = 0.f;
+            unsigned long long acc_b = 0ull;
             const float2 *row = fa + b * PA;
             if constexpr (PA % 2 == 0) {
 #pragma unroll
                 for (int c = 0; c < PA; c += 2) {
                     const float4 v = *reinterpret_cast<const float4 *>(row + c);
-                    rb = fmaf(Lp[c], v.x, rb);
-                    ib = fmaf(Lp[c], v.y, ib);
-                    rb = fmaf(Lp[c + 1], v.z, rb);
-                    ib = fmaf(Lp[c + 1], v.w, ib);
+                    f2fma(acc_b, lp2[c], f2pack(v.x, v.y));
+                    f2fma(acc_b, lp2[c + 1], f2pack(v.z, v.w));
                 }
             } else {
 #pragma unroll
                 for (int c = 0; c < PA; c++) {
                     const float2 v = row[c];
-                    rb = fmaf(Lp[c], v.x, rb);
-                    ib = fmaf(Lp[c], v.y, ib);
+                    f2fma(acc_b, lp2[c], f2pack(v.x, v.y));
                 }
             }
-            ra = fmaf(Lt[b], rb, ra);
-            ia = fmaf(Lt[b], ib, ia);
+            f2fma(acc_a, lt2[b], acc_b);
         }
         const float la = pick<PS>(Ls, a);
-        r = fmaf(la, ra, r);
-        i = fmaf(la, ia, i);
+        f2fma(acc, f2pack(la, la), acc_a);
     }
+    f2unpack(acc, r, i);
 }
 
 template <int PS, int PA, int RB>
@@ -996,6 +1014,9 @@ struct __align__(16) AntEntry {
     typename CT<T>::c sv[2][PSP];
 };
 
+// FP32 anterpolation accumulates with the packed two-lane FMA (f2fma).
+constexpr bool kAntPacked = true;
+
 // Columns c of one output row (factor, b) that an anterpolation thread owns: four or
 // two consecutive ones in FP32 when Pang allows it, one otherwise.
 template <int PA, bool MX>
@@ -1045,10 +1066,14 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
     const int ub = rb / PAQ, uc0 = (rb % PAQ) * CQ;
     for (int q = 0; q < ca.nrhs; q++) {
         C acc[CQ][PS];
+        unsigned long long acc2[CQ][PS];  // FP32: packed (re, im) accumulators of f2fma
 #pragma unroll
         for (int j = 0; j < CQ; j++)
 #pragma unroll
-            for (int a = 0; a < PS; a++) acc[j][a].x = acc[j][a].y = T(0);
+            for (int a = 0; a < PS; a++) {
+                acc[j][a].x = acc[j][a].y = T(0);
+                acc2[j][a] = 0ull;
+            }
         int ev_next = e0 + threadIdx.x < e1 ? ad_list[e0 + threadIdx.x] : 0;
         for (long long base = e0; base < e1; base += 128) {
             const long long e = base + threadIdx.x;
@@ -1248,21 +1273,46 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                     } else {
                         lp[0] = en.Lp[uc0];
                     }
-                    C sv[PS];
+                    if constexpr (MX && kAntPacked) {
+                        unsigned long long sv[PS];
+                        const unsigned long long *row = reinterpret_cast<const unsigned long long *>(en.sv[fac]);
 #pragma unroll
-                    for (int a = 0; a < PS; a++) sv[a] = en.sv[fac][a];
+                        for (int a = 0; a < PS; a++) sv[a] = row[a];
 #pragma unroll
-                    for (int j = 0; j < CQ; j++) {
-                        const T w = lt * lp[j];
+                        for (int j = 0; j < CQ; j++) {
+                            const float w = lt * lp[j];
+                            const unsigned long long w2 = f2pack(w, w);
 #pragma unroll
-                        for (int a = 0; a < PS; a++) {
-                            acc[j][a].x = fma(w, sv[a].x, acc[j][a].x);
-                            acc[j][a].y = fma(w, sv[a].y, acc[j][a].y);
+                            for (int a = 0; a < PS; a++) f2fma(acc2[j][a], w2, sv[a]);
+                        }
+                    } else {
+                        C sv[PS];
+#pragma unroll
+                        for (int a = 0; a < PS; a++) sv[a] = en.sv[fac][a];
+#pragma unroll
+                        for (int j = 0; j < CQ; j++) {
+                            const T w = lt * lp[j];
+#pragma unroll
+                            for (int a = 0; a < PS; a++) {
+                                acc[j][a].x = fma(w, sv[a].x, acc[j][a].x);
+                                acc[j][a].y = fma(w, sv[a].y, acc[j][a].y);
+                            }
                         }
                     }
                 }
             }
             __syncthreads();
+        }
+        if constexpr (MX && kAntPacked) {
+#pragma unroll
+            for (int j = 0; j < CQ; j++)
+#pragma unroll
+                for (int a = 0; a < PS; a++) {
+                    float x, y;
+                    f2unpack(acc2[j][a], x, y);
+                    acc[j][a].x = x;
+                    acc[j][a].y = y;
+                }
         }
         // the loop's last barrier ends every read of the entries: the union's partial sums reuse them
         if (active && eg > 0) {
