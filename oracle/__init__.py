@@ -8,6 +8,8 @@ reference legs use this package.  It shares no code with
   Eq. field1 (kernel of Eq. GreenFunction / Eq. double_layer, identity term of
   Eq. CombLayIE) and its conjugate transpose, on all rows or a row subset.
 * ``ifgf``: Algorithm 1 written loop by loop in FP64 (``oracle.c``).
+* ``field`` / ``far_field``: the combined-layer potential of Eq. CombinedLayer at
+  off-surface targets and its far-field pattern (Eq. FarField), plain numpy sums.
 * ``mie``: closed-form sound-soft sphere solutions (module ``oracle.mie``).
 """
 from __future__ import annotations
@@ -318,3 +320,54 @@ def csr_apply(rowptr, col, val, sigma) -> np.ndarray:
         j0, j1 = rp[l], rp[l + 1]
         out[:, l] = s[:, cl[j0:j1]] @ v[j0:j1]
     return out
+
+
+def _root_side(x) -> float:
+    lo, hi = x.min(0), x.max(0)
+    return float((hi - lo).max() * (1 + 2.0 ** -30))
+
+
+def field(points, normals, weights, k, eta, sigma, targets, chunk: int = 256) -> np.ndarray:
+    """Combined-layer potential of Eq. CombinedLayer at arbitrary targets x, discretised with
+    the surface quadrature (the off-surface counterpart of Eq. field1):
+
+        u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m,
+        Phi = e^{ikr} / (4 pi r)                      (Eq. GreenFunction)
+        dPhi/dnu(y) = e^{ikr} (1 - ikr) <x - y, nu(y)> / (4 pi r^3)   (Eq. double_layer)
+
+    Every source is summed (targets are not surface points); a pair closer than 1e-14 times
+    the root-box side contributes 0, the rule of the on-surface sum.  sigma: (nrhs, N);
+    targets: (M, 3); returns (nrhs, M) complex128."""
+    x, nu, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(sigma, N)
+    t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+    tol = 1e-14 * _root_side(x)
+    ws = s * w[None, :]
+    out = np.zeros((s.shape[0], t.shape[0]), dtype=np.complex128)
+    for j0 in range(0, t.shape[0], chunk):
+        d = t[j0:j0 + chunk, None, :] - x[None, :, :]          # x - y, (c, N, 3)
+        r = np.sqrt(np.einsum("cni,cni->cn", d, d))
+        dn = np.einsum("cni,ni->cn", d, nu)                     # <x - y, nu(y)>
+        keep = r >= tol
+        rr = np.where(keep, r, 1.0)
+        e = np.exp(1j * k * rr) / (4.0 * math.pi * rr)
+        K = e * (1.0 - 1j * k * rr) * dn / rr ** 2 - 1j * eta * e
+        K = np.where(keep, K, 0.0)
+        out[:, j0:j0 + chunk] = ws @ K.T
+    return out
+
+
+def far_field(points, normals, weights, k, eta, sigma, xhat) -> np.ndarray:
+    """Far-field pattern of Eq. FarField with the surface quadrature:
+
+        u_inf(xhat) = (1 / 4 pi) sum_m [-i k <xhat, nu_m> - i eta] e^{-i k <xhat, y_m>} w_m sigma_m
+
+    (d/dnu(y) of e^{-ik xhat.y} is -ik xhat.nu(y)).  sigma: (nrhs, N); xhat: (M, 3) directions,
+    used as given; returns (nrhs, M) complex128."""
+    x, nu, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(sigma, N)
+    xh = np.ascontiguousarray(xhat, dtype=np.float64).reshape(-1, 3)
+    K = (-1j * k * (xh @ nu.T) - 1j * eta) * np.exp(-1j * k * (xh @ x.T)) / (4.0 * math.pi)  # (M, N)
+    return (s * w[None, :]) @ K.T

@@ -64,6 +64,19 @@ def far_field(xhat, k: float, d=(0.0, 0.0, 1.0)) -> np.ndarray:
     return (1j / k) * u
 
 
+def scattered_field(x, k: float, d=(0.0, 0.0, 1.0)) -> np.ndarray:
+    """Exact scattered field of the sound-soft unit sphere at exterior points |x| > 1 for
+    incidence e^{i k d.x}: u^s(x) = -sum_n i^n (2n+1) (j_n(k) / h_n(k)) h_n(k|x|) P_n(xhat.d),
+    the outgoing expansion whose boundary values cancel the plane wave's on |x| = 1."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    r = np.linalg.norm(x, axis=1)
+    c = (x / r[:, None]) @ np.asarray(d, dtype=np.float64)
+    u = np.zeros(x.shape[0], dtype=np.complex128)
+    for n in range(_nmax(k) + 1):
+        u -= (1j ** n) * (2 * n + 1) * (spherical_jn(n, k) / hankel1(n, k)) * hankel1(n, k * r) * eval_legendre(n, c)
+    return u
+
+
 def far_field_quadrature(points, normals, weights, phi, k: float, eta: float, xhat) -> np.ndarray:
     """Eq. FarField evaluated with the surface quadrature:
     u_inf(xhat) = (1/4pi) sum_m [-i k (xhat.nu_m) - i eta] exp(-i k xhat.y_m) phi_m w_m."""
