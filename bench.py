@@ -169,11 +169,12 @@ def tf32_peak_tflops():
 
 
 def kernel_source_digest():
-    """sha256 of the CUDA sources; recorded next to ncu traffic so that stale counters are not used."""
+    """sha256 of the sources of the forward apply (its kernels, their instantiations and its host
+    launch code); recorded next to ncu traffic so that stale counters are not used."""
     src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2112_06316_gb300", "csrc")
     h = hashlib.sha256()
     for fn in sorted(os.listdir(src)):
-        if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+        if fn in ("fwd_kernels.cuh", "kernels.cuh", "apply.cu", "ifgf_internal.h") or fn.startswith("inst_"):
             with open(os.path.join(src, fn), "rb") as f:
                 h.update(fn.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
@@ -385,6 +386,25 @@ def run_ours(args):
            "h2d_bytes_per_step": int(hs.numel() * hs.element_size()),
            "d2h_bytes_per_step": int(hy.numel() * hy.element_size())}
 
+    # ---- off-surface evaluation of the same density (mixed): far field on the 200 x 200 direction
+    # grid of Eq. SphereGrid, combined-layer potential on a 200 x 200 plane z = 1.5 (Eq. PlanarGrid) ----
+    pol, az = np.meshgrid(np.linspace(0.0, math.pi, 200), np.linspace(0.0, 2 * math.pi, 200), indexing="ij")
+    xh = torch.from_numpy(np.stack([np.sin(pol) * np.cos(az), np.sin(pol) * np.sin(az), np.cos(pol)],
+                                   -1).reshape(-1, 3)).to(dev)
+    gx, gy = np.meshgrid(np.linspace(-3.0, 3.0, 200), np.linspace(-3.0, 3.0, 200), indexing="ij")
+    plane = torch.from_numpy(np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, 1.5)], -1)).to(dev)
+    ff = torch.empty((nrhs, xh.shape[0]), dtype=torch.complex64, device=dev)
+    nf = torch.empty((nrhs, plane.shape[0]), dtype=torch.complex64, device=dev)
+    k_off = max(3, args.steps // 10)
+    t_ff = float(np.mean(timed(lambda: plan.far_field(sig32, xh, out=ff), k_off, 2)))
+    t_nf = float(np.mean(timed(lambda: plan.field(sig32, plane, out=nf), k_off, 2)))
+    off_surface = {
+        "far_field": {"targets": int(xh.shape[0]), "ms_per_step": t_ff,
+                      "Gpairs_per_s": N * nrhs * xh.shape[0] / (t_ff * 1e6)},
+        "plane_potential": {"targets": int(plane.shape[0]), "ms_per_step": t_nf,
+                            "Gpairs_per_s": N * nrhs * plane.shape[0] / (t_nf * 1e6)},
+        "note": "direct sums over all N sources (ifgf_far_field, ifgf_field), mixed precision"}
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -395,9 +415,11 @@ def run_ours(args):
                                   f"nrhs={nrhs}",
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
-           "roofline": roofline, "e2e": e2e, "adjoint": adjoint,
+           "roofline": roofline, "e2e": e2e, "adjoint": adjoint, "off_surface": off_surface,
            "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
-           "gpu_launches": launches_per_apply * args.steps + len(adj_stages) * max(3, args.steps // 4),
+           # gather, sum and (when the sources are split into chunks) the reduction per off-surface call
+           "gpu_launches": launches_per_apply * args.steps + len(adj_stages) * max(3, args.steps // 4)
+                           + 2 * 3 * k_off,
            "clocks": clk}
 
     if not args.quick:

@@ -218,6 +218,43 @@ ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev, void *y_d
 ifgf_status ifgf_gmres(ifgf_plan *plan, const void *rhs_dev, void *x_dev, int restart, int maxit, double tol,
                        ifgf_precision apply_prec, int *iters, double *resid_hist, void *stream);
 
+/* ---- evaluation off the surface (Section 5: fields from a solved density) ----
+ * Direct sums over every quadrature point of the plan (all N sources, in
+ * O(N * M) work), one GPU thread per target; the interpolation orders of the plan
+ * play no part.  sigma_dev is the density in the caller's point order, as for
+ * ifgf_apply (device, N x nrhs column-major: complex128 for IFGF_FP64, complex64
+ * for IFGF_MIXED); out_dev receives M x nrhs values column-major (out[q*M + j]),
+ * same complex type.  Targets are device FP64 arrays of M x 3 (x0,y0,z0,x1,...)
+ * and are used as given (non-finite values give non-finite results).
+ * Asynchronous on `stream`.  The first call for a given (M, nrhs, precision)
+ * size may grow a plan-owned device scratch buffer (w*sigma in Morton order and,
+ * when the targets alone do not fill the GPU, per-chunk partial sums that a
+ * second kernel adds in a fixed order, so results are deterministic).
+ * Errors: IFGF_EINVAL (null plan, nrhs < 0, M < 0 or M >= 2^31 - 128, null or
+ * aliasing pointers with M, nrhs > 0, unknown precision), IFGF_ENOMEM, IFGF_ECUDA.
+ * M = 0 or nrhs = 0 returns IFGF_OK without work. */
+
+/* Combined-layer potential of Eq. CombinedLayer at targets x_j off the surface
+ * (for example the planar grids of Eq. PlanarGrid):
+ *   u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m
+ * with Phi of Eq. GreenFunction and dPhi/dnu of Eq. double_layer, eta = the plan's
+ * coupling.  Targets are meant to lie off the surface: in FP64 a pair closer than
+ * 1e-14 times the root-box side contributes 0 (the rule of the on-surface sum),
+ * while the mixed form resolves distances only to about 1e-7 of a leaf box, so a
+ * target placed exactly on a source point gives no meaningful value there.  With
+ * the solved density this is the scattered field u^s; its accuracy near the
+ * surface (closer than about one quadrature patch) is that of the plain surface
+ * quadrature, no singular correction is applied. */
+ifgf_status ifgf_field(ifgf_plan *plan, const void *sigma_dev, const double *x_dev, int64_t M, void *out_dev,
+                       int nrhs, ifgf_precision prec, void *stream);
+
+/* Far-field pattern of Eq. FarField at directions xhat_j (unit vectors, e.g. the
+ * spherical grid of Eq. SphereGrid):
+ *   u_inf(xhat) = (1/4pi) sum_m [-i k <xhat, nu_m> - i eta] e^{-i k <xhat, y_m>} w_m sigma_m,
+ * the limit of u(R xhat) R e^{-ikR} as R grows.  Arguments as ifgf_field. */
+ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
+                           void *out_dev, int nrhs, ifgf_precision prec, void *stream);
+
 /* ---- batched applies over many plans (one CUDA graph) ----------------------
  * A group applies several plans (e.g. many scatterers of uneven size, each with
  * its own right-hand sides) as one captured CUDA graph.  The first

@@ -327,7 +327,7 @@ def _root_side(x) -> float:
     return float((hi - lo).max() * (1 + 2.0 ** -30))
 
 
-def field(points, normals, weights, k, eta, sigma, targets, chunk: int = 256) -> np.ndarray:
+def field(points, normals, weights, k, eta, sigma, targets) -> np.ndarray:
     """Combined-layer potential of Eq. CombinedLayer at arbitrary targets x, discretised with
     the surface quadrature (the off-surface counterpart of Eq. field1):
 
@@ -345,6 +345,7 @@ def field(points, normals, weights, k, eta, sigma, targets, chunk: int = 256) ->
     tol = 1e-14 * _root_side(x)
     ws = s * w[None, :]
     out = np.zeros((s.shape[0], t.shape[0]), dtype=np.complex128)
+    chunk = max(1, 4_000_000 // N)  # targets per block of pairs (bounds the temporaries)
     for j0 in range(0, t.shape[0], chunk):
         d = t[j0:j0 + chunk, None, :] - x[None, :, :]          # x - y, (c, N, 3)
         r = np.sqrt(np.einsum("cni,cni->cn", d, d))
@@ -369,5 +370,11 @@ def far_field(points, normals, weights, k, eta, sigma, xhat) -> np.ndarray:
     N = x.shape[0]
     s = _dens(sigma, N)
     xh = np.ascontiguousarray(xhat, dtype=np.float64).reshape(-1, 3)
-    K = (-1j * k * (xh @ nu.T) - 1j * eta) * np.exp(-1j * k * (xh @ x.T)) / (4.0 * math.pi)  # (M, N)
-    return (s * w[None, :]) @ K.T
+    ws = s * w[None, :]
+    out = np.zeros((s.shape[0], xh.shape[0]), dtype=np.complex128)
+    chunk = max(1, 4_000_000 // N)  # directions per block of terms (bounds the temporaries)
+    for j0 in range(0, xh.shape[0], chunk):
+        d = xh[j0:j0 + chunk]
+        K = (-1j * k * (d @ nu.T) - 1j * eta) * np.exp(-1j * k * (d @ x.T)) / (4.0 * math.pi)  # (c, N)
+        out[:, j0:j0 + chunk] = ws @ K.T
+    return out

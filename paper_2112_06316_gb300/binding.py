@@ -72,6 +72,8 @@ _SIGS = [
     ("ifgf_apply_vjp", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_far_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
@@ -308,6 +310,35 @@ class Plan:
             raise ValueError("out must match sigma's shape/dtype and be contiguous")
         self.apply_ptr(s.data_ptr(), y.data_ptr(), int(s.shape[0]), prec, stream)
         return y.reshape(-1) if squeeze else y
+
+    def _eval_off_surface(self, fn, sigma, targets, out, stream):
+        import torch
+
+        if not (isinstance(sigma, torch.Tensor) and sigma.is_cuda):
+            raise TypeError("sigma must be a CUDA torch tensor")
+        prec = FP64 if sigma.dtype == torch.complex128 else MIXED if sigma.dtype == torch.complex64 else None
+        if prec is None:
+            raise TypeError("sigma must be complex64 (mixed) or complex128 (FP64)")
+        squeeze = sigma.dim() == 1
+        s = (sigma.reshape(1, -1) if squeeze else sigma).contiguous()
+        if s.shape[-1] != self.N:
+            raise ValueError(f"sigma must have N={self.N} columns")
+        t = torch.as_tensor(targets, dtype=torch.float64, device=sigma.device).reshape(-1, 3).contiguous()
+        M = int(t.shape[0])
+        y = torch.empty((s.shape[0], M), dtype=s.dtype, device=s.device) if out is None else out
+        if y.shape != (s.shape[0], M) or y.dtype != s.dtype or not y.is_contiguous():
+            raise ValueError("out must be a contiguous (nrhs, M) tensor of sigma's dtype")
+        check(fn(self._h, _VP(s.data_ptr()), _VP(t.data_ptr()), ctypes.c_int64(M), _VP(y.data_ptr()),
+                 ctypes.c_int(s.shape[0]), ctypes.c_int(prec), _VP(_stream_ptr(stream))))
+        return y.reshape(-1) if squeeze else y
+
+    def field(self, sigma, targets, out=None, stream=None):
+        """Combined-layer potential (``ifgf_field``) at targets (M, 3) for sigma of shape (nrhs, N) or (N,)."""
+        return self._eval_off_surface(lib().ifgf_field, sigma, targets, out, stream)
+
+    def far_field(self, sigma, directions, out=None, stream=None):
+        """Far-field pattern (``ifgf_far_field``) at unit directions (M, 3)."""
+        return self._eval_off_surface(lib().ifgf_far_field, sigma, directions, out, stream)
 
     def gmres(self, rhs, x0=None, restart: int = 50, maxit: int = 200, tol: float = 1e-6,
               precision: int = FP64, stream=None):

@@ -235,6 +235,9 @@ void free_plan_device(Plan &p) {
     if (p.dk_ws) cudaFree(p.dk_ws);
     p.dk_ws = nullptr;
     p.dk_ws_bytes = 0;
+    if (p.field_ws) cudaFree(p.field_ws);
+    p.field_ws = nullptr;
+    p.field_ws_bytes = 0;
     for (int i = 0; i < Plan::kMaxEv; i++)
         if (p.ev[i]) {
             cudaEventDestroy(p.ev[i]);

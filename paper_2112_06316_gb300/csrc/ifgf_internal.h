@@ -161,6 +161,8 @@ struct Plan {
     size_t adj_ws_bytes = 0;
     void *dk_ws = nullptr;       // k-gradient: one level's anterpolated H plus the partial sums
     size_t dk_ws_bytes = 0;
+    void *field_ws = nullptr;    // off-surface / far-field evaluation: gathered w*sigma and per-chunk partial sums
+    size_t field_ws_bytes = 0;
 
     // bumped whenever device buffers baked into a captured graph may change
     uint64_t gen = 0;

@@ -1,0 +1,169 @@
+"""GPU: off-surface potential (Eq. CombinedLayer) and far-field pattern (Eq. FarField).
+
+``ifgf_field`` / ``ifgf_far_field`` through the C ABI against the oracle's plain
+numpy sums, element by element (FP64 <= 1e-12 relative l2, mixed <= 1e-5), against
+the closed-form scattered field and far field of the sound-soft sphere for the
+exact Mie density, at the bench's 16-wavelength sphere on sampled targets, and on
+the edge cases (no targets, no right-hand sides, invalid arguments).
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mie
+from workloads import cube_sphere, random_density, sphere_workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2112_06316_gb300 import binding
+    from paper_2112_06316_gb300 import build as _b
+
+    _b.build()
+    return binding
+
+
+def unit(v):
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+@pytest.fixture(scope="module")
+def small(B):
+    s = cube_sphere(16, 8)  # N = 1,536, unit sphere two wavelengths across (k = 2 pi)
+    k = 2 * math.pi
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, levels=4))
+    return s, k, plan
+
+
+def run(plan, fn, sig, tgt, dtype):
+    out = getattr(plan, fn)(torch.from_numpy(sig.astype(dtype)).cuda(), torch.from_numpy(tgt).cuda())
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_far_field_vs_oracle(B, oracle_lib, small, nrhs):
+    s, k, plan = small
+    rng = np.random.default_rng(11)
+    xh = unit(rng.normal(size=(333, 3)))  # ragged over the 128-thread blocks
+    sig = random_density(s.N, nrhs, 12)
+    ref = oracle_lib.far_field(s.points, s.normals, s.weights, k, k, sig, xh)
+    y64 = run(plan, "far_field", sig, xh, np.complex128)
+    y32 = run(plan, "far_field", sig, xh, np.complex64)
+    assert y64.shape == ref.shape and y32.shape == ref.shape
+    assert rel(y64, ref) < 1e-12
+    assert rel(y32, ref) < 1e-5
+    for q in range(nrhs):  # every column on its own, not only the stacked norm
+        assert rel(y32[q], ref[q]) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 5])
+def test_potential_vs_oracle(B, oracle_lib, small, nrhs):
+    s, k, plan = small
+    rng = np.random.default_rng(13)
+    x = unit(rng.normal(size=(201, 3))) * rng.uniform(1.05, 4.0, size=(201, 1))
+    x[7] = [0.0, 0.0, 0.0]        # the centre of the sphere (inside: the interior value of the representation)
+    x[8] = [30.0, -20.0, 10.0]    # far outside the root box
+    sig = random_density(s.N, nrhs, 14)
+    ref = oracle_lib.field(s.points, s.normals, s.weights, k, k, sig, x)
+    y64 = run(plan, "field", sig, x, np.complex128)
+    y32 = run(plan, "field", sig, x, np.complex64)
+    assert rel(y64, ref) < 1e-12
+    assert rel(y32, ref) < 1e-5
+    # FP64: a target on a source point drops that pair, as the oracle does
+    x1 = s.points[[5, 900]] * 1.0
+    ref1 = oracle_lib.field(s.points, s.normals, s.weights, k, k, sig, x1)
+    assert rel(run(plan, "field", sig, x1, np.complex128), ref1) < 1e-12
+
+
+def test_fp64_deterministic(B, small):
+    s, k, plan = small
+    rng = np.random.default_rng(15)
+    xh = unit(rng.normal(size=(77, 3)))
+    sig = random_density(s.N, 2, 16)
+    a = run(plan, "far_field", sig, xh, np.complex128)
+    b = run(plan, "far_field", sig, xh, np.complex128)
+    assert np.array_equal(a, b)
+
+
+def test_mie_scattered_and_far_field(B):
+    """Exact Mie density on the unit sphere: the GPU sums reproduce the closed-form
+    scattered field (|x| = 1.5, 3) and far field (the paper's far-field error, Eq.
+    FarFieldRelErr, over a spherical grid of Eq. SphereGrid)."""
+    s = cube_sphere(32, 8)
+    k = math.pi
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k))
+    phi = mie.density(s.points, k, k)
+    xh = mie.sphere_grid(21, 21)
+    ue = mie.far_field(xh, k)
+    u64 = run(plan, "far_field", phi, xh, np.complex128)
+    u32 = run(plan, "far_field", phi, xh, np.complex64)
+    assert rel(u64, ue) < 1e-7 and mie.far_field_error(ue, u64) < 1e-6
+    assert rel(u32, ue) < 5e-6 and mie.far_field_error(ue, u32) < 5e-5
+    rng = np.random.default_rng(17)
+    d = unit(rng.normal(size=(40, 3)))
+    for R, bar in ((1.5, 2e-7), (3.0, 2e-8)):
+        x = d * R
+        us = mie.scattered_field(x, k)
+        assert rel(run(plan, "field", phi, x, np.complex128), us) < bar
+        assert rel(run(plan, "field", phi, x, np.complex64), us) < 5e-6
+
+
+def test_bench_sphere_sampled(B, oracle_lib):
+    """The 16-wavelength sphere of the bench (N = 393,216): far field on the 200 x 200
+    grid of Eq. SphereGrid and on 160,000 directions (one leaf-box chunk), potential on
+    a 100 x 100 plane of Eq. PlanarGrid; sampled outputs against the oracle."""
+    s, k = sphere_workload(256, 8, 16.0)
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8, factor_mode=1))
+    sig = random_density(s.N, 1, 18)
+    rng = np.random.default_rng(19)
+    xh = mie.sphere_grid(200, 200)
+    pick = rng.choice(xh.shape[0], 48, replace=False)
+    ref = oracle_lib.far_field(s.points, s.normals, s.weights, k, k, sig, xh[pick])
+    y32 = run(plan, "far_field", sig, xh, np.complex64)
+    assert rel(y32[:, pick], ref) < 1e-5
+    xh2 = unit(rng.normal(size=(160000, 3)))
+    pick2 = rng.choice(xh2.shape[0], 32, replace=False)
+    y2 = run(plan, "far_field", sig, xh2, np.complex64)
+    assert rel(y2[:, pick2], oracle_lib.far_field(s.points, s.normals, s.weights, k, k, sig, xh2[pick2])) < 1e-5
+    g = np.linspace(-3.0, 3.0, 100)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    plane = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 1.5)], -1)
+    pick3 = rng.choice(plane.shape[0], 48, replace=False)
+    y3 = run(plan, "field", sig, plane, np.complex64)
+    assert rel(y3[:, pick3], oracle_lib.field(s.points, s.normals, s.weights, k, k, sig, plane[pick3])) < 1e-5
+
+
+def test_edge_cases(B, small):
+    s, k, plan = small
+    sig = torch.from_numpy(random_density(s.N, 2, 20)).cuda()
+    none = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    assert plan.far_field(sig, none).shape == (2, 0)
+    assert plan.field(sig[:0], torch.ones((4, 3), dtype=torch.float64, device="cuda") * 2).shape == (0, 4)
+    t = torch.ones((4, 3), dtype=torch.float64, device="cuda") * 2
+    out = torch.empty((2, 4), dtype=torch.complex128, device="cuda")
+    lib = B.lib()
+    h = plan.handle
+    VP = ctypes.c_void_p
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.ifgf_field(h, VP(sig.data_ptr()), VP(t.data_ptr()), ctypes.c_int64(-1), VP(out.data_ptr()), 2, 0, st) == -1
+    assert lib.ifgf_far_field(h, VP(sig.data_ptr()), None, ctypes.c_int64(4), VP(out.data_ptr()), 2, 0, st) == -1
+    assert lib.ifgf_field(h, VP(sig.data_ptr()), VP(t.data_ptr()), ctypes.c_int64(4), VP(sig.data_ptr()), 2, 0, st) == -1
+    assert b"alias" in lib.ifgf_last_error()
+    assert lib.ifgf_field(h, VP(sig.data_ptr()), VP(t.data_ptr()), ctypes.c_int64(4), VP(out.data_ptr()), 2, 7, st) == -1
+    assert lib.ifgf_far_field(None, VP(sig.data_ptr()), VP(t.data_ptr()), ctypes.c_int64(4), VP(out.data_ptr()), 2, 0,
+                              st) == -1
+    with pytest.raises(TypeError):
+        plan.far_field(sig.real.contiguous(), t)
