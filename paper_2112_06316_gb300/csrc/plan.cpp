@@ -65,15 +65,22 @@ int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L,
     double lt = leaf_target > 0 ? leaf_target : 64.0;
     double best = INFINITY;
     int D = 3;
+    // keys at the finest candidate level; the level-d key is the prefix key >> 3 (16 - d)
+    // (box sides are powers of two apart, so the floors nest exactly)
     std::vector<uint64_t> keys(N);
-    for (int d = 3; d <= 16; d++) {
-        double H = std::ldexp(L, -(d - 1));
-        int nside = 1 << (d - 1);
+    {
+        const double H = std::ldexp(L, -15);
+        const int nside = 1 << 15;
         for (int64_t i = 0; i < N; i++)
             keys[i] = morton(leaf_coord(xyz[3 * i], c0[0], H, nside), leaf_coord(xyz[3 * i + 1], c0[1], H, nside),
                              leaf_coord(xyz[3 * i + 2], c0[2], H, nside));
         std::sort(keys.begin(), keys.end());
-        int64_t nb = std::unique(keys.begin(), keys.end()) - keys.begin();
+    }
+    for (int d = 3; d <= 16; d++) {
+        const int sh = 3 * (16 - d);
+        int64_t nb = 0;
+        for (int64_t i = 0; i < N; i++)
+            if (i == 0 || (keys[i] >> sh) != (keys[i - 1] >> sh)) nb++;
         double m = std::fabs(std::log((double)N / nb / lt));
         if (m < best) {
             best = m;
@@ -134,12 +141,10 @@ inline double snap(double u) {
     return std::fabs(u - r) <= 1e-12 * std::max(std::fabs(u), 1.0) ? r : u;
 }
 
-// Mark in `bits` every cone of box b (level L) that x may fall into (Eq. ConeIntervals
-// with clamped indices; phi in [0, 2 pi)).
-inline void mark_point(const Plan &p, const HostLevel &L, int b, const double *x, double tau, uint64_t *bits) {
-    double y0[3];
-    box_center(p, L, b, y0);
-    double dx = x[0] - y0[0], dy = x[1] - y0[1], dz = x[2] - y0[2];
+// Mark in `bits` every cone (level L) that the point at offset (dx, dy, dz) from a box
+// centre may fall into (Eq. ConeIntervals with clamped indices; phi in [0, 2 pi)).
+inline void mark_offset(const HostLevel &L, double dx, double dy, double dz, double tau, uint64_t *bits,
+                        std::vector<int> *touched = nullptr) {
     double rho = std::sqrt(dx * dx + dy * dy);
     double r = std::sqrt(dx * dx + dy * dy + dz * dz);
     double s = L.h / r;
@@ -165,8 +170,32 @@ inline void mark_point(const Plan &p, const HostLevel &L, int b, const double *x
             for (int e = 0; e < np_n; e++) {
                 int is = ns < 0 ? a : cs[a], it = nt < 0 ? c : ct[c], ip = np < 0 ? e : cp[e];
                 int cone = (is * L.nC + it) * L.nph + ip;
-                bits[cone >> 6] |= 1ULL << (cone & 63);
+                const uint64_t m = 1ULL << (cone & 63);
+                if (touched && !(bits[cone >> 6] & m)) touched->push_back(cone);
+                bits[cone >> 6] |= m;
             }
+}
+
+// The same for an absolute position x and box b of level L.
+inline void mark_point(const Plan &p, const HostLevel &L, int b, const double *x, double tau, uint64_t *bits) {
+    double y0[3];
+    box_center(p, L, b, y0);
+    mark_offset(L, x[0] - y0[0], x[1] - y0[1], x[2] - y0[2], tau, bits);
+}
+
+// Offset of interpolation node n of cone `cone` (level L) from its box centre:
+// (h / s) (sin theta cos phi, sin theta sin phi, cos theta) (Eq. defparametrizationins).
+inline void node_offset(const Plan &p, const HostLevel &L, int cone, int n, double *v) {
+    int ip = cone % L.nph, it = (cone / L.nph) % L.nC, is = cone / (L.nph * L.nC);
+    int na = p.Pang;
+    int a = n / (na * na), bb = (n / na) % na, c = n % na;
+    double s = (is + 0.5 * (p.cs.x[a] + 1.0)) * L.ds;
+    double th = (it + 0.5 * (p.ca.x[bb] + 1.0)) * L.dth;
+    double ph = (ip + 0.5 * (p.ca.x[c] + 1.0)) * L.dph;
+    double r = L.h / s;
+    v[0] = r * std::sin(th) * std::cos(ph);
+    v[1] = r * std::sin(th) * std::sin(ph);
+    v[2] = r * std::cos(th);
 }
 
 inline void node_position(const Plan &p, const HostLevel &L, int b, int cone, int n, double *x) {
@@ -368,6 +397,64 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
         const int words = (L.ncone + 63) / 64;
         std::vector<std::vector<int>> lists(L.nbox);
         const HostLevel *PL = d > 3 ? &p.lv[d - 1] : nullptr;
+        // The cones that the parent's cone nodes mark in a child depend only on (parent cone id,
+        // child octant): a node's offset from the child centre is its offset from the parent
+        // centre plus (1/2 - bit) H_d per axis.  Each used pair is classified once (CSR by key
+        // = compact parent cone index * 8 + octant).
+        std::vector<int> key_of;
+        std::vector<int64_t> mk_start;
+        std::vector<int> mk_list;
+        if (PL) {
+            key_of.assign(PL->ncone, -1);
+            std::vector<int> used;
+            for (int64_t rc = 0; rc < PL->nrc; rc++) {
+                const int g = PL->rc_cone[rc];
+                if (key_of[g] < 0) {
+                    key_of[g] = 0;
+                    used.push_back(g);
+                }
+            }
+            std::sort(used.begin(), used.end());
+            for (size_t i = 0; i < used.size(); i++) key_of[used[i]] = (int)i;
+            const int64_t nkey = (int64_t)used.size() * 8;
+            std::vector<std::vector<int>> kl(nkey);
+            std::vector<unsigned char> need(nkey, 0);  // keys some (child box, parent cone) pair uses
+            for (int b = 0; b < L.nbox; b++) {
+                const int pb = L.parent[b];
+                const int o = (L.ijk[3 * b] & 1) + 2 * (L.ijk[3 * b + 1] & 1) + 4 * (L.ijk[3 * b + 2] & 1);
+                for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++)
+                    need[(int64_t)key_of[PL->rc_cone[rc]] * 8 + o] = 1;
+            }
+#pragma omp parallel
+            {
+                std::vector<uint64_t> kb(words, 0ULL);
+                std::vector<int> touched;
+                std::vector<double> off(3 * (size_t)p.P);
+#pragma omp for schedule(dynamic, 4)
+                for (int64_t gi = 0; gi < (int64_t)used.size(); gi++) {
+                    bool any = false;
+                    for (int o = 0; o < 8; o++) any = any || need[gi * 8 + o];
+                    if (!any) continue;
+                    for (int n = 0; n < p.P; n++) node_offset(p, *PL, used[gi], n, &off[3 * n]);
+                    for (int o = 0; o < 8; o++) {
+                        if (!need[gi * 8 + o]) continue;
+                        const double sx = (0.5 - (o & 1)) * L.H, sy = (0.5 - ((o >> 1) & 1)) * L.H,
+                                     sz = (0.5 - ((o >> 2) & 1)) * L.H;
+                        touched.clear();
+                        for (int n = 0; n < p.P; n++)
+                            mark_offset(L, off[3 * n] + sx, off[3 * n + 1] + sy, off[3 * n + 2] + sz, tau, kb.data(),
+                                        &touched);
+                        std::sort(touched.begin(), touched.end());
+                        for (int c : touched) kb[c >> 6] = 0ULL;
+                        kl[gi * 8 + o] = touched;
+                    }
+                }
+            }
+            mk_start.assign(nkey + 1, 0);
+            for (int64_t kk = 0; kk < nkey; kk++) mk_start[kk + 1] = mk_start[kk] + (int64_t)kl[kk].size();
+            mk_list.resize(mk_start[nkey]);
+            for (int64_t kk = 0; kk < nkey; kk++) std::copy(kl[kk].begin(), kl[kk].end(), mk_list.begin() + mk_start[kk]);
+        }
 #pragma omp parallel
         {
             std::vector<uint64_t> bits(words);
@@ -379,13 +466,15 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                     for (int s = L.start[cb]; s < L.start[cb + 1]; s++) mark_point(p, L, b, &xs[3 * s], tau, bits.data());
                 }
                 if (PL) {
-                    int pb = L.parent[b];
-                    for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++)
-                        for (int n = 0; n < p.P; n++) {
-                            double x[3];
-                            node_position(p, *PL, pb, PL->rc_cone[rc], n, x);
-                            mark_point(p, L, b, x, tau, bits.data());
+                    const int pb = L.parent[b];
+                    const int o = (L.ijk[3 * b] & 1) + 2 * (L.ijk[3 * b + 1] & 1) + 4 * (L.ijk[3 * b + 2] & 1);
+                    for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++) {
+                        const int64_t kk = (int64_t)key_of[PL->rc_cone[rc]] * 8 + o;
+                        for (int64_t j = mk_start[kk]; j < mk_start[kk + 1]; j++) {
+                            const int c = mk_list[j];
+                            bits[c >> 6] |= 1ULL << (c & 63);
                         }
+                    }
                 }
                 std::vector<int> &v = lists[b];
                 for (int wi = 0; wi < words; wi++) {
