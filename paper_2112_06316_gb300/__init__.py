@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     MIXED,
     Group,
     IFGFError,
+    IFGFOperator,
     Params,
     Plan,
     lib,

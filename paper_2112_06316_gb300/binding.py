@@ -392,6 +392,19 @@ class Plan:
         return int(m.value)
 
 
+class IFGFOperator(Plan):
+    """The operator A of Eq. CombLayIE for one surface and wavenumber: a ``Plan`` built from
+    (points, normals, weights, k, params).  ``params`` supplies every setting but k (defaults
+    of ``Params`` when omitted); ``apply``, ``adjoint``, ``vjp``, ``gmres``, ``field`` and
+    ``far_field`` are the plan's."""
+
+    def __init__(self, points, normals, weights, k: float, params: Params | None = None, stream=None):
+        import dataclasses
+
+        prm = Params(k=float(k)) if params is None else dataclasses.replace(params, k=float(k))
+        super().__init__(points, normals, weights, prm, stream)
+
+
 def supported_orders():
     return [tuple(int(v) for v in s.split("x")) for s in lib().ifgf_supported_orders().decode().split(",")]
 

@@ -167,3 +167,13 @@ def test_edge_cases(B, small):
                               st) == -1
     with pytest.raises(TypeError):
         plan.far_field(sig.real.contiguous(), t)
+
+
+def test_operator_wrapper_is_the_plan(B, small):
+    """IFGFOperator(points, normals, weights, k, params) builds the same plan as Plan(..., Params(k))."""
+    s, k, plan = small
+    op = B.IFGFOperator(s.points, s.normals, s.weights, k, B.Params(k=0.0, levels=4))
+    assert op.params.k == k and op.info()["nrc"] == plan.info()["nrc"]
+    sig = torch.from_numpy(random_density(s.N, 1, 21)).cuda()
+    assert torch.equal(op.apply(sig), plan.apply(sig))
+    op.close()
