@@ -212,6 +212,21 @@ def algorithmic_flops(info, P, nrhs, split_levels):
     return leaf, near, cousin, prop
 
 
+def reduce_over_ranks(ms: float, points: float, world: int, device="cpu"):
+    """Whole-job figures of independent replicas: (max over ranks of the time per step, sum over
+    ranks of the points per step).  Every rank must call it (collectives of the default group)."""
+    if world <= 1:
+        return ms, float(points)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    p = torch.tensor([float(points)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -307,14 +322,8 @@ def run_ours(args):
     clocks.start()
     t_mixed = timed(lambda: plan.apply(sig32, out=y32), args.steps, args.warmup)
     clk = clocks.stop()
-    ms = float(np.mean(t_mixed))
-    if world > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = N * nrhs * world / (ms * 1e3)
+    ms, points = reduce_over_ranks(float(np.mean(t_mixed)), N * nrhs, world, dev)
+    value = points / (ms * 1e3)
 
     # ---- per-launch device times (profiled apply) ----
     plan.set_profiling(True)
