@@ -200,3 +200,51 @@ def test_ifgf_oracle_levels_match_table1(oracle_lib):
         s, k = sphere_workload(n, 8 if n % 8 == 0 else 6, float(r["diameter_wavelengths"]))
         assert s.N == r["N"]
         assert oracle_lib.auto_levels(s.points) == r["levels"], r
+
+
+def _fig3_errors(oracle_lib, HL, eta, Ps=3, npts=100):
+    """Section 3.3 / Fig. 3 set-up: interpolate the analytic factors along one ray x = y0 + (h/s) u
+    over the cone segment closest to the source box (s in [eta0 - eta0/n_s, eta0], n_s of the
+    size rule), Ps first-kind Chebyshev points; max error of the reconstructed kernel over
+    the segment, relative to max |K|, for the combined factor and for the split pair."""
+    k = 2 * math.pi
+    H = HL * 1.0
+    h = math.sqrt(3) / 2 * H
+    y0 = np.zeros(3)
+    y = np.array([0.4, -0.3, 0.45]) * H
+    u = np.array([1.0, 0.7, 0.4]) / np.linalg.norm([1.0, 0.7, 0.4])
+    nu = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    ns = 2 ** max(0, math.ceil(math.log2(2 * H)))
+    e0 = math.sqrt(3) / 3
+    a, b = e0 - e0 / ns, e0
+    nodes = a + (np.cos((2 * np.arange(Ps) + 1) * math.pi / (2 * Ps)) + 1) / 2 * (b - a)
+    vc = np.array([oracle_lib.wfactors(k, eta, y0 + h / s * u, y0, h, y, nu, split=False)[0] for s in nodes])
+    vs = np.array([oracle_lib.wfactors(k, eta, y0 + h / s * u, y0, h, y, nu, split=True) for s in nodes])
+
+    def interp(v, t):
+        return oracle_lib.cheb_interp_1d(v.real, t) + 1j * oracle_lib.cheb_interp_1d(v.imag, t)
+
+    ec, es, kk = [], [], []
+    for s in np.linspace(a, b, npts + 1)[1:]:
+        t = 2 * (s - a) / (b - a) - 1
+        x = y0 + h / s * u
+        r = h / s
+        E1 = np.exp(1j * k * r) / (4 * math.pi * r)
+        K = oracle_lib.kernel(k, eta, x, y, nu)
+        ec.append(abs(E1 * interp(vc, t) - K))
+        es.append(abs(E1 / r * interp(vs[:, 0], t) + E1 * interp(vs[:, 1], t) - K))
+        kk.append(abs(K))
+    return max(ec) / max(kk), max(es) / max(kk)
+
+
+@pytest.mark.parametrize("eta", [0.0, 2 * math.pi])
+def test_fig3_factor_interpolation_level_independent(oracle_lib, eta):
+    """For H >= lambda the combined factor and the split pair interpolate equally well (Fig. 3
+    text), and with the segment size halved as H doubles (Remark cone_seg_size) the error
+    stays bounded as the box grows 8-fold; a factor carrying the unfactored oscillation
+    e^{ik|x - y|} would fail both."""
+    errs = [_fig3_errors(oracle_lib, HL, eta) for HL in (1.0, 2.0, 4.0, 8.0)]
+    for c, s in errs:
+        assert 0.9 < c / s < 1.25, errs
+        assert c < 1e-2, errs
+    assert max(c for c, _ in errs[1:]) < 4 * min(c for c, _ in errs[1:]), errs
