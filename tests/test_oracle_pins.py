@@ -248,3 +248,25 @@ def test_fig3_factor_interpolation_level_independent(oracle_lib, eta):
         assert 0.9 < c / s < 1.25, errs
         assert c < 1e-2, errs
     assert max(c for c, _ in errs[1:]) < 4 * min(c for c, _ in errs[1:]), errs
+
+
+def test_ifgf_oracle_reaches_direct_sum_to_rounding(oracle_lib):
+    """With fine cone segments and high orders the interpolation error vanishes and
+    Algorithm 1 reproduces the direct sum to rounding: one level (cousin interpolation
+    only) to 1e-13, two levels (propagation through split and combined factors) to 2e-8."""
+    k = math.pi
+    s = cube_sphere(12, 12)  # N = 864
+    sig = random_density(s.N, 1, 3)
+    yd = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5)
+    for (ps, pa, nc0, ns0), bar in (((7, 9, 4, 2), 1e-8), ((11, 12, 8, 4), 1e-13)):
+        p = oracle_lib.IFGFParams(k=k, levels=3, Ps=ps, Pang=pa, nC0=nc0, nS0=ns0, identity_coef=0.5)
+        y, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, p, sig)
+        assert rel(y, yd) < bar, (ps, pa, rel(y, yd))
+    s = cube_sphere(24, 12)  # N = 3,456, D = 4
+    sig = random_density(s.N, 1, 3)
+    yd = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5)
+    for fm in (0, 1, 2):
+        p = oracle_lib.IFGFParams(k=k, levels=4, Ps=7, Pang=9, nC0=4, nS0=2, identity_coef=0.5, factor_mode=fm)
+        y, info = oracle_lib.ifgf(s.points, s.normals, s.weights, p, sig)
+        assert info["prop_evals"][3] > 0
+        assert rel(y, yd) < 2e-8, (fm, rel(y, yd))
