@@ -153,7 +153,7 @@ inline void mark_offset(const HostLevel &L, double dx, double dy, double dz, dou
     if (ph < 0) ph += 2.0 * M_PI;
     if (ph >= 2.0 * M_PI) ph = 0.0;
     double us = snap(s / L.ds), ut = snap(th / L.dth), up = snap(ph / L.dph);
-    int cs[3], ct[3], cp[3];
+    int cs[3] = {0, 0, 0}, ct[3] = {0, 0, 0}, cp[3] = {0, 0, 0};
     double bs = 0, bt = 0, bp = 0;
     if (tau > 0) {
         // tau plus the reach of FP32 rounding of the geometry (relative 4e-7 of r)
@@ -196,21 +196,6 @@ inline void node_offset(const Plan &p, const HostLevel &L, int cone, int n, doub
     v[0] = r * std::sin(th) * std::cos(ph);
     v[1] = r * std::sin(th) * std::sin(ph);
     v[2] = r * std::cos(th);
-}
-
-inline void node_position(const Plan &p, const HostLevel &L, int b, int cone, int n, double *x) {
-    int ip = cone % L.nph, it = (cone / L.nph) % L.nC, is = cone / (L.nph * L.nC);
-    int na = p.Pang;
-    int a = n / (na * na), bb = (n / na) % na, c = n % na;
-    double s = (is + 0.5 * (p.cs.x[a] + 1.0)) * L.ds;
-    double th = (it + 0.5 * (p.ca.x[bb] + 1.0)) * L.dth;
-    double ph = (ip + 0.5 * (p.ca.x[c] + 1.0)) * L.dph;
-    double y0[3];
-    box_center(p, L, b, y0);
-    double r = L.h / s;
-    x[0] = y0[0] + r * std::sin(th) * std::cos(ph);
-    x[1] = y0[1] + r * std::sin(th) * std::sin(ph);
-    x[2] = y0[2] + r * std::cos(th);
 }
 
 }  // namespace
@@ -519,10 +504,7 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
 // Adjoint lists: for every relevant cone of level d, the cousin targets and parent
 // cone nodes that the forward apply interpolates from it, classified with the same
 // rule as the kernels (no margin band).  Entry order is deterministic.
-static int classify_exact(const Plan &p, const HostLevel &L, int b, const double *x) {
-    double y0[3];
-    box_center(p, L, b, y0);
-    double dx = x[0] - y0[0], dy = x[1] - y0[1], dz = x[2] - y0[2];
+static int classify_offset(const HostLevel &L, double dx, double dy, double dz) {
     double rho = std::sqrt(dx * dx + dy * dy);
     double r = std::sqrt(dx * dx + dy * dy + dz * dz);
     double s = L.h / r;
@@ -537,11 +519,65 @@ static int classify_exact(const Plan &p, const HostLevel &L, int b, const double
     return (is * L.nC + it) * L.nph + ip;
 }
 
+static int classify_exact(const Plan &p, const HostLevel &L, int b, const double *x) {
+    double y0[3];
+    box_center(p, L, b, y0);
+    return classify_offset(L, x[0] - y0[0], x[1] - y0[1], x[2] - y0[2]);
+}
+
 ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
     const int64_t N = p.N;
     for (int d = 3; d <= p.D; d++) {
         HostLevel &L = p.lv[d];
         const HostLevel *PL = d > 3 ? &p.lv[d - 1] : nullptr;
+        // Child cone of every parent cone node, per (parent cone id, child octant) used at this
+        // level (translation invariant, as in build_host_plan): node_cone[idx * P + n], idx from
+        // key_idx[compact parent cone index * 8 + octant].
+        std::vector<int> key_of, key_idx, node_cone;
+        if (PL) {
+            key_of.assign(PL->ncone, -1);
+            std::vector<int> used;
+            for (int64_t rc = 0; rc < PL->nrc; rc++) {
+                const int g = PL->rc_cone[rc];
+                if (key_of[g] < 0) {
+                    key_of[g] = 0;
+                    used.push_back(g);
+                }
+            }
+            std::sort(used.begin(), used.end());
+            for (size_t i = 0; i < used.size(); i++) key_of[used[i]] = (int)i;
+            key_idx.assign(used.size() * 8, -1);
+            for (int b = 0; b < L.nbox; b++) {
+                const int pb = L.parent[b];
+                const int o = (L.ijk[3 * b] & 1) + 2 * (L.ijk[3 * b + 1] & 1) + 4 * (L.ijk[3 * b + 2] & 1);
+                for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++)
+                    key_idx[(size_t)key_of[PL->rc_cone[rc]] * 8 + o] = 0;
+            }
+            std::vector<int64_t> keys;  // needed (compact cone index * 8 + octant), ascending
+            for (size_t kk = 0; kk < key_idx.size(); kk++)
+                if (key_idx[kk] == 0) {
+                    key_idx[kk] = (int)keys.size();
+                    keys.push_back((int64_t)kk);
+                }
+            node_cone.resize(keys.size() * (size_t)p.P);
+#pragma omp parallel
+            {
+                std::vector<double> off(3 * (size_t)p.P);
+                int last = -1;
+#pragma omp for schedule(dynamic, 16)
+                for (int64_t i = 0; i < (int64_t)keys.size(); i++) {
+                    const int gi = (int)(keys[i] / 8), o = (int)(keys[i] % 8);
+                    if (gi != last) {
+                        for (int n = 0; n < p.P; n++) node_offset(p, *PL, used[gi], n, &off[3 * n]);
+                        last = gi;
+                    }
+                    const double sx = (0.5 - (o & 1)) * L.H, sy = (0.5 - ((o >> 1) & 1)) * L.H,
+                                 sz = (0.5 - ((o >> 2) & 1)) * L.H;
+                    for (int n = 0; n < p.P; n++)
+                        node_cone[i * p.P + n] = classify_offset(L, off[3 * n] + sx, off[3 * n + 1] + sy, off[3 * n + 2] + sz);
+                }
+            }
+        }
         std::vector<std::vector<std::vector<int>>> per_box(L.nbox);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int b = 0; b < L.nbox; b++) {
@@ -556,14 +592,15 @@ ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
                 }
             }
             if (PL) {
-                int pb = L.parent[b];
-                for (int rcp = PL->rc_start[pb]; rcp < PL->rc_start[pb + 1]; rcp++)
+                const int pb = L.parent[b];
+                const int o = (L.ijk[3 * b] & 1) + 2 * (L.ijk[3 * b + 1] & 1) + 4 * (L.ijk[3 * b + 2] & 1);
+                for (int rcp = PL->rc_start[pb]; rcp < PL->rc_start[pb + 1]; rcp++) {
+                    const int *nc = &node_cone[(size_t)key_idx[(size_t)key_of[PL->rc_cone[rcp]] * 8 + o] * p.P];
                     for (int n = 0; n < p.P; n++) {
-                        double x[3];
-                        node_position(p, *PL, pb, PL->rc_cone[rcp], n, x);
-                        int rc = L.cone_map[(size_t)b * L.ncone + classify_exact(p, L, b, x)];
+                        int rc = L.cone_map[(size_t)b * L.ncone + nc[n]];
                         if (rc >= 0) lists[rc - r0].push_back((int)(N + (int64_t)rcp * p.P + n));
                     }
+                }
             }
         }
         L.ad_start.assign(L.nrc + 1, 0);
