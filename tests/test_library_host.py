@@ -107,3 +107,29 @@ def test_auto_levels_match_oracle_rule(B, oracle_lib):
         s, k = sphere_workload(n, m, wl)
         pi = B.dry_run(s.points, s.normals, s.weights, B.Params(k=k))
         assert pi["D"] == oracle_lib.auto_levels(s.points)
+
+
+def test_entry_points_reject_a_null_plan_without_a_gpu(B):
+    """Every call that takes a plan checks it before any device work: a null plan gives
+    IFGF_EINVAL and a message, on a machine without a GPU too."""
+    import ctypes
+
+    lib = B.lib()
+    dk = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    info = B.CInfo()
+    calls = {
+        "ifgf_apply": lambda: lib.ifgf_apply(None, None, None, 1, B.MIXED, None),
+        "ifgf_apply_adjoint": lambda: lib.ifgf_apply_adjoint(None, None, None, 1, B.MIXED, None),
+        "ifgf_apply_vjp": lambda: lib.ifgf_apply_vjp(None, None, None, None, 1, ctypes.byref(dk), B.MIXED, None),
+        "ifgf_apply_noalloc": lambda: lib.ifgf_apply_noalloc(None, None, None, 1, B.MIXED, None),
+        "ifgf_field": lambda: lib.ifgf_field(None, None, None, ctypes.c_int64(4), None, 1, B.MIXED, None),
+        "ifgf_far_field": lambda: lib.ifgf_far_field(None, None, None, ctypes.c_int64(4), None, 1, B.MIXED, None),
+        "ifgf_gmres": lambda: lib.ifgf_gmres(None, None, None, 10, 10, 1e-6, B.FP64, ctypes.byref(it), None, None),
+        "ifgf_plan_info": lambda: lib.ifgf_plan_info(None, ctypes.byref(info)),
+        "ifgf_plan_set_correction": lambda: lib.ifgf_plan_set_correction(None, None, None, None, ctypes.c_int64(0)),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+        assert lib.ifgf_last_error(), name
+    lib.ifgf_plan_destroy(None)  # a no-op
