@@ -218,6 +218,36 @@ ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev, void *y_d
 ifgf_status ifgf_gmres(ifgf_plan *plan, const void *rhs_dev, void *x_dev, int restart, int maxit, double tol,
                        ifgf_precision apply_prec, int *iters, double *resid_hist, void *stream);
 
+/* ---- rectangular-polar singular / near-singular correction (Section 4.2) ------
+ * Builds, on the host, the sparse correction C that ifgf_plan_set_correction takes:
+ * for every target x_l and every patch within the proximity distance `delta` of it
+ * (Eq. SingGridPts), the patch integral of K(x_l, y) phi(y) by the rectangular-polar
+ * method (Eq. IntOpAtSing with Eq. BetaCov: Fejer's first rule with N_beta points per
+ * direction after the change of variables of Eq. CoV with Kress exponent d_grade,
+ * centred at the closest patch point of Eq. MinNode), minus the regular Fejer row
+ * (Eq. ReguIntOpQuadrature, m != l) that the accelerated operator already sums.
+ * The surface is Q = N / m^2 patches of m x m Chebyshev-Gauss nodes (Eq. FejersNodes):
+ *   xyz, normals, weights: host, the points as given to ifgf_plan_create (N x 3, N x 3, N).
+ *   patch_node: host, N int32: point l is node (i, j) of patch q where
+ *               patch_node[l] = q * m * m + i * m + j, (u_i, v_j) = (cos(pi (2i+1)/(2m)),
+ *               cos(pi (2j+1)/(2m))); a permutation of 0..N-1.
+ *   k, eta: the operator's wavenumber and coupling; delta >= 0: proximity distance;
+ *   n_beta in 2..512 (e.g. 48); d_grade >= 2 (e.g. 5).
+ * Each patch's map y(u, v) is the tensor Chebyshev interpolant of its node positions,
+ * oriented like the given normals.  Outputs: *rowptr_out (N + 1 int64), *col_out
+ * (nnz int32, caller point indices) and *val_out (nnz complex128, interleaved re, im),
+ * allocated by the library and released with ifgf_free.  Synchronous, host only (no
+ * GPU is touched; OpenMP threads).  Errors: IFGF_EINVAL (null pointers, N not a
+ * multiple of m^2, m outside 2..64, patch_node not a permutation, non-finite input,
+ * invalid k, eta, delta, n_beta or d_grade), IFGF_ENOMEM; outputs are NULL on error. */
+ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const double *weights, int64_t N,
+                               const int32_t *patch_node, int32_t m, double k, double eta, double delta,
+                               int32_t n_beta, double d_grade, int64_t **rowptr_out, int32_t **col_out,
+                               double **val_out);
+
+/* Releases an array returned by ifgf_rp_correction (NULL is a no-op). */
+void ifgf_free(void *ptr);
+
 /* ---- evaluation off the surface (Section 5: fields from a solved density) ----
  * Direct sums over every quadrature point of the plan (all N sources, in
  * O(N * M) work), one GPU thread per target; the interpolation orders of the plan

@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     Params,
     Plan,
     lib,
+    rp_correction,
     supported_orders,
 )
 from .autograd import IFGFApply, ifgf_apply  # noqa: F401

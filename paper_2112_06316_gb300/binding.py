@@ -72,6 +72,10 @@ _SIGS = [
     ("ifgf_apply_vjp", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_rp_correction", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    ("ifgf_free", None, [_VP]),
     ("ifgf_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_far_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -390,6 +394,35 @@ class Plan:
         m = ctypes.c_int64()
         check(lib().ifgf_plan_check(self._h, _VP(_stream_ptr(stream)), ctypes.byref(m)))
         return int(m.value)
+
+
+def rp_correction(points, normals, weights, patch_node, m: int, k: float, eta: float | None = None,
+                  delta: float = 0.0, n_beta: int = 48, d_grade: float = 5.0):
+    """Rectangular-polar correction (``ifgf_rp_correction``; host only, no GPU) as numpy CSR
+    (rowptr int64 (N+1,), col int32 (nnz,), val complex128 (nnz,)) over the caller's point order,
+    ready for ``Plan.set_correction``."""
+    x = _host(points, np.float64)
+    n = _host(normals, np.float64)
+    w = _host(weights, np.float64)
+    pn = _host(patch_node, np.int32)
+    N = int(x.shape[0])
+    if x.shape != (N, 3) or n.shape != (N, 3) or w.shape != (N,) or pn.shape != (N,):
+        raise ValueError("points/normals (N, 3), weights and patch_node (N,) expected")
+    rp, cl, vl = _VP(), _VP(), _VP()
+    check(lib().ifgf_rp_correction(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(N), pn.ctypes.data,
+                                   ctypes.c_int32(m), ctypes.c_double(k), ctypes.c_double(k if eta is None else eta),
+                                   ctypes.c_double(delta), ctypes.c_int32(n_beta), ctypes.c_double(d_grade),
+                                   ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl)))
+    try:
+        rowptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int64)), shape=(N + 1,)).copy()
+        nnz = int(rowptr[-1])
+        col = np.ctypeslib.as_array(ctypes.cast(cl, ctypes.POINTER(ctypes.c_int32)), shape=(max(nnz, 1),))[:nnz].copy()
+        val = np.ctypeslib.as_array(ctypes.cast(vl, ctypes.POINTER(ctypes.c_double)),
+                                    shape=(max(2 * nnz, 2),))[:2 * nnz].copy().view(np.complex128)
+    finally:
+        for ptr in (rp, cl, vl):
+            lib().ifgf_free(ptr)
+    return rowptr, col, val
 
 
 class IFGFOperator(Plan):

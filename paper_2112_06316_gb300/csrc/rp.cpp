@@ -1,0 +1,477 @@
+// Rectangular-polar (RP) singular / near-singular correction, host side (Section 4.2).
+//
+// The surface is the union of Q patches, each carrying the m x m Chebyshev-Gauss nodes of
+// Eq. FejersNodes.  For a target x_l and a patch Gamma^q within the proximity distance delta
+// of it (Eq. SingGridPts), the patch integral of K(x_l, y) phi(y) is
+//   sum_{n,m} a^q_{nm} beta^{q,l}_{nm}                                   (Eq. IntOpAtSing)
+// with a^q the Chebyshev coefficients of phi on the patch (Eq. ChebyCoeff) and beta the
+// integrals of K T_n T_m J (Eq. BetaAtSing), computed with Fejer's first rule after the
+// clustering change of variables xi_alpha (Eq. CoV, Kress map Eq. wMap / Eq. vMap) centred at
+// the patch point closest to x_l (Eq. MinNode).  Folding Eq. ChebyCoeff into Eq. IntOpAtSing
+// makes the result linear in the nodal values of phi: row l gets, for node (i, j) of the
+// patch, c_ij = sum over the graded quadrature of K J l_i(u) l_j(v) w_u w_v, l_i the Lagrange
+// basis of the nodes.  The regular Fejer row (Eq. ReguIntOpQuadrature, m != l) that the
+// accelerated operator already sums is subtracted, so that
+//   y = c_I phi + (regular sum) + C phi
+// uses the RP value on the near patches.
+//
+// The patch map y^q(u, v) is not passed in: it is the tensor Chebyshev interpolant of the
+// patch's node positions (degree m - 1 per direction, the representation Section 4.1 uses
+// for densities), its normal the normalised y_u x y_v oriented like the caller's normals.
+// The closest patch point is found by projected Gauss-Newton from the nearest node.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "ifgf_internal.h"
+
+namespace ifgf {
+
+void clear_error();
+
+namespace {
+
+using cd = std::complex<double>;
+constexpr double kPiD = 3.14159265358979323846;
+
+// T_0..T_{n-1}(t) and their derivatives (three-term recurrence).
+inline void cheb_vals(int n, double t, double *T, double *dT) {
+    T[0] = 1.0;
+    dT[0] = 0.0;
+    if (n > 1) {
+        T[1] = t;
+        dT[1] = 1.0;
+    }
+    for (int k = 2; k < n; k++) {
+        T[k] = 2.0 * t * T[k - 1] - T[k - 2];
+        dT[k] = 2.0 * T[k - 1] + 2.0 * t * dT[k - 1] - dT[k - 2];
+    }
+}
+
+// Chebyshev-Gauss nodes (Eq. FejersNodes) and Fejer first-rule weights (Eq. FejersWeights).
+void fejer_rule(int J, std::vector<double> &s, std::vector<double> &w) {
+    s.resize(J);
+    w.resize(J);
+    for (int j = 0; j < J; j++) {
+        s[j] = std::cos(kPiD * (2.0 * j + 1.0) / (2.0 * J));
+        double acc = 0.0;
+        for (int l = 1; l <= J / 2; l++) acc += std::cos(l * kPiD * (2.0 * j + 1.0) / J) / (4.0 * l * l - 1.0);
+        w[j] = 2.0 / J * (1.0 - 2.0 * acc);
+    }
+}
+
+// Kress map w(tau; d) of Eq. wMap / Eq. vMap on [0, 2 pi] and its derivative.
+inline double kress_nu(double t, double d) {
+    const double a = (kPiD - t) / kPiD;
+    return (1.0 / d - 0.5) * a * a * a + (1.0 / d) * (t - kPiD) / kPiD + 0.5;
+}
+inline double kress_dnu(double t, double d) {
+    const double a = (kPiD - t) / kPiD;
+    return -3.0 / kPiD * (1.0 / d - 0.5) * a * a + 1.0 / (d * kPiD);
+}
+inline void kress_w(double t, double d, double &w, double &dw) {
+    const double n1 = kress_nu(t, d), n2 = kress_nu(2.0 * kPiD - t, d);
+    const double A = std::pow(n1, d), B = std::pow(n2, d);
+    const double dA = d * std::pow(n1, d - 1.0) * kress_dnu(t, d);
+    const double dB = -d * std::pow(n2, d - 1.0) * kress_dnu(2.0 * kPiD - t, d);
+    const double S = A + B;
+    w = 2.0 * kPiD * A / S;
+    dw = 2.0 * kPiD * (dA * B - A * dB) / (S * S);
+}
+
+// Change of variables xi_alpha(tau; d) of Eq. CoV, clustering at alpha, and d xi / d tau.
+inline void cov(double alpha, double tau, double d, double &xi, double &dxi) {
+    double w, dw;
+    if (alpha >= 1.0) {
+        kress_w(kPiD * std::fabs((tau - 1.0) / 2.0), d, w, dw);
+        xi = 1.0 - (2.0 / kPiD) * w;
+        dxi = dw;  // d/dtau of -(2/pi) w(pi (1 - tau) / 2)
+    } else if (alpha <= -1.0) {
+        kress_w(kPiD * std::fabs((tau + 1.0) / 2.0), d, w, dw);
+        xi = -1.0 + (2.0 / kPiD) * w;
+        dxi = dw;
+    } else {
+        const double sg = tau > 0 ? 1.0 : (tau < 0 ? -1.0 : 0.0);
+        kress_w(kPiD * std::fabs(tau), d, w, dw);
+        xi = alpha + (sg - alpha) / kPiD * w;
+        dxi = (1.0 - alpha * sg) * dw;
+    }
+}
+
+// Tensor Chebyshev interpolant of one patch's node positions:
+// y_a(u, v) = sum_{n,p} c[(a * m + n) * m + p] T_n(u) T_p(v).
+struct PatchMap {
+    int m = 0;
+    std::vector<double> c;  // 3 m m
+    double ctr[3] = {0, 0, 0}, rad = 0;
+    double orient = 1.0;    // +-1: sign that makes y_u x y_v point like the caller's normals
+
+    void eval(double u, double v, double *y, double *yu, double *yv, std::vector<double> &tmp) const {
+        tmp.resize(4 * (size_t)m);
+        double *Tu = tmp.data(), *dTu = Tu + m, *Tv = dTu + m, *dTv = Tv + m;
+        cheb_vals(m, u, Tu, dTu);
+        cheb_vals(m, v, Tv, dTv);
+        for (int a = 0; a < 3; a++) {
+            double s = 0, su = 0, sv = 0;
+            for (int n = 0; n < m; n++) {
+                const double *cr = &c[((size_t)a * m + n) * m];
+                double r = 0, rv = 0;
+                for (int p = 0; p < m; p++) {
+                    r += cr[p] * Tv[p];
+                    rv += cr[p] * dTv[p];
+                }
+                s += Tu[n] * r;
+                su += dTu[n] * r;
+                sv += Tu[n] * rv;
+            }
+            y[a] = s;
+            yu[a] = su;
+            yv[a] = sv;
+        }
+    }
+};
+
+inline void cross(const double *a, const double *b, double *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// Combined-field kernel dPhi/dnu(y) - i eta Phi at (x, y, nu) (Eq. GreenFunction, Eq. double_layer);
+// zero closer than tol.
+inline cd cfie_kernel(double k, double eta, const double *x, const double *y, const double *nu, double tol) {
+    const double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+    const double r = std::sqrt(dot3(d, d));
+    if (!(r >= tol)) return cd(0.0, 0.0);
+    const cd e = std::exp(cd(0.0, k * r)) / (4.0 * kPiD * r);
+    return e * (cd(1.0, -k * r) * dot3(d, nu) / (r * r) - cd(0.0, eta));
+}
+
+}  // namespace
+
+namespace {
+
+// Closest point of patch P to x (Eq. MinNode): projected Gauss-Newton on |x - y(u, v)|^2
+// started at (u0, v0), with coordinates held at the parameter-square boundary while the
+// gradient pushes outward.
+void closest_point(const PatchMap &P, const double *x, double &u, double &v, std::vector<double> &tmp) {
+    double y[3], yu[3], yv[3];
+    for (int it = 0; it < 60; it++) {
+        P.eval(u, v, y, yu, yv, tmp);
+        const double r[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+        const double gu = dot3(yu, r), gv = dot3(yv, r);
+        const double a = dot3(yu, yu), b = dot3(yu, yv), c = dot3(yv, yv);
+        const bool fu = (u >= 1.0 && gu > 0) || (u <= -1.0 && gu < 0);  // u held at the boundary
+        const bool fv = (v >= 1.0 && gv > 0) || (v <= -1.0 && gv < 0);
+        double du = 0, dv = 0;
+        if (!fu && !fv) {
+            const double det = a * c - b * b;
+            if (!(det > 0)) break;
+            du = (c * gu - b * gv) / det;
+            dv = (a * gv - b * gu) / det;
+        } else if (!fu) {
+            du = gu / a;
+        } else if (!fv) {
+            dv = gv / c;
+        }
+        const double un = std::min(1.0, std::max(-1.0, u + du)), vn = std::min(1.0, std::max(-1.0, v + dv));
+        const double step = std::max(std::fabs(un - u), std::fabs(vn - v));
+        u = un;
+        v = vn;
+        if (step < 1e-15) break;
+    }
+}
+
+}  // namespace
+
+// Builds C (CSR over the caller's point order; values complex128 interleaved).
+static ifgf_status build_rp(const double *xyz, const double *nrm, const double *w, int64_t N, const int32_t *patch_node,
+                            int m, double k, double eta, double delta, int nbeta, double dgrade,
+                            std::vector<int64_t> &rowptr, std::vector<int32_t> &col, std::vector<double> &val) {
+    const int mm = m * m;
+    const int64_t Q = N / mm;
+    std::vector<int64_t> node_pt((size_t)N, -1);  // (q, i, j) -> caller index
+    for (int64_t l = 0; l < N; l++) {
+        const int32_t t = patch_node[l];
+        if (t < 0 || t >= N || node_pt[t] >= 0) {
+            set_error("patch_node must be a permutation of 0..N-1 (entry %lld = %d)", (long long)l, (int)t);
+            return IFGF_EINVAL;
+        }
+        node_pt[t] = l;
+    }
+    std::vector<double> sm, wm, sb, wb;
+    fejer_rule(m, sm, wm);
+    fejer_rule(nbeta, sb, wb);
+    // alpha_n T_n(s_i) / m: l_i(u) = sum_n lag[i * m + n] T_n(u) (Eq. ChebyCoeff folded in)
+    std::vector<double> lag((size_t)mm), Tn(m), dTn(m);
+    for (int i = 0; i < m; i++) {
+        cheb_vals(m, sm[i], Tn.data(), dTn.data());
+        for (int n = 0; n < m; n++) lag[(size_t)i * m + n] = (n == 0 ? 1.0 : 2.0) * Tn[n] / m;
+    }
+    // root-box side (AABB max extent (1 + 2^-30)) for the kernel cut-off
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t l = 0; l < N; l++)
+        for (int a = 0; a < 3; a++) {
+            lo[a] = std::min(lo[a], xyz[3 * l + a]);
+            hi[a] = std::max(hi[a], xyz[3 * l + a]);
+        }
+    const double L = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]}) * (1.0 + std::ldexp(1.0, -30));
+    const double tol = 1e-14 * L;
+
+    // patch interpolants (coefficients from the node positions, Eq. ChebyCoeff per coordinate)
+    std::vector<PatchMap> P((size_t)Q);
+#pragma omp parallel
+    {
+        std::vector<double> tmp;
+        std::vector<double> T(m), dT(m);
+#pragma omp for schedule(static)
+        for (int64_t q = 0; q < Q; q++) {
+            PatchMap &pm = P[q];
+            pm.m = m;
+            pm.c.assign(3 * (size_t)mm, 0.0);
+            for (int i = 0; i < m; i++)
+                for (int j = 0; j < m; j++) {
+                    const double *y = xyz + 3 * node_pt[q * mm + i * m + j];
+                    for (int a = 0; a < 3; a++)
+                        for (int n = 0; n < m; n++) {
+                            const double li = lag[(size_t)i * m + n];
+                            for (int p = 0; p < m; p++) pm.c[((size_t)a * m + n) * m + p] += y[a] * li * lag[(size_t)j * m + p];
+                        }
+                }
+            double cx[3] = {0, 0, 0};
+            for (int t = 0; t < mm; t++)
+                for (int a = 0; a < 3; a++) cx[a] += xyz[3 * node_pt[q * mm + t] + a] / mm;
+            double rad = 0;
+            for (int t = 0; t < mm; t++) {
+                const double *y = xyz + 3 * node_pt[q * mm + t];
+                rad = std::max(rad, std::sqrt((y[0] - cx[0]) * (y[0] - cx[0]) + (y[1] - cx[1]) * (y[1] - cx[1]) +
+                                              (y[2] - cx[2]) * (y[2] - cx[2])));
+            }
+            for (int a = 0; a < 3; a++) pm.ctr[a] = cx[a];
+            pm.rad = 1.25 * rad;  // the interpolant's patch between and just beyond the nodes
+            // orientation from the node nearest the patch centre
+            const int ic = m / 2, jc = m / 2;
+            const int64_t lc = node_pt[q * mm + ic * m + jc];
+            double y[3], yu[3], yv[3], nn[3];
+            pm.eval(sm[ic], sm[jc], y, yu, yv, tmp);
+            cross(yu, yv, nn);
+            pm.orient = dot3(nn, nrm + 3 * lc) >= 0 ? 1.0 : -1.0;
+        }
+    }
+
+    std::vector<std::vector<std::pair<int32_t, cd>>> rows((size_t)N);
+    int bad = 0;
+#pragma omp parallel
+    {
+        std::vector<double> tmp, ua(nbeta), wua(nbeta), vb(nbeta), wvb(nbeta);
+        std::vector<double> Tu((size_t)nbeta * m), dTu((size_t)nbeta * m), Tv((size_t)nbeta * m), dTv((size_t)nbeta * m);
+        std::vector<double> E((size_t)3 * m * nbeta), Ev((size_t)3 * m * nbeta);
+        std::vector<double> Lu((size_t)nbeta * m), Lv((size_t)nbeta * m);
+        std::vector<cd> G((size_t)nbeta * nbeta), H((size_t)m * nbeta);
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t l = 0; l < N; l++) {
+            const double *x = xyz + 3 * l;
+            const int64_t ql = patch_node[l] / mm;
+            auto &row = rows[l];
+            for (int64_t q = 0; q < Q; q++) {
+                const PatchMap &pm = P[q];
+                const double dc = std::sqrt((x[0] - pm.ctr[0]) * (x[0] - pm.ctr[0]) + (x[1] - pm.ctr[1]) * (x[1] - pm.ctr[1]) +
+                                            (x[2] - pm.ctr[2]) * (x[2] - pm.ctr[2]));
+                if (q != ql && dc > pm.rad + delta) continue;
+                // closest patch point (Eq. MinNode): exact for the target's own patch
+                double ub, vb_;
+                if (q == ql) {
+                    const int t = patch_node[l] % mm;
+                    ub = sm[t / m];
+                    vb_ = sm[t % m];
+                } else {
+                    double best = INFINITY;
+                    int tb = 0;
+                    for (int t = 0; t < mm; t++) {
+                        const double *y = xyz + 3 * node_pt[q * mm + t];
+                        const double d2 = (x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) + (x[2] - y[2]) * (x[2] - y[2]);
+                        if (d2 < best) {
+                            best = d2;
+                            tb = t;
+                        }
+                    }
+                    ub = sm[tb / m];
+                    vb_ = sm[tb % m];
+                    closest_point(pm, x, ub, vb_, tmp);
+                    double y[3], yu[3], yv[3];
+                    pm.eval(ub, vb_, y, yu, yv, tmp);
+                    const double dd = std::sqrt((x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) + (x[2] - y[2]) * (x[2] - y[2]));
+                    if (!(dd <= delta)) continue;  // regular interaction (Eq. ReguGridPts)
+                }
+                // graded Fejer nodes (Eq. CovNodesWeights)
+                for (int a = 0; a < nbeta; a++) {
+                    double xi, dxi;
+                    cov(ub, sb[a], dgrade, xi, dxi);
+                    ua[a] = xi;
+                    wua[a] = dxi * wb[a];
+                    cov(vb_, sb[a], dgrade, xi, dxi);
+                    vb[a] = xi;
+                    wvb[a] = dxi * wb[a];
+                    cheb_vals(m, ua[a], &Tu[(size_t)a * m], &dTu[(size_t)a * m]);
+                    cheb_vals(m, vb[a], &Tv[(size_t)a * m], &dTv[(size_t)a * m]);
+                }
+                // patch map on the graded grid: E[c][n][b] = sum_p coef T_p(v_b), Ev with T_p'
+                for (int c = 0; c < 3; c++)
+                    for (int n = 0; n < m; n++) {
+                        const double *cr = &pm.c[((size_t)c * m + n) * m];
+                        for (int b = 0; b < nbeta; b++) {
+                            double s = 0, sv = 0;
+                            for (int p = 0; p < m; p++) {
+                                s += cr[p] * Tv[(size_t)b * m + p];
+                                sv += cr[p] * dTv[(size_t)b * m + p];
+                            }
+                            E[((size_t)c * m + n) * nbeta + b] = s;
+                            Ev[((size_t)c * m + n) * nbeta + b] = sv;
+                        }
+                    }
+                for (int a = 0; a < nbeta; a++)
+                    for (int b = 0; b < nbeta; b++) {
+                        double y[3], yu[3], yv[3];
+                        for (int c = 0; c < 3; c++) {
+                            double s = 0, su = 0, sv = 0;
+                            for (int n = 0; n < m; n++) {
+                                const size_t o = ((size_t)c * m + n) * nbeta + b;
+                                s += Tu[(size_t)a * m + n] * E[o];
+                                su += dTu[(size_t)a * m + n] * E[o];
+                                sv += Tu[(size_t)a * m + n] * Ev[o];
+                            }
+                            y[c] = s;
+                            yu[c] = su;
+                            yv[c] = sv;
+                        }
+                        double nn[3];
+                        cross(yu, yv, nn);
+                        const double J = std::sqrt(dot3(nn, nn));
+                        const double nu[3] = {pm.orient * nn[0] / J, pm.orient * nn[1] / J, pm.orient * nn[2] / J};
+                        G[(size_t)a * nbeta + b] = cfie_kernel(k, eta, x, y, nu, tol) * (J * wua[a] * wvb[b]);
+                    }
+                // c_ij = sum_ab G_ab l_i(u_a) l_j(v_b)
+                for (int a = 0; a < nbeta; a++)
+                    for (int i = 0; i < m; i++) {
+                        double su = 0, sv = 0;
+                        for (int n = 0; n < m; n++) {
+                            su += lag[(size_t)i * m + n] * Tu[(size_t)a * m + n];
+                            sv += lag[(size_t)i * m + n] * Tv[(size_t)a * m + n];
+                        }
+                        Lu[(size_t)a * m + i] = su;
+                        Lv[(size_t)a * m + i] = sv;
+                    }
+                for (int i = 0; i < m; i++)
+                    for (int b = 0; b < nbeta; b++) {
+                        cd s = 0;
+                        for (int a = 0; a < nbeta; a++) s += Lu[(size_t)a * m + i] * G[(size_t)a * nbeta + b];
+                        H[(size_t)i * nbeta + b] = s;
+                    }
+                for (int i = 0; i < m; i++)
+                    for (int j = 0; j < m; j++) {
+                        cd s = 0;
+                        for (int b = 0; b < nbeta; b++) s += H[(size_t)i * nbeta + b] * Lv[(size_t)b * m + j];
+                        const int64_t lp = node_pt[q * mm + i * m + j];
+                        if (lp != l) s -= cfie_kernel(k, eta, x, xyz + 3 * lp, nrm + 3 * lp, tol) * w[lp];
+                        if (!std::isfinite(s.real()) || !std::isfinite(s.imag())) {
+#pragma omp atomic write
+                            bad = 1;
+                        }
+                        row.emplace_back((int32_t)lp, s);
+                    }
+            }
+        }
+    }
+    if (bad) {
+        set_error("non-finite correction entry (degenerate patch geometry?)");
+        return IFGF_EINVAL;
+    }
+    rowptr.assign((size_t)N + 1, 0);
+    for (int64_t l = 0; l < N; l++) rowptr[l + 1] = rowptr[l] + (int64_t)rows[l].size();
+    col.resize((size_t)rowptr[N]);
+    val.resize(2 * (size_t)rowptr[N]);
+    for (int64_t l = 0; l < N; l++) {
+        int64_t o = rowptr[l];
+        for (const auto &e : rows[l]) {
+            col[o] = e.first;
+            val[2 * o] = e.second.real();
+            val[2 * o + 1] = e.second.imag();
+            o++;
+        }
+    }
+    return IFGF_OK;
+}
+
+}  // namespace ifgf
+
+using namespace ifgf;
+
+extern "C" {
+
+ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const double *weights, int64_t N,
+                               const int32_t *patch_node, int32_t m, double k, double eta, double delta,
+                               int32_t n_beta, double d_grade, int64_t **rowptr_out, int32_t **col_out,
+                               double **val_out) {
+    clear_error();
+    if (!rowptr_out || !col_out || !val_out) {
+        set_error("null output pointer");
+        return IFGF_EINVAL;
+    }
+    *rowptr_out = nullptr;
+    *col_out = nullptr;
+    *val_out = nullptr;
+    if (!xyz || !normals || !weights || !patch_node) {
+        set_error("null input array");
+        return IFGF_EINVAL;
+    }
+    if (m < 2 || m > 64 || N < (int64_t)m * m || N % ((int64_t)m * m) != 0 || N > (int64_t)0x7fffffff) {
+        set_error("N (%lld) must be a positive multiple of m * m with 2 <= m <= 64 (m = %d)", (long long)N, (int)m);
+        return IFGF_EINVAL;
+    }
+    if (!(k > 0) || !std::isfinite(k) || !std::isfinite(eta) || !(delta >= 0) || !std::isfinite(delta) ||
+        n_beta < 2 || n_beta > 512 || !(d_grade >= 2) || !std::isfinite(d_grade)) {
+        set_error("invalid k, eta, delta, n_beta or d_grade");
+        return IFGF_EINVAL;
+    }
+    for (int64_t i = 0; i < 3 * N; i++)
+        if (!std::isfinite(xyz[i]) || !std::isfinite(normals[i])) {
+            set_error("non-finite point or normal");
+            return IFGF_EINVAL;
+        }
+    std::vector<int64_t> rp;
+    std::vector<int32_t> cl;
+    std::vector<double> vl;
+    ifgf_status st;
+    try {
+        st = build_rp(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rp, cl, vl);
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return IFGF_ENOMEM;
+    }
+    if (st != IFGF_OK) return st;
+    int64_t *r = (int64_t *)std::malloc(sizeof(int64_t) * rp.size());
+    int32_t *c = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(cl.size(), 1));
+    double *v = (double *)std::malloc(sizeof(double) * std::max<size_t>(vl.size(), 1));
+    if (!r || !c || !v) {
+        std::free(r);
+        std::free(c);
+        std::free(v);
+        set_error("host allocation failed");
+        return IFGF_ENOMEM;
+    }
+    std::memcpy(r, rp.data(), sizeof(int64_t) * rp.size());
+    if (!cl.empty()) std::memcpy(c, cl.data(), sizeof(int32_t) * cl.size());
+    if (!vl.empty()) std::memcpy(v, vl.data(), sizeof(double) * vl.size());
+    *rowptr_out = r;
+    *col_out = c;
+    *val_out = v;
+    return IFGF_OK;
+}
+
+void ifgf_free(void *ptr) { std::free(ptr); }
+
+}  // extern "C"

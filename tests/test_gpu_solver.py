@@ -101,3 +101,24 @@ def test_gmres_edge_cases(B):
     assert not ok and it == 0
     with pytest.raises(B.IFGFError, match="EINVAL"):
         plan.gmres(b, restart=0)
+
+
+def test_library_rp_correction_on_the_gpu_apply(B):
+    """The product path end to end: the library's own host RP correction
+    (ifgf_rp_correction) attached to a plan and applied on the GPU reproduces the sphere's
+    eigen-relations like the oracle's correction does."""
+    from workloads import patch_node_index
+
+    n, m, k = 32, 8, 2 * math.pi
+    s = cube_sphere(n, m)
+    rp, col, val = B.rp_correction(s.points, s.normals, s.weights, patch_node_index(s), m, k, k,
+                                   delta=math.pi / (2 * (n // m)))
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8))
+    plan.set_correction(rp, col, val)
+    for l, mm in ((0, 0), (2, 1), (5, -3), (9, 4)):
+        Y = mie.real_ylm(l, mm, s.points).astype(np.complex128)
+        lam = mie.eigenvalue(l, k, k)
+        assert rel(plan.apply(torch.from_numpy(Y).cuda()).cpu().numpy(), lam * Y) < 1e-4, (l, mm)
+        assert rel(plan.apply(torch.from_numpy(Y.astype(np.complex64)).cuda()).cpu().numpy(), lam * Y) < 1e-4
+    assert plan.missed_lookups() == 0
+    plan.close()

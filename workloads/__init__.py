@@ -9,6 +9,7 @@ from .geometry import (  # noqa: F401
     fejer_weights,
     cube_sphere,
     ellipsoid,
+    patch_node_index,
     star_body,
     sphere_workload,
     random_density,

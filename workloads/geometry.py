@@ -129,6 +129,22 @@ def _finish(name, x, xu, xv, wpar, pid, uv, meta):
                    np.ascontiguousarray(wpar * J), pid, uv, meta)
 
 
+def patch_node_index(s: Surface) -> np.ndarray:
+    """For every point, q * m^2 + i * m + j: the point is node (i, j) of patch q, where i and j
+    index the Chebyshev-Gauss nodes of Eq. FejersNodes (cos(pi (2i+1) / (2m))) along the patch's
+    own u and v parameters.  For the cube-sphere family (sphere, ellipsoid, star body)."""
+    n, m = int(s.meta["n"]), int(s.meta["m"])
+    P = n // m
+    t = fejer_nodes(m)
+    pid = s.patch.astype(np.int64)
+    su, sv = (pid // P) % P, pid % P
+    ul = P * (s.uv[:, 0] + 1.0) - (2 * su + 1)  # local patch parameters in (-1, 1)
+    vl = P * (s.uv[:, 1] + 1.0) - (2 * sv + 1)
+    i = np.argmin(np.abs(ul[:, None] - t[None, :]), axis=1)
+    j = np.argmin(np.abs(vl[:, None] - t[None, :]), axis=1)
+    return (pid * m * m + i * m + j).astype(np.int32)
+
+
 def cube_sphere(n: int, m: int | None = None, radius: float = 1.0) -> Surface:
     """Sphere of the given radius: 6 faces x n x n points, m x m Fejer sub-patches.
 
