@@ -191,7 +191,7 @@ void closest_point(const PatchMap &P, const double *x, double &u, double &v, std
 // Builds C (CSR over the caller's point order; values complex128 interleaved).
 static ifgf_status build_rp(const double *xyz, const double *nrm, const double *w, int64_t N, const int32_t *patch_node,
                             int m, double k, double eta, double delta, int nbeta, double dgrade,
-                            std::vector<int64_t> &rowptr, std::vector<int32_t> &col, std::vector<double> &val) {
+                            int64_t **rowptr_out, int32_t **col_out, double **val_out) {
     const int mm = m * m;
     const int64_t Q = N / mm;
     std::vector<int64_t> node_pt((size_t)N, -1);  // (q, i, j) -> caller index
@@ -390,10 +390,24 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         set_error("non-finite correction entry (degenerate patch geometry?)");
         return IFGF_EINVAL;
     }
-    rowptr.assign((size_t)N + 1, 0);
+    // CSR straight into the caller's arrays, each row released once copied (bounds the peak)
+    int64_t *rowptr = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)N + 1));
+    if (!rowptr) {
+        set_error("host allocation failed");
+        return IFGF_ENOMEM;
+    }
+    rowptr[0] = 0;
     for (int64_t l = 0; l < N; l++) rowptr[l + 1] = rowptr[l] + (int64_t)rows[l].size();
-    col.resize((size_t)rowptr[N]);
-    val.resize(2 * (size_t)rowptr[N]);
+    const size_t nnz = (size_t)rowptr[N];
+    int32_t *col = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(nnz, 1));
+    double *val = (double *)std::malloc(sizeof(double) * 2 * std::max<size_t>(nnz, 1));
+    if (!col || !val) {
+        std::free(rowptr);
+        std::free(col);
+        std::free(val);
+        set_error("host allocation failed (%zu correction entries)", nnz);
+        return IFGF_ENOMEM;
+    }
     for (int64_t l = 0; l < N; l++) {
         int64_t o = rowptr[l];
         for (const auto &e : rows[l]) {
@@ -402,7 +416,11 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
             val[2 * o + 1] = e.second.imag();
             o++;
         }
+        std::vector<std::pair<int32_t, cd>>().swap(rows[l]);
     }
+    *rowptr_out = rowptr;
+    *col_out = col;
+    *val_out = val;
     return IFGF_OK;
 }
 
@@ -442,34 +460,13 @@ ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const d
             set_error("non-finite point or normal");
             return IFGF_EINVAL;
         }
-    std::vector<int64_t> rp;
-    std::vector<int32_t> cl;
-    std::vector<double> vl;
-    ifgf_status st;
     try {
-        st = build_rp(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rp, cl, vl);
+        return build_rp(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rowptr_out, col_out,
+                        val_out);
     } catch (const std::bad_alloc &) {
         set_error("host allocation failed");
         return IFGF_ENOMEM;
     }
-    if (st != IFGF_OK) return st;
-    int64_t *r = (int64_t *)std::malloc(sizeof(int64_t) * rp.size());
-    int32_t *c = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(cl.size(), 1));
-    double *v = (double *)std::malloc(sizeof(double) * std::max<size_t>(vl.size(), 1));
-    if (!r || !c || !v) {
-        std::free(r);
-        std::free(c);
-        std::free(v);
-        set_error("host allocation failed");
-        return IFGF_ENOMEM;
-    }
-    std::memcpy(r, rp.data(), sizeof(int64_t) * rp.size());
-    if (!cl.empty()) std::memcpy(c, cl.data(), sizeof(int32_t) * cl.size());
-    if (!vl.empty()) std::memcpy(v, vl.data(), sizeof(double) * vl.size());
-    *rowptr_out = r;
-    *col_out = c;
-    *val_out = v;
-    return IFGF_OK;
 }
 
 void ifgf_free(void *ptr) { std::free(ptr); }
