@@ -147,7 +147,8 @@ inline cd cfie_kernel(double k, double eta, const double *x, const double *y, co
     const double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
     const double r = std::sqrt(dot3(d, d));
     if (!(r >= tol)) return cd(0.0, 0.0);
-    const cd e = std::exp(cd(0.0, k * r)) / (4.0 * kPiD * r);
+    const double a = 1.0 / (4.0 * kPiD * r);
+    const cd e(a * std::cos(k * r), a * std::sin(k * r));
     return e * (cd(1.0, -k * r) * dot3(d, nu) / (r * r) - cd(0.0, eta));
 }
 
