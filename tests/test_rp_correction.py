@@ -79,3 +79,24 @@ def test_rp_validation(B):
         B.rp_correction(*args, pn, 8, 1.0, delta=0.3, n_beta=1)
     rp, col, val = B.rp_correction(*args, pn, 8, 1.0, delta=0.0)  # own patches only
     assert rp[-1] == s.N * 64 and np.all(np.isfinite(val))
+
+
+def test_single_layer_from_two_couplings(B, oracle_lib):
+    """With c_I = 0 the corrected operator is D - i eta S, so S = i (A_{eta=1} - A_{eta=0}); on the
+    unit sphere that reproduces S[Y_n] = i k j_n(k) h_n(k) Y_n and D[Y_n] = (i k^2 j_n' h_n - 1/2) Y_n."""
+    n, m, k = 32, 8, 2 * math.pi
+    s = cube_sphere(n, m)
+    pn = patch_node_index(s)
+    delta = math.pi / (2 * (n // m))
+
+    def A(eta, Y):
+        rp, col, val = B.rp_correction(s.points, s.normals, s.weights, pn, m, k, eta, delta=delta)
+        return oracle_lib.direct(s.points, s.normals, s.weights, k, eta, Y, cI=0.0) + oracle_lib.csr_apply(rp, col, val, Y)
+
+    # (k = 2 pi is a zero of j_0, where S has the eigenvalue 0: start at degree 1)
+    for l, mm in ((1, 1), (3, 2), (7, -4)):
+        Y = mie.real_ylm(l, mm, s.points)[None, :].astype(complex)
+        D = A(0.0, Y)
+        S = 1j * (A(1.0, Y) - D)
+        assert rel(S, mie.single_layer_eigenvalue(l, k) * Y) < 3e-5, l
+        assert rel(D, mie.double_layer_eigenvalue(l, k) * Y) < 3e-5, l
