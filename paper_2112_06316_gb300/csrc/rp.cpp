@@ -148,7 +148,9 @@ inline cd cfie_kernel(double k, double eta, const double *x, const double *y, co
     const double r = std::sqrt(dot3(d, d));
     if (!(r >= tol)) return cd(0.0, 0.0);
     const double a = 1.0 / (4.0 * kPiD * r);
-    const cd e(a * std::cos(k * r), a * std::sin(k * r));
+    double sn, cs;
+    ::sincos(k * r, &sn, &cs);
+    const cd e(a * cs, a * sn);
     return e * (cd(1.0, -k * r) * dot3(d, nu) / (r * r) - cd(0.0, eta));
 }
 
@@ -273,6 +275,7 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         std::vector<double> E((size_t)3 * m * nbeta), Ev((size_t)3 * m * nbeta);
         std::vector<double> Lu((size_t)nbeta * m), Lv((size_t)nbeta * m);
         std::vector<cd> G((size_t)nbeta * nbeta), H((size_t)m * nbeta);
+        std::vector<double> Yg((size_t)9 * nbeta * nbeta);
 #pragma omp for schedule(dynamic, 16)
         for (int64_t l = 0; l < N; l++) {
             const double *x = xyz + 3 * l;
@@ -334,20 +337,30 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
                             Ev[((size_t)c * m + n) * nbeta + b] = sv;
                         }
                     }
+                // y, y_u, y_v on the grid, coordinate-major rows over b (contiguous, vectorisable)
+                std::fill(Yg.begin(), Yg.end(), 0.0);
+                for (int c = 0; c < 3; c++)
+                    for (int a = 0; a < nbeta; a++) {
+                        double *yr = &Yg[((size_t)(3 * c + 0) * nbeta + a) * nbeta];
+                        double *yur = &Yg[((size_t)(3 * c + 1) * nbeta + a) * nbeta];
+                        double *yvr = &Yg[((size_t)(3 * c + 2) * nbeta + a) * nbeta];
+                        for (int n = 0; n < m; n++) {
+                            const double tu = Tu[(size_t)a * m + n], dtu = dTu[(size_t)a * m + n];
+                            const double *e = &E[((size_t)c * m + n) * nbeta], *ev = &Ev[((size_t)c * m + n) * nbeta];
+                            for (int b = 0; b < nbeta; b++) {
+                                yr[b] += tu * e[b];
+                                yur[b] += dtu * e[b];
+                                yvr[b] += tu * ev[b];
+                            }
+                        }
+                    }
                 for (int a = 0; a < nbeta; a++)
                     for (int b = 0; b < nbeta; b++) {
                         double y[3], yu[3], yv[3];
                         for (int c = 0; c < 3; c++) {
-                            double s = 0, su = 0, sv = 0;
-                            for (int n = 0; n < m; n++) {
-                                const size_t o = ((size_t)c * m + n) * nbeta + b;
-                                s += Tu[(size_t)a * m + n] * E[o];
-                                su += dTu[(size_t)a * m + n] * E[o];
-                                sv += Tu[(size_t)a * m + n] * Ev[o];
-                            }
-                            y[c] = s;
-                            yu[c] = su;
-                            yv[c] = sv;
+                            y[c] = Yg[((size_t)(3 * c + 0) * nbeta + a) * nbeta + b];
+                            yu[c] = Yg[((size_t)(3 * c + 1) * nbeta + a) * nbeta + b];
+                            yv[c] = Yg[((size_t)(3 * c + 2) * nbeta + a) * nbeta + b];
                         }
                         double nn[3];
                         cross(yu, yv, nn);
