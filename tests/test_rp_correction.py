@@ -100,3 +100,18 @@ def test_single_layer_from_two_couplings(B, oracle_lib):
         S = 1j * (A(1.0, Y) - D)
         assert rel(S, mie.single_layer_eigenvalue(l, k) * Y) < 3e-5, l
         assert rel(D, mie.double_layer_eigenvalue(l, k) * Y) < 3e-5, l
+
+
+def test_rp_quadrature_self_convergence(B, oracle_lib):
+    """Doubling the RP quadrature points (Eq. BetaCov) shrinks the change of C phi by more
+    than ten: 24 -> 48 -> 96 points per direction."""
+    s = cube_sphere(16, 8)
+    pn = patch_node_index(s)
+    sig = random_density(s.N, 1, 2)
+    out = {}
+    for nb in (24, 48, 96):
+        rp, col, val = B.rp_correction(s.points, s.normals, s.weights, pn, 8, 2 * math.pi, delta=math.pi / 4,
+                                       n_beta=nb)
+        out[nb] = oracle_lib.csr_apply(rp, col, val, sig)
+    e24, e48 = rel(out[24], out[96]), rel(out[48], out[96])
+    assert e48 < 0.1 * e24 and e48 < 1e-3, (e24, e48)
