@@ -266,10 +266,47 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         }
     }
 
+    // Uniform grid over the patch centres with cells no smaller than max radius + delta: a patch
+    // that can lie within delta of x has its centre in x's cell or one of the 26 around it.
+    double rmax = 0, clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t q = 0; q < Q; q++) {
+        rmax = std::max(rmax, P[q].rad);
+        for (int a = 0; a < 3; a++) {
+            clo[a] = std::min(clo[a], P[q].ctr[a]);
+            chi[a] = std::max(chi[a], P[q].ctr[a]);
+        }
+    }
+    double hc = std::max(rmax + delta, 1e-300);
+    int64_t gd[3];
+    for (;;) {
+        for (int a = 0; a < 3; a++) gd[a] = (int64_t)std::floor((chi[a] - clo[a]) / hc) + 1;
+        if (gd[0] * gd[1] * gd[2] <= 8 * Q + 4096) break;
+        hc *= 1.5;  // coarser cells keep the grid within a few entries per patch
+    }
+    auto cell_of = [&](const double *c, int64_t *ijk) {
+        for (int a = 0; a < 3; a++)
+            ijk[a] = std::min(gd[a] - 1, std::max<int64_t>(0, (int64_t)std::floor((c[a] - clo[a]) / hc)));
+    };
+    std::vector<int64_t> cstart((size_t)(gd[0] * gd[1] * gd[2]) + 1, 0);
+    std::vector<int64_t> clist((size_t)Q);
+    {
+        std::vector<int64_t> cq((size_t)Q);
+        for (int64_t q = 0; q < Q; q++) {
+            int64_t ijk[3];
+            cell_of(P[q].ctr, ijk);
+            cq[q] = (ijk[0] * gd[1] + ijk[1]) * gd[2] + ijk[2];
+            cstart[cq[q] + 1]++;
+        }
+        for (size_t c = 0; c + 1 < cstart.size(); c++) cstart[c + 1] += cstart[c];
+        std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+        for (int64_t q = 0; q < Q; q++) clist[fill[cq[q]]++] = q;
+    }
+
     std::vector<std::vector<std::pair<int32_t, cd>>> rows((size_t)N);
     int bad = 0;
 #pragma omp parallel
     {
+        std::vector<int64_t> cand;
         std::vector<double> tmp, ua(nbeta), wua(nbeta), vb(nbeta), wvb(nbeta);
         std::vector<double> Tu((size_t)nbeta * m), dTu((size_t)nbeta * m), Tv((size_t)nbeta * m), dTv((size_t)nbeta * m);
         std::vector<double> E((size_t)3 * m * nbeta), Ev((size_t)3 * m * nbeta);
@@ -281,7 +318,23 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
             const double *x = xyz + 3 * l;
             const int64_t ql = patch_node[l] / mm;
             auto &row = rows[l];
-            for (int64_t q = 0; q < Q; q++) {
+            // candidate patches from the 27 cells around x (ascending patch order)
+            cand.clear();
+            {
+                int64_t ijk[3];
+                cell_of(x, ijk);
+                for (int64_t i0 = std::max<int64_t>(0, ijk[0] - 1); i0 <= std::min(gd[0] - 1, ijk[0] + 1); i0++)
+                    for (int64_t i1 = std::max<int64_t>(0, ijk[1] - 1); i1 <= std::min(gd[1] - 1, ijk[1] + 1); i1++)
+                        for (int64_t i2 = std::max<int64_t>(0, ijk[2] - 1); i2 <= std::min(gd[2] - 1, ijk[2] + 1); i2++) {
+                            const int64_t c = (i0 * gd[1] + i1) * gd[2] + i2;
+                            for (int64_t t = cstart[c]; t < cstart[c + 1]; t++) cand.push_back(clist[t]);
+                        }
+                bool own = false;
+                for (int64_t q : cand) own = own || q == ql;
+                if (!own) cand.push_back(ql);
+                std::sort(cand.begin(), cand.end());
+            }
+            for (int64_t q : cand) {
                 const PatchMap &pm = P[q];
                 const double dc = std::sqrt((x[0] - pm.ctr[0]) * (x[0] - pm.ctr[0]) + (x[1] - pm.ctr[1]) * (x[1] - pm.ctr[1]) +
                                             (x[2] - pm.ctr[2]) * (x[2] - pm.ctr[2]));
