@@ -270,3 +270,70 @@ def test_ifgf_oracle_reaches_direct_sum_to_rounding(oracle_lib):
         y, info = oracle_lib.ifgf(s.points, s.normals, s.weights, p, sig)
         assert info["prop_evals"][3] > 0
         assert rel(y, yd) < 2e-8, (fm, rel(y, yd))
+
+
+# ---------------------------------------------------------------- cone grid per level (Remark cone_seg_size)
+def _cone_grid(oracle_lib, s, k, levels, cone_rule=0):
+    sig = random_density(s.N, 1, 5)
+    _, info = oracle_lib.ifgf(s.points, s.normals, s.weights,
+                              oracle_lib.IFGFParams(k=k, levels=levels, cone_rule=cone_rule), sig)
+    assert info["D"] == levels
+    return {d: (info["ns"][d], info["nC"][d]) for d in range(3, levels + 1)}, info
+
+
+def test_cone_grid_size_rule_16_wavelength_sphere(oracle_lib):
+    """Per-level (n_s, n_C) under the size rule (reading of Remark cone_seg_size and the
+    Fig. 3 text: constant segments while H <= lambda/2, then n_s and n_C double each time the
+    box side doubles), derived by hand for the 16-wavelength unit sphere (k = 16 pi, so
+    lambda = 1/8) with six levels.  The root box side is the point cloud's largest extent, a
+    hair under 2, so H_d = L / 2^(d-1) gives H_d / lambda just under 4, 2, 1, 1/2 for d = 3..6:
+    the leaf (d = 6) keeps (n_S0, n_C0) = (1, 2) and every coarser level doubles both:
+    (2, 4), (4, 8), (8, 16).  With k 1% larger every H_d / lambda moves just above those
+    powers of two, so every level gets one more doubling: (2, 4) at the leaf up to (16, 32).
+    A doubling that fires one level early or late, or an exponent rounded down instead of up
+    (floor instead of ceiling of log2(2 H_d / lambda)), fails one of the two cases."""
+    s = cube_sphere(32, 8)  # N = 6,144; the cone grid depends on H_d and k only
+    grid, info = _cone_grid(oracle_lib, s, 16 * math.pi, 6)
+    assert 1.99 < info["root_side"] < 2.0
+    assert grid == {3: (8, 16), 4: (4, 8), 5: (2, 4), 6: (1, 2)}, grid
+    grid, _ = _cone_grid(oracle_lib, s, 16 * math.pi * 1.01, 6)
+    assert grid == {3: (16, 32), 4: (8, 16), 5: (4, 8), 6: (2, 4)}, grid
+
+
+def test_cone_grid_literal_rule(oracle_lib):
+    """cone_rule = 1, the remark read literally: the leaf level D keeps (n_S0, n_C0) = (1, 2)
+    and n_s, n_C double on the way from level d to d - 1 exactly when k H_d > 1/2.  Unit
+    sphere, root side L = 1.9955 (the Fejer nodes stop short of the poles), five levels:
+    H_5 = L/16 = 0.1247, H_4 = L/8 = 0.2494.
+    * k = pi:     k H_5 = 0.392 (no doubling into level 4), k H_4 = 0.784 (doubling into 3)
+                  -> levels 5, 4, 3 = (1, 2), (1, 2), (2, 4);
+    * k = 1.5 pi: k H_5 = 0.588, k H_4 = 1.175 -> (1, 2), (2, 4), (4, 8).
+    The size rule gives (1, 2) at every level for k = pi (lambda = 2: all H_d <= lambda/2),
+    so the two rules are told apart; at the 16-wavelength sphere (k H_6 = 3.1 > 1/2 at every
+    level) the literal rule coincides with the size rule above."""
+    s = cube_sphere(26)  # N = 4,056
+    grid, info = _cone_grid(oracle_lib, s, math.pi, 5, cone_rule=1)
+    assert abs(info["root_side"] - 1.9955) < 1e-4
+    assert grid == {3: (2, 4), 4: (1, 2), 5: (1, 2)}, grid
+    grid, _ = _cone_grid(oracle_lib, s, 1.5 * math.pi, 5, cone_rule=1)
+    assert grid == {3: (4, 8), 4: (2, 4), 5: (1, 2)}, grid
+    grid, _ = _cone_grid(oracle_lib, s, math.pi, 5, cone_rule=0)
+    assert grid == {3: (1, 2), 4: (1, 2), 5: (1, 2)}, grid
+    grid, _ = _cone_grid(oracle_lib, cube_sphere(32, 8), 16 * math.pi, 6, cone_rule=1)
+    assert grid == {3: (8, 16), 4: (4, 8), 5: (2, 4), 6: (1, 2)}, grid
+
+
+def test_relevant_cones_per_level_roughly_constant(oracle_lib):
+    """Section 3.5: with the cone refinement of Remark cone_seg_size the number of relevant
+    cone segments per level stays roughly constant while the number of boxes grows about
+    fourfold per level on a surface.  8-wavelength sphere (N = 55,296, automatic depth 5 as in
+    Table 1): boxes grow ~20x from level 3 to 5, relevant cones stay within a factor 2.5.  One
+    missing or extra doubling at any level would move that level's count by ~8x."""
+    s, k = sphere_workload(96, 8, 8.0)
+    sig = random_density(s.N, 1, 5)
+    _, info = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k), sig)
+    assert info["D"] == 5
+    nb = [info["nbox"][d] for d in (3, 4, 5)]
+    nrc = [info["nrc"][d] for d in (3, 4, 5)]
+    assert nb[2] / nb[0] > 15, nb
+    assert max(nrc) / min(nrc) < 2.5, nrc
