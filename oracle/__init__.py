@@ -7,7 +7,7 @@ reference legs use this package.  It shares no code with
 * ``direct`` / ``direct_adjoint``: the plain O(N^2) combined-field sum of
   Eq. field1 (kernel of Eq. GreenFunction / Eq. double_layer, identity term of
   Eq. CombLayIE) and its conjugate transpose, on all rows or a row subset.
-* ``ifgf``: Algorithm 1 written loop by loop in FP64 (``oracle.c``).
+* ``ifgf``: the IFGF apply of Section 3.4 in FP64, stage by stage (``oracle.c``).
 * ``field`` / ``far_field``: the combined-layer potential of Eq. CombinedLayer at
   off-surface targets and its far-field pattern (Eq. FarField), plain numpy sums.
 * ``mie``: closed-form sound-soft sphere solutions (module ``oracle.mie``).

@@ -11,11 +11,12 @@
  *                         the combined-field kernel of Eq. CombinedLayer, Eq. GreenFunction,
  *                         Eq. double_layer; the 1/2 identity term of Eq. CombLayIE is cI)
  *   oracle_direct_adjoint_rows: (A^H g)_m = conj(cI) g_m + w_m sum_{l != m} conj(K(x_l, x_m)) g_l
- *   oracle_ifgf:          the same sum accelerated by Algorithm 1 (Section 3.4), written loop by
- *                         loop in the paper's order: leaf evaluation of F at the relevant cone
- *                         nodes, then for d = D..3 interpolation onto cousin points and, for
- *                         d > 3, onto the parent's relevant cone nodes; the level-D neighbour
- *                         interactions by direct summation (Remark level_D_neighboring).
+ *   oracle_ifgf:          the same sum accelerated by the IFGF method of Section 3.4, in stages:
+ *                         the leaf expansions of the analytic factor at the cone-segment
+ *                         interpolation points, then for d = D..3 interpolation onto the cousin
+ *                         points and, for d > 3, onto the parent's interpolation points with
+ *                         re-centring (Eq. cent_fact); the level-D neighbour interactions by
+ *                         direct summation (Remark level_D_neighboring).
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - Chebyshev interpolation uses first-kind nodes cos((2k+1)pi/(2n)) with the discrete-
@@ -25,7 +26,7 @@
  *   - Cone counts (Remark cone_seg_size): cone_rule 0 doubles (n_s, n_C) each time H_d exceeds
  *     lambda/2 * 2^e; cone_rule 1 is the literal remark (leaf level at (nS0, nC0), doubling
  *     from level d to d-1 when k H_d > 1/2).
- *   - Propagation factor (Algorithm 1): the ratio of centred factors E(x; y_child) / E(x; y_parent)
+ *   - Propagation factor (Section 3.4, child to parent): the ratio of centred factors E(x; y_child) / E(x; y_parent)
  *     of Eq. cent_fact.
  *   - Interpolated factors: combined W_C = W~2 - i k W3 - i eta W1 (q = 1) on levels with
  *     H >= lambda/2 and the split pair {W2 (q = 2), W13 = -i k W3 - i eta W1 (q = 1)} below
@@ -668,22 +669,31 @@ int oracle_auto_levels(int64_t N, const double *xyz, double leaf_target) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* Algorithm 1                                                                */
+/* IFGF apply (Section 3.4)                                                   */
+/*                                                                           */
+/* The method splits the sum of Eq. field1 into level-D neighbour pairs,     */
+/* summed directly, and, for every level d = D..3, pairs (x, B) of a box B   */
+/* and a point x in one of B's cousin boxes (Eq. NeighborsCousins).  For the  */
+/* latter the field of B's sources at x is the centred factor E(x; y_B)      */
+/* (Eq. cent_fact) times an analytic factor F_B that is interpolated in the  */
+/* spherical cone segment around y_B containing x (Section 3.2, Eq.          */
+/* ChebyPoly).  F_B is known exactly only at the leaf level; coarser boxes   */
+/* obtain it at their interpolation points from their children's             */
+/* interpolants, re-centred from child to parent.  The stages below follow   */
+/* that order: structure, leaf expansions, one pass per level from the       */
+/* finest to level 3, near field, identity term.                              */
 
-int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const double *nrm, const double *w,
-                int nrhs, const double *sigma, double *out, oracle_info *info) {
-    if (N <= 0 || nrhs <= 0 || nrhs > 64 || !(prm->k > 0) || prm->Ps < 1 || prm->Pang < 1 || prm->Ps > 31 ||
-        prm->Pang > 31)
-        return -1;
-    otree T;
-    memset(&T, 0, sizeof(T));
-    T.N = N; T.xyz = xyz; T.nrm = nrm; T.w = w; T.nrhs = nrhs;
-    T.k = prm->k; T.eta = prm->eta; T.Ps = prm->Ps; T.Pang = prm->Pang; T.P = prm->Ps * prm->Pang * prm->Pang;
+/* Octree, cone grids (Remark cone_seg_size) and relevant cone segments (Eq.
+ * RelevantCones) for the given parameters; allocates the per-level F and C. */
+static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const double *xyz, const double *nrm,
+                      const double *w, int nrhs) {
+    T->N = N; T->xyz = xyz; T->nrm = nrm; T->w = w; T->nrhs = nrhs;
+    T->k = prm->k; T->eta = prm->eta; T->Ps = prm->Ps; T->Pang = prm->Pang; T->P = prm->Ps * prm->Pang * prm->Pang;
     if (prm->root_side > 0) {
-        T.L = prm->root_side;
-        for (int a = 0; a < 3; a++) T.c0[a] = prm->root_center[a];
+        T->L = prm->root_side;
+        for (int a = 0; a < 3; a++) T->c0[a] = prm->root_center[a];
     } else {
-        T.L = root_side_of(N, xyz, T.c0);
+        T->L = root_side_of(N, xyz, T->c0);
     }
     /* level count */
     int D = prm->levels;
@@ -692,36 +702,36 @@ int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const do
         double best = INFINITY;
         D = 3;
         for (int d = 3; d <= 16; d++) {
-            int nb = count_boxes(xyz, N, T.c0, T.L, d);
+            int nb = count_boxes(xyz, N, T->c0, T->L, d);
             double m = fabs(log((double)N / nb / lt));
             if (m < best) { best = m; D = d; }
             if ((double)N / nb < lt / 16.0) break;
         }
     }
     if (D < 3 || D > 16) return -1;
-    T.D = D;
-    for (int i = 0; i < T.Ps; i++) T.ts[i] = cheb_node(i, T.Ps);
-    for (int i = 0; i < T.Pang; i++) T.ta[i] = cheb_node(i, T.Pang);
-    cheb_coeff_matrix(T.Ps, T.As);
-    cheb_coeff_matrix(T.Pang, T.Aa);
+    T->D = D;
+    for (int i = 0; i < T->Ps; i++) T->ts[i] = cheb_node(i, T->Ps);
+    for (int i = 0; i < T->Pang; i++) T->ta[i] = cheb_node(i, T->Pang);
+    cheb_coeff_matrix(T->Ps, T->As);
+    cheb_coeff_matrix(T->Pang, T->Aa);
 
-    double lam = 2.0 * OR_PI / T.k;
-    for (int d = 1; d <= D; d++) build_level(&T, d);
+    double lam = 2.0 * OR_PI / T->k;
+    for (int d = 1; d <= D; d++) build_level(T, d);
     for (int d = 2; d <= D; d++) {
-        olevel *L = &T.lv[d];
+        olevel *L = &T->lv[d];
         L->parent = (int *)malloc(sizeof(int) * L->nbox);
         for (int b = 0; b < L->nbox; b++)
-            L->parent[b] = find_box(&T.lv[d - 1], L->ijk[3 * b] >> 1, L->ijk[3 * b + 1] >> 1, L->ijk[3 * b + 2] >> 1);
+            L->parent[b] = find_box(&T->lv[d - 1], L->ijk[3 * b] >> 1, L->ijk[3 * b + 1] >> 1, L->ijk[3 * b + 2] >> 1);
     }
     /* cone grid per level (Remark cone_seg_size) */
     int e_lit = 0;
     for (int d = D; d >= 3; d--) {
-        olevel *L = &T.lv[d];
+        olevel *L = &T->lv[d];
         int e = 0;
         if (prm->cone_rule == 0) {
             while (L->H > ldexp(0.5 * lam, e)) e++;
         } else {
-            if (d < D && T.k * T.lv[d + 1].H > 0.5) e_lit++;
+            if (d < D && T->k * T->lv[d + 1].H > 0.5) e_lit++;
             e = e_lit;
         }
         L->ns = prm->nS0 << e;
@@ -736,151 +746,198 @@ int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const do
         else L->split = (L->H < 0.5 * lam) ? 1 : 0;
         L->nfac = nfac_of(L);
     }
-    for (int d = 3; d <= D; d++) build_cousins(&T, d);
-    for (int d = 3; d <= D; d++) build_relevant_cones(&T, d);
+    for (int d = 3; d <= D; d++) build_cousins(T, d);
+    for (int d = 3; d <= D; d++) build_relevant_cones(T, d);
     for (int d = 3; d <= D; d++) {
-        olevel *L = &T.lv[d];
-        int64_t sz = L->nrc * L->nfac * nrhs * T.P;
+        olevel *L = &T->lv[d];
+        int64_t sz = L->nrc * L->nfac * nrhs * T->P;
         L->F = (cplx *)calloc(sz > 0 ? sz : 1, sizeof(cplx));
         L->C = (cplx *)calloc(sz > 0 ? sz : 1, sizeof(cplx));
     }
+    return 0;
+}
+
+/* Leaf expansions: at every interpolation point x of every relevant cone segment of every
+ * level-D box, F(x) = sum over the box's sources y of w_y sigma_y W(x, y) with the analytic
+ * factor W of Eq. V3 / Eq. W2W2 / Eq. w23 (the combined factor or the split pair). */
+static int64_t stage_leaf_expansions(otree *T, const cplx *sg) {
+    const int D = T->D;
+    const int64_t N = T->N;
+    const int nrhs = T->nrhs;
+    olevel *L = &T->lv[D];
+    int64_t leaf_evals = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : leaf_evals)
+    for (int b = 0; b < L->nbox; b++) {
+        double y0[3];
+        box_center(T, D, b, y0);
+        for (int rc = L->rc_start[b]; rc < L->rc_start[b + 1]; rc++)
+            for (int nn = 0; nn < T->P; nn++) {
+                double x[3];
+                node_position(T, D, b, L->rc_ids[rc], nn, x);
+                for (int i = 0; i < L->pcount[b]; i++) {
+                    int m = L->perm[L->pstart[b] + i];
+                    cplx W[2];
+                    wfactors(T->k, T->eta, x, y0, L->h, T->xyz + 3 * m, T->nrm + 3 * m, L->split, W);
+                    for (int fc = 0; fc < L->nfac; fc++)
+                        for (int q = 0; q < nrhs; q++)
+                            L->F[fidx(T, L, rc, fc, q) + nn] += T->w[m] * sg[(int64_t)q * N + m] * W[fc];
+                    leaf_evals++;
+                }
+            }
+    }
+    return leaf_evals;
+}
+
+/* Re-centre the child box's interpolated factor at point x (a parent interpolation point)
+ * onto the parent: ratio of centred factors E(x; y_child) / E(x; y_parent) of Eq. cent_fact,
+ * per factor when both levels store the split pair, through the child's field otherwise. */
+static void recentre_to_parent(const otree *T, const olevel *CL, olevel *PL, int crc, const double *t3,
+                               const double *x, const double *yc, const double *yp, int rc, int nn) {
+    for (int q = 0; q < T->nrhs; q++) {
+        if (CL->split && PL->split) {
+            cplx v2 = cheb_eval3(T, CL->C + fidx(T, CL, crc, 0, q), t3);
+            cplx v13 = cheb_eval3(T, CL->C + fidx(T, CL, crc, 1, q), t3);
+            PL->F[fidx(T, PL, rc, 0, q) + nn] += v2 * centred(T->k, x, yc, 2) / centred(T->k, x, yp, 2);
+            PL->F[fidx(T, PL, rc, 1, q) + nn] += v13 * centred(T->k, x, yc, 1) / centred(T->k, x, yp, 1);
+        } else if (CL->split) {
+            cplx v2 = cheb_eval3(T, CL->C + fidx(T, CL, crc, 0, q), t3);
+            cplx v13 = cheb_eval3(T, CL->C + fidx(T, CL, crc, 1, q), t3);
+            PL->F[fidx(T, PL, rc, 0, q) + nn] +=
+                (centred(T->k, x, yc, 2) * v2 + centred(T->k, x, yc, 1) * v13) / centred(T->k, x, yp, 1);
+        } else {
+            cplx v = cheb_eval3(T, CL->C + fidx(T, CL, crc, 0, q), t3);
+            PL->F[fidx(T, PL, rc, 0, q) + nn] += v * centred(T->k, x, yc, 1) / centred(T->k, x, yp, 1);
+        }
+    }
+}
+
+/* One level d of the recursion, for every box B of the level: (a) the factor's interpolant
+ * (Chebyshev coefficients of Eq. ChebyCoeffs per cone segment) evaluated at each point x in
+ * B's cousin boxes and multiplied by E(x; y_B), added to the field u at x; (b) above level 3,
+ * the same interpolant evaluated at every interpolation point of the parent's relevant cone
+ * segments and re-centred onto the parent (recentre_to_parent), accumulated into the parent's
+ * F.  Returns nonzero if a point falls outside the relevant segments (cannot happen for a
+ * consistent tree). */
+static int stage_level(otree *T, int d, cplx *u, int64_t *n_cousin, int64_t *n_parent) {
+    const int64_t N = T->N;
+    const int nrhs = T->nrhs;
+    olevel *L = &T->lv[d];
+    level_coefficients(T, d);
+    int64_t nce = 0, npe = 0;
+    int err = 0;
+    int *plist = (int *)malloc(sizeof(int) * N);
+    for (int b = 0; b < L->nbox && !err; b++) {
+        /* (a) cousin points of B (Eq. NeighborsCousins) */
+        int np = 0;
+        for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) {
+            int cb = L->co_list[c];
+            for (int i = 0; i < L->pcount[cb]; i++) plist[np++] = L->perm[L->pstart[cb] + i];
+        }
+        int lerr = 0;
+#pragma omp parallel for schedule(static) reduction(| : lerr)
+        for (int i = 0; i < np; i++) {
+            int pt = plist[i];
+            cplx res[64];
+            if (field_from_box(T, d, b, T->xyz + 3 * pt, res)) { lerr |= 1; continue; }
+            for (int q = 0; q < nrhs; q++) u[(int64_t)q * N + pt] += res[q];
+        }
+        nce += np;
+        if (lerr) err = 1;
+        /* (b) the parent's interpolation points */
+        if (d > 3 && !err) {
+            olevel *PL = &T->lv[d - 1];
+            int pb = L->parent[b];
+            double yp[3], yc[3];
+            box_center(T, d - 1, pb, yp);
+            box_center(T, d, b, yc);
+            int r0 = PL->rc_start[pb], r1 = PL->rc_start[pb + 1];
+            int64_t nw = (int64_t)(r1 - r0) * T->P;
+#pragma omp parallel for schedule(static) reduction(| : lerr)
+            for (int64_t wi = 0; wi < nw; wi++) {
+                int rc = r0 + (int)(wi / T->P), nn = (int)(wi % T->P);
+                double x[3], t3[3];
+                node_position(T, d - 1, pb, PL->rc_ids[rc], nn, x);
+                int crc = rc_find(L, b, classify(T, d, b, x, t3));
+                if (crc < 0) { lerr |= 1; continue; }
+                recentre_to_parent(T, L, PL, crc, t3, x, yc, yp, rc, nn);
+            }
+            npe += nw;
+            if (lerr) err = 1;
+        }
+    }
+    free(plist);
+    *n_cousin = nce;
+    *n_parent = npe;
+    return err;
+}
+
+/* Level-D neighbour pairs (own box and the 26 adjacent ones) by direct summation of the
+ * combined-field kernel (Remark level_D_neighboring), m != l, pairs closer than 1e-14 L
+ * dropped.  Returns the number of pairs visited. */
+static int64_t stage_near_field(const otree *T, const cplx *sg, cplx *u) {
+    const int D = T->D;
+    const int64_t N = T->N;
+    const int nrhs = T->nrhs;
+    const olevel *L = &T->lv[D];
+    const double tol = 1e-14 * T->L;
+    int64_t near_pairs = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : near_pairs)
+    for (int b = 0; b < L->nbox; b++) {
+        const int *q3 = L->ijk + 3 * b;
+        int nbl[27], nn = 0;
+        for (int o0 = -1; o0 <= 1; o0++)
+            for (int o1 = -1; o1 <= 1; o1++)
+                for (int o2 = -1; o2 <= 1; o2++) {
+                    int c = find_box(L, q3[0] + o0, q3[1] + o1, q3[2] + o2);
+                    if (c >= 0) nbl[nn++] = c;
+                }
+        for (int i = 0; i < L->pcount[b]; i++) {
+            int l = L->perm[L->pstart[b] + i];
+            for (int j = 0; j < nn; j++) {
+                int c = nbl[j];
+                for (int s = 0; s < L->pcount[c]; s++) {
+                    int m = L->perm[L->pstart[c] + s];
+                    if (m == l) continue;
+                    const double *x = T->xyz + 3 * l, *y = T->xyz + 3 * m;
+                    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+                    near_pairs++;
+                    if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
+                    cplx K = cfie_kernel(T->k, T->eta, x, y, T->nrm + 3 * m) * T->w[m];
+                    for (int qq = 0; qq < nrhs; qq++) u[(int64_t)qq * N + l] += K * sg[(int64_t)qq * N + m];
+                }
+            }
+        }
+    }
+    return near_pairs;
+}
+
+int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const double *nrm, const double *w,
+                int nrhs, const double *sigma, double *out, oracle_info *info) {
+    if (N <= 0 || nrhs <= 0 || nrhs > 64 || !(prm->k > 0) || prm->Ps < 1 || prm->Pang < 1 || prm->Ps > 31 ||
+        prm->Pang > 31)
+        return -1;
+    otree T;
+    memset(&T, 0, sizeof(T));
+    if (setup_tree(&T, prm, N, xyz, nrm, w, nrhs)) {
+        free_tree(&T);
+        return -1;
+    }
+    const int D = T.D;
     const cplx *sg = (const cplx *)sigma;
     cplx *u = (cplx *)calloc((size_t)N * nrhs, sizeof(cplx));
     int err = 0;
-    int64_t leaf_evals = 0;
-
-    /* leaf level: F at all relevant interpolation points (Algorithm 1, first loop nest) */
-    {
-        olevel *L = &T.lv[D];
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : leaf_evals)
-        for (int b = 0; b < L->nbox; b++) {
-            double y0[3];
-            box_center(&T, D, b, y0);
-            for (int rc = L->rc_start[b]; rc < L->rc_start[b + 1]; rc++)
-                for (int nn = 0; nn < T.P; nn++) {
-                    double x[3];
-                    node_position(&T, D, b, L->rc_ids[rc], nn, x);
-                    for (int i = 0; i < L->pcount[b]; i++) {
-                        int m = L->perm[L->pstart[b] + i];
-                        cplx W[2];
-                        wfactors(T.k, T.eta, x, y0, L->h, xyz + 3 * m, nrm + 3 * m, L->split, W);
-                        for (int fc = 0; fc < L->nfac; fc++)
-                            for (int q = 0; q < nrhs; q++)
-                                L->F[fidx(&T, L, rc, fc, q) + nn] += w[m] * sg[(int64_t)q * N + m] * W[fc];
-                        leaf_evals++;
-                    }
-                }
-        }
-    }
-
-    /* levels D..3: cousin interpolation and, for d > 3, propagation to the parent */
+    const int64_t leaf_evals = stage_leaf_expansions(&T, sg);
     for (int d = D; d >= 3 && !err; d--) {
-        olevel *L = &T.lv[d];
-        level_coefficients(&T, d);
         int64_t nce = 0, npe = 0;
-        int *plist = (int *)malloc(sizeof(int) * N);
-        for (int b = 0; b < L->nbox && !err; b++) {
-            /* cousin points V B (Eq. NeighborsCousins) */
-            int np = 0;
-            for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) {
-                int cb = L->co_list[c];
-                for (int i = 0; i < L->pcount[cb]; i++) plist[np++] = L->perm[L->pstart[cb] + i];
-            }
-            int lerr = 0;
-#pragma omp parallel for schedule(static) reduction(| : lerr)
-            for (int i = 0; i < np; i++) {
-                int pt = plist[i];
-                cplx res[64];
-                if (field_from_box(&T, d, b, xyz + 3 * pt, res)) { lerr |= 1; continue; }
-                for (int q = 0; q < nrhs; q++) u[(int64_t)q * N + pt] += res[q];
-            }
-            nce += np;
-            if (lerr) err = 1;
-            if (d > 3 && !err) {
-                olevel *PL = &T.lv[d - 1];
-                int pb = L->parent[b];
-                double yp[3];
-                box_center(&T, d - 1, pb, yp);
-                int r0 = PL->rc_start[pb], r1 = PL->rc_start[pb + 1];
-                int64_t nw = (int64_t)(r1 - r0) * T.P;
-#pragma omp parallel for schedule(static) reduction(| : lerr)
-                for (int64_t wi = 0; wi < nw; wi++) {
-                    int rc = r0 + (int)(wi / T.P), nn = (int)(wi % T.P);
-                    double x[3];
-                    node_position(&T, d - 1, pb, PL->rc_ids[rc], nn, x);
-                    cplx res[64];
-                    const olevel *CL = L;
-                    double t3[3];
-                    int cone = classify(&T, d, b, x, t3);
-                    int crc = rc_find(CL, b, cone);
-                    if (crc < 0) { lerr |= 1; continue; }
-                    double yc[3];
-                    box_center(&T, d, b, yc);
-                    for (int q = 0; q < nrhs; q++) {
-                        if (CL->split && PL->split) {
-                            /* split -> split: each factor re-centred with its own q */
-                            cplx v2 = cheb_eval3(&T, CL->C + fidx(&T, CL, crc, 0, q), t3);
-                            cplx v13 = cheb_eval3(&T, CL->C + fidx(&T, CL, crc, 1, q), t3);
-                            PL->F[fidx(&T, PL, rc, 0, q) + nn] += v2 * centred(T.k, x, yc, 2) / centred(T.k, x, yp, 2);
-                            PL->F[fidx(&T, PL, rc, 1, q) + nn] += v13 * centred(T.k, x, yc, 1) / centred(T.k, x, yp, 1);
-                        } else if (CL->split) {
-                            /* split -> combined: evaluate the child's field, re-centre with q = 1 */
-                            cplx v2 = cheb_eval3(&T, CL->C + fidx(&T, CL, crc, 0, q), t3);
-                            cplx v13 = cheb_eval3(&T, CL->C + fidx(&T, CL, crc, 1, q), t3);
-                            res[q] = (centred(T.k, x, yc, 2) * v2 + centred(T.k, x, yc, 1) * v13) /
-                                     centred(T.k, x, yp, 1);
-                            PL->F[fidx(&T, PL, rc, 0, q) + nn] += res[q];
-                        } else {
-                            cplx v = cheb_eval3(&T, CL->C + fidx(&T, CL, crc, 0, q), t3);
-                            PL->F[fidx(&T, PL, rc, 0, q) + nn] += v * centred(T.k, x, yc, 1) / centred(T.k, x, yp, 1);
-                        }
-                    }
-                }
-                npe += nw;
-                if (lerr) err = 1;
-            }
-        }
-        free(plist);
+        err = stage_level(&T, d, u, &nce, &npe);
         if (info) {
             info->cousin_evals[d] = nce;
             if (d > 3) info->prop_evals[d - 1] = npe;
         }
     }
-
-    /* level-D neighbour interactions by direct summation (Remark level_D_neighboring) */
     int64_t near_pairs = 0;
-    if (!err) {
-        olevel *L = &T.lv[D];
-        double tol = 1e-14 * T.L;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : near_pairs)
-        for (int b = 0; b < L->nbox; b++) {
-            const int *q3 = L->ijk + 3 * b;
-            int nbl[27], nn = 0;
-            for (int o0 = -1; o0 <= 1; o0++)
-                for (int o1 = -1; o1 <= 1; o1++)
-                    for (int o2 = -1; o2 <= 1; o2++) {
-                        int c = find_box(L, q3[0] + o0, q3[1] + o1, q3[2] + o2);
-                        if (c >= 0) nbl[nn++] = c;
-                    }
-            for (int i = 0; i < L->pcount[b]; i++) {
-                int l = L->perm[L->pstart[b] + i];
-                for (int j = 0; j < nn; j++) {
-                    int c = nbl[j];
-                    for (int s = 0; s < L->pcount[c]; s++) {
-                        int m = L->perm[L->pstart[c] + s];
-                        if (m == l) continue;
-                        const double *x = xyz + 3 * l, *y = xyz + 3 * m;
-                        double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-                        near_pairs++;
-                        if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
-                        cplx K = cfie_kernel(T.k, T.eta, x, y, nrm + 3 * m) * w[m];
-                        for (int qq = 0; qq < nrhs; qq++) u[(int64_t)qq * N + l] += K * sg[(int64_t)qq * N + m];
-                    }
-                }
-            }
-        }
-    }
-    if (!err) {
+    if (!err) near_pairs = stage_near_field(&T, sg, u);
+    if (!err) {  /* identity term of Eq. CombLayIE */
         cplx *o = (cplx *)out;
         for (int64_t i = 0; i < N * nrhs; i++) o[i] = prm->identity_coef * sg[i] + u[i];
     }

@@ -3,7 +3,7 @@
 //
 // Pipeline of one apply (Algorithm 1 + Remark level_D_neighboring):
 //   gather   a = w * sigma in Morton order
-//   K1 leaf  F^D at every relevant level-D cone node (Algorithm 1, first loop nest)
+//   K1 leaf  F^D at every relevant level-D cone node (Section 3.4, leaf expansions)
 //   K3 prop  for d = D..4: F^{d-1}(x) = sum_children Interp(F^d_child)(x) E(x;y_c)/E(x;y_p)
 //   K4 near  u = level-D neighbour interactions by direct summation
 //   K2 cous  for d = D..3: u(x) += sum_cousin-boxes E(x;y_k) Interp(F^d_k)(x)
