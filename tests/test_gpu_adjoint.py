@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+from parity import check
 from workloads import cube_sphere, random_density, sphere_workload
 
 pytestmark = pytest.mark.gpu
@@ -56,7 +57,7 @@ def test_dot_product_identity_fp64(B, oracle_lib, fm):
     rhs = np.vdot(Ahg, sig)
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
     Ahg32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
-    assert rel(Ahg32, Ahg) < 1e-5
+    check(Ahg32, Ahg, 1e-5)
     assert plan.missed_lookups() == 0
 
 
@@ -72,7 +73,7 @@ def test_mixed_adjoint_orders_and_factors(B, orders, fm):
     g = random_density(s.N, 2, 4)
     a64 = plan.adjoint(cu(g)).cpu().numpy()
     a32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
-    assert rel(a32, a64) < 1e-5
+    check(a32, a64, 1e-5)
     assert plan.missed_lookups() == 0
 
 
@@ -93,9 +94,9 @@ def test_adjoint_matches_oracle_matrix_transpose(B, oracle_lib):
     g = random_density(N, 3, 7)
     ref = (M.conj().T @ g.T).T
     got = plan.adjoint(cu(g)).cpu().numpy()
-    assert rel(got, ref) < 1e-10
+    check(got, ref, 1e-10)
     got32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
-    assert rel(got32, ref) < 1e-5
+    check(got32, ref, 1e-5)
 
 
 def test_adjoint_vs_dense_direct_adjoint(B, oracle_lib):
@@ -124,4 +125,4 @@ def test_mixed_adjoint_full_size(B):
     a64 = plan.adjoint(cu(g)).cpu().numpy()
     a32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
     assert plan.missed_lookups() == 0
-    assert rel(a32, a64) < 1e-5
+    check(a32, a64, 1e-5)

@@ -10,15 +10,12 @@ import math
 import numpy as np
 import pytest
 
+from parity import check, rel
 from workloads import cube_sphere, ellipsoid, random_density, sphere_workload, star_body
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
 @pytest.fixture(scope="module")
@@ -47,9 +44,8 @@ def run_case(lib, oracle_lib, x, n, w, k, prm_kw, nrhs=1, seed=1, tol64=1e-10, t
     y64 = gpu_apply(plan, sig, np.complex128)
     y32 = gpu_apply(plan, sig, np.complex64)
     assert plan.missed_lookups() == 0
-    e64, e32 = rel(y64, ref), rel(y32, ref)
-    assert e64 <= tol64, e64
-    assert e32 <= tol32, e32
+    e64 = check(y64, ref, tol64, "fp64")
+    e32 = check(y32, ref, tol32, "mixed")
     info = plan.info()
     assert info["D"] == oinfo["D"]
     plan.close()
@@ -113,7 +109,7 @@ def test_tiny_inputs(lib, oracle_lib):
         plan = lib.Plan(x, n, w, lib.Params(k=3.0))
         y = gpu_apply(plan, sig, np.complex128)
         ref, _ = oracle_lib.ifgf(x, n, w, oracle_lib.IFGFParams(k=3.0, identity_coef=0.5), sig)
-        assert rel(y, ref) < 1e-12
+        check(y, ref, 1e-12)
         if N == 1:
             assert np.allclose(y, 0.5 * sig, rtol=0, atol=1e-15)
         z = torch.zeros((0, N), dtype=torch.complex128, device="cuda")
@@ -151,8 +147,8 @@ def test_sparse_correction(lib, oracle_lib):
     y1 = gpu_apply(plan, sig, np.complex128)
     y1m = gpu_apply(plan, sig, np.complex64)
     ref = oracle_lib.csr_apply(rowptr, col, val, sig)
-    assert rel(y1 - y0, ref) < 1e-13
-    assert rel(y1m - y0m, ref) < 1e-5
+    check(y1 - y0, ref, 1e-13)
+    check(y1m - y0m, ref, 1e-5)
     plan.set_correction(np.zeros(N + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, complex))
     assert np.array_equal(gpu_apply(plan, sig, np.complex128), y0)
 
@@ -181,7 +177,7 @@ def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
     assert plan.missed_lookups() == 0
     assert rel(y64[:, rows], yd) < 1e-4
     assert rel(y32[:, rows], yd) < 1e-4
-    assert rel(y32, y64) < 1e-5
+    check(y32, y64, 1e-5)
 
 
 @pytest.mark.parametrize("engine", [1, 0])
@@ -207,9 +203,8 @@ def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm, engine):
     assert plan.missed_lookups() == 0
     plan.set_tc_fill(2.0)
     y_cc = gpu_apply(plan, sig, np.complex64)
-    e_ref, e_cc = rel(y_tc, ref), rel(y_tc, y_cc)
-    assert e_ref <= 1e-5, e_ref
-    assert e_cc <= 2e-6, e_cc
+    check(y_tc, ref, 1e-5, "tensor cores vs oracle")
+    check(y_tc, y_cc, 2e-6, "tensor cores vs CUDA cores")
     plan.close()
 
 
@@ -225,9 +220,8 @@ def test_tensor_core_propagation_full_size_level_choice(lib):
     y_cc = gpu_apply(plan, sig, np.complex64)
     y64 = gpu_apply(plan, sig, np.complex128)
     assert plan.missed_lookups() == 0
-    e_cc, e64 = rel(y_def, y_cc), rel(y_def, y64)
-    assert e_cc <= 2e-6, e_cc
-    assert e64 <= 1e-5, e64
+    check(y_def, y_cc, 2e-6, "default vs CUDA-core propagation")
+    check(y_def, y64, 1e-5, "mixed vs fp64")
     plan.close()
 
 
@@ -247,4 +241,32 @@ def test_concurrent_stages_match_single_stream(lib, prec):
     plan.set_profiling(False)
     assert plan.missed_lookups() == 0
     assert np.array_equal(y_par, y_seq)
+    plan.close()
+
+
+@pytest.mark.slow
+def test_bench_configuration_full_size_vs_oracle(lib, oracle_lib):
+    """The timed configuration itself against the oracle over all N: 16-wavelength sphere
+    (6 x 256 x 256 points, N = 393,216, automatic depth 6), orders (5, 8, 8), the combined
+    factor on every level (factor mode 1) and the default tensor-core fill threshold, so the
+    two finest propagation steps run on the tensor cores.  FP64 <= 1e-10 and mixed <= 1e-5
+    against the oracle's Algorithm 1 with identical parameters, in l2 and element-wise."""
+    s, k = sphere_workload(256, 8, 16.0)
+    prm = {"Ps": 5, "Pang": 8, "factor_mode": 1}
+    sig = random_density(s.N, 1, 2)
+    ref, oinfo = oracle_lib.ifgf(s.points, s.normals, s.weights,
+                                 oracle_lib.IFGFParams(k=k, identity_coef=0.5, **prm), sig)
+    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, **prm))
+    info = plan.info()
+    assert info["D"] == oinfo["D"] == 6
+    y64 = gpu_apply(plan, sig, np.complex128)
+    y32 = gpu_apply(plan, sig, np.complex64)
+    assert plan.missed_lookups() == 0
+    plan.set_profiling(True)
+    gpu_apply(plan, sig, np.complex64)
+    kinds = {kd for kd, _, _ in plan.stage_times()}
+    plan.set_profiling(False)
+    assert "prop_tc" in kinds  # the tensor-core propagation ran
+    check(y64, ref, 1e-10, "fp64")
+    check(y32, ref, 1e-5, "mixed")
     plan.close()

@@ -16,6 +16,7 @@ import math
 import numpy as np
 import pytest
 
+from parity import check
 from workloads import random_density, sphere_workload, star_body
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -48,7 +49,7 @@ def test_sphere_128_wavelengths(B, oracle_lib):
     y32 = plan.apply(torch.from_numpy(sig.astype(np.complex64)).cuda()).cpu().numpy()
     y64 = plan.apply(torch.from_numpy(sig).cuda()).cpu().numpy()
     assert plan.missed_lookups() == 0
-    assert rel(y32, y64) < 1e-5
+    check(y32, y64, 1e-5)
     rows = np.random.default_rng(5).choice(s.N, 1000, replace=False)
     ref = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5, rows=rows)
     e64 = rel(y64[:, rows], ref)
@@ -84,7 +85,7 @@ def test_star_body_32_wavelengths_gradients(B, oracle_lib):
     # mixed forward against FP64
     y32 = plan.apply(torch.from_numpy(sig_np.astype(np.complex64)).cuda()).cpu().numpy()
     y64 = plan.apply(torch.from_numpy(sig_np).cuda()).cpu().numpy()
-    assert rel(y32, y64) < 1e-5
+    check(y32, y64, 1e-5)
     # gradients from the hand-written backward (FP64 form)
     sig = torch.from_numpy(sig_np).cuda().requires_grad_(True)
     b = torch.from_numpy(random_density(s.N, 1, 42)[0]).cuda()
@@ -119,7 +120,7 @@ def test_star_body_32_wavelengths_gradients(B, oracle_lib):
     print(f"star body: adjoint vs dense adjoint columns {e64:.2e}")
     assert e64 < 3e-4  # orders (5, 8, 8) reach ~6e-5 on the spheres; the star body is rougher
     assert rel(a32[:, cols], ref) < 1.01 * e64 + 1e-5
-    assert rel(a32, a64) < 1e-5
+    check(a32, a64, 1e-5)
     assert plan.missed_lookups() == 0
     # adjoint / forward device time (mixed), CUDA events, warm
     s32 = torch.from_numpy(sig_np.astype(np.complex64)).cuda().reshape(1, -1)
