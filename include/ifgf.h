@@ -190,8 +190,8 @@ ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g
  * message giving the required size; the workspace grows with N, nrhs, the
  * precision (complex128 needs twice complex64) and the number of relevant cone
  * segments.  The first call on a device looks the array's address up with that
- * device current (once per device); make that first call before any stream
- * capture begins.  All calls share the one array and it keeps the last call's
+ * device current (once per device and CUDA context: again after cudaDeviceReset);
+ * make that first call before any stream capture begins.  All calls share the one array and it keeps the last call's
  * contents (every value an apply reads is written earlier in the same apply, so
  * nothing needs clearing).  Calls that overlap on the GPU -- on different streams,
  * or with ifgf_apply_noalloc of another plan -- race on the array and must be
@@ -292,8 +292,9 @@ ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double 
  * round-robin over `nstreams` forked capture streams so that independent plans
  * overlap), instantiates the graph and launches it on `stream`; later calls with
  * the same buffers, nrhs and precision replay it with one cudaGraphLaunch.  A
- * change of buffers, nrhs, precision, stream count, or of a plan's workspace or
- * correction triggers a new capture.  The group references the plans (they must
+ * change of buffers, nrhs, precision, stream count, of a plan's workspace or
+ * correction, or of a plan's kernel choice (ifgf_plan_set_rhs_block,
+ * ifgf_plan_set_tc_fill, ifgf_plan_set_tc_engine) triggers a new capture.  The group references the plans (they must
  * outlive it) and each plan may appear once.  The paper has no batched apply. */
 typedef struct ifgf_group ifgf_group;
 
@@ -308,6 +309,10 @@ ifgf_status ifgf_group_set_streams(ifgf_group *group, int nstreams);
  * as ifgf_apply; capture failures return IFGF_ECUDA. */
 ifgf_status ifgf_group_apply(ifgf_group *group, const void *const *sigma, void *const *y, const int *nrhs,
                              ifgf_precision prec, void *stream);
+
+/* Number of graphs the group has captured so far (each recapture adds one);
+ * a replay adds nothing.  Errors: IFGF_EINVAL (null group or output). */
+ifgf_status ifgf_group_captures(const ifgf_group *group, int64_t *captures);
 
 /* Release the group and its graph (not the plans). NULL is a no-op. */
 void ifgf_group_destroy(ifgf_group *group);

@@ -91,6 +91,7 @@ _SIGS = [
     ("ifgf_group_create", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
     ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    ("ifgf_group_captures", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     ("ifgf_group_destroy", None, [_VP]),
 ]
 STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc"]
@@ -469,6 +470,12 @@ class Group:
         nr = (ctypes.c_int * n)(*[int(s.shape[0]) if s.dim() == 2 else 1 for s in sigmas])
         check(lib().ifgf_group_apply(self._h, sp, yp, nr, ctypes.c_int(prec), _VP(_stream_ptr(stream))))
         return outs
+
+    def captures(self) -> int:
+        """Number of CUDA graphs this group has captured (replays add nothing)."""
+        n = ctypes.c_int64()
+        check(lib().ifgf_group_captures(self._h, ctypes.byref(n)))
+        return int(n.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -261,6 +261,8 @@ ifgf_status ifgf_plan_set_rhs_block(ifgf_plan *plan, int rhs_block) {
         set_error("rhs_block must be 1 or 4");
         return IFGF_EINVAL;
     }
+    // the setting decides which kernels a captured group graph holds: a change forces a recapture
+    if (plan->p.rhs_block != rhs_block) plan->p.gen++;
     plan->p.rhs_block = rhs_block;
     return IFGF_OK;
 }
@@ -271,6 +273,7 @@ ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill) {
         set_error("min_fill must be >= 0");
         return IFGF_EINVAL;
     }
+    if (plan->p.tc_min_fill != min_fill) plan->p.gen++;
     plan->p.tc_min_fill = min_fill;
     return IFGF_OK;
 }
@@ -281,6 +284,7 @@ ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine) {
         set_error("engine must be 0 (mma.sync) or 1 (tcgen05)");
         return IFGF_EINVAL;
     }
+    if (plan->p.tc_engine != engine) plan->p.gen++;
     plan->p.tc_engine = engine;
     return IFGF_OK;
 }

@@ -33,6 +33,7 @@ struct ifgf_group {
     int cap_prec = -1;
     int cap_nstreams = -1;
     int device = -1;
+    int64_t captures = 0;  // graphs captured so far
 };
 
 static void drop_graph(ifgf_group *g) {
@@ -83,6 +84,16 @@ ifgf_status ifgf_group_set_streams(ifgf_group *g, int nstreams) {
     }
     if (nstreams != g->nstreams) drop_graph(g);
     g->nstreams = nstreams;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_group_captures(const ifgf_group *g, int64_t *captures) {
+    clear_error();
+    if (!g || !captures) {
+        set_error("null group or output");
+        return IFGF_EINVAL;
+    }
+    *captures = g->captures;
     return IFGF_OK;
 }
 
@@ -184,6 +195,7 @@ ifgf_status ifgf_group_apply(ifgf_group *g, const void *const *sigma, void *cons
         for (int i = 0; i < n; i++) g->cap_gen[i] = g->plans[i]->p.gen;
         g->cap_prec = (int)prec;
         g->cap_nstreams = g->nstreams;
+        g->captures++;
     }
     cudaError_t e = cudaGraphLaunch(g->exec, cs);
     if (e != cudaSuccess) return gfail(e, "cudaGraphLaunch");

@@ -97,3 +97,36 @@ def test_config3_full_batch(B):
     for o, p, s in zip(outs, plans, sig):
         assert torch.equal(o, p.apply(s))
     assert all(p.missed_lookups() == 0 for p in plans)
+
+
+def test_group_recaptures_on_kernel_settings(B):
+    """The per-plan settings that choose kernels (right-hand-side blocking, tensor-core fill
+    threshold and engine) are baked into a captured graph: changing one must trigger a new
+    capture, and the replayed result must equal a per-plan apply under the new setting."""
+    bodies = scatterer_batch(seed=5, count=3, n_min=24, n_max=40, d_max=5.0)
+    plans = [B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8)) for s, k in bodies]
+    sig = [torch.from_numpy(random_density(s.N, 4, 50 + i).astype(np.complex64)).cuda()
+           for i, (s, k) in enumerate(bodies)]
+    g = B.Group(plans, nstreams=2)
+    outs = [torch.empty_like(s) for s in sig]
+
+    def run_and_compare():
+        g.apply(sig, outs)
+        torch.cuda.synchronize()
+        for p, s, o in zip(plans, sig, outs):
+            assert torch.equal(o, p.apply(s))
+
+    run_and_compare()
+    assert g.captures() == 1
+    run_and_compare()  # replay
+    assert g.captures() == 1
+    changes = [lambda p: p.set_rhs_block(1), lambda p: p.set_tc_fill(0.0), lambda p: p.set_tc_engine(0),
+               lambda p: p.set_tc_fill(2.0), lambda p: p.set_rhs_block(4)]
+    for i, change in enumerate(changes):
+        change(plans[i % len(plans)])
+        run_and_compare()
+        assert g.captures() == 2 + i
+    plans[0].set_rhs_block(4)  # unchanged value: the graph stays
+    run_and_compare()
+    assert g.captures() == 1 + len(changes)
+    g.close()
