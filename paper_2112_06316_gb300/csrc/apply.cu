@@ -249,18 +249,39 @@ void free_plan_device(Plan &p) {
     p.ws = Workspace();
 }
 
-ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {
-    if (p.ws.base && p.ws.nrhs >= nrhs && p.ws.prec == prec) return IFGF_OK;
+// Byte offsets of the workspace parts for nrhs right-hand sides in one precision: a, u, then F of
+// levels 3..D, each 256-byte aligned; returns the total.  ensure_workspace and the allocation-free
+// apply share this layout.
+size_t workspace_layout(const Plan &p, int nrhs, int prec, WorkspaceLayout &lay) {
     const size_t cb = prec == IFGF_FP64 ? 16 : 8;  // bytes per complex
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t off = 0;
-    size_t oa = off; off += al(cb * p.N * nrhs);
-    size_t ou = off; off += al(cb * p.N * nrhs);
-    size_t oF[IFGF_MAXD + 1] = {};
+    lay = WorkspaceLayout();
+    lay.a = off; off += al(cb * (size_t)p.N * nrhs);
+    lay.u = off; off += al(cb * (size_t)p.N * nrhs);
     for (int d = 3; d <= p.D; d++) {
-        oF[d] = off;
+        lay.F[d] = off;
         off += al(cb * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
     }
+    lay.total = off;
+    return off;
+}
+
+void workspace_bind(Workspace &ws, const Plan &p, void *base, const WorkspaceLayout &lay, int nrhs, int prec) {
+    char *c = static_cast<char *>(base);
+    ws.base = base;
+    ws.bytes = lay.total;
+    ws.nrhs = nrhs;
+    ws.prec = prec;
+    ws.a = c + lay.a;
+    ws.u = c + lay.u;
+    for (int d = 3; d <= p.D; d++) ws.F[d] = c + lay.F[d];
+}
+
+ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {
+    if (p.ws.base && p.ws.nrhs >= nrhs && p.ws.prec == prec) return IFGF_OK;
+    WorkspaceLayout lay;
+    const size_t off = workspace_layout(p, nrhs, prec, lay);
     if (p.ws.base) cudaFree(p.ws.base);
     p.ws = Workspace();
     p.gen++;
@@ -270,14 +291,7 @@ ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {
         set_error("workspace cudaMalloc(%zu bytes) failed: %s", off, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
     }
-    p.ws.base = base;
-    p.ws.bytes = off;
-    p.ws.nrhs = nrhs;
-    p.ws.prec = prec;
-    char *c = (char *)base;
-    p.ws.a = c + oa;
-    p.ws.u = c + ou;
-    for (int d = 3; d <= p.D; d++) p.ws.F[d] = c + oF[d];
+    workspace_bind(p.ws, p, base, lay, nrhs, prec);
     return IFGF_OK;
 }
 

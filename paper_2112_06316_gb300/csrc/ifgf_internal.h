@@ -100,6 +100,11 @@ struct Workspace {
     void *F[IFGF_MAXD + 1] = {};  // cone values per level, [nrhs][nrc][nfac][Pstride]
 };
 
+// byte offsets of the workspace parts (workspace_layout)
+struct WorkspaceLayout {
+    size_t a = 0, u = 0, F[IFGF_MAXD + 1] = {}, total = 0;
+};
+
 struct Plan {
     ifgf_params prm;
     int64_t N = 0;
@@ -210,6 +215,8 @@ int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L,
 
 // apply.cu
 ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const double *w, cudaStream_t s);
+size_t workspace_layout(const Plan &p, int nrhs, int prec, WorkspaceLayout &lay);
+void workspace_bind(Workspace &ws, const Plan &p, void *base, const WorkspaceLayout &lay, int nrhs, int prec);
 ifgf_status ensure_workspace(Plan &p, int nrhs, int prec);
 ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
 void free_plan_device(Plan &p);

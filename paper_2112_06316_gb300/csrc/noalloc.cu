@@ -28,10 +28,39 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};  // id of the context the cached address belongs to
 
-// Device address of g_scratch on the current device, looked up once per device.
-// In host code the name g_scratch is only a host-side stand-in for the symbol,
-// not a device address, so kernels must receive the address returned here.
+// Driver calls that identify the calling thread's current context, resolved through the runtime
+// (no link-time dependency on the driver library).  Context ids are unique for the life of the
+// process, so a context created after cudaDeviceReset never matches an earlier one.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+bool current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = (CtxGetCurrentFn)f1;
+            get_id = (CtxGetIdFn)f2;
+        }
+        resolved = true;
+    }
+    void *ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of g_scratch on the current device, looked up once per device and context.
+// In host code the name g_scratch is only a host-side stand-in for the symbol, not a device
+// address, so kernels must receive the address returned here.  The lookup is repeated only when
+// the device's context has changed (after cudaDeviceReset the module is loaded again and the
+// array may sit elsewhere); where the context cannot be identified the first address is kept.
 ifgf_status scratch_address(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -43,8 +72,10 @@ ifgf_status scratch_address(void **out) {
         set_error("device ordinal %d out of range", dev);
         return IFGF_EUNSUPPORTED;
     }
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev] || (have_ctx && g_ctx[dev] != ctx)) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess || !ptr) {
@@ -52,12 +83,11 @@ ifgf_status scratch_address(void **out) {
             return IFGF_ECUDA;
         }
         g_addr[dev] = ptr;
+        g_ctx[dev] = have_ctx ? ctx : 0;
     }
     *out = g_addr[dev];
     return IFGF_OK;
 }
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 }  // namespace ifgf
@@ -85,18 +115,9 @@ extern "C" ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev
         return IFGF_EINVAL;
     }
     Plan &p = plan->p;
-    // same layout as the plan-owned workspace: a, u, then F of levels 3..D
-    const size_t cb = prec == IFGF_FP64 ? 16 : 8;
-    size_t off[IFGF_MAXD + 3] = {};
-    size_t total = 0;
-    off[0] = total;
-    total += align256(cb * (size_t)p.N * nrhs);
-    off[1] = total;
-    total += align256(cb * (size_t)p.N * nrhs);
-    for (int d = 3; d <= p.D; d++) {
-        off[d + 2] = total;
-        total += align256(cb * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
-    }
+    // same layout as the plan-owned workspace
+    WorkspaceLayout lay;
+    const size_t total = workspace_layout(p, nrhs, (int)prec, lay);
     if (total > kNoAllocScratchBytes) {
         set_error("ifgf_apply_noalloc: workspace of %zu bytes exceeds the fixed %zu-byte scratch (N=%lld, nrhs=%d); "
                   "use ifgf_apply", total, kNoAllocScratchBytes, (long long)p.N, nrhs);
@@ -106,14 +127,7 @@ extern "C" ifgf_status ifgf_apply_noalloc(ifgf_plan *plan, const void *sigma_dev
     ifgf_status st = scratch_address(&base);
     if (st != IFGF_OK) return st;
     Workspace ws;
-    char *c = static_cast<char *>(base);
-    ws.base = base;
-    ws.bytes = total;
-    ws.nrhs = nrhs;
-    ws.prec = (int)prec;
-    ws.a = c + off[0];
-    ws.u = c + off[1];
-    for (int d = 3; d <= p.D; d++) ws.F[d] = c + off[d + 2];
+    workspace_bind(ws, p, base, lay, nrhs, (int)prec);
     cudaStream_t s = (cudaStream_t)stream;
     st = run_apply_on(p, ws, sigma_dev, y_dev, nrhs, (int)prec, s);
     if (st != IFGF_OK) return st;
