@@ -337,6 +337,17 @@ ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill);
  * Errors: IFGF_EINVAL for any other value. */
 ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine);
 
+/* Tunable: engine of the mixed cousin interpolation (the evaluation of each box's
+ * cone interpolants at the points of its cousin boxes, Section 3.4).  1 (default)
+ * = cone-stationary: plan-time lists give, for every relevant cone segment, the
+ * cousin points inside it; a warp stages one cone's values once and interpolates
+ * 64 of its points (two per lane), writing each value to its (box, cousin, point)
+ * slot, and a second pass adds each point's slots in fixed order.  0 = point-
+ * stationary: a warp owns up to 32 points of one box and walks its cousin boxes,
+ * staging the cones its lanes fall in.  Plans with N >= 2^24 points always use 0.
+ * Errors: IFGF_EINVAL for any other value. */
+ifgf_status ifgf_plan_set_cousin_engine(ifgf_plan *plan, int engine);
+
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
 
@@ -354,7 +365,8 @@ ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable);
 /* Per-launch device times of the last apply with profiling on: fills up to `cap`
  * entries of kind (0 gather, 1 leaf evaluation, 2 propagation, 3 near field,
  * 4 cousin interpolation, 5 scatter, 6 correction, 7 propagation on the tensor
- * cores: one entry per level, all its octant launches), level (octree level or 0) and
+ * cores: one entry per level, all its octant launches, 8 second pass of the
+ * cone-stationary cousin interpolation), level (octree level or 0) and
  * ms (milliseconds); any output pointer may be NULL.  Waits for the last event.
  * Returns the number of entries (0 if profiling is off), or a negative ifgf_status. */
 int ifgf_plan_stage_times(ifgf_plan *plan, int cap, int *kind, int *level, double *ms);

@@ -92,9 +92,10 @@ _SIGS = [
     ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("ifgf_group_captures", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    ("ifgf_plan_set_cousin_engine", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_destroy", None, [_VP]),
 ]
-STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc"]
+STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc", "cousin_sum"]
 
 _lib = None
 
@@ -387,6 +388,10 @@ class Plan:
     def set_tc_engine(self, engine: int):
         """1 = tcgen05 (tensor memory), 0 = warp-level mma.sync."""
         check(lib().ifgf_plan_set_tc_engine(self._h, ctypes.c_int(engine)))
+
+    def set_cousin_engine(self, engine: int):
+        """1 = cone-stationary cousin interpolation (default), 0 = point-stationary."""
+        check(lib().ifgf_plan_set_cousin_engine(self._h, ctypes.c_int(engine)))
 
     def set_rhs_block(self, rhs_block: int):
         check(lib().ifgf_plan_set_rhs_block(self._h, ctypes.c_int(rhs_block)))

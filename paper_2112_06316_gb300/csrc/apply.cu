@@ -55,6 +55,53 @@ static ifgf_status upload(Plan &p, T *&dst, const T *src, size_t n, cudaStream_t
     return IFGF_OK;
 }
 
+// Plan-time geometry of the cone-stationary cousin interpolation, in FP64, once per plan: for
+// every entry (target x, relevant cone (box c, segment (is, it, ip))) the local coordinates of x
+// in that segment (Eq. ConeIntervals mapped to [-1, 1] per axis: s = h / r, theta, phi about the
+// centre y_c) and the centred factor E(x; y_c) = e^{ik r} / (4 pi r) of Eq. cent_fact, rounded to
+// FP32, and the entry's slot in the value buffer (box of x, cousin slot, position in the box).
+// One warp per work item (one cone, <= kCsItem entries), as in the apply kernel.
+__global__ void __launch_bounds__(128) k_cousin_geo(int nitems, const int4 *__restrict__ items,
+                                                    const uint32_t *__restrict__ ent, const int *__restrict__ rc_box,
+                                                    const int *__restrict__ rc_cone, const int *__restrict__ ijk,
+                                                    const int *__restrict__ start, const int *__restrict__ box_of,
+                                                    const int *__restrict__ pvoff, const double *__restrict__ x64,
+                                                    double c00, double c01, double c02, double H, double h, double ds,
+                                                    double dth, double dph, int nC, int nph, double k,
+                                                    float4 *__restrict__ geo4, float2 *__restrict__ geo2) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * 4 + warp;
+    if (item >= nitems) return;
+    const int4 w = items[item];
+    const int rc = w.x, c = rc_box[rc], cone = rc_cone[rc];
+    const int ip = cone % nph, it = (cone / nph) % nC, is = cone / (nph * nC);
+    const double y0 = c00 + (ijk[3 * c] + 0.5) * H, y1 = c01 + (ijk[3 * c + 1] + 0.5) * H,
+                 y2 = c02 + (ijk[3 * c + 2] + 0.5) * H;
+    const double twopi = 2.0 * 3.14159265358979323846;
+    for (int m = lane; m < w.z; m += 32) {
+        const int e = w.y + m;
+        const uint32_t en = ent[e];
+        const int i = (int)(en & 0xFFFFFFu), slot = (int)(en >> 24);
+        const double dx = x64[3 * i] - y0, dy = x64[3 * i + 1] - y1, dz = x64[3 * i + 2] - y2;
+        const double rho = sqrt(dx * dx + dy * dy);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double ph = atan2(dy, dx);
+        if (ph < 0) ph += twopi;
+        if (ph >= twopi) ph = 0.0;
+        const double us = (h / r) / ds - is, ut = atan2(rho, dz) / dth - it;
+        double up = ph / dph - ip;
+        if (up > 0.5 * nph) up -= nph;  // phi wrapped across 2 pi relative to the segment
+        else if (up < -0.5 * nph) up += nph;
+        double sn, cs;
+        sincos(k * r, &sn, &cs);
+        const double a = 1.0 / (4.0 * 3.14159265358979323846 * r);
+        const int b = box_of[i], s0 = start[b];
+        const int dest = pvoff[b] + slot * (start[b + 1] - s0) + (i - s0);
+        geo4[e] = make_float4((float)(2.0 * us - 1.0), (float)(2.0 * ut - 1.0), (float)(2.0 * up - 1.0), (float)(a * cs));
+        geo2[e] = make_float2((float)(a * sn), __int_as_float(dest));
+    }
+}
+
 #define UP(dst, vec)                                                               \
     do {                                                                           \
         ifgf_status st_ = upload(p, dst, (vec).data(), (vec).size(), s);           \
@@ -133,6 +180,50 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         }
         p.ncchunk[d] = (int)ch.size();
         UP(p.d_cchunk[d], ch);
+    }
+    // cone-stationary cousin interpolation: work items of at most kCsItem entries of one cone
+    if (p.cs_ok) {
+        for (int d = 3; d <= D; d++) {
+            HostLevel &L = p.lv[d];
+            std::vector<int4> items;
+            for (int64_t rc = 0; rc < L.nrc; rc++)
+                for (int64_t e = L.cs_start[rc]; e < L.cs_start[rc + 1]; e += kCsItem)
+                    items.push_back(make_int4((int)rc, (int)e, (int)std::min<int64_t>(kCsItem, L.cs_start[rc + 1] - e), 0));
+            p.ncs_item[d] = (int)items.size();
+            UP(p.d_cs_item[d], items);
+            UP(p.d_cs_pvoff[d], L.cs_pvoff);
+            {
+                const size_t ne = L.cs_ent.size() > 0 ? L.cs_ent.size() : 1;
+                cudaError_t err;
+                p.d_cs_geo4[d] = dalloc<float4>(p, ne, err);
+                if (p.d_cs_geo4[d]) p.d_cs_geo2[d] = dalloc<float2>(p, ne, err);
+                if (!p.d_cs_geo2[d]) {
+                    set_error("cudaMalloc failed: %s", cudaGetErrorString(err));
+                    return IFGF_ENOMEM;
+                }
+                uint32_t *ent = nullptr;
+                CK(cudaMalloc(&ent, sizeof(uint32_t) * ne));
+                cudaError_t e2 = cudaMemcpyAsync(ent, L.cs_ent.data(), sizeof(uint32_t) * L.cs_ent.size(),
+                                                 cudaMemcpyHostToDevice, s);
+                const DevLevel &dl = p.dl[d];
+                if (e2 == cudaSuccess && !items.empty()) {
+                    k_cousin_geo<<<(unsigned)((items.size() + 3) / 4), 128, 0, s>>>(
+                        (int)items.size(), p.d_cs_item[d], ent, dl.rc_box, dl.rc_cone, dl.ijk, dl.start,
+                        p.d_box_of[d], p.d_cs_pvoff[d], p.d_x64, p.c0[0], p.c0[1], p.c0[2], L.H, L.h, L.ds, L.dth,
+                        L.dph, L.nC, L.nph, p.prm.k, p.d_cs_geo4[d], p.d_cs_geo2[d]);
+                    e2 = cudaGetLastError();
+                }
+                if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+                cudaFree(ent);
+                if (e2 != cudaSuccess) {
+                    set_error("cousin geometry: %s", cudaGetErrorString(e2));
+                    return IFGF_ECUDA;
+                }
+            }
+            std::vector<int64_t>().swap(L.cs_start);
+            std::vector<uint32_t>().swap(L.cs_ent);
+            std::vector<int>().swap(L.cs_pvoff);
+        }
     }
     // tensor-core propagation tables (orders with Pang = 8)
     if (p.Pang == 8) {
@@ -263,6 +354,8 @@ size_t workspace_layout(const Plan &p, int nrhs, int prec, WorkspaceLayout &lay)
         lay.F[d] = off;
         off += al(cb * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
     }
+    lay.pv = off;
+    if (prec == IFGF_MIXED && p.cs_ok && p.cousin_engine == 1) off += al(8 * (size_t)nrhs * p.cs_max_entries);
     lay.total = off;
     return off;
 }
@@ -276,12 +369,13 @@ void workspace_bind(Workspace &ws, const Plan &p, void *base, const WorkspaceLay
     ws.a = c + lay.a;
     ws.u = c + lay.u;
     for (int d = 3; d <= p.D; d++) ws.F[d] = c + lay.F[d];
+    ws.pv = c + lay.pv;
 }
 
 ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {
-    if (p.ws.base && p.ws.nrhs >= nrhs && p.ws.prec == prec) return IFGF_OK;
     WorkspaceLayout lay;
     const size_t off = workspace_layout(p, nrhs, prec, lay);
+    if (p.ws.base && p.ws.nrhs >= nrhs && p.ws.prec == prec && p.ws.bytes >= off) return IFGF_OK;
     if (p.ws.base) cudaFree(p.ws.base);
     p.ws = Workspace();
     p.gen++;

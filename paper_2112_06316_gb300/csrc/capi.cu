@@ -168,6 +168,7 @@ ifgf_status ifgf_plan_create(const double *xyz, const double *normals, const dou
     ifgf_status st;
     try {
         st = build_host_plan(p, xyz, normals, weights);
+        if (st == IFGF_OK) st = build_cousin_lists(p);
     } catch (const std::bad_alloc &) {
         set_error("host allocation failed while building the plan");
         st = IFGF_ENOMEM;
@@ -286,6 +287,17 @@ ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine) {
     }
     if (plan->p.tc_engine != engine) plan->p.gen++;
     plan->p.tc_engine = engine;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_set_cousin_engine(ifgf_plan *plan, int engine) {
+    clear_error();
+    if (!plan || (engine != 0 && engine != 1)) {
+        set_error("engine must be 0 (target-stationary) or 1 (cone-stationary)");
+        return IFGF_EINVAL;
+    }
+    if (plan->p.cousin_engine != engine) plan->p.gen++;
+    plan->p.cousin_engine = engine;
     return IFGF_OK;
 }
 

@@ -881,6 +881,167 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
 }
 
 
+// ---------------------------------------------------------------------------
+// K2 (mixed), cone-stationary.  The host lists, for every relevant cone of level d, the
+// cousin targets that fall in it (FP64 classification); once per plan, k_cousin_geo stores
+// each entry's local coordinates in the cone, its centred factor and its output slot.
+// Phase 1: one warp per work item (one cone, <= 64 of its targets) copies the cone's node
+// values into shared memory once; each lane interpolates two targets, so every 16-byte
+// shared load is a broadcast that feeds four packed FMAs, and writes E(x; y_c)
+// Interp(F_c)(x) to the value buffer at the target's (box, cousin slot) position.  Phase 2 (k_cousin_sum): one thread per target adds
+// its slots in cousin-list order with compensation, so the field stays deterministic.
+constexpr int kCsWarps = 4;
+
+// per-target interpolation weights and centred factor of one (target, cone) pair
+template <int PS, int PA>
+struct CsTgt {
+    unsigned long long lt2[PA], lp2[PA];  // (L, L) pairs of the angular bases
+    float Ls[PS];
+    float Er, Ei, irabs;  // E(x; y_c) = e^{ikr} / (4 pi r); 1 / r (absolute)
+    int dest;             // slot in the value buffer, -1 for an idle lane
+};
+
+// Interpolation weights of entry e from its plan-time geometry: local coordinates in the list's
+// cone segment and the centred factor, both computed once per plan in FP64 (k_cousin_geo).
+template <int PS, int PA>
+__device__ __forceinline__ void cs_load(const ChebTab &tb, const float4 *__restrict__ geo4,
+                                        const float2 *__restrict__ geo2, int e, CsTgt<PS, PA> &g) {
+    const float4 a = __ldg(geo4 + e);
+    const float2 b = __ldg(geo2 + e);
+    float Lt[PA], Lp[PA];
+    lagrange<PS, float>(a.x, tb.fxs, tb.fcs, g.Ls);
+    lagrange<PA, float>(a.y, tb.fxa, tb.fca, Lt);
+    lagrange<PA, float>(a.z, tb.fxa, tb.fca, Lp);
+#pragma unroll
+    for (int k = 0; k < PA; k++) {
+        g.lt2[k] = f2pack(Lt[k], Lt[k]);
+        g.lp2[k] = f2pack(Lp[k], Lp[k]);
+    }
+    g.Er = a.w;
+    g.Ei = b.x;
+    g.irabs = 4.f * kPiF * sqrtf(a.w * a.w + b.x * b.x);  // |E| = 1 / (4 pi r)
+    g.dest = __float_as_int(b.y);
+}
+
+// interpolation of one factor's node values f (shared memory) for two targets at once
+template <int PS, int PA>
+__device__ __forceinline__ void cs_interp2(const float2 *f, const CsTgt<PS, PA> &g0, const CsTgt<PS, PA> &g1,
+                                           unsigned long long &v0, unsigned long long &v1) {
+    v0 = 0ull;
+    v1 = 0ull;
+#pragma unroll 1
+    for (int a = 0; a < PS; a++) {
+        const float2 *fa = f + a * PA * PA;
+        unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+        for (int b = 0; b < PA; b++) {
+            unsigned long long b0 = 0ull, b1 = 0ull;
+            const float2 *row = fa + b * PA;
+            if constexpr (PA % 2 == 0) {
+#pragma unroll
+                for (int k = 0; k < PA; k += 2) {
+                    const float4 v = *reinterpret_cast<const float4 *>(row + k);
+                    const unsigned long long x = f2pack(v.x, v.y), y = f2pack(v.z, v.w);
+                    f2fma(b0, g0.lp2[k], x);
+                    f2fma(b1, g1.lp2[k], x);
+                    f2fma(b0, g0.lp2[k + 1], y);
+                    f2fma(b1, g1.lp2[k + 1], y);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < PA; k++) {
+                    const float2 v = row[k];
+                    const unsigned long long x = f2pack(v.x, v.y);
+                    f2fma(b0, g0.lp2[k], x);
+                    f2fma(b1, g1.lp2[k], x);
+                }
+            }
+            f2fma(a0, g0.lt2[b], b0);
+            f2fma(a1, g1.lt2[b], b1);
+        }
+        const float l0 = pick<PS>(g0.Ls, a), l1 = pick<PS>(g1.Ls, a);
+        f2fma(v0, f2pack(l0, l0), a0);
+        f2fma(v1, f2pack(l1, l1), a1);
+    }
+}
+
+template <int PS, int PA, bool SPLIT>
+__global__ void __launch_bounds__(kCsWarps * 32) k_cousin_cs(CommonArgs ca, LevelArgs L, const int4 *__restrict__ items,
+                                                             int nitems, const float4 *__restrict__ geo4,
+                                                             const float2 *__restrict__ geo2, ChebTab tb,
+                                                             float2 *__restrict__ pv, long long pv_stride) {
+    constexpr int P = PS * PA * PA, PST = P + (P & 1), NF = SPLIT ? 2 : 1;
+    constexpr int NV4 = NF * PST / 2;  // float4 of one cone's values (all factors, contiguous)
+    __shared__ __align__(16) float2 sF[kCsWarps][NF * PST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.x * kCsWarps + warp;
+    if (item >= nitems) return;  // warp-uniform: no block-wide barrier below
+    const int4 w = items[item];
+    const int rc = w.x, e0 = w.y, cnt = w.z;
+    CsTgt<PS, PA> g0, g1;
+    const bool has0 = lane < cnt, has1 = lane + 32 < cnt;
+    cs_load<PS, PA>(tb, geo4, geo2, e0 + (has0 ? lane : 0), g0);
+    cs_load<PS, PA>(tb, geo4, geo2, e0 + (has1 ? lane + 32 : 0), g1);
+    const float2 *F = (const float2 *)L.F;
+    float2 *buf = sF[warp];
+    for (int q = 0; q < ca.nrhs; q++) {
+        __syncwarp();  // the previous right-hand side's readers are done
+        const float4 *src = reinterpret_cast<const float4 *>(F + ((long long)q * L.nrc + rc) * NF * PST);
+        float4 *dst = reinterpret_cast<float4 *>(buf);
+        for (int v = lane; v < NV4; v += 32) cp_async16(dst + v, src + v);
+        cp_async_wait_all();
+        __syncwarp();
+        unsigned long long v0, v1;
+        cs_interp2<PS, PA>(buf, g0, g1, v0, v1);
+        float vr0, vi0, vr1, vi1;
+        f2unpack(v0, vr0, vi0);
+        f2unpack(v1, vr1, vi1);
+        if constexpr (SPLIT) {  // E (W2 / r + W13) with the second factor's interpolant
+            unsigned long long w0, w1;
+            cs_interp2<PS, PA>(buf + PST, g0, g1, w0, w1);
+            float wr0, wi0, wr1, wi1;
+            f2unpack(w0, wr0, wi0);
+            f2unpack(w1, wr1, wi1);
+            vr0 = vr0 * g0.irabs + wr0;
+            vi0 = vi0 * g0.irabs + wi0;
+            vr1 = vr1 * g1.irabs + wr1;
+            vi1 = vi1 * g1.irabs + wi1;
+        }
+        float2 *out = pv + (long long)q * pv_stride;
+        if (has0) out[g0.dest] = make_float2(g0.Er * vr0 - g0.Ei * vi0, g0.Er * vi0 + g0.Ei * vr0);
+        if (has1) out[g1.dest] = make_float2(g1.Er * vr1 - g1.Ei * vi1, g1.Er * vi1 + g1.Ei * vr1);
+    }
+}
+
+// Phase 2: u(x) += sum over the cousin slots of x's level-d box of the phase-1 values, in
+// slot order with Kahan compensation (one thread per target; the slots of a box's targets
+// are contiguous, so consecutive threads read consecutive values).
+__global__ void __launch_bounds__(kBlock) k_cousin_sum(CommonArgs ca, LevelArgs L, const int *__restrict__ box_of,
+                                                       const int *__restrict__ pvoff, const float2 *__restrict__ pv,
+                                                       long long pv_stride, float2 *__restrict__ u) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ca.N) return;
+    const int b = box_of[i];
+    const int s0 = L.start[b], nt = L.start[b + 1] - s0;
+    const int ncous = L.co_start[b + 1] - L.co_start[b];
+    const long long base = (long long)pvoff[b] + (i - s0);
+    for (int q = 0; q < ca.nrhs; q++) {
+        const float2 *src = pv + (long long)q * pv_stride + base;
+        CAcc acc;
+        acc.zero();
+        for (int j = 0; j < ncous; j++) {
+            const float2 v = __ldg(src + (long long)j * nt);
+            acc.add(v.x, v.y);
+        }
+        const long long o = (long long)q * ca.N + i;
+        float2 x = u[o];
+        const float2 z = acc.get();
+        x.x += z.x;
+        x.y += z.y;
+        u[o] = x;
+    }
+}
+
 // K3 (mixed), staged: one warp owns 32 nodes of one parent relevant cone and walks the
 // parent box's children; for every distinct child cone its lanes fall into, the warp
 // copies that cone's node values (all factors) into shared memory with cp.async and the
@@ -2873,7 +3034,24 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         float2 *u32 = (float2 *)p.ws.u;
         auto cousin = [&](int d) {
             const int nch = p.ncchunk[d];
-            if (nch > 0) {
+            if (p.cs_ok && p.cousin_engine == 1) {
+                const int ni = p.ncs_item[d];
+                const long long stride = p.cs_max_entries;
+                float2 *pv = (float2 *)p.ws.pv;
+                if (ni > 0) {
+                    const unsigned g = (unsigned)((ni + kCsWarps - 1) / kCsWarps);
+                    if (L[d].split)
+                        k_cousin_cs<PS, PA, true><<<g, kCsWarps * 32, 0, sb>>>(
+                            ca, L[d], p.d_cs_item[d], ni, p.d_cs_geo4[d], p.d_cs_geo2[d], tb, pv, stride);
+                    else
+                        k_cousin_cs<PS, PA, false><<<g, kCsWarps * 32, 0, sb>>>(
+                            ca, L[d], p.d_cs_item[d], ni, p.d_cs_geo4[d], p.d_cs_geo2[d], tb, pv, stride);
+                    prof_mark(p, sb, kStCousin, d);
+                    k_cousin_sum<<<nblk(N), kBlock, 0, sb>>>(ca, L[d], p.d_box_of[d], p.d_cs_pvoff[d], pv, stride, u32);
+                    prof_mark(p, sb, kStCousinSum, d);
+                }
+                return;
+            } else if (nch > 0) {
                 const unsigned g = (unsigned)((nch + kCwWarps - 1) / kCwWarps);
                 if (rb1) k_cousin_w<PS, PA, 1><<<g, kCwWarps * 32, 0, sb>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb, u32);
                 else k_cousin_w<PS, PA, kRB><<<g, kCwWarps * 32, 0, sb>>>(ca, L[d], L[D], p.d_cchunk[d], nch, tb, u32);

@@ -46,6 +46,13 @@ struct HostLevel {
     std::vector<int64_t> ad_start;
     std::vector<int> ad_list;
     int64_t cousin_evals = 0, prop_evals = 0;
+    // forward cousin lists of the mixed path (host copies, released after upload): for every
+    // relevant cone, the cousin targets it serves as (sorted position | slot << 24), where slot is
+    // the cone owner's index in the target box's cousin list; cs_pvoff[b] = first entry of box b
+    // in the per-(box, slot, target) value buffer ([slot][target in b] blocks)
+    std::vector<int64_t> cs_start;
+    std::vector<uint32_t> cs_ent;
+    std::vector<int> cs_pvoff;
 };
 
 // Tensor-core propagation into level d-1 (mixed path, Pang = 8): pairs (parent
@@ -55,6 +62,7 @@ struct HostLevel {
 // writes the same parent cone twice.
 constexpr int kDkDotBlocks = 1216;  // blocks of each level's Re <H, F> reduction in the k-gradient (8 per SM)
 constexpr int kTcTile = 64;   // pairs per tile
+constexpr int kCsItem = 64;   // cousin targets per work item of the cone-stationary interpolation (two per lane)
 constexpr int kTcPairs = 32;  // pairs per block of the warp-level (mma.sync) engine: a tile is two blocks
 struct TcLevel {
     int ntiles = 0, ngroups = 0;
@@ -98,11 +106,12 @@ struct Workspace {
     void *a = nullptr;   // w * sigma in sorted order, [nrhs][N]
     void *u = nullptr;   // accumulated field in sorted order, [nrhs][N]
     void *F[IFGF_MAXD + 1] = {};  // cone values per level, [nrhs][nrc][nfac][Pstride]
+    void *pv = nullptr;  // mixed path: one level's cousin-interpolation values, [nrhs][pairs]
 };
 
 // byte offsets of the workspace parts (workspace_layout)
 struct WorkspaceLayout {
-    size_t a = 0, u = 0, F[IFGF_MAXD + 1] = {}, total = 0;
+    size_t a = 0, u = 0, F[IFGF_MAXD + 1] = {}, pv = 0, total = 0;
 };
 
 struct Plan {
@@ -131,6 +140,19 @@ struct Plan {
     // the targets of every box split into near-equal runs of at most 32
     int4 *d_cchunk[IFGF_MAXD + 1] = {};
     int ncchunk[IFGF_MAXD + 1] = {};
+    // cone-stationary cousin interpolation (mixed path; needs N < 2^24 and fewer than 2^31
+    // (target, cousin) pairs per level): work items (relevant cone, first entry, count <= 64),
+    // packed entries and per-box offsets of the value buffer (HostLevel::cs_*)
+    bool cs_ok = false;
+    int cousin_engine = 1;  // 1 = cone-stationary when the lists exist, 0 = target-stationary (k_cousin_w)
+    int4 *d_cs_item[IFGF_MAXD + 1] = {};
+    int ncs_item[IFGF_MAXD + 1] = {};
+    // per entry, FP64-computed once per plan: (local coordinates t_s, t_theta, t_phi, Re E) and
+    // (Im E, value-buffer slot as int bits)
+    float4 *d_cs_geo4[IFGF_MAXD + 1] = {};
+    float2 *d_cs_geo2[IFGF_MAXD + 1] = {};
+    int *d_cs_pvoff[IFGF_MAXD + 1] = {};
+    int64_t cs_max_entries = 0;  // largest per-level pair count (size of the value buffer per rhs)
     int *d_nb_start = nullptr, *d_nb_list = nullptr;
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
@@ -193,7 +215,8 @@ struct Plan {
 // stage kinds reported by ifgf_plan_stage_times
 enum StageKind {
     kStGather = 0, kStLeaf = 1, kStProp = 2, kStNear = 3, kStCousin = 4, kStScatter = 5, kStCorr = 6,
-    kStPropTc = 7  // propagation on the tensor cores
+    kStPropTc = 7,    // propagation on the tensor cores
+    kStCousinSum = 8  // second pass of the cone-stationary cousin interpolation
 };
 
 inline void prof_begin(Plan &p, cudaStream_t s) {
@@ -211,6 +234,7 @@ inline void prof_mark(Plan &p, cudaStream_t s, int kind, int level) {
 // plan.cpp
 ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const double *w);
 ifgf_status build_adjoint_lists(Plan &p, const double *xs_sorted);
+ifgf_status build_cousin_lists(Plan &p);
 int morton_levels_auto(const double *xyz, int64_t N, const double *c0, double L, double leaf_target);
 
 // apply.cu

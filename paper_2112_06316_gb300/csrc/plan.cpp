@@ -615,4 +615,89 @@ ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
     return IFGF_OK;
 }
 
+// Forward cousin lists of the mixed path: for every relevant cone (box c, cone gamma) of level d,
+// the targets x in c's cousin boxes that fall in gamma (Eq. NeighborsCousins is symmetric: x is
+// a cousin point of c iff c is a cousin of x's box), classified in FP64 with the rule of the
+// adjoint lists, in cousin-list then Morton order.  Each entry packs x's sorted position and
+// the slot of c in the cousin list of x's box; cs_pvoff gives the value-buffer block of each box.
+ifgf_status build_cousin_lists(Plan &p) {
+    const int64_t N = p.N;
+    p.cs_ok = N < (int64_t(1) << 24);
+    p.cs_max_entries = 0;
+    for (int d = 3; d <= p.D && p.cs_ok; d++) p.cs_ok = p.lv[d].cousin_evals < (int64_t(1) << 31);
+    if (!p.cs_ok) return IFGF_OK;  // the kernels fall back to the target-stationary cousin interpolation
+    const double *xs = p.xs.data();
+    for (int d = 3; d <= p.D; d++) {
+        HostLevel &L = p.lv[d];
+        // slot of box c in the cousin list of each of its cousins
+        std::vector<uint8_t> rev(L.co_list.size());
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+        for (int c = 0; c < L.nbox; c++)
+            for (int ci = L.co_start[c]; ci < L.co_start[c + 1]; ci++) {
+                const int cb = L.co_list[ci];
+                int j = -1;
+                for (int k = L.co_start[cb]; k < L.co_start[cb + 1]; k++)
+                    if (L.co_list[k] == c) {
+                        j = k - L.co_start[cb];
+                        break;
+                    }
+                if (j < 0 || j > 255) bad |= 1;
+                else rev[ci] = (uint8_t)j;
+            }
+        if (bad) {  // more than 256 cousins or an asymmetric relation: keep the other kernel
+            p.cs_ok = false;
+            return IFGF_OK;
+        }
+        std::vector<std::vector<std::vector<uint32_t>>> per_box(L.nbox);
+        int miss = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : miss)
+        for (int c = 0; c < L.nbox; c++) {
+            const int r0 = L.rc_start[c], nr = L.rc_start[c + 1] - r0;
+            std::vector<std::vector<uint32_t>> &lists = per_box[c];
+            lists.assign(nr, std::vector<uint32_t>());
+            for (int ci = L.co_start[c]; ci < L.co_start[c + 1]; ci++) {
+                const int cb = L.co_list[ci];
+                const uint32_t slot = (uint32_t)rev[ci] << 24;
+                for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
+                    const int rc = L.cone_map[(size_t)c * L.ncone + classify_exact(p, L, c, xs + 3 * si)];
+                    if (rc < 0) {
+                        miss |= 1;
+                        continue;
+                    }
+                    lists[rc - r0].push_back((uint32_t)si | slot);
+                }
+            }
+        }
+        if (miss) {
+            set_error("cousin lists: a cousin target falls outside the relevant cone segments");
+            return IFGF_EINVAL;
+        }
+        L.cs_start.assign(L.nrc + 1, 0);
+        for (int c = 0; c < L.nbox; c++)
+            for (size_t j = 0; j < per_box[c].size(); j++) L.cs_start[L.rc_start[c] + j + 1] = per_box[c][j].size();
+        for (int64_t r = 0; r < L.nrc; r++) L.cs_start[r + 1] += L.cs_start[r];
+        L.cs_ent.resize(L.cs_start[L.nrc]);
+        for (int c = 0; c < L.nbox; c++) {
+            for (size_t j = 0; j < per_box[c].size(); j++)
+                std::copy(per_box[c][j].begin(), per_box[c][j].end(), L.cs_ent.begin() + L.cs_start[L.rc_start[c] + j]);
+            std::vector<std::vector<uint32_t>>().swap(per_box[c]);
+        }
+        L.cs_pvoff.assign(L.nbox + 1, 0);
+        int64_t off = 0;
+        for (int b = 0; b < L.nbox; b++) {
+            L.cs_pvoff[b] = (int)off;
+            off += (int64_t)(L.co_start[b + 1] - L.co_start[b]) * (L.start[b + 1] - L.start[b]);
+        }
+        L.cs_pvoff[L.nbox] = (int)off;
+        if (off != L.cousin_evals || (int64_t)L.cs_ent.size() != off) {
+            set_error("cousin lists: %lld entries for %lld cousin pairs", (long long)L.cs_ent.size(),
+                      (long long)L.cousin_evals);
+            return IFGF_EINVAL;
+        }
+        p.cs_max_entries = std::max(p.cs_max_entries, off);
+    }
+    return IFGF_OK;
+}
+
 }  // namespace ifgf

@@ -120,10 +120,12 @@ def test_group_recaptures_on_kernel_settings(B):
     assert g.captures() == 1
     run_and_compare()  # replay
     assert g.captures() == 1
-    changes = [lambda p: p.set_rhs_block(1), lambda p: p.set_tc_fill(0.0), lambda p: p.set_tc_engine(0),
-               lambda p: p.set_tc_fill(2.0), lambda p: p.set_rhs_block(4)]
-    for i, change in enumerate(changes):
-        change(plans[i % len(plans)])
+    # each step changes one plan's setting away from its current value
+    changes = [(0, lambda p: p.set_rhs_block(1)), (1, lambda p: p.set_tc_fill(0.0)),
+               (2, lambda p: p.set_tc_engine(0)), (1, lambda p: p.set_tc_fill(2.0)),
+               (0, lambda p: p.set_rhs_block(4))]
+    for i, (j, change) in enumerate(changes):
+        change(plans[j])
         run_and_compare()
         assert g.captures() == 2 + i
     plans[0].set_rhs_block(4)  # unchanged value: the graph stays

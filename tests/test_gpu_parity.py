@@ -270,3 +270,26 @@ def test_bench_configuration_full_size_vs_oracle(lib, oracle_lib):
     check(y64, ref, 1e-10, "fp64")
     check(y32, ref, 1e-5, "mixed")
     plan.close()
+
+
+@pytest.mark.parametrize("fm", [0, 1, 2])
+def test_cousin_engines(lib, oracle_lib, fm):
+    """Both mixed cousin-interpolation engines (cone-stationary lists, the default, and the
+    point-stationary kernel kept for plans of 2^24 points or more) against the oracle, with
+    split, combined and mixed factor levels, three right-hand sides; the two agree to FP32
+    rounding.  The cone-stationary engine's second pass sums in fixed order: bitwise
+    reproducible."""
+    s, k = sphere_workload(64, 8, 6.0)
+    sig = random_density(s.N, 3, 41)
+    prm = dict(levels=5, Ps=5, Pang=8, factor_mode=fm)
+    ref, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k, identity_coef=0.5, **prm), sig)
+    plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, **prm))
+    y1 = gpu_apply(plan, sig, np.complex64)
+    assert np.array_equal(y1, gpu_apply(plan, sig, np.complex64))
+    plan.set_cousin_engine(0)
+    y0 = gpu_apply(plan, sig, np.complex64)
+    assert plan.missed_lookups() == 0
+    check(y1, ref, 1e-5, "cone-stationary")
+    check(y0, ref, 1e-5, "point-stationary")
+    check(y1, y0, 2e-6, "engines")
+    plan.close()

@@ -75,14 +75,16 @@ def test_noalloc_matches_apply(B, prec, dtype, tol):
 
 @pytest.mark.parametrize("prec,dtype", [(0, np.complex128), (1, np.complex64)])
 def test_noalloc_after_another_plan(B, prec, dtype):
-    # plan A: 4-wavelength sphere, five levels (three propagation steps), orders (5, 8) with
-    # every propagation level forced onto the tensor cores
+    # plan A: 4-wavelength sphere, five levels (three propagation steps), orders (5, 8), the
+    # combined factor on every level (its FP64 workspace, 57 MiB, fits the 64 MiB array), every
+    # propagation level forced onto the tensor cores
     sa, ka = sphere_workload(48, 6, 4.0)
-    plan_a = B.Plan(sa.points, sa.normals, sa.weights, B.Params(k=ka, levels=5, Ps=5, Pang=8))
+    plan_a = B.Plan(sa.points, sa.normals, sa.weights, B.Params(k=ka, levels=5, Ps=5, Pang=8, factor_mode=1))
     plan_a.set_tc_fill(0.0)
     sig_a = torch.from_numpy(random_density(sa.N, 1, 21).astype(dtype)).cuda()
-    # plan B (under test): 3-wavelength sphere, four levels, orders (5, 8), tensor-core
-    # propagation, a sparse correction with empty and full rows, two right-hand sides
+    # plan B (under test): 3-wavelength sphere, four levels, orders (5, 8), split factors at the
+    # leaf level and the combined one above, tensor-core propagation, a sparse correction with
+    # empty and full rows, two right-hand sides
     sb, kb = sphere_workload(32, 8, 3.0)
     plan_b = B.Plan(sb.points, sb.normals, sb.weights, B.Params(k=kb, levels=4, Ps=5, Pang=8))
     plan_b.set_tc_fill(0.0)
