@@ -15,8 +15,14 @@ timed steps to flush the 129 MB L2.  With torchrun (N > 1) every rank runs an
 independent replica (the apply does not shard across GPUs); value = points of
 all ranks / max-over-ranks time.
 
---impl reference times the FP64 CPU oracle (Algorithm 1 as written, OpenMP on
-the host cores) on a bounded sample of the same workload.
+Beside the headline: a four-right-hand-side apply (per-rhs throughput), the
+adjoint and the vector-Jacobian product, an end-to-end apply through pinned host
+buffers, off-surface evaluation, the FP64 apply, the paper's orders (3, 5, 5),
+the 24-scatterer batch as one CUDA graph at the headline orders, and the FP64
+CPU oracle applied to the whole workload on the host cores (cpu_baseline).
+
+--impl reference times the FP64 CPU oracle (the IFGF apply of Section 3.4, OpenMP
+on the host cores) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -38,7 +44,6 @@ sys.path.insert(0, ROOT)
 METRIC = "CFIE matvec Mpts/s at rel err≤1e-4: mixed vs FP64 IFGF; adjoint/forward ratio"
 UNIT = "Mpts/s"
 FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 
 
 def parse():
@@ -60,7 +65,8 @@ def parse():
     ap.add_argument("--tc-engine", type=int, default=None, help="tensor-core propagation engine: 1 tcgen05, 0 mma.sync")
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
-    ap.add_argument("--batch", action="store_true", help="also time the 24-scatterer graph apply")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-scatterer graph apply")
+    ap.add_argument("--batch-orders", default="5x8", help="Ps x Pang of the 24-scatterer graph apply")
     return ap.parse_args()
 
 
@@ -151,8 +157,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_OF_STAGE = {"leaf": "k_leaf32x2", "near": "k_near32", "cousin": "k_cousin_w", "prop": "k_prop_w",
-                   "prop_tc": "k_prop_t5"}
+KERNEL_OF_STAGE = {"leaf": "k_leaf32x2", "near": "k_near32", "cousin": "k_cousin_cs", "cousin_sum": "k_cousin_sum",
+                   "prop": "k_prop_w", "prop_tc": "k_prop_t5"}
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "dram_traffic_sphere16lambda_5x8.txt")
 
@@ -211,6 +217,12 @@ def algorithmic_flops(info, P, nrhs, split_levels):
     cousin = {d: info["cousin_evals"][d] * (100 + 4 * P * nrhs * nf(d)) for d in range(3, D + 1)}
     prop = {d: info["prop_evals"][d] * (100 + 4 * P * nrhs * nf(d + 1)) for d in range(3, D)}
     return leaf, near, cousin, prop
+
+
+def launches_of(stages):
+    """Kernel launches of one profiled apply: one per stage entry, eight (one per child octant)
+    for a tensor-core propagation level."""
+    return sum(8 if kind == "prop_tc" else 1 for kind, _, _ in stages)
 
 
 def reduce_over_ranks(ms: float, points: float, world: int, device="cpu"):
@@ -326,12 +338,20 @@ def run_ours(args):
     ms, points = reduce_over_ranks(float(np.mean(t_mixed)), N * nrhs, world, dev)
     value = points / (ms * 1e3)
 
+    # ---- several right-hand sides per apply: per-rhs throughput ----
+    sig4 = torch.from_numpy(random_density_like(np.zeros((4, N)), 11).astype(np.complex64)).to(dev)
+    y4 = torch.empty_like(sig4)
+    t4 = timed(lambda: plan.apply(sig4, out=y4), max(3, args.steps // 5), 2)
+    ms4 = float(np.mean(t4))
+    multi_rhs = {"nrhs": 4, "ms_per_step": ms4, "value_per_rhs": N * 4 / (ms4 * 1e3), "unit": UNIT,
+                 "speedup_per_rhs_vs_nrhs1": (N * 4 / ms4) / (N * nrhs / float(np.mean(t_mixed)))}
+
     # ---- per-launch device times (profiled apply) ----
     plan.set_profiling(True)
     plan.apply(sig32, out=y32)
     stages = plan.stage_times()
     plan.set_profiling(False)
-    launches_per_apply = len(stages)
+    launches_per_apply = launches_of(stages)
     split = info["split"]
     leaf_f, near_f, cousin_f, prop_f = algorithmic_flops(info, P, nrhs, split)
     by_kind = {}
@@ -342,6 +362,7 @@ def run_ours(args):
         lv = [lvl for k2, lvl, _ in stages if k2 == kind]
         if lv:
             flops_of[kind] = sum(prop_f[lvl] for lvl in lv)
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     dom = max((kk for kk in by_kind if kk in flops_of), key=lambda kk: by_kind[kk])
     # kernel launches: the tensor-core propagation records one entry per level for its 8 octant launches
     n_dom = sum(8 if kind == "prop_tc" else 1 for kind, _, _ in stages if kind == dom)
@@ -352,8 +373,9 @@ def run_ours(args):
         bound, peak, basis = "tensor", tf32_peak_tflops(), "TF32 tensor: measured sustained bf16 x 1.1/2.25"
     else:
         bound = "alu"
-        peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        basis = f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x {sm_mhz:g} MHz"
+        peak = num_sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        basis = (f"FP32 FMA: {num_sms} SMs (multi_processor_count of the device) x {FP32_LANES_PER_SM} lanes "
+                 f"x 2 flops x {sm_mhz:g} MHz (maximum SM clock)")
     roofline = {"bound": bound, "kernel": KERNEL_OF_STAGE.get(dom, dom), "stage": dom,
                 "launches_per_apply": n_dom, "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -425,10 +447,10 @@ def run_ours(args):
                                   f"nrhs={nrhs}",
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
-           "roofline": roofline, "e2e": e2e, "adjoint": adjoint, "off_surface": off_surface,
+           "roofline": roofline, "e2e": e2e, "multi_rhs": multi_rhs, "adjoint": adjoint, "off_surface": off_surface,
            "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
            # gather, sum and (when the sources are split into chunks) the reduction per off-surface call
-           "gpu_launches": launches_per_apply * args.steps + len(adj_stages) * max(3, args.steps // 4)
+           "gpu_launches": launches_per_apply * (args.steps + len(t4)) + len(adj_stages) * max(3, args.steps // 4)
                            + 2 * 3 * k_off,
            "clocks": clk}
 
@@ -466,41 +488,66 @@ def run_ours(args):
                                         "rows": int(len(rows))}
             out["fp64"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["fp64"]
             out["paper_orders_3x5"]["rel_err_vs_direct"] = out["rel_err_vs_direct"]["paper_orders_3x5_mixed"]
-            tree = full_octree(s)
-            tree.update(nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode)
-            # repeated oracle applies on the cap sample: about 10 s (at most 30 s) of CPU work
-            caps = []
-            t_all = time.perf_counter()
+            # the oracle IFGF on the whole workload (same orders, cone grid and factor mode), timed once
+            # (about 10-20 s on the host cores); a second apply when the first took under 15 s
+            po = oracle.IFGFParams(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0, factor_mode=args.factor_mode,
+                                   identity_coef=0.5)
+            t_or = []
             while True:
-                n_cap, t_cap = oracle_cap_apply(s, k, sig, tree, Ps, Pang)
-                caps.append(t_cap)
-                el = time.perf_counter() - t_all
-                if el >= 10.0 or el + t_cap > 30.0:
+                t = time.perf_counter()
+                y_or, _ = oracle.ifgf(s.points, s.normals, s.weights, po, sig)
+                t_or.append(time.perf_counter() - t)
+                if len(t_or) >= 2 or t_or[0] >= 15.0:
                     break
-            t_cap = float(np.mean(caps))
+            t_cpu = float(np.mean(t_or))
+            e_or = y32.cpu().numpy() - y_or
+            out["rel_err_vs_oracle"] = {"mixed_l2": float(np.linalg.norm(e_or) / np.linalg.norm(y_or)),
+                                        "mixed_max": float(np.abs(e_or).max() / np.abs(y_or).max())}
             out["cpu_baseline"] = {
-                "value": n_cap * nrhs / (t_cap * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                "sample": f"{len(caps)} oracle IFGF applies (FP64, OpenMP) on the {n_cap}-point spherical cap z > 0.75 "
-                          f"of the workload, full sphere's octree, orders ({Ps},{Pang},{Pang}), factor mode "
-                          f"{args.factor_mode}; {t_cap:.2f} s each, {sum(caps):.1f} s in total",
+                "value": N * nrhs / (t_cpu * 1e6), "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"the whole workload: {len(t_or)} oracle IFGF apply(s) (FP64, OpenMP) of all N={N} points, "
+                          f"orders ({Ps},{Pang},{Pang}), factor mode {args.factor_mode}; {t_cpu:.1f} s each",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
-    if args.batch:
+    if not args.no_batch:
         from paper_2112_06316_gb300 import Group
         from workloads import random_density as _rd, scatterer_batch
 
+        bPs, bPang = (int(v) for v in args.batch_orders.split("x"))
         bodies = scatterer_batch(seed=3)
         t0 = time.perf_counter()
-        bplans = [Plan(b.points, b.normals, b.weights, Params(k=kb)) for b, kb in bodies]
-        bsig = [torch.from_numpy(_rd(b.N, 4, 300 + i).astype(np.complex64)).to(dev) for i, (b, _) in enumerate(bodies)]
+        bplans = [Plan(b.points, b.normals, b.weights, Params(k=kb, Ps=bPs, Pang=bPang, factor_mode=args.factor_mode))
+                  for b, kb in bodies]
+        bsig_h = [_rd(b.N, 4, 300 + i) for i, (b, _) in enumerate(bodies)]
+        bsig = [torch.from_numpy(x.astype(np.complex64)).to(dev) for x in bsig_h]
         bout = [torch.empty_like(x) for x in bsig]
         build_s = time.perf_counter() - t0
         grp = Group(bplans)
         tb = timed(lambda: grp.apply(bsig, bout), max(3, args.steps // 10), 2)
         npts = sum(b.N for b, _ in bodies) * 4
-        out["batch_24_scatterers"] = {"value": npts / (float(np.mean(tb)) * 1e3), "unit": UNIT,
-                                      "ms_per_step": float(np.mean(tb)), "points_x_rhs": npts,
-                                      "orders": "3x5", "plan_build_s": round(build_s, 1)}
+        batch = {"value": npts / (float(np.mean(tb)) * 1e3), "unit": UNIT, "ms_per_step": float(np.mean(tb)),
+                 "bodies": len(bodies), "points_x_rhs": npts, "nrhs_per_body": 4,
+                 "orders": f"{bPs}x{bPang}", "plan_build_s": round(build_s, 1)}
+        if rank == 0 and not args.quick:
+            import oracle
+
+            # error of every body's first right-hand side against 200 direct-sum rows
+            errs = []
+            for i, (b, kb) in enumerate(bodies):
+                r = np.random.default_rng(10 + i).choice(b.N, min(200, b.N), replace=False)
+                yd = oracle.direct(b.points, b.normals, b.weights, kb, kb, bsig_h[i][:1], cI=0.5, rows=r)
+                yb = bout[i][:1].cpu().numpy()[:, r]
+                errs.append(float(np.linalg.norm(yb - yd) / np.linalg.norm(yd)))
+            batch["rel_err_vs_direct_max_over_bodies"] = max(errs)
+            batch["rel_err_vs_direct_median"] = float(np.median(errs))
+        out["batch_24_scatterers"] = batch
+        nl = 0
+        for bp, x in zip(bplans, bsig):  # launches of one graph replay, counted from profiled applies
+            bp.set_profiling(True)
+            bp.apply(x)
+            nl += launches_of(bp.stage_times())
+            bp.set_profiling(False)
+        out["gpu_launches"] += nl * len(tb)
         grp.close()
         for bp in bplans:
             bp.close()
