@@ -171,10 +171,40 @@ ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev
  * cone values with the adjoint cone values (near field, cousin interpolation,
  * propagation ratios, leaf factors).  The paper has no adjoint or k-derivative.
  * Runs one forward apply and one adjoint apply internally (gsigma is used as
- * scratch for the forward output); synchronises `stream` when dk is requested.
+ * scratch for the forward output); the k-derivative of the cousin and propagation
+ * stages is reduced inside the adjoint's anterpolation, that of the leaf
+ * evaluation and the near field by two more passes.  Synchronises `stream` when
+ * dk is requested.
  * Errors as ifgf_apply; sigma, g and gsigma must be distinct. */
 ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g_dev, void *gsigma_dev, int nrhs,
                            double *dk_host, ifgf_precision prec, void *stream);
+
+/* Bytes of the workspace that an apply with nrhs right-hand sides in precision prec
+ * uses: w*sigma and the field in Morton order, every level's cone values and, on
+ * the mixed path, the cousin-interpolation value buffer.  Host-only, synchronous.
+ * Errors: IFGF_EINVAL. */
+ifgf_status ifgf_plan_workspace_bytes(const ifgf_plan *plan, int nrhs, ifgf_precision prec, int64_t *bytes);
+
+/* ifgf_apply on a caller-owned workspace: ws_dev is device memory of at least
+ * ifgf_plan_workspace_bytes(nrhs, prec) bytes, 256-byte aligned, not aliasing
+ * sigma or y; the library neither keeps nor frees it.  After the call (in stream
+ * order) ws_dev holds the forward state of this sigma -- w*sigma in Morton order
+ * and every level's cone values -- which ifgf_apply_vjp_ws reads, so a caller
+ * (an autograd forward, for instance) can keep it for the backward pass without a
+ * second forward apply.  Arguments, results and errors otherwise as ifgf_apply;
+ * IFGF_EINVAL for a missing, small or misaligned workspace.  The paper has no
+ * counterpart (no derivatives). */
+ifgf_status ifgf_apply_ws(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs, ifgf_precision prec,
+                          void *ws_dev, int64_t ws_bytes, void *stream);
+
+/* ifgf_apply_vjp on the forward state that ifgf_apply_ws left in ws_dev (same
+ * plan, nrhs and precision, and the sigma whose gradient is wanted): gsigma =
+ * A^H g and, if dk_host is not NULL, *dk_host = Re <g, dA/dk sigma>, without
+ * re-running the forward apply.  ws_dev is read only.  Synchronises `stream`
+ * when dk is requested.  Errors as ifgf_apply_vjp, IFGF_EINVAL for a missing,
+ * small or misaligned workspace. */
+ifgf_status ifgf_apply_vjp_ws(ifgf_plan *plan, const void *ws_dev, int64_t ws_bytes, const void *g_dev,
+                              void *gsigma_dev, int nrhs, double *dk_host, ifgf_precision prec, void *stream);
 
 /* ifgf_apply without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc at apply time -- for

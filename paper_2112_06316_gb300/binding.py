@@ -72,6 +72,10 @@ _SIGS = [
     ("ifgf_apply_vjp", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.c_int, _VP]),
     ("ifgf_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_plan_workspace_bytes", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    ("ifgf_apply_ws", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int64, _VP]),
+    ("ifgf_apply_vjp_ws", ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, _VP]),
     ("ifgf_rp_correction", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
@@ -284,6 +288,49 @@ class Plan:
         check(lib().ifgf_apply_vjp(self._h, _VP(s_.data_ptr()), _VP(g_.data_ptr()), _VP(out.data_ptr()),
                                    ctypes.c_int(s_.shape[0]), ctypes.byref(dk), ctypes.c_int(prec),
                                    _VP(_stream_ptr(stream))))
+        return (out.reshape(-1) if squeeze else out), float(dk.value)
+
+    def workspace_bytes(self, nrhs: int, prec: int) -> int:
+        """Bytes of the apply workspace for nrhs right-hand sides in one precision."""
+        n = ctypes.c_int64()
+        check(lib().ifgf_plan_workspace_bytes(self._h, ctypes.c_int(nrhs), ctypes.c_int(prec), ctypes.byref(n)))
+        return int(n.value)
+
+    def apply_with_state(self, sigma, stream=None):
+        """(y, state): y = A sigma computed on a fresh workspace tensor `state` that holds the
+        forward state afterwards (for vjp_from_state)."""
+        import torch
+
+        prec = FP64 if sigma.dtype == torch.complex128 else MIXED if sigma.dtype == torch.complex64 else None
+        if prec is None or not sigma.is_cuda:
+            raise TypeError("sigma must be a complex64 or complex128 CUDA tensor")
+        squeeze = sigma.dim() == 1
+        s_ = (sigma.reshape(1, -1) if squeeze else sigma).contiguous()
+        if s_.shape[-1] != self.N:
+            raise ValueError(f"sigma must have N={self.N} columns")
+        nb = self.workspace_bytes(int(s_.shape[0]), prec)
+        state = torch.empty(max(nb, 1) + 256, dtype=torch.uint8, device=s_.device)
+        off = (-state.data_ptr()) % 256  # 256-byte aligned view
+        ws = state[off:off + max(nb, 1)]
+        y = torch.empty_like(s_)
+        check(lib().ifgf_apply_ws(self._h, _VP(s_.data_ptr()), _VP(y.data_ptr()), ctypes.c_int(s_.shape[0]),
+                                  ctypes.c_int(prec), _VP(ws.data_ptr()), ctypes.c_int64(nb), _VP(_stream_ptr(stream))))
+        return (y.reshape(-1) if squeeze else y), ws
+
+    def vjp_from_state(self, state, g, stream=None):
+        """(A^H g, Re <g, dA/dk sigma>) from the forward state of apply_with_state(sigma)."""
+        import torch
+
+        prec = FP64 if g.dtype == torch.complex128 else MIXED if g.dtype == torch.complex64 else None
+        if prec is None:
+            raise TypeError("complex64 or complex128 expected")
+        squeeze = g.dim() == 1
+        g_ = (g.reshape(1, -1) if squeeze else g).contiguous()
+        out = torch.empty_like(g_)
+        dk = ctypes.c_double(0.0)
+        check(lib().ifgf_apply_vjp_ws(self._h, _VP(state.data_ptr()), ctypes.c_int64(state.numel()),
+                                      _VP(g_.data_ptr()), _VP(out.data_ptr()), ctypes.c_int(g_.shape[0]),
+                                      ctypes.byref(dk), ctypes.c_int(prec), _VP(_stream_ptr(stream))))
         return (out.reshape(-1) if squeeze else out), float(dk.value)
 
     def apply_noalloc_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):

@@ -12,15 +12,15 @@ namespace ifgf {
 
 template <int PS, int PA>
 ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec, cudaStream_t s, void *gs, void *bws,
-                          void **G);
+                          void **G, void *const *Fd, double *dk_partials);
 template <int PS, int PA>
-ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
                      long long *nparts);
 #define IFGF_EXTERN(a, b)                                                                                           \
     extern template ifgf_status run_adjoint_t<a, b>(Plan &, const void *, void *, int, int, cudaStream_t, void *,     \
-                                                    void *, void **);                                               \
-    extern template ifgf_status run_dk_t<a, b>(Plan &, int, int, cudaStream_t, const void *, void **, void *,         \
-                                               double *, long long *);
+                                                    void *, void **, void *const *, double *);                      \
+    extern template ifgf_status run_dk_t<a, b>(Plan &, int, int, cudaStream_t, const void *, void **, double *,       \
+                                               long long *);
 IFGF_EXTERN(3, 5)
 IFGF_EXTERN(4, 6)
 IFGF_EXTERN(5, 7)
@@ -29,7 +29,10 @@ IFGF_EXTERN(6, 8)
 #undef IFGF_EXTERN
 
 ifgf_status apply_correction_adjoint(Plan &p, const void *g, void *y, int nrhs, int prec, cudaStream_t s);
+ifgf_status apply_correction(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
 ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
+ifgf_status run_apply_on(Plan &p, const Workspace &ws, const void *sigma, void *y, int nrhs, int prec,
+                         cudaStream_t s);
 void clear_error();
 
 namespace {
@@ -78,8 +81,11 @@ ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
 
 // A^H g into out (without the correction); leaves the gathered g and the cone
 // values G of every level in the adjoint workspace (returned through gs_out / G).
+// With Fd (the forward cone values of every level) the anterpolation also writes the
+// cousin and propagation parts of Re <g, dA/dk sigma>, one double per relevant cone
+// and level in order, to dk_partials.
 ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, int prec, cudaStream_t s, void **gs_out,
-                         void **G) {
+                         void **G, void *const *Fd = nullptr, double *dk_partials = nullptr) {
     ifgf_status st = ensure_adjoint_lists(p, s);
     if (st != IFGF_OK) return st;
     const size_t cb = prec == IFGF_FP64 ? 16 : 8;
@@ -104,8 +110,9 @@ ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, in
     char *c = (char *)p.adj_ws;
     for (int d = 3; d <= p.D; d++) G[d] = c + oG[d];
     *gs_out = c + ogs;
-#define IFGF_CASE(a, b) \
-    if (p.Ps == a && p.Pang == b) return run_adjoint_t<a, b>(p, g_dev, out_dev, nrhs, prec, s, c + ogs, c + ob, G);
+#define IFGF_CASE(a, b)                                                                                     \
+    if (p.Ps == a && p.Pang == b)                                                                           \
+        return run_adjoint_t<a, b>(p, g_dev, out_dev, nrhs, prec, s, c + ogs, c + ob, G, Fd, dk_partials);
     IFGF_CASE(3, 5)
     IFGF_CASE(4, 6)
     IFGF_CASE(5, 7)
@@ -116,10 +123,10 @@ ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, in
     return IFGF_EUNSUPPORTED;
 }
 
-ifgf_status run_dk(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
+ifgf_status run_dk(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
                    long long *nparts) {
 #define IFGF_CASE(a, b) \
-    if (p.Ps == a && p.Pang == b) return run_dk_t<a, b>(p, nrhs, prec, s, gs, G, H, partials, nparts);
+    if (p.Ps == a && p.Pang == b) return run_dk_t<a, b>(p, nrhs, prec, s, gs, G, partials, nparts);
     IFGF_CASE(3, 5)
     IFGF_CASE(4, 6)
     IFGF_CASE(5, 7)
@@ -168,6 +175,75 @@ extern "C" ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, vo
     return apply_correction_adjoint(p, g_dev, out_dev, nrhs, (int)prec, s);
 }
 
+namespace ifgf {
+namespace {
+
+// Gradient part of the vector-Jacobian product on a forward state `fwd` (w sigma and the cone
+// values of every level left by a forward apply of sigma): gsigma = A^H g and, when dk_host is
+// given, dk = Re <g, dA/dk sigma> (near field and leaf evaluation by their own reductions, the
+// cousin and propagation terms inside the fused anterpolation).
+ifgf_status vjp_core(Plan &p, const Workspace &fwd, const void *g_dev, void *gsigma_dev, int nrhs, double *dk_host,
+                     int prec, cudaStream_t s) {
+    double *partials = nullptr;
+    long long need = 0;
+    if (dk_host) {
+        need = (p.N + 127) / 128 + (p.lv[p.D].nrc * p.P + 127) / 128;
+        for (int d = 3; d <= p.D; d++) need += p.lv[d].nrc;
+        const size_t bytes = sizeof(double) * (need + 1);
+        if (bytes > p.dk_ws_bytes) {
+            if (p.dk_ws) cudaFree(p.dk_ws);
+            p.dk_ws = nullptr;
+            p.dk_ws_bytes = 0;
+            cudaError_t e = cudaMalloc(&p.dk_ws, bytes);
+            if (e != cudaSuccess) return cuda_fail(e, "k-gradient workspace");
+            p.dk_ws_bytes = bytes;
+        }
+        partials = (double *)p.dk_ws;
+    }
+    void *gs = nullptr, *G[IFGF_MAXD + 1] = {};
+    void *Fd[IFGF_MAXD + 1] = {};
+    for (int d = 3; d <= p.D; d++) Fd[d] = fwd.F[d];
+    ifgf_status st = adjoint_core(p, g_dev, gsigma_dev, nrhs, prec, s, &gs, G, dk_host ? Fd : nullptr, partials);
+    if (st != IFGF_OK) return st;
+    st = apply_correction_adjoint(p, g_dev, gsigma_dev, nrhs, prec, s);
+    if (st != IFGF_OK || !dk_host) return st;
+    long long ncone = 0;
+    for (int d = 3; d <= p.D; d++) ncone += p.lv[d].nrc;
+    long long np = 0;
+    const Workspace saved = p.ws;
+    p.ws = fwd;  // run_dk reads w sigma and F_D of the forward state
+    st = run_dk(p, nrhs, prec, s, gs, G, partials + ncone, &np);
+    p.ws = saved;
+    if (st != IFGF_OK) return st;
+    np += ncone;
+    std::vector<double> h(np > 0 ? np : 1, 0.0);
+    if (np > 0) {
+        cudaError_t e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "vjp partial copy");
+    }
+    double sum = 0.0;
+    for (long long i = 0; i < np; i++) sum += h[i];
+    *dk_host = sum;
+    return IFGF_OK;
+}
+
+// Caller-provided workspace: checks its size and alignment and lays the parts out in it.
+ifgf_status bind_user_workspace(const Plan &p, void *ws_dev, int64_t ws_bytes, int nrhs, int prec, Workspace &ws) {
+    WorkspaceLayout lay;
+    const size_t need = workspace_layout(p, nrhs, prec, lay);
+    if (!ws_dev || ws_bytes < 0 || (size_t)ws_bytes < need || ((uintptr_t)ws_dev & 255) != 0) {
+        set_error("workspace must be a 256-byte aligned device buffer of at least %zu bytes (got %lld at %p)", need,
+                  (long long)ws_bytes, ws_dev);
+        return IFGF_EINVAL;
+    }
+    workspace_bind(ws, p, ws_dev, lay, nrhs, prec);
+    return IFGF_OK;
+}
+
+}  // namespace
+}  // namespace ifgf
+
 extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g_dev, void *gsigma_dev,
                                       int nrhs, double *dk_host, ifgf_precision prec, void *stream) {
     clear_error();
@@ -184,40 +260,51 @@ extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, co
     // forward state (a = w sigma, cone values F) in the plan workspace; gsigma is scratch here
     st = run_apply(p, sigma_dev, gsigma_dev, nrhs, (int)prec, s);
     if (st != IFGF_OK) return st;
-    void *gs = nullptr, *G[IFGF_MAXD + 1] = {};
-    st = adjoint_core(p, g_dev, gsigma_dev, nrhs, (int)prec, s, &gs, G);
-    if (st != IFGF_OK) return st;
-    st = apply_correction_adjoint(p, g_dev, gsigma_dev, nrhs, (int)prec, s);
-    if (st != IFGF_OK) return st;
-    if (!dk_host) return IFGF_OK;
-    // partial sums: near field, one reduction per level, leaf; scratch H for the largest level
-    long long need = (p.N + 127) / 128 + (long long)kDkDotBlocks * (p.D - 2) + (p.lv[p.D].nrc * p.P + 127) / 128;
-    size_t hbytes = 0;
-    for (int d = 3; d <= p.D; d++)
-        hbytes = std::max(hbytes, (prec == IFGF_FP64 ? 16 : 8) * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
-    hbytes = (hbytes + 255) & ~(size_t)255;
-    const size_t bytes = hbytes + sizeof(double) * (need + 1);
-    if (bytes > p.dk_ws_bytes) {
-        if (p.dk_ws) cudaFree(p.dk_ws);
-        p.dk_ws = nullptr;
-        p.dk_ws_bytes = 0;
-        cudaError_t e = cudaMalloc(&p.dk_ws, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "k-gradient workspace");
-        p.dk_ws_bytes = bytes;
+    return vjp_core(p, p.ws, g_dev, gsigma_dev, nrhs, dk_host, (int)prec, s);
+}
+
+extern "C" ifgf_status ifgf_plan_workspace_bytes(const ifgf_plan *plan, int nrhs, ifgf_precision prec,
+                                                 int64_t *bytes) {
+    clear_error();
+    if (!plan || !bytes || nrhs < 0 || (prec != IFGF_FP64 && prec != IFGF_MIXED)) {
+        set_error("null plan or output, negative nrhs or unknown precision");
+        return IFGF_EINVAL;
     }
-    void *H = p.dk_ws;
-    double *partials = (double *)((char *)p.dk_ws + hbytes);
-    long long np = 0;
-    st = run_dk(p, nrhs, (int)prec, s, gs, G, H, partials, &np);
-    std::vector<double> h(np > 0 ? np : 1, 0.0);
-    if (st == IFGF_OK && np > 0) {
-        cudaError_t e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) st = cuda_fail(e, "vjp partial copy");
-    }
-    if (st != IFGF_OK) return st;
-    double sum = 0.0;
-    for (long long i = 0; i < np; i++) sum += h[i];
-    *dk_host = sum;
+    WorkspaceLayout lay;
+    *bytes = (int64_t)workspace_layout(plan->p, nrhs, (int)prec, lay);
     return IFGF_OK;
+}
+
+extern "C" ifgf_status ifgf_apply_ws(ifgf_plan *plan, const void *sigma_dev, void *y_dev, int nrhs,
+                                     ifgf_precision prec, void *ws_dev, int64_t ws_bytes, void *stream) {
+    clear_error();
+    ifgf_status st = check_args(plan, sigma_dev, y_dev, nrhs, prec);
+    if (st != IFGF_OK || nrhs == 0) return st;
+    Plan &p = plan->p;
+    Workspace ws;
+    st = bind_user_workspace(p, ws_dev, ws_bytes, nrhs, (int)prec, ws);
+    if (st != IFGF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = run_apply_on(p, ws, sigma_dev, y_dev, nrhs, (int)prec, s);
+    if (st != IFGF_OK) return st;
+    return apply_correction(p, sigma_dev, y_dev, nrhs, (int)prec, s);
+}
+
+extern "C" ifgf_status ifgf_apply_vjp_ws(ifgf_plan *plan, const void *ws_dev, int64_t ws_bytes, const void *g_dev,
+                                         void *gsigma_dev, int nrhs, double *dk_host, ifgf_precision prec,
+                                         void *stream) {
+    clear_error();
+    ifgf_status st = check_args(plan, g_dev, gsigma_dev, nrhs, prec);
+    if (st != IFGF_OK) return st;
+    if (dk_host) *dk_host = 0.0;
+    if (nrhs == 0) return IFGF_OK;
+    Plan &p = plan->p;
+    Workspace ws;
+    st = bind_user_workspace(p, const_cast<void *>(ws_dev), ws_bytes, nrhs, (int)prec, ws);
+    if (st != IFGF_OK) return st;
+    if ((const void *)gsigma_dev == ws_dev || g_dev == ws_dev) {
+        set_error("the workspace must not alias g or gsigma");
+        return IFGF_EINVAL;
+    }
+    return vjp_core(p, ws, g_dev, gsigma_dev, nrhs, dk_host, (int)prec, (cudaStream_t)stream);
 }

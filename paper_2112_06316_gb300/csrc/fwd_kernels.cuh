@@ -1165,14 +1165,38 @@ __device__ __forceinline__ C cconj_mul(C a, C b) {  // conj(a) * b
     return r;
 }
 
+// Sum of one double per thread of the block, written to partials[blockIdx.x] (the
+// k-derivative reductions; every thread of the block must call it).
+__device__ __forceinline__ void block_sum_store(double v, double *partials) {
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) partials[blockIdx.x] = v;
+    }
+}
+
+// Re(conj(a) * b)
+template <typename C>
+__device__ __forceinline__ double re_conj_mul(C a, C b) {
+    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+
 // Per-entry data staged in shared memory by the anterpolation kernel: the angular
 // basis values and, per factor, the radial basis values times the entry's complex
 // weight (sv[f][a] = Ls[a] v_f).  Rows padded so that vector loads stay aligned.
-template <typename T, int PS, int PA>
+template <typename T, int PS, int PA, int NSV>
 struct __align__(16) AntEntry {
     static constexpr int PAP = (PA + 3) & ~3, PSP = (PS + 1) & ~1;
     T Lt[PAP], Lp[PAP];
-    typename CT<T>::c sv[2][PSP];
+    typename CT<T>::c sv[NSV][PSP];  // [factor] weights; FP32 with the k-derivative also [2 + factor]
+    T rho;                           // k-derivative factor of the entry (FP64 with the k-derivative)
 };
 
 // FP32 anterpolation accumulates with the packed two-lane FMA (f2fma).
@@ -1187,17 +1211,21 @@ struct AntCols {
 
 // Anterpolation into the relevant cones of level d (transpose of K2 and K3):
 // G_d[rc] = sum over its cousin targets of L(t) conj(E) g  +  sum over parent
-// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  With DK every entry's
-// weight is scaled by -i rho, rho = r (cousin target) or r_c - r_p (parent node):
-// the k-derivative of E and of the ratio, so that Re <H_d, F_d> is the
-// k-derivative of the level's cousin and propagation terms.  One block per rc.  The
-// FP32 version keeps six blocks per SM (at most 80 registers): the entry set-up
-// chases dependent loads, and that occupancy hides them better than the extra
-// registers of an uncapped build would pay back.
-template <int PS, int PA, bool MX, bool DK>
-__global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD, int has_parent,
-                                              const long long *__restrict__ ad_start, const int *__restrict__ ad_list,
-                                              ChebTab tb, const void *gs_, const void *Gp_, void *Gc_) {
+// nodes propagated from it of L(t) conj(ratio) G_{d-1}.  One block per rc.
+// With FUSE the block also accumulates H_d[rc], the same sum with every entry's
+// weight scaled by -i rho, rho = r (cousin target) or r_c - r_p (parent node) --
+// the k-derivatives of E and of the ratio -- and adds Re <H_d[rc], F_d[rc]> (F_d
+// the forward cone values) to dk_partials[rc]: the k-derivative of the level's
+// cousin and propagation terms, without storing H.  Each thread dots its own
+// entry group's share of H (the shares sum to H by linearity).  The FP32 adjoint
+// keeps six blocks per SM (at most 80 registers): the entry set-up chases
+// dependent loads, and that occupancy hides them better than the extra registers
+// of an uncapped build would pay back.
+template <int PS, int PA, bool MX, bool FUSE>
+__global__ void __launch_bounds__(128, MX ? (FUSE ? 4 : 6) : 4) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD,
+                                              int has_parent, const long long *__restrict__ ad_start,
+                                              const int *__restrict__ ad_list, ChebTab tb, const void *gs_,
+                                              const void *Gp_, void *Gc_, const void *Fd_, double *dk_partials) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
     constexpr int P = PS * PA * PA, PA2 = PA * PA;
@@ -1205,7 +1233,12 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
     const C *Gp = (const C *)Gp_;
     C *Gc = (C *)Gc_;
     constexpr int CQ = AntCols<PA, MX>::CQ, PAQ = PA / CQ;
-    typedef AntEntry<T, PS, PA> Ent;
+    // the k-derivative weights (-i rho) sv: staged as two more rows in FP32 (packed FMAs), formed
+    // from rho in the accumulation in FP64 (same FMA count; keeps the stage within 48 KB)
+    constexpr int NSV = (FUSE && MX) ? 4 : 2;
+    typedef AntEntry<T, PS, PA, NSV> Ent;
+    const C *Fd = (const C *)Fd_;
+    double dk = 0.0;  // FUSE: this thread's share of Re <H_d[rc], F_d[rc]> over all right-hand sides
     // the entries of one batch, and after the last batch the partial sums of the entry groups
     union Stage {
         Ent ent[128];
@@ -1226,14 +1259,18 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
     const int fac = uo / (PA * PAQ), rb = uo % (PA * PAQ);
     const int ub = rb / PAQ, uc0 = (rb % PAQ) * CQ;
     for (int q = 0; q < ca.nrhs; q++) {
-        C acc[CQ][PS];
-        unsigned long long acc2[CQ][PS];  // FP32: packed (re, im) accumulators of f2fma
+        C acc[CQ][PS], acck[FUSE ? CQ : 1][PS];
+        unsigned long long acc2[CQ][PS], acck2[FUSE ? CQ : 1][PS];  // FP32: packed (re, im) accumulators of f2fma
 #pragma unroll
         for (int j = 0; j < CQ; j++)
 #pragma unroll
             for (int a = 0; a < PS; a++) {
                 acc[j][a].x = acc[j][a].y = T(0);
                 acc2[j][a] = 0ull;
+                if constexpr (FUSE) {
+                    acck[j][a].x = acck[j][a].y = T(0);
+                    acck2[j][a] = 0ull;
+                }
             }
         int ev_next = e0 + threadIdx.x < e1 ? ad_list[e0 + threadIdx.x] : 0;
         for (long long base = e0; base < e1; base += 128) {
@@ -1245,7 +1282,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
             C v0, v1;
             v0.x = v0.y = v1.x = v1.y = T(0);
             int cone_got = L.rc_cone[rc];
-            T rho = T(0);  // k-derivative factor of the entry's weight (DK)
+            T rho = T(0);  // k-derivative factor of the entry's weight (FUSE)
             if (e < e1) {
                 if (ev < ca.N) {  // cousin target
                     const int i = ev;
@@ -1370,13 +1407,6 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         v0 = cconj_mul(ratio1, gp0);
                     }
                 }
-                if constexpr (DK) {  // (-i rho) v
-                    const C w0 = v0, w1 = v1;
-                    v0.x = rho * w0.y;
-                    v0.y = -rho * w0.x;
-                    v1.x = rho * w1.y;
-                    v1.y = -rho * w1.x;
-                }
                 // express the local coordinates in the list's cone (an FP32 classification can land
                 // in a neighbouring cone near a boundary): t' = t + 2 (i_got - i_list), phi wrapping
                 const int cl = L.rc_cone[rc];
@@ -1390,7 +1420,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                     t3[1] += T(2 * (itg - itl));
                     t3[2] += T(2 * dp);
                     const T lim = T(1.02);
-                    if (!DK && q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
+                    if (q == 0 && (fabs(t3[0]) > lim || fabs(t3[1]) > lim || fabs(t3[2]) > lim)) atomicAdd(ca.missed, 1ULL);
                 }
             }
             {
@@ -1417,6 +1447,21 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         me.sv[1][a] = z;
                     }
                 }
+                me.rho = rho;
+                if constexpr (FUSE && MX) {  // (-i rho) times the weights
+#pragma unroll
+                    for (int f = 0; f < 2; f++) {
+                        if (f == 1 && !csplit) break;
+#pragma unroll
+                        for (int a = 0; a < PS; a++) {
+                            const C z = me.sv[f][a];
+                            C zk;
+                            zk.x = rho * z.y;
+                            zk.y = -rho * z.x;
+                            me.sv[NSV - 2 + f][a] = zk;
+                        }
+                    }
+                }
             }
             __syncthreads();
             if (active) {
@@ -1435,28 +1480,41 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                         lp[0] = en.Lp[uc0];
                     }
                     if constexpr (MX && kAntPacked) {
-                        unsigned long long sv[PS];
+                        unsigned long long sv[PS], svk[FUSE ? PS : 1];
                         const unsigned long long *row = reinterpret_cast<const unsigned long long *>(en.sv[fac]);
 #pragma unroll
                         for (int a = 0; a < PS; a++) sv[a] = row[a];
+                        if constexpr (FUSE) {
+                            const unsigned long long *rowk = reinterpret_cast<const unsigned long long *>(en.sv[NSV - 2 + fac]);
+#pragma unroll
+                            for (int a = 0; a < PS; a++) svk[a] = rowk[a];
+                        }
 #pragma unroll
                         for (int j = 0; j < CQ; j++) {
                             const float w = lt * lp[j];
                             const unsigned long long w2 = f2pack(w, w);
 #pragma unroll
-                            for (int a = 0; a < PS; a++) f2fma(acc2[j][a], w2, sv[a]);
+                            for (int a = 0; a < PS; a++) {
+                                f2fma(acc2[j][a], w2, sv[a]);
+                                if constexpr (FUSE) f2fma(acck2[j][a], w2, svk[a]);
+                            }
                         }
                     } else {
                         C sv[PS];
 #pragma unroll
                         for (int a = 0; a < PS; a++) sv[a] = en.sv[fac][a];
+                        const T rho = FUSE ? en.rho : T(0);
 #pragma unroll
                         for (int j = 0; j < CQ; j++) {
-                            const T w = lt * lp[j];
+                            const T w = lt * lp[j], wr = w * rho;
 #pragma unroll
                             for (int a = 0; a < PS; a++) {
                                 acc[j][a].x = fma(w, sv[a].x, acc[j][a].x);
                                 acc[j][a].y = fma(w, sv[a].y, acc[j][a].y);
+                                if constexpr (FUSE) {  // (-i rho) w sv
+                                    acck[j][a].x = fma(wr, sv[a].y, acck[j][a].x);
+                                    acck[j][a].y = fma(-wr, sv[a].x, acck[j][a].y);
+                                }
                             }
                         }
                     }
@@ -1473,7 +1531,21 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
                     f2unpack(acc2[j][a], x, y);
                     acc[j][a].x = x;
                     acc[j][a].y = y;
+                    if constexpr (FUSE) {
+                        f2unpack(acck2[j][a], x, y);
+                        acck[j][a].x = x;
+                        acck[j][a].y = y;
+                    }
                 }
+        }
+        if constexpr (FUSE) {  // this entry group's share of H dotted with the forward values
+            if (active) {
+                const C *fo = Fd + (((long long)q * L.nrc + rc) * nfac + fac) * ca.Pstride + ub * PA + uc0;
+#pragma unroll
+                for (int j = 0; j < CQ; j++)
+#pragma unroll
+                    for (int a = 0; a < PS; a++) dk += re_conj_mul(acck[j][a], fo[a * PA2 + j]);
+            }
         }
         // the loop's last barrier ends every read of the entries: the union's partial sums reuse them
         if (active && eg > 0) {
@@ -1500,6 +1572,7 @@ __global__ void __launch_bounds__(128, MX ? 6 : 4) k_ant(CommonArgs ca, LevelArg
         }
         __syncthreads();
     }
+    if constexpr (FUSE) block_sum_store(dk, dk_partials);
 }
 
 // Transposed leaf evaluation: b_j += sum over the cone nodes of j's leaf box of
@@ -1793,46 +1866,11 @@ __global__ void k_scatter_adj(int N, int nrhs, const int *__restrict__ perm, dou
 // ============================================================================
 // k-derivative reductions:  Re <g, (dA/dk) sigma>  with the plan frozen and eta
 // fixed.  Each kernel mirrors a forward stage and reduces conj(cotangent) times
-// the k-derivative of that stage's output, using the forward cone values F and
-// the adjoint cone values G.  One double per block is written to `partials`.
+// the k-derivative of that stage's output, using the forward state (w sigma, the
+// cone values F) and the adjoint state (gathered g, the cone values G).  One
+// double per block is written to `partials`.  The cousin and propagation terms
+// are reduced inside the anterpolation (k_ant with FUSE).
 // ============================================================================
-__device__ __forceinline__ void block_sum_store(double v, double *partials) {
-    __shared__ double sh[32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) partials[blockIdx.x] = v;
-    }
-}
-
-// Re(conj(a) * b)
-template <typename C>
-__device__ __forceinline__ double re_conj_mul(C a, C b) {
-    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-}
-
-// Re <H, F> over the cone values of one level (both stored [nrhs][nrc][nfac][Pstride],
-// nodes n < P only); grid-stride over kDkDotBlocks blocks, one double per block.
-template <typename C>
-__global__ void __launch_bounds__(128) k_dot_re(const C *__restrict__ H, const C *__restrict__ F, long long rows,
-                                                int P, int Pstride, double *partials) {
-    double acc = 0.0;
-    const long long tot = rows * P;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long row = t / P, n = t % P;
-        const C h = H[row * Pstride + n], f = F[row * Pstride + n];
-        acc += (double)h.x * (double)f.x + (double)h.y * (double)f.y;
-    }
-    block_sum_store(acc, partials);
-}
-
 // near field: sum_i conj(g_i) sum_j dK/dk(x_i, x_j) a_j,  dK/dk = i r K - i E1 dn / r
 template <bool MX>
 __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, const void *a_, const void *gs_,
@@ -1853,16 +1891,18 @@ __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, con
                     if (j == i) continue;
                     T Er, Ei, Br, Bi, R, dnr;
                     if constexpr (MX) {
-                        const float d0 = (float)(L.ijk[3 * b] - L.ijk[3 * c]) + ca.f32[3 * i] - ca.f32[3 * j];
-                        const float d1 = (float)(L.ijk[3 * b + 1] - L.ijk[3 * c + 1]) + ca.f32[3 * i + 1] - ca.f32[3 * j + 1];
-                        const float d2 = (float)(L.ijk[3 * b + 2] - L.ijk[3 * c + 2]) + ca.f32[3 * i + 2] - ca.f32[3 * j + 2];
+                        const float4 fi = __ldg(ca.pn32 + 2 * i), fj = __ldg(ca.pn32 + 2 * j);
+                        const float d0 = (float)(L.ijk[3 * b] - L.ijk[3 * c]) + fi.x - fj.x;
+                        const float d1 = (float)(L.ijk[3 * b + 1] - L.ijk[3 * c + 1]) + fi.y - fj.y;
+                        const float d2 = (float)(L.ijk[3 * b + 2] - L.ijk[3 * c + 2]) + fi.z - fj.z;
                         const float r2 = d0 * d0 + d1 * d1 + d2 * d2, ir = rsqrtf(r2), r = r2 * ir;
                         if (!(r >= (float)(ca.tol / ca.HD))) continue;
                         float t = ca.kappa_hi * r;
                         t -= rintf(t);
                         float sn, cs;
                         cis_cycles(t, sn, cs);
-                        const float dn = d0 * ca.n32[3 * j] + d1 * ca.n32[3 * j + 1] + d2 * ca.n32[3 * j + 2];
+                        const float4 nj = __ldg(ca.pn32 + 2 * j + 1);
+                        const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
                         const float amp = ir / (4.f * kPiF * ca.HDf);
                         Er = amp * cs; Ei = amp * sn;
                         Br = dn * ir * ir / ca.HDf; Bi = -(ca.kf * dn * ir + ca.etaf);
@@ -1913,32 +1953,38 @@ __global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, Che
     if (tid < L.nrc * P) {
         const int rc = (int)(tid / P), n = (int)(tid % P);
         const int b = L.rc_box[rc];
+        // the node's geometry, once (FP32 in leaf units, FP64 absolute)
+        float s32 = 0.f, u32[3] = {0.f, 0.f, 0.f};
+        double s64 = 0.0, u64[3] = {0.0, 0.0, 0.0}, y0[3] = {0.0, 0.0, 0.0};
+        if constexpr (MX) node32<PS, PA>(L, tb, L.rc_cone[rc], n, s32, u32);
+        else {
+            node64<PS, PA>(L, tb, L.rc_cone[rc], n, s64, u64);
+            center64(ca, L, b, y0);
+        }
         for (int q = 0; q < ca.nrhs; q++) {
             T s0r = T(0), s0i = T(0), s1r = T(0), s1i = T(0);
             for (int j = L.start[b]; j < L.start[b + 1]; j++) {
                 T cs, sn, w1, w2, w3, soh, ph0;
                 if constexpr (MX) {
-                    float s, u[3];
-                    node32<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
+                    const float s = s32, *u = u32;
                     const float hu = L.hu, ir = s / hu;
-                    const float f0 = ca.f32[3 * j], f1 = ca.f32[3 * j + 1], f2 = ca.f32[3 * j + 2];
+                    const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
+                    const float f0 = fj.x, f1 = fj.y, f2 = fj.z;
                     const float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
                     const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2, ia = rsqrtf(a2), am = a2 * ia;
-                    const float yy = f0 * f0 + f1 * f1 + f2 * f2, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
-                    const float phl = (s * yy / hu - 2.f * uy) / (am + 1.f);  // leaf units
+                    const float yy = fj.w, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
+                    const float phl = __fdividef(s * yy / hu - 2.f * uy, am + 1.f);  // leaf units; am + 1 in [1, 3]
                     float t = ca.kappa_hi * phl;
                     t -= rintf(t);
                     float snf, csf;
                     cis_cycles(t, snf, csf);
                     sn = snf; cs = csf;
-                    const float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
+                    const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
                     w1 = ia; w3 = dn * ia * ia; w2 = w3 * ia;
                     soh = s / (hu * ca.HDf);
                     ph0 = phl * ca.HDf;
                 } else {
-                    double s, u[3], y0[3];
-                    node64<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
-                    center64(ca, L, b, y0);
+                    const double s = s64, *u = u64;
                     const double r = L.h / s;
                     const double yv[3] = {ca.x64[3 * j] - y0[0], ca.x64[3 * j + 1] - y0[1], ca.x64[3 * j + 2] - y0[2]};
                     const double dv[3] = {u[0] - yv[0] / r, u[1] - yv[1] / r, u[2] - yv[2] / r};
@@ -3126,7 +3172,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
 // ============================================================================
 template <int PS, int PA>
 ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec, cudaStream_t s, void *gs, void *bws,
-                          void **G) {
+                          void **G, void *const *Fd, double *dk_partials) {
     const int D = p.D;
     const int N = (int)p.N;
     CommonArgs ca = common_args(p, nrhs);
@@ -3140,9 +3186,16 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         prof_mark(p, s, kStGather, 0);
         for (int d = 3; d <= D; d++)
             if (L[d].nrc) {
-                k_ant<PS, PA, false, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
-                                                                       (const long long *)p.d_ad_start[d], p.d_ad_list[d],
-                                                                       tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
+                const Plan::AntArgs aa = {(const long long *)p.d_ad_start[d], p.d_ad_list[d]};
+                if (Fd)
+                    k_ant<PS, PA, false, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                        ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
+                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials);
+                else
+                    k_ant<PS, PA, false, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                        ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
+                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr);
+                if (Fd) dk_partials += L[d].nrc;
                 prof_mark(p, s, kStCousin, d);
             }
         k_near_adj<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
@@ -3159,9 +3212,16 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         prof_mark(p, s, kStGather, 0);
         for (int d = 3; d <= D; d++)
             if (L[d].nrc) {
-                k_ant<PS, PA, true, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3,
-                                                                      (const long long *)p.d_ad_start[d], p.d_ad_list[d],
-                                                                      tb, gs, d > 3 ? G[d - 1] : nullptr, G[d]);
+                const Plan::AntArgs aa = {(const long long *)p.d_ad_start[d], p.d_ad_list[d]};
+                if (Fd)
+                    k_ant<PS, PA, true, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                        ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
+                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials);
+                else
+                    k_ant<PS, PA, true, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(
+                        ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
+                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr);
+                if (Fd) dk_partials += L[d].nrc;
                 prof_mark(p, s, kStCousin, d);
             }
         k_near_adj32<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)gs, (float2 *)bws);
@@ -3190,59 +3250,35 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
 // k-derivative reductions (forward state in p.ws, adjoint state gs / G)
 // ============================================================================
 template <int PS, int PA>
-ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, void *H, double *partials,
+ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs, void **G, double *partials,
                      long long *nparts) {
     constexpr int P = PS * PA * PA;
     const int D = p.D;
     const int N = (int)p.N;
     CommonArgs ca = common_args(p, nrhs);
     ChebTab tb = cheb_tab(p);
-    LevelArgs L[IFGF_MAXD + 1];
-    for (int d = 3; d <= D; d++) L[d] = level_args(p, d, p.ws.F[d]);
+    LevelArgs LD = level_args(p, D, p.ws.F[D]);
     long long off = 0;
     const bool mx = prec == IFGF_MIXED;
-    if (mx) k_dk_near<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
-    else k_dk_near<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], p.ws.a, gs, partials + off);
+    if (mx) k_dk_near<true><<<nblk(N), kBlock, 0, s>>>(ca, LD, p.ws.a, gs, partials + off);
+    else k_dk_near<false><<<nblk(N), kBlock, 0, s>>>(ca, LD, p.ws.a, gs, partials + off);
     off += nblk(N);
-    // cousin interpolation and propagation of level d: anterpolation with k-derivative
-    // weights into H, then Re <H, F_d>
-    for (int d = 3; d <= D; d++) {
-        if (!L[d].nrc) continue;
-        const long long rows = (long long)nrhs * L[d].nrc * L[d].nfac;
-        if (mx) {
-            k_ant<PS, PA, true, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
-                ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, (const long long *)p.d_ad_start[d], p.d_ad_list[d],
-                tb, gs, d > 3 ? G[d - 1] : nullptr, H);
-            k_dot_re<float2><<<kDkDotBlocks, kBlock, 0, s>>>((const float2 *)H, (const float2 *)p.ws.F[d], rows, P,
-                                                          p.Pstride, partials + off);
-        } else {
-            k_ant<PS, PA, false, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
-                ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, (const long long *)p.d_ad_start[d], p.d_ad_list[d],
-                tb, gs, d > 3 ? G[d - 1] : nullptr, H);
-            k_dot_re<double2><<<kDkDotBlocks, kBlock, 0, s>>>((const double2 *)H, (const double2 *)p.ws.F[d], rows,
-                                                           P, p.Pstride, partials + off);
-        }
-        off += kDkDotBlocks;
-    }
-    {
-        const long long nt = L[D].nrc * P;
-        if (nt) {
-            if (mx) k_dk_leaf<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, L[D], tb, p.ws.a, G[D], partials + off);
-            else k_dk_leaf<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, L[D], tb, p.ws.a, G[D], partials + off);
-            off += nblk(nt);
-        }
+    const long long nt = LD.nrc * P;
+    if (nt) {
+        if (mx) k_dk_leaf<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off);
+        else k_dk_leaf<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off);
+        off += nblk(nt);
     }
     *nparts = off;
     CK(cudaGetLastError());
     return IFGF_OK;
 }
 
-// number of partial sums run_dk_t writes
+// number of partial sums a vector-Jacobian product writes: one per relevant cone (the fused
+// anterpolation), then the near-field and leaf reductions of run_dk_t
 inline long long dk_partials_needed(const Plan &p) {
-    const long long nN = nblk(p.N);
-    long long n = nN * (1 + (p.D - 2));
-    for (int d = p.D; d >= 4; d--) n += nblk(p.lv[d - 1].nrc * p.P);
-    n += nblk(p.lv[p.D].nrc * p.P);
+    long long n = nblk(p.N) + nblk(p.lv[p.D].nrc * p.P);
+    for (int d = 3; d <= p.D; d++) n += p.lv[d].nrc;
     return n;
 }
 

@@ -60,7 +60,6 @@ struct HostLevel {
 // propagation weights depend only on that key — and cut into tiles of up to
 // kTcTile pairs; tiles are ordered by octant so one launch per octant never
 // writes the same parent cone twice.
-constexpr int kDkDotBlocks = 1216;  // blocks of each level's Re <H, F> reduction in the k-gradient (8 per SM)
 constexpr int kTcTile = 64;   // pairs per tile
 constexpr int kCsItem = 64;   // cousin targets per work item of the cone-stationary interpolation (two per lane)
 constexpr int kTcPairs = 32;  // pairs per block of the warp-level (mma.sync) engine: a tile is two blocks
@@ -201,6 +200,12 @@ struct Plan {
     cudaStream_t aux = nullptr;
     static constexpr int kMaxDep = IFGF_MAXD + 3;
     cudaEvent_t dep[kMaxDep] = {};
+
+    // anterpolation list pointers of one level (device)
+    struct AntArgs {
+        const long long *start;
+        const int *list;
+    };
 
     // optional per-launch timing (events recorded on the apply stream; the apply then runs on
     // that stream alone so that every launch has its own interval)

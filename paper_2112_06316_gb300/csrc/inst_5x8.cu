@@ -5,7 +5,7 @@ namespace ifgf {
 template ifgf_status prepare_t<5, 8>(Plan &, cudaStream_t);
 template ifgf_status run_apply_t<5, 8>(Plan &, const void *, void *, int, int, cudaStream_t);
 template ifgf_status run_adjoint_t<5, 8>(Plan &, const void *, void *, int, int, cudaStream_t, void *, void *,
-                                              void **);
-template ifgf_status run_dk_t<5, 8>(Plan &, int, int, cudaStream_t, const void *, void **, void *, double *,
+                                              void **, void *const *, double *);
+template ifgf_status run_dk_t<5, 8>(Plan &, int, int, cudaStream_t, const void *, void **, double *,
                                          long long *);
 }  // namespace ifgf

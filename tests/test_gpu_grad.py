@@ -72,3 +72,29 @@ def test_vjp_density_part_is_the_adjoint(B, orders):
     assert torch.allclose(gs, plan.adjoint(g), rtol=0, atol=0)
     gs32, dk32 = plan.vjp(sig.to(torch.complex64), g.to(torch.complex64))
     assert abs(dk32 - dk) <= 1e-4 * abs(dk)
+
+
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_vjp_from_saved_forward_state(B, dtype):
+    """ifgf_apply_ws leaves the forward state in a caller-owned workspace; ifgf_apply_vjp_ws
+    on it gives the same gradient and k-derivative as ifgf_apply_vjp (which re-runs the
+    forward apply), bit for bit, even after other applies of the plan -- the autograd
+    backward therefore needs no second forward apply.  A workspace that is too small is
+    refused."""
+    s, k = sphere_workload(32, 8, 3.0)
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8, levels=4))
+    plan.set_tc_fill(0.0)
+    sig = torch.from_numpy(random_density(s.N, 2, 6).astype(dtype)).cuda()
+    g = torch.from_numpy(random_density(s.N, 2, 7).astype(dtype)).cuda()
+    y_ref = plan.apply(sig).clone()
+    y, state = plan.apply_with_state(sig)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_ref)
+    gs_ref, dk_ref = plan.vjp(sig, g)
+    plan.apply(torch.from_numpy(random_density(s.N, 2, 8).astype(dtype)).cuda())  # other state in the plan
+    gs, dk = plan.vjp_from_state(state, g)
+    assert torch.equal(gs, gs_ref)
+    assert dk == dk_ref
+    with pytest.raises(B.IFGFError):
+        plan.vjp_from_state(state[: state.numel() // 2], g)
+    plan.close()
