@@ -275,6 +275,21 @@ ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const d
                                int32_t n_beta, double d_grade, int64_t **rowptr_out, int32_t **col_out,
                                double **val_out);
 
+/* ifgf_rp_correction with the quadrature on the current GPU: the host builds the
+ * patch maps, finds the patches within `delta` of every target and their closest
+ * points (as ifgf_rp_correction does), and one CUDA block per (target, patch)
+ * pair evaluates the graded Fejer quadrature, the kernel and the two nodal
+ * contractions in FP64 and subtracts the regular row.  Same arguments, outputs
+ * (host arrays released with ifgf_free), sparsity and entry order as
+ * ifgf_rp_correction; the values agree to FP64 rounding.  Requires m <= 16 and
+ * n_beta <= 64 (IFGF_EUNSUPPORTED otherwise).  Allocates device memory for the
+ * duration of the call; synchronous on `stream`.  Errors as ifgf_rp_correction,
+ * plus IFGF_ECUDA. */
+ifgf_status ifgf_rp_correction_gpu(const double *xyz, const double *normals, const double *weights, int64_t N,
+                                   const int32_t *patch_node, int32_t m, double k, double eta, double delta,
+                                   int32_t n_beta, double d_grade, void *stream, int64_t **rowptr_out,
+                                   int32_t **col_out, double **val_out);
+
 /* Releases an array returned by ifgf_rp_correction (NULL is a no-op). */
 void ifgf_free(void *ptr);
 
@@ -367,16 +382,22 @@ ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill);
  * Errors: IFGF_EINVAL for any other value. */
 ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine);
 
-/* Tunable: engine of the mixed cousin interpolation (the evaluation of each box's
- * cone interpolants at the points of its cousin boxes, Section 3.4).  1 (default)
- * = cone-stationary: plan-time lists give, for every relevant cone segment, the
- * cousin points inside it; a warp stages one cone's values once and interpolates
- * 64 of its points (two per lane), writing each value to its (box, cousin, point)
- * slot, and a second pass adds each point's slots in fixed order.  0 = point-
- * stationary: a warp owns up to 32 points of one box and walks its cousin boxes,
- * staging the cones its lanes fall in.  Plans with N >= 2^24 points always use 0.
- * Errors: IFGF_EINVAL for any other value. */
-ifgf_status ifgf_plan_set_cousin_engine(ifgf_plan *plan, int engine);
+/* Tunable: engine of the mixed CUDA-core interpolation kernels (Section 3.4: each
+ * box's cone interpolants evaluated at the points of its cousin boxes, and at the
+ * parent's cone-segment nodes).  1 (default) = cone-stationary: for the cousin
+ * interpolation, plan-time lists give, for every relevant cone segment, the
+ * cousin points inside it, with their local coordinates and centred factor
+ * computed once in FP64; a warp stages one cone's values once and interpolates 64
+ * of its points (two per lane), writing each value to its (box, cousin, point)
+ * slot, and a second pass adds each point's slots in fixed order.  For the
+ * propagation of levels that do not run on the tensor cores (orders with Pang =
+ * 8), a warp takes up to 64 parent nodes that fall in one child cone and walks
+ * the (parent cone, child box) pairs that share that geometry, staging each
+ * pair's child cone once.  0 = point-stationary: a warp owns up to 32 points
+ * (parent nodes) of one box and walks its cousin boxes (children), staging the
+ * cones its lanes fall in.  Plans with N >= 2^24 points always use 0 for the
+ * cousin interpolation.  Errors: IFGF_EINVAL for any other value. */
+ifgf_status ifgf_plan_set_interp_engine(ifgf_plan *plan, int engine);
 
 /* Plan statistics (host struct filled synchronously). */
 ifgf_status ifgf_plan_info(const ifgf_plan *plan, ifgf_info *out);
@@ -396,7 +417,8 @@ ifgf_status ifgf_plan_set_profiling(ifgf_plan *plan, int enable);
  * entries of kind (0 gather, 1 leaf evaluation, 2 propagation, 3 near field,
  * 4 cousin interpolation, 5 scatter, 6 correction, 7 propagation on the tensor
  * cores: one entry per level, all its octant launches, 8 second pass of the
- * cone-stationary cousin interpolation), level (octree level or 0) and
+ * cone-stationary cousin interpolation, 9 cone-stationary propagation on CUDA
+ * cores: one entry per level), level (octree level or 0) and
  * ms (milliseconds); any output pointer may be NULL.  Waits for the last event.
  * Returns the number of entries (0 if profiling is off), or a negative ifgf_status. */
 int ifgf_plan_stage_times(ifgf_plan *plan, int cap, int *kind, int *level, double *ms);

@@ -79,6 +79,9 @@ _SIGS = [
     ("ifgf_rp_correction", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
                                           ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    ("ifgf_rp_correction_gpu", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int32, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_double, _VP,
+                                              ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
     ("ifgf_free", None, [_VP]),
     ("ifgf_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_far_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
@@ -96,10 +99,10 @@ _SIGS = [
     ("ifgf_group_set_streams", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("ifgf_group_captures", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
-    ("ifgf_plan_set_cousin_engine", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("ifgf_plan_set_interp_engine", ctypes.c_int, [_VP, ctypes.c_int]),
     ("ifgf_group_destroy", None, [_VP]),
 ]
-STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc", "cousin_sum"]
+STAGES = ["gather", "leaf", "prop", "near", "cousin", "scatter", "correction", "prop_tc", "cousin_sum", "prop_cs"]
 
 _lib = None
 
@@ -436,9 +439,9 @@ class Plan:
         """1 = tcgen05 (tensor memory), 0 = warp-level mma.sync."""
         check(lib().ifgf_plan_set_tc_engine(self._h, ctypes.c_int(engine)))
 
-    def set_cousin_engine(self, engine: int):
-        """1 = cone-stationary cousin interpolation (default), 0 = point-stationary."""
-        check(lib().ifgf_plan_set_cousin_engine(self._h, ctypes.c_int(engine)))
+    def set_interp_engine(self, engine: int):
+        """1 = cone-stationary CUDA-core interpolation kernels (default), 0 = point-stationary."""
+        check(lib().ifgf_plan_set_interp_engine(self._h, ctypes.c_int(engine)))
 
     def set_rhs_block(self, rhs_block: int):
         check(lib().ifgf_plan_set_rhs_block(self._h, ctypes.c_int(rhs_block)))
@@ -450,10 +453,11 @@ class Plan:
 
 
 def rp_correction(points, normals, weights, patch_node, m: int, k: float, eta: float | None = None,
-                  delta: float = 0.0, n_beta: int = 48, d_grade: float = 5.0):
-    """Rectangular-polar correction (``ifgf_rp_correction``; host only, no GPU) as numpy CSR
-    (rowptr int64 (N+1,), col int32 (nnz,), val complex128 (nnz,)) over the caller's point order,
-    ready for ``Plan.set_correction``."""
+                  delta: float = 0.0, n_beta: int = 48, d_grade: float = 5.0, device: bool = False, stream=None):
+    """Rectangular-polar correction as numpy CSR (rowptr int64 (N+1,), col int32 (nnz,), val
+    complex128 (nnz,)) over the caller's point order, ready for ``Plan.set_correction``:
+    ``ifgf_rp_correction`` (host only) or, with ``device``, ``ifgf_rp_correction_gpu`` (the
+    quadrature on the current GPU)."""
     x = _host(points, np.float64)
     n = _host(normals, np.float64)
     w = _host(weights, np.float64)
@@ -462,10 +466,14 @@ def rp_correction(points, normals, weights, patch_node, m: int, k: float, eta: f
     if x.shape != (N, 3) or n.shape != (N, 3) or w.shape != (N,) or pn.shape != (N,):
         raise ValueError("points/normals (N, 3), weights and patch_node (N,) expected")
     rp, cl, vl = _VP(), _VP(), _VP()
-    check(lib().ifgf_rp_correction(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(N), pn.ctypes.data,
-                                   ctypes.c_int32(m), ctypes.c_double(k), ctypes.c_double(k if eta is None else eta),
-                                   ctypes.c_double(delta), ctypes.c_int32(n_beta), ctypes.c_double(d_grade),
-                                   ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl)))
+    args = (x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(N), pn.ctypes.data, ctypes.c_int32(m),
+            ctypes.c_double(k), ctypes.c_double(k if eta is None else eta), ctypes.c_double(delta),
+            ctypes.c_int32(n_beta), ctypes.c_double(d_grade))
+    if device:
+        check(lib().ifgf_rp_correction_gpu(*args, _VP(_stream_ptr(stream)), ctypes.byref(rp), ctypes.byref(cl),
+                                           ctypes.byref(vl)))
+    else:
+        check(lib().ifgf_rp_correction(*args, ctypes.byref(rp), ctypes.byref(cl), ctypes.byref(vl)))
     try:
         rowptr = np.ctypeslib.as_array(ctypes.cast(rp, ctypes.POINTER(ctypes.c_int64)), shape=(N + 1,)).copy()
         nnz = int(rowptr[-1])

@@ -191,10 +191,22 @@ void closest_point(const PatchMap &P, const double *x, double &u, double &v, std
 
 }  // namespace
 
-// Builds C (CSR over the caller's point order; values complex128 interleaved).
+// device quadrature of the (target, near patch) pairs (rp_gpu.cu)
+ifgf_status rp_quadrature_device(int m, int nbeta, double k, double eta, double tol, double dgrade,
+                                 const std::vector<double> &coef, const std::vector<double> &orient, const double *xyz,
+                                 const double *nrm, const double *w, int64_t N, const std::vector<int64_t> &node_pt,
+                                 const std::vector<double> &sb, const std::vector<double> &wb,
+                                 const std::vector<double> &lag, const std::vector<int64_t> &pl,
+                                 const std::vector<int> &pq, const std::vector<double> &puv, cudaStream_t s,
+                                 std::vector<double> &out);
+
+// Builds C (CSR over the caller's point order; values complex128 interleaved).  With `device`
+// the host finds the near patches and closest points only, and the quadrature of every pair runs
+// on the current GPU (rp_quadrature_device) with the same formulas.
 static ifgf_status build_rp(const double *xyz, const double *nrm, const double *w, int64_t N, const int32_t *patch_node,
                             int m, double k, double eta, double delta, int nbeta, double dgrade,
-                            int64_t **rowptr_out, int32_t **col_out, double **val_out) {
+                            int64_t **rowptr_out, int32_t **col_out, double **val_out, bool device = false,
+                            cudaStream_t stream = nullptr) {
     const int mm = m * m;
     const int64_t Q = N / mm;
     std::vector<int64_t> node_pt((size_t)N, -1);  // (q, i, j) -> caller index
@@ -302,7 +314,9 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         for (int64_t q = 0; q < Q; q++) clist[fill[cq[q]]++] = q;
     }
 
-    std::vector<std::vector<std::pair<int32_t, cd>>> rows((size_t)N);
+    std::vector<std::vector<std::pair<int32_t, cd>>> rows(device ? 0 : (size_t)N);
+    // device mode: per target, the near patches and their closest-point parameters
+    std::vector<std::vector<std::pair<int64_t, std::pair<double, double>>>> near(device ? (size_t)N : 0);
     int bad = 0;
 #pragma omp parallel
     {
@@ -317,7 +331,8 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         for (int64_t l = 0; l < N; l++) {
             const double *x = xyz + 3 * l;
             const int64_t ql = patch_node[l] / mm;
-            auto &row = rows[l];
+            std::vector<std::pair<int32_t, cd>> dummy;
+            auto &row = device ? dummy : rows[l];
             // candidate patches from the 27 cells around x (ascending patch order)
             cand.clear();
             {
@@ -363,6 +378,10 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
                     pm.eval(ub, vb_, y, yu, yv, tmp);
                     const double dd = std::sqrt((x[0] - y[0]) * (x[0] - y[0]) + (x[1] - y[1]) * (x[1] - y[1]) + (x[2] - y[2]) * (x[2] - y[2]));
                     if (!(dd <= delta)) continue;  // regular interaction (Eq. ReguGridPts)
+                }
+                if (device) {
+                    near[l].push_back({q, {ub, vb_}});
+                    continue;
                 }
                 // graded Fejer nodes (Eq. CovNodesWeights)
                 for (int a = 0; a < nbeta; a++) {
@@ -457,6 +476,51 @@ static ifgf_status build_rp(const double *xyz, const double *nrm, const double *
         set_error("non-finite correction entry (degenerate patch geometry?)");
         return IFGF_EINVAL;
     }
+    if (device) {  // the quadrature on the GPU, then the CSR in target order
+        std::vector<int64_t> pl;
+        std::vector<int> pq;
+        std::vector<double> puv, coef((size_t)Q * 3 * mm), orient((size_t)Q);
+        for (int64_t l = 0; l < N; l++)
+            for (const auto &e : near[l]) {
+                pl.push_back(l);
+                pq.push_back((int)e.first);
+                puv.push_back(e.second.first);
+                puv.push_back(e.second.second);
+            }
+        for (int64_t q = 0; q < Q; q++) {
+            std::copy(P[q].c.begin(), P[q].c.end(), coef.begin() + q * 3 * mm);
+            orient[q] = P[q].orient;
+        }
+        std::vector<double> vals;
+        ifgf_status st = rp_quadrature_device(m, nbeta, k, eta, tol, dgrade, coef, orient, xyz, nrm, w, N, node_pt, sb,
+                                              wb, lag, pl, pq, puv, stream, vals);
+        if (st != IFGF_OK) return st;
+        for (double v : vals)
+            if (!std::isfinite(v)) {
+                set_error("non-finite correction entry (degenerate patch geometry?)");
+                return IFGF_EINVAL;
+            }
+        const size_t nnz = pl.size() * (size_t)mm;
+        int64_t *rowptr = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)N + 1));
+        int32_t *col = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(nnz, 1));
+        double *val = (double *)std::malloc(sizeof(double) * 2 * std::max<size_t>(nnz, 1));
+        if (!rowptr || !col || !val) {
+            std::free(rowptr);
+            std::free(col);
+            std::free(val);
+            set_error("host allocation failed (%zu correction entries)", nnz);
+            return IFGF_ENOMEM;
+        }
+        rowptr[0] = 0;
+        for (int64_t l = 0; l < N; l++) rowptr[l + 1] = rowptr[l] + (int64_t)near[l].size() * mm;
+        for (size_t pr = 0; pr < pl.size(); pr++)
+            for (int t = 0; t < mm; t++) col[pr * mm + t] = (int32_t)node_pt[(size_t)pq[pr] * mm + t];
+        std::memcpy(val, vals.data(), sizeof(double) * 2 * nnz);
+        *rowptr_out = rowptr;
+        *col_out = col;
+        *val_out = val;
+        return IFGF_OK;
+    }
     // CSR straight into the caller's arrays, each row released once copied (bounds the peak)
     int64_t *rowptr = (int64_t *)std::malloc(sizeof(int64_t) * ((size_t)N + 1));
     if (!rowptr) {
@@ -497,10 +561,10 @@ using namespace ifgf;
 
 extern "C" {
 
-ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const double *weights, int64_t N,
-                               const int32_t *patch_node, int32_t m, double k, double eta, double delta,
-                               int32_t n_beta, double d_grade, int64_t **rowptr_out, int32_t **col_out,
-                               double **val_out) {
+static ifgf_status rp_entry(const double *xyz, const double *normals, const double *weights, int64_t N,
+                            const int32_t *patch_node, int32_t m, double k, double eta, double delta, int32_t n_beta,
+                            double d_grade, int64_t **rowptr_out, int32_t **col_out, double **val_out, bool device,
+                            void *stream) {
     clear_error();
     if (!rowptr_out || !col_out || !val_out) {
         set_error("null output pointer");
@@ -522,6 +586,11 @@ ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const d
         set_error("invalid k, eta, delta, n_beta or d_grade");
         return IFGF_EINVAL;
     }
+    if (device && (m > 16 || n_beta > 64)) {
+        set_error("the device quadrature takes m <= 16 and n_beta <= 64 (m = %d, n_beta = %d); use ifgf_rp_correction",
+                  (int)m, (int)n_beta);
+        return IFGF_EUNSUPPORTED;
+    }
     for (int64_t i = 0; i < 3 * N; i++)
         if (!std::isfinite(xyz[i]) || !std::isfinite(normals[i])) {
             set_error("non-finite point or normal");
@@ -529,11 +598,27 @@ ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const d
         }
     try {
         return build_rp(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rowptr_out, col_out,
-                        val_out);
+                        val_out, device, (cudaStream_t)stream);
     } catch (const std::bad_alloc &) {
         set_error("host allocation failed");
         return IFGF_ENOMEM;
     }
+}
+
+ifgf_status ifgf_rp_correction(const double *xyz, const double *normals, const double *weights, int64_t N,
+                               const int32_t *patch_node, int32_t m, double k, double eta, double delta,
+                               int32_t n_beta, double d_grade, int64_t **rowptr_out, int32_t **col_out,
+                               double **val_out) {
+    return rp_entry(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rowptr_out, col_out,
+                    val_out, false, nullptr);
+}
+
+ifgf_status ifgf_rp_correction_gpu(const double *xyz, const double *normals, const double *weights, int64_t N,
+                                   const int32_t *patch_node, int32_t m, double k, double eta, double delta,
+                                   int32_t n_beta, double d_grade, void *stream, int64_t **rowptr_out,
+                                   int32_t **col_out, double **val_out) {
+    return rp_entry(xyz, normals, weights, N, patch_node, m, k, eta, delta, n_beta, d_grade, rowptr_out, col_out,
+                    val_out, true, stream);
 }
 
 void ifgf_free(void *ptr) { std::free(ptr); }
