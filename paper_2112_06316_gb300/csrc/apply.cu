@@ -147,6 +147,21 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     UP(p.d_leaf_of, p.leaf_of);
     UP(p.d_nb_start, p.nb_start);
     UP(p.d_nb_list, p.nb_list);
+    {
+        const HostLevel &L = p.lv[D];
+        std::vector<int4> ch;
+        for (int b = 0; b < L.nbox; b++) {
+            const int n = L.start[b + 1] - L.start[b];
+            const int nch = (n + 63) / 64;
+            for (int k = 0; k < nch; k++) {
+                const int s0 = L.start[b] + (int)((int64_t)n * k / nch);
+                const int s1 = L.start[b] + (int)((int64_t)n * (k + 1) / nch);
+                ch.push_back(make_int4(b, s0, s1 - s0, 0));
+            }
+        }
+        p.nnchunk = (int)ch.size();
+        UP(p.d_nchunk, ch);
+    }
     for (int d = 3; d <= D; d++) {
         const HostLevel &L = p.lv[d];
         DevLevel &dl = p.dl[d];
@@ -355,7 +370,7 @@ size_t workspace_layout(const Plan &p, int nrhs, int prec, WorkspaceLayout &lay)
         off += al(cb * (size_t)nrhs * p.lv[d].nrc * p.lv[d].nfac * p.Pstride);
     }
     lay.pv = off;
-    if (prec == IFGF_MIXED && p.cs_ok && p.cousin_engine == 1) off += al(8 * (size_t)nrhs * p.cs_max_entries);
+    if (prec == IFGF_MIXED && p.cs_ok && p.interp_engine == 1) off += al(8 * (size_t)nrhs * p.cs_max_entries);
     lay.total = off;
     return off;
 }

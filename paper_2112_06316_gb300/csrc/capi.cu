@@ -290,14 +290,14 @@ ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine) {
     return IFGF_OK;
 }
 
-ifgf_status ifgf_plan_set_cousin_engine(ifgf_plan *plan, int engine) {
+ifgf_status ifgf_plan_set_interp_engine(ifgf_plan *plan, int engine) {
     clear_error();
     if (!plan || (engine != 0 && engine != 1)) {
-        set_error("engine must be 0 (target-stationary) or 1 (cone-stationary)");
+        set_error("engine must be 0 (point-stationary) or 1 (cone-stationary)");
         return IFGF_EINVAL;
     }
-    if (plan->p.cousin_engine != engine) plan->p.gen++;
-    plan->p.cousin_engine = engine;
+    if (plan->p.interp_engine != engine) plan->p.gen++;
+    plan->p.interp_engine = engine;
     return IFGF_OK;
 }
 

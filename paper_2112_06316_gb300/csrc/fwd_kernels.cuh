@@ -620,56 +620,89 @@ __device__ __forceinline__ void prop_add(CAcc &a0, CAcc &a1, bool csplit, bool p
     }
 }
 
-// K4 (mixed), RB right-hand sides per pass
+// K4 (mixed), RB right-hand sides per pass.  One warp per chunk of at most 64 targets of one
+// leaf box, two per lane: every lane walks the same neighbour boxes and sources (no divergence),
+// each source record (a 32-byte broadcast load) feeds two pairs, and the two independent sums
+// keep the FMA and MUFU pipes busy while the next record is in flight.  Per target the sources
+// are summed in neighbour-list order, as in the oracle's near-field stage.
+constexpr int kNearWarps = 4;
+
+// contribution of source j (offset fj, normal nj from the target's box offset D) to one target:
+// K = e^{ikR}/(4 pi R) [ dn_u / (r^2 HD) - i (k dn_u / r + eta) ],  R = r HD, times `keep` (1, or 0
+// for the target itself and for coincident points: no branch, r^2 floored so that the zeroed
+// terms stay finite)
+__device__ __forceinline__ void near_pair32(const CommonArgs &ca, float D0, float D1, float D2, const float4 &fj,
+                                            const float4 &nj, float c4, float iHD, float tolu2, bool keep,
+                                            float &Kr, float &Ki) {
+    const float d0 = D0 - fj.x, d1 = D1 - fj.y, d2 = D2 - fj.z;
+    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const bool k2 = keep && r2 >= tolu2;
+    const float ir = rsqrtf(fmaxf(r2, 1e-30f));
+    const float r = r2 * ir;
+    float t = ca.kappa_hi * r;
+    t -= rintf(t);
+    float sn, cs;
+    cis_cycles(t, sn, cs);
+    const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
+    const float amp = k2 ? c4 * ir : 0.f;
+    const float A = amp * dn * ir * ir * iHD, Bv = -amp * (ca.kf * dn * ir + ca.etaf);
+    Kr = cs * A - sn * Bv;
+    Ki = sn * A + cs * Bv;
+}
+
 template <int RB>
-__global__ void __launch_bounds__(kBlock) k_near32(CommonArgs ca, LevelArgs L, const float2 *__restrict__ a,
-                                                   float2 *__restrict__ u) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ca.N) return;
-    int b = ca.leaf_of[i];
+__global__ void __launch_bounds__(kNearWarps * 32) k_near32(CommonArgs ca, LevelArgs L, const int4 *__restrict__ chunks,
+                                                           int nchunk, const float2 *__restrict__ a,
+                                                           float2 *__restrict__ u) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kNearWarps + warp;
+    if (ch >= nchunk) return;  // warp-uniform
+    const int4 cw = chunks[ch];
+    const int b = cw.x;
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
     const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
     const float4 *pn = ca.pn32;
-    const float4 fi = __ldg(pn + 2 * i);
-    const float kf = ca.kf, etaf = ca.etaf, kap = ca.kappa_hi;
+    const float4 f0 = __ldg(pn + 2 * i0), f1 = __ldg(pn + 2 * i1);
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
-    const float tolu = (float)(ca.tol / ca.HD);
+    const float tolu = (float)(ca.tol / ca.HD), tolu2 = tolu * tolu;
+    const int nb0 = ca.nb_start[b], nb1 = ca.nb_start[b + 1];
     for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
-        PAcc acc[RB];
+        PAcc A0[RB], A1[RB];
 #pragma unroll
-        for (int qq = 0; qq < RB; qq++) acc[qq].zero();
-        for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
-            int c = ca.nb_list[nb];
-            const float D0 = (float)(bi0 - L.ijk[3 * c]) + fi.x, D1 = (float)(bi1 - L.ijk[3 * c + 1]) + fi.y,
-                        D2 = (float)(bi2 - L.ijk[3 * c + 2]) + fi.z;
-            for (int j = L.start[c]; j < L.start[c + 1]; j++) {
-                if (j == i) continue;
+        for (int qq = 0; qq < RB; qq++) {
+            A0[qq].zero();
+            A1[qq].zero();
+        }
+        for (int nb = nb0; nb < nb1; nb++) {
+            const int c = ca.nb_list[nb];
+            const float E0 = (float)(bi0 - L.ijk[3 * c]), E1 = (float)(bi1 - L.ijk[3 * c + 1]),
+                        E2 = (float)(bi2 - L.ijk[3 * c + 2]);
+            const float D00 = E0 + f0.x, D01 = E1 + f0.y, D02 = E2 + f0.z;
+            const float D10 = E0 + f1.x, D11 = E1 + f1.y, D12 = E2 + f1.z;
+            const int j1 = L.start[c + 1];
+#pragma unroll 2
+            for (int j = L.start[c]; j < j1; j++) {
                 const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
-                float d0 = D0 - fj.x, d1 = D1 - fj.y, d2 = D2 - fj.z;
-                float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                float ir = rsqrtf(r2);
-                float r = r2 * ir;
-                if (!(r >= tolu)) continue;
-                float t = kap * r;
-                t -= rintf(t);
-                float sn, cs;
-                cis_cycles(t, sn, cs);
-                float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
-                // K = e^{ikR}/(4 pi R) [ dn_u / (r^2 HD) - i (k dn_u / r + eta) ],  R = r HD
-                float A = dn * ir * ir * iHD, B = -(kf * dn * ir + etaf);
-                float amp = c4 * ir;
-                float Kr = amp * (cs * A - sn * B), Ki = amp * (sn * A + cs * B);
+                float K0r, K0i, K1r, K1i;
+                near_pair32(ca, D00, D01, D02, fj, nj, c4, iHD, tolu2, j != i0, K0r, K0i);
+                near_pair32(ca, D10, D11, D12, fj, nj, c4, iHD, tolu2, j != i1, K1r, K1i);
 #pragma unroll
                 for (int qq = 0; qq < RB; qq++) {
                     if (RB == 1 || q0 + qq < ca.nrhs) {
-                        float2 aj = a[(long long)(q0 + qq) * ca.N + j];
-                        acc[qq].add(Kr * aj.x - Ki * aj.y, Kr * aj.y + Ki * aj.x);
+                        const float2 aj = a[(long long)(q0 + qq) * ca.N + j];
+                        A0[qq].add(K0r * aj.x - K0i * aj.y, K0r * aj.y + K0i * aj.x);
+                        A1[qq].add(K1r * aj.x - K1i * aj.y, K1r * aj.y + K1i * aj.x);
                     }
                 }
             }
         }
 #pragma unroll
         for (int qq = 0; qq < RB; qq++)
-            if (RB == 1 || q0 + qq < ca.nrhs) u[(long long)(q0 + qq) * ca.N + i] = acc[qq].get();
+            if (RB == 1 || q0 + qq < ca.nrhs) {
+                if (v0) u[(long long)(q0 + qq) * ca.N + i0] = A0[qq].get();
+                if (v1) u[(long long)(q0 + qq) * ca.N + i1] = A1[qq].get();
+            }
     }
 }
 
@@ -923,10 +956,11 @@ __device__ __forceinline__ void cs_load(const ChebTab &tb, const float4 *__restr
     g.dest = __float_as_int(b.y);
 }
 
-// interpolation of one factor's node values f (shared memory) for two targets at once
-template <int PS, int PA>
-__device__ __forceinline__ void cs_interp2(const float2 *f, const CsTgt<PS, PA> &g0, const CsTgt<PS, PA> &g1,
-                                           unsigned long long &v0, unsigned long long &v1) {
+// interpolation of one factor's node values f (shared memory) for two targets at once; W holds a
+// target's packed angular weights lt2, lp2 and radial weights Ls
+template <int PS, int PA, typename W>
+__device__ __forceinline__ void cs_interp2(const float2 *f, const W &g0, const W &g1, unsigned long long &v0,
+                                           unsigned long long &v1) {
     v0 = 0ull;
     v1 = 0ull;
 #pragma unroll 1
@@ -2756,6 +2790,145 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     }
 }
 
+// K3 (mixed), cone-stationary, on the grouping of the tensor-core tables (Pang = 8): within a
+// group (child octant, parent cone id) the parent nodes are ordered by the child cone they fall
+// in, and every (parent cone, child box) pair of a tile maps the same nodes to the same child
+// cone id.  One warp per item (<= 64 nodes of one child cone, two per lane, and one tile of <= 64
+// pairs): the nodes' geometry and basis weights are computed once, then for every pair the warp
+// stages that pair's child cone (double-buffered cp.async) and interpolates it for its nodes with
+// broadcast shared reads, times the centred-factor ratio, adding into the parent cone values.
+// The caller zeroes F_{d-1} and launches one octant at a time, so each parent value has one
+// writer per launch and the result is deterministic.
+template <int PS, int PA>
+struct PcNode {
+    unsigned long long lt2[PA], lp2[PA];
+    float Ls[PS];
+    float rr, ri, g1, irs;  // ratio e^{ik(r_c - r_p)} r_p / r_c, r_p / r_c, 1 / r_c (absolute)
+    int node;               // parent node index, -1 for an idle slot
+};
+
+template <int PS>
+__device__ __forceinline__ void pc_node(const CommonArgs &ca, const LevelArgs &C, const LevelArgs &Pl,
+                                        const ChebTab &tb, int gamma, int node, float o0, float o1, float o2,
+                                        PcNode<PS, 8> &g) {
+    g.node = node;
+    float nv[3], rp, rcv, t3[3];
+    tc_child_cone<PS>(C, Pl, tb, gamma, node >= 0 ? node : 0, o0, o1, o2, nv, rp, rcv, t3);
+    const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+    float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
+    t -= rintf(t);
+    float sn, cs;
+    cis_cycles(t, sn, cs);
+    g.g1 = rp / rcv;
+    g.rr = cs * g.g1;
+    g.ri = sn * g.g1;
+    g.irs = 1.f / (rcv * ca.HDf);
+    float Lt[8], Lp[8];
+    lagrange<PS, float>(t3[0], tb.fxs, tb.fcs, g.Ls);
+    lagrange<8, float>(t3[1], tb.fxa, tb.fca, Lt);
+    lagrange<8, float>(t3[2], tb.fxa, tb.fca, Lp);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        g.lt2[k] = f2pack(Lt[k], Lt[k]);
+        g.lp2[k] = f2pack(Lp[k], Lp[k]);
+    }
+}
+
+// add one parent node's share from one child (interpolated factor values v, and w for a split
+// child) into the parent cone values at FP[base + fac * pstride + node]: with both levels split,
+// each factor re-centred with its own power of r (ratio g1 for W2, ratio for W13); a split child
+// into a combined parent through the child's field (W2 / r_c + W13); otherwise the ratio
+template <bool CSPLIT, bool PSPLIT, typename N>
+__device__ __forceinline__ void pc_store(float2 *FP, long long base, int pstride, const N &g,
+                                         unsigned long long v, unsigned long long w) {
+    if (g.node < 0) return;
+    float vr, vi, wr, wi;
+    f2unpack(v, vr, vi);
+    f2unpack(w, wr, wi);
+    if (CSPLIT && PSPLIT) {
+        const float r2r = g.rr * g.g1, r2i = g.ri * g.g1;
+        atomicAdd(FP + base + g.node, make_float2(vr * r2r - vi * r2i, vr * r2i + vi * r2r));
+        atomicAdd(FP + base + pstride + g.node, make_float2(wr * g.rr - wi * g.ri, wr * g.ri + wi * g.rr));
+    } else {
+        if (CSPLIT) {
+            vr = vr * g.irs + wr;
+            vi = vi * g.irs + wi;
+        }
+        atomicAdd(FP + base + g.node, make_float2(vr * g.rr - vi * g.ri, vr * g.ri + vi * g.rr));
+    }
+}
+
+template <int PS, bool CSPLIT, bool PSPLIT>
+__global__ void __launch_bounds__(kCsWarps * 32) k_prop_cs(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
+                                                           TcLevel T, int item0, int nitem) {
+    constexpr int P = PS * 64, PST = P, NF = CSPLIT ? 2 : 1;
+    constexpr int NV4 = NF * PST / 2;  // float4 of one child cone's values (all factors, contiguous)
+    __shared__ __align__(16) float2 sF[kCsWarps][2][NF * PST];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * kCsWarps + warp;
+    if (it >= nitem) return;  // warp-uniform: no block-wide barrier below
+    const int4 w = T.cs_items[item0 + it];
+    const int tile = w.x, row0 = w.y, rows = w.z, slot = w.w;
+    const int g = T.tile_group[tile];
+    const int gamma = T.grp_gamma[g], pb = T.grp_pb[g], cb0 = T.grp_cb[g];
+    const int cc = T.grp_cones[16 * g + slot];
+    const int ts = T.tile_start[tile], np = T.tile_count[tile];
+    // child-centre offset from the parent centre (leaf units; exact: integers times powers of two)
+    const float o0 = (C.ijk[3 * cb0] + 0.5f) * C.scale - (Pl.ijk[3 * pb] + 0.5f) * Pl.scale;
+    const float o1 = (C.ijk[3 * cb0 + 1] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 1] + 0.5f) * Pl.scale;
+    const float o2 = (C.ijk[3 * cb0 + 2] + 0.5f) * C.scale - (Pl.ijk[3 * pb + 2] + 0.5f) * Pl.scale;
+    // every lane looks up the child cone storage index of pairs lane and lane + 32
+    int crc_a = -1, crc_b = -1, rcp_a = -1, rcp_b = -1;
+    if (lane < np) {
+        crc_a = C.cone_map[(long long)T.pair_cb[ts + lane] * C.ncone + cc];
+        rcp_a = T.pair_rcp[ts + lane];
+    }
+    if (lane + 32 < np) {
+        crc_b = C.cone_map[(long long)T.pair_cb[ts + lane + 32] * C.ncone + cc];
+        rcp_b = T.pair_rcp[ts + lane + 32];
+    }
+    PcNode<PS, 8> n0, n1;
+    pc_node<PS>(ca, C, Pl, tb, gamma, lane < rows ? (int)T.grp_perm[(long long)g * P + row0 + lane] : -1, o0, o1, o2,
+                n0);
+    pc_node<PS>(ca, C, Pl, tb, gamma, lane + 32 < rows ? (int)T.grp_perm[(long long)g * P + row0 + lane + 32] : -1,
+                o0, o1, o2, n1);
+    const float2 *FC = (const float2 *)C.F;
+    float2 *FP = (float2 *)Pl.F;
+    for (int q = 0; q < ca.nrhs; q++) {
+        auto crc_of = [&](int pr) { return __shfl_sync(0xffffffffu, pr < 32 ? crc_a : crc_b, pr & 31); };
+        auto rcp_of = [&](int pr) { return __shfl_sync(0xffffffffu, pr < 32 ? rcp_a : rcp_b, pr & 31); };
+        auto stage = [&](int pr, int bsel) {
+            const int crc = crc_of(pr);
+            if (crc < 0) return;
+            const float4 *src = reinterpret_cast<const float4 *>(FC + ((long long)q * C.nrc + crc) * NF * PST);
+            float4 *dst = reinterpret_cast<float4 *>(sF[warp][bsel]);
+            for (int v = lane; v < NV4; v += 32) cp_async16(dst + v, src + v);
+        };
+        __syncwarp();  // the previous right-hand side's readers are done
+        stage(0, 0);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        for (int pr = 0; pr < np; pr++) {
+            const int bsel = pr & 1;
+            if (pr + 1 < np) stage(pr + 1, bsel ^ 1);  // the buffer last read at pair pr - 1
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // pair pr's copy has landed
+            __syncwarp();
+            const int crc = crc_of(pr), rcp = rcp_of(pr);
+            if (crc < 0) atomicAdd(ca.missed, 1ULL);  // warp-uniform
+            else {
+                const float2 *buf = sF[warp][bsel];
+                unsigned long long v0, v1, w0 = 0ull, w1 = 0ull;
+                cs_interp2<PS, 8>(buf, n0, n1, v0, v1);
+                if constexpr (CSPLIT) cs_interp2<PS, 8>(buf + PST, n0, n1, w0, w1);
+                pc_store<CSPLIT, PSPLIT>(FP, ((long long)q * Pl.nrc + rcp) * Pl.nfac * ca.Pstride, ca.Pstride, n0, v0, w0);
+                pc_store<CSPLIT, PSPLIT>(FP, ((long long)q * Pl.nrc + rcp) * Pl.nfac * ca.Pstride, ca.Pstride, n1, v1, w1);
+            }
+            __syncwarp();  // buffer bsel may be overwritten by the stage of pair pr + 2
+        }
+        cp_async_wait_all();
+    }
+}
+
 // Once per plan: for every group key (child octant, parent cone), the child cone of each of the P
 // parent nodes (FP32, the classification the propagation kernels use), the distinct cones in
 // ascending order (at most 16; nodes of further cones go last and are counted as missed when
@@ -2940,6 +3113,35 @@ ifgf_status t5_prepare(Plan &p, cudaStream_t s) {
         T.oct_item_start[8] = (int)items.size();
         T.nitems = (int)items.size();
         T.items_ok = ok;
+        {  // the cone-stationary CUDA-core engine: runs of one child cone in chunks of <= 64 nodes
+            std::vector<int4> cs;
+            for (int o = 0; o < 8; o++) {
+                T.oct_cs_start[o] = (int)cs.size();
+                for (int t = T.oct_tile_start[o]; t < T.oct_tile_start[o + 1]; t++) {
+                    const int g = tg[t];
+                    int off = 0;
+                    for (int j = 0; j < nc[g]; j++) {
+                        const int n = cnt[17 * (size_t)g + j];
+                        for (int r = 0; r < n; r += 64) cs.push_back(make_int4(t, off + r, std::min(64, n - r), j));
+                        off += n;
+                    }
+                }
+            }
+            T.oct_cs_start[8] = (int)cs.size();
+            T.ncs_items = (int)cs.size();
+            void *ptr = nullptr;
+            e = cudaMalloc(&ptr, sizeof(int4) * (cs.size() + 1));
+            if (e == cudaSuccess && !cs.empty())
+                e = cudaMemcpy(ptr, cs.data(), sizeof(int4) * cs.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                if (ptr) cudaFree(ptr);
+                set_error("propagation items: %s", cudaGetErrorString(e));
+                return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
+            }
+            p.allocs.push_back(ptr);
+            p.device_bytes += (int64_t)(sizeof(int4) * (cs.size() + 1));
+            T.cs_items = (int4 *)ptr;
+        }
         // item headers and child-cone storage indices (host copies of the tile and group tables)
         std::vector<int> ts(T.ntiles), tcn(T.ntiles), gg(T.ngroups), gpb(T.ngroups), gcb(T.ngroups),
             gcones(16 * (size_t)T.ngroups), pcb;
@@ -3080,7 +3282,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         float2 *u32 = (float2 *)p.ws.u;
         auto cousin = [&](int d) {
             const int nch = p.ncchunk[d];
-            if (p.cs_ok && p.cousin_engine == 1) {
+            if (p.cs_ok && p.interp_engine == 1) {
                 const int ni = p.ncs_item[d];
                 const long long stride = p.cs_max_entries;
                 float2 *pv = (float2 *)p.ws.pv;
@@ -3107,8 +3309,11 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         k_gather<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w32, (const float2 *)sigma, (float2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
         fork(0);
-        if (rb1) k_near32<1><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const float2 *)p.ws.a, u32);
-        else k_near32<kRB><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const float2 *)p.ws.a, u32);
+        {
+            const unsigned gn = (unsigned)((p.nnchunk + kNearWarps - 1) / kNearWarps);
+            if (rb1) k_near32<1><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
+            else k_near32<kRB><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
+        }
         prof_mark(p, sb, kStNear, D);
         if (L[D].nrc) {
             const unsigned g = nblk(L[D].nrc * P);
@@ -3146,6 +3351,24 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                         }
                     }
                     prof_mark(p, s, kStPropTc, d - 1);
+                }
+            } else if (L[d - 1].nrc && PA == 8 && p.use_tc && p.tc[d].items_ok && p.interp_engine == 1) {
+                if constexpr (PA == 8) {
+                    const size_t bytes = sizeof(float2) * (size_t)nrhs * L[d - 1].nrc * L[d - 1].nfac * p.Pstride;
+                    CK(cudaMemsetAsync(L[d - 1].F, 0, bytes, s));
+                    const TcLevel &T = p.tc[d];
+                    for (int o = 0; o < 8; o++) {
+                        const int i0 = T.oct_cs_start[o], ni = T.oct_cs_start[o + 1] - i0;
+                        if (ni <= 0) continue;
+                        const unsigned gc = (unsigned)((ni + kCsWarps - 1) / kCsWarps);
+                        if (L[d].split && L[d - 1].split)
+                            k_prop_cs<PS, true, true><<<gc, kCsWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                        else if (L[d].split)
+                            k_prop_cs<PS, true, false><<<gc, kCsWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                        else
+                            k_prop_cs<PS, false, false><<<gc, kCsWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                    }
+                    prof_mark(p, s, kStPropCs, d - 1);
                 }
             } else if (L[d - 1].nrc) {
                 const long long nw = L[d - 1].nrc * (long long)((P + 31) / 32);

@@ -86,6 +86,11 @@ struct TcLevel {
     int *item_crc = nullptr;
     int oct_item_start[9] = {};
     bool items_ok = false;  // every group has at most 16 child cones
+    // work items of the cone-stationary CUDA-core propagation, ordered by octant: (tile, first row
+    // in the group's node order, rows <= 64, cone slot) -- one warp each
+    int4 *cs_items = nullptr;
+    int ncs_items = 0;
+    int oct_cs_start[9] = {};
 };
 
 // Device arrays of one level.
@@ -143,7 +148,10 @@ struct Plan {
     // (target, cousin) pairs per level): work items (relevant cone, first entry, count <= 64),
     // packed entries and per-box offsets of the value buffer (HostLevel::cs_*)
     bool cs_ok = false;
-    int cousin_engine = 1;  // 1 = cone-stationary when the lists exist, 0 = target-stationary (k_cousin_w)
+    // CUDA-core interpolation kernels: 1 = cone-stationary (cousin lists; grouped propagation where
+    // the tensor-core tables exist and the tensor cores do not take the level), 0 = point-stationary
+    // (k_cousin_w, k_prop_w)
+    int interp_engine = 1;
     int4 *d_cs_item[IFGF_MAXD + 1] = {};
     int ncs_item[IFGF_MAXD + 1] = {};
     // per entry, FP64-computed once per plan: (local coordinates t_s, t_theta, t_phi, Re E) and
@@ -153,6 +161,10 @@ struct Plan {
     int *d_cs_pvoff[IFGF_MAXD + 1] = {};
     int64_t cs_max_entries = 0;  // largest per-level pair count (size of the value buffer per rhs)
     int *d_nb_start = nullptr, *d_nb_list = nullptr;
+    // near-field work chunks: (leaf box, first sorted target, count <= 64, 0), the targets of every
+    // leaf box in near-equal runs of at most 64
+    int4 *d_nchunk = nullptr;
+    int nnchunk = 0;
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
     float4 *d_pn32 = nullptr;                                      // sorted, (offset, |offset|^2), (normal, 0)
@@ -221,7 +233,8 @@ struct Plan {
 enum StageKind {
     kStGather = 0, kStLeaf = 1, kStProp = 2, kStNear = 3, kStCousin = 4, kStScatter = 5, kStCorr = 6,
     kStPropTc = 7,    // propagation on the tensor cores
-    kStCousinSum = 8  // second pass of the cone-stationary cousin interpolation
+    kStCousinSum = 8,  // second pass of the cone-stationary cousin interpolation
+    kStPropCs = 9      // cone-stationary propagation on CUDA cores (all its octant launches)
 };
 
 inline void prof_begin(Plan &p, cudaStream_t s) {

@@ -273,20 +273,26 @@ def test_bench_configuration_full_size_vs_oracle(lib, oracle_lib):
 
 
 @pytest.mark.parametrize("fm", [0, 1, 2])
-def test_cousin_engines(lib, oracle_lib, fm):
-    """Both mixed cousin-interpolation engines (cone-stationary lists, the default, and the
-    point-stationary kernel kept for plans of 2^24 points or more) against the oracle, with
-    split, combined and mixed factor levels, three right-hand sides; the two agree to FP32
-    rounding.  The cone-stationary engine's second pass sums in fixed order: bitwise
-    reproducible."""
+def test_interp_engines(lib, oracle_lib, fm):
+    """Both mixed CUDA-core interpolation engines (cone-stationary: cousin lists and grouped
+    propagation, the default; point-stationary: kept for plans of 2^24 points or more) against
+    the oracle, with split, combined and mixed factor levels, three right-hand sides, the
+    propagation on CUDA cores (tensor-core fill threshold above 1); the two agree to FP32
+    rounding.  Both are bitwise reproducible (fixed summation order)."""
     s, k = sphere_workload(64, 8, 6.0)
     sig = random_density(s.N, 3, 41)
     prm = dict(levels=5, Ps=5, Pang=8, factor_mode=fm)
     ref, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k, identity_coef=0.5, **prm), sig)
     plan = lib.Plan(s.points, s.normals, s.weights, lib.Params(k=k, **prm))
+    plan.set_tc_fill(2.0)
     y1 = gpu_apply(plan, sig, np.complex64)
     assert np.array_equal(y1, gpu_apply(plan, sig, np.complex64))
-    plan.set_cousin_engine(0)
+    plan.set_profiling(True)
+    gpu_apply(plan, sig, np.complex64)
+    kinds = [kd for kd, _, _ in plan.stage_times()]
+    plan.set_profiling(False)
+    assert "prop_cs" in kinds and "cousin_sum" in kinds, kinds
+    plan.set_interp_engine(0)
     y0 = gpu_apply(plan, sig, np.complex64)
     assert plan.missed_lookups() == 0
     check(y1, ref, 1e-5, "cone-stationary")
