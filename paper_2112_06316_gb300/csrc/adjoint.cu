@@ -187,7 +187,10 @@ ifgf_status vjp_core(Plan &p, const Workspace &fwd, const void *g_dev, void *gsi
     double *partials = nullptr;
     long long need = 0;
     if (dk_host) {
-        need = (p.N + 127) / 128 + (p.lv[p.D].nrc * p.P + 127) / 128;
+        // per relevant cone (fused anterpolation), then the near field and the leaf: FP64 by their own
+        // passes (one block per 128 targets / nodes), mixed inside the adjoint kernels (one block per
+        // 128 sources / per four leaf chunks)
+        need = (p.N + 127) / 128 + std::max<long long>((p.lv[p.D].nrc * p.P + 127) / 128, (p.ncchunk[p.D] + 3) / 4);
         for (int d = 3; d <= p.D; d++) need += p.lv[d].nrc;
         const size_t bytes = sizeof(double) * (need + 1);
         if (bytes > p.dk_ws_bytes) {
@@ -203,19 +206,26 @@ ifgf_status vjp_core(Plan &p, const Workspace &fwd, const void *g_dev, void *gsi
     void *gs = nullptr, *G[IFGF_MAXD + 1] = {};
     void *Fd[IFGF_MAXD + 1] = {};
     for (int d = 3; d <= p.D; d++) Fd[d] = fwd.F[d];
+    const Workspace saved = p.ws;
+    p.ws = fwd;  // the k-derivative reads w sigma and the cone values of the forward state
     ifgf_status st = adjoint_core(p, g_dev, gsigma_dev, nrhs, prec, s, &gs, G, dk_host ? Fd : nullptr, partials);
+    p.ws = saved;
     if (st != IFGF_OK) return st;
     st = apply_correction_adjoint(p, g_dev, gsigma_dev, nrhs, prec, s);
     if (st != IFGF_OK || !dk_host) return st;
-    long long ncone = 0;
-    for (int d = 3; d <= p.D; d++) ncone += p.lv[d].nrc;
     long long np = 0;
-    const Workspace saved = p.ws;
-    p.ws = fwd;  // run_dk reads w sigma and F_D of the forward state
-    st = run_dk(p, nrhs, prec, s, gs, G, partials + ncone, &np);
-    p.ws = saved;
-    if (st != IFGF_OK) return st;
-    np += ncone;
+    for (int d = 3; d <= p.D; d++) np += p.lv[d].nrc;
+    if (prec == IFGF_MIXED) {  // near field and leaf reduced inside the adjoint kernels
+        np += (p.N + 127) / 128;
+        if (p.lv[p.D].nrc) np += (p.ncchunk[p.D] + 3) / 4;
+    } else {
+        long long nd = 0;
+        p.ws = fwd;
+        st = run_dk(p, nrhs, prec, s, gs, G, partials + np, &nd);
+        p.ws = saved;
+        if (st != IFGF_OK) return st;
+        np += nd;
+    }
     std::vector<double> h(np > 0 ? np : 1, 0.0);
     if (np > 0) {
         cudaError_t e = cudaMemcpyAsync(h.data(), partials, sizeof(double) * np, cudaMemcpyDeviceToHost, s);

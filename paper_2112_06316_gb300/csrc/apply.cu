@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(128) k_cousin_geo(int nitems, const int4 *__re
 
 ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const double *w, cudaStream_t s) {
     CK(cudaGetDevice(&p.device));
+    CK(cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device));
     const int64_t N = p.N;
     const int D = p.D;
     std::vector<double> x64(3 * N), n64(3 * N), w64(N);

@@ -281,8 +281,8 @@ ifgf_status ifgf_plan_set_tc_fill(ifgf_plan *plan, double min_fill) {
 
 ifgf_status ifgf_plan_set_tc_engine(ifgf_plan *plan, int engine) {
     clear_error();
-    if (!plan || (engine != 0 && engine != 1)) {
-        set_error("engine must be 0 (mma.sync) or 1 (tcgen05)");
+    if (!plan || engine < 0 || engine > 2) {
+        set_error("engine must be 0 (mma.sync), 1 (tcgen05, angular contraction) or 2 (tcgen05, c contraction)");
         return IFGF_EINVAL;
     }
     if (plan->p.tc_engine != engine) plan->p.gen++;

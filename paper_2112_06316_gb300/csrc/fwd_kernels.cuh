@@ -1693,27 +1693,30 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
 // and loads its cone values once into the warp's shared-memory slots; the warp
 // then walks the 32 nodes with broadcast loads, every lane evaluating
 // conj(W(x_node, y_j)) G for its source.
-template <int PS, int PA, bool SPLIT>
+template <int PS, int PA, bool SPLIT, bool DK>
 __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, const int4 *__restrict__ chunks,
                                                     int nchunk, ChebTab tb, const float2 *__restrict__ G,
-                                                    float2 *__restrict__ bo) {
+                                                    float2 *__restrict__ bo, const float2 *__restrict__ a_fwd,
+                                                    double *dk_partials) {
     constexpr int P = PS * PA * PA;
     __shared__ float4 s_dir[4][32];  // (u0, u1, u2, 1/r) per node, r in leaf units
     __shared__ float4 s_g[4][32];    // (G0, G1) per node; G1 = (s/h, 0) when the factor is combined
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ch = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (ch >= nchunk) return;  // warp-uniform
-    const int4 cw = chunks[ch];
+    double dk = 0.0;  // DK: this thread's share of the leaf part of Re <g, dA/dk sigma>
+    const bool live = ch < nchunk;  // warp-uniform
+    const int4 cw = chunks[live ? ch : 0];
     const int b = cw.x;
-    const bool act = lane < cw.z;
+    const bool act = live && lane < cw.z;
     const int j = cw.y + (act ? lane : 0);
     const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
     const float hu = L.hu, kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, hd = ca.HDf;
     const float yy = fj.w;  // |f|^2
     const int r0 = L.rc_start[b], r1 = L.rc_start[b + 1];
-    for (int q = 0; q < ca.nrhs; q++) {
-        PAcc acc;
+    for (int q = 0; q < ca.nrhs && live; q++) {
+        PAcc acc, dacc;
         acc.zero();
+        dacc.zero();
         for (int rc = r0; rc < r1; rc++) {
             const int cone = L.rc_cone[rc];
             const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
@@ -1743,21 +1746,33 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
                     const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
                     const float ia = rsqrtf(a2), am = a2 * ia;
                     const float uy = u0 * fj.x + u1 * fj.y + u2 * fj.z;
-                    float t = kap * __fdividef(ir * yy - 2.f * uy, am + 1.f);
+                    const float phl = __fdividef(ir * yy - 2.f * uy, am + 1.f);  // phase distance, leaf units
+                    float t = kap * phl;
                     t -= rintf(t);
                     float sn, cs;
                     cis_cycles(t, sn, cs);
                     const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
                     const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
+                    const float ph0 = phl * hd;  // absolute: dW/dk = i ph0 W - i e w3 (combined, W13), i ph0 W2
                     if (SPLIT) {
                         const float g1x = gk.z, g1y = gk.w;
                         const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
                         acc.add(W0r * g0x + W0i * g0y + W1r * g1x + W1i * g1y,
                                 W0r * g0y - W0i * g0x + W1r * g1y - W1i * g1x);
+                        if constexpr (DK) {  // conj(dW) G
+                            const float d0r = -ph0 * W0i, d0i = ph0 * W0r;
+                            const float d1r = -ph0 * W1i + sn * w3, d1i = ph0 * W1r - cs * w3;
+                            dacc.add(d0r * g0x + d0i * g0y + d1r * g1x + d1i * g1y,
+                                     d0r * g0y - d0i * g0x + d1r * g1y - d1i * g1x);
+                        }
                     } else {
                         const float soh = gk.z;
                         const float W0r = cs * soh * w2 + sn * g, W0i = sn * soh * w2 - cs * g;
                         acc.add(W0r * g0x + W0i * g0y, W0r * g0y - W0i * g0x);  // conj(W) G
+                        if constexpr (DK) {
+                            const float d0r = -ph0 * W0i + sn * w3, d0i = ph0 * W0r - cs * w3;
+                            dacc.add(d0r * g0x + d0i * g0y, d0r * g0y - d0i * g0x);
+                        }
                     }
                 }
             }
@@ -1768,16 +1783,27 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
             v.x += w.x;
             v.y += w.y;
             bo[(long long)q * ca.N + j] = v;
+            if constexpr (DK) {  // Re(conj(T) a_j), T = sum conj(dW) G
+                const float2 z = dacc.get(), aj = a_fwd[(long long)q * ca.N + j];
+                dk += (double)z.x * aj.x + (double)z.y * aj.y;
+            }
         }
     }
+    if constexpr (DK) block_sum_store(dk, dk_partials);
 }
 
 // Transposed near field (mixed): b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i,
-// packed point records, constants hoisted, Kahan-compensated sums.
+// packed point records, constants hoisted.  With DK the same pairs also give the near-field part of
+// Re <g, dA/dk sigma> = sum_j Re( a_j sum_i conj(g_i) dK/dk(x_i, x_j) ), dK/dk = i R K - i E dn / r
+// (a = w sigma of the forward state), one double per block in dk_partials.
+template <bool DK>
 __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, const float2 *__restrict__ gs,
-                                                    float2 *__restrict__ bo) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ca.N) return;
+                                                    float2 *__restrict__ bo, const float2 *__restrict__ a_fwd,
+                                                    double *dk_partials) {
+    const int jt = blockIdx.x * blockDim.x + threadIdx.x;
+    double dk = 0.0;
+    const bool live = jt < ca.N;
+    const int j = live ? jt : 0;
     const int b = ca.leaf_of[j];
     const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
     const float4 *pn = ca.pn32;
@@ -1785,9 +1811,10 @@ __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, 
     const float kf = ca.kf, etaf = ca.etaf, kap = ca.kappa_hi;
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
     const float tolu = (float)(ca.tol / ca.HD);
-    for (int q = 0; q < ca.nrhs; q++) {
-        PAcc acc;
+    for (int q = 0; q < ca.nrhs && live; q++) {
+        PAcc acc, dacc;
         acc.zero();
+        dacc.zero();
         for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
             const int c = ca.nb_list[nb];
             const float D0 = (float)(L.ijk[3 * c] - bi0) - fj.x, D1 = (float)(L.ijk[3 * c + 1] - bi1) - fj.y,
@@ -1808,10 +1835,20 @@ __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, 
                 const float Kr = amp * (cs * A - sn * Bv), Ki = amp * (sn * A + cs * Bv);
                 const float2 g = gs[(long long)q * ca.N + i];
                 acc.add(Kr * g.x + Ki * g.y, Kr * g.y - Ki * g.x);  // conj(K) g
+                if constexpr (DK) {  // conj(g) dK/dk
+                    const float R = r * ca.HDf, dnr = dn * ir;
+                    const float dKr = -R * Ki + amp * sn * dnr, dKi = R * Kr - amp * cs * dnr;
+                    dacc.add(g.x * dKr + g.y * dKi, g.x * dKi - g.y * dKr);
+                }
             }
         }
         bo[(long long)q * ca.N + j] = acc.get();
+        if constexpr (DK) {
+            const float2 z = dacc.get(), aj = a_fwd[(long long)q * ca.N + j];
+            dk += (double)z.x * aj.x - (double)z.y * aj.y;  // Re(z a_j)
+        }
     }
+    if constexpr (DK) block_sum_store(dk, dk_partials);
 }
 
 // Transposed near field: b_j = sum_{i in the 27-neighbourhood, i != j} conj(K(x_i, x_j)) g_i.
@@ -2929,6 +2966,261 @@ __global__ void __launch_bounds__(kCsWarps * 32) k_prop_cs(CommonArgs ca, LevelA
     }
 }
 
+// ---------------------------------------------------------------------------
+// K3 (mixed, Pang = 8) on tcgen05, c-axis contraction.  For one work item (<= 128 parent nodes
+// that fall in one child cone, TMEM lane = node) and one tile of (parent cone, child box) pairs
+// of the same group key, the interpolant of every pair's child cone at the nodes is
+//     sum_a Ls[a] sum_b Lt[b] D[node, (a, b)],   D[node, (a, b, re/im)] = sum_c Lp[node][c] F_pair[a, b, c]
+// The c-contraction runs on the tensor cores per pair: M = 128 nodes, N = NF x 80 ((factor, a, b,
+// re/im)) = NF x PS x 16, K = 8, three TF32 split terms (hi hi + hi lo + lo hi) with A = Lp (hi / lo) in tensor
+// memory, B = the pair's child cone values (hi / lo) in shared memory (K-major, no swizzle), and
+// FP32 accumulators in tensor memory.  The threads (one per node) then do the b- and
+// a-contractions (45 packed FMAs per factor), the centred-factor ratio and a reduction store into
+// the parent values.  The readback of pair p - 1 overlaps the MMAs of pair p (two D buffers, two B
+// buffers).  Two blocks fit per SM (TMEM 256 columns each for one factor).  The caller zeroes
+// F_{d-1} and launches one octant at a time: one writer per parent value per launch.
+// Every wait is bounded; a timeout sets a block flag that skips the remaining MMAs and is
+// reported through the missed counter (high word).
+// ---------------------------------------------------------------------------
+constexpr int kT6Threads = 128;
+
+template <int PS, int NF>
+struct T6Cfg {
+    static constexpr int kNF = PS * 16;                    // (a, b, re/im) columns of one factor
+    static constexpr int kN = NF * kNF;                    // MMA N (a multiple of 16, at most 192)
+    static constexpr int kTileBytes = kN * 8 * 4;          // one B tile (kN rows x K = 8 TF32)
+    static constexpr int kTileStride = (kTileBytes + 1023) & ~1023;
+    static constexpr uint32_t kColA = 2 * kN;              // A hi at kColA, A lo at kColA + 8
+    static constexpr uint32_t kCols = 2 * kN + 16 <= 256 ? 256 : 512;  // TMEM allocation
+};
+
+// 16 consecutive TMEM columns of this warp's 32 lanes; the wait is in the same statement, so the
+// outputs cannot be used before the load has completed
+__device__ __forceinline__ void t6_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+struct T6Misc {
+    unsigned long long done[2];
+    uint32_t tmem;
+    int abort_;
+};
+
+template <int PS, bool CSPLIT, bool PSPLIT>
+__global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
+                                                       TcLevel T, int item0, int nitem) {
+    constexpr int P = PS * 64, NF = CSPLIT ? 2 : 1;
+    typedef T6Cfg<PS, NF> Cfg;
+    __shared__ __align__(1024) unsigned char sB[2][2][Cfg::kTileStride];  // [buffer][hi / lo]
+    __shared__ T6Misc sm;
+    __shared__ int s_crc[kTcTile], s_rcp[kTcTile];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        sm.abort_ = 0;
+        for (int b = 0; b < 2; b++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.done[b])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
+                     "r"(Cfg::kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = sm.tmem;
+    volatile int *abort_flag = &sm.abort_;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    // instruction descriptor: F32 accumulate, TF32 A and B, K-major, N / 8, M / 16
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Cfg::kN >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const float2 *FC = (const float2 *)C.F;
+    float2 *FP = (float2 *)Pl.F;
+    int G = 0;  // pairs issued by this block so far: D / B buffer G & 1, mbarrier parity (G >> 1) & 1
+    for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
+        const long long item = item0 + it;
+        const int4 h0 = T.item_hdr[3 * item], h1 = T.item_hdr[3 * item + 1], h2 = T.item_hdr[3 * item + 2];
+        const int row0 = h0.x, nrows = h0.y, grp = h0.z, gamma = h0.w;
+        const int ccone = h1.x, p0 = h1.y, np = h1.z;
+        const float o0 = __int_as_float(h2.x), o1 = __int_as_float(h2.y), o2 = __int_as_float(h2.z);
+        __syncthreads();  // the previous item's readers of s_crc / s_rcp are done
+        if (tid < kTcTile) {
+            s_crc[tid] = T.item_crc[kTcTile * item + tid];
+            s_rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
+            if (tid < np && s_crc[tid] < 0) atomicAdd(ca.missed, 1ULL);  // a child cone outside the relevant set
+        }
+        // this thread's node: geometry, basis weights, centred-factor ratio; A row = Lp (hi / lo)
+        const int node = tid < nrows ? (int)T.grp_perm[(long long)grp * P + row0 + tid] : -1;
+        float Ls[PS], rr = 0.f, ri = 0.f, g1 = 0.f, irs = 0.f;
+        unsigned long long lt2[8];
+        uint32_t ah[8], al[8];
+        {
+            float Lt[8], Lp[8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) Lt[e] = Lp[e] = 0.f;
+#pragma unroll
+            for (int e = 0; e < PS; e++) Ls[e] = 0.f;
+            if (node >= 0) {
+                float nv[3], rp, rcv, t3[3];
+                const int cone = tc_child_cone<PS>(C, Pl, tb, gamma, node, o0, o1, o2, nv, rp, rcv, t3);
+                if (cone != ccone) atomicAdd(ca.missed, 1ULL);  // the plan's order puts every node in its cone
+                const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
+                float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
+                t -= rintf(t);
+                float sn, cs;
+                cis_cycles(t, sn, cs);
+                g1 = rp / rcv;
+                rr = cs * g1;
+                ri = sn * g1;
+                irs = 1.f / (rcv * ca.HDf);
+                lagrange<PS, float>(t3[0], tb.fxs, tb.fcs, Ls);
+                lagrange<8, float>(t3[1], tb.fxa, tb.fca, Lt);
+                lagrange<8, float>(t3[2], tb.fxa, tb.fca, Lp);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                lt2[e] = f2pack(Lt[e], Lt[e]);
+                split_tf32(Lp[e], ah[e], al[e]);
+            }
+        }
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(lane_base + Cfg::kColA),
+            "r"(ah[0]), "r"(ah[1]), "r"(ah[2]), "r"(ah[3]), "r"(ah[4]), "r"(ah[5]), "r"(ah[6]), "r"(ah[7])
+            : "memory");
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(lane_base + Cfg::kColA + 8u),
+            "r"(al[0]), "r"(al[1]), "r"(al[2]), "r"(al[3]), "r"(al[4]), "r"(al[5]), "r"(al[6]), "r"(al[7])
+            : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        __syncthreads();  // the item's pair tables are in shared memory
+        const int nsteps = ca.nrhs * np;  // (right-hand side, pair)
+        // B staging: unit u = (factor, a, b, half) holds 4 complex child values (one row half for the
+        // re and the im row); each thread owns units tid + 128 r, fetched two steps ahead into registers
+        constexpr int NU = NF * PS * 16, R = (NU + kT6Threads - 1) / kT6Threads;
+        float4 pre[2][R][2];
+        auto fetch = [&](int step, int slot) {
+            const int q = step / np, pr = step % np;
+            const int crc = s_crc[pr];
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int u = tid + kT6Threads * r;
+                pre[slot][r][0] = pre[slot][r][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (u < NU && crc >= 0) {
+                    const int half = u & 1, rab = u >> 1, f = rab / (PS * 8), ab = rab % (PS * 8);
+                    const float4 *src = reinterpret_cast<const float4 *>(
+                        FC + (((long long)q * C.nrc + crc) * C.nfac + f) * ca.Pstride + ab * 8 + 4 * half);
+                    pre[slot][r][0] = __ldg(src);
+                    pre[slot][r][1] = __ldg(src + 1);
+                }
+            }
+        };
+        if (nsteps > 0) fetch(0, 0);
+        if (nsteps > 1) fetch(1, 1);
+        // step st uses prefetch slot st & 1 (a compile-time index: the loop runs two steps per pass)
+        auto step = [&](const int st, auto slot_c) {
+            constexpr int slot = decltype(slot_c)::value;
+            const int gs = G + st;
+            if (st < nsteps) {  // stage B of step st: rows (factor, a, b, re/im), K = c, hi / lo
+                unsigned char *bh = sB[gs & 1][0], *bl = sB[gs & 1][1];
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int u = tid + kT6Threads * r;
+                    if (u >= NU) continue;
+                    const float4 v0 = pre[slot][r][0], v1 = pre[slot][r][1];
+                    uint4 hr, lr, hi, li;
+                    split_tf32(v0.x, hr.x, lr.x);
+                    split_tf32(v0.z, hr.y, lr.y);
+                    split_tf32(v1.x, hr.z, lr.z);
+                    split_tf32(v1.z, hr.w, lr.w);
+                    split_tf32(v0.y, hi.x, li.x);
+                    split_tf32(v0.w, hi.y, li.y);
+                    split_tf32(v1.y, hi.z, li.z);
+                    split_tf32(v1.w, hi.w, li.w);
+                    const int nre = 2 * (u >> 1), k = 4 * (u & 1);
+                    *reinterpret_cast<uint4 *>(bh + t5_off(nre, k)) = hr;
+                    *reinterpret_cast<uint4 *>(bl + t5_off(nre, k)) = lr;
+                    *reinterpret_cast<uint4 *>(bh + t5_off(nre + 1, k)) = hi;
+                    *reinterpret_cast<uint4 *>(bl + t5_off(nre + 1, k)) = li;
+                }
+                if (st + 2 < nsteps) fetch(st + 2, slot);  // in flight during this step and the next
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();  // B staged; the readers of D buffer gs & 1 (step st - 2) are done
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (st < nsteps && tid == 0 && !*abort_flag) {
+                const uint32_t d = tmem + (uint32_t)((gs & 1) * Cfg::kN);
+                const uint32_t bH = smem_u32(sB[gs & 1][0]), bL = smem_u32(sB[gs & 1][1]);
+                const uint32_t aH = tmem + Cfg::kColA, aL = aH + 8u;
+                t5_mma(d, aH, t5_desc(bH), idesc, 0u);
+                t5_mma(d, aH, t5_desc(bL), idesc, 1u);
+                t5_mma(d, aL, t5_desc(bH), idesc, 1u);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 smem_u32(&sm.done[gs & 1]))
+                             : "memory");
+            }
+            if (st >= 1) {  // read back step st - 1 and add it into the parent values
+                const int gp = gs - 1, q = (st - 1) / np, pr = (st - 1) % np;
+                const bool ok = t5_wait(smem_u32(&sm.done[gp & 1]), (gp >> 1) & 1, abort_flag);
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t dcol = lane_base + (uint32_t)((gp & 1) * Cfg::kN);
+                unsigned long long acc[NF];
+#pragma unroll
+                for (int f = 0; f < NF; f++) {
+                    unsigned long long s = 0ull;
+#pragma unroll
+                    for (int a = 0; a < PS; a++) {  // columns 16 a .. 16 a + 15: (b, re/im) of radial index a
+                        uint32_t v[16];
+                        t6_ld16(dcol + (uint32_t)(f * Cfg::kNF + 16 * a), v);
+                        unsigned long long sa = 0ull;
+#pragma unroll
+                        for (int b = 0; b < 8; b++)
+                            f2fma(sa, lt2[b], f2pack(__uint_as_float(v[2 * b]), __uint_as_float(v[2 * b + 1])));
+                        f2fma(s, f2pack(Ls[a], Ls[a]), sa);
+                    }
+                    acc[f] = ok ? s : 0ull;
+                }
+                const int rcp = s_rcp[pr];
+                if (node >= 0 && rcp >= 0 && s_crc[pr] >= 0) {
+                    const long long base = ((long long)q * Pl.nrc + rcp) * Pl.nfac * ca.Pstride;
+                    float vr, vi, wr = 0.f, wi = 0.f;
+                    f2unpack(acc[0], vr, vi);
+                    if constexpr (CSPLIT) f2unpack(acc[NF - 1], wr, wi);
+                    if (CSPLIT && PSPLIT) {
+                        const float r2r = rr * g1, r2i = ri * g1;
+                        atomicAdd(FP + base + node, make_float2(vr * r2r - vi * r2i, vr * r2i + vi * r2r));
+                        atomicAdd(FP + base + ca.Pstride + node, make_float2(wr * rr - wi * ri, wr * ri + wi * rr));
+                    } else {
+                        if (CSPLIT) {
+                            vr = vr * irs + wr;
+                            vi = vi * irs + wi;
+                        }
+                        atomicAdd(FP + base + node, make_float2(vr * rr - vi * ri, vr * ri + vi * rr));
+                    }
+                }
+            }
+        };
+        for (int st = 0; st <= nsteps; st += 2) {
+            step(st, std::integral_constant<int, 0>{});
+            if (st + 1 <= nsteps) step(st + 1, std::integral_constant<int, 1>{});
+        }
+        G += nsteps;
+    }
+    if (tid == 0 && sm.abort_) atomicAdd(ca.missed, 1ULL << 32);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(Cfg::kCols));
+    }
+}
+
 // Once per plan: for every group key (child octant, parent cone), the child cone of each of the P
 // parent nodes (FP32, the classification the propagation kernels use), the distinct cones in
 // ascending order (at most 16; nodes of further cones go last and are counted as missed when
@@ -3346,6 +3638,17 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                             const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
                             if (ni > 0)
                                 k_prop_t5<PS><<<ni, kT5Threads, kT5Smem, s>>>(ca, L[d], L[d - 1], tb, T, i0);
+                        } else if (p.tc_engine == 2) {
+                            const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
+                            const int gr = std::min(ni, 2 * p.num_sms);  // persistent: two blocks per SM
+                            if (ni > 0) {
+                                if (L[d].split && L[d - 1].split)
+                                    k_prop_t6<PS, true, true><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                                else if (L[d].split)
+                                    k_prop_t6<PS, true, false><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                                else
+                                    k_prop_t6<PS, false, false><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                            }
                         } else {
                             k_prop_tc<PS><<<dim3(2 * nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
                         }
@@ -3447,17 +3750,24 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
                 if (Fd) dk_partials += L[d].nrc;
                 prof_mark(p, s, kStCousin, d);
             }
-        k_near_adj32<<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)gs, (float2 *)bws);
+        // with the k-derivative (Fd given), the near-field and leaf parts of Re <g, dA/dk sigma> come from
+        // the same pair loops: one double per block after the anterpolation's per-cone partials
+        const float2 *afw = (const float2 *)p.ws.a;
+        if (Fd) k_near_adj32<true><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)gs, (float2 *)bws, afw, dk_partials);
+        else k_near_adj32<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], (const float2 *)gs, (float2 *)bws, nullptr, nullptr);
+        if (Fd) dk_partials += nblk(N);
         prof_mark(p, s, kStNear, D);
         if (L[D].nrc) {
             const int nch = p.ncchunk[D];
             const unsigned gw = (unsigned)((nch + 3) / 4);
-            if (L[D].split)
-                k_leaf_adj_w<PS, PA, true><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, (const float2 *)G[D],
-                                                              (float2 *)bws);
-            else
-                k_leaf_adj_w<PS, PA, false><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, (const float2 *)G[D],
-                                                               (float2 *)bws);
+            const float2 *GD = (const float2 *)G[D];
+            if (L[D].split) {
+                if (Fd) k_leaf_adj_w<PS, PA, true, true><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, afw, dk_partials);
+                else k_leaf_adj_w<PS, PA, true, false><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, nullptr, nullptr);
+            } else {
+                if (Fd) k_leaf_adj_w<PS, PA, false, true><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, afw, dk_partials);
+                else k_leaf_adj_w<PS, PA, false, false><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, nullptr, nullptr);
+            }
             prof_mark(p, s, kStLeaf, D);
         }
         k_scatter_adj<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w32,

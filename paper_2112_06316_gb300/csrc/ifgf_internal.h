@@ -175,6 +175,7 @@ struct Plan {
     double tc_min_fill = 0.4;
     // tensor-core propagation engine: 1 = tcgen05 (TMEM accumulators), 0 = warp-level mma.sync
     int tc_engine = 1;
+    int num_sms = 152;  // multiprocessors of the plan's device
     std::vector<void *> allocs;
     int64_t device_bytes = 0;
 

@@ -180,13 +180,14 @@ def test_config2_qualified_orders_vs_direct(lib, oracle_lib):
     check(y32, y64, 1e-5)
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine", [2, 1, 0])
 @pytest.mark.parametrize("fm", [0, 1, 2])
 @pytest.mark.parametrize("ps", [5, 6])
 def test_tensor_core_propagation_modes(lib, oracle_lib, ps, fm, engine):
-    """Orders with Pang = 8 propagate through the tensor cores on the mixed path (engine 1:
-    tcgen05 with TMEM accumulators over the K = 64 angular contraction; engine 0: warp
-    mma.sync over K = P; both with a three-term TF32 split), forced on at every level (fill
+    """Orders with Pang = 8 propagate through the tensor cores on the mixed path (engine 2:
+    tcgen05 over the K = 8 c-contraction per (node run, pair), the b- and a-contractions on CUDA
+    cores; engine 1: tcgen05 with TMEM accumulators over the K = 64 angular contraction; engine 0:
+    warp mma.sync over K = P; all with a three-term TF32 split), forced on at every level (fill
     threshold 0);
     two propagation levels (D = 5) in every factor-mode combination (split -> split,
     split -> combined, combined -> combined), two right-hand sides.  The result matches the
