@@ -2971,13 +2971,14 @@ __global__ void __launch_bounds__(kCsWarps * 32) k_prop_cs(CommonArgs ca, LevelA
 // that fall in one child cone, TMEM lane = node) and one tile of (parent cone, child box) pairs
 // of the same group key, the interpolant of every pair's child cone at the nodes is
 //     sum_a Ls[a] sum_b Lt[b] D[node, (a, b)],   D[node, (a, b, re/im)] = sum_c Lp[node][c] F_pair[a, b, c]
-// The c-contraction runs on the tensor cores per pair: M = 128 nodes, N = NF x 80 ((factor, a, b,
-// re/im)) = NF x PS x 16, K = 8, three TF32 split terms (hi hi + hi lo + lo hi) with A = Lp (hi / lo) in tensor
+// The c-contraction runs on the tensor cores per pair: M = 128 nodes, N = NF x PS x 16 ((factor,
+// a, b, re/im)), K = 8, three TF32 split terms (hi hi + hi lo + lo hi) with A = Lp (hi / lo) in tensor
 // memory, B = the pair's child cone values (hi / lo) in shared memory (K-major, no swizzle), and
 // FP32 accumulators in tensor memory.  The threads (one per node) then do the b- and
 // a-contractions (45 packed FMAs per factor), the centred-factor ratio and a reduction store into
-// the parent values.  The readback of pair p - 1 overlaps the MMAs of pair p (two D buffers, two B
-// buffers).  Two blocks fit per SM (TMEM 256 columns each for one factor).  The caller zeroes
+// the parent values.  The readback of step p - 2 overlaps the MMAs of steps p - 1 and p (three D
+// buffers and three B buffers; the child values are fetched into registers two steps ahead).  With
+// one factor at orders (5, 8) two blocks fit per SM (256 TMEM columns each).  The caller zeroes
 // F_{d-1} and launches one octant at a time: one writer per parent value per launch.
 // Every wait is bounded; a timeout sets a block flag that skips the remaining MMAs and is
 // reported through the missed counter (high word).
@@ -2990,9 +2991,26 @@ struct T6Cfg {
     static constexpr int kN = NF * kNF;                    // MMA N (a multiple of 16, at most 192)
     static constexpr int kTileBytes = kN * 8 * 4;          // one B tile (kN rows x K = 8 TF32)
     static constexpr int kTileStride = (kTileBytes + 1023) & ~1023;
-    static constexpr uint32_t kColA = 2 * kN;              // A hi at kColA, A lo at kColA + 8
-    static constexpr uint32_t kCols = 2 * kN + 16 <= 256 ? 256 : 512;  // TMEM allocation
+    // D and B buffers: three (readback two steps behind) when they and A fit in the 512 tensor-memory
+    // columns of an SM, else two (readback one step behind)
+    static constexpr int kBuf = 3 * kN + 16 <= 512 ? 3 : 2;
+    static constexpr uint32_t kColA = kBuf * kN;           // A hi at kColA, A lo at kColA + 8
+    static constexpr uint32_t kCols = kBuf * kN + 16 <= 256 ? 256 : 512;  // TMEM allocation
+    static_assert(kBuf * kN + 16 <= (int)kCols && kCols <= 512, "tensor memory budget");
 };
+
+// 32 consecutive TMEM columns of this warp's 32 lanes, wait included (see t6_ld16)
+__device__ __forceinline__ void t6_ld32w(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
 
 // 16 consecutive TMEM columns of this warp's 32 lanes; the wait is in the same statement, so the
 // outputs cannot be used before the load has completed
@@ -3006,7 +3024,7 @@ __device__ __forceinline__ void t6_ld16(uint32_t taddr, uint32_t *r) {
 }
 
 struct T6Misc {
-    unsigned long long done[2];
+    unsigned long long done[3];
     uint32_t tmem;
     int abort_;
 };
@@ -3016,13 +3034,13 @@ __global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs
                                                        TcLevel T, int item0, int nitem) {
     constexpr int P = PS * 64, NF = CSPLIT ? 2 : 1;
     typedef T6Cfg<PS, NF> Cfg;
-    __shared__ __align__(1024) unsigned char sB[2][2][Cfg::kTileStride];  // [buffer][hi / lo]
+    __shared__ __align__(1024) unsigned char sB[Cfg::kBuf][2][Cfg::kTileStride];  // [buffer][hi / lo]
     __shared__ T6Misc sm;
     __shared__ int s_crc[kTcTile], s_rcp[kTcTile];
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         sm.abort_ = 0;
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < Cfg::kBuf; b++)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.done[b])));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -3042,7 +3060,7 @@ __global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs
                            ((uint32_t)(128 >> 4) << 24);
     const float2 *FC = (const float2 *)C.F;
     float2 *FP = (float2 *)Pl.F;
-    int G = 0;  // pairs issued by this block so far: D / B buffer G & 1, mbarrier parity (G >> 1) & 1
+    int G = 0;  // steps issued by this block so far: D / B buffer G % 3, mbarrier parity (G / 3) & 1
     for (int it = blockIdx.x; it < nitem; it += gridDim.x) {
         const long long item = item0 + it;
         const int4 h0 = T.item_hdr[3 * item], h1 = T.item_hdr[3 * item + 1], h2 = T.item_hdr[3 * item + 2];
@@ -3126,8 +3144,9 @@ __global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs
         auto step = [&](const int st, auto slot_c) {
             constexpr int slot = decltype(slot_c)::value;
             const int gs = G + st;
+            const int bsel = gs % Cfg::kBuf;
             if (st < nsteps) {  // stage B of step st: rows (factor, a, b, re/im), K = c, hi / lo
-                unsigned char *bh = sB[gs & 1][0], *bl = sB[gs & 1][1];
+                unsigned char *bh = sB[bsel][0], *bl = sB[bsel][1];
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     const int u = tid + kT6Threads * r;
@@ -3152,37 +3171,43 @@ __global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            __syncthreads();  // B staged; the readers of D buffer gs & 1 (step st - 2) are done
+            __syncthreads();  // B staged; the readers of D buffer gs % kBuf (step st - kBuf) are done
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             if (st < nsteps && tid == 0 && !*abort_flag) {
-                const uint32_t d = tmem + (uint32_t)((gs & 1) * Cfg::kN);
-                const uint32_t bH = smem_u32(sB[gs & 1][0]), bL = smem_u32(sB[gs & 1][1]);
+                const uint32_t d = tmem + (uint32_t)(bsel * Cfg::kN);
+                const uint32_t bH = smem_u32(sB[bsel][0]), bL = smem_u32(sB[bsel][1]);
                 const uint32_t aH = tmem + Cfg::kColA, aL = aH + 8u;
                 t5_mma(d, aH, t5_desc(bH), idesc, 0u);
                 t5_mma(d, aH, t5_desc(bL), idesc, 1u);
                 t5_mma(d, aL, t5_desc(bH), idesc, 1u);
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                 smem_u32(&sm.done[gs & 1]))
+                                 smem_u32(&sm.done[bsel]))
                              : "memory");
             }
-            if (st >= 1) {  // read back step st - 1 and add it into the parent values
-                const int gp = gs - 1, q = (st - 1) / np, pr = (st - 1) % np;
-                const bool ok = t5_wait(smem_u32(&sm.done[gp & 1]), (gp >> 1) & 1, abort_flag);
+            constexpr int LAG = Cfg::kBuf - 1;  // steps between an MMA and its readback
+            if (st >= LAG) {  // read back step st - LAG and add it into the parent values
+                const int gp = gs - LAG, q = (st - LAG) / np, pr = (st - LAG) % np;
+                const bool ok = t5_wait(smem_u32(&sm.done[gp % Cfg::kBuf]), (gp / Cfg::kBuf) & 1, abort_flag);
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t dcol = lane_base + (uint32_t)((gp & 1) * Cfg::kN);
+                const uint32_t dcol = lane_base + (uint32_t)((gp % Cfg::kBuf) * Cfg::kN);
                 unsigned long long acc[NF];
 #pragma unroll
                 for (int f = 0; f < NF; f++) {
                     unsigned long long s = 0ull;
 #pragma unroll
-                    for (int a = 0; a < PS; a++) {  // columns 16 a .. 16 a + 15: (b, re/im) of radial index a
-                        uint32_t v[16];
-                        t6_ld16(dcol + (uint32_t)(f * Cfg::kNF + 16 * a), v);
-                        unsigned long long sa = 0ull;
+                    for (int a0 = 0; a0 < PS; a0 += 2) {  // columns 16 a .. 16 a + 15: (b, re/im) of radial index a
+                        uint32_t v[32];
+                        if (a0 + 1 < PS) t6_ld32w(dcol + (uint32_t)(f * Cfg::kNF + 16 * a0), v);
+                        else t6_ld16(dcol + (uint32_t)(f * Cfg::kNF + 16 * a0), v);
 #pragma unroll
-                        for (int b = 0; b < 8; b++)
-                            f2fma(sa, lt2[b], f2pack(__uint_as_float(v[2 * b]), __uint_as_float(v[2 * b + 1])));
-                        f2fma(s, f2pack(Ls[a], Ls[a]), sa);
+                        for (int a = a0; a < a0 + 2 && a < PS; a++) {
+                            const uint32_t *va = v + 16 * (a - a0);
+                            unsigned long long sa = 0ull;
+#pragma unroll
+                            for (int b = 0; b < 8; b++)
+                                f2fma(sa, lt2[b], f2pack(__uint_as_float(va[2 * b]), __uint_as_float(va[2 * b + 1])));
+                            f2fma(s, f2pack(Ls[a], Ls[a]), sa);
+                        }
                     }
                     acc[f] = ok ? s : 0ull;
                 }
@@ -3206,9 +3231,10 @@ __global__ void __launch_bounds__(kT6Threads) k_prop_t6(CommonArgs ca, LevelArgs
                 }
             }
         };
-        for (int st = 0; st <= nsteps; st += 2) {
+        const int last = nsteps + Cfg::kBuf - 2;  // drain steps read back the last pairs
+        for (int st = 0; st <= last; st += 2) {
             step(st, std::integral_constant<int, 0>{});
-            if (st + 1 <= nsteps) step(st + 1, std::integral_constant<int, 1>{});
+            if (st + 1 <= last) step(st + 1, std::integral_constant<int, 1>{});
         }
         G += nsteps;
     }
@@ -3640,14 +3666,18 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                                 k_prop_t5<PS><<<ni, kT5Threads, kT5Smem, s>>>(ca, L[d], L[d - 1], tb, T, i0);
                         } else if (p.tc_engine == 2) {
                             const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
-                            const int gr = std::min(ni, 2 * p.num_sms);  // persistent: two blocks per SM
+                            // persistent: as many blocks per SM as their tensor memory allows
+                            auto grid = [&](uint32_t cols) { return std::min(ni, (cols <= 256 ? 2 : 1) * p.num_sms); };
                             if (ni > 0) {
                                 if (L[d].split && L[d - 1].split)
-                                    k_prop_t6<PS, true, true><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                                    k_prop_t6<PS, true, true><<<grid(T6Cfg<PS, 2>::kCols), kT6Threads, 0, s>>>(
+                                        ca, L[d], L[d - 1], tb, T, i0, ni);
                                 else if (L[d].split)
-                                    k_prop_t6<PS, true, false><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                                    k_prop_t6<PS, true, false><<<grid(T6Cfg<PS, 2>::kCols), kT6Threads, 0, s>>>(
+                                        ca, L[d], L[d - 1], tb, T, i0, ni);
                                 else
-                                    k_prop_t6<PS, false, false><<<gr, kT6Threads, 0, s>>>(ca, L[d], L[d - 1], tb, T, i0, ni);
+                                    k_prop_t6<PS, false, false><<<grid(T6Cfg<PS, 1>::kCols), kT6Threads, 0, s>>>(
+                                        ca, L[d], L[d - 1], tb, T, i0, ni);
                             }
                         } else {
                             k_prop_tc<PS><<<dim3(2 * nt, P / kTcRows), 128, 0, s>>>(ca, L[d], L[d - 1], tb, T, t0);
