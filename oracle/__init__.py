@@ -8,6 +8,8 @@ reference legs use this package.  It shares no code with
   Eq. field1 (kernel of Eq. GreenFunction / Eq. double_layer, identity term of
   Eq. CombLayIE) and its conjugate transpose, on all rows or a row subset.
 * ``ifgf``: the IFGF apply of Section 3.4 in FP64, stage by stage (``oracle.c``).
+* ``ifgf_far_field``: the far-field pattern from the IFGF level-3 interpolants
+  (the s -> 0 limit of the factorisation), FP64.
 * ``field`` / ``far_field``: the combined-layer potential of Eq. CombinedLayer at
   off-surface targets and its far-field pattern (Eq. FarField), plain numpy sums.
 * ``mie``: closed-form sound-soft sphere solutions (module ``oracle.mie``).
@@ -50,6 +52,7 @@ class OracleParams(ctypes.Structure):
         ("cone_rule", ctypes.c_int), ("factor_mode", ctypes.c_int),
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
+        ("far_field", ctypes.c_int),
     ]
 
 
@@ -77,6 +80,7 @@ def lib():
         _lib.oracle_direct_rows.restype = ctypes.c_int
         _lib.oracle_direct_adjoint_rows.restype = ctypes.c_int
         _lib.oracle_ifgf.restype = ctypes.c_int
+        _lib.oracle_ifgf_far_field.restype = ctypes.c_int
         _lib.oracle_cheb_interp_1d.restype = ctypes.c_double
         _lib.oracle_cheb_interp_1d.argtypes = [ctypes.c_int, dp, ctypes.c_double]
         _lib.oracle_num_threads.restype = ctypes.c_int
@@ -104,6 +108,7 @@ class IFGFParams:
     identity_coef: float = 0.0
     root_center: tuple = (0.0, 0.0, 0.0)
     root_side: float = 0.0
+    far_field: int = 0
 
     def to_c(self) -> OracleParams:
         p = OracleParams()
@@ -116,6 +121,7 @@ class IFGFParams:
         for a in range(3):
             p.root_center[a] = self.root_center[a]
         p.root_side = self.root_side
+        p.far_field = self.far_field
         return p
 
 
@@ -206,6 +212,34 @@ def ifgf(points, normals, weights, params: IFGFParams, sigma):
                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(info))
     if rc != 0:
         raise RuntimeError(f"oracle_ifgf failed ({rc})")
+    return out, _info_dict(info)
+
+
+def ifgf_far_field(points, normals, weights, params: IFGFParams, sigma, xhat):
+    """Far-field pattern (Eq. FarField) from the IFGF level-3 interpolants in FP64: the leaf
+    expansions and propagation of Section 3.4, then for every direction the s -> 0 limit
+    sum_B e^{-ik xhat.y_B} / (4 pi) Interp(F_B)(0, theta, phi) over the level-3 boxes (the
+    plan keeps every is = 0 segment of level 3).  xhat: (M, 3) unit directions.  Returns
+    ((nrhs, M) complex128, info dict)."""
+    x, n, w = _geom(points, normals, weights)
+    N = x.shape[0]
+    s = _dens(sigma, N)
+    nrhs = s.shape[0]
+    xh = np.ascontiguousarray(xhat, dtype=np.float64).reshape(-1, 3)
+    M = xh.shape[0]
+    out = np.zeros((nrhs, M), dtype=np.complex128)
+    info = OracleInfo()
+    p = params.to_c()
+    rc = lib().oracle_ifgf_far_field(ctypes.byref(p), ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w),
+                                     ctypes.c_int(nrhs), s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     ctypes.c_int64(M), _dptr(xh),
+                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(info))
+    if rc != 0:
+        raise RuntimeError(f"oracle_ifgf_far_field failed ({rc})")
+    return out, _info_dict(info)
+
+
+def _info_dict(info) -> dict:
     D = info.D
     d = {
         "D": D,
@@ -221,7 +255,7 @@ def ifgf(points, normals, weights, params: IFGFParams, sigma):
         "leaf_evals": info.leaf_evals,
         "near_pairs": info.near_pairs,
     }
-    return out, d
+    return d
 
 
 def auto_levels(points, leaf_target=64.0) -> int:

@@ -17,6 +17,8 @@
  *                         points and, for d > 3, onto the parent's interpolation points with
  *                         re-centring (Eq. cent_fact); the level-D neighbour interactions by
  *                         direct summation (Remark level_D_neighboring).
+ *   oracle_ifgf_far_field: the far-field pattern (Eq. FarField) from the level-3 interpolants:
+ *                         the s -> 0 limit of E(x; y_B) F_B(x) summed over the level-3 boxes.
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - Chebyshev interpolation uses first-kind nodes cos((2k+1)pi/(2n)) with the discrete-
@@ -61,6 +63,7 @@ typedef struct {
     int cone_rule, factor_mode;
     double identity_coef;
     double root_center[3], root_side;
+    int far_field; /* 1: level 3 also keeps every segment with is = 0 (oracle_ifgf_far_field) */
 } oracle_params;
 
 typedef struct {
@@ -260,7 +263,7 @@ typedef struct {
 } olevel;
 
 typedef struct {
-    int D, P, Ps, Pang, nrhs;
+    int D, P, Ps, Pang, nrhs, far_field;
     double k, eta, L, c0[3];
     const double *xyz, *nrm, *w;
     int64_t N;
@@ -447,8 +450,13 @@ static void build_relevant_cones(otree *T, int d) {
             const olevel *PL = &T->lv[d - 1];
             cap += (int64_t)(PL->rc_start[pb + 1] - PL->rc_start[pb]) * P;
         }
+        const int ffar = d == 3 && T->far_field;
+        if (ffar) cap += (int64_t)L->nC * L->nph;
         int *v = (int *)malloc(sizeof(int) * (cap > 0 ? cap : 1));
         int64_t n = 0;
+        /* far field: s = h / r -> 0 lies in the segments with is = 0, in every direction */
+        if (ffar)
+            for (int c = 0; c < L->nC * L->nph; c++) v[n++] = c;
         for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) {
             int cb = L->co_list[c];
             for (int i = 0; i < L->pcount[cb]; i++) {
@@ -689,6 +697,7 @@ static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const doubl
                       const double *w, int nrhs) {
     T->N = N; T->xyz = xyz; T->nrm = nrm; T->w = w; T->nrhs = nrhs;
     T->k = prm->k; T->eta = prm->eta; T->Ps = prm->Ps; T->Pang = prm->Pang; T->P = prm->Ps * prm->Pang * prm->Pang;
+    T->far_field = prm->far_field != 0;
     if (prm->root_side > 0) {
         T->L = prm->root_side;
         for (int a = 0; a < 3; a++) T->c0[a] = prm->root_center[a];
@@ -827,9 +836,9 @@ static int stage_level(otree *T, int d, cplx *u, int64_t *n_cousin, int64_t *n_p
     int err = 0;
     int *plist = (int *)malloc(sizeof(int) * N);
     for (int b = 0; b < L->nbox && !err; b++) {
-        /* (a) cousin points of B (Eq. NeighborsCousins) */
+        /* (a) cousin points of B (Eq. NeighborsCousins); skipped when u is NULL */
         int np = 0;
-        for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) {
+        for (int c = L->co_start[b]; u && c < L->co_start[b + 1]; c++) {
             int cb = L->co_list[c];
             for (int i = 0; i < L->pcount[cb]; i++) plist[np++] = L->perm[L->pstart[cb] + i];
         }
@@ -911,6 +920,22 @@ static int64_t stage_near_field(const otree *T, const cplx *sg, cplx *u) {
     return near_pairs;
 }
 
+/* structural part of oracle_info */
+static void tree_info(const otree *T, oracle_info *info) {
+    info->D = T->D;
+    info->root_side = T->L;
+    for (int a = 0; a < 3; a++) info->root_center[a] = T->c0[a];
+    for (int d = 1; d <= T->D; d++) {
+        info->nbox[d] = T->lv[d].nbox;
+        if (d >= 3) {
+            info->ns[d] = T->lv[d].ns;
+            info->nC[d] = T->lv[d].nC;
+            info->split[d] = T->lv[d].split;
+            info->nrc[d] = T->lv[d].nrc;
+        }
+    }
+}
+
 int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const double *nrm, const double *w,
                 int nrhs, const double *sigma, double *out, oracle_info *info) {
     if (N <= 0 || nrhs <= 0 || nrhs > 64 || !(prm->k > 0) || prm->Ps < 1 || prm->Pang < 1 || prm->Ps > 31 ||
@@ -942,22 +967,83 @@ int oracle_ifgf(const oracle_params *prm, int64_t N, const double *xyz, const do
         for (int64_t i = 0; i < N * nrhs; i++) o[i] = prm->identity_coef * sg[i] + u[i];
     }
     if (info) {
-        info->D = D;
-        info->root_side = T.L;
-        for (int a = 0; a < 3; a++) info->root_center[a] = T.c0[a];
-        for (int d = 1; d <= D; d++) {
-            info->nbox[d] = T.lv[d].nbox;
-            if (d >= 3) {
-                info->ns[d] = T.lv[d].ns;
-                info->nC[d] = T.lv[d].nC;
-                info->split[d] = T.lv[d].split;
-                info->nrc[d] = T.lv[d].nrc;
-            }
-        }
+        tree_info(&T, info);
         info->leaf_evals = leaf_evals;
         info->near_pairs = near_pairs;
     }
     free(u);
     free_tree(&T);
     return err ? -2 : 0;
+}
+
+/* Far-field pattern (Eq. FarField) from the level-3 interpolants.  With x = R xhat the
+ * centred factors of Eq. cent_fact satisfy R e^{-ikR} E_1(x; y_B) -> e^{-ik xhat.y_B} / (4 pi)
+ * and R e^{-ikR} E_2(x; y_B) -> 0 as R -> infinity, while s = h / |x - y_B| -> 0 and the
+ * direction of x - y_B tends to xhat.  The level-3 boxes partition the sources, so
+ *   u_inf(xhat) = sum_B e^{-ik xhat.y_B} / (4 pi) Interp(F_B)(s = 0, theta(xhat), phi(xhat)),
+ * with F_B the combined factor, or the q = 1 member W13 of the split pair (its W2 member
+ * carries E_2 and drops out).  The point s = 0 is the lower end of segment is = 0 (local
+ * coordinate -1), which the far-field option keeps relevant at level 3 in every direction.
+ * The factors come from the leaf expansions and the propagation of Section 3.4 exactly as
+ * in oracle_ifgf; the cousin interpolations and the near field are not needed. */
+int oracle_ifgf_far_field(const oracle_params *prm, int64_t N, const double *xyz, const double *nrm,
+                          const double *w, int nrhs, const double *sigma, int64_t M, const double *xhat,
+                          double *out, oracle_info *info) {
+    if (N <= 0 || M < 0 || nrhs <= 0 || nrhs > 64 || !(prm->k > 0) || prm->Ps < 1 || prm->Pang < 1 ||
+        prm->Ps > 31 || prm->Pang > 31)
+        return -1;
+    oracle_params q = *prm;
+    q.far_field = 1;
+    otree T;
+    memset(&T, 0, sizeof(T));
+    if (setup_tree(&T, &q, N, xyz, nrm, w, nrhs)) {
+        free_tree(&T);
+        return -1;
+    }
+    const cplx *sg = (const cplx *)sigma;
+    const int64_t leaf_evals = stage_leaf_expansions(&T, sg);
+    int err = 0;
+    for (int d = T.D; d >= 3 && !err; d--) {
+        int64_t nce = 0, npe = 0;
+        err = stage_level(&T, d, NULL, &nce, &npe);
+        if (info && d > 3) info->prop_evals[d - 1] = npe;
+    }
+    const olevel *L = &T.lv[3];
+    const int fac = L->split ? 1 : 0;
+    cplx *o = (cplx *)out;
+    int lerr = 0;
+#pragma omp parallel for schedule(static) reduction(| : lerr)
+    for (int64_t j = 0; j < (err ? 0 : M); j++) {
+        const double *e = xhat + 3 * j;
+        /* direction only: theta, phi of xhat on the cone grid, s = 0 */
+        double th = atan2(sqrt(e[0] * e[0] + e[1] * e[1]), e[2]);
+        double ph = atan2(e[1], e[0]);
+        if (ph < 0) ph += 2.0 * OR_PI;
+        if (ph >= 2.0 * OR_PI) ph = 0.0;
+        double ut = snap_boundary(th / L->dth), up = snap_boundary(ph / L->dph);
+        int it = (int)floor(ut), ip = (int)floor(up);
+        if (it > L->nC - 1) it = L->nC - 1;
+        if (ip > L->nph - 1) ip = L->nph - 1;
+        if (it < 0) it = 0;
+        if (ip < 0) ip = 0;
+        const double t3[3] = {-1.0, 2.0 * (ut - it) - 1.0, 2.0 * (up - ip) - 1.0};
+        const int cone = it * L->nph + ip; /* is = 0 */
+        cplx acc[64];
+        for (int qq = 0; qq < nrhs; qq++) acc[qq] = 0.0;
+        for (int b = 0; b < L->nbox; b++) {
+            int rc = rc_find(L, b, cone);
+            if (rc < 0) { lerr |= 1; continue; }
+            double y0[3];
+            box_center(&T, 3, b, y0);
+            const cplx ph0 = cexp(-I * T.k * (e[0] * y0[0] + e[1] * y0[1] + e[2] * y0[2])) / (4.0 * OR_PI);
+            for (int qq = 0; qq < nrhs; qq++) acc[qq] += ph0 * cheb_eval3(&T, L->C + fidx(&T, L, rc, fac, qq), t3);
+        }
+        for (int qq = 0; qq < nrhs; qq++) o[(int64_t)qq * M + j] = acc[qq];
+    }
+    if (info) {
+        tree_info(&T, info);
+        info->leaf_evals = leaf_evals;
+    }
+    free_tree(&T);
+    return (err || lerr) ? -2 : 0;
 }

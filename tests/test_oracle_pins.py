@@ -337,3 +337,50 @@ def test_relevant_cones_per_level_roughly_constant(oracle_lib):
     nrc = [info["nrc"][d] for d in (3, 4, 5)]
     assert nb[2] / nb[0] > 15, nb
     assert max(nrc) / min(nrc) < 2.5, nrc
+
+
+# ---------------------------------------------------------------- IFGF far field (Eq. FarField, Section 3.4)
+@pytest.mark.parametrize("fm", [0, 1])
+def test_ifgf_far_field_mie(oracle_lib, fm):
+    """The far-field pattern taken from the level-3 interpolants at s = 0, for the exact Mie
+    density of a sound-soft unit sphere (k = pi), against the closed-form far field.  With
+    factor_mode 0 level 3 stores the split pair (its W13 member is the one that survives the
+    limit); factor_mode 1 the combined factor.  The error falls with the interpolation orders
+    to the size of the IFGF error of an apply."""
+    from oracle import mie
+
+    s = cube_sphere(24, 6)
+    k = math.pi
+    phi = mie.density(s.points, k, k)
+    xh = mie.sphere_grid(11, 11)
+    ue = mie.far_field(xh, k)
+    errs = {}
+    for ps, pa, lev in ((3, 5, 3), (5, 8, 3), (5, 8, 4)):
+        out, info = oracle_lib.ifgf_far_field(
+            s.points, s.normals, s.weights,
+            oracle_lib.IFGFParams(k=k, Ps=ps, Pang=pa, levels=lev, factor_mode=fm), phi, xh)
+        assert info["split"][3] == (1 if fm == 0 else 0)
+        errs[(ps, pa, lev)] = rel(out[0], ue)
+    assert errs[(3, 5, 3)] < 1e-3
+    assert errs[(5, 8, 3)] < 1e-5 and errs[(5, 8, 4)] < 3e-5  # combined factor at H < lambda/2: less accurate
+    assert errs[(5, 8, 3)] < errs[(3, 5, 3)] / 30
+
+
+def test_ifgf_far_field_converges_to_sum(oracle_lib):
+    """A 3-wavelength sphere with random densities (two right-hand sides), D = 4: the IFGF far
+    field approaches the plain quadrature sum of Eq. FarField as the orders grow, for every
+    direction (max-modulus error), with the combined factor at level 3."""
+    s, k = sphere_workload(24, 6, 3.0)
+    sig = random_density(s.N, 2, 31)
+    rng = np.random.default_rng(32)
+    xh = rng.normal(size=(60, 3))
+    xh /= np.linalg.norm(xh, axis=1)[:, None]
+    ref = oracle_lib.far_field(s.points, s.normals, s.weights, k, k, sig, xh)
+    e = []
+    for ps, pa in ((3, 5), (5, 7), (6, 8)):
+        out, info = oracle_lib.ifgf_far_field(s.points, s.normals, s.weights,
+                                              oracle_lib.IFGFParams(k=k, Ps=ps, Pang=pa, levels=4), sig, xh)
+        assert info["split"][3] == 0 and info["D"] == 4
+        e.append(float(np.abs(out - ref).max() / np.abs(ref).max()))
+    assert e[0] < 5e-3 and e[2] < 1e-4
+    assert e[0] > e[1] > e[2]
