@@ -158,7 +158,7 @@ class ClockSampler:
 
 
 KERNEL_OF_STAGE = {"leaf": "k_leaf32x2", "near": "k_near32", "cousin": "k_cousin_cs", "cousin_sum": "k_cousin_sum",
-                   "prop": "k_prop_w", "prop_tc": "k_prop_t5"}
+                   "prop": "k_prop_w", "prop_tc": "k_prop_t5", "prop_cs": "k_prop_cs"}
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "dram_traffic_sphere16lambda_5x8.txt")
 
@@ -221,8 +221,8 @@ def algorithmic_flops(info, P, nrhs, split_levels):
 
 def launches_of(stages):
     """Kernel launches of one profiled apply: one per stage entry, eight (one per child octant)
-    for a tensor-core propagation level."""
-    return sum(8 if kind == "prop_tc" else 1 for kind, _, _ in stages)
+    for a tensor-core or cone-stationary propagation level."""
+    return sum(8 if kind in ("prop_tc", "prop_cs") else 1 for kind, _, _ in stages)
 
 
 def reduce_over_ranks(ms: float, points: float, world: int, device="cpu"):
@@ -358,14 +358,14 @@ def run_ours(args):
     for kind, lvl, t in stages:
         by_kind[kind] = by_kind.get(kind, 0.0) + t
     flops_of = {"leaf": leaf_f, "near": near_f, "cousin": sum(cousin_f.values())}
-    for kind in ("prop", "prop_tc"):  # CUDA-core and tensor-core propagation levels
+    for kind in ("prop", "prop_tc", "prop_cs"):  # CUDA-core, tensor-core, cone-stationary propagation levels
         lv = [lvl for k2, lvl, _ in stages if k2 == kind]
         if lv:
             flops_of[kind] = sum(prop_f[lvl] for lvl in lv)
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     dom = max((kk for kk in by_kind if kk in flops_of), key=lambda kk: by_kind[kk])
-    # kernel launches: the tensor-core propagation records one entry per level for its 8 octant launches
-    n_dom = sum(8 if kind == "prop_tc" else 1 for kind, _, _ in stages if kind == dom)
+    # kernel launches: both propagation kinds record one entry per level for their 8 octant launches
+    n_dom = sum(8 if kind in ("prop_tc", "prop_cs") else 1 for kind, _, _ in stages if kind == dom)
     dom_ms = by_kind[dom]
     achieved = flops_of[dom] / (dom_ms * 1e-3) / 1e12
     sm_mhz = clk["sm_max_mhz"] or 2070.0
@@ -517,43 +517,43 @@ def run_ours(args):
                           f"orders ({Ps},{Pang},{Pang}), factor mode {args.factor_mode}; {t_cpu:.1f} s each",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
-        # ---- the corrected operator: rectangular-polar correction built on the GPU, applied by K5 in
-        # every apply (the operator GMRES uses in the sound-soft solve) ----
-        from paper_2112_06316_gb300 import rp_correction
-        from workloads import patch_node_index
+    # ---- the corrected operator: rectangular-polar correction built on the GPU, applied by K5 in
+    # every apply (the operator GMRES uses in the sound-soft solve) ----
+    from paper_2112_06316_gb300 import rp_correction
+    from workloads import patch_node_index
 
-        t0 = time.perf_counter()
-        rpc = rp_correction(s.points, s.normals, s.weights, patch_node_index(s), 8, k, k,
-                            delta=math.pi / (2 * (args.n // 8)), device=True)
-        rp_s = time.perf_counter() - t0
-        nnz = int(rpc[0][-1])
-        t0 = time.perf_counter()
-        plan.set_correction(*rpc)
-        attach_s = time.perf_counter() - t0
-        del rpc
-        t_corr = timed(lambda: plan.apply(sig32, out=y32), max(5, args.steps // 4), 2)
-        plan.set_profiling(True)
-        kspmv = []
-        for _ in range(5):
-            plan.apply(sig32, out=y32)
-            kspmv += [t for kd, _, t in plan.stage_times() if kd == "correction"]
-        plan.set_profiling(False)
-        k5_ms = float(np.median(kspmv))
-        k5_bytes = nnz * 12 + N * nrhs * 16  # complex64 value + int32 column per entry; sigma read, y updated
-        hbm = None
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                hbm = float(json.load(f)["hbm_gbs"])
-        except (OSError, ValueError, KeyError):
-            hbm = 6800.0
-        out["corrected_apply"] = {
-            "value": N * nrhs / (float(np.mean(t_corr)) * 1e3), "unit": UNIT, "ms_per_step": float(np.mean(t_corr)),
-            "correction_nnz": nnz, "rp_precompute_gpu_s": round(rp_s, 2), "attach_s": round(attach_s, 2),
-            "k_spmv": {"ms": k5_ms, "bytes_model": "nnz x 12 B + N x nrhs x 16 B", "bytes": k5_bytes,
-                       "GBps": k5_bytes / (k5_ms * 1e-3) / 1e9, "peak_GBps": hbm,
-                       "frac": k5_bytes / (k5_ms * 1e-3) / 1e9 / hbm}}
-        out["gpu_launches"] += (launches_per_apply + 1) * (len(t_corr) + 5)
-        plan.set_correction(np.zeros(N + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, complex))
+    t0 = time.perf_counter()
+    rpc = rp_correction(s.points, s.normals, s.weights, patch_node_index(s), 8, k, k,
+                        delta=math.pi / (2 * (args.n // 8)), device=True)
+    rp_s = time.perf_counter() - t0
+    nnz = int(rpc[0][-1])
+    t0 = time.perf_counter()
+    plan.set_correction(*rpc)
+    attach_s = time.perf_counter() - t0
+    del rpc
+    t_corr = timed(lambda: plan.apply(sig32, out=y32), max(5, args.steps // 4), 2)
+    plan.set_profiling(True)
+    kspmv = []
+    for _ in range(5):
+        plan.apply(sig32, out=y32)
+        kspmv += [t for kd, _, t in plan.stage_times() if kd == "correction"]
+    plan.set_profiling(False)
+    k5_ms = float(np.median(kspmv))
+    k5_bytes = nnz * 12 + N * nrhs * 16  # complex64 value + int32 column per entry; sigma read, y updated
+    hbm = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        hbm = 6800.0
+    out["corrected_apply"] = {
+        "value": N * nrhs / (float(np.mean(t_corr)) * 1e3), "unit": UNIT, "ms_per_step": float(np.mean(t_corr)),
+        "correction_nnz": nnz, "rp_precompute_gpu_s": round(rp_s, 2), "attach_s": round(attach_s, 2),
+        "k_spmv": {"ms": k5_ms, "bytes_model": "nnz x 12 B + N x nrhs x 16 B", "bytes": k5_bytes,
+                   "GBps": k5_bytes / (k5_ms * 1e-3) / 1e9, "peak_GBps": hbm,
+                   "frac": k5_bytes / (k5_ms * 1e-3) / 1e9 / hbm}}
+    out["gpu_launches"] += (launches_per_apply + 1) * (len(t_corr) + 5)
+    plan.set_correction(np.zeros(N + 1, np.int64), np.zeros(0, np.int32), np.zeros(0, complex))
     if not args.no_batch:
         from paper_2112_06316_gb300 import Group
         from workloads import random_density as _rd, scatterer_batch
