@@ -445,6 +445,41 @@ def run_ours(args):
                             "Gpairs_per_s": N * nrhs * plane.shape[0] / (t_nf * 1e6)},
         "note": "direct sums over all N sources (ifgf_far_field, ifgf_field), mixed precision"}
 
+    # ---- the same far field from the level-3 interpolants (plan option far_field=1: the is = 0 cone
+    # segments of level 3 kept relevant), against the direct sum above ----
+    t0 = time.perf_counter()
+    plan_ff = Plan(s.points, s.normals, s.weights, Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0,
+                                                          factor_mode=args.factor_mode, far_field=1))
+    ff_plan_s = time.perf_counter() - t0
+    if args.tc_fill is not None:
+        plan_ff.set_tc_fill(args.tc_fill)
+    if args.tc_engine is not None:
+        plan_ff.set_tc_engine(args.tc_engine)
+    ffi = torch.empty_like(ff)
+    t_ffi = float(np.mean(timed(lambda: plan_ff.far_field_ifgf(sig32, xh, out=ffi), k_off, 2)))
+    t_app_ff = float(np.mean(timed(lambda: plan_ff.apply(sig32, out=y32), k_off, 2)))
+    plan_ff.set_profiling(True)
+    plan_ff.apply(sig32, out=y32)
+    ff_apply_launches = launches_of(plan_ff.stage_times())
+    plan_ff.far_field_ifgf(sig32, xh, out=ffi)
+    up_stages = plan_ff.stage_times()
+    plan_ff.set_profiling(False)
+    torch.cuda.synchronize()
+    d_ff = (ffi - ff).abs()
+    off_surface["far_field_ifgf"] = {
+        "targets": int(xh.shape[0]), "ms_per_step": t_ffi, "speedup_vs_direct_sum": t_ff / t_ffi,
+        "rel_err_vs_direct_sum_l2": float(torch.linalg.vector_norm(ffi - ff) / torch.linalg.vector_norm(ff)),
+        "rel_err_vs_direct_sum_max": float(d_ff.max() / ff.abs().max()),
+        "upward_pass_ms": round(sum(t for _, _, t in up_stages), 4),
+        "apply_ms_of_the_far_field_plan": t_app_ff, "plan_build_s": round(ff_plan_s, 2),
+        "nrc_level3": {"with_far_field_cones": plan_ff.info()["nrc"][3], "without": info["nrc"][3]},
+        "note": "ifgf_far_field_ifgf: upward pass (leaf expansions, propagation) plus one warp per direction "
+                "over the level-3 boxes, mixed precision"}
+    assert plan_ff.missed_lookups() == 0
+    k_ffi = k_off + 2 + 1  # timed calls and warm-up, and the profiled call
+    ff_launches = launches_of(up_stages) + 1  # the upward pass and k_far_ifgf
+    plan_ff.close()
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -459,7 +494,7 @@ def run_ours(args):
            "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
            # gather, sum and (when the sources are split into chunks) the reduction per off-surface call
            "gpu_launches": launches_per_apply * (args.steps + len(t4)) + len(adj_stages) * max(3, args.steps // 4)
-                           + 2 * 3 * k_off,
+                           + 2 * 3 * k_off + ff_launches * k_ffi + ff_apply_launches * (k_off + 3),
            "clocks": clk}
 
     if not args.quick:

@@ -84,6 +84,11 @@ typedef struct {
                              (Eq. RelevantCones) so that a point within this fraction of a cone
                              boundary marks both neighbours; keeps the FP32 classification
                              inside the relevant set.  Default 1e-4; 0 = exact marking. */
+    int far_field;        /* 1: also keep every level-3 cone segment with is = 0 (all directions
+                             of the s -> 0 end of the cone grid) relevant, and the segments of
+                             the finer levels that feed them, so that ifgf_far_field_ifgf can
+                             evaluate the far-field pattern from the level-3 interpolants.
+                             Adds work to every apply of the plan.  Default 0. */
 } ifgf_params;
 
 /* Plan statistics (ifgf_plan_info). Arrays are indexed by level d (0..IFGF_MAXD). */
@@ -329,6 +334,24 @@ ifgf_status ifgf_field(ifgf_plan *plan, const void *sigma_dev, const double *x_d
  * the limit of u(R xhat) R e^{-ikR} as R grows.  Arguments as ifgf_field. */
 ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
                            void *out_dev, int nrhs, ifgf_precision prec, void *stream);
+
+/* Far-field pattern of Eq. FarField through the IFGF factorisation (Section 3.4 with the
+ * limit s -> 0 of Eq. defparametrizationins).  For x = R xhat the centred factor of a level-3
+ * box B satisfies R e^{-ikR} e^{ik|x - y_B|} / (4 pi |x - y_B|) -> e^{-ik xhat.y_B} / (4 pi),
+ * while s = h_3 / |x - y_B| -> 0 and the direction of x - y_B tends to xhat, so
+ *   u_inf(xhat) = sum over level-3 boxes B of e^{-ik xhat.y_B} / (4 pi) F_B(s = 0, xhat),
+ * where F_B is B's interpolated analytic factor (the combined factor, or the W13 member of the
+ * split pair on a split level; the W2 member decays one order faster and drops out).  Runs the
+ * leaf expansions and the propagation of an apply (not the cousin interpolation, the near
+ * field or the sparse correction), then one warp per direction sums the level-3 interpolants
+ * at local coordinate s = -1 of segment is = 0.  Cost: the upward pass plus M x (level-3 boxes)
+ * x Ps Pang^2 per right-hand side, against N M for ifgf_far_field.
+ *   plan:     created with params.far_field = 1 (IFGF_EINVAL otherwise)
+ *   sigma_dev, xhat_dev, M, out_dev, nrhs, prec, stream: as ifgf_far_field (xhat unit vectors,
+ *             [M][3] FP64; out [nrhs][M] complex128 for IFGF_FP64, complex64 for IFGF_MIXED).
+ * Uses (and may grow) the plan's own workspace, like ifgf_apply. */
+ifgf_status ifgf_far_field_ifgf(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
+                                void *out_dev, int nrhs, ifgf_precision prec, void *stream);
 
 /* ---- batched applies over many plans (one CUDA graph) ----------------------
  * A group applies several plans (e.g. many scatterers of uneven size, each with

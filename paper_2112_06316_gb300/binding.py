@@ -39,6 +39,7 @@ class CParams(ctypes.Structure):
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
         ("cone_band", ctypes.c_double),
+        ("far_field", ctypes.c_int),
     ]
 
 
@@ -85,6 +86,7 @@ _SIGS = [
     ("ifgf_free", None, [_VP]),
     ("ifgf_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_far_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_far_field_ifgf", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
@@ -149,6 +151,7 @@ class Params:
     root_center: tuple = (0.0, 0.0, 0.0)
     root_side: float = 0.0
     cone_band: float = 1e-4
+    far_field: int = 0
 
     def to_c(self) -> CParams:
         p = CParams()
@@ -162,6 +165,7 @@ class Params:
             p.root_center[a] = self.root_center[a]
         p.root_side = self.root_side
         p.cone_band = self.cone_band
+        p.far_field = self.far_field
         return p
 
 
@@ -395,6 +399,11 @@ class Plan:
     def far_field(self, sigma, directions, out=None, stream=None):
         """Far-field pattern (``ifgf_far_field``) at unit directions (M, 3)."""
         return self._eval_off_surface(lib().ifgf_far_field, sigma, directions, out, stream)
+
+    def far_field_ifgf(self, sigma, directions, out=None, stream=None):
+        """Far-field pattern from the IFGF level-3 interpolants (``ifgf_far_field_ifgf``); the
+        plan must have been created with ``Params(far_field=1)``."""
+        return self._eval_off_surface(lib().ifgf_far_field_ifgf, sigma, directions, out, stream)
 
     def gmres(self, rhs, x0=None, restart: int = 50, maxit: int = 200, tol: float = 1e-6,
               precision: int = FP64, stream=None):

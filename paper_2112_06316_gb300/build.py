@@ -49,11 +49,14 @@ def _compile(src: str, flags: list[str]) -> str:
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if src.endswith(".cu"):
-        cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3",
+        # a missing return (diagnostic 940) is an error: falling off the end of a value-returning
+        # function or lambda is undefined behaviour that the optimiser exploits
+        cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--diag-error=940",
+               "-Xcompiler", "-fPIC,-fopenmp,-O3,-Werror=return-type",
                "-Xptxas", "-O3", *inc, *flags, "-c", src, "-o", obj]
     else:
-        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-I", _cuda_include(), *flags, "-c", src,
-               "-o", obj]
+        cmd = ["g++", "-O3", "-std=c++17", "-fPIC", "-fopenmp", "-Werror=return-type", *inc, "-I", _cuda_include(),
+               *flags, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

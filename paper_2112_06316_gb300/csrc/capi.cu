@@ -35,6 +35,7 @@ void ifgf_params_default(ifgf_params *p, double k) {
     p->identity_coef = 0.5;
     p->root_side = 0.0;
     p->cone_band = 1e-4;
+    p->far_field = 0;
 }
 
 const char *ifgf_supported_orders(void) { return "3x5,4x6,5x7,5x8,6x8"; }
@@ -65,7 +66,8 @@ static ifgf_status validate(const double *xyz, const double *normals, const doub
         return IFGF_EINVAL;
     }
     if (pr.nC0 < 1 || pr.nS0 < 1 || pr.nC0 > 64 || pr.nS0 > 64 || pr.cone_rule < 0 || pr.cone_rule > 1 ||
-        pr.factor_mode < 0 || pr.factor_mode > 2 || !(pr.cone_band >= 0) || !std::isfinite(pr.identity_coef)) {
+        pr.factor_mode < 0 || pr.factor_mode > 2 || !(pr.cone_band >= 0) || !std::isfinite(pr.identity_coef) ||
+        pr.far_field < 0 || pr.far_field > 1) {
         set_error("invalid cone or factor parameters");
         return IFGF_EINVAL;
     }

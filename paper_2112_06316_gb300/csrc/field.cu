@@ -12,6 +12,9 @@
 // into chunks (blockIdx.y) whose partial sums a second kernel adds in a fixed
 // order, so results are deterministic.
 //
+// ifgf_far_field_ifgf instead takes the far-field pattern from the IFGF level-3 interpolants
+// (the s -> 0 limit of the factorisation; kernel k_far_ifgf beside the forward kernels).
+//
 // Mixed precision keeps the phase exact to ~1e-7 cycles without FP64 per pair:
 // per (target, leaf box) the box part of the phase is formed once (far field:
 // a two-float product with the exact half-integer box offset; potential: FP64
@@ -408,6 +411,63 @@ static ifgf_status field_run(ifgf_plan *plan, const void *sigma, const double *t
     return IFGF_OK;
 }
 
+ifgf_status run_apply(Plan &p, const void *sigma, void *y, int nrhs, int prec, cudaStream_t s);
+template <int PS, int PA>
+ifgf_status run_far_t(Plan &p, const double *xhat, long long M, void *out, int nrhs, int prec, cudaStream_t s);
+extern template ifgf_status run_far_t<3, 5>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
+extern template ifgf_status run_far_t<4, 6>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
+extern template ifgf_status run_far_t<5, 7>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
+extern template ifgf_status run_far_t<5, 8>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
+extern template ifgf_status run_far_t<6, 8>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
+
+// Far-field pattern through the IFGF factorisation: the upward pass of an apply (leaf
+// expansions and propagation into the level-3 cone values), then the s -> 0 evaluation.
+static ifgf_status far_ifgf_run(ifgf_plan *plan, const void *sigma, const double *xhat, int64_t M, void *out,
+                                int nrhs, ifgf_precision prec, void *stream) {
+    clear_error();
+    if (!plan) {
+        set_error("null plan");
+        return IFGF_EINVAL;
+    }
+    if (nrhs < 0 || M < 0 || M > (int64_t)0x7fffffff) {
+        set_error("invalid nrhs (%d) or direction count (%lld)", nrhs, (long long)M);
+        return IFGF_EINVAL;
+    }
+    if (prec != IFGF_FP64 && prec != IFGF_MIXED) {
+        set_error("unknown precision %d", (int)prec);
+        return IFGF_EINVAL;
+    }
+    Plan &p = plan->p;
+    if (!p.prm.far_field) {
+        set_error("the plan was created without params.far_field = 1: its level-3 cone values do not reach s = 0");
+        return IFGF_EINVAL;
+    }
+    if (nrhs == 0 || M == 0) return IFGF_OK;
+    if (!sigma || !xhat || !out) {
+        set_error("null device pointer");
+        return IFGF_EINVAL;
+    }
+    if (out == sigma || (const void *)xhat == out) {
+        set_error("out must not alias sigma or the directions");
+        return IFGF_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p.upward_only = true;
+    ifgf_status st = run_apply(p, sigma, nullptr, nrhs, (int)prec, s);
+    p.upward_only = false;
+    if (st != IFGF_OK) return st;
+#define IFGF_CASE(a, b) \
+    if (p.Ps == a && p.Pang == b) return run_far_t<a, b>(p, xhat, M, out, nrhs, (int)prec, s);
+    IFGF_CASE(3, 5)
+    IFGF_CASE(4, 6)
+    IFGF_CASE(5, 7)
+    IFGF_CASE(5, 8)
+    IFGF_CASE(6, 8)
+#undef IFGF_CASE
+    set_error("orders Ps=%d Pang=%d not compiled", p.Ps, p.Pang);
+    return IFGF_EUNSUPPORTED;
+}
+
 }  // namespace ifgf
 
 using namespace ifgf;
@@ -422,6 +482,11 @@ ifgf_status ifgf_field(ifgf_plan *plan, const void *sigma_dev, const double *x_d
 ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
                            void *out_dev, int nrhs, ifgf_precision prec, void *stream) {
     return field_run(plan, sigma_dev, xhat_dev, M, out_dev, nrhs, prec, stream, true);
+}
+
+ifgf_status ifgf_far_field_ifgf(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
+                                void *out_dev, int nrhs, ifgf_precision prec, void *stream) {
+    return far_ifgf_run(plan, sigma_dev, xhat_dev, M, out_dev, nrhs, prec, stream);
 }
 
 }  // extern "C"

@@ -3555,50 +3555,67 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
     // on F_d: they run on the plan's auxiliary stream beside the leaf / propagation chain (fork after
     // the gather, one event per finished level, join before the scatter).  The auxiliary stream runs
     // near, then cousin D, ..., 3 in order, so the field u has one writer at a time.
-    const bool par = !p.profile && p.aux;
+    // upward pass only (far-field evaluation): leaf expansions and propagation, nothing that writes u
+    const bool down = !p.upward_only;
+    const bool par = !p.profile && p.aux && down;
     const cudaStream_t sb = par ? p.aux : s;
+    // fork / join record the first failure of their event calls (checked after the join); they
+    // return nothing, so that every path through them is well defined
+    cudaError_t dep_err = cudaSuccess;
     auto fork = [&](int slot) {
-        if (par) {
-            CK(cudaEventRecord(p.dep[slot], s));
-            CK(cudaStreamWaitEvent(sb, p.dep[slot], 0));
+        if (par && dep_err == cudaSuccess) {
+            dep_err = cudaEventRecord(p.dep[slot], s);
+            if (dep_err == cudaSuccess) dep_err = cudaStreamWaitEvent(sb, p.dep[slot], 0);
         }
     };
     auto join = [&]() {
-        if (par) {
-            CK(cudaEventRecord(p.dep[Plan::kMaxDep - 1], sb));
-            CK(cudaStreamWaitEvent(s, p.dep[Plan::kMaxDep - 1], 0));
+        if (par && dep_err == cudaSuccess) {
+            dep_err = cudaEventRecord(p.dep[Plan::kMaxDep - 1], sb);
+            if (dep_err == cudaSuccess) dep_err = cudaStreamWaitEvent(s, p.dep[Plan::kMaxDep - 1], 0);
         }
     };
     if (prec == IFGF_FP64) {
         k_gather<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w64, (const double2 *)sigma, (double2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
         fork(0);
-        k_near64<<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const double2 *)p.ws.a, (double2 *)p.ws.u);
-        prof_mark(p, sb, kStNear, D);
+        if (down) {
+            k_near64<<<nblk(N), kBlock, 0, sb>>>(ca, L[D], (const double2 *)p.ws.a, (double2 *)p.ws.u);
+            prof_mark(p, sb, kStNear, D);
+        }
         if (L[D].nrc) {
             k_leaf64<PS, PA><<<nblk(L[D].nrc * P), kBlock, 0, s>>>(ca, L[D], tb, (const double2 *)p.ws.a);
             prof_mark(p, s, kStLeaf, D);
         }
         fork(1);
-        k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], p.d_box_of[D], tb, (double2 *)p.ws.u);
-        prof_mark(p, sb, kStCousin, D);
+        if (down) {
+            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], p.d_box_of[D], tb, (double2 *)p.ws.u);
+            prof_mark(p, sb, kStCousin, D);
+        }
         for (int d = D; d >= 4; d--) {
             if (L[d - 1].nrc) {
                 k_prop64<PS, PA><<<nblk(L[d - 1].nrc * P), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
             fork(2 + D - d);
-            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[d - 1], p.d_box_of[d - 1], tb, (double2 *)p.ws.u);
-            prof_mark(p, sb, kStCousin, d - 1);
+            if (down) {
+                k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[d - 1], p.d_box_of[d - 1], tb,
+                                                               (double2 *)p.ws.u);
+                prof_mark(p, sb, kStCousin, d - 1);
+            }
         }
         join();
-        k_scatter<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const double2 *)sigma,
-                                                       (const double2 *)p.ws.u, (double2 *)y);
-        prof_mark(p, s, kStScatter, 0);
+        CK(dep_err);
+        if (down) {
+            k_scatter<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef,
+                                                           (const double2 *)sigma, (const double2 *)p.ws.u,
+                                                           (double2 *)y);
+            prof_mark(p, s, kStScatter, 0);
+        }
     } else {
         const bool rb1 = nrhs == 1 || p.rhs_block == 1;
         float2 *u32 = (float2 *)p.ws.u;
         auto cousin = [&](int d) {
+            if (!down) return;
             const int nch = p.ncchunk[d];
             if (p.cs_ok && p.interp_engine == 1) {
                 const int ni = p.ncs_item[d];
@@ -3627,12 +3644,12 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         k_gather<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w32, (const float2 *)sigma, (float2 *)p.ws.a);
         prof_mark(p, s, kStGather, 0);
         fork(0);
-        {
+        if (down) {
             const unsigned gn = (unsigned)((p.nnchunk + kNearWarps - 1) / kNearWarps);
             if (rb1) k_near32<1><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
             else k_near32<kRB><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
         }
-        prof_mark(p, sb, kStNear, D);
+        if (down) prof_mark(p, sb, kStNear, D);
         if (L[D].nrc) {
             const unsigned g = nblk(L[D].nrc * P);
             const float2 *a32 = (const float2 *)p.ws.a;
@@ -3714,9 +3731,12 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             cousin(d - 1);
         }
         join();
-        k_scatter<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, (const float2 *)sigma,
-                                                      (const float2 *)p.ws.u, (float2 *)y);
-        prof_mark(p, s, kStScatter, 0);
+        CK(dep_err);
+        if (down) {
+            k_scatter<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef,
+                                                          (const float2 *)sigma, (const float2 *)p.ws.u, (float2 *)y);
+            prof_mark(p, s, kStScatter, 0);
+        }
     }
     CK(cudaGetLastError());
     return IFGF_OK;
@@ -3843,6 +3863,118 @@ inline long long dk_partials_needed(const Plan &p) {
     long long n = nblk(p.N) + nblk(p.lv[p.D].nrc * p.P);
     for (int d = 3; d <= p.D; d++) n += p.lv[d].nrc;
     return n;
+}
+
+// ============================================================================
+// far-field pattern from the level-3 interpolants (Eq. FarField, Section 3.4)
+// ============================================================================
+// With x = R xhat, R e^{-ikR} times the centred factor e^{ik|x - y_B|} / (4 pi |x - y_B|) of a
+// level-3 box tends to e^{-ik xhat.y_B} / (4 pi), s = h_3 / |x - y_B| tends to 0 and the
+// direction of x - y_B to xhat, so u_inf(xhat) = sum_B e^{-ik xhat.y_B} / (4 pi) F_B(0, xhat).
+// Every box shares the cone (is = 0, it, ip) of xhat and the interpolation weights (local s
+// coordinate -1), so the sum over boxes is one weighted reduction of the boxes' node values.
+// One warp per direction: lane l holds the weights of nodes l, l + 32, ... and reads those
+// nodes of each box (coalesced), scales its partial by the box's phase (from shared memory),
+// and the warp adds its lanes at the end.  FP64 path: FP64 throughout; mixed path: node sums
+// in FP32 (the stored values are FP32), phases and the sum over boxes in FP64.
+constexpr int kFarWarps = 4;
+constexpr int kFarMaxBox = 64;  // level 3 has 4^3 boxes (side L / 4)
+
+template <int PS, int PA, typename TF>
+__global__ void __launch_bounds__(kFarWarps * 32)
+    k_far_ifgf(CommonArgs ca, LevelArgs L, ChebTab tb, const typename C2T<TF>::type *__restrict__ F,
+               const double *__restrict__ xhat, long long M, int fac, typename C2T<TF>::type *__restrict__ out) {
+    constexpr int P = PS * PA * PA, NJ = (P + 31) / 32;
+    __shared__ double2 s_ph[kFarWarps][kFarMaxBox];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long j = (long long)blockIdx.x * kFarWarps + warp;
+    if (j >= M) return;  // whole warp
+    const double e0 = xhat[3 * j], e1 = xhat[3 * j + 1], e2 = xhat[3 * j + 2];
+    // direction of xhat on the cone grid (theta, phi as in classify64), segment is = 0
+    double th = atan2(sqrt(e0 * e0 + e1 * e1), e2);
+    double ph = atan2(e1, e0);
+    if (ph < 0) ph += 2.0 * kPi;
+    if (ph >= 2.0 * kPi) ph = 0.0;
+    const double ut = snap64(th / L.dth), up = snap64(ph / L.dph);
+    const int it = max(min((int)floor(ut), L.nC - 1), 0), ip = max(min((int)floor(up), L.nph - 1), 0);
+    const int cone = it * L.nph + ip;
+    double Ls[PS], Lt[PA], Lp[PA];
+    lagrange<PS, double>(-1.0, tb.xs, tb.cs, Ls);
+    lagrange<PA, double>(2.0 * (ut - it) - 1.0, tb.xa, tb.ca, Lt);
+    lagrange<PA, double>(2.0 * (up - ip) - 1.0, tb.xa, tb.ca, Lp);
+    TF w[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; jj++) {
+        const int n = lane + 32 * jj;
+        w[jj] = n < P ? (TF)(Ls[n / (PA * PA)] * Lt[(n / PA) % PA] * Lp[n % PA]) : TF(0);
+    }
+    const double c4 = 1.0 / (4.0 * kPi);
+    for (int b = lane; b < L.nbox; b += 32) {
+        double y0[3];
+        center64(ca, L, b, y0);
+        double sn, cs;
+        sincos(-ca.k * (e0 * y0[0] + e1 * y0[1] + e2 * y0[2]), &sn, &cs);
+        s_ph[warp][b] = make_double2(c4 * cs, c4 * sn);
+    }
+    __syncwarp();
+    for (int q = 0; q < ca.nrhs; q++) {
+        double ar = 0.0, ai = 0.0;
+        for (int b = 0; b < L.nbox; b++) {
+            const int rc = L.cone_map[(long long)b * L.ncone + cone];
+            if (rc < 0) {  // outside the relevant set: the plan lacks the far-field segments
+                if (lane == 0 && q == 0) atomicAdd(ca.missed, 1ULL);
+                continue;
+            }
+            const typename C2T<TF>::type *f = F + (((long long)q * L.nrc + rc) * L.nfac + fac) * ca.Pstride;
+            TF vr = TF(0), vi = TF(0);
+#pragma unroll
+            for (int jj = 0; jj < NJ; jj++) {
+                const int n = lane + 32 * jj;
+                if (n < P) {
+                    const typename C2T<TF>::type v = f[n];
+                    vr += w[jj] * v.x;
+                    vi += w[jj] * v.y;
+                }
+            }
+            const double2 e = s_ph[warp][b];
+            ar += e.x * (double)vr - e.y * (double)vi;
+            ai += e.x * (double)vi + e.y * (double)vr;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) {
+            typename C2T<TF>::type r;
+            r.x = (TF)ar;
+            r.y = (TF)ai;
+            out[(long long)q * M + j] = r;
+        }
+    }
+}
+
+// launch of the far-field evaluation on the level-3 cone values that the upward pass left in
+// the plan's workspace
+template <int PS, int PA>
+ifgf_status run_far_t(Plan &p, const double *xhat, long long M, void *out, int nrhs, int prec, cudaStream_t s) {
+    if (p.lv[3].nbox > kFarMaxBox) {
+        set_error("far field: %d level-3 boxes (at most %d)", p.lv[3].nbox, kFarMaxBox);
+        return IFGF_EINTERNAL;
+    }
+    CommonArgs ca = common_args(p, nrhs);
+    ChebTab tb = cheb_tab(p);
+    LevelArgs L3 = level_args(p, 3, p.ws.F[3]);
+    const int fac = L3.split ? 1 : 0;  // the W13 member of a split pair; W2 drops out
+    const unsigned g = (unsigned)((M + kFarWarps - 1) / kFarWarps);
+    if (prec == IFGF_FP64)
+        k_far_ifgf<PS, PA, double><<<g, kFarWarps * 32, 0, s>>>(ca, L3, tb, (const double2 *)p.ws.F[3], xhat, M, fac,
+                                                                (double2 *)out);
+    else
+        k_far_ifgf<PS, PA, float><<<g, kFarWarps * 32, 0, s>>>(ca, L3, tb, (const float2 *)p.ws.F[3], xhat, M, fac,
+                                                               (float2 *)out);
+    CK(cudaGetLastError());
+    return IFGF_OK;
 }
 
 }  // namespace ifgf

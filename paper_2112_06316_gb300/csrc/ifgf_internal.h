@@ -220,6 +220,10 @@ struct Plan {
         const int *list;
     };
 
+    // set for the duration of ifgf_far_field_ifgf: the forward launch sequence stops after the
+    // leaf expansions and the propagation (no near field, cousin interpolation or scatter)
+    bool upward_only = false;
+
     // optional per-launch timing (events recorded on the apply stream; the apply then runs on
     // that stream alone so that every launch has its own interval)
     bool profile = false;

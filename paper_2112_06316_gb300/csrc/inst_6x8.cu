@@ -8,4 +8,5 @@ template ifgf_status run_adjoint_t<6, 8>(Plan &, const void *, void *, int, int,
                                               void **, void *const *, double *);
 template ifgf_status run_dk_t<6, 8>(Plan &, int, int, cudaStream_t, const void *, void **, double *,
                                          long long *);
+template ifgf_status run_far_t<6, 8>(Plan &, const double *, long long, void *, int, int, cudaStream_t);
 }  // namespace ifgf

@@ -446,6 +446,10 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
 #pragma omp for schedule(dynamic, 1)
             for (int b = 0; b < L.nbox; b++) {
                 std::fill(bits.begin(), bits.end(), 0ULL);
+                // far-field option: s = h / r -> 0 lies in the segments with is = 0 (cone ids
+                // 0 .. nC nph - 1), kept in every direction at level 3
+                if (d == 3 && prm.far_field)
+                    for (int c = 0; c < L.nC * L.nph; c++) bits[c >> 6] |= 1ULL << (c & 63);
                 for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
                     int cb = L.co_list[c];
                     for (int s = L.start[cb]; s < L.start[cb + 1]; s++) mark_point(p, L, b, &xs[3 * s], tau, bits.data());

@@ -178,3 +178,97 @@ def test_operator_wrapper_is_the_plan(B, small):
     sig = torch.from_numpy(random_density(s.N, 1, 21)).cuda()
     assert torch.equal(op.apply(sig), plan.apply(sig))
     op.close()
+
+
+# ---------------------------------------------------------------- far field from the IFGF interpolants
+FAR_CASES = {
+    # name: (geometry, params, nrhs, tensor-core fill)
+    "sphere1_D3_split_3x5": (lambda: (cube_sphere(24, 6), math.pi), dict(levels=3), 2, None),
+    "sphere3_D4_combined_5x8": (lambda: sphere_workload(24, 6, 3.0), dict(levels=4, Ps=5, Pang=8), 1, None),
+    "sphere4_D5_split_tc_5x8": (lambda: sphere_workload(48, 6, 4.0), dict(levels=5, Ps=5, Pang=8, factor_mode=2),
+                                3, 0.0),
+    "sphere3_D4_6x8": (lambda: sphere_workload(32, 8, 3.0), dict(levels=4, Ps=6, Pang=8), 1, None),
+}
+
+
+@pytest.mark.parametrize("case", list(FAR_CASES))
+def test_far_field_ifgf_vs_oracle(B, oracle_lib, case):
+    """ifgf_far_field_ifgf against the oracle's far field from the level-3 interpolants,
+    element by element (FP64 <= 1e-10, mixed <= 1e-5), and against the plain quadrature sum
+    of Eq. FarField within the IFGF error of the orders used; repeatable bit for bit; an
+    ordinary apply on the same plan afterwards is unchanged."""
+    geo, kw, nrhs, fill = FAR_CASES[case]
+    s, k = geo()
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, far_field=1, **kw))
+    if fill is not None:
+        plan.set_tc_fill(fill)
+    sig = random_density(s.N, nrhs, 41)
+    rng = np.random.default_rng(42)
+    xh = unit(rng.normal(size=(333, 3)))
+    xh[:6] = [[0, 0, 1], [0, 0, -1], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0]]  # cone-grid poles and seams
+    ref, info = oracle_lib.ifgf_far_field(s.points, s.normals, s.weights,
+                                          oracle_lib.IFGFParams(k=k, **kw), sig, xh)
+    assert info["D"] == plan.info()["D"]
+    y64 = run(plan, "far_field_ifgf", sig, xh, np.complex128)
+    y32 = run(plan, "far_field_ifgf", sig, xh, np.complex64)
+    assert plan.missed_lookups() == 0
+    check(y64, ref, 1e-10, "fp64")
+    check(y32, ref, 1e-5, "mixed")
+    direct = oracle_lib.far_field(s.points, s.normals, s.weights, k, k, sig, xh)
+    bound = 3e-3 if kw.get("Ps", 3) == 3 else 1e-4
+    assert rel(y64, direct) < bound
+    assert np.array_equal(run(plan, "far_field_ifgf", sig, xh, np.complex64), y32)
+    # the upward-only pass leaves the plan's apply as it was
+    sg = torch.from_numpy(sig.astype(np.complex128)).cuda()
+    ya = plan.apply(sg).cpu().numpy()
+    yr, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k, identity_coef=0.5, **kw), sig)
+    check(ya, yr, 1e-10, "apply after far field")
+    plan.close()
+
+
+def test_far_field_ifgf_mie(B):
+    """Exact Mie density on the unit sphere (k = pi): the IFGF far field on a grid of Eq.
+    SphereGrid against the closed form (Eq. FarFieldRelErr), at orders (5, 8)."""
+    s = cube_sphere(32, 8)
+    k = math.pi
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8, far_field=1))
+    phi = mie.density(s.points, k, k)
+    xh = mie.sphere_grid(41, 41)
+    ue = mie.far_field(xh, k)
+    u64 = run(plan, "far_field_ifgf", phi, xh, np.complex128)
+    u32 = run(plan, "far_field_ifgf", phi, xh, np.complex64)
+    assert mie.far_field_error(ue, u64) < 2e-5 and mie.far_field_error(ue, u32) < 3e-5
+    plan.close()
+
+
+def test_far_field_ifgf_edge_cases(B):
+    s = cube_sphere(16, 8)
+    k = 2 * math.pi
+    lib = B.lib()
+    plain = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, levels=3))
+    sig = torch.from_numpy(random_density(s.N, 1, 43)).cuda()
+    xh = torch.from_numpy(unit(np.random.default_rng(44).normal(size=(5, 3)))).cuda()
+    out = torch.zeros((1, 5), dtype=torch.complex128, device="cuda")
+    # a plan without the far-field segments is refused
+    st = lib.ifgf_far_field_ifgf(plain.handle, ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(xh.data_ptr()),
+                                 ctypes.c_int64(5), ctypes.c_void_p(out.data_ptr()), ctypes.c_int(1), ctypes.c_int(0),
+                                 ctypes.c_void_p(0))
+    assert st == -1 and "far_field" in lib.ifgf_last_error().decode()
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, levels=3, far_field=1))
+    # no directions / no right-hand sides: nothing to do
+    for M, nrhs in ((0, 1), (5, 0)):
+        st = lib.ifgf_far_field_ifgf(plan.handle, ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(xh.data_ptr()),
+                                     ctypes.c_int64(M), ctypes.c_void_p(out.data_ptr()), ctypes.c_int(nrhs),
+                                     ctypes.c_int(0), ctypes.c_void_p(0))
+        assert st == 0
+    # invalid precision, aliasing output
+    st = lib.ifgf_far_field_ifgf(plan.handle, ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(xh.data_ptr()),
+                                 ctypes.c_int64(5), ctypes.c_void_p(out.data_ptr()), ctypes.c_int(1), ctypes.c_int(7),
+                                 ctypes.c_void_p(0))
+    assert st == -1
+    st = lib.ifgf_far_field_ifgf(plan.handle, ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(xh.data_ptr()),
+                                 ctypes.c_int64(5), ctypes.c_void_p(sig.data_ptr()), ctypes.c_int(1), ctypes.c_int(0),
+                                 ctypes.c_void_p(0))
+    assert st == -1
+    plain.close()
+    plan.close()
