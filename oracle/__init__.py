@@ -52,7 +52,7 @@ class OracleParams(ctypes.Structure):
         ("cone_rule", ctypes.c_int), ("factor_mode", ctypes.c_int),
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
-        ("far_field", ctypes.c_int),
+        ("far_field", ctypes.c_int), ("layer", ctypes.c_int),
     ]
 
 
@@ -79,6 +79,8 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         _lib.oracle_direct_rows.restype = ctypes.c_int
         _lib.oracle_direct_adjoint_rows.restype = ctypes.c_int
+        _lib.oracle_direct_rows_layer.restype = ctypes.c_int
+        _lib.oracle_direct_adjoint_rows_layer.restype = ctypes.c_int
         _lib.oracle_ifgf.restype = ctypes.c_int
         _lib.oracle_ifgf_far_field.restype = ctypes.c_int
         _lib.oracle_cheb_interp_1d.restype = ctypes.c_double
@@ -109,6 +111,7 @@ class IFGFParams:
     root_center: tuple = (0.0, 0.0, 0.0)
     root_side: float = 0.0
     far_field: int = 0
+    layer: int = 0  # 0 combined field, 1 double layer, 2 single layer
 
     def to_c(self) -> OracleParams:
         p = OracleParams()
@@ -122,6 +125,7 @@ class IFGFParams:
             p.root_center[a] = self.root_center[a]
         p.root_side = self.root_side
         p.far_field = self.far_field
+        p.layer = self.layer
         return p
 
 
@@ -145,8 +149,10 @@ def _dens(sigma, N):
     return np.ascontiguousarray(s, dtype=np.complex128)
 
 
-def direct(points, normals, weights, k, eta, sigma, cI=0.0, rows=None) -> np.ndarray:
-    """y_l = cI sigma_l + sum_{m != l} K(x_l, x_m) w_m sigma_m for l in rows (all if None).
+def direct(points, normals, weights, k, eta, sigma, cI=0.0, rows=None, layer=0) -> np.ndarray:
+    """y_l = cI sigma_l + sum_{m != l} K(x_l, x_m) w_m sigma_m for l in rows (all if None), with K the
+    combined field dPhi/dnu(y) - i eta Phi (layer 0), the double layer dPhi/dnu(y) (1) or the single
+    layer Phi (2).
 
     sigma: (nrhs, N) complex; returns (nrhs, len(rows)) complex128.
     """
@@ -162,8 +168,8 @@ def direct(points, normals, weights, k, eta, sigma, cI=0.0, rows=None) -> np.nda
         nrows = r.shape[0]
     out = np.zeros((nrhs, nrows), dtype=np.complex128)
     cI = complex(cI)
-    rc = lib().oracle_direct_rows(
-        ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
+    rc = lib().oracle_direct_rows_layer(
+        ctypes.c_int(layer), ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
         ctypes.c_double(cI.real), ctypes.c_double(cI.imag), ctypes.c_int(nrhs),
         s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_int64(nrows),
         None if r is None else r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -173,8 +179,8 @@ def direct(points, normals, weights, k, eta, sigma, cI=0.0, rows=None) -> np.nda
     return out
 
 
-def direct_adjoint(points, normals, weights, k, eta, g, cI=0.0, rows=None) -> np.ndarray:
-    """(A^H g)_m = conj(cI) g_m + w_m sum_{l != m} conj(K(x_l, x_m)) g_l for m in rows."""
+def direct_adjoint(points, normals, weights, k, eta, g, cI=0.0, rows=None, layer=0) -> np.ndarray:
+    """(A^H g)_m = conj(cI) g_m + w_m sum_{l != m} conj(K(x_l, x_m)) g_l for m in rows (K of `layer`)."""
     x, n, w = _geom(points, normals, weights)
     N = x.shape[0]
     s = _dens(g, N)
@@ -187,8 +193,8 @@ def direct_adjoint(points, normals, weights, k, eta, g, cI=0.0, rows=None) -> np
         nrows = r.shape[0]
     out = np.zeros((nrhs, nrows), dtype=np.complex128)
     cI = complex(cI)
-    rc = lib().oracle_direct_adjoint_rows(
-        ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
+    rc = lib().oracle_direct_adjoint_rows_layer(
+        ctypes.c_int(layer), ctypes.c_int64(N), _dptr(x), _dptr(n), _dptr(w), ctypes.c_double(k), ctypes.c_double(eta),
         ctypes.c_double(cI.real), ctypes.c_double(cI.imag), ctypes.c_int(nrhs),
         s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.c_int64(nrows),
         None if r is None else r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
@@ -361,11 +367,12 @@ def _root_side(x) -> float:
     return float((hi - lo).max() * (1 + 2.0 ** -30))
 
 
-def field(points, normals, weights, k, eta, sigma, targets) -> np.ndarray:
+def field(points, normals, weights, k, eta, sigma, targets, layer=0) -> np.ndarray:
     """Combined-layer potential of Eq. CombinedLayer at arbitrary targets x, discretised with
     the surface quadrature (the off-surface counterpart of Eq. field1):
 
-        u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m,
+        u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m
+        (layer 1: the dPhi/dnu term alone; layer 2: Phi alone),
         Phi = e^{ikr} / (4 pi r)                      (Eq. GreenFunction)
         dPhi/dnu(y) = e^{ikr} (1 - ikr) <x - y, nu(y)> / (4 pi r^3)   (Eq. double_layer)
 
@@ -387,18 +394,20 @@ def field(points, normals, weights, k, eta, sigma, targets) -> np.ndarray:
         keep = r >= tol
         rr = np.where(keep, r, 1.0)
         e = np.exp(1j * k * rr) / (4.0 * math.pi * rr)
-        K = e * (1.0 - 1j * k * rr) * dn / rr ** 2 - 1j * eta * e
+        dl = e * (1.0 - 1j * k * rr) * dn / rr ** 2
+        K = e if layer == 2 else dl if layer == 1 else dl - 1j * eta * e
         K = np.where(keep, K, 0.0)
         out[:, j0:j0 + chunk] = ws @ K.T
     return out
 
 
-def far_field(points, normals, weights, k, eta, sigma, xhat) -> np.ndarray:
+def far_field(points, normals, weights, k, eta, sigma, xhat, layer=0) -> np.ndarray:
     """Far-field pattern of Eq. FarField with the surface quadrature:
 
         u_inf(xhat) = (1 / 4 pi) sum_m [-i k <xhat, nu_m> - i eta] e^{-i k <xhat, y_m>} w_m sigma_m
 
-    (d/dnu(y) of e^{-ik xhat.y} is -ik xhat.nu(y)).  sigma: (nrhs, N); xhat: (M, 3) directions,
+    (d/dnu(y) of e^{-ik xhat.y} is -ik xhat.nu(y); layer 1 keeps that term alone, layer 2 replaces the
+    bracket by 1).  sigma: (nrhs, N); xhat: (M, 3) directions,
     used as given; returns (nrhs, M) complex128."""
     x, nu, w = _geom(points, normals, weights)
     N = x.shape[0]
@@ -409,6 +418,7 @@ def far_field(points, normals, weights, k, eta, sigma, xhat) -> np.ndarray:
     chunk = max(1, 4_000_000 // N)  # directions per block of terms (bounds the temporaries)
     for j0 in range(0, xh.shape[0], chunk):
         d = xh[j0:j0 + chunk]
-        K = (-1j * k * (d @ nu.T) - 1j * eta) * np.exp(-1j * k * (d @ x.T)) / (4.0 * math.pi)  # (c, N)
+        c = 1.0 if layer == 2 else -1j * k * (d @ nu.T) - (0.0 if layer == 1 else 1j * eta)
+        K = c * np.exp(-1j * k * (d @ x.T)) / (4.0 * math.pi)  # (c, N)
         out[:, j0:j0 + chunk] = ws @ K.T
     return out

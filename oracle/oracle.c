@@ -9,7 +9,9 @@
  * What it computes (all FP64):
  *   oracle_direct_rows:   y_l = cI s_l + sum_{m != l} K(x_l, x_m) w_m s_m   (Eq. field1 with
  *                         the combined-field kernel of Eq. CombinedLayer, Eq. GreenFunction,
- *                         Eq. double_layer; the 1/2 identity term of Eq. CombLayIE is cI)
+ *                         Eq. double_layer; the 1/2 identity term of Eq. CombLayIE is cI);
+ *                         the *_layer variants and oracle_params.layer take the double layer
+ *                         dPhi/dnu or the single layer Phi alone instead
  *   oracle_direct_adjoint_rows: (A^H g)_m = conj(cI) g_m + w_m sum_{l != m} conj(K(x_l, x_m)) g_l
  *   oracle_ifgf:          the same sum accelerated by the IFGF method of Section 3.4, in stages:
  *                         the leaf expansions of the analytic factor at the cone-segment
@@ -64,6 +66,7 @@ typedef struct {
     double identity_coef;
     double root_center[3], root_side;
     int far_field; /* 1: level 3 also keeps every segment with is = 0 (oracle_ifgf_far_field) */
+    int layer;     /* 0 combined field, 1 double layer, 2 single layer (layer_kernel) */
 } oracle_params;
 
 typedef struct {
@@ -85,16 +88,23 @@ int oracle_num_threads(void) {
 }
 
 /* ------------------------------------------------------------------------- */
-/* kernel: K(x,y) = dPhi/dnu(y) - i eta Phi  (Eq. GreenFunction, Eq. double_layer) */
+/* kernels (Eq. GreenFunction, Eq. double_layer): layer 0 the combined field K = dPhi/dnu(y) - i eta Phi
+ * (Eq. CombinedLayer), layer 1 the double layer dPhi/dnu(y), layer 2 the single layer Phi */
 
-static cplx cfie_kernel(double k, double eta, const double *x, const double *y, const double *ny) {
+static cplx layer_kernel(int layer, double k, double eta, const double *x, const double *y, const double *ny) {
     double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
     double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
     cplx e = cexp(I * k * r);
     cplx Phi = e / (4.0 * OR_PI * r);
     double dn = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
     cplx dPhi = e * (1.0 - I * k * r) * dn / (4.0 * OR_PI * r * r * r);
+    if (layer == 2) return Phi;
+    if (layer == 1) return dPhi;
     return dPhi - I * eta * Phi;
+}
+
+static cplx cfie_kernel(double k, double eta, const double *x, const double *y, const double *ny) {
+    return layer_kernel(0, k, eta, x, y, ny);
 }
 
 void oracle_kernel(double k, double eta, const double *x, const double *y, const double *ny, double *out) {
@@ -135,9 +145,9 @@ static double root_side_of(int64_t N, const double *xyz, double *center) {
 /* ------------------------------------------------------------------------- */
 /* direct sums (Eq. field1)                                                   */
 
-int oracle_direct_rows(int64_t N, const double *xyz, const double *nrm, const double *w, double k, double eta,
-                       double cI_re, double cI_im, int nrhs, const double *sigma, int64_t nrows,
-                       const int64_t *rows, double *out) {
+int oracle_direct_rows_layer(int layer, int64_t N, const double *xyz, const double *nrm, const double *w,
+                             double k, double eta, double cI_re, double cI_im, int nrhs, const double *sigma,
+                             int64_t nrows, const int64_t *rows, double *out) {
     if (N <= 0 || nrhs <= 0 || nrhs > 64) return -1;
     double c[3];
     double tol = 1e-14 * root_side_of(N, xyz, c);
@@ -154,7 +164,7 @@ int oracle_direct_rows(int64_t N, const double *xyz, const double *nrm, const do
             const double *x = xyz + 3 * l, *y = xyz + 3 * m;
             double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
             if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
-            cplx K = cfie_kernel(k, eta, x, y, nrm + 3 * m) * w[m];
+            cplx K = layer_kernel(layer, k, eta, x, y, nrm + 3 * m) * w[m];
             for (int q = 0; q < nrhs; q++) acc[q] += K * sg[(int64_t)q * N + m];
         }
         for (int q = 0; q < nrhs; q++) o[(int64_t)q * nrows + t] = cI * sg[(int64_t)q * N + l] + acc[q];
@@ -162,9 +172,15 @@ int oracle_direct_rows(int64_t N, const double *xyz, const double *nrm, const do
     return 0;
 }
 
-int oracle_direct_adjoint_rows(int64_t N, const double *xyz, const double *nrm, const double *w, double k,
-                               double eta, double cI_re, double cI_im, int nrhs, const double *g, int64_t nrows,
-                               const int64_t *rows, double *out) {
+int oracle_direct_rows(int64_t N, const double *xyz, const double *nrm, const double *w, double k, double eta,
+                       double cI_re, double cI_im, int nrhs, const double *sigma, int64_t nrows,
+                       const int64_t *rows, double *out) {
+    return oracle_direct_rows_layer(0, N, xyz, nrm, w, k, eta, cI_re, cI_im, nrhs, sigma, nrows, rows, out);
+}
+
+int oracle_direct_adjoint_rows_layer(int layer, int64_t N, const double *xyz, const double *nrm, const double *w,
+                                     double k, double eta, double cI_re, double cI_im, int nrhs, const double *g,
+                                     int64_t nrows, const int64_t *rows, double *out) {
     if (N <= 0 || nrhs <= 0 || nrhs > 64) return -1;
     double c[3];
     double tol = 1e-14 * root_side_of(N, xyz, c);
@@ -181,12 +197,18 @@ int oracle_direct_adjoint_rows(int64_t N, const double *xyz, const double *nrm, 
             const double *x = xyz + 3 * l, *y = xyz + 3 * m;
             double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
             if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
-            cplx K = conj(cfie_kernel(k, eta, x, y, nrm + 3 * m)) * w[m];
+            cplx K = conj(layer_kernel(layer, k, eta, x, y, nrm + 3 * m)) * w[m];
             for (int q = 0; q < nrhs; q++) acc[q] += K * gg[(int64_t)q * N + l];
         }
         for (int q = 0; q < nrhs; q++) o[(int64_t)q * nrows + t] = conj(cI) * gg[(int64_t)q * N + m] + acc[q];
     }
     return 0;
+}
+
+int oracle_direct_adjoint_rows(int64_t N, const double *xyz, const double *nrm, const double *w, double k,
+                               double eta, double cI_re, double cI_im, int nrhs, const double *g, int64_t nrows,
+                               const int64_t *rows, double *out) {
+    return oracle_direct_adjoint_rows_layer(0, N, xyz, nrm, w, k, eta, cI_re, cI_im, nrhs, g, nrows, rows, out);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -263,7 +285,7 @@ typedef struct {
 } olevel;
 
 typedef struct {
-    int D, P, Ps, Pang, nrhs, far_field;
+    int D, P, Ps, Pang, nrhs, far_field, layer;
     double k, eta, L, c0[3];
     const double *xyz, *nrm, *w;
     int64_t N;
@@ -501,10 +523,13 @@ static void build_relevant_cones(otree *T, int d) {
 /* analytic factors (Eq. V3, Eq. W2W2, Eq. w23)                               */
 
 /* Factors at target x for source y (normal ny) in the box with centre y0 and
- * half-diagonal h.  split = 0: out[0] = W_C = W~2 - i k W3 - i eta W1;
- * split = 1: out[0] = W2, out[1] = W13 = -i k W3 - i eta W1. */
-static void wfactors(double k, double eta, const double *x, const double *y0, double h, const double *y,
-                     const double *ny, int split, cplx *out) {
+ * half-diagonal h, for the kernel of `layer`: the double layer dPhi/dnu = E_2 W2 + E_1 (-i k W3) with
+ * E_1 W~2 = E_2 W2 (W~2 = (s/h) W2), the single layer Phi = E_1 W1 (Eq. V3, Eq. W2W2, Eq. w23).
+ * split = 0: out[0] is the one q = 1 factor (combined field W~2 - i k W3 - i eta W1, double layer
+ * W~2 - i k W3, single layer W1); split = 1: out[0] the q = 2 factor (W2, W2, 0) and out[1] the q = 1
+ * factor (-i k W3 - i eta W1, -i k W3, W1). */
+static void wfactors_layer(int layer, double k, double eta, const double *x, const double *y0, double h,
+                           const double *y, const double *ny, int split, cplx *out) {
     double dx[3] = {x[0] - y0[0], x[1] - y0[1], x[2] - y0[2]};
     double r = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
     double s = h / r;
@@ -518,12 +543,30 @@ static void wfactors(double k, double eta, const double *x, const double *y0, do
     cplx e = cexp(I * psi);
     double dn = dv[0] * ny[0] + dv[1] * ny[1] + dv[2] * ny[2];
     cplx W1 = e / a, W3 = e * dn / (a * a), W2 = e * dn / (a * a * a);
-    if (split) {
-        out[0] = W2;
-        out[1] = -I * k * W3 - I * eta * W1;
+    const cplx sl = W1;                       /* single layer, q = 1 */
+    const cplx dl2 = W2, dl1 = -I * k * W3;   /* double layer: q = 2 and q = 1 parts */
+    cplx q2, q1;
+    if (layer == 2) {
+        q2 = 0.0;
+        q1 = sl;
+    } else if (layer == 1) {
+        q2 = dl2;
+        q1 = dl1;
     } else {
-        out[0] = (s / h) * W2 - I * k * W3 - I * eta * W1;
+        q2 = dl2;
+        q1 = dl1 - I * eta * sl;
     }
+    if (split) {
+        out[0] = q2;
+        out[1] = q1;
+    } else {
+        out[0] = (s / h) * q2 + q1;
+    }
+}
+
+static void wfactors(double k, double eta, const double *x, const double *y0, double h, const double *y,
+                     const double *ny, int split, cplx *out) {
+    wfactors_layer(0, k, eta, x, y0, h, y, ny, split, out);
 }
 
 /* Same factors with the literal phase k (h/s)(|u - v s| - 1) (tests compare the two forms). */
@@ -698,6 +741,7 @@ static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const doubl
     T->N = N; T->xyz = xyz; T->nrm = nrm; T->w = w; T->nrhs = nrhs;
     T->k = prm->k; T->eta = prm->eta; T->Ps = prm->Ps; T->Pang = prm->Pang; T->P = prm->Ps * prm->Pang * prm->Pang;
     T->far_field = prm->far_field != 0;
+    T->layer = prm->layer;
     if (prm->root_side > 0) {
         T->L = prm->root_side;
         for (int a = 0; a < 3; a++) T->c0[a] = prm->root_center[a];
@@ -786,7 +830,7 @@ static int64_t stage_leaf_expansions(otree *T, const cplx *sg) {
                 for (int i = 0; i < L->pcount[b]; i++) {
                     int m = L->perm[L->pstart[b] + i];
                     cplx W[2];
-                    wfactors(T->k, T->eta, x, y0, L->h, T->xyz + 3 * m, T->nrm + 3 * m, L->split, W);
+                    wfactors_layer(T->layer, T->k, T->eta, x, y0, L->h, T->xyz + 3 * m, T->nrm + 3 * m, L->split, W);
                     for (int fc = 0; fc < L->nfac; fc++)
                         for (int q = 0; q < nrhs; q++)
                             L->F[fidx(T, L, rc, fc, q) + nn] += T->w[m] * sg[(int64_t)q * N + m] * W[fc];
@@ -911,7 +955,7 @@ static int64_t stage_near_field(const otree *T, const cplx *sg, cplx *u) {
                     double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
                     near_pairs++;
                     if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
-                    cplx K = cfie_kernel(T->k, T->eta, x, y, T->nrm + 3 * m) * T->w[m];
+                    cplx K = layer_kernel(T->layer, T->k, T->eta, x, y, T->nrm + 3 * m) * T->w[m];
                     for (int qq = 0; qq < nrhs; qq++) u[(int64_t)qq * N + l] += K * sg[(int64_t)qq * N + m];
                 }
             }

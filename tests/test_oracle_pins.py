@@ -100,6 +100,19 @@ def test_direct_sum_brute_force(oracle_lib):
     lhs = np.vdot(g, got)
     rhs = np.vdot(oracle_lib.direct_adjoint(x, nu, w, k, eta, g, cI=cI), sig)
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # the single and double layers alone (layers 2 and 1) against the loop over Phi and dPhi/dnu
+    for layer in (1, 2):
+        ref = cI * sig.copy()
+        for l in range(N):
+            for m in range(N):
+                if m != l:
+                    phi, dphi = oracle_lib.layer_kernels(k, x[l], x[m], nu[m])
+                    ref[:, l] += (dphi if layer == 1 else phi) * w[m] * sig[:, m]
+        got = oracle_lib.direct(x, nu, w, k, eta, sig, cI=cI, layer=layer)
+        assert rel(got, ref) < 1e-14, layer
+        lhs = np.vdot(g, got)
+        rhs = np.vdot(oracle_lib.direct_adjoint(x, nu, w, k, eta, g, cI=cI, layer=layer), sig)
+        assert abs(lhs - rhs) < 1e-12 * abs(lhs)
 
 
 # ---------------------------------------------------------------- Chebyshev (Eq. ChebyPoly, ChebyNodes)
@@ -384,3 +397,21 @@ def test_ifgf_far_field_converges_to_sum(oracle_lib):
         e.append(float(np.abs(out - ref).max() / np.abs(ref).max()))
     assert e[0] < 5e-3 and e[2] < 1e-4
     assert e[0] > e[1] > e[2]
+
+
+@pytest.mark.parametrize("layer", [1, 2])
+def test_ifgf_oracle_layers_converge_to_direct(oracle_lib, layer):
+    """The IFGF apply with the double layer alone (1) or the single layer alone (2): 3-wavelength
+    sphere, D = 4, split factors below lambda/2 and the combined factor above (the single layer's
+    q = 2 factor is zero); the error against the direct sum of that layer falls with the orders."""
+    s, k = sphere_workload(24, 6, 3.0)
+    sig = random_density(s.N, 1, 33)
+    ref = oracle_lib.direct(s.points, s.normals, s.weights, k, k, sig, cI=0.5, layer=layer)
+    e = []
+    for ps, pa in ((3, 5), (5, 8)):
+        y, info = oracle_lib.ifgf(s.points, s.normals, s.weights,
+                                  oracle_lib.IFGFParams(k=k, Ps=ps, Pang=pa, levels=4, identity_coef=0.5,
+                                                        layer=layer), sig)
+        assert info["split"][4] == 1 and info["split"][3] == 0
+        e.append(rel(y, ref))
+    assert e[0] < 5e-3 and e[1] < 1e-4 and e[1] < e[0] / 10

@@ -4,6 +4,8 @@
   Mie density with the surface quadrature (two independent routes).
 * The corrected discrete operator (direct sum + RP correction, Section 4.2)
   reproduces the eigen-relations A Y_n = lambda_n Y_n of the unit sphere.
+* The single- and double-layer sums alone (layers 2 and 1), with their shares of the
+  correction, reproduce the eigenvalues of S and D on the unit sphere.
 * The exact Mie density solves the corrected discrete CFIE to the same accuracy.
 * The off-surface combined-layer potential of the exact Mie density matches the
   closed-form exterior field, and tends to the far-field pattern as |x| grows.
@@ -64,6 +66,24 @@ def test_rp_eigen_relations(oracle_lib, corrected_sphere):
         assert rel(y, lam * Y) < 3e-5, (l, m)
         y0 = oracle_lib.direct(s.points, s.normals, s.weights, k, k, Y, cI=0.5)
         assert rel(y0, lam * Y) > 1e-2  # the uncorrected quadrature is far off
+
+
+def test_single_and_double_layer_eigen_relations(oracle_lib, corrected_sphere):
+    """The oracle's double-layer and single-layer direct sums (layers 1 and 2), each with its
+    share of the rectangular-polar correction (C is linear in eta: C_D = C(0) and
+    C_S = i (C(k) - C(0)) / k), reproduce the unit sphere's eigenvalues
+    D[Y_n] = (i k^2 j_n' h_n - 1/2) Y_n and S[Y_n] = i k j_n h_n Y_n."""
+    s, k, rp, col, val = corrected_sphere
+    n, m = 32, 8
+    rp0, col0, val0 = oracle_lib.rp_correction_sphere(s.points, s.normals, s.weights, n, m, 1.0, k, 0.0)
+    for l, mm in ((1, 1), (3, 2), (7, -4)):  # (k = 2 pi is a zero of j_0: S has the eigenvalue 0 there)
+        Y = mie.real_ylm(l, mm, s.points)[None, :].astype(complex)
+        cD = oracle_lib.csr_apply(rp0, col0, val0, Y)
+        cS = 1j * (oracle_lib.csr_apply(rp, col, val, Y) - cD) / k
+        D = oracle_lib.direct(s.points, s.normals, s.weights, k, 0.0, Y, layer=1) + cD
+        S = oracle_lib.direct(s.points, s.normals, s.weights, k, 0.0, Y, layer=2) + cS
+        assert rel(D, mie.double_layer_eigenvalue(l, k) * Y) < 3e-5, l
+        assert rel(S, mie.single_layer_eigenvalue(l, k) * Y) < 3e-5, l
 
 
 def test_mie_density_solves_corrected_system(oracle_lib, corrected_sphere):
