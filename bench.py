@@ -476,6 +476,32 @@ def run_ours(args):
         "note": "ifgf_far_field_ifgf: upward pass (leaf expansions, propagation) plus one warp per direction "
                 "over the level-3 boxes, mixed precision"}
     assert plan_ff.missed_lookups() == 0
+    # ---- the plane potential with the plane's points inside the octree (zero-weight targets) ----
+    t0 = time.perf_counter()
+    plan_nf = Plan.with_targets(s.points, s.normals, s.weights, plane.cpu().numpy(),
+                                Params(k=k, Ps=Ps, Pang=Pang, nC0=args.nc0, nS0=args.ns0,
+                                       factor_mode=args.factor_mode))
+    nf_plan_s = time.perf_counter() - t0
+    if args.tc_fill is not None:
+        plan_nf.set_tc_fill(args.tc_fill)
+    if args.tc_engine is not None:
+        plan_nf.set_tc_engine(args.tc_engine)
+    nfi = torch.empty_like(nf)
+    t_nfi = float(np.mean(timed(lambda: plan_nf.field_ifgf(sig32, out=nfi), k_off, 2)))
+    plan_nf.set_profiling(True)
+    plan_nf.field_ifgf(sig32, out=nfi)
+    nf_launches = launches_of(plan_nf.stage_times())
+    plan_nf.set_profiling(False)
+    torch.cuda.synchronize()
+    off_surface["plane_potential_ifgf"] = {
+        "targets": int(plane.shape[0]), "ms_per_step": t_nfi, "speedup_vs_direct_sum": t_nf / t_nfi,
+        "rel_err_vs_direct_sum_l2": float(torch.linalg.vector_norm(nfi - nf) / torch.linalg.vector_norm(nf)),
+        "rel_err_vs_direct_sum_max": float((nfi - nf).abs().max() / nf.abs().max()),
+        "plan_build_s": round(nf_plan_s, 2), "D": plan_nf.info()["D"],
+        "note": "ifgf_field_ifgf: the plane's points join the octree with weight 0; one apply over sources "
+                "and targets, mixed precision"}
+    assert plan_nf.missed_lookups() == 0
+    plan_nf.close()
     k_ffi = k_off + 2 + 1  # timed calls and warm-up, and the profiled call
     ff_launches = launches_of(up_stages) + 1  # the upward pass and k_far_ifgf
     plan_ff.close()
@@ -494,7 +520,8 @@ def run_ours(args):
            "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
            # gather, sum and (when the sources are split into chunks) the reduction per off-surface call
            "gpu_launches": launches_per_apply * (args.steps + len(t4)) + len(adj_stages) * max(3, args.steps // 4)
-                           + 2 * 3 * k_off + ff_launches * k_ffi + ff_apply_launches * (k_off + 3),
+                           + 2 * 3 * k_off + ff_launches * k_ffi + ff_apply_launches * (k_off + 3)
+                           + nf_launches * (k_off + 3),
            "clocks": clk}
 
     if not args.quick:

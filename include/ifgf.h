@@ -89,7 +89,20 @@ typedef struct {
                              the finer levels that feed them, so that ifgf_far_field_ifgf can
                              evaluate the far-field pattern from the level-3 interpolants.
                              Adds work to every apply of the plan.  Default 0. */
+    int layer;            /* kernel of the operator (ifgf_layer): IFGF_LAYER_COMBINED (default) the
+                             combined field dPhi/dnu(y) - i eta Phi of Eq. CombinedLayer;
+                             IFGF_LAYER_DOUBLE the double layer dPhi/dnu(y) alone (Eq. double_layer);
+                             IFGF_LAYER_SINGLE the single layer Phi alone (Eq. GreenFunction), for
+                             other formulations (Section 2).  eta is ignored by the last two.  Applies
+                             to every evaluation of the plan: apply, adjoint, k-gradient, off-surface
+                             potential and far fields.  The rectangular-polar correction
+                             (ifgf_rp_correction*) is built for the combined kernel; it is linear in eta,
+                             so the double layer's is C(eta = 0) and the single layer's
+                             i (C(eta = 1) - C(eta = 0)). */
 } ifgf_params;
+
+/* Values of ifgf_params.layer. */
+typedef enum { IFGF_LAYER_COMBINED = 0, IFGF_LAYER_DOUBLE = 1, IFGF_LAYER_SINGLE = 2 } ifgf_layer;
 
 /* Plan statistics (ifgf_plan_info). Arrays are indexed by level d (0..IFGF_MAXD). */
 #define IFGF_MAXD 20
@@ -334,6 +347,26 @@ ifgf_status ifgf_field(ifgf_plan *plan, const void *sigma_dev, const double *x_d
  * the limit of u(R xhat) R e^{-ikR} as R grows.  Arguments as ifgf_field. */
 ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
                            void *out_dev, int nrhs, ifgf_precision prec, void *stream);
+
+/* Plan over N surface points (as ifgf_plan_create) plus M off-surface targets (targets [M][3]
+ * host FP64, finite; anywhere, inside or outside the surface's bounding box).  The targets join
+ * the octree as points with weight 0 and no normal, so they act on nothing, and their rows of the
+ * apply are the potential of Eq. CombinedLayer at the targets (ifgf_field_ifgf): the same
+ * leaf expansions, propagation, cousin interpolation and near field as every other row, accelerated
+ * instead of the N M direct sum of ifgf_field.  The plan's own applies (ifgf_apply and the rest)
+ * act on all N + M points; sizes: 1 <= M, N + M <= 2^31 - 1.  IFGF_EINVAL on invalid input. */
+ifgf_status ifgf_plan_create_with_targets(const double *xyz, const double *normals, const double *weights,
+                                          int64_t N, const double *targets, int64_t M, const ifgf_params *params,
+                                          void *stream, ifgf_plan **out);
+
+/* Potential at the M targets of a plan made by ifgf_plan_create_with_targets (the off-surface
+ * counterpart of Eq. field1, with the plan's layer): out[q][t] = sum_m K(x_t, y_m) w_m sigma[q][m].
+ * sigma_dev [nrhs][N] (the surface densities), out_dev [nrhs][M]; complex128 for IFGF_FP64,
+ * complex64 for IFGF_MIXED.  Pads the density with zeros at the targets (a plan-owned scratch of
+ * 2 (N + M) nrhs complex values), runs the apply and copies the targets' rows.  No sparse correction
+ * is added (it belongs to on-surface rows).  IFGF_EINVAL for a plan without targets. */
+ifgf_status ifgf_field_ifgf(ifgf_plan *plan, const void *sigma_dev, void *out_dev, int nrhs, ifgf_precision prec,
+                            void *stream);
 
 /* Far-field pattern of Eq. FarField through the IFGF factorisation (Section 3.4 with the
  * limit s -> 0 of Eq. defparametrizationins).  For x = R xhat the centred factor of a level-3

@@ -8,6 +8,9 @@ and streams.
 """
 from .binding import (  # noqa: F401
     FP64,
+    LAYER_COMBINED,
+    LAYER_DOUBLE,
+    LAYER_SINGLE,
     MIXED,
     Group,
     IFGFError,

@@ -22,6 +22,10 @@ STATUS = {0: "IFGF_OK", -1: "IFGF_EINVAL", -2: "IFGF_ENOMEM", -3: "IFGF_ECUDA", 
           -5: "IFGF_EUNSUPPORTED", -6: "IFGF_EINTERNAL"}
 FP64 = 0
 MIXED = 1
+# ifgf_layer: the operator's kernel (combined field, double layer alone, single layer alone)
+LAYER_COMBINED = 0
+LAYER_DOUBLE = 1
+LAYER_SINGLE = 2
 
 
 class IFGFError(RuntimeError):
@@ -39,7 +43,7 @@ class CParams(ctypes.Structure):
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
         ("cone_band", ctypes.c_double),
-        ("far_field", ctypes.c_int),
+        ("far_field", ctypes.c_int), ("layer", ctypes.c_int),
     ]
 
 
@@ -87,6 +91,9 @@ _SIGS = [
     ("ifgf_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_far_field", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_far_field_ifgf", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    ("ifgf_plan_create_with_targets", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, _VP, ctypes.c_int64,
+                                                     ctypes.POINTER(CParams), _VP, ctypes.POINTER(_VP)]),
+    ("ifgf_field_ifgf", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     ("ifgf_gmres", ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(ctypes.c_int), _VP, _VP]),
     ("ifgf_plan_info", ctypes.c_int, [_VP, ctypes.POINTER(CInfo)]),
@@ -152,6 +159,7 @@ class Params:
     root_side: float = 0.0
     cone_band: float = 1e-4
     far_field: int = 0
+    layer: int = 0  # LAYER_COMBINED, LAYER_DOUBLE or LAYER_SINGLE
 
     def to_c(self) -> CParams:
         p = CParams()
@@ -166,6 +174,7 @@ class Params:
         p.root_side = self.root_side
         p.cone_band = self.cone_band
         p.far_field = self.far_field
+        p.layer = self.layer
         return p
 
 
@@ -225,6 +234,31 @@ class Plan:
         check(lib().ifgf_plan_create(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(self.N),
                                      ctypes.byref(cp), _VP(_stream_ptr(stream)), ctypes.byref(h)))
         self._h = h
+
+    @classmethod
+    def with_targets(cls, points, normals, weights, targets, params: Params, stream=None) -> "Plan":
+        """A plan over the surface points plus off-surface targets (``ifgf_plan_create_with_targets``);
+        ``field_ifgf`` then gives the potential at the targets.  ``N`` is the number of surface points;
+        the plan's own applies act on all ``N + n_targets`` points."""
+        x = _host(points, np.float64)
+        n = _host(normals, np.float64)
+        w = _host(weights, np.float64)
+        t = _host(targets, np.float64).reshape(-1, 3)
+        if x.ndim != 2 or x.shape[1] != 3 or n.shape != x.shape or w.shape != (x.shape[0],):
+            raise ValueError("points/normals must be (N, 3) and weights (N,)")
+        self = cls.__new__(cls)
+        self.params = params
+        cp = params.to_c()
+        h = _VP()
+        check(lib().ifgf_plan_create_with_targets(x.ctypes.data, n.ctypes.data, w.ctypes.data,
+                                                  ctypes.c_int64(x.shape[0]), t.ctypes.data,
+                                                  ctypes.c_int64(t.shape[0]), ctypes.byref(cp),
+                                                  _VP(_stream_ptr(stream)), ctypes.byref(h)))
+        self._h = h
+        self.N = int(x.shape[0] + t.shape[0])
+        self.n_sources = int(x.shape[0])
+        self.n_targets = int(t.shape[0])
+        return self
 
     @property
     def handle(self):
@@ -399,6 +433,30 @@ class Plan:
     def far_field(self, sigma, directions, out=None, stream=None):
         """Far-field pattern (``ifgf_far_field``) at unit directions (M, 3)."""
         return self._eval_off_surface(lib().ifgf_far_field, sigma, directions, out, stream)
+
+    def field_ifgf(self, sigma, out=None, stream=None):
+        """Potential at the targets of a plan made by ``Plan.with_targets`` (``ifgf_field_ifgf``) for
+        surface densities sigma of shape (nrhs, n_sources) or (n_sources,)."""
+        import torch
+
+        if not (isinstance(sigma, torch.Tensor) and sigma.is_cuda):
+            raise TypeError("sigma must be a CUDA torch tensor")
+        prec = FP64 if sigma.dtype == torch.complex128 else MIXED if sigma.dtype == torch.complex64 else None
+        if prec is None:
+            raise TypeError("sigma must be complex64 (mixed) or complex128 (FP64)")
+        nt = getattr(self, "n_targets", 0)
+        if not nt:
+            raise ValueError("the plan has no targets (build it with Plan.with_targets)")
+        squeeze = sigma.dim() == 1
+        s = (sigma.reshape(1, -1) if squeeze else sigma).contiguous()
+        if s.shape[-1] != self.n_sources:
+            raise ValueError(f"sigma must have n_sources={self.n_sources} columns")
+        y = torch.empty((s.shape[0], nt), dtype=s.dtype, device=s.device) if out is None else out
+        if y.shape != (s.shape[0], nt) or y.dtype != s.dtype or not y.is_contiguous():
+            raise ValueError("out must be a contiguous (nrhs, n_targets) tensor of sigma's dtype")
+        check(lib().ifgf_field_ifgf(self._h, _VP(s.data_ptr()), _VP(y.data_ptr()), ctypes.c_int(s.shape[0]),
+                                    ctypes.c_int(prec), _VP(_stream_ptr(stream))))
+        return y.reshape(-1) if squeeze else y
 
     def far_field_ifgf(self, sigma, directions, out=None, stream=None):
         """Far-field pattern from the IFGF level-3 interpolants (``ifgf_far_field_ifgf``); the

@@ -116,15 +116,18 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     std::vector<double> x64(3 * N), n64(3 * N), w64(N);
     std::vector<float> f32(3 * N), n32(3 * N), w32(N);
     const HostLevel &LD = p.lv[D];
+    // the kernels take the double-layer coefficient from the normals: the device copies are the
+    // normals times that coefficient (0 for the single layer alone, else 1)
+    const double alpha = p.prm.layer == IFGF_LAYER_SINGLE ? 0.0 : 1.0;
     for (int64_t si = 0; si < N; si++) {
         int o = p.perm[si];
         int b = p.leaf_of[si];
         for (int a = 0; a < 3; a++) {
             x64[3 * si + a] = xyz[3 * o + a];
-            n64[3 * si + a] = nrm[3 * o + a];
+            n64[3 * si + a] = alpha * nrm[3 * o + a];
             double cen = p.c0[a] + (LD.ijk[3 * b + a] + 0.5) * p.HD;
             f32[3 * si + a] = (float)((xyz[3 * o + a] - cen) / p.HD);
-            n32[3 * si + a] = (float)nrm[3 * o + a];
+            n32[3 * si + a] = (float)(alpha * nrm[3 * o + a]);
         }
         w64[si] = w[o];
         w32[si] = (float)w[o];

@@ -1,7 +1,9 @@
 // C ABI entry points (declared in include/ifgf.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "ifgf_internal.h"
 
@@ -36,6 +38,7 @@ void ifgf_params_default(ifgf_params *p, double k) {
     p->root_side = 0.0;
     p->cone_band = 1e-4;
     p->far_field = 0;
+    p->layer = IFGF_LAYER_COMBINED;
 }
 
 const char *ifgf_supported_orders(void) { return "3x5,4x6,5x7,5x8,6x8"; }
@@ -67,8 +70,8 @@ static ifgf_status validate(const double *xyz, const double *normals, const doub
     }
     if (pr.nC0 < 1 || pr.nS0 < 1 || pr.nC0 > 64 || pr.nS0 > 64 || pr.cone_rule < 0 || pr.cone_rule > 1 ||
         pr.factor_mode < 0 || pr.factor_mode > 2 || !(pr.cone_band >= 0) || !std::isfinite(pr.identity_coef) ||
-        pr.far_field < 0 || pr.far_field > 1) {
-        set_error("invalid cone or factor parameters");
+        pr.far_field < 0 || pr.far_field > 1 || pr.layer < IFGF_LAYER_COMBINED || pr.layer > IFGF_LAYER_SINGLE) {
+        set_error("invalid cone, factor, far-field or layer parameters");
         return IFGF_EINVAL;
     }
     if (!supported_pair(pr.Ps, pr.Pang)) {
@@ -149,17 +152,9 @@ ifgf_status ifgf_plan_dry_run(const double *xyz, const double *normals, const do
     return st;
 }
 
-ifgf_status ifgf_plan_create(const double *xyz, const double *normals, const double *weights, int64_t N,
-                             const ifgf_params *params, void *stream, ifgf_plan **out) {
-    clear_error();
-    if (out) *out = nullptr;
-    if (!out) {
-        set_error("null output pointer");
-        return IFGF_EINVAL;
-    }
-    ifgf_status vst = validate(xyz, normals, weights, N, params);
-    if (vst != IFGF_OK) return vst;
-    const ifgf_params &pr = *params;
+// Octree, cone structure and device upload of a validated point set.
+static ifgf_status create_plan(const double *xyz, const double *normals, const double *weights, int64_t N,
+                               const ifgf_params &pr, void *stream, ifgf_plan **out) {
     ifgf_plan *pl = new (std::nothrow) ifgf_plan();
     if (!pl) {
         set_error("host allocation failed");
@@ -182,6 +177,59 @@ ifgf_status ifgf_plan_create(const double *xyz, const double *normals, const dou
         return st;
     }
     *out = pl;
+    return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_create(const double *xyz, const double *normals, const double *weights, int64_t N,
+                             const ifgf_params *params, void *stream, ifgf_plan **out) {
+    clear_error();
+    if (out) *out = nullptr;
+    if (!out) {
+        set_error("null output pointer");
+        return IFGF_EINVAL;
+    }
+    ifgf_status vst = validate(xyz, normals, weights, N, params);
+    if (vst != IFGF_OK) return vst;
+    return create_plan(xyz, normals, weights, N, *params, stream, out);
+}
+
+ifgf_status ifgf_plan_create_with_targets(const double *xyz, const double *normals, const double *weights, int64_t N,
+                                          const double *targets, int64_t M, const ifgf_params *params, void *stream,
+                                          ifgf_plan **out) {
+    clear_error();
+    if (out) *out = nullptr;
+    if (!out) {
+        set_error("null output pointer");
+        return IFGF_EINVAL;
+    }
+    ifgf_status vst = validate(xyz, normals, weights, N, params);
+    if (vst != IFGF_OK) return vst;
+    if (M < 1 || !targets || N + M > (int64_t)0x7fffffff) {
+        set_error("targets: need 1 <= M and N + M <= 2^31 - 1, and a target array (M = %lld)", (long long)M);
+        return IFGF_EINVAL;
+    }
+    for (int64_t i = 0; i < 3 * M; i++)
+        if (!std::isfinite(targets[i])) {
+            set_error("non-finite target coordinate at index %lld", (long long)(i / 3));
+            return IFGF_EINVAL;
+        }
+    std::vector<double> x, n, w;
+    try {
+        x.resize(3 * (size_t)(N + M));
+        n.assign(3 * (size_t)(N + M), 0.0);
+        w.assign((size_t)(N + M), 0.0);
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return IFGF_ENOMEM;
+    }
+    std::copy(xyz, xyz + 3 * N, x.begin());
+    std::copy(targets, targets + 3 * M, x.begin() + 3 * N);
+    std::copy(normals, normals + 3 * N, n.begin());
+    std::copy(weights, weights + N, w.begin());
+    ifgf_status st = create_plan(x.data(), n.data(), w.data(), N + M, *params, stream, out);
+    if (st != IFGF_OK) return st;
+    (*out)->p.n_src = N;
+    (*out)->p.n_tgt = M;
     return IFGF_OK;
 }
 

@@ -2,7 +2,9 @@
 // post-processing of a solved density, Section 5):
 //   * the combined-layer potential of Eq. CombinedLayer at arbitrary targets x
 //     (the near-field planes of Eq. PlanarGrid are such target sets),
-//       u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m;
+//       u(x) = sum_m [dPhi(x, y_m)/dnu(y_m) - i eta Phi(x, y_m)] w_m sigma_m
+//     (with the plan's layer: the double layer alone is eta = 0, the single layer alone has no
+//     normal term and Phi's coefficient 1, carried as eta = i);
 //   * its far-field pattern of Eq. FarField at directions xhat,
 //       u_inf(xhat) = (1/4pi) sum_m [-i k xhat.nu_m - i eta] e^{-i k xhat.y_m} w_m sigma_m.
 // Both are direct sums over every quadrature point (no octree acceleration),
@@ -13,7 +15,9 @@
 // order, so results are deterministic.
 //
 // ifgf_far_field_ifgf instead takes the far-field pattern from the IFGF level-3 interpolants
-// (the s -> 0 limit of the factorisation; kernel k_far_ifgf beside the forward kernels).
+// (the s -> 0 limit of the factorisation; kernel k_far_ifgf beside the forward kernels), and
+// ifgf_field_ifgf the potential at targets that were part of the plan's octree (zero-weight points:
+// their rows of the apply are the off-surface potential, accelerated like any other row).
 //
 // Mixed precision keeps the phase exact to ~1e-7 cycles without FP64 per pair:
 // per (target, leaf box) the box part of the phase is formed once (far field:
@@ -37,10 +41,10 @@ constexpr int kFieldRB = 4;  // right-hand sides per register block when nrhs > 
 
 struct FieldArgs {
     int N, M, nrhs, nbox, split;
-    double k, eta, HD, tol;
+    double k, eta, etai, HD, tol;  // coupling eta + i etai (the kernel's Phi coefficient is -i (eta + i etai))
     double c0[3];                          // root box corner
     double kap;                            // k HD / (2 pi): phase cycles per leaf unit
-    float kf, etaf, kapf, c4, iHD, tolu;   // c4 = 1 / (4 pi HD); tolu = tol / HD
+    float kf, etaf, etaif, kapf, c4, iHD, tolu;  // c4 = 1 / (4 pi HD); tolu = tol / HD
     const int *ijk, *start;                // leaf boxes (level D): integer coordinates, point ranges
     const double *x64, *n64;               // sorted absolute positions / normals
     const float4 *pn32;                    // sorted (leaf offset f, |f|^2), (normal, 0)
@@ -115,8 +119,8 @@ __global__ void __launch_bounds__(kFieldBlock) k_far32(FieldArgs fa, const float
                 float sn, cs;
                 __sincosf(2.f * kPiF * tt, &sn, &cs);
                 const float tau = __fmaf_rn(kx, nu.x, __fmaf_rn(ky, nu.y, __fmaf_rn(kz, nu.z, fa.etaf)));
-                // (-i tau) e^{-i 2 pi tt} = (-tau sn, -tau cs)
-                const float wr = -tau * sn, wi = -tau * cs;
+                // (etai - i tau) e^{-i 2 pi tt} = (etai cs - tau sn, -etai sn - tau cs)
+                const float wr = __fmaf_rn(fa.etaif, cs, -tau * sn), wi = -__fmaf_rn(fa.etaif, sn, tau * cs);
 #pragma unroll
                 for (int qq = 0; qq < RB; qq++) {
                     if (RB == 1 || q0 + qq < fa.nrhs) {
@@ -154,7 +158,8 @@ __global__ void __launch_bounds__(kFieldBlock) k_pot32(FieldArgs fa, const float
     const double iH = 1.0 / fa.HD;
     const double X = (fa.tgt[3 * j] - fa.c0[0]) * iH, Y = (fa.tgt[3 * j + 1] - fa.c0[1]) * iH,
                  Z = (fa.tgt[3 * j + 2] - fa.c0[2]) * iH;
-    const float kf = fa.kf, etaf = fa.etaf, kapf = fa.kapf, c4 = fa.c4, iHD = fa.iHD, tolu = fa.tolu;
+    const float kf = fa.kf, etaf = fa.etaf, etaif = fa.etaif, kapf = fa.kapf, c4 = fa.c4, iHD = fa.iHD,
+                tolu = fa.tolu;
     for (int q0 = 0; q0 < fa.nrhs; q0 += RB) {
         float sr[RB], cr[RB], si[RB], ci[RB];
 #pragma unroll
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(kFieldBlock) k_pot32(FieldArgs fa, const float
                 float sn, cs;
                 __sincosf(2.f * kPiF * t, &sn, &cs);
                 const float dn = __fmaf_rn(d0, nu.x, __fmaf_rn(d1, nu.y, d2 * nu.z));
-                // K = e^{ikR} / (4 pi R) [dn / (r^2 HD) - i (k dn / r + eta)],  R = r HD
-                const float A = dn * ir * ir * iHD, B = -__fmaf_rn(kf * dn, ir, etaf);
+                // K = e^{ikR} / (4 pi R) [dn / (r^2 HD) + etai - i (k dn / r + eta)],  R = r HD
+                const float A = __fmaf_rn(dn * ir * ir, iHD, etaif), B = -__fmaf_rn(kf * dn, ir, etaf);
                 const float amp = c4 * ir;
                 const float Kr = amp * __fmaf_rn(cs, A, -sn * B), Ki = amp * __fmaf_rn(sn, A, cs * B);
 #pragma unroll
@@ -221,7 +226,7 @@ __global__ void __launch_bounds__(kFieldBlock) k_field64(FieldArgs fa, const dou
     box_range(fa, blockIdx.y, b0, b1);
     const int m0 = __ldg(fa.start + b0), m1 = __ldg(fa.start + b1);
     const double tx = fa.tgt[3 * j], ty = fa.tgt[3 * j + 1], tz = fa.tgt[3 * j + 2];
-    const double k = fa.k, eta = fa.eta, inv4pi = 1.0 / (4.0 * kPi);
+    const double k = fa.k, eta = fa.eta, etai = fa.etai, inv4pi = 1.0 / (4.0 * kPi);
     for (int q = 0; q < fa.nrhs; q++) {
         const double2 *aq = a + (long long)q * fa.N;
         double ar = 0.0, ai = 0.0;
@@ -230,12 +235,12 @@ __global__ void __launch_bounds__(kFieldBlock) k_field64(FieldArgs fa, const dou
             const double nx = __ldg(fa.n64 + 3 * m), ny = __ldg(fa.n64 + 3 * m + 1), nz = __ldg(fa.n64 + 3 * m + 2);
             double Kr, Ki;
             if (FAR) {
-                // (-i (k xhat.nu + eta)) e^{-i k xhat.y} / (4 pi)
+                // (etai - i (k xhat.nu + eta)) e^{-i k xhat.y} / (4 pi)
                 const double tau = k * (tx * nx + ty * ny + tz * nz) + eta;
                 double sn, cs;
                 sincos(k * (tx * yx + ty * yy + tz * yz), &sn, &cs);
-                Kr = -tau * sn * inv4pi;
-                Ki = -tau * cs * inv4pi;
+                Kr = (etai * cs - tau * sn) * inv4pi;
+                Ki = -(etai * sn + tau * cs) * inv4pi;
             } else {
                 const double dx = tx - yx, dy = ty - yy, dz = tz - yz;
                 const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -243,8 +248,8 @@ __global__ void __launch_bounds__(kFieldBlock) k_field64(FieldArgs fa, const dou
                 const double dn = dx * nx + dy * ny + dz * nz;
                 double sn, cs;
                 sincos(k * r, &sn, &cs);
-                // e^{ikr} / (4 pi r) [(1 - ikr) dn / r^2 - i eta]
-                const double A = dn / (r * r), B = -(k * dn / r + eta);
+                // e^{ikr} / (4 pi r) [(1 - ikr) dn / r^2 + etai - i eta]
+                const double A = dn / (r * r) + etai, B = -(k * dn / r + eta);
                 const double amp = inv4pi / r;
                 Kr = amp * (cs * A - sn * B);
                 Ki = amp * (sn * A + cs * B);
@@ -360,13 +365,14 @@ static ifgf_status field_run(ifgf_plan *plan, const void *sigma, const double *t
     fa.nbox = LD.nbox;
     fa.split = split;
     fa.k = p.prm.k;
-    fa.eta = p.prm.eta;
+    coupling(p.prm, fa.eta, fa.etai);
     fa.HD = p.HD;
     fa.tol = 1e-14 * p.L;
     for (int i = 0; i < 3; i++) fa.c0[i] = p.c0[i];
     fa.kap = p.prm.k * p.HD / (2.0 * kPi);
     fa.kf = (float)p.prm.k;
-    fa.etaf = (float)p.prm.eta;
+    fa.etaf = (float)fa.eta;
+    fa.etaif = (float)fa.etai;
     fa.kapf = (float)fa.kap;
     fa.c4 = (float)(1.0 / (4.0 * kPi * p.HD));
     fa.iHD = (float)(1.0 / p.HD);
@@ -468,6 +474,57 @@ static ifgf_status far_ifgf_run(ifgf_plan *plan, const void *sigma, const double
     return IFGF_EUNSUPPORTED;
 }
 
+// Potential at the targets of a plan built with targets: the apply over sources and targets with the
+// density padded by zeros at the targets (weight 0: they are no sources), the targets' rows copied out.
+static ifgf_status field_ifgf_run(ifgf_plan *plan, const void *sigma, void *out, int nrhs, ifgf_precision prec,
+                                  void *stream) {
+    clear_error();
+    if (!plan) {
+        set_error("null plan");
+        return IFGF_EINVAL;
+    }
+    if (nrhs < 0) {
+        set_error("invalid nrhs (%d)", nrhs);
+        return IFGF_EINVAL;
+    }
+    if (prec != IFGF_FP64 && prec != IFGF_MIXED) {
+        set_error("unknown precision %d", (int)prec);
+        return IFGF_EINVAL;
+    }
+    Plan &p = plan->p;
+    if (p.n_tgt <= 0) {
+        set_error("the plan has no targets: create it with ifgf_plan_create_with_targets");
+        return IFGF_EINVAL;
+    }
+    if (nrhs == 0) return IFGF_OK;
+    if (!sigma || !out || sigma == out) {
+        set_error("null or aliasing device pointer");
+        return IFGF_EINVAL;
+    }
+    const size_t cb = prec == IFGF_FP64 ? 16 : 8;
+    const size_t ns = (size_t)p.n_src, nt = (size_t)p.n_tgt, nall = ns + nt;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t half = al(cb * nall * (size_t)nrhs);
+    ifgf_status st = field_workspace(p, 2 * half);
+    if (st != IFGF_OK) return st;
+    char *pad = (char *)p.field_ws, *yall = pad + half;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpy2DAsync(pad, cb * nall, sigma, cb * ns, cb * ns, (size_t)nrhs, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemset2DAsync(pad + cb * ns, cb * nall, 0, cb * nt, (size_t)nrhs, s);
+    if (e != cudaSuccess) {
+        set_error("target density padding: %s", cudaGetErrorString(e));
+        return IFGF_ECUDA;
+    }
+    st = run_apply(p, pad, yall, nrhs, (int)prec, s);
+    if (st != IFGF_OK) return st;
+    e = cudaMemcpy2DAsync(out, cb * nt, yall + cb * ns, cb * nall, cb * nt, (size_t)nrhs, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        set_error("target rows: %s", cudaGetErrorString(e));
+        return IFGF_ECUDA;
+    }
+    return IFGF_OK;
+}
+
 }  // namespace ifgf
 
 using namespace ifgf;
@@ -482,6 +539,11 @@ ifgf_status ifgf_field(ifgf_plan *plan, const void *sigma_dev, const double *x_d
 ifgf_status ifgf_far_field(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,
                            void *out_dev, int nrhs, ifgf_precision prec, void *stream) {
     return field_run(plan, sigma_dev, xhat_dev, M, out_dev, nrhs, prec, stream, true);
+}
+
+ifgf_status ifgf_field_ifgf(ifgf_plan *plan, const void *sigma_dev, void *out_dev, int nrhs, ifgf_precision prec,
+                            void *stream) {
+    return field_ifgf_run(plan, sigma_dev, out_dev, nrhs, prec, stream);
 }
 
 ifgf_status ifgf_far_field_ifgf(ifgf_plan *plan, const void *sigma_dev, const double *xhat_dev, int64_t M,

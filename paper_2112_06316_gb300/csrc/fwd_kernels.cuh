@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf64(CommonArgs ca, LevelArgs L, C
     node64<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
     double y0[3];
     center64(ca, L, b, y0);
-    const double r = L.h / s, k = ca.k, eta = ca.eta, soh = s / L.h;
+    const double r = L.h / s, k = ca.k, eta = ca.eta, etai = ca.etai, soh = s / L.h;
     const int j0 = L.start[b], j1 = L.start[b + 1];
     double2 *F = (double2 *)L.F;
     for (int q0 = 0; q0 < ca.nrhs; q0 += kRB) {
@@ -156,14 +156,14 @@ __global__ void __launch_bounds__(kBlock) k_leaf64(CommonArgs ca, LevelArgs L, C
             double ia = 1.0 / am;
             double w1 = ia, w3 = dn * ia * ia, w2 = w3 * ia;
             double2 W0, W1;
+            // -i k W3 - i (eta + i etai) W1 = e (etai w1 - i g),  g = k w3 + eta w1
+            const double g = k * w3 + eta * w1, hr = etai * w1;
             if (L.split) {
                 W0 = make_double2(cs * w2, sn * w2);
-                // -i k W3 - i eta W1 = -i e (k w3 + eta w1)
-                double g = k * w3 + eta * w1;
-                W1 = make_double2(sn * g, -cs * g);
+                W1 = make_double2(cs * hr + sn * g, sn * hr - cs * g);
             } else {
-                double g = k * w3 + eta * w1;
-                W0 = make_double2(cs * soh * w2 + sn * g, sn * soh * w2 - cs * g);
+                const double a = soh * w2 + hr;
+                W0 = make_double2(cs * a + sn * g, sn * a - cs * g);
             }
 #pragma unroll
             for (int qq = 0; qq < kRB; qq++) {
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) k_near64(CommonArgs ca, LevelArgs L, c
     if (i >= ca.N) return;
     int b = ca.leaf_of[i];
     const double x0 = ca.x64[3 * i], x1 = ca.x64[3 * i + 1], x2 = ca.x64[3 * i + 2];
-    const double k = ca.k, eta = ca.eta, c4 = 1.0 / (4.0 * kPi);
+    const double k = ca.k, eta = ca.eta, etai = ca.etai, c4 = 1.0 / (4.0 * kPi);
     for (int q0 = 0; q0 < ca.nrhs; q0 += kRB) {
         double2 acc[kRB];
 #pragma unroll
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(kBlock) k_near64(CommonArgs ca, LevelArgs L, c
                 sincos(k * r, &sn, &cs);
                 double ir = 1.0 / r;
                 double dn = d0 * ca.n64[3 * j] + d1 * ca.n64[3 * j + 1] + d2 * ca.n64[3 * j + 2];
-                // K = e^{ikr}/(4 pi r) [ (1 - i k r) dn / r^2 - i eta ]
-                double A = dn * ir * ir, B = -(k * dn * ir + eta);
+                // K = e^{ikr}/(4 pi r) [ (1 - i k r) dn / r^2 - i (eta + i etai) ]
+                double A = dn * ir * ir + etai, B = -(k * dn * ir + eta);
                 double2 K = make_double2(c4 * ir * (cs * A - sn * B), c4 * ir * (sn * A + cs * B));
 #pragma unroll
                 for (int qq = 0; qq < kRB; qq++) {
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
     const float ir = s / hu;               // 1 / r (leaf units)
     const float kap = ca.kappa_hi;         // k HD / (2 pi)
     const float soh = s / (hu * ca.HDf);   // s / h (absolute)
-    const float kf = ca.kf, etaf = ca.etaf;
+    const float kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif;
     const int j0 = L.start[b], j1 = L.start[b + 1];
     const float4 *pn = ca.pn32;
     float2 *F = (float2 *)L.F;
@@ -483,15 +483,15 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
             cis_cycles(t, sn, cs);
             float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
             float w3 = dn * ia * ia, w2 = w3 * ia;
-            float g = kf * w3 + etaf * ia;
+            float g = kf * w3 + etaf * ia, hr = etaif * ia;
             float W0r, W0i, W1r = 0.f, W1i = 0.f;
             if (SPLIT) {
                 W0r = cs * w2;
                 W0i = sn * w2;
-                W1r = sn * g;
-                W1i = -cs * g;
+                W1r = cs * hr + sn * g;
+                W1i = sn * hr - cs * g;
             } else {
-                const float w2s = soh * w2;
+                const float w2s = soh * w2 + hr;
                 W0r = cs * w2s + sn * g;
                 W0i = sn * w2s - cs * g;
             }
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L,
     const float hu = L.hu;
     const float ir0 = s0 / hu, ir1 = s1 / hu;  // 1 / r (leaf units)
     const float soh0 = s0 / (hu * ca.HDf), soh1 = s1 / (hu * ca.HDf);
-    const float kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf;
+    const float kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif;
     const int j0 = L.start[b], j1 = L.start[b + 1];
     const float4 *pn = ca.pn32;
     PAcc p00, p01, p10, p11;  // [node][factor]
@@ -549,13 +549,13 @@ __global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L,
         float sn, cs;
         cis_cycles(t, sn, cs);
         const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
-        const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
+        const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia, hr = etaif * ia;
         if (SPLIT) {
-            const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
+            const float W0r = cs * w2, W0i = sn * w2, W1r = cs * hr + sn * g, W1i = sn * hr - cs * g;
             A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
             A1.add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
         } else {
-            const float w2s = soh * w2;
+            const float w2s = soh * w2 + hr;
             const float W0r = cs * w2s + sn * g, W0i = sn * w2s - cs * g;
             A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
         }
@@ -628,7 +628,7 @@ __device__ __forceinline__ void prop_add(CAcc &a0, CAcc &a1, bool csplit, bool p
 constexpr int kNearWarps = 4;
 
 // contribution of source j (offset fj, normal nj from the target's box offset D) to one target:
-// K = e^{ikR}/(4 pi R) [ dn_u / (r^2 HD) - i (k dn_u / r + eta) ],  R = r HD, times `keep` (1, or 0
+// K = e^{ikR}/(4 pi R) [ dn_u / (r^2 HD) + etai - i (k dn_u / r + eta) ],  R = r HD, times `keep` (1, or 0
 // for the target itself and for coincident points: no branch, r^2 floored so that the zeroed
 // terms stay finite)
 __device__ __forceinline__ void near_pair32(const CommonArgs &ca, float D0, float D1, float D2, const float4 &fj,
@@ -645,7 +645,7 @@ __device__ __forceinline__ void near_pair32(const CommonArgs &ca, float D0, floa
     cis_cycles(t, sn, cs);
     const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
     const float amp = k2 ? c4 * ir : 0.f;
-    const float A = amp * dn * ir * ir * iHD, Bv = -amp * (ca.kf * dn * ir + ca.etaf);
+    const float A = amp * fmaf(dn * ir * ir, iHD, ca.etaif), Bv = -amp * (ca.kf * dn * ir + ca.etaf);
     Kr = cs * A - sn * Bv;
     Ki = sn * A + cs * Bv;
 }
@@ -1643,11 +1643,13 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
                     float sn, cs;
                     cis_cycles(t, sn, cs);
                     const float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
-                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = ca.kf * w3 + ca.etaf * ia;
+                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = ca.kf * w3 + ca.etaf * ia,
+                                hr = ca.etaif * ia;
                     if (split) {
-                        W0r = cs * w2; W0i = sn * w2; W1r = sn * g; W1i = -cs * g;
+                        W0r = cs * w2; W0i = sn * w2; W1r = cs * hr + sn * g; W1i = sn * hr - cs * g;
                     } else {
-                        W0r = cs * soh * w2 + sn * g; W0i = sn * soh * w2 - cs * g;
+                        const float a = soh * w2 + hr;
+                        W0r = cs * a + sn * g; W0i = sn * a - cs * g;
                     }
                 } else {
                     double s, u[3], y0[3];
@@ -1663,11 +1665,13 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
                     double sn, cs;
                     sincos(psi, &sn, &cs);
                     const double dn = dv[0] * ca.n64[3 * j] + dv[1] * ca.n64[3 * j + 1] + dv[2] * ca.n64[3 * j + 2];
-                    const double ia = 1.0 / am, w3 = dn * ia * ia, w2 = w3 * ia, g = ca.k * w3 + ca.eta * ia;
+                    const double ia = 1.0 / am, w3 = dn * ia * ia, w2 = w3 * ia, g = ca.k * w3 + ca.eta * ia,
+                                 hr = ca.etai * ia;
                     if (split) {
-                        W0r = cs * w2; W0i = sn * w2; W1r = sn * g; W1i = -cs * g;
+                        W0r = cs * w2; W0i = sn * w2; W1r = cs * hr + sn * g; W1i = sn * hr - cs * g;
                     } else {
-                        W0r = cs * soh * w2 + sn * g; W0i = sn * soh * w2 - cs * g;
+                        const double a = soh * w2 + hr;
+                        W0r = cs * a + sn * g; W0i = sn * a - cs * g;
                     }
                 }
                 const C g0 = G[gb * ca.Pstride + n];
@@ -1710,7 +1714,7 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
     const bool act = live && lane < cw.z;
     const int j = cw.y + (act ? lane : 0);
     const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
-    const float hu = L.hu, kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, hd = ca.HDf;
+    const float hu = L.hu, kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif, hd = ca.HDf;
     const float yy = fj.w;  // |f|^2
     const int r0 = L.rc_start[b], r1 = L.rc_start[b + 1];
     for (int q = 0; q < ca.nrhs && live; q++) {
@@ -1752,11 +1756,11 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
                     float sn, cs;
                     cis_cycles(t, sn, cs);
                     const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
-                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia;
+                    const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia, hr = etaif * ia;
                     const float ph0 = phl * hd;  // absolute: dW/dk = i ph0 W - i e w3 (combined, W13), i ph0 W2
                     if (SPLIT) {
                         const float g1x = gk.z, g1y = gk.w;
-                        const float W0r = cs * w2, W0i = sn * w2, W1r = sn * g, W1i = -cs * g;
+                        const float W0r = cs * w2, W0i = sn * w2, W1r = cs * hr + sn * g, W1i = sn * hr - cs * g;
                         acc.add(W0r * g0x + W0i * g0y + W1r * g1x + W1i * g1y,
                                 W0r * g0y - W0i * g0x + W1r * g1y - W1i * g1x);
                         if constexpr (DK) {  // conj(dW) G
@@ -1766,8 +1770,8 @@ __global__ void __launch_bounds__(128) k_leaf_adj_w(CommonArgs ca, LevelArgs L, 
                                      d0r * g0y - d0i * g0x + d1r * g1y - d1i * g1x);
                         }
                     } else {
-                        const float soh = gk.z;
-                        const float W0r = cs * soh * w2 + sn * g, W0i = sn * soh * w2 - cs * g;
+                        const float a = gk.z * w2 + hr;  // gk.z = s / h
+                        const float W0r = cs * a + sn * g, W0i = sn * a - cs * g;
                         acc.add(W0r * g0x + W0i * g0y, W0r * g0y - W0i * g0x);  // conj(W) G
                         if constexpr (DK) {
                             const float d0r = -ph0 * W0i + sn * w3, d0i = ph0 * W0r - cs * w3;
@@ -1808,7 +1812,7 @@ __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, 
     const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
     const float4 *pn = ca.pn32;
     const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
-    const float kf = ca.kf, etaf = ca.etaf, kap = ca.kappa_hi;
+    const float kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif, kap = ca.kappa_hi;
     const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
     const float tolu = (float)(ca.tol / ca.HD);
     for (int q = 0; q < ca.nrhs && live; q++) {
@@ -1830,7 +1834,7 @@ __global__ void __launch_bounds__(128) k_near_adj32(CommonArgs ca, LevelArgs L, 
                 float sn, cs;
                 cis_cycles(t, sn, cs);
                 const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
-                const float A = dn * ir * ir * iHD, Bv = -(kf * dn * ir + etaf);
+                const float A = dn * ir * ir * iHD + etaif, Bv = -(kf * dn * ir + etaf);
                 const float amp = c4 * ir;
                 const float Kr = amp * (cs * A - sn * Bv), Ki = amp * (sn * A + cs * Bv);
                 const float2 g = gs[(long long)q * ca.N + i];
@@ -1879,7 +1883,7 @@ __global__ void __launch_bounds__(128) k_near_adj(CommonArgs ca, LevelArgs L, co
                     float sn, cs;
                     cis_cycles(t, sn, cs);
                     const float dn = d0 * ca.n32[3 * j] + d1 * ca.n32[3 * j + 1] + d2 * ca.n32[3 * j + 2];
-                    const float A = dn * ir * ir / ca.HDf, Bv = -(ca.kf * dn * ir + ca.etaf);
+                    const float A = dn * ir * ir / ca.HDf + ca.etaif, Bv = -(ca.kf * dn * ir + ca.etaf);
                     const float amp = ir / (4.f * kPiF * ca.HDf);
                     Kr = amp * (cs * A - sn * Bv);
                     Ki = amp * (sn * A + cs * Bv);
@@ -1892,7 +1896,7 @@ __global__ void __launch_bounds__(128) k_near_adj(CommonArgs ca, LevelArgs L, co
                     sincos(ca.k * r, &sn, &cs);
                     const double ir = 1.0 / r;
                     const double dn = d0 * ca.n64[3 * j] + d1 * ca.n64[3 * j + 1] + d2 * ca.n64[3 * j + 2];
-                    const double A = dn * ir * ir, Bv = -(ca.k * dn * ir + ca.eta);
+                    const double A = dn * ir * ir + ca.etai, Bv = -(ca.k * dn * ir + ca.eta);
                     const double amp = ir / (4.0 * kPi);
                     Kr = amp * (cs * A - sn * Bv);
                     Ki = amp * (sn * A + cs * Bv);
@@ -1976,7 +1980,7 @@ __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, con
                         const float dn = d0 * nj.x + d1 * nj.y + d2 * nj.z;
                         const float amp = ir / (4.f * kPiF * ca.HDf);
                         Er = amp * cs; Ei = amp * sn;
-                        Br = dn * ir * ir / ca.HDf; Bi = -(ca.kf * dn * ir + ca.etaf);
+                        Br = dn * ir * ir / ca.HDf + ca.etaif; Bi = -(ca.kf * dn * ir + ca.etaf);
                         R = r * ca.HDf;
                         dnr = dn * ir;
                     } else {
@@ -1988,7 +1992,7 @@ __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, con
                         sincos(ca.k * r, &sn, &cs);
                         const double ir = 1.0 / r, dn = d0 * ca.n64[3 * j] + d1 * ca.n64[3 * j + 1] + d2 * ca.n64[3 * j + 2];
                         Er = cs * ir / (4.0 * kPi); Ei = sn * ir / (4.0 * kPi);
-                        Br = dn * ir * ir; Bi = -(ca.k * dn * ir + ca.eta);
+                        Br = dn * ir * ir + ca.etai; Bi = -(ca.k * dn * ir + ca.eta);
                         R = r;
                         dnr = dn * ir;
                     }
@@ -2069,20 +2073,22 @@ __global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, Che
                     w1 = ia; w3 = dn * ia * ia; w2 = w3 * ia;
                     soh = s / L.h;
                 }
-                const T kk = MX ? (T)ca.kf : (T)ca.k, ee = MX ? (T)ca.etaf : (T)ca.eta;
-                // W = e (A + i B): combined A = soh w2, B = -(k w3 + eta w1); split: W2 = e w2, W13 = e (-i (k w3 + eta w1))
+                const T kk = MX ? (T)ca.kf : (T)ca.k, ee = MX ? (T)ca.etaf : (T)ca.eta,
+                        ei = MX ? (T)ca.etaif : (T)ca.etai;
+                // W = e (A + i B): combined A = soh w2 + etai w1, B = -(k w3 + eta w1); split: W2 = e w2,
+                // W13 = e (etai w1 - i (k w3 + eta w1))
                 T d0r, d0i, d1r = T(0), d1i = T(0);
+                const T g = kk * w3 + ee * w1, hr = ei * w1;
                 if (L.split) {
                     // dW2/dk = i ph0 e w2
                     d0r = -ph0 * sn * w2; d0i = ph0 * cs * w2;
-                    // W13 = e * (0 - i g), g = k w3 + eta w1;  dW13 = i ph0 W13 - i e w3
-                    const T g = kk * w3 + ee * w1;
-                    const T W13r = sn * g, W13i = -cs * g;
+                    // dW13 = i ph0 W13 - i e w3
+                    const T W13r = cs * hr + sn * g, W13i = sn * hr - cs * g;
                     d1r = -ph0 * W13i + sn * w3;
                     d1i = ph0 * W13r - cs * w3;
                 } else {
-                    const T g = kk * w3 + ee * w1;
-                    const T Wr = cs * soh * w2 + sn * g, Wi = sn * soh * w2 - cs * g;
+                    const T a0 = soh * w2 + hr;
+                    const T Wr = cs * a0 + sn * g, Wi = sn * a0 - cs * g;
                     d0r = -ph0 * Wi + sn * w3;
                     d0i = ph0 * Wr - cs * w3;
                 }
@@ -3351,9 +3357,10 @@ static inline LevelArgs level_args(const Plan &p, int d, void *F) {
 static inline CommonArgs common_args(const Plan &p, int nrhs) {
     CommonArgs c;
     c.N = (int)p.N; c.nrhs = nrhs; c.D = p.D; c.Pstride = p.Pstride;
-    c.k = p.prm.k; c.eta = p.prm.eta; c.HD = p.HD; c.L = p.L; c.tol = 1e-14 * p.L;
+    c.k = p.prm.k; c.HD = p.HD; c.L = p.L; c.tol = 1e-14 * p.L;
+    coupling(p.prm, c.eta, c.etai);
     for (int a = 0; a < 3; a++) c.c0[a] = p.c0[a];
-    c.kf = (float)p.prm.k; c.etaf = (float)p.prm.eta; c.HDf = (float)p.HD;
+    c.kf = (float)p.prm.k; c.etaf = (float)c.eta; c.etaif = (float)c.etai; c.HDf = (float)p.HD;
     double kap = p.prm.k * p.HD / (2.0 * kPi);
     c.kappa_hi = (float)kap;
     c.kappa_lo = (float)(kap - (double)c.kappa_hi);
@@ -3875,8 +3882,8 @@ inline long long dk_partials_needed(const Plan &p) {
 // coordinate -1), so the sum over boxes is one weighted reduction of the boxes' node values.
 // One warp per direction: lane l holds the weights of nodes l, l + 32, ... and reads those
 // nodes of each box (coalesced), scales its partial by the box's phase (from shared memory),
-// and the warp adds its lanes at the end.  FP64 path: FP64 throughout; mixed path: node sums
-// in FP32 (the stored values are FP32), phases and the sum over boxes in FP64.
+// and the warp adds its lanes at the end.  FP64 path: FP64 throughout; mixed path: the phases
+// are formed in FP64 and rounded to FP32, the sums run in FP32 (the stored values are FP32).
 constexpr int kFarWarps = 4;
 constexpr int kFarMaxBox = 64;  // level 3 has 4^3 boxes (side L / 4)
 
@@ -3885,7 +3892,8 @@ __global__ void __launch_bounds__(kFarWarps * 32)
     k_far_ifgf(CommonArgs ca, LevelArgs L, ChebTab tb, const typename C2T<TF>::type *__restrict__ F,
                const double *__restrict__ xhat, long long M, int fac, typename C2T<TF>::type *__restrict__ out) {
     constexpr int P = PS * PA * PA, NJ = (P + 31) / 32;
-    __shared__ double2 s_ph[kFarWarps][kFarMaxBox];
+    using C2 = typename C2T<TF>::type;
+    __shared__ C2 s_ph[kFarWarps][kFarMaxBox];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long j = (long long)blockIdx.x * kFarWarps + warp;
     if (j >= M) return;  // whole warp
@@ -3914,31 +3922,34 @@ __global__ void __launch_bounds__(kFarWarps * 32)
         center64(ca, L, b, y0);
         double sn, cs;
         sincos(-ca.k * (e0 * y0[0] + e1 * y0[1] + e2 * y0[2]), &sn, &cs);
-        s_ph[warp][b] = make_double2(c4 * cs, c4 * sn);
+        C2 e;
+        e.x = (TF)(c4 * cs);
+        e.y = (TF)(c4 * sn);
+        s_ph[warp][b] = e;
     }
     __syncwarp();
     for (int q = 0; q < ca.nrhs; q++) {
-        double ar = 0.0, ai = 0.0;
+        TF ar = TF(0), ai = TF(0);
         for (int b = 0; b < L.nbox; b++) {
             const int rc = L.cone_map[(long long)b * L.ncone + cone];
             if (rc < 0) {  // outside the relevant set: the plan lacks the far-field segments
                 if (lane == 0 && q == 0) atomicAdd(ca.missed, 1ULL);
                 continue;
             }
-            const typename C2T<TF>::type *f = F + (((long long)q * L.nrc + rc) * L.nfac + fac) * ca.Pstride;
+            const C2 *f = F + (((long long)q * L.nrc + rc) * L.nfac + fac) * ca.Pstride;
             TF vr = TF(0), vi = TF(0);
 #pragma unroll
             for (int jj = 0; jj < NJ; jj++) {
                 const int n = lane + 32 * jj;
                 if (n < P) {
-                    const typename C2T<TF>::type v = f[n];
+                    const C2 v = f[n];
                     vr += w[jj] * v.x;
                     vi += w[jj] * v.y;
                 }
             }
-            const double2 e = s_ph[warp][b];
-            ar += e.x * (double)vr - e.y * (double)vi;
-            ai += e.x * (double)vi + e.y * (double)vr;
+            const C2 e = s_ph[warp][b];
+            ar += e.x * vr - e.y * vi;
+            ai += e.x * vi + e.y * vr;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -3946,9 +3957,9 @@ __global__ void __launch_bounds__(kFarWarps * 32)
             ai += __shfl_xor_sync(0xffffffffu, ai, o);
         }
         if (lane == 0) {
-            typename C2T<TF>::type r;
-            r.x = (TF)ar;
-            r.y = (TF)ai;
+            C2 r;
+            r.x = ar;
+            r.y = ai;
             out[(long long)q * M + j] = r;
         }
     }

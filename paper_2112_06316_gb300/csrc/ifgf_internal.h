@@ -200,6 +200,9 @@ struct Plan {
     size_t adj_ws_bytes = 0;
     void *dk_ws = nullptr;       // k-gradient: one level's anterpolated H plus the partial sums
     size_t dk_ws_bytes = 0;
+    // plans built with off-surface targets (ifgf_plan_create_with_targets): the points are the n_src
+    // sources followed by the n_tgt targets (weight 0); N = n_src + n_tgt.  0, 0 for an ordinary plan.
+    int64_t n_src = 0, n_tgt = 0;
     void *field_ws = nullptr;    // off-surface / far-field evaluation: gathered w*sigma and per-chunk partial sums
     size_t field_ws_bytes = 0;
 
@@ -241,6 +244,14 @@ enum StageKind {
     kStCousinSum = 8,  // second pass of the cone-stationary cousin interpolation
     kStPropCs = 9      // cone-stationary propagation on CUDA cores (all its octant launches)
 };
+
+// Coupling of the kernel alpha dPhi/dnu(y) + beta Phi written as beta = -i (eta + i etai): the combined
+// field of Eq. CombinedLayer is (eta, 0), the double layer alone (0, 0), the single layer alone (0, 1)
+// (beta = 1; its alpha = 0 is carried by zero device normals).
+inline void coupling(const ifgf_params &pr, double &eta, double &etai) {
+    eta = pr.layer == IFGF_LAYER_COMBINED ? pr.eta : 0.0;
+    etai = pr.layer == IFGF_LAYER_SINGLE ? 1.0 : 0.0;
+}
 
 inline void prof_begin(Plan &p, cudaStream_t s) {
     p.nev = 0;

@@ -26,9 +26,12 @@ struct LevelArgs {
 
 struct CommonArgs {
     int N, nrhs, D, Pstride;
-    double k, eta, HD, L, tol;
+    // the kernel is alpha dPhi/dnu(y) + beta Phi with beta = -i (eta + i etai): alpha enters through the
+    // normals (zero for the single layer alone), eta / etai are the real and imaginary parts of the
+    // coupling (combined field: (eta, 0); double layer: (0, 0); single layer: (0, 1), beta = 1)
+    double k, eta, etai, HD, L, tol;
     double c0[3];
-    float kf, etaf, HDf, kappa_hi, kappa_lo;  // kappa = k HD / (2 pi) split in two floats
+    float kf, etaf, etaif, HDf, kappa_hi, kappa_lo;  // kappa = k HD / (2 pi) split in two floats
     const int *leaf_of, *nb_start, *nb_list;
     const double *x64, *n64, *w64;
     const float *f32, *n32, *w32;

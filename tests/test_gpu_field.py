@@ -272,3 +272,65 @@ def test_far_field_ifgf_edge_cases(B):
     assert st == -1
     plain.close()
     plan.close()
+
+
+# ---------------------------------------------------------------- potential at targets inside the octree
+def _targets(rng):
+    g = np.linspace(-2.0, 2.0, 30)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    plane = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 1.5)], -1)  # a plane of Eq. PlanarGrid
+    d = unit(rng.normal(size=(200, 3)))
+    return np.concatenate([plane, d * rng.uniform(1.2, 3.0, (200, 1))])
+
+
+@pytest.mark.parametrize("layer,orders", [(0, (3, 5)), (0, (5, 8)), (2, (5, 8))])
+def test_field_ifgf_vs_oracle(B, oracle_lib, layer, orders):
+    """ifgf_field_ifgf: the targets join the octree as zero-weight points; against the oracle's IFGF
+    on the same point set (element by element: FP64 <= 1e-10, mixed <= 1e-5) and against the plain
+    quadrature sum of Eq. CombinedLayer within the IFGF error of the orders."""
+    s, k = sphere_workload(24, 6, 3.0)
+    rng = np.random.default_rng(61)
+    tg = _targets(rng)
+    M = tg.shape[0]
+    ps, pa = orders
+    kw = dict(levels=5, Ps=ps, Pang=pa, layer=layer)
+    plan = B.Plan.with_targets(s.points, s.normals, s.weights, tg, B.Params(k=k, **kw))
+    assert plan.n_targets == M and plan.N == s.N + M
+    sig = random_density(s.N, 2, 62)
+    xa = np.concatenate([s.points, tg])
+    na = np.concatenate([s.normals, np.zeros_like(tg)])
+    wa = np.concatenate([s.weights, np.zeros(M)])
+    sa = np.concatenate([sig, np.zeros((2, M), complex)], axis=1)
+    ya, info = oracle_lib.ifgf(xa, na, wa, oracle_lib.IFGFParams(k=k, identity_coef=0.5, **kw), sa)
+    ref = ya[:, s.N:]
+    assert info["D"] == plan.info()["D"]
+    for dt, tol in ((np.complex128, 1e-10), (np.complex64, 1e-5)):
+        y = plan.field_ifgf(torch.from_numpy(sig.astype(dt)).cuda())
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), ref, tol, str(dt))
+    assert plan.missed_lookups() == 0
+    direct = oracle_lib.field(s.points, s.normals, s.weights, k, k, sig, tg, layer=layer)
+    assert rel(ref, direct) < (5e-3 if ps == 3 else 2e-4)
+    plan.close()
+
+
+def test_field_ifgf_edge_cases(B):
+    s = cube_sphere(16, 8)
+    k = 2 * math.pi
+    plain = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, levels=3))
+    sig = torch.from_numpy(random_density(s.N, 1, 63)).cuda()
+    out = torch.zeros((1, 4), dtype=torch.complex128, device="cuda")
+    lib = B.lib()
+    st = lib.ifgf_field_ifgf(plain.handle, ctypes.c_void_p(sig.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_int(1), ctypes.c_int(0), ctypes.c_void_p(0))
+    assert st == -1 and "targets" in lib.ifgf_last_error().decode()
+    bad = np.array([[2.0, 0.0, 0.0], [np.nan, 0.0, 0.0]])
+    with pytest.raises(B.IFGFError):
+        B.Plan.with_targets(s.points, s.normals, s.weights, bad, B.Params(k=k, levels=3))
+    with pytest.raises(B.IFGFError):
+        B.Plan.with_targets(s.points, s.normals, s.weights, np.zeros((0, 3)), B.Params(k=k, levels=3))
+    plan = B.Plan.with_targets(s.points, s.normals, s.weights, np.array([[3.0, 0.0, 0.0]]),
+                               B.Params(k=k, levels=3))
+    assert plan.field_ifgf(sig[:0]).shape == (0, 1)
+    plain.close()
+    plan.close()
