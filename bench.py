@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-scatterer graph apply")
     ap.add_argument("--batch-orders", default="5x8", help="Ps x Pang of the 24-scatterer graph apply")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default kernel choices instead of autotuning them on this workload")
     return ap.parse_args()
 
 
@@ -330,6 +332,17 @@ def run_ours(args):
         barrier()
         return [a.elapsed_time(b) for a, b in ev]
 
+    # ---- kernel choices of the mixed apply (tensor-core fill threshold and engine, interpolation engine):
+    # autotuned on this workload, outside the timed region, unless given on the command line ----
+    autotune = None
+    if args.tc_fill is None and args.tc_engine is None and not args.no_tune:
+        from paper_2112_06316_gb300.autotune import Autotuner, tune_plan
+
+        cache = os.path.join(tempfile.gettempdir(), f"ifgf_bench_tune_{os.getpid()}.json")
+        tr = tune_plan(plan, sig32, Autotuner(cache), reps=3, force=True)
+        autotune = {"config": tr.config, "ms": tr.ms, "candidates": len(tr.table),
+                    "table": [[c, round(t, 4)] for c, t in tr.table]}
+
     # ---- headline: mixed apply ----
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -514,9 +527,13 @@ def run_ours(args):
                                   f"orders ({Ps},{Pang},{Pang}), nC0={args.nc0}, nS0={args.ns0}, "
                                   f"factor mode {args.factor_mode} (1: combined factor on every level), eta=k, "
                                   f"nrhs={nrhs}",
+                      "kernel_choices": autotune["config"] if autotune else
+                      {"tc_fill": 0.4 if args.tc_fill is None else args.tc_fill,
+                       "tc_engine": 1 if args.tc_engine is None else args.tc_engine, "interp_engine": 1},
                       "l2_flush_between_steps": True, "parallelism": "replicas" if world > 1 else "single",
                       "plan_build_s": round(plan_s, 2)},
            "roofline": roofline, "e2e": e2e, "multi_rhs": multi_rhs, "adjoint": adjoint, "off_surface": off_surface,
+           "autotune": autotune,
            "adjoint_forward_ratio": adjoint["adjoint_forward_ratio"],
            # gather, sum and (when the sources are split into chunks) the reduction per off-surface call
            "gpu_launches": launches_per_apply * (args.steps + len(t4)) + len(adj_stages) * max(3, args.steps // 4)

@@ -154,7 +154,7 @@ ifgf_status ifgf_plan_dry_run(const double *xyz, const double *normals, const do
 
 // Octree, cone structure and device upload of a validated point set.
 static ifgf_status create_plan(const double *xyz, const double *normals, const double *weights, int64_t N,
-                               const ifgf_params &pr, void *stream, ifgf_plan **out) {
+                               const ifgf_params &pr, void *stream, ifgf_plan **out, int64_t n_src = 0) {
     ifgf_plan *pl = new (std::nothrow) ifgf_plan();
     if (!pl) {
         set_error("host allocation failed");
@@ -162,6 +162,8 @@ static ifgf_status create_plan(const double *xyz, const double *normals, const d
     }
     Plan &p = pl->p;
     init_plan(p, pr, N);
+    p.n_src = n_src;
+    p.n_tgt = n_src > 0 ? N - n_src : 0;
     ifgf_status st;
     try {
         st = build_host_plan(p, xyz, normals, weights);
@@ -226,11 +228,7 @@ ifgf_status ifgf_plan_create_with_targets(const double *xyz, const double *norma
     std::copy(targets, targets + 3 * M, x.begin() + 3 * N);
     std::copy(normals, normals + 3 * N, n.begin());
     std::copy(weights, weights + N, w.begin());
-    ifgf_status st = create_plan(x.data(), n.data(), w.data(), N + M, *params, stream, out);
-    if (st != IFGF_OK) return st;
-    (*out)->p.n_src = N;
-    (*out)->p.n_tgt = M;
-    return IFGF_OK;
+    return create_plan(x.data(), n.data(), w.data(), N + M, *params, stream, out, N);
 }
 
 void ifgf_plan_destroy(ifgf_plan *plan) {

@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(kBlock) k_cousin64(CommonArgs ca, LevelArgs L,
         for (int qq = 0; qq < kRB; qq++) acc[qq] = make_double2(0, 0);
         for (int ci = L.co_start[b]; ci < L.co_start[b + 1]; ci++) {
             int c = L.co_list[ci];
+            if (L.rc_start[c] == L.rc_start[c + 1]) continue;  // no sources in c
             double y0[3];
             center64(ca, L, c, y0);
             double r, t3[3];
@@ -845,6 +846,7 @@ __global__ void __launch_bounds__(kCwWarps * 32) k_cousin_w(CommonArgs ca, Level
         for (int qq = 0; qq < RB; qq++) acc[qq].zero();
         for (int ci = c0; ci < c1; ci++) {
             const int c = L.co_list[ci];
+            if (L.rc_start[c] == L.rc_start[c + 1]) continue;  // no sources in c (warp-uniform)
             CousGeo g;
             cousin_geo32(ca, L, c, I, f, g);
             if (!act) g.rc = -2;
@@ -3566,8 +3568,9 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
     const bool down = !p.upward_only;
     const bool par = !p.profile && p.aux && down;
     const cudaStream_t sb = par ? p.aux : s;
-    // fork / join record the first failure of their event calls (checked after the join); they
-    // return nothing, so that every path through them is well defined
+    // fork / join (and the cousin launches' buffer clearing) record the first failure of their
+    // calls (checked after the join); they return nothing, so that every path through them is well
+    // defined
     cudaError_t dep_err = cudaSuccess;
     auto fork = [&](int slot) {
         if (par && dep_err == cudaSuccess) {
@@ -3630,6 +3633,9 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 float2 *pv = (float2 *)p.ws.pv;
                 if (ni > 0) {
                     const unsigned g = (unsigned)((ni + kCsWarps - 1) / kCsWarps);
+                    // slots of cousins without sources are never written: zero them first
+                    if (p.has_inactive && dep_err == cudaSuccess)
+                        dep_err = cudaMemsetAsync(pv, 0, sizeof(float2) * (size_t)nrhs * stride, sb);
                     if (L[d].split)
                         k_cousin_cs<PS, PA, true><<<g, kCsWarps * 32, 0, sb>>>(
                             ca, L[d], p.d_cs_item[d], ni, p.d_cs_geo4[d], p.d_cs_geo2[d], tb, pv, stride);
@@ -3931,6 +3937,7 @@ __global__ void __launch_bounds__(kFarWarps * 32)
     for (int q = 0; q < ca.nrhs; q++) {
         TF ar = TF(0), ai = TF(0);
         for (int b = 0; b < L.nbox; b++) {
+            if (L.rc_start[b] == L.rc_start[b + 1]) continue;  // no sources in b
             const int rc = L.cone_map[(long long)b * L.ncone + cone];
             if (rc < 0) {  // outside the relevant set: the plan lacks the far-field segments
                 if (lane == 0 && q == 0) atomicAdd(ca.missed, 1ULL);

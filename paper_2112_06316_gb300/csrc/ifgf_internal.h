@@ -37,6 +37,9 @@ struct HostLevel {
     int ns = 0, nC = 0, nph = 0, ncone = 0;
     double ds = 0, dth = 0, dph = 0;
     int split = 0, nfac = 1;
+    // source boxes: boxes holding a point of positive weight (all boxes unless the plan has targets);
+    // the others have no relevant cones, no children in ch_list and act on nothing
+    std::vector<uint8_t> active;
     std::vector<int> rc_start, rc_cone, rc_box;  // relevant cones (Eq. RelevantCones)
     std::vector<int> cone_map;                   // nbox * ncone -> rc index or -1
     int64_t nrc = 0;
@@ -203,6 +206,7 @@ struct Plan {
     // plans built with off-surface targets (ifgf_plan_create_with_targets): the points are the n_src
     // sources followed by the n_tgt targets (weight 0); N = n_src + n_tgt.  0, 0 for an ordinary plan.
     int64_t n_src = 0, n_tgt = 0;
+    bool has_inactive = false;  // some box holds targets only (see HostLevel::active)
     void *field_ws = nullptr;    // off-surface / far-field evaluation: gathered w*sigma and per-chunk partial sums
     size_t field_ws_bytes = 0;
 

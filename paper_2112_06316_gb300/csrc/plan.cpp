@@ -224,7 +224,9 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
     }
     for (int a = 0; a < 3; a++) p.c0[a] = p.center[a] - 0.5 * p.L;
     // ---- level count ----
-    int D = prm.levels > 0 ? prm.levels : morton_levels_auto(xyz, N, p.c0, p.L, prm.leaf_target);
+    // the automatic level count follows the sources (the first n_src points of a plan with targets)
+    int D = prm.levels > 0 ? prm.levels
+                           : morton_levels_auto(xyz, p.n_src > 0 ? p.n_src : N, p.c0, p.L, prm.leaf_target);
     if (D < 3 || D > 16) {
         set_error("levels must be in 3..16 (got %d)", D);
         return IFGF_EINVAL;
@@ -283,15 +285,28 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                 L.parent[b] = find_box(p.lv[d - 1], L.ijk[3 * b] >> 1, L.ijk[3 * b + 1] >> 1, L.ijk[3 * b + 2] >> 1);
         }
     }
+    // source boxes (points of positive weight; a plan with targets has boxes without any)
+    p.has_inactive = false;
+    for (int d = 1; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.active.assign(L.nbox, 0);
+        for (int b = 0; b < L.nbox; b++) {
+            for (int s = L.start[b]; s < L.start[b + 1] && !L.active[b]; s++) L.active[b] = w[p.perm[s]] > 0;
+            p.has_inactive = p.has_inactive || !L.active[b];
+        }
+    }
+    // children lists hold the source children only: propagation reads nothing from the others
     for (int d = 1; d < D; d++) {
         HostLevel &L = p.lv[d];
         const HostLevel &C = p.lv[d + 1];
         L.ch_start.assign(L.nbox + 1, 0);
-        for (int b = 0; b < C.nbox; b++) L.ch_start[C.parent[b] + 1]++;
+        for (int b = 0; b < C.nbox; b++)
+            if (C.active[b]) L.ch_start[C.parent[b] + 1]++;
         for (int b = 0; b < L.nbox; b++) L.ch_start[b + 1] += L.ch_start[b];
-        L.ch_list.assign(C.nbox, 0);
+        L.ch_list.assign(L.ch_start[L.nbox], 0);
         std::vector<int> fill(L.ch_start.begin(), L.ch_start.end() - 1);
-        for (int b = 0; b < C.nbox; b++) L.ch_list[fill[C.parent[b]]++] = b;
+        for (int b = 0; b < C.nbox; b++)
+            if (C.active[b]) L.ch_list[fill[C.parent[b]]++] = b;
     }
     p.lv[D].ch_start.assign(p.lv[D].nbox + 1, 0);
     // leaf neighbours (27-neighbourhood including the box itself)
@@ -339,9 +354,10 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                         }
         }
         L.co_start[L.nbox] = (int)L.co_list.size();
-        int64_t ev = 0;
+        int64_t ev = 0;  // (source box, point in one of its cousins) pairs
         for (int b = 0; b < L.nbox; b++)
-            for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) ev += L.start[L.co_list[c] + 1] - L.start[L.co_list[c]];
+            for (int c = L.co_start[b]; c < L.co_start[b + 1] && L.active[b]; c++)
+                ev += L.start[L.co_list[c] + 1] - L.start[L.co_list[c]];
         L.cousin_evals = ev;
     }
     // cone grids (Remark cone_seg_size) and factor split (Section 3.3)
@@ -405,6 +421,7 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
             std::vector<std::vector<int>> kl(nkey);
             std::vector<unsigned char> need(nkey, 0);  // keys some (child box, parent cone) pair uses
             for (int b = 0; b < L.nbox; b++) {
+                if (!L.active[b]) continue;
                 const int pb = L.parent[b];
                 const int o = (L.ijk[3 * b] & 1) + 2 * (L.ijk[3 * b + 1] & 1) + 4 * (L.ijk[3 * b + 2] & 1);
                 for (int rc = PL->rc_start[pb]; rc < PL->rc_start[pb + 1]; rc++)
@@ -445,6 +462,7 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
             std::vector<uint64_t> bits(words);
 #pragma omp for schedule(dynamic, 1)
             for (int b = 0; b < L.nbox; b++) {
+                if (!L.active[b]) continue;  // no sources: no factor to interpolate
                 std::fill(bits.begin(), bits.end(), 0ULL);
                 // far-field option: s = h / r -> 0 lies in the segments with is = 0 (cone ids
                 // 0 .. nC nph - 1), kept in every direction at level 3
@@ -491,7 +509,8 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
             }
         if (PL) {
             int64_t pe = 0;
-            for (int b = 0; b < L.nbox; b++) pe += (int64_t)(PL->rc_start[L.parent[b] + 1] - PL->rc_start[L.parent[b]]) * p.P;
+            for (int b = 0; b < L.nbox; b++)
+                if (L.active[b]) pe += (int64_t)(PL->rc_start[L.parent[b] + 1] - PL->rc_start[L.parent[b]]) * p.P;
             p.lv[d - 1].prop_evals = pe;
         }
     }
@@ -588,6 +607,7 @@ ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
             const int r0 = L.rc_start[b], nr = L.rc_start[b + 1] - r0;
             std::vector<std::vector<int>> &lists = per_box[b];
             lists.assign(nr, std::vector<int>());
+            if (nr == 0) continue;
             for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
                 int cb = L.co_list[c];
                 for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
@@ -660,7 +680,7 @@ ifgf_status build_cousin_lists(Plan &p) {
             const int r0 = L.rc_start[c], nr = L.rc_start[c + 1] - r0;
             std::vector<std::vector<uint32_t>> &lists = per_box[c];
             lists.assign(nr, std::vector<uint32_t>());
-            for (int ci = L.co_start[c]; ci < L.co_start[c + 1]; ci++) {
+            for (int ci = L.co_start[c]; ci < L.co_start[c + 1] && nr > 0; ci++) {
                 const int cb = L.co_list[ci];
                 const uint32_t slot = (uint32_t)rev[ci] << 24;
                 for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
@@ -694,7 +714,9 @@ ifgf_status build_cousin_lists(Plan &p) {
             off += (int64_t)(L.co_start[b + 1] - L.co_start[b]) * (L.start[b + 1] - L.start[b]);
         }
         L.cs_pvoff[L.nbox] = (int)off;
-        if (off != L.cousin_evals || (int64_t)L.cs_ent.size() != off) {
+        // the value buffer has a slot for every cousin (those without sources stay zero); the entries
+        // cover the (source box, cousin point) pairs
+        if ((int64_t)L.cs_ent.size() != L.cousin_evals || (!p.has_inactive && off != L.cousin_evals)) {
             set_error("cousin lists: %lld entries for %lld cousin pairs", (long long)L.cs_ent.size(),
                       (long long)L.cousin_evals);
             return IFGF_EINVAL;

@@ -6,7 +6,8 @@ import math
 import numpy as np
 import pytest
 
-from workloads import random_density, scatterer_batch
+from parity import check
+from workloads import random_density, scatterer_batch, sphere_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +133,27 @@ def test_group_recaptures_on_kernel_settings(B):
     run_and_compare()
     assert g.captures() == 1 + len(changes)
     g.close()
+
+
+def test_tune_plan_kernel_choices(B, oracle_lib, tmp_path):
+    """tune_plan times the plan's kernel choices (tensor-core fill threshold and engine, interpolation
+    engine), caches the fastest and leaves the plan configured with it; the tuned apply still matches
+    the oracle element by element, and a second tuner reads the cache without timing."""
+    from paper_2112_06316_gb300.autotune import Autotuner, PLAN_CANDIDATES, tune_plan
+
+    s, k = sphere_workload(48, 6, 4.0)
+    kw = dict(levels=5, Ps=5, Pang=8)
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, **kw))
+    sig = random_density(s.N, 1, 71)
+    st = torch.from_numpy(sig.astype(np.complex64)).cuda()
+    r = tune_plan(plan, st, Autotuner(str(tmp_path / "t.json")), reps=2)
+    assert not r.cached and len(r.table) == len(PLAN_CANDIDATES)
+    assert r.ms == min(t for _, t in r.table)
+    y = plan.apply(st)
+    torch.cuda.synchronize()
+    ref, _ = oracle_lib.ifgf(s.points, s.normals, s.weights, oracle_lib.IFGFParams(k=k, identity_coef=0.5, **kw), sig)
+    check(y.cpu().numpy(), ref, 1e-5, str(r.config))
+    assert plan.missed_lookups() == 0
+    r2 = tune_plan(plan, st, Autotuner(str(tmp_path / "t.json")))
+    assert r2.cached and r2.config == r.config
+    plan.close()
