@@ -219,46 +219,41 @@ def dry_run(points, normals, weights, params: Params) -> dict:
 
 
 class Plan:
-    """An ``ifgf_plan``: octree, cone structure and device geometry for one surface."""
+    """An ``ifgf_plan``: octree, cone structure and device geometry for one surface.
 
-    def __init__(self, points, normals, weights, params: Params, stream=None):
+    With ``targets`` ((M, 3) off-surface points) the plan is built by
+    ``ifgf_plan_create_with_targets``: the targets join the octree as points of weight 0 and
+    ``field_ifgf`` gives the potential there; the plan's own applies act on all
+    ``n_sources + n_targets`` points (``N``)."""
+
+    def __init__(self, points, normals, weights, params: Params, stream=None, targets=None):
         x = _host(points, np.float64)
         n = _host(normals, np.float64)
         w = _host(weights, np.float64)
         if x.ndim != 2 or x.shape[1] != 3 or n.shape != x.shape or w.shape != (x.shape[0],):
             raise ValueError("points/normals must be (N, 3) and weights (N,)")
-        self.N = int(x.shape[0])
         self.params = params
+        self.n_sources = int(x.shape[0])
         cp = params.to_c()
         h = _VP()
-        check(lib().ifgf_plan_create(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(self.N),
-                                     ctypes.byref(cp), _VP(_stream_ptr(stream)), ctypes.byref(h)))
+        if targets is None:
+            self.n_targets = 0
+            check(lib().ifgf_plan_create(x.ctypes.data, n.ctypes.data, w.ctypes.data, ctypes.c_int64(self.n_sources),
+                                         ctypes.byref(cp), _VP(_stream_ptr(stream)), ctypes.byref(h)))
+        else:
+            t = _host(targets, np.float64).reshape(-1, 3)
+            self.n_targets = int(t.shape[0])
+            check(lib().ifgf_plan_create_with_targets(x.ctypes.data, n.ctypes.data, w.ctypes.data,
+                                                      ctypes.c_int64(self.n_sources), t.ctypes.data,
+                                                      ctypes.c_int64(self.n_targets), ctypes.byref(cp),
+                                                      _VP(_stream_ptr(stream)), ctypes.byref(h)))
+        self.N = self.n_sources + self.n_targets
         self._h = h
 
     @classmethod
     def with_targets(cls, points, normals, weights, targets, params: Params, stream=None) -> "Plan":
-        """A plan over the surface points plus off-surface targets (``ifgf_plan_create_with_targets``);
-        ``field_ifgf`` then gives the potential at the targets.  ``N`` is the number of surface points;
-        the plan's own applies act on all ``N + n_targets`` points."""
-        x = _host(points, np.float64)
-        n = _host(normals, np.float64)
-        w = _host(weights, np.float64)
-        t = _host(targets, np.float64).reshape(-1, 3)
-        if x.ndim != 2 or x.shape[1] != 3 or n.shape != x.shape or w.shape != (x.shape[0],):
-            raise ValueError("points/normals must be (N, 3) and weights (N,)")
-        self = cls.__new__(cls)
-        self.params = params
-        cp = params.to_c()
-        h = _VP()
-        check(lib().ifgf_plan_create_with_targets(x.ctypes.data, n.ctypes.data, w.ctypes.data,
-                                                  ctypes.c_int64(x.shape[0]), t.ctypes.data,
-                                                  ctypes.c_int64(t.shape[0]), ctypes.byref(cp),
-                                                  _VP(_stream_ptr(stream)), ctypes.byref(h)))
-        self._h = h
-        self.N = int(x.shape[0] + t.shape[0])
-        self.n_sources = int(x.shape[0])
-        self.n_targets = int(t.shape[0])
-        return self
+        """``Plan(points, normals, weights, params, stream, targets=targets)``."""
+        return cls(points, normals, weights, params, stream=stream, targets=targets)
 
     @property
     def handle(self):
@@ -444,7 +439,7 @@ class Plan:
         prec = FP64 if sigma.dtype == torch.complex128 else MIXED if sigma.dtype == torch.complex64 else None
         if prec is None:
             raise TypeError("sigma must be complex64 (mixed) or complex128 (FP64)")
-        nt = getattr(self, "n_targets", 0)
+        nt = self.n_targets
         if not nt:
             raise ValueError("the plan has no targets (build it with Plan.with_targets)")
         squeeze = sigma.dim() == 1

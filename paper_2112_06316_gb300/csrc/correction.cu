@@ -23,10 +23,29 @@ __global__ void k_spmv(int N, int nrhs, const long long *__restrict__ rowptr, co
     for (int q = 0; q < nrhs; q++) {
         const typename C2T<T>::type *sq = sigma + (long long)q * N;
         T ar = 0, ai = 0;
-        for (long long j = j0 + lane; j < j1; j += 32) {
-            typename C2T<T>::type v = val[j], s = sq[col[j]];
-            ar += v.x * s.x - v.y * s.y;
-            ai += v.x * s.y + v.y * s.x;
+        // four entries per lane in flight: the value and column loads of all four are issued before
+        // the dependent density loads (the row is ~600 entries long, bound by memory latency)
+        long long j = j0 + lane;
+        for (; j + 96 < j1; j += 128) {
+            typename C2T<T>::type v[4], sv[4];
+            int cl[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                v[u] = __ldg(val + j + 32 * u);
+                cl[u] = __ldg(col + j + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) sv[u] = __ldg(sq + cl[u]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                ar += v[u].x * sv[u].x - v[u].y * sv[u].y;
+                ai += v[u].x * sv[u].y + v[u].y * sv[u].x;
+            }
+        }
+        for (; j < j1; j += 32) {
+            const typename C2T<T>::type v = __ldg(val + j), sv = __ldg(sq + __ldg(col + j));
+            ar += v.x * sv.x - v.y * sv.y;
+            ai += v.x * sv.y + v.y * sv.x;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

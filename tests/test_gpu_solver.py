@@ -150,9 +150,9 @@ def test_mie_solve_full_size_16_wavelengths(B):
     the correction built on the GPU (ifgf_rp_correction_gpu, about 600 entries per row), the
     headline apply (orders (5, 8, 8), combined factor, mixed precision) with the correction in
     every GMRES iteration (FP64 Arnoldi), plane wave along z.  The density is compared with the
-    Mie series and the far field (ifgf_far_field) on the 200 x 200 grid of Eq. SphereGrid with
-    the error of Eq. FarFieldRelErr; the paper's Table 1 reports far-field errors of order 1e-4
-    for spheres of this size."""
+    Mie series and the far field (ifgf_far_field, and ifgf_far_field_ifgf from the level-3
+    interpolants) on the 200 x 200 grid of Eq. SphereGrid with the error of Eq. FarFieldRelErr;
+    the paper's Table 1 reports far-field errors of order 1e-4 for spheres of this size."""
     import time
 
     from workloads import patch_node_index, sphere_workload
@@ -179,3 +179,11 @@ def test_mie_solve_full_size_16_wavelengths(B):
     assert e_far < 5e-4, e_far
     assert plan.missed_lookups() == 0
     plan.close()
+    # the same far field from the level-3 interpolants (a plan with the far-field cone segments)
+    pf = B.Plan(s.points, s.normals, s.weights, B.Params(k=k, Ps=5, Pang=8, factor_mode=1, far_field=1))
+    ui_f = pf.far_field_ifgf(x, torch.from_numpy(xh).cuda()).cpu().numpy()
+    e_far_ifgf = mie.far_field_error(mie.far_field(xh, k), ui_f)
+    print(f"far-field err from the level-3 interpolants {e_far_ifgf:.2e}")
+    assert e_far_ifgf < 5e-4, e_far_ifgf
+    assert pf.missed_lookups() == 0
+    pf.close()
