@@ -159,7 +159,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-KERNEL_OF_STAGE = {"leaf": "k_leaf32x2", "near": "k_near32", "cousin": "k_cousin_cs", "cousin_sum": "k_cousin_sum",
+KERNEL_OF_STAGE = {"leaf": "k_leaf32p", "near": "k_near32", "cousin": "k_cousin_cs", "cousin_sum": "k_cousin_sum",
                    "prop": "k_prop_w", "prop_tc": "k_prop_t5", "prop_cs": "k_prop_cs"}
 TRAFFIC_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                             "dram_traffic_sphere16lambda_5x8.txt")
@@ -221,10 +221,12 @@ def algorithmic_flops(info, P, nrhs, split_levels):
     return leaf, near, cousin, prop
 
 
-def launches_of(stages):
-    """Kernel launches of one profiled apply: one per stage entry, eight (one per child octant)
-    for a tensor-core or cone-stationary propagation level."""
-    return sum(8 if kind in ("prop_tc", "prop_cs") else 1 for kind, _, _ in stages)
+def launches_of(stages, nrhs=1):
+    """Kernel launches of one profiled mixed apply: one per stage entry, eight (one per child octant)
+    for a tensor-core or cone-stationary propagation level, two for the leaf stage with one
+    right-hand side (the density pairs are packed first)."""
+    return sum(8 if kind in ("prop_tc", "prop_cs") else 2 if kind == "leaf" and nrhs == 1 else 1
+               for kind, _, _ in stages)
 
 
 def reduce_over_ranks(ms: float, points: float, world: int, device="cpu"):
@@ -669,7 +671,7 @@ def run_ours(args):
         for bp, x in zip(bplans, bsig):  # launches of one graph replay, counted from profiled applies
             bp.set_profiling(True)
             bp.apply(x)
-            nl += launches_of(bp.stage_times())
+            nl += launches_of(bp.stage_times(), nrhs=int(x.shape[0]) if x.dim() > 1 else 1)
             bp.set_profiling(False)
         out["gpu_launches"] += nl * len(tb)
         grp.close()

@@ -146,6 +146,28 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
             pn[2 * i + 1] = make_float4(n32[3 * i], n32[3 * i + 1], n32[3 * i + 2], 0.f);
         }
         UP(p.d_pn32, pn);
+        // the same records in source pairs per leaf box (an odd box ends with a zero source)
+        const HostLevel &LDb = p.lv[D];
+        std::vector<int> pstart(LDb.nbox + 1, 0);
+        for (int b = 0; b < LDb.nbox; b++) pstart[b + 1] = pstart[b] + (LDb.start[b + 1] - LDb.start[b] + 1) / 2;
+        p.npairs = pstart[LDb.nbox];
+        std::vector<float4> pp(4 * (size_t)p.npairs);
+        std::vector<int2> psrc(p.npairs);
+        for (int b = 0; b < LDb.nbox; b++)
+            for (int j = LDb.start[b], m = pstart[b]; j < LDb.start[b + 1]; j += 2, m++) {
+                const bool two = j + 1 < LDb.start[b + 1];
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 a0 = pn[2 * j], b0 = pn[2 * j + 1];
+                const float4 a1 = two ? pn[2 * j + 2] : z, b1 = two ? pn[2 * j + 3] : z;
+                pp[4 * (size_t)m] = make_float4(a0.x, a1.x, a0.y, a1.y);
+                pp[4 * (size_t)m + 1] = make_float4(a0.z, a1.z, a0.w, a1.w);
+                pp[4 * (size_t)m + 2] = make_float4(b0.x, b1.x, b0.y, b1.y);
+                pp[4 * (size_t)m + 3] = make_float4(b0.z, b1.z, 0.f, 0.f);
+                psrc[m] = make_int2(j, two ? j + 1 : -1);
+            }
+        UP(p.d_pp32, pp);
+        UP(p.d_pstart, pstart);
+        UP(p.d_pair_src, psrc);
     }
     UP(p.d_perm, p.perm);
     UP(p.d_leaf_of, p.leaf_of);
@@ -375,6 +397,8 @@ size_t workspace_layout(const Plan &p, int nrhs, int prec, WorkspaceLayout &lay)
     }
     lay.pv = off;
     if (prec == IFGF_MIXED && p.cs_ok && p.interp_engine == 1) off += al(8 * (size_t)nrhs * p.cs_max_entries);
+    lay.ap = off;
+    if (prec == IFGF_MIXED) off += al(16 * (size_t)nrhs * p.npairs);
     lay.total = off;
     return off;
 }
@@ -389,6 +413,7 @@ void workspace_bind(Workspace &ws, const Plan &p, void *base, const WorkspaceLay
     ws.u = c + lay.u;
     for (int d = 3; d <= p.D; d++) ws.F[d] = c + lay.F[d];
     ws.pv = c + lay.pv;
+    ws.ap = c + lay.ap;
 }
 
 ifgf_status ensure_workspace(Plan &p, int nrhs, int prec) {

@@ -516,11 +516,68 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
     }
 }
 
-// K1 (mixed), one right-hand side, two adjacent cone nodes per thread: every source record
-// (offset, |offset|^2, normal, weighted density) is loaded once for both nodes.
+// Packed two-lane FP32 arithmetic (fma.rn.f32x2, sm_100 and later): one instruction
+// performs the real and imaginary FMAs of a complex value times a real weight, each
+// lane rounded exactly as fmaf.  Halves the issue slots of the interpolation sums.
+__device__ __forceinline__ unsigned long long f2pack(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float &x, float &y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+// acc += (w, w) * v, lane by lane
+__device__ __forceinline__ void f2fma(unsigned long long &acc, unsigned long long w, unsigned long long v) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
+}
+using u64 = unsigned long long;
+__device__ __forceinline__ u64 f2add(u64 a, u64 b) {
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 f2sub(u64 a, u64 b) {
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 f2mul(u64 a, u64 b) {
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 f2fma3(u64 a, u64 b, u64 c) {  // a * b + c, lane by lane
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ u64 f2dup(float x) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+
+// ap[q][m] = (a[s0].x, a[s1].x, a[s0].y, a[s1].y) for the pair (s0, s1) (s1 < 0: the padding zero)
+__global__ void __launch_bounds__(kBlock) k_pack_pairs(int N, int npairs, int nrhs, const int2 *__restrict__ src,
+                                                       const float2 *__restrict__ a, float4 *__restrict__ ap) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)npairs * nrhs) return;
+    const int q = (int)(i / npairs), m = (int)(i % npairs);
+    const int2 sp = src[m];
+    const float2 a0 = a[(long long)q * N + sp.x];
+    const float2 a1 = sp.y >= 0 ? a[(long long)q * N + sp.y] : make_float2(0.f, 0.f);
+    ap[i] = make_float4(a0.x, a1.x, a0.y, a1.y);
+}
+
+// K1 (mixed), one right-hand side, two adjacent cone nodes per thread and two sources per
+// instruction (the pair layout above): per (node, source pair) the factor of Eq. V3 / Eq. W2W2 /
+// Eq. w23 with the arithmetic of k_leaf32 (every source record loaded once for both nodes), the
+// sums of the even and odd sources kept apart and added at the end.
 template <int PS, int PA, bool SPLIT>
-__global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L, ChebTab tb,
-                                                     const float2 *__restrict__ a) {
+__global__ void __launch_bounds__(kBlock) k_leaf32p(CommonArgs ca, LevelArgs L, ChebTab tb,
+                                                    const ulonglong2 *__restrict__ pp, const int *__restrict__ pstart,
+                                                    const ulonglong2 *__restrict__ ap) {
     constexpr int P = PS * PA * PA, PH = (P + 1) / 2;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= L.nrc * PH) return;
@@ -534,46 +591,79 @@ __global__ void __launch_bounds__(kBlock) k_leaf32x2(CommonArgs ca, LevelArgs L,
     const float hu = L.hu;
     const float ir0 = s0 / hu, ir1 = s1 / hu;  // 1 / r (leaf units)
     const float soh0 = s0 / (hu * ca.HDf), soh1 = s1 / (hu * ca.HDf);
-    const float kap = ca.kappa_hi, kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif;
-    const int j0 = L.start[b], j1 = L.start[b + 1];
-    const float4 *pn = ca.pn32;
-    PAcc p00, p01, p10, p11;  // [node][factor]
-    p00.zero(); p01.zero(); p10.zero(); p11.zero();
-    auto eval = [&](const float *u, float ir, float soh, const float4 &fj, const float4 &nj, const float2 &aj,
-                    PAcc &A0, PAcc &A1) {
-        const float dv0 = u[0] - fj.x * ir, dv1 = u[1] - fj.y * ir, dv2 = u[2] - fj.z * ir;
-        const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
-        const float ia = rsqrtf(a2), am = a2 * ia;
-        const float uy = u[0] * fj.x + u[1] * fj.y + u[2] * fj.z;
-        float t = kap * __fdividef(ir * fj.w - 2.f * uy, am + 1.f);
-        t -= rintf(t);
-        float sn, cs;
-        cis_cycles(t, sn, cs);
-        const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
-        const float w3 = dn * ia * ia, w2 = w3 * ia, g = kf * w3 + etaf * ia, hr = etaif * ia;
-        if (SPLIT) {
-            const float W0r = cs * w2, W0i = sn * w2, W1r = cs * hr + sn * g, W1i = sn * hr - cs * g;
-            A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
-            A1.add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
-        } else {
-            const float w2s = soh * w2 + hr;
-            const float W0r = cs * w2s + sn * g, W0i = sn * w2s - cs * g;
-            A0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
-        }
+    const u64 kap2 = f2dup(ca.kappa_hi), kf2 = f2dup(ca.kf), eta2 = f2dup(ca.etaf), etai2 = f2dup(ca.etaif);
+    const u64 one2 = f2dup(1.f), mtwo2 = f2dup(-2.f);
+    struct Node {
+        u64 ux, uy, uz, mir, ir, soh;
     };
-    for (int j = j0; j < j1; j++) {
-        const float4 fj = __ldg(pn + 2 * j), nj = __ldg(pn + 2 * j + 1);
-        const float2 aj = a[j];
-        eval(u0, ir0, soh0, fj, nj, aj, p00, p01);
-        eval(u1, ir1, soh1, fj, nj, aj, p10, p11);
+    const Node nd[2] = {{f2dup(u0[0]), f2dup(u0[1]), f2dup(u0[2]), f2dup(-ir0), f2dup(ir0), f2dup(soh0)},
+                        {f2dup(u1[0]), f2dup(u1[1]), f2dup(u1[2]), f2dup(-ir1), f2dup(ir1), f2dup(soh1)}};
+    // accumulators per node: re = sum W0r ax - sum W0i ay (kept as two sums), im = sum W0r ay + W0i ax
+    u64 r0a[2] = {0ull, 0ull}, r0b[2] = {0ull, 0ull}, i0[2] = {0ull, 0ull};
+    u64 r1a[2] = {0ull, 0ull}, r1b[2] = {0ull, 0ull}, i1[2] = {0ull, 0ull};
+    const int p0 = pstart[b], p1 = pstart[b + 1];
+    for (int pm = p0; pm < p1; pm++) {
+        const ulonglong2 R0 = __ldg(pp + 4 * pm), R1 = __ldg(pp + 4 * pm + 1), R2 = __ldg(pp + 4 * pm + 2),
+                         R3 = __ldg(pp + 4 * pm + 3), A = __ldg(ap + pm);
+        const u64 fx = R0.x, fy = R0.y, fz = R1.x, yy = R1.y, nx = R2.x, ny = R2.y, nz = R3.x;
+        const u64 ax = A.x, ay = A.y;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const Node &v = nd[k];
+            const u64 dvx = f2fma3(fx, v.mir, v.ux), dvy = f2fma3(fy, v.mir, v.uy), dvz = f2fma3(fz, v.mir, v.uz);
+            const u64 a2 = f2fma3(dvz, dvz, f2fma3(dvy, dvy, f2mul(dvx, dvx)));
+            float a2l, a2h;
+            f2unpack(a2, a2l, a2h);
+            const u64 ia = f2pack(rsqrtf(a2l), rsqrtf(a2h));
+            const u64 am = f2mul(a2, ia);
+            const u64 uy = f2fma3(fz, v.uz, f2fma3(fy, v.uy, f2mul(fx, v.ux)));
+            const u64 num = f2fma3(uy, mtwo2, f2mul(v.ir, yy));  // ir |f|^2 - 2 u.f
+            float dl, dh;
+            f2unpack(f2add(am, one2), dl, dh);  // am + 1 in [1, 3]: the fast reciprocal is exact to 2 ulp
+            u64 t = f2mul(kap2, f2mul(num, f2pack(__fdividef(1.f, dl), __fdividef(1.f, dh))));
+            float tl, th;
+            f2unpack(t, tl, th);
+            t = f2sub(t, f2pack(rintf(tl), rintf(th)));
+            f2unpack(t, tl, th);
+            float snl, csl, snh, csh;
+            cis_cycles(tl, snl, csl);
+            cis_cycles(th, snh, csh);
+            const u64 sn = f2pack(snl, snh), cs = f2pack(csl, csh), ncs = f2pack(-csl, -csh);
+            const u64 dn = f2fma3(dvz, nz, f2fma3(dvy, ny, f2mul(dvx, nx)));
+            const u64 w3 = f2mul(dn, f2mul(ia, ia)), w2 = f2mul(w3, ia);
+            const u64 g = f2fma3(kf2, w3, f2mul(eta2, ia)), hr = f2mul(etai2, ia);
+            if (SPLIT) {
+                const u64 W0r = f2mul(cs, w2), W0i = f2mul(sn, w2);
+                const u64 W1r = f2fma3(sn, g, f2mul(cs, hr)), W1i = f2fma3(ncs, g, f2mul(sn, hr));
+                r0a[k] = f2fma3(W0r, ax, r0a[k]);
+                r0b[k] = f2fma3(W0i, ay, r0b[k]);
+                i0[k] = f2fma3(W0i, ax, f2fma3(W0r, ay, i0[k]));
+                r1a[k] = f2fma3(W1r, ax, r1a[k]);
+                r1b[k] = f2fma3(W1i, ay, r1b[k]);
+                i1[k] = f2fma3(W1i, ax, f2fma3(W1r, ay, i1[k]));
+            } else {
+                const u64 w2s = f2fma3(v.soh, w2, hr);
+                const u64 W0r = f2fma3(sn, g, f2mul(cs, w2s)), W0i = f2fma3(ncs, g, f2mul(sn, w2s));
+                r0a[k] = f2fma3(W0r, ax, r0a[k]);
+                r0b[k] = f2fma3(W0i, ay, r0b[k]);
+                i0[k] = f2fma3(W0i, ax, f2fma3(W0r, ay, i0[k]));
+            }
+        }
     }
+    auto fold = [](u64 ra, u64 rb, u64 im) {  // (even + odd sources)
+        float ral, rah, rbl, rbh, iml, imh;
+        f2unpack(ra, ral, rah);
+        f2unpack(rb, rbl, rbh);
+        f2unpack(im, iml, imh);
+        return make_float2((ral - rbl) + (rah - rbh), iml + imh);
+    };
     float2 *F = (float2 *)L.F;
     const long long base = (long long)rc * L.nfac;
-    F[base * ca.Pstride + n0] = p00.get();
-    if (SPLIT) F[(base + 1) * ca.Pstride + n0] = p01.get();
+    F[base * ca.Pstride + n0] = fold(r0a[0], r0b[0], i0[0]);
+    if (SPLIT) F[(base + 1) * ca.Pstride + n0] = fold(r1a[0], r1b[0], i1[0]);
     if (has1) {
-        F[base * ca.Pstride + n1] = p10.get();
-        if (SPLIT) F[(base + 1) * ca.Pstride + n1] = p11.get();
+        F[base * ca.Pstride + n1] = fold(r0a[1], r0b[1], i0[1]);
+        if (SPLIT) F[(base + 1) * ca.Pstride + n1] = fold(r1a[1], r1b[1], i1[1]);
     }
 }
 
@@ -707,6 +797,81 @@ __global__ void __launch_bounds__(kNearWarps * 32) k_near32(CommonArgs ca, Level
     }
 }
 
+// K4 (mixed), one right-hand side, on the source pairs: the chunks and neighbour walk of k_near32,
+// each target against two sources per instruction (near_pair32's arithmetic, lane by lane); the
+// even and odd sources are summed apart and added at the end.
+__global__ void __launch_bounds__(kNearWarps * 32) k_near32p(CommonArgs ca, LevelArgs L, const int4 *__restrict__ chunks,
+                                                            int nchunk, const ulonglong2 *__restrict__ pp,
+                                                            const int *__restrict__ pstart,
+                                                            const ulonglong2 *__restrict__ ap, float2 *__restrict__ u) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kNearWarps + warp;
+    if (ch >= nchunk) return;  // warp-uniform
+    const int4 cw = chunks[ch];
+    const int b = cw.x;
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
+    const int bi0 = L.ijk[3 * b], bi1 = L.ijk[3 * b + 1], bi2 = L.ijk[3 * b + 2];
+    const float4 f0 = __ldg(ca.pn32 + 2 * i0), f1 = __ldg(ca.pn32 + 2 * i1);
+    const float c4 = 1.f / (4.f * kPiF * ca.HDf);
+    const float tolu = (float)(ca.tol / ca.HD), tolu2 = tolu * tolu;
+    const u64 kap2 = f2dup(ca.kappa_hi), kf2 = f2dup(ca.kf), eta2 = f2dup(ca.etaf), etai2 = f2dup(ca.etaif);
+    const u64 iHD2 = f2dup(1.f / ca.HDf);
+    u64 ra[2] = {0ull, 0ull}, rb[2] = {0ull, 0ull}, im[2] = {0ull, 0ull};
+    const int fi[2] = {i0, i1};
+    for (int nb = ca.nb_start[b]; nb < ca.nb_start[b + 1]; nb++) {
+        const int c = ca.nb_list[nb];
+        const float E0 = (float)(bi0 - L.ijk[3 * c]), E1 = (float)(bi1 - L.ijk[3 * c + 1]),
+                    E2 = (float)(bi2 - L.ijk[3 * c + 2]);
+        const u64 Dx[2] = {f2dup(E0 + f0.x), f2dup(E0 + f1.x)}, Dy[2] = {f2dup(E1 + f0.y), f2dup(E1 + f1.y)},
+                  Dz[2] = {f2dup(E2 + f0.z), f2dup(E2 + f1.z)};
+        const int js = L.start[c];
+        for (int pm = pstart[c]; pm < pstart[c + 1]; pm++) {
+            const ulonglong2 R0 = __ldg(pp + 4 * pm), R1 = __ldg(pp + 4 * pm + 1), R2 = __ldg(pp + 4 * pm + 2),
+                             R3 = __ldg(pp + 4 * pm + 3), A = __ldg(ap + pm);
+            const int jl = js + 2 * (pm - pstart[c]);  // sorted index of the even source
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const u64 dx = f2sub(Dx[k], R0.x), dy = f2sub(Dy[k], R0.y), dz = f2sub(Dz[k], R1.x);
+                const u64 r2 = f2fma3(dz, dz, f2fma3(dy, dy, f2mul(dx, dx)));
+                float r2l, r2h;
+                f2unpack(r2, r2l, r2h);
+                const bool kl = fi[k] != jl && r2l >= tolu2, kh = fi[k] != jl + 1 && r2h >= tolu2;
+                const float irl = rsqrtf(fmaxf(r2l, 1e-30f)), irh = rsqrtf(fmaxf(r2h, 1e-30f));
+                const u64 ir = f2pack(irl, irh);
+                u64 t = f2mul(kap2, f2mul(r2, ir));
+                float tl, th;
+                f2unpack(t, tl, th);
+                t = f2sub(t, f2pack(rintf(tl), rintf(th)));
+                f2unpack(t, tl, th);
+                float snl, csl, snh, csh;
+                cis_cycles(tl, snl, csl);
+                cis_cycles(th, snh, csh);
+                const u64 dn = f2fma3(dz, R3.x, f2fma3(dy, R2.y, f2mul(dx, R2.x)));
+                const u64 amp = f2pack(kl ? c4 * irl : 0.f, kh ? c4 * irh : 0.f);
+                const u64 dnir = f2mul(dn, ir);
+                // K = amp e^{i 2 pi t} (A' - i B'),  A' = dn / (r^2 HD) + etai, B' = k dn / r + eta
+                const u64 Ar = f2mul(amp, f2fma3(f2mul(dnir, ir), iHD2, etai2));
+                const u64 nB = f2mul(amp, f2fma3(kf2, dnir, eta2));
+                const u64 Kr = f2fma3(f2pack(snl, snh), nB, f2mul(f2pack(csl, csh), Ar));
+                const u64 Ki = f2fma3(f2pack(-csl, -csh), nB, f2mul(f2pack(snl, snh), Ar));
+                ra[k] = f2fma3(Kr, A.x, ra[k]);
+                rb[k] = f2fma3(Ki, A.y, rb[k]);
+                im[k] = f2fma3(Ki, A.x, f2fma3(Kr, A.y, im[k]));
+            }
+        }
+    }
+    auto fold = [](u64 a, u64 bb, u64 c) {
+        float al, ah, bl, bh, cl, chh;
+        f2unpack(a, al, ah);
+        f2unpack(bb, bl, bh);
+        f2unpack(c, cl, chh);
+        return make_float2((al - bl) + (ah - bh), cl + chh);
+    };
+    if (v0) u[i0] = fold(ra[0], rb[0], im[0]);
+    if (v1) u[i1] = fold(ra[1], rb[1], im[1]);
+}
+
 // K2 (mixed): geometry of one (target, cousin box) pair.
 struct CousGeo {
     int rc;
@@ -756,21 +921,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Packed two-lane FP32 arithmetic (fma.rn.f32x2, sm_100 and later): one instruction
-// performs the real and imaginary FMAs of a complex value times a real weight, each
-// lane rounded exactly as fmaf.  Halves the issue slots of the interpolation sums.
-__device__ __forceinline__ unsigned long long f2pack(float x, float y) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-    return r;
-}
-__device__ __forceinline__ void f2unpack(unsigned long long v, float &x, float &y) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
-}
-// acc += (w, w) * v, lane by lane
-__device__ __forceinline__ void f2fma(unsigned long long &acc, unsigned long long w, unsigned long long v) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(v));
-}
 
 template <int PS, int PA>
 __device__ __forceinline__ void interp3f_one(const float2 *f, const float *Ls, const float *Lt, const float *Lp,
@@ -3655,25 +3805,34 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             prof_mark(p, sb, kStCousin, d);
         };
         k_gather<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.d_w32, (const float2 *)sigma, (float2 *)p.ws.a);
+        const ulonglong2 *pp = (const ulonglong2 *)p.d_pp32, *ap = (const ulonglong2 *)p.ws.ap;
+        if (nrhs == 1)  // one right-hand side: the leaf and the near field run on source pairs
+            k_pack_pairs<<<nblk(p.npairs), kBlock, 0, s>>>(N, p.npairs, 1, p.d_pair_src, (const float2 *)p.ws.a,
+                                                           (float4 *)p.ws.ap);
         prof_mark(p, s, kStGather, 0);
         fork(0);
         if (down) {
             const unsigned gn = (unsigned)((p.nnchunk + kNearWarps - 1) / kNearWarps);
-            if (rb1) k_near32<1><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
-            else k_near32<kRB><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
+            if (nrhs == 1)
+                k_near32p<<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, pp, p.d_pstart, ap, u32);
+            else if (rb1)
+                k_near32<1><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
+            else
+                k_near32<kRB><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
         }
         if (down) prof_mark(p, sb, kStNear, D);
         if (L[D].nrc) {
             const unsigned g = nblk(L[D].nrc * P);
             const float2 *a32 = (const float2 *)p.ws.a;
             const unsigned g2 = nblk(L[D].nrc * ((P + 1) / 2));
-            if (L[D].split) {
-                if (nrhs == 1) k_leaf32x2<PS, PA, true><<<g2, kBlock, 0, s>>>(ca, L[D], tb, a32);
-                else if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+            if (nrhs == 1) {  // source pairs (packed after the gather): two sources per instruction
+                if (L[D].split) k_leaf32p<PS, PA, true><<<g2, kBlock, 0, s>>>(ca, L[D], tb, pp, p.d_pstart, ap);
+                else k_leaf32p<PS, PA, false><<<g2, kBlock, 0, s>>>(ca, L[D], tb, pp, p.d_pstart, ap);
+            } else if (L[D].split) {
+                if (rb1) k_leaf32<PS, PA, 1, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
                 else k_leaf32<PS, PA, kRB, true><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
             } else {
-                if (nrhs == 1) k_leaf32x2<PS, PA, false><<<g2, kBlock, 0, s>>>(ca, L[D], tb, a32);
-                else if (rb1) k_leaf32<PS, PA, 1, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
+                if (rb1) k_leaf32<PS, PA, 1, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
                 else k_leaf32<PS, PA, kRB, false><<<g, kBlock, 0, s>>>(ca, L[D], tb, a32);
             }
             prof_mark(p, s, kStLeaf, D);

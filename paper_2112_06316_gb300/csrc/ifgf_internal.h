@@ -114,11 +114,12 @@ struct Workspace {
     void *u = nullptr;   // accumulated field in sorted order, [nrhs][N]
     void *F[IFGF_MAXD + 1] = {};  // cone values per level, [nrhs][nrc][nfac][Pstride]
     void *pv = nullptr;  // mixed path: one level's cousin-interpolation values, [nrhs][pairs]
+    void *ap = nullptr;  // mixed path: weighted densities of the source pairs, [nrhs][npairs] float4
 };
 
 // byte offsets of the workspace parts (workspace_layout)
 struct WorkspaceLayout {
-    size_t a = 0, u = 0, F[IFGF_MAXD + 1] = {}, pv = 0, total = 0;
+    size_t a = 0, u = 0, F[IFGF_MAXD + 1] = {}, pv = 0, ap = 0, total = 0;
 };
 
 struct Plan {
@@ -171,6 +172,12 @@ struct Plan {
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
     float4 *d_pn32 = nullptr;                                      // sorted, (offset, |offset|^2), (normal, 0)
+    // sources of every leaf box in pairs (the packed leaf kernel): 4 float4 records per pair, the first
+    // pair of box b at pstart[b], (sorted index, sorted index or -1) per pair
+    float4 *d_pp32 = nullptr;
+    int *d_pstart = nullptr;
+    int2 *d_pair_src = nullptr;
+    int npairs = 0;
     unsigned long long *d_missed = nullptr;
     TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
     bool use_tc = false;
