@@ -232,6 +232,11 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
                     items.push_back(make_int4((int)rc, (int)e, (int)std::min<int64_t>(kCsItem, L.cs_start[rc + 1] - e), 0));
             p.ncs_item[d] = (int)items.size();
             UP(p.d_cs_item[d], items);
+            {
+                std::vector<int> first(L.nrc > 0 ? L.nrc : 1, 0);
+                for (int64_t rc = 0; rc < L.nrc; rc++) first[rc] = (int)L.cs_start[rc];
+                UP(p.d_cs_first[d], first);
+            }
             UP(p.d_cs_pvoff[d], L.cs_pvoff);
             {
                 const size_t ne = L.cs_ent.size() > 0 ? L.cs_ent.size() : 1;

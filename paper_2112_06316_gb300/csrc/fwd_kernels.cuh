@@ -1411,7 +1411,9 @@ template <int PS, int PA, bool MX, bool FUSE>
 __global__ void __launch_bounds__(128, MX ? (FUSE ? 4 : 6) : 4) k_ant(CommonArgs ca, LevelArgs L, LevelArgs Pl, LevelArgs LD,
                                               int has_parent, const long long *__restrict__ ad_start,
                                               const int *__restrict__ ad_list, ChebTab tb, const void *gs_,
-                                              const void *Gp_, void *Gc_, const void *Fd_, double *dk_partials) {
+                                              const void *Gp_, void *Gc_, const void *Fd_, double *dk_partials,
+                                              const int *__restrict__ cs_first, const float4 *__restrict__ cs_geo4,
+                                              const float2 *__restrict__ cs_geo2) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
     constexpr int P = PS * PA * PA, PA2 = PA * PA;
@@ -1474,7 +1476,18 @@ __global__ void __launch_bounds__(128, MX ? (FUSE ? 4 : 6) : 4) k_ant(CommonArgs
                     const int i = ev;
                     const C g = gs[(long long)q * ca.N + i];
                     T Er, Ei, ir_abs;
-                    if constexpr (MX) {
+                    if (MX && cs_first) {
+                        // the forward lists hold this cone's cousin targets in the same order, with their
+                        // local coordinates and centred factor from FP64 (|E| = 1 / (4 pi r))
+                        const long long ge = (long long)cs_first[rc] + (e - e0);
+                        const float4 g4 = __ldg(cs_geo4 + ge);
+                        const float2 g2 = __ldg(cs_geo2 + ge);
+                        t3[0] = (T)g4.x; t3[1] = (T)g4.y; t3[2] = (T)g4.z;
+                        Er = (T)g4.w;
+                        Ei = (T)g2.x;
+                        ir_abs = (T)(4.f * kPiF * sqrtf(g4.w * g4.w + g2.x * g2.x));
+                        rho = (T)1 / ir_abs;
+                    } else if constexpr (MX) {
                         const int bl = ca.leaf_of[i];
                         const float sc = (float)L.scale;
                         const float M0 = LD.ijk[3 * bl] + 0.5f - (L.ijk[3 * cbox] + 0.5f) * sc;
@@ -3938,11 +3951,11 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
                 if (Fd)
                     k_ant<PS, PA, false, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
                         ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
-                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials);
+                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials, nullptr, nullptr, nullptr);
                 else
                     k_ant<PS, PA, false, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(
                         ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
-                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr);
+                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr, nullptr, nullptr, nullptr);
                 if (Fd) dk_partials += L[d].nrc;
                 prof_mark(p, s, kStCousin, d);
             }
@@ -3961,14 +3974,19 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         for (int d = 3; d <= D; d++)
             if (L[d].nrc) {
                 const Plan::AntArgs aa = {(const long long *)p.d_ad_start[d], p.d_ad_list[d]};
+                // the cone-stationary forward lists' geometry serves the cousin entries
+                const bool cg = p.cs_ok && p.d_cs_first[d];
+                const int *csf = cg ? p.d_cs_first[d] : nullptr;
+                const float4 *cg4 = cg ? p.d_cs_geo4[d] : nullptr;
+                const float2 *cg2 = cg ? p.d_cs_geo2[d] : nullptr;
                 if (Fd)
                     k_ant<PS, PA, true, true><<<(unsigned)L[d].nrc, 128, 0, s>>>(
                         ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
-                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials);
+                        d > 3 ? G[d - 1] : nullptr, G[d], Fd[d], dk_partials, csf, cg4, cg2);
                 else
                     k_ant<PS, PA, true, false><<<(unsigned)L[d].nrc, 128, 0, s>>>(
                         ca, L[d], d > 3 ? L[d - 1] : L[d], L[D], d > 3, aa.start, aa.list, tb, gs,
-                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr);
+                        d > 3 ? G[d - 1] : nullptr, G[d], nullptr, nullptr, csf, cg4, cg2);
                 if (Fd) dk_partials += L[d].nrc;
                 prof_mark(p, s, kStCousin, d);
             }

@@ -161,6 +161,7 @@ struct Plan {
     // per entry, FP64-computed once per plan: (local coordinates t_s, t_theta, t_phi, Re E) and
     // (Im E, value-buffer slot as int bits)
     float4 *d_cs_geo4[IFGF_MAXD + 1] = {};
+    int *d_cs_first[IFGF_MAXD + 1] = {};  // per relevant cone: its first entry (the adjoint reuses the geometry)
     float2 *d_cs_geo2[IFGF_MAXD + 1] = {};
     int *d_cs_pvoff[IFGF_MAXD + 1] = {};
     int64_t cs_max_entries = 0;  // largest per-level pair count (size of the value buffer per rhs)
