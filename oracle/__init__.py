@@ -52,7 +52,7 @@ class OracleParams(ctypes.Structure):
         ("cone_rule", ctypes.c_int), ("factor_mode", ctypes.c_int),
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
-        ("far_field", ctypes.c_int), ("layer", ctypes.c_int),
+        ("far_field", ctypes.c_int), ("layer", ctypes.c_int), ("leaf_max", ctypes.c_int),
     ]
 
 
@@ -112,6 +112,7 @@ class IFGFParams:
     root_side: float = 0.0
     far_field: int = 0
     layer: int = 0  # 0 combined field, 1 double layer, 2 single layer
+    leaf_max: int = 0  # > 0: adaptive octree (boxes of at most leaf_max points are leaves)
 
     def to_c(self) -> OracleParams:
         p = OracleParams()
@@ -126,6 +127,7 @@ class IFGFParams:
         p.root_side = self.root_side
         p.far_field = self.far_field
         p.layer = self.layer
+        p.leaf_max = self.leaf_max
         return p
 
 

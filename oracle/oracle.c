@@ -19,6 +19,11 @@
  *                         points and, for d > 3, onto the parent's interpolation points with
  *                         re-centring (Eq. cent_fact); the level-D neighbour interactions by
  *                         direct summation (Remark level_D_neighboring).
+ *                         With oracle_params.leaf_max > 0 the octree is adaptive: a box of at most
+ *                         leaf_max points is a leaf at its level (leaf expansions there, no boxes
+ *                         below it), cousin interpolations reach only points that still have a box at
+ *                         that level, and the near field pairs points whose boxes neighbour at the
+ *                         coarser of their two leaf levels.
  *   oracle_ifgf_far_field: the far-field pattern (Eq. FarField) from the level-3 interpolants:
  *                         the s -> 0 limit of E(x; y_B) F_B(x) summed over the level-3 boxes.
  *
@@ -67,6 +72,7 @@ typedef struct {
     double root_center[3], root_side;
     int far_field; /* 1: level 3 also keeps every segment with is = 0 (oracle_ifgf_far_field) */
     int layer;     /* 0 combined field, 1 double layer, 2 single layer (layer_kernel) */
+    int leaf_max;  /* 0: uniform tree; > 0: a box of level 3..D-1 with at most leaf_max points is a leaf */
 } oracle_params;
 
 typedef struct {
@@ -282,10 +288,12 @@ typedef struct {
     int *rc_start, *rc_ids;
     int64_t nrc;
     cplx *F, *C;
+    unsigned char *alive, *leaf; /* adaptive tree: a box exists (alive) when every ancestor is subdivided;
+                                    a leaf is alive and not subdivided (always at level D) */
 } olevel;
 
 typedef struct {
-    int D, P, Ps, Pang, nrhs, far_field, layer;
+    int D, P, Ps, Pang, nrhs, far_field, layer, leaf_max;
     double k, eta, L, c0[3];
     const double *xyz, *nrm, *w;
     int64_t N;
@@ -464,6 +472,11 @@ static void build_relevant_cones(otree *T, int d) {
     int *cnt = (int *)calloc(L->nbox, sizeof(int));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int b = 0; b < L->nbox; b++) {
+        if (!L->alive[b]) { /* below a leaf: no factor, no cones */
+            ids[b] = (int *)malloc(sizeof(int));
+            cnt[b] = 0;
+            continue;
+        }
         int64_t cap = 0;
         for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) cap += L->pcount[L->co_list[c]];
         int pb = -1;
@@ -481,6 +494,7 @@ static void build_relevant_cones(otree *T, int d) {
             for (int c = 0; c < L->nC * L->nph; c++) v[n++] = c;
         for (int c = L->co_start[b]; c < L->co_start[b + 1]; c++) {
             int cb = L->co_list[c];
+            if (!L->alive[cb]) continue; /* points below a coarser leaf take no level-d interpolation */
             for (int i = 0; i < L->pcount[cb]; i++) {
                 int pt = L->perm[L->pstart[cb] + i];
                 v[n++] = classify(T, d, b, T->xyz + 3 * pt, NULL);
@@ -674,6 +688,7 @@ static void free_tree(otree *T) {
     for (int d = 1; d <= T->D; d++) {
         olevel *L = &T->lv[d];
         free(L->key); free(L->ijk); free(L->pstart); free(L->pcount); free(L->perm); free(L->parent);
+        free(L->alive); free(L->leaf);
         free(L->co_start); free(L->co_list); free(L->rc_start); free(L->rc_ids); free(L->F); free(L->C);
     }
 }
@@ -742,6 +757,7 @@ static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const doubl
     T->k = prm->k; T->eta = prm->eta; T->Ps = prm->Ps; T->Pang = prm->Pang; T->P = prm->Ps * prm->Pang * prm->Pang;
     T->far_field = prm->far_field != 0;
     T->layer = prm->layer;
+    T->leaf_max = prm->leaf_max > 0 ? prm->leaf_max : 0;
     if (prm->root_side > 0) {
         T->L = prm->root_side;
         for (int a = 0; a < 3; a++) T->c0[a] = prm->root_center[a];
@@ -775,6 +791,18 @@ static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const doubl
         L->parent = (int *)malloc(sizeof(int) * L->nbox);
         for (int b = 0; b < L->nbox; b++)
             L->parent[b] = find_box(&T->lv[d - 1], L->ijk[3 * b] >> 1, L->ijk[3 * b + 1] >> 1, L->ijk[3 * b + 2] >> 1);
+    }
+    /* adaptive octree: level-3 boxes exist; a box with at most leaf_max points (or at level D) is a
+     * leaf; the boxes below a leaf do not exist */
+    for (int d = 3; d <= D; d++) {
+        olevel *L = &T->lv[d];
+        L->alive = (unsigned char *)malloc(L->nbox > 0 ? L->nbox : 1);
+        L->leaf = (unsigned char *)malloc(L->nbox > 0 ? L->nbox : 1);
+        for (int b = 0; b < L->nbox; b++) {
+            const olevel *PL = &T->lv[d - 1];
+            L->alive[b] = d == 3 ? 1 : (PL->alive[L->parent[b]] && !PL->leaf[L->parent[b]]);
+            L->leaf[b] = L->alive[b] && (d == D || (T->leaf_max > 0 && L->pcount[b] <= T->leaf_max));
+        }
     }
     /* cone grid per level (Remark cone_seg_size) */
     int e_lit = 0;
@@ -814,13 +842,14 @@ static int setup_tree(otree *T, const oracle_params *prm, int64_t N, const doubl
  * level-D box, F(x) = sum over the box's sources y of w_y sigma_y W(x, y) with the analytic
  * factor W of Eq. V3 / Eq. W2W2 / Eq. w23 (the combined factor or the split pair). */
 static int64_t stage_leaf_expansions(otree *T, const cplx *sg) {
-    const int D = T->D;
     const int64_t N = T->N;
     const int nrhs = T->nrhs;
-    olevel *L = &T->lv[D];
     int64_t leaf_evals = 0;
+    for (int D = 3; D <= T->D; D++) { /* every level's leaf boxes (only level D in a uniform tree) */
+    olevel *L = &T->lv[D];
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : leaf_evals)
     for (int b = 0; b < L->nbox; b++) {
+        if (!L->leaf[b]) continue;
         double y0[3];
         box_center(T, D, b, y0);
         for (int rc = L->rc_start[b]; rc < L->rc_start[b + 1]; rc++)
@@ -837,6 +866,7 @@ static int64_t stage_leaf_expansions(otree *T, const cplx *sg) {
                     leaf_evals++;
                 }
             }
+    }
     }
     return leaf_evals;
 }
@@ -880,10 +910,12 @@ static int stage_level(otree *T, int d, cplx *u, int64_t *n_cousin, int64_t *n_p
     int err = 0;
     int *plist = (int *)malloc(sizeof(int) * N);
     for (int b = 0; b < L->nbox && !err; b++) {
-        /* (a) cousin points of B (Eq. NeighborsCousins); skipped when u is NULL */
+        if (!L->alive[b]) continue;
+        /* (a) cousin points of B (Eq. NeighborsCousins) that have a level-d box; skipped when u is NULL */
         int np = 0;
         for (int c = L->co_start[b]; u && c < L->co_start[b + 1]; c++) {
             int cb = L->co_list[c];
+            if (!L->alive[cb]) continue;
             for (int i = 0; i < L->pcount[cb]; i++) plist[np++] = L->perm[L->pstart[cb] + i];
         }
         int lerr = 0;
@@ -924,10 +956,60 @@ static int stage_level(otree *T, int d, cplx *u, int64_t *n_cousin, int64_t *n_p
     return err;
 }
 
+/* Near field of the adaptive octree.  A target in a leaf of level d_t and a source in a leaf of
+ * level d_s interact directly when their boxes at level m = min(d_t, d_s) are neighbours (or the
+ * same box); every other pair is carried by exactly one cousin interpolation (the level at which
+ * their boxes stop being neighbours is at most m).  In a uniform tree m = D and this is the
+ * 27-neighbourhood rule of stage_near_field.  Direct summation as there. */
+static int64_t stage_near_field_adaptive(const otree *T, const cplx *sg, cplx *u) {
+    const int D = T->D;
+    const int64_t N = T->N;
+    const int nrhs = T->nrhs;
+    const double tol = 1e-14 * T->L;
+    /* per point: level-D cell and leaf level */
+    int *cell = (int *)malloc(sizeof(int) * 3 * N), *lev = (int *)malloc(sizeof(int) * N);
+    const olevel *LD = &T->lv[D];
+    for (int b = 0; b < LD->nbox; b++)
+        for (int i = 0; i < LD->pcount[b]; i++) {
+            const int pt = LD->perm[LD->pstart[b] + i];
+            for (int a = 0; a < 3; a++) cell[3 * pt + a] = LD->ijk[3 * b + a];
+        }
+    for (int d = 3; d <= D; d++) {
+        const olevel *L = &T->lv[d];
+        for (int b = 0; b < L->nbox; b++)
+            if (L->leaf[b])
+                for (int i = 0; i < L->pcount[b]; i++) lev[L->perm[L->pstart[b] + i]] = d;
+    }
+    int64_t near_pairs = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : near_pairs)
+    for (int64_t l = 0; l < N; l++) {
+        for (int64_t m = 0; m < N; m++) {
+            if (m == l) continue;
+            const int lv = lev[l] < lev[m] ? lev[l] : lev[m], sh = D - lv;
+            int nbr = 1;
+            for (int a = 0; a < 3; a++) {
+                const int dd = (cell[3 * l + a] >> sh) - (cell[3 * m + a] >> sh);
+                if (dd < -1 || dd > 1) nbr = 0;
+            }
+            if (!nbr) continue;
+            const double *x = T->xyz + 3 * l, *y = T->xyz + 3 * m;
+            double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+            near_pairs++;
+            if (sqrt(d0 * d0 + d1 * d1 + d2 * d2) < tol) continue;
+            cplx K = layer_kernel(T->layer, T->k, T->eta, x, y, T->nrm + 3 * m) * T->w[m];
+            for (int qq = 0; qq < nrhs; qq++) u[(int64_t)qq * N + l] += K * sg[(int64_t)qq * N + m];
+        }
+    }
+    free(cell);
+    free(lev);
+    return near_pairs;
+}
+
 /* Level-D neighbour pairs (own box and the 26 adjacent ones) by direct summation of the
  * combined-field kernel (Remark level_D_neighboring), m != l, pairs closer than 1e-14 L
  * dropped.  Returns the number of pairs visited. */
 static int64_t stage_near_field(const otree *T, const cplx *sg, cplx *u) {
+    if (T->leaf_max > 0) return stage_near_field_adaptive(T, sg, u);
     const int D = T->D;
     const int64_t N = T->N;
     const int nrhs = T->nrhs;

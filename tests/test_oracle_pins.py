@@ -415,3 +415,48 @@ def test_ifgf_oracle_layers_converge_to_direct(oracle_lib, layer):
         assert info["split"][4] == 1 and info["split"][3] == 0
         e.append(rel(y, ref))
     assert e[0] < 5e-3 and e[1] < 1e-4 and e[1] < e[0] / 10
+
+
+# ---------------------------------------------------------------- adaptive octree (leaves at several levels)
+def _two_spheres():
+    """A unit sphere (1,536 points) and a sphere of radius 0.15 centred at (1.6, 0, 0) with 3,456
+    points: a point density 20x higher in one corner of the root box."""
+    from workloads import cube_sphere
+
+    a, b = cube_sphere(16, 8), cube_sphere(24, 8)
+    pts = np.concatenate([a.points, 0.15 * b.points + np.array([1.6, 0.0, 0.0])])
+    nrm = np.concatenate([a.normals, b.normals])
+    w = np.concatenate([a.weights, 0.15 ** 2 * b.weights])
+    return pts, nrm, w
+
+
+def test_adaptive_tree_reduces_to_uniform(oracle_lib):
+    """With a leaf budget above every box's point count every level-3 box is a leaf, and the
+    adaptive apply is the uniform three-level apply (up to rounding order in the near field)."""
+    pts, nrm, w = _two_spheres()
+    k = 2 * math.pi
+    sig = random_density(pts.shape[0], 2, 41)
+    P = lambda **kw: oracle_lib.IFGFParams(k=k, identity_coef=0.5, **kw)
+    y3, _ = oracle_lib.ifgf(pts, nrm, w, P(levels=3), sig)
+    ya, _ = oracle_lib.ifgf(pts, nrm, w, P(levels=6, leaf_max=10 ** 9), sig)
+    assert rel(ya, y3) < 1e-13
+
+
+def test_adaptive_tree_converges_to_direct(oracle_lib):
+    """Adaptive tree on the two-sphere set (levels up to 6, leaves of at most 64 points): the error
+    against the direct sum falls with the orders to 3e-8 (every pair enters exactly once: through
+    one cousin interpolation or through the near field at the coarser of the two leaf levels), and
+    the relevant cone segments are a fraction of the uniform tree's."""
+    pts, nrm, w = _two_spheres()
+    k = 2 * math.pi
+    sig = random_density(pts.shape[0], 1, 42)
+    ref = oracle_lib.direct(pts, nrm, w, k, k, sig, cI=0.5)
+    P = lambda **kw: oracle_lib.IFGFParams(k=k, identity_coef=0.5, levels=6, **kw)
+    e = []
+    for kw in (dict(Ps=3, Pang=5), dict(Ps=5, Pang=8), dict(Ps=6, Pang=8, nC0=4, nS0=2)):
+        y, info = oracle_lib.ifgf(pts, nrm, w, P(leaf_max=64, **kw), sig)
+        e.append(rel(y, ref))
+    assert e[0] < 1e-3 and e[1] < 1e-5 and e[2] < 1e-7, e
+    _, iu = oracle_lib.ifgf(pts, nrm, w, P(Ps=5, Pang=8), sig)
+    _, ia = oracle_lib.ifgf(pts, nrm, w, P(Ps=5, Pang=8, leaf_max=64), sig)
+    assert sum(ia["nrc"]) < sum(iu["nrc"]) / 5
