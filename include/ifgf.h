@@ -99,6 +99,14 @@ typedef struct {
                              (ifgf_rp_correction*) is built for the combined kernel; it is linear in eta,
                              so the double layer's is C(eta = 0) and the single layer's
                              i (C(eta = 1) - C(eta = 0)). */
+    int leaf_max;         /* 0 (default): uniform octree, every leaf at level `levels`.  > 0: adaptive
+                             octree for non-uniform point densities: a box of level 3..D-1 holding at
+                             most leaf_max points is a leaf (its factor comes from its points directly
+                             and no boxes exist below it), `levels` is the maximum depth.  Points of
+                             two leaves interact directly when their boxes neighbour at the coarser
+                             of the two leaf levels; every other pair goes through one cousin
+                             interpolation.  The adjoint and the k-gradient are not built for
+                             adaptive plans (IFGF_EUNSUPPORTED). */
 } ifgf_params;
 
 /* Values of ifgf_params.layer. */
@@ -117,10 +125,14 @@ typedef struct {
     int64_t nrc[IFGF_MAXD + 1];   /* relevant cone segments per level */
     int64_t cousin_evals[IFGF_MAXD + 1]; /* target interpolations per level */
     int64_t prop_evals[IFGF_MAXD + 1];   /* interpolations into this level's cone nodes */
-    int64_t leaf_evals;           /* factor evaluations at level-D cone nodes */
-    int64_t near_pairs;           /* level-D neighbour pairs (including l == m slots) */
+    int64_t leaf_evals;           /* factor evaluations at leaf cone nodes (level D; every level's
+                                     leaves in an adaptive tree) */
+    int64_t near_pairs;           /* near-field pairs (including l == m slots) */
     int64_t correction_nnz;       /* stored correction entries (0 if none) */
     int64_t device_bytes;         /* device memory held by the plan (excluding workspaces) */
+    int64_t near_block_chunks;    /* adaptive trees: near-field chunks (at most 64 targets of one leaf)
+                                     whose long source lists run as one thread block each; 0 for
+                                     uniform trees and from ifgf_plan_dry_run */
 } ifgf_info;
 
 typedef struct ifgf_plan ifgf_plan;

@@ -43,7 +43,7 @@ class CParams(ctypes.Structure):
         ("identity_coef", ctypes.c_double),
         ("root_center", ctypes.c_double * 3), ("root_side", ctypes.c_double),
         ("cone_band", ctypes.c_double),
-        ("far_field", ctypes.c_int), ("layer", ctypes.c_int),
+        ("far_field", ctypes.c_int), ("layer", ctypes.c_int), ("leaf_max", ctypes.c_int),
     ]
 
 
@@ -58,6 +58,7 @@ class CInfo(ctypes.Structure):
         ("prop_evals", ctypes.c_int64 * (MAXD + 1)),
         ("leaf_evals", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
         ("correction_nnz", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("near_block_chunks", ctypes.c_int64),
     ]
 
 
@@ -160,6 +161,7 @@ class Params:
     cone_band: float = 1e-4
     far_field: int = 0
     layer: int = 0  # LAYER_COMBINED, LAYER_DOUBLE or LAYER_SINGLE
+    leaf_max: int = 0  # > 0: adaptive octree, boxes of at most leaf_max points are leaves
 
     def to_c(self) -> CParams:
         p = CParams()
@@ -175,6 +177,7 @@ class Params:
         p.cone_band = self.cone_band
         p.far_field = self.far_field
         p.layer = self.layer
+        p.leaf_max = self.leaf_max
         return p
 
 
@@ -203,6 +206,7 @@ def _info_dict(ci) -> dict:
         "prop_evals": [ci.prop_evals[i] for i in range(D + 1)],
         "leaf_evals": ci.leaf_evals, "near_pairs": ci.near_pairs,
         "correction_nnz": ci.correction_nnz, "device_bytes": ci.device_bytes,
+        "near_block_chunks": ci.near_block_chunks,
     }
 
 
@@ -394,9 +398,9 @@ class Plan:
         if s.shape[-1] != self.N:
             raise ValueError(f"sigma must have N={self.N} columns")
         s = s.contiguous()
-        y = torch.empty_like(s) if out is None else out
-        if y.shape != s.shape or y.dtype != s.dtype or not y.is_contiguous():
+        if out is not None and (out.shape != sigma.shape or out.dtype != sigma.dtype or not out.is_contiguous()):
             raise ValueError("out must match sigma's shape/dtype and be contiguous")
+        y = torch.empty_like(s) if out is None else out.view(s.shape)
         self.apply_ptr(s.data_ptr(), y.data_ptr(), int(s.shape[0]), prec, stream)
         return y.reshape(-1) if squeeze else y
 

@@ -2,12 +2,23 @@
 // compiled interpolation orders (kernels in fwd_kernels.cuh, instantiated per
 // order pair in inst_<Ps>x<Pang>.cu).
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 
 #include "ifgf_internal.h"
 
 namespace ifgf {
+
+// level-D box coordinates packed 21 bits per axis (depth <= 20: coordinates below 2^19)
+static inline uint64_t pack_ijk(const int *q) {
+    return (uint64_t)q[0] | ((uint64_t)q[1] << 21) | ((uint64_t)q[2] << 42);
+}
+static inline float bits_float(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, sizeof f);
+    return f;
+}
 
 #define CK(call)                                                                                  \
     do {                                                                                          \
@@ -138,6 +149,7 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     UP(p.d_f32, f32);
     UP(p.d_n32, n32);
     UP(p.d_w32, w32);
+    std::vector<int> pstart_h;  // first source pair of each level-D box
     {
         std::vector<float4> pn(2 * (size_t)N);
         for (int64_t i = 0; i < N; i++) {
@@ -148,7 +160,8 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         UP(p.d_pn32, pn);
         // the same records in source pairs per leaf box (an odd box ends with a zero source)
         const HostLevel &LDb = p.lv[D];
-        std::vector<int> pstart(LDb.nbox + 1, 0);
+        std::vector<int> &pstart = pstart_h;
+        pstart.assign(LDb.nbox + 1, 0);
         for (int b = 0; b < LDb.nbox; b++) pstart[b + 1] = pstart[b] + (LDb.start[b + 1] - LDb.start[b] + 1) / 2;
         p.npairs = pstart[LDb.nbox];
         std::vector<float4> pp(4 * (size_t)p.npairs);
@@ -162,7 +175,9 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
                 pp[4 * (size_t)m] = make_float4(a0.x, a1.x, a0.y, a1.y);
                 pp[4 * (size_t)m + 1] = make_float4(a0.z, a1.z, a0.w, a1.w);
                 pp[4 * (size_t)m + 2] = make_float4(b0.x, b1.x, b0.y, b1.y);
-                pp[4 * (size_t)m + 3] = make_float4(b0.z, b1.z, 0.f, 0.f);
+                // last slot: the box's coordinates packed 21 bits per axis (read by the adaptive near field)
+                const uint64_t kb = pack_ijk(&LDb.ijk[3 * b]);
+                pp[4 * (size_t)m + 3] = make_float4(b0.z, b1.z, bits_float((uint32_t)kb), bits_float((uint32_t)(kb >> 32)));
                 psrc[m] = make_int2(j, two ? j + 1 : -1);
             }
         UP(p.d_pp32, pp);
@@ -174,17 +189,66 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
     UP(p.d_nb_start, p.nb_start);
     UP(p.d_nb_list, p.nb_list);
     {
-        const HostLevel &L = p.lv[D];
-        std::vector<int4> ch;
-        for (int b = 0; b < L.nbox; b++) {
-            const int n = L.start[b + 1] - L.start[b];
+        // near-field chunks (.x the level-D box of the first target, .y the first target, .z the count,
+        // .w the leaf's index): at most 64 targets of one leaf box (level-D boxes, or leaves of any level
+        // in an adaptive tree), in point order; an adaptive tree's chunks with long source lists last
+        std::vector<int2> leaves;  // point ranges of the leaves
+        for (int d = 3; d <= D; d++) {
+            const HostLevel &L = p.lv[d];
+            for (int b = 0; b < L.nbox; b++)
+                if (L.leaf[b]) leaves.push_back(make_int2(L.start[b], L.start[b + 1]));
+        }
+        std::sort(leaves.begin(), leaves.end(), [](int2 a, int2 b) { return a.x < b.x; });
+        std::vector<int64_t> leaf_pairs(leaves.size(), 0);  // near source pairs of each leaf (adaptive)
+        if (p.adaptive) {
+            // per leaf: its near sources (the level-D boxes of its first level-D box's list, which every
+            // level-D box under the leaf shares) as merged point / pair ranges
+            const HostLevel &LD = p.lv[D];
+            std::vector<int> nr_start(leaves.size() + 1, 0);
+            std::vector<int4> nr;
+            std::vector<int4> tmp;
+            for (size_t li = 0; li < leaves.size(); li++) {
+                const int e = p.leaf_of[leaves[li].x];
+                tmp.clear();
+                for (int q = p.nb_start[e]; q < p.nb_start[e + 1]; q++) {
+                    const int c = p.nb_list[q];
+                    tmp.push_back(make_int4(LD.start[c], LD.start[c + 1], pstart_h[c], pstart_h[c + 1]));
+                }
+                std::sort(tmp.begin(), tmp.end(), [](const int4 &a, const int4 &b) { return a.x < b.x; });
+                for (size_t t = 0; t < tmp.size(); t++) {
+                    leaf_pairs[li] += tmp[t].w - tmp[t].z;
+                    if ((int)nr.size() > nr_start[li] && nr.back().y == tmp[t].x) {
+                        nr.back().y = tmp[t].y;  // consecutive level-D boxes: one range
+                        nr.back().w = tmp[t].w;
+                    } else {
+                        nr.push_back(tmp[t]);
+                    }
+                }
+                nr_start[li + 1] = (int)nr.size();
+            }
+            if (nr.empty()) nr.push_back(make_int4(0, 0, 0, 0));
+            UP(p.d_nr_start, nr_start);
+            UP(p.d_nr, nr);
+            std::vector<unsigned long long> pk(N);
+            for (int b = 0; b < LD.nbox; b++)
+                for (int si = LD.start[b]; si < LD.start[b + 1]; si++) pk[si] = pack_ijk(&LD.ijk[3 * b]);
+            UP(p.d_pt_ijk, pk);
+        }
+        // chunks of leaves with long source lists (adaptive trees) go last: one block each
+        constexpr int64_t kHeavyPairs = 2048;
+        std::vector<int4> ch, heavy;
+        for (size_t li = 0; li < leaves.size(); li++) {
+            const int2 r = leaves[li];
+            const int n = r.y - r.x;
             const int nch = (n + 63) / 64;
             for (int k = 0; k < nch; k++) {
-                const int s0 = L.start[b] + (int)((int64_t)n * k / nch);
-                const int s1 = L.start[b] + (int)((int64_t)n * (k + 1) / nch);
-                ch.push_back(make_int4(b, s0, s1 - s0, 0));
+                const int s0 = r.x + (int)((int64_t)n * k / nch);
+                const int s1 = r.x + (int)((int64_t)n * (k + 1) / nch);
+                (leaf_pairs[li] > kHeavyPairs ? heavy : ch).push_back(make_int4(p.leaf_of[s0], s0, s1 - s0, (int)li));
             }
         }
+        p.nnchunk_light = (int)ch.size();
+        ch.insert(ch.end(), heavy.begin(), heavy.end());
         p.nnchunk = (int)ch.size();
         UP(p.d_nchunk, ch);
     }
@@ -209,8 +273,12 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         for (int b = 0; b < L.nbox; b++)
             for (int si = L.start[b]; si < L.start[b + 1]; si++) box_of[si] = b;
         UP(p.d_box_of[d], box_of);
+        UP(p.d_alive[d], L.alive);
+        p.nleaf_rc[d] = (int)L.leaf_rc.size();
+        if (!L.leaf_rc.empty()) UP(p.d_leaf_rc[d], L.leaf_rc);
         std::vector<int4> ch;
         for (int b = 0; b < L.nbox; b++) {
+            if (!L.alive[b]) continue;  // below a coarser leaf: no level-d interpolation for these points
             const int n = L.start[b + 1] - L.start[b];
             const int nch = (n + 31) / 32;
             for (int k = 0; k < nch; k++) {

@@ -39,6 +39,7 @@ void ifgf_params_default(ifgf_params *p, double k) {
     p->cone_band = 1e-4;
     p->far_field = 0;
     p->layer = IFGF_LAYER_COMBINED;
+    p->leaf_max = 0;
 }
 
 const char *ifgf_supported_orders(void) { return "3x5,4x6,5x7,5x8,6x8"; }
@@ -70,8 +71,9 @@ static ifgf_status validate(const double *xyz, const double *normals, const doub
     }
     if (pr.nC0 < 1 || pr.nS0 < 1 || pr.nC0 > 64 || pr.nS0 > 64 || pr.cone_rule < 0 || pr.cone_rule > 1 ||
         pr.factor_mode < 0 || pr.factor_mode > 2 || !(pr.cone_band >= 0) || !std::isfinite(pr.identity_coef) ||
-        pr.far_field < 0 || pr.far_field > 1 || pr.layer < IFGF_LAYER_COMBINED || pr.layer > IFGF_LAYER_SINGLE) {
-        set_error("invalid cone, factor, far-field or layer parameters");
+        pr.far_field < 0 || pr.far_field > 1 || pr.layer < IFGF_LAYER_COMBINED || pr.layer > IFGF_LAYER_SINGLE ||
+        pr.leaf_max < 0) {
+        set_error("invalid cone, factor, far-field, layer or leaf_max parameters");
         return IFGF_EINVAL;
     }
     if (!supported_pair(pr.Ps, pr.Pang)) {
@@ -129,6 +131,7 @@ static void fill_info(const Plan &p, ifgf_info *out) {
     out->near_pairs = p.near_pairs;
     out->correction_nnz = p.corr_nnz;
     out->device_bytes = p.device_bytes;
+    out->near_block_chunks = p.adaptive ? p.nnchunk - p.nnchunk_light : 0;
 }
 
 ifgf_status ifgf_plan_dry_run(const double *xyz, const double *normals, const double *weights, int64_t N,

@@ -123,13 +123,15 @@ __device__ __forceinline__ void node64(const LevelArgs &L, const ChebTab &tb, in
     u[2] = ct;
 }
 
-// K1 (FP64): F at the relevant leaf cone nodes.
+// K1 (FP64): F at the relevant leaf cone nodes.  rc_list: the relevant cones of the leaves of a
+// coarser level of an adaptive tree (nlist of them); nullptr: every relevant cone of the level.
 template <int PS, int PA>
-__global__ void __launch_bounds__(kBlock) k_leaf64(CommonArgs ca, LevelArgs L, ChebTab tb, const double2 *__restrict__ a) {
+__global__ void __launch_bounds__(kBlock) k_leaf64(CommonArgs ca, LevelArgs L, ChebTab tb, const double2 *__restrict__ a,
+                                                   const int *__restrict__ rc_list, long long nlist) {
     constexpr int P = PS * PA * PA;
     long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid >= L.nrc * P) return;
-    int rc = (int)(tid / P), n = (int)(tid % P);
+    if (tid >= nlist * P) return;
+    int rc = rc_list ? rc_list[tid / P] : (int)(tid / P), n = (int)(tid % P);
     int b = L.rc_box[rc];
     double s, u[3];
     node64<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
@@ -311,10 +313,12 @@ __global__ void __launch_bounds__(kBlock) k_near64(CommonArgs ca, LevelArgs L, c
 // K2 (FP64): u(x) += sum over cousin boxes of level d of E(x;y_k) Interp(F_k)(x).
 template <int PS, int PA>
 __global__ void __launch_bounds__(kBlock) k_cousin64(CommonArgs ca, LevelArgs L, const int *__restrict__ box_of,
-                                                     ChebTab tb, double2 *__restrict__ u) {
+                                                     const uint8_t *__restrict__ alive, ChebTab tb,
+                                                     double2 *__restrict__ u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ca.N) return;
     int b = box_of[i];
+    if (!alive[b]) return;  // below a coarser leaf: no level-d box for this point
     const double x0 = ca.x64[3 * i], x1 = ca.x64[3 * i + 1], x2 = ca.x64[3 * i + 2];
     const double2 *F = (const double2 *)L.F;
     const double c4 = 1.0 / (4.0 * kPi);
@@ -513,6 +517,68 @@ __global__ void __launch_bounds__(kBlock) k_leaf32(CommonArgs ca, LevelArgs L, C
                 if (SPLIT) F[(base + 1) * ca.Pstride + n] = acc1[qq].get();
             }
         }
+    }
+}
+
+// K1 (mixed) for the leaves of a coarser level d of an adaptive tree: the arithmetic of k_leaf32 with
+// one thread per (listed relevant cone, node).  A source's offset from the leaf's centre is its
+// offset from its level-D box centre plus the difference of the two centres, exact in leaf units
+// (integer box coordinates times powers of two).
+template <int PS, int PA, bool SPLIT>
+__global__ void __launch_bounds__(kBlock) k_leaf32a(CommonArgs ca, LevelArgs L, LevelArgs LD, ChebTab tb,
+                                                    const float2 *__restrict__ a, const int *__restrict__ rc_list,
+                                                    long long nlist) {
+    constexpr int P = PS * PA * PA;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= nlist * P) return;
+    const int rc = rc_list[tid / P], n = (int)(tid % P);
+    const int b = L.rc_box[rc];
+    float s, u[3];
+    node32<PS, PA>(L, tb, L.rc_cone[rc], n, s, u);
+    const float ir = s / L.hu, kap = ca.kappa_hi, soh = s / (L.hu * ca.HDf);
+    const float kf = ca.kf, etaf = ca.etaf, etaif = ca.etaif;
+    const float cb0 = (L.ijk[3 * b] + 0.5f) * L.scale, cb1 = (L.ijk[3 * b + 1] + 0.5f) * L.scale,
+                cb2 = (L.ijk[3 * b + 2] + 0.5f) * L.scale;
+    const int j0 = L.start[b], j1 = L.start[b + 1];
+    float2 *F = (float2 *)L.F;
+    for (int q = 0; q < ca.nrhs; q++) {
+        PAcc acc0, acc1;
+        acc0.zero();
+        acc1.zero();
+        for (int j = j0; j < j1; j++) {
+            const int e = ca.leaf_of[j];
+            const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
+            const float f0 = fj.x + ((LD.ijk[3 * e] + 0.5f) - cb0), f1 = fj.y + ((LD.ijk[3 * e + 1] + 0.5f) - cb1),
+                        f2 = fj.z + ((LD.ijk[3 * e + 2] + 0.5f) - cb2);
+            const float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
+            const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
+            const float ia = rsqrtf(a2), am = a2 * ia;
+            const float yy = f0 * f0 + f1 * f1 + f2 * f2, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
+            float t = kap * __fdividef(ir * yy - 2.f * uy, am + 1.f);
+            t -= rintf(t);
+            float sn, cs;
+            cis_cycles(t, sn, cs);
+            const float dn = dv0 * nj.x + dv1 * nj.y + dv2 * nj.z;
+            const float w3 = dn * ia * ia, w2 = w3 * ia;
+            const float g = kf * w3 + etaf * ia, hr = etaif * ia;
+            float W0r, W0i, W1r = 0.f, W1i = 0.f;
+            if (SPLIT) {
+                W0r = cs * w2;
+                W0i = sn * w2;
+                W1r = cs * hr + sn * g;
+                W1i = sn * hr - cs * g;
+            } else {
+                const float w2s = soh * w2 + hr;
+                W0r = cs * w2s + sn * g;
+                W0i = sn * w2s - cs * g;
+            }
+            const float2 aj = a[(long long)q * ca.N + j];
+            acc0.add(aj.x * W0r - aj.y * W0i, aj.x * W0i + aj.y * W0r);
+            if (SPLIT) acc1.add(aj.x * W1r - aj.y * W1i, aj.x * W1i + aj.y * W1r);
+        }
+        const long long base = ((long long)q * L.nrc + rc) * L.nfac;
+        F[base * ca.Pstride + n] = acc0.get();
+        if (SPLIT) F[(base + 1) * ca.Pstride + n] = acc1.get();
     }
 }
 
@@ -872,6 +938,252 @@ __global__ void __launch_bounds__(kNearWarps * 32) k_near32p(CommonArgs ca, Leve
     if (v1) u[i1] = fold(ra[1], rb[1], im[1]);
 }
 
+// ---- near field of an adaptive tree -------------------------------------------------------------
+// A chunk holds at most 64 targets of one leaf (of any level); the leaf's near sources are a list of
+// contiguous point ranges (every level-D box under an existing box is contiguous in point order) with
+// the matching pair ranges.  A source's level-D box differs from pair to pair, so its integer box
+// coordinates travel with it, packed 21 bits per axis (depth <= 20); the target-source offset is the
+// exact integer box difference plus the two leaf-unit offsets, as in k_near32.  The source itself is
+// dropped by the distance test (its offset is exactly zero), like any pair closer than the tolerance.
+// Chunks of leaves with long lists (a small leaf of a coarse level beside dense boxes) run as one
+// block whose warps split the sources, summed in warp order in shared memory.
+constexpr int kNearBlkWarps = 16;
+
+__device__ __forceinline__ void unpack_ijk(unsigned long long k, int &c0, int &c1, int &c2) {
+    c0 = (int)(k & 0x1fffffULL);
+    c1 = (int)((k >> 21) & 0x1fffffULL);
+    c2 = (int)((k >> 42) & 0x1fffffULL);
+}
+
+// the two targets of a lane: level-D box coordinates and leaf-unit offsets
+struct NearTargets {
+    int ai[2][3];
+    float4 fv[2];
+};
+
+__device__ __forceinline__ NearTargets near_targets(const CommonArgs &ca, const unsigned long long *__restrict__ pt_ijk,
+                                                    int i0, int i1) {
+    NearTargets t;
+    unpack_ijk(__ldg(pt_ijk + i0), t.ai[0][0], t.ai[0][1], t.ai[0][2]);
+    unpack_ijk(__ldg(pt_ijk + i1), t.ai[1][0], t.ai[1][1], t.ai[1][2]);
+    t.fv[0] = __ldg(ca.pn32 + 2 * i0);
+    t.fv[1] = __ldg(ca.pn32 + 2 * i1);
+    return t;
+}
+
+// one right-hand side: the lane's two targets against the source pairs p0, p0 + step, ... < p1
+// (k_near32p's arithmetic with per-pair box coordinates); accumulates (Re Kr a, Im Ki a, imag) per target
+__device__ __forceinline__ void near_pairs_acc(const CommonArgs &ca, const NearTargets &t, int p0, int p1, int step,
+                                               const ulonglong2 *__restrict__ pp, const ulonglong2 *__restrict__ ap,
+                                               u64 (&ra)[2], u64 (&rb)[2], u64 (&im)[2]) {
+    const float c4 = 1.f / (4.f * kPiF * ca.HDf);
+    const float tolu = (float)(ca.tol / ca.HD), tolu2 = tolu * tolu;
+    const u64 kap2 = f2dup(ca.kappa_hi), kf2 = f2dup(ca.kf), eta2 = f2dup(ca.etaf), etai2 = f2dup(ca.etaif);
+    const u64 iHD2 = f2dup(1.f / ca.HDf);
+    for (int pm = p0; pm < p1; pm += step) {
+        const ulonglong2 R0 = __ldg(pp + 4 * pm), R1 = __ldg(pp + 4 * pm + 1), R2 = __ldg(pp + 4 * pm + 2),
+                         R3 = __ldg(pp + 4 * pm + 3), A = __ldg(ap + pm);
+        int c0, c1, c2;
+        unpack_ijk(R3.y, c0, c1, c2);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const u64 dx = f2sub(f2dup((float)(t.ai[k][0] - c0) + t.fv[k].x), R0.x),
+                      dy = f2sub(f2dup((float)(t.ai[k][1] - c1) + t.fv[k].y), R0.y),
+                      dz = f2sub(f2dup((float)(t.ai[k][2] - c2) + t.fv[k].z), R1.x);
+            const u64 r2 = f2fma3(dz, dz, f2fma3(dy, dy, f2mul(dx, dx)));
+            float r2l, r2h;
+            f2unpack(r2, r2l, r2h);
+            const bool kl = r2l >= tolu2, kh = r2h >= tolu2;
+            const float irl = rsqrtf(fmaxf(r2l, 1e-30f)), irh = rsqrtf(fmaxf(r2h, 1e-30f));
+            const u64 ir = f2pack(irl, irh);
+            u64 tt = f2mul(kap2, f2mul(r2, ir));
+            float tl, th;
+            f2unpack(tt, tl, th);
+            tt = f2sub(tt, f2pack(rintf(tl), rintf(th)));
+            f2unpack(tt, tl, th);
+            float snl, csl, snh, csh;
+            cis_cycles(tl, snl, csl);
+            cis_cycles(th, snh, csh);
+            const u64 dn = f2fma3(dz, R3.x, f2fma3(dy, R2.y, f2mul(dx, R2.x)));
+            const u64 amp = f2pack(kl ? c4 * irl : 0.f, kh ? c4 * irh : 0.f);
+            const u64 dnir = f2mul(dn, ir);
+            const u64 Ar = f2mul(amp, f2fma3(f2mul(dnir, ir), iHD2, etai2));
+            const u64 nB = f2mul(amp, f2fma3(kf2, dnir, eta2));
+            const u64 Kr = f2fma3(f2pack(snl, snh), nB, f2mul(f2pack(csl, csh), Ar));
+            const u64 Ki = f2fma3(f2pack(-csl, -csh), nB, f2mul(f2pack(snl, snh), Ar));
+            ra[k] = f2fma3(Kr, A.x, ra[k]);
+            rb[k] = f2fma3(Ki, A.y, rb[k]);
+            im[k] = f2fma3(Ki, A.x, f2fma3(Kr, A.y, im[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ float2 near_fold(u64 x, u64 y, u64 z) {
+    float xl, xh, yl, yh, zl, zh;
+    f2unpack(x, xl, xh);
+    f2unpack(y, yl, yh);
+    f2unpack(z, zl, zh);
+    return make_float2((xl - yl) + (xh - yh), zl + zh);
+}
+
+// several right-hand sides, RB at a time from q0: the lane's two targets against the sources
+// j0, j0 + step, ... < j1 (near_pair32's arithmetic)
+template <int RB>
+__device__ __forceinline__ void near_points_acc(const CommonArgs &ca, const NearTargets &t, int j0, int j1, int step,
+                                                const unsigned long long *__restrict__ pt_ijk, int q0,
+                                                const float2 *__restrict__ a, PAcc (&A0)[RB], PAcc (&A1)[RB]) {
+    const float c4 = 1.f / (4.f * kPiF * ca.HDf), iHD = 1.f / ca.HDf;
+    const float tolu = (float)(ca.tol / ca.HD), tolu2 = tolu * tolu;
+    for (int j = j0; j < j1; j += step) {
+        const float4 fj = __ldg(ca.pn32 + 2 * j), nj = __ldg(ca.pn32 + 2 * j + 1);
+        int c0, c1, c2;
+        unpack_ijk(__ldg(pt_ijk + j), c0, c1, c2);
+        float K0r, K0i, K1r, K1i;
+        near_pair32(ca, (float)(t.ai[0][0] - c0) + t.fv[0].x, (float)(t.ai[0][1] - c1) + t.fv[0].y,
+                    (float)(t.ai[0][2] - c2) + t.fv[0].z, fj, nj, c4, iHD, tolu2, true, K0r, K0i);
+        near_pair32(ca, (float)(t.ai[1][0] - c0) + t.fv[1].x, (float)(t.ai[1][1] - c1) + t.fv[1].y,
+                    (float)(t.ai[1][2] - c2) + t.fv[1].z, fj, nj, c4, iHD, tolu2, true, K1r, K1i);
+#pragma unroll
+        for (int qq = 0; qq < RB; qq++) {
+            if (RB == 1 || q0 + qq < ca.nrhs) {
+                const float2 aj = a[(long long)(q0 + qq) * ca.N + j];
+                A0[qq].add(K0r * aj.x - K0i * aj.y, K0r * aj.y + K0i * aj.x);
+                A1[qq].add(K1r * aj.x - K1i * aj.y, K1r * aj.y + K1i * aj.x);
+            }
+        }
+    }
+}
+
+// one warp per chunk (at most 64 targets), several right-hand sides
+template <int RB>
+__global__ void __launch_bounds__(kNearWarps * 32) k_near32r(CommonArgs ca, const int4 *__restrict__ chunks, int nchunk,
+                                                            const int *__restrict__ nr_start,
+                                                            const int4 *__restrict__ nr,
+                                                            const unsigned long long *__restrict__ pt_ijk,
+                                                            const float2 *__restrict__ a, float2 *__restrict__ u) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kNearWarps + warp;
+    if (ch >= nchunk) return;  // warp-uniform
+    const int4 cw = chunks[ch];
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
+    const NearTargets t = near_targets(ca, pt_ijk, i0, i1);
+    const int r0 = nr_start[cw.w], r1 = nr_start[cw.w + 1];
+    for (int q0 = 0; q0 < ca.nrhs; q0 += RB) {
+        PAcc A0[RB], A1[RB];
+#pragma unroll
+        for (int qq = 0; qq < RB; qq++) {
+            A0[qq].zero();
+            A1[qq].zero();
+        }
+        for (int r = r0; r < r1; r++) {
+            const int4 rg = __ldg(nr + r);
+            near_points_acc<RB>(ca, t, rg.x, rg.y, 1, pt_ijk, q0, a, A0, A1);
+        }
+#pragma unroll
+        for (int qq = 0; qq < RB; qq++)
+            if (RB == 1 || q0 + qq < ca.nrhs) {
+                if (v0) u[(long long)(q0 + qq) * ca.N + i0] = A0[qq].get();
+                if (v1) u[(long long)(q0 + qq) * ca.N + i1] = A1[qq].get();
+            }
+    }
+}
+
+// one warp per chunk, one right-hand side on the source pairs (the pair record's last slot holds the
+// packed coordinates of its level-D box; both sources of a pair share it)
+__global__ void __launch_bounds__(kNearWarps * 32) k_near32pr(CommonArgs ca, const int4 *__restrict__ chunks, int nchunk,
+                                                             const int *__restrict__ nr_start,
+                                                             const int4 *__restrict__ nr,
+                                                             const unsigned long long *__restrict__ pt_ijk,
+                                                             const ulonglong2 *__restrict__ pp,
+                                                             const ulonglong2 *__restrict__ ap, float2 *__restrict__ u) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * kNearWarps + warp;
+    if (ch >= nchunk) return;  // warp-uniform
+    const int4 cw = chunks[ch];
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
+    const NearTargets t = near_targets(ca, pt_ijk, i0, i1);
+    u64 ra[2] = {0ull, 0ull}, rb[2] = {0ull, 0ull}, im[2] = {0ull, 0ull};
+    for (int r = nr_start[cw.w]; r < nr_start[cw.w + 1]; r++) {
+        const int4 rg = __ldg(nr + r);
+        near_pairs_acc(ca, t, rg.z, rg.w, 1, pp, ap, ra, rb, im);
+    }
+    if (v0) u[i0] = near_fold(ra[0], rb[0], im[0]);
+    if (v1) u[i1] = near_fold(ra[1], rb[1], im[1]);
+}
+
+// one block per chunk of a leaf with a long source list: warp w takes every kNearBlkWarps-th source
+// (pair) of each range; the warps' partial sums are added in warp order
+__global__ void __launch_bounds__(kNearBlkWarps * 32) k_near32pr_blk(CommonArgs ca, const int4 *__restrict__ chunks,
+                                                                    const int *__restrict__ nr_start,
+                                                                    const int4 *__restrict__ nr,
+                                                                    const unsigned long long *__restrict__ pt_ijk,
+                                                                    const ulonglong2 *__restrict__ pp,
+                                                                    const ulonglong2 *__restrict__ ap,
+                                                                    float2 *__restrict__ u) {
+    __shared__ float2 part[kNearBlkWarps][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 cw = chunks[blockIdx.x];
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
+    const NearTargets t = near_targets(ca, pt_ijk, i0, i1);
+    u64 ra[2] = {0ull, 0ull}, rb[2] = {0ull, 0ull}, im[2] = {0ull, 0ull};
+    for (int r = nr_start[cw.w]; r < nr_start[cw.w + 1]; r++) {
+        const int4 rg = __ldg(nr + r);
+        near_pairs_acc(ca, t, rg.z + warp, rg.w, kNearBlkWarps, pp, ap, ra, rb, im);
+    }
+    part[warp][lane] = near_fold(ra[0], rb[0], im[0]);
+    part[warp][lane + 32] = near_fold(ra[1], rb[1], im[1]);
+    __syncthreads();
+    if (threadIdx.x < cw.z) {
+        float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < kNearBlkWarps; w++) {
+            z.x += part[w][threadIdx.x].x;
+            z.y += part[w][threadIdx.x].y;
+        }
+        u[cw.y + threadIdx.x] = z;
+    }
+}
+
+// the same for several right-hand sides, one at a time
+__global__ void __launch_bounds__(kNearBlkWarps * 32) k_near32r_blk(CommonArgs ca, const int4 *__restrict__ chunks,
+                                                                   const int *__restrict__ nr_start,
+                                                                   const int4 *__restrict__ nr,
+                                                                   const unsigned long long *__restrict__ pt_ijk,
+                                                                   const float2 *__restrict__ a,
+                                                                   float2 *__restrict__ u) {
+    __shared__ float2 part[kNearBlkWarps][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int4 cw = chunks[blockIdx.x];
+    const bool v0 = lane < cw.z, v1 = lane + 32 < cw.z;
+    const int i0 = cw.y + (v0 ? lane : 0), i1 = cw.y + (v1 ? lane + 32 : 0);
+    const NearTargets t = near_targets(ca, pt_ijk, i0, i1);
+    for (int q = 0; q < ca.nrhs; q++) {
+        PAcc A0[1], A1[1];
+        A0[0].zero();
+        A1[0].zero();
+        for (int r = nr_start[cw.w]; r < nr_start[cw.w + 1]; r++) {
+            const int4 rg = __ldg(nr + r);
+            near_points_acc<1>(ca, t, rg.x + warp, rg.y, kNearBlkWarps, pt_ijk, q, a, A0, A1);
+        }
+        part[warp][lane] = A0[0].get();
+        part[warp][lane + 32] = A1[0].get();
+        __syncthreads();
+        if (threadIdx.x < cw.z) {
+            float2 z = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int w = 0; w < kNearBlkWarps; w++) {
+                z.x += part[w][threadIdx.x].x;
+                z.y += part[w][threadIdx.x].y;
+            }
+            u[(long long)q * ca.N + cw.y + threadIdx.x] = z;
+        }
+        __syncthreads();  // part is rewritten by the next right-hand side
+    }
+}
+
 // K2 (mixed): geometry of one (target, cousin box) pair.
 struct CousGeo {
     int rc;
@@ -1203,11 +1515,13 @@ __global__ void __launch_bounds__(kCsWarps * 32) k_cousin_cs(CommonArgs ca, Leve
 // slot order with Kahan compensation (one thread per target; the slots of a box's targets
 // are contiguous, so consecutive threads read consecutive values).
 __global__ void __launch_bounds__(kBlock) k_cousin_sum(CommonArgs ca, LevelArgs L, const int *__restrict__ box_of,
-                                                       const int *__restrict__ pvoff, const float2 *__restrict__ pv,
-                                                       long long pv_stride, float2 *__restrict__ u) {
+                                                       const uint8_t *__restrict__ alive, const int *__restrict__ pvoff,
+                                                       const float2 *__restrict__ pv, long long pv_stride,
+                                                       float2 *__restrict__ u) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ca.N) return;
     const int b = box_of[i];
+    if (!alive[b]) return;  // below a coarser leaf: no level-d box for this point
     const int s0 = L.start[b], nt = L.start[b + 1] - s0;
     const int ncous = L.co_start[b + 1] - L.co_start[b];
     const long long base = (long long)pvoff[b] + (i - s0);
@@ -3756,12 +4070,14 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
             prof_mark(p, sb, kStNear, D);
         }
         if (L[D].nrc) {
-            k_leaf64<PS, PA><<<nblk(L[D].nrc * P), kBlock, 0, s>>>(ca, L[D], tb, (const double2 *)p.ws.a);
+            k_leaf64<PS, PA><<<nblk(L[D].nrc * P), kBlock, 0, s>>>(ca, L[D], tb, (const double2 *)p.ws.a, nullptr,
+                                                                   L[D].nrc);
             prof_mark(p, s, kStLeaf, D);
         }
         fork(1);
         if (down) {
-            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], p.d_box_of[D], tb, (double2 *)p.ws.u);
+            k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[D], p.d_box_of[D], p.d_alive[D], tb,
+                                                           (double2 *)p.ws.u);
             prof_mark(p, sb, kStCousin, D);
         }
         for (int d = D; d >= 4; d--) {
@@ -3769,9 +4085,15 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 k_prop64<PS, PA><<<nblk(L[d - 1].nrc * P), kBlock, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
             }
+            if (p.nleaf_rc[d - 1]) {  // adaptive tree: the leaves of level d-1 (no children, F from sources)
+                const long long nl = p.nleaf_rc[d - 1];
+                k_leaf64<PS, PA><<<nblk(nl * P), kBlock, 0, s>>>(ca, L[d - 1], tb, (const double2 *)p.ws.a,
+                                                                 p.d_leaf_rc[d - 1], nl);
+                prof_mark(p, s, kStLeaf, d - 1);
+            }
             fork(2 + D - d);
             if (down) {
-                k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[d - 1], p.d_box_of[d - 1], tb,
+                k_cousin64<PS, PA><<<nblk(N), kBlock, 0, sb>>>(ca, L[d - 1], p.d_box_of[d - 1], p.d_alive[d - 1], tb,
                                                                (double2 *)p.ws.u);
                 prof_mark(p, sb, kStCousin, d - 1);
             }
@@ -3806,7 +4128,8 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                         k_cousin_cs<PS, PA, false><<<g, kCsWarps * 32, 0, sb>>>(
                             ca, L[d], p.d_cs_item[d], ni, p.d_cs_geo4[d], p.d_cs_geo2[d], tb, pv, stride);
                     prof_mark(p, sb, kStCousin, d);
-                    k_cousin_sum<<<nblk(N), kBlock, 0, sb>>>(ca, L[d], p.d_box_of[d], p.d_cs_pvoff[d], pv, stride, u32);
+                    k_cousin_sum<<<nblk(N), kBlock, 0, sb>>>(ca, L[d], p.d_box_of[d], p.d_alive[d], p.d_cs_pvoff[d], pv,
+                                                             stride, u32);
                     prof_mark(p, sb, kStCousinSum, d);
                 }
                 return;
@@ -3826,7 +4149,31 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
         fork(0);
         if (down) {
             const unsigned gn = (unsigned)((p.nnchunk + kNearWarps - 1) / kNearWarps);
-            if (nrhs == 1)
+            if (p.adaptive) {  // leaves of several levels: ranges of near sources per leaf
+                const unsigned gl = (unsigned)((p.nnchunk_light + kNearWarps - 1) / kNearWarps);
+                const int4 *hv = p.d_nchunk + p.nnchunk_light;
+                const int nh = p.nnchunk - p.nnchunk_light;
+                if (nrhs == 1) {
+                    if (gl)
+                        k_near32pr<<<gl, kNearWarps * 32, 0, sb>>>(ca, p.d_nchunk, p.nnchunk_light, p.d_nr_start, p.d_nr,
+                                                                   p.d_pt_ijk, pp, ap, u32);
+                    if (nh)
+                        k_near32pr_blk<<<nh, kNearBlkWarps * 32, 0, sb>>>(ca, hv, p.d_nr_start, p.d_nr, p.d_pt_ijk, pp,
+                                                                          ap, u32);
+                } else {
+                    const float2 *a32 = (const float2 *)p.ws.a;
+                    if (gl && rb1)
+                        k_near32r<1><<<gl, kNearWarps * 32, 0, sb>>>(ca, p.d_nchunk, p.nnchunk_light, p.d_nr_start,
+                                                                     p.d_nr, p.d_pt_ijk, a32, u32);
+                    else if (gl)
+                        k_near32r<kRB><<<gl, kNearWarps * 32, 0, sb>>>(ca, p.d_nchunk, p.nnchunk_light, p.d_nr_start,
+                                                                       p.d_nr, p.d_pt_ijk, a32, u32);
+                    if (nh)
+                        k_near32r_blk<<<nh, kNearBlkWarps * 32, 0, sb>>>(ca, hv, p.d_nr_start, p.d_nr, p.d_pt_ijk, a32,
+                                                                         u32);
+                }
+            }
+            else if (nrhs == 1)
                 k_near32p<<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, pp, p.d_pstart, ap, u32);
             else if (rb1)
                 k_near32<1><<<gn, kNearWarps * 32, 0, sb>>>(ca, L[D], p.d_nchunk, p.nnchunk, (const float2 *)p.ws.a, u32);
@@ -3911,6 +4258,17 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 if (rb1) k_prop_w<PS, PA, 1><<<gw, kCwWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb);
                 else k_prop_w<PS, PA, kRB><<<gw, kCwWarps * 32, 0, s>>>(ca, L[d], L[d - 1], tb);
                 prof_mark(p, s, kStProp, d - 1);
+            }
+            if (p.nleaf_rc[d - 1]) {  // adaptive tree: the leaves of level d-1 (no children, F from sources)
+                const long long nl = p.nleaf_rc[d - 1];
+                const float2 *a32 = (const float2 *)p.ws.a;
+                if (L[d - 1].split)
+                    k_leaf32a<PS, PA, true><<<nblk(nl * P), kBlock, 0, s>>>(ca, L[d - 1], L[D], tb, a32,
+                                                                            p.d_leaf_rc[d - 1], nl);
+                else
+                    k_leaf32a<PS, PA, false><<<nblk(nl * P), kBlock, 0, s>>>(ca, L[d - 1], L[D], tb, a32,
+                                                                             p.d_leaf_rc[d - 1], nl);
+                prof_mark(p, s, kStLeaf, d - 1);
             }
             fork(2 + D - d);
             cousin(d - 1);

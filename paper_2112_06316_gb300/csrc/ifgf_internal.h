@@ -40,6 +40,10 @@ struct HostLevel {
     // source boxes: boxes holding a point of positive weight (all boxes unless the plan has targets);
     // the others have no relevant cones, no children in ch_list and act on nothing
     std::vector<uint8_t> active;
+    // adaptive octree: a box exists (alive) when every ancestor is subdivided; a leaf is alive and not
+    // subdivided.  Uniform trees: all boxes alive, leaves at level D.  `active` implies alive.
+    std::vector<uint8_t> alive, leaf;
+    std::vector<int> leaf_rc;  // relevant cones of the source leaf boxes of this level (levels < D)
     std::vector<int> rc_start, rc_cone, rc_box;  // relevant cones (Eq. RelevantCones)
     std::vector<int> cone_map;                   // nbox * ncone -> rc index or -1
     int64_t nrc = 0;
@@ -162,6 +166,9 @@ struct Plan {
     // (Im E, value-buffer slot as int bits)
     float4 *d_cs_geo4[IFGF_MAXD + 1] = {};
     int *d_cs_first[IFGF_MAXD + 1] = {};  // per relevant cone: its first entry (the adjoint reuses the geometry)
+    uint8_t *d_alive[IFGF_MAXD + 1] = {};  // per box: it exists (adaptive octree; all 1 otherwise)
+    int *d_leaf_rc[IFGF_MAXD + 1] = {};    // relevant cones of the level's source leaves (levels < D)
+    int nleaf_rc[IFGF_MAXD + 1] = {};
     float2 *d_cs_geo2[IFGF_MAXD + 1] = {};
     int *d_cs_pvoff[IFGF_MAXD + 1] = {};
     int64_t cs_max_entries = 0;  // largest per-level pair count (size of the value buffer per rhs)
@@ -170,6 +177,7 @@ struct Plan {
     // leaf box in near-equal runs of at most 64
     int4 *d_nchunk = nullptr;
     int nnchunk = 0;
+    int nnchunk_light = 0;  // adaptive trees: the chunks before it run one warp each, the rest one block each
     double *d_x64 = nullptr, *d_n64 = nullptr, *d_w64 = nullptr;  // sorted, absolute FP64
     float *d_f32 = nullptr, *d_n32 = nullptr, *d_w32 = nullptr;   // sorted, leaf offsets / normals / weights
     float4 *d_pn32 = nullptr;                                      // sorted, (offset, |offset|^2), (normal, 0)
@@ -178,6 +186,11 @@ struct Plan {
     float4 *d_pp32 = nullptr;
     int *d_pstart = nullptr;
     int2 *d_pair_src = nullptr;
+    // adaptive trees: per leaf (in point order) its near sources as (point start, point end, pair start,
+    // pair end) ranges; per point its level-D box coordinates packed 21 bits per axis
+    int *d_nr_start = nullptr;
+    int4 *d_nr = nullptr;
+    unsigned long long *d_pt_ijk = nullptr;
     int npairs = 0;
     unsigned long long *d_missed = nullptr;
     TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
@@ -214,7 +227,8 @@ struct Plan {
     // plans built with off-surface targets (ifgf_plan_create_with_targets): the points are the n_src
     // sources followed by the n_tgt targets (weight 0); N = n_src + n_tgt.  0, 0 for an ordinary plan.
     int64_t n_src = 0, n_tgt = 0;
-    bool has_inactive = false;  // some box holds targets only (see HostLevel::active)
+    bool has_inactive = false;  // some box holds targets only or lies below a leaf (see HostLevel)
+    bool adaptive = false;      // leaves at several levels (params.leaf_max > 0)
     void *field_ws = nullptr;    // off-surface / far-field evaluation: gathered w*sigma and per-chunk partial sums
     size_t field_ws_bytes = 0;
 

@@ -285,13 +285,32 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                 L.parent[b] = find_box(p.lv[d - 1], L.ijk[3 * b] >> 1, L.ijk[3 * b + 1] >> 1, L.ijk[3 * b + 2] >> 1);
         }
     }
-    // source boxes (points of positive weight; a plan with targets has boxes without any)
+    // adaptive octree (leaf_max > 0): a box of level 3..D-1 holding at most leaf_max points is a leaf
+    // and the boxes below it do not exist; otherwise every box exists and the leaves are at level D
+    p.adaptive = prm.leaf_max > 0;
     p.has_inactive = false;
+    for (int d = 1; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.alive.assign(L.nbox, 1);
+        L.leaf.assign(L.nbox, d == D ? 1 : 0);
+        if (d < 3) continue;
+        for (int b = 0; b < L.nbox; b++) {
+            if (d > 3) {
+                const HostLevel &PL = p.lv[d - 1];
+                L.alive[b] = PL.alive[L.parent[b]] && !PL.leaf[L.parent[b]];
+            }
+            L.leaf[b] = L.alive[b] && (d == D || (p.adaptive && L.start[b + 1] - L.start[b] <= prm.leaf_max));
+            p.has_inactive = p.has_inactive || !L.alive[b];
+        }
+    }
+    // source boxes: existing boxes holding a point of positive weight (a plan with targets has boxes
+    // without any)
     for (int d = 1; d <= D; d++) {
         HostLevel &L = p.lv[d];
         L.active.assign(L.nbox, 0);
         for (int b = 0; b < L.nbox; b++) {
-            for (int s = L.start[b]; s < L.start[b + 1] && !L.active[b]; s++) L.active[b] = w[p.perm[s]] > 0;
+            for (int s = L.start[b]; s < L.start[b + 1] && !L.active[b] && L.alive[b]; s++)
+                L.active[b] = w[p.perm[s]] > 0;
             p.has_inactive = p.has_inactive || !L.active[b];
         }
     }
@@ -309,24 +328,39 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
             if (C.active[b]) L.ch_list[fill[C.parent[b]]++] = b;
     }
     p.lv[D].ch_start.assign(p.lv[D].nbox + 1, 0);
-    // leaf neighbours (27-neighbourhood including the box itself)
+    // near-field lists per level-D box (the 27-neighbourhood including the box itself).  In an adaptive
+    // tree a point of a leaf at level d_t and one of a leaf at level d_s are near when their boxes at
+    // level min(d_t, d_s) neighbour: for the level-D box b below the leaf B (level d_B) that is every
+    // level-D box below an existing neighbour of B, and every level-D box below a leaf of a coarser
+    // level m that neighbours B's ancestor there (each source box exactly once).
     {
         const HostLevel &L = p.lv[D];
         p.nb_start.assign(L.nbox + 1, 0);
         p.nb_list.clear();
         int64_t pairs = 0;
+        std::vector<int> anc(D + 1);
         for (int b = 0; b < L.nbox; b++) {
             p.nb_start[b] = (int)p.nb_list.size();
             int64_t cnt = 0;
-            for (int o0 = -1; o0 <= 1; o0++)
-                for (int o1 = -1; o1 <= 1; o1++)
-                    for (int o2 = -1; o2 <= 1; o2++) {
-                        int c = find_box(L, L.ijk[3 * b] + o0, L.ijk[3 * b + 1] + o1, L.ijk[3 * b + 2] + o2);
-                        if (c >= 0) {
-                            p.nb_list.push_back(c);
-                            cnt += L.start[c + 1] - L.start[c];
+            anc[D] = b;
+            for (int d = D; d > 3; d--) anc[d - 1] = p.lv[d].parent[anc[d]];
+            int dB = 3;
+            while (!p.lv[dB].leaf[anc[dB]]) dB++;
+            for (int m = p.adaptive ? 3 : D; m <= dB; m++) {
+                const HostLevel &M = p.lv[m];
+                const int *q = &M.ijk[3 * anc[m]];
+                for (int o0 = -1; o0 <= 1; o0++)
+                    for (int o1 = -1; o1 <= 1; o1++)
+                        for (int o2 = -1; o2 <= 1; o2++) {
+                            const int c = find_box(M, q[0] + o0, q[1] + o1, q[2] + o2);
+                            if (c < 0 || !M.alive[c] || (m < dB && !M.leaf[c])) continue;
+                            const int f0 = p.leaf_of[M.start[c]], f1 = p.leaf_of[M.start[c + 1] - 1];
+                            for (int e = f0; e <= f1; e++) {
+                                p.nb_list.push_back(e);
+                                cnt += L.start[e + 1] - L.start[e];
+                            }
                         }
-                    }
+            }
             pairs += cnt * (L.start[b + 1] - L.start[b]);
         }
         p.nb_start[L.nbox] = (int)p.nb_list.size();
@@ -354,10 +388,10 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                         }
         }
         L.co_start[L.nbox] = (int)L.co_list.size();
-        int64_t ev = 0;  // (source box, point in one of its cousins) pairs
+        int64_t ev = 0;  // (source box, point in one of its existing cousins) pairs
         for (int b = 0; b < L.nbox; b++)
             for (int c = L.co_start[b]; c < L.co_start[b + 1] && L.active[b]; c++)
-                ev += L.start[L.co_list[c] + 1] - L.start[L.co_list[c]];
+                if (L.alive[L.co_list[c]]) ev += L.start[L.co_list[c] + 1] - L.start[L.co_list[c]];
         L.cousin_evals = ev;
     }
     // cone grids (Remark cone_seg_size) and factor split (Section 3.3)
@@ -470,6 +504,7 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
                     for (int c = 0; c < L.nC * L.nph; c++) bits[c >> 6] |= 1ULL << (c & 63);
                 for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
                     int cb = L.co_list[c];
+                    if (!L.alive[cb]) continue;  // points below a coarser leaf take no level-d interpolation
                     for (int s = L.start[cb]; s < L.start[cb + 1]; s++) mark_point(p, L, b, &xs[3 * s], tau, bits.data());
                 }
                 if (PL) {
@@ -514,13 +549,19 @@ ifgf_status build_host_plan(Plan &p, const double *xyz, const double *nrm, const
             p.lv[d - 1].prop_evals = pe;
         }
     }
-    {
-        const HostLevel &L = p.lv[D];
-        int64_t le = 0;
-        for (int b = 0; b < L.nbox; b++)
+    // leaf expansions: every level's source leaves (level D: all of its source boxes)
+    int64_t le = 0;
+    for (int d = 3; d <= D; d++) {
+        HostLevel &L = p.lv[d];
+        L.leaf_rc.clear();
+        for (int b = 0; b < L.nbox; b++) {
+            if (!L.leaf[b] || !L.active[b]) continue;
             le += (int64_t)(L.rc_start[b + 1] - L.rc_start[b]) * p.P * (L.start[b + 1] - L.start[b]);
-        p.leaf_evals = le;
+            if (d < D)
+                for (int rc = L.rc_start[b]; rc < L.rc_start[b + 1]; rc++) L.leaf_rc.push_back(rc);
+        }
     }
+    p.leaf_evals = le;
     return IFGF_OK;
 }
 
@@ -610,6 +651,7 @@ ifgf_status build_adjoint_lists(Plan &p, const double *xs) {
             if (nr == 0) continue;
             for (int c = L.co_start[b]; c < L.co_start[b + 1]; c++) {
                 int cb = L.co_list[c];
+                if (!L.alive[cb]) continue;
                 for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
                     int rc = L.cone_map[(size_t)b * L.ncone + classify_exact(p, L, b, xs + 3 * si)];
                     if (rc >= 0) lists[rc - r0].push_back(si);
@@ -682,6 +724,7 @@ ifgf_status build_cousin_lists(Plan &p) {
             lists.assign(nr, std::vector<uint32_t>());
             for (int ci = L.co_start[c]; ci < L.co_start[c + 1] && nr > 0; ci++) {
                 const int cb = L.co_list[ci];
+                if (!L.alive[cb]) continue;  // no level-d box for these points
                 const uint32_t slot = (uint32_t)rev[ci] << 24;
                 for (int si = L.start[cb]; si < L.start[cb + 1]; si++) {
                     const int rc = L.cone_map[(size_t)c * L.ncone + classify_exact(p, L, c, xs + 3 * si)];

@@ -421,13 +421,10 @@ def test_ifgf_oracle_layers_converge_to_direct(oracle_lib, layer):
 def _two_spheres():
     """A unit sphere (1,536 points) and a sphere of radius 0.15 centred at (1.6, 0, 0) with 3,456
     points: a point density 20x higher in one corner of the root box."""
-    from workloads import cube_sphere
+    from workloads import two_spheres
 
-    a, b = cube_sphere(16, 8), cube_sphere(24, 8)
-    pts = np.concatenate([a.points, 0.15 * b.points + np.array([1.6, 0.0, 0.0])])
-    nrm = np.concatenate([a.normals, b.normals])
-    w = np.concatenate([a.weights, 0.15 ** 2 * b.weights])
-    return pts, nrm, w
+    s = two_spheres()
+    return s.points, s.normals, s.weights
 
 
 def test_adaptive_tree_reduces_to_uniform(oracle_lib):

@@ -12,6 +12,7 @@ from .geometry import (  # noqa: F401
     patch_node_index,
     star_body,
     sphere_workload,
+    two_spheres,
     random_density,
     scatterer_batch,
     Surface,

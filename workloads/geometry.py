@@ -245,6 +245,21 @@ def sphere_workload(n: int, m: int, wavelengths_diameter: float, radius: float =
     return s, 2.0 * math.pi / lam
 
 
+def two_spheres(n_big: int = 16, n_small: int = 24, radius_small: float = 0.15, offset: float = 1.6,
+                m: int = 8) -> Surface:
+    """A non-uniform point set: the unit cube-sphere (6 n_big^2 points) and a cube-sphere of radius
+    radius_small centred at (offset, 0, 0) with 6 n_small^2 points.  With the defaults (1,536 and
+    3,456 points) the small sphere's point density is 20x the large one's, in one corner of the
+    root box.  Patch ids of the small sphere follow the large sphere's."""
+    a, b = cube_sphere(n_big, m), cube_sphere(n_small, m)
+    c = np.array([offset, 0.0, 0.0])
+    return Surface("two_spheres", np.concatenate([a.points, radius_small * b.points + c]),
+                   np.concatenate([a.normals, b.normals]),
+                   np.concatenate([a.weights, radius_small ** 2 * b.weights]),
+                   np.concatenate([a.patch, b.patch + int(a.patch.max()) + 1]).astype(np.int32),
+                   np.concatenate([a.uv, b.uv]), dict(n_big=n_big, n_small=n_small, m=m))
+
+
 def random_density(N: int, nrhs: int, seed: int) -> np.ndarray:
     """Complex128 density, shape (nrhs, N) (one row per right-hand side).
 
