@@ -18,8 +18,9 @@ all ranks / max-over-ranks time.
 Beside the headline: a four-right-hand-side apply (per-rhs throughput), the
 adjoint and the vector-Jacobian product, an end-to-end apply through pinned host
 buffers, off-surface evaluation, the FP64 apply, the paper's orders (3, 5, 5),
-the 24-scatterer batch as one CUDA graph at the headline orders, and the FP64
-CPU oracle applied to the whole workload on the host cores (cpu_baseline).
+the 24-scatterer batch as one CUDA graph at the headline orders, the adaptive
+octree against the uniform one on a two-density point set, and the FP64 CPU
+oracle applied to the whole workload on the host cores (cpu_baseline).
 
 --impl reference times the FP64 CPU oracle (the IFGF apply of Section 3.4, OpenMP
 on the host cores) on a bounded sample of the same workload.
@@ -221,12 +222,15 @@ def algorithmic_flops(info, P, nrhs, split_levels):
     return leaf, near, cousin, prop
 
 
-def launches_of(stages, nrhs=1):
+def launches_of(stages, nrhs=1, near_blocks=0):
     """Kernel launches of one profiled mixed apply: one per stage entry, eight (one per child octant)
-    for a tensor-core or cone-stationary propagation level, two for the leaf stage with one
-    right-hand side (the density pairs are packed first)."""
-    return sum(8 if kind in ("prop_tc", "prop_cs") else 2 if kind == "leaf" and nrhs == 1 else 1
-               for kind, _, _ in stages)
+    for a tensor-core or cone-stationary propagation level, two for the level-D leaf stage with one
+    right-hand side (the density pairs are packed first; an adaptive tree's coarser leaves take one
+    each), two for the near field of an adaptive tree with block chunks (near_blocks > 0)."""
+    D = max((lev for kind, lev, _ in stages if kind == "leaf"), default=0)
+    return sum(8 if kind in ("prop_tc", "prop_cs") else 2 if kind == "leaf" and nrhs == 1 and lev == D
+               else 2 if kind == "near" and near_blocks > 0 else 1
+               for kind, lev, _ in stages)
 
 
 def reduce_over_ranks(ms: float, points: float, world: int, device="cpu"):
@@ -278,6 +282,61 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def adaptive_leg(args, timed, dev, Ps, Pang, rank, out):
+    """The adaptive octree (leaf_max = 64, depth up to 8) against the uniform tree (the automatic depth
+    and the best fixed depth) on a non-uniform point set: the unit sphere 8 wavelengths across (6 x 128
+    x 128 points) and a sphere of radius 0.1 centred at (1.6, 0, 0) with as many points (a point
+    density 100x higher), mixed apply at the headline orders, one right-hand side; errors against the
+    direct sum on sampled rows (rank 0)."""
+    import torch
+
+    from paper_2112_06316_gb300 import Params, Plan
+    from workloads import random_density, two_spheres
+
+    s2 = two_spheres(128, 128, 0.1, 1.6)
+    k2 = 8 * math.pi
+    sig_np = random_density(s2.N, 1, 11)
+    sig2 = torch.from_numpy(sig_np.astype(np.complex64)).to(dev)
+    y2 = torch.empty_like(sig2)
+    kk = max(5, args.steps // 4)
+    res = {"workload": f"two spheres: unit sphere 8 wavelengths across (k={k2:.4f}), cube-sphere 6x128x128, and "
+                       f"radius 0.1 at (1.6, 0, 0), 6x128x128 (density 100x); N={s2.N}; orders ({Ps},{Pang},{Pang}), "
+                       f"factor mode {args.factor_mode}, one right-hand side, mixed",
+           "N": s2.N, "steps": kk}
+    ys = {}
+    for name, kw in (("adaptive_leaf64_D8", dict(levels=8, leaf_max=64)), ("uniform_auto_depth", {}),
+                     ("uniform_D7", dict(levels=7))):
+        t0 = time.perf_counter()
+        pl = Plan(s2.points, s2.normals, s2.weights, Params(k=k2, Ps=Ps, Pang=Pang, factor_mode=args.factor_mode, **kw))
+        tb = time.perf_counter() - t0
+        info = pl.info()
+        t = float(np.mean(timed(lambda: pl.apply(sig2, out=y2), kk, 2)))
+        pl.set_profiling(True)
+        pl.apply(sig2, out=y2)
+        st = pl.stage_times()
+        pl.set_profiling(False)
+        torch.cuda.synchronize()
+        out["gpu_launches"] += launches_of(st, 1, info["near_block_chunks"]) * (kk + 2 + 1)
+        assert pl.missed_lookups() == 0
+        ys[name] = y2.cpu().numpy().copy()
+        res[name] = {"ms_per_step": t, "value": s2.N / (t * 1e3), "D": info["D"], "plan_build_s": round(tb, 2),
+                     "relevant_cones": int(sum(info["nrc"])), "near_pairs": int(info["near_pairs"]),
+                     "near_block_chunks": int(info["near_block_chunks"])}
+        pl.close()
+    res["speedup_vs_uniform_auto"] = res["uniform_auto_depth"]["ms_per_step"] / res["adaptive_leaf64_D8"]["ms_per_step"]
+    res["speedup_vs_uniform_D7"] = res["uniform_D7"]["ms_per_step"] / res["adaptive_leaf64_D8"]["ms_per_step"]
+    if rank == 0:
+        import oracle
+
+        oracle.build()
+        rows = np.random.default_rng(12).choice(s2.N, min(args.rows, s2.N), replace=False)
+        yd = oracle.direct(s2.points, s2.normals, s2.weights, k2, k2, sig_np, cI=0.5, rows=rows)
+        for name, y in ys.items():
+            res[name]["rel_err_vs_direct"] = float(np.linalg.norm(y.reshape(1, -1)[:, rows] - yd) / np.linalg.norm(yd))
+        res["rows"] = int(len(rows))
+    return res
 
 
 def run_ours(args):
@@ -598,6 +657,7 @@ def run_ours(args):
                           f"orders ({Ps},{Pang},{Pang}), factor mode {args.factor_mode}; {t_cpu:.1f} s each",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
+        out["adaptive_octree"] = adaptive_leg(args, timed, dev, Ps, Pang, rank, out)
     # ---- the corrected operator: rectangular-polar correction built on the GPU, applied by K5 in
     # every apply (the operator GMRES uses in the sound-soft solve) ----
     from paper_2112_06316_gb300 import rp_correction
