@@ -2949,28 +2949,32 @@ __global__ void __launch_bounds__(128, 4) k_prop_tc(CommonArgs ca, LevelArgs C, 
 // child cone (kept in tensor memory as TF32 hi / lo), and the radial factor
 // Ls[node][a] applied when D is read back.
 // A block owns 128 parent nodes (TMEM lanes) in the plan's child-cone order and
-// one tile of up to 64 pairs.  Each step (child cone, factor, radial index a)
-// stages B (64 pairs x re/im = 128 columns, K = 64) in shared memory as
-// TF32 hi / lo and runs 8 k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of
-// tcgen05.mma 128 x 128 x 8 (A from tensor memory, B from shared memory) into
-// one of three 128-column TMEM buffers.  TMEM columns: D0 0-127, D1 128-255,
-// D2 256-383, A hi 384-447, A lo 448-511.
-// Warp-specialised: warps 0-7 stage operands and read D back (two threads per
-// node, one per half of the pairs), warp 8 only issues MMAs.  mbarriers hand the
-// work over: full (per B stage: B staged), done and empty (per D buffer: MMAs
-// complete via tcgen05.commit; D read back).  With three D buffers the workers
-// stage step s + 2 as soon as the MMAs of step s are done and before reading
-// D(s) back, so the MMAs of s + 2 wait for the staging only.  Every wait is bounded; a timeout
-// sets a block flag that ends the remaining waits early and is reported in the
-// missed counter (high word).
+// one half of a tile (up to 32 of its 64 pairs; two blocks per tile), so that two
+// blocks share an SM and each one's start-up, node geometry and epilogue overlap
+// the other's MMAs.  Each step (child cone, factor, radial index a) stages B (32
+// pairs x re/im = 64 columns, K = 64) in shared memory as TF32 hi / lo and runs 8
+// k-slices x 3 split terms (hi*hi + hi*lo + lo*hi) of tcgen05.mma 128 x 64 x 8 (A
+// from tensor memory, B from shared memory) into one of two 64-column TMEM
+// buffers.  TMEM columns (256 per block): D0 0-63, D1 64-127, A hi 128-191,
+// A lo 192-255.
+// Warp-specialised: warps 0-3 stage operands and read D back (one thread per
+// node), warp 4 only issues MMAs.  mbarriers hand the work over: full (per B
+// stage: B staged), done and empty (per D buffer: MMAs complete via
+// tcgen05.commit; D read back).  The workers stage step s + 2 as soon as the MMAs
+// of step s are done (its B stage is then free) and before reading D(s) back, so
+// the MMAs of s + 1 run during both.  Every wait is bounded; a timeout sets a
+// block flag that ends the remaining waits early and is reported in the missed
+// counter (high word).
 // ============================================================================
 constexpr int kT5Rows = 128;     // parent nodes per block (TMEM lanes)
-constexpr int kT5Cols = 128;     // TMEM columns of one step's D (three buffers)
-constexpr int kT5Work = 256;     // staging / readback threads (warps 0-7)
+constexpr int kT5Pairs = 32;     // pairs per block (half a tile)
+constexpr int kT5Cols = 2 * kT5Pairs;  // TMEM columns of one step's D (two buffers); the MMA's N
+constexpr int kT5Work = 128;     // staging / readback threads (warps 0-3)
 constexpr int kT5Threads = kT5Work + 32;  // + the MMA-issuing warp
 constexpr int kT5K = 64;         // contraction length (b, c)
-constexpr int kT5TileBytes = kT5Rows * kT5K * 4;  // one 128 x 64 TF32 operand tile (B of one step)
-constexpr uint32_t kT5ColA = 384;  // TMEM column of A hi (A lo at + 64)
+constexpr int kT5TileBytes = kT5Cols * kT5K * 4;  // one 64 x 64 TF32 operand tile (B of one step)
+constexpr uint32_t kT5ColA = 2 * kT5Cols;  // TMEM column of A hi (A lo at + 64)
+constexpr uint32_t kT5TmemCols = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -2980,6 +2984,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 // (SBO), so that the rows an MMA reads together fall in distinct banks
 __device__ __forceinline__ int t5_off(int r, int k) {
     return (k >> 3) * 4096 + (r >> 3) * 256 + ((k >> 2) & 1) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+// the same layout for the 64-row B tile of k_prop_t5 (k-slices of 2 KB)
+__device__ __forceinline__ int t5h_off(int r, int k) {
+    return (k >> 3) * 2048 + (r >> 3) * 256 + ((k >> 2) & 1) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ uint64_t t5_desc(uint32_t addr) {
@@ -3047,51 +3056,56 @@ __device__ __forceinline__ uint32_t tmem_row_base(uint32_t tmem, int quadrant) {
 
 struct T5Misc {
     short perm[kT5Rows];
-    int crc[1][kTcTile];
-    int rcp[kTcTile];
-    unsigned long long full[2], done[3], empty[3];
+    int crc[kT5Pairs];
+    int rcp[kT5Pairs];
+    unsigned long long full[2], done[2], empty[2];
     uint32_t tmem;
     int abort_;
 };
 
-// dynamic shared memory: B[stage][hi / lo], misc
-constexpr size_t kT5Smem = 4 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
+// dynamic shared memory: B[stage][hi / lo], misc; padded so that at most two blocks fit on an SM
+// (their 2 x 256 TMEM columns are then always free for tcgen05.alloc)
+constexpr size_t kT5SmemUsed = 4 * (size_t)kT5TileBytes + sizeof(T5Misc) + 1024;
+constexpr size_t kT5Smem = 80 * 1024;
+static_assert(kT5SmemUsed <= kT5Smem, "k_prop_t5 shared memory");
 
 template <int PS>
-__global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
+__global__ void __launch_bounds__(kT5Threads, 2) k_prop_t5(CommonArgs ca, LevelArgs C, LevelArgs Pl, ChebTab tb,
                                                            TcLevel T, int item0) {
-    constexpr int P = PS * 64, NT5 = kTcTile, NH = kTcTile / 2;
+    constexpr int P = PS * 64, NH = kT5Pairs;
     extern __shared__ unsigned char t5_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)t5_dyn + 1023) & ~(uintptr_t)1023);
     unsigned char *sB = base;  // buffer b: sB + (2 * b + hl) * kT5TileBytes
     T5Misc &sm = *reinterpret_cast<T5Misc *>(base + 4 * kT5TileBytes);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool worker = warp < 8;
-    const int qd = warp & 3, hf = (warp >> 2) & 1;  // TMEM lane quadrant, half of the pairs
+    const bool worker = warp < 4;
+    const int qd = warp & 3;  // TMEM lane quadrant
     const int row = 32 * qd + lane;
-    // item header (filled once per plan): nodes, group, child cone, pairs, child-centre offset
-    const long long it = item0 + blockIdx.x;
+    // item header (filled once per plan): nodes, group, child cone, pairs, child-centre offset; this
+    // block takes the pairs [32 half, 32 half + 32) of the item's tile
+    const long long it = item0 + (blockIdx.x >> 1);
+    const int half = blockIdx.x & 1;
     const int4 h0 = T.item_hdr[3 * it], h1 = T.item_hdr[3 * it + 1], h2 = T.item_hdr[3 * it + 2];
     const int row0 = h0.x, nrows = h0.y, grp = h0.z, gamma = h0.w;
-    const int ccone = h1.x, p0 = h1.y, np = h1.z;
+    const int ccone = h1.x, p0 = h1.y + kT5Pairs * half, np = h1.z - kT5Pairs * half;
+    if (np <= 0) return;  // block-uniform: the tile has no second half
     const float o0 = __int_as_float(h2.x), o1 = __int_as_float(h2.y), o2 = __int_as_float(h2.z);
-    if (tid < NT5) {
+    if (tid < kT5Pairs) {
         sm.rcp[tid] = tid < np ? T.pair_rcp[p0 + tid] : -1;
-        sm.crc[0][tid] = T.item_crc[kTcTile * it + tid];
+        sm.crc[tid] = T.item_crc[kTcTile * it + kT5Pairs * half + tid];
     }
     if (tid == 0) {
         sm.abort_ = 0;
-        for (int b = 0; b < 2; b++)
+        for (int b = 0; b < 2; b++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.full[b])), "r"(kT5Work));
-        for (int b = 0; b < 3; b++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&sm.empty[b])), "r"(kT5Work));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&sm.done[b])));
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&sm.tmem)),
-                     "r"(512));
+                     "r"(kT5TmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     // the item's nodes (one child cone) in the plan's node order (k_tc_order)
@@ -3105,11 +3119,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     // staging item: pair = 8 warp + (lane & 7), nodes [16 qn, 16 qn + 16) of the step's radial index with
     // qn = lane >> 3.  16-byte shared stores are serviced 8 lanes at a time: lanes 0-3 and 4-7 of each
     // group of 8 store the re / im rows in opposite order, so the 8 lanes cover all 8 bank groups
-    const int s_pair = 8 * (warp & 7) + (lane & 7), s_qn = lane >> 3;
+    const int s_pair = 8 * (warp & 3) + (lane & 7), s_qn = lane >> 3;
     // child values of step st (factor cf_lo + st / PS, radial index st % PS) of right-hand side q
     auto fetch_to = [&](int q, int cf_lo, int st, float4 *dst) {
         const int a = st % PS, cf = cf_lo + st / PS;
-        const int crc = sm.crc[0][s_pair];
+        const int crc = sm.crc[s_pair];
 #pragma unroll
         for (int e = 0; e < 8; e++) dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (crc >= 0) {
@@ -3122,7 +3136,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     // the first pipeline's first step is in flight while the node geometry is computed
     float4 pre[8];
     if (worker) fetch_to(0, 0, 0, pre);  // right-hand side 0, pass 0 (factor 0), step 0
-    // this thread's node (both threads of the node compute it): geometry, cone slot, Lagrange factors
+    // this thread's node: geometry, cone slot, Lagrange factors
     const int node = worker ? sm.perm[row] : -1;
     int slot = -1;
     float Ls[PS], rr = 0.f, ri = 0.f, g1 = 0.f, irs = 0.f;
@@ -3136,7 +3150,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             float nv[3], rp, rcv, t3[3];
             const int cone = tc_child_cone<PS>(C, Pl, tb, gamma, node, o0, o1, o2, nv, rp, rcv, t3);
             if (cone == ccone) slot = 0;
-            else if (hf == 0) atomicAdd(ca.missed, 1ULL);  // the plan's order puts every node in its cone
+            else if (half == 0) atomicAdd(ca.missed, 1ULL);  // the plan's order puts every node in its cone
             const float oo = o0 * o0 + o1 * o1 + o2 * o2, no = nv[0] * o0 + nv[1] * o1 + nv[2] * o2;
             float t = ca.kappa_hi * ((oo - 2.f * no) / (rcv + rp));
             t -= rintf(t);
@@ -3150,25 +3164,21 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             lagrange<8, float>(t3[1], tb.fxa, tb.fca, Lt);
             lagrange<8, float>(t3[2], tb.fxa, tb.fca, Lp);
         }
-        // A[row][(b, c)] = Lt[b] Lp[c] into TMEM lane `row`: this thread writes b in [4 hf, 4 hf + 4)
-        uint32_t ah[32], al[32];
-        auto fill_a = [&](int b, float lt) {
-#pragma unroll
-            for (int c = 0; c < 8; c++) split_tf32(lt * Lp[c], ah[8 * (b & 3) + c], al[8 * (b & 3) + c]);
-        };
-        if (hf == 0) {
-#pragma unroll
-            for (int bb = 0; bb < 4; bb++) fill_a(bb, Lt[bb]);
-        } else {
-#pragma unroll
-            for (int bb = 4; bb < 8; bb++) fill_a(bb, Lt[bb]);
-        }
+        // A[row][(b, c)] = Lt[b] Lp[c] into TMEM lane `row`, b in [0, 4) then [4, 8)
         const uint32_t lane_base = tmem_row_base(sm.tmem, qd);
-        t5_st32(lane_base + kT5ColA + 32u * hf, ah);
-        t5_st32(lane_base + kT5ColA + 64u + 32u * hf, al);
+#pragma unroll
+        for (int hb = 0; hb < 2; hb++) {
+            uint32_t ah[32], al[32];
+#pragma unroll
+            for (int bb = 0; bb < 4; bb++)
+#pragma unroll
+                for (int c = 0; c < 8; c++) split_tf32(Lt[4 * hb + bb] * Lp[c], ah[8 * bb + c], al[8 * bb + c]);
+            t5_st32(lane_base + kT5ColA + 32u * hb, ah);
+            t5_st32(lane_base + kT5ColA + 64u + 32u * hb, al);
+        }
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     }
-    if (tid < NT5 && tid < np && sm.crc[0][tid] < 0) atomicAdd(ca.missed, 1ULL);
+    if (tid < kT5Pairs && tid < np && sm.crc[tid] < 0) atomicAdd(ca.missed, 1ULL);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");  // A in TMEM, for the MMAs
     __syncthreads();
     const int npass = (csplit && psplit) ? 2 : 1;
@@ -3177,9 +3187,9 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     const int first_ri = (lane >> 2) & 1;
     const uint32_t idesc_base = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kT5Rows >> 4) << 24);
     const uint32_t aH = tmem + kT5ColA, aL = tmem + kT5ColA + 64u;
-    const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16) + 64u * hf;  // pairs 32 hf .. 32 hf + 31
-    // global step index G: B stage G & 1 (use G >> 1), D buffer G % 3 (use G / 3); a barrier's phase
-    // parity is its use count & 1
+    const uint32_t my_taddr = tmem + ((uint32_t)(32 * qd) << 16);  // this node's row, the block's 32 pairs
+    // global step index G: B stage and D buffer G & 1 (use G >> 1); a barrier's phase parity is its
+    // use count & 1
     int G = 0;
     for (int q = 0; q < ca.nrhs; q++) {
         for (int pass = 0; pass < npass; pass++) {
@@ -3210,8 +3220,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                             split_tf32(im ? u1.y : u1.x, h.z, l.z);
                             split_tf32(im ? u1.w : u1.z, h.w, l.w);
                             const int k = 16 * s_qn + 4 * kq;
-                            *reinterpret_cast<uint4 *>(bh + t5_off(n, k)) = h;
-                            *reinterpret_cast<uint4 *>(bl + t5_off(n, k)) = l;
+                            *reinterpret_cast<uint4 *>(bh + t5h_off(n, k)) = h;
+                            *reinterpret_cast<uint4 *>(bl + t5h_off(n, k)) = l;
                         }
                     }
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -3230,15 +3240,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 }
                 if (nsteps > 2) fetch(2);
                 for (int st = 0; st < nsteps; st++) {
-                    const int gs = G + st, dsel = gs % 3;
+                    const int gs = G + st, dsel = gs & 1;
                     const int a = st % PS, cf = cf_lo + st / PS;
-                    const bool ok = t5_wait(smem_u32(&sm.done[dsel]), (gs / 3) & 1, abort_flag);
+                    const bool ok = t5_wait(smem_u32(&sm.done[dsel]), (gs >> 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     if (st + 2 < nsteps) {  // B stage gs & 1 was consumed by the MMAs just waited for
                         stage(gs + 2);
                         if (st + 3 < nsteps) fetch(st + 3);
                     }
-                    // D row of this node, this thread's pairs 32 hf .. 32 hf + 31: columns 64 hf + 2 i + re/im
+                    // D row of this node: columns 2 i + re/im for the block's pairs i
                     const float sc = (csplit && !psplit && cf == 0) ? irs : 1.f;
                     const float w = (slot == 0 && ok) ? sc * pick<PS>(Ls, a) : 0.f;
                     const uint32_t dcol = my_taddr + (uint32_t)(dsel * kT5Cols);
@@ -3259,24 +3269,24 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
             } else if (lane == 0) {
                 // MMA issuer
                 for (int st = 0; st < nsteps; st++) {
-                    const int gs = G + st, bsel = gs & 1, dsel = gs % 3;
-                    t5_wait(smem_u32(&sm.full[bsel]), (gs >> 1) & 1, abort_flag);
-                    if (gs >= 3) t5_wait(smem_u32(&sm.empty[dsel]), (gs / 3 - 1) & 1, abort_flag);
+                    const int gs = G + st, sel = gs & 1;
+                    t5_wait(smem_u32(&sm.full[sel]), (gs >> 1) & 1, abort_flag);
+                    if (gs >= 2) t5_wait(smem_u32(&sm.empty[sel]), ((gs >> 1) - 1) & 1, abort_flag);
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t idesc = idesc_base | ((uint32_t)(kT5Cols >> 3) << 17);
-                    const uint32_t d = tmem + (uint32_t)(dsel * kT5Cols);
-                    const uint32_t bH = smem_u32(sB + (2 * bsel) * kT5TileBytes), bL = bH + kT5TileBytes;
+                    const uint32_t d = tmem + (uint32_t)(sel * kT5Cols);
+                    const uint32_t bH = smem_u32(sB + (2 * sel) * kT5TileBytes), bL = bH + kT5TileBytes;
                     if (!*abort_flag) {
 #pragma unroll 1
                         for (int kk = 0; kk < 8; kk++) {
-                            const uint32_t ko = 4096u * kk, ka = 8u * kk;
+                            const uint32_t ko = 2048u * kk, ka = 8u * kk;
                             t5_mma(d, aH + ka, t5_desc(bH + ko), idesc, kk > 0 ? 1u : 0u);
                             t5_mma(d, aH + ka, t5_desc(bL + ko), idesc, 1u);
                             t5_mma(d, aL + ka, t5_desc(bH + ko), idesc, 1u);
                         }
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                                smem_u32(&sm.done[dsel]))
+                                smem_u32(&sm.done[sel]))
                             : "memory");
                     }
                 }
@@ -3295,7 +3305,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
                 // parent value has one writer in this launch: reduction stores (no read round trip)
 #pragma unroll
                 for (int i = 0; i < NH; i++) {
-                    const int rcp = sm.rcp[NH * hf + i];
+                    const int rcp = sm.rcp[i];
                     if (rcp < 0) continue;
                     const long long o = (((long long)q * Pl.nrc + rcp) * Pl.nfac + fp) * ca.Pstride + node;
                     atomicAdd(FP + o, make_float2(prr * E[i][0] - pri * E[i][1], prr * E[i][1] + pri * E[i][0]));
@@ -3306,9 +3316,9 @@ __global__ void __launch_bounds__(kT5Threads, 1) k_prop_t5(CommonArgs ca, LevelA
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (tid == 0 && sm.abort_) atomicAdd(ca.missed, 1ULL << 32);
-    if (warp == 8) {
+    if (warp == 4) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kT5TmemCols));
     }
 }
 
@@ -4212,7 +4222,7 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                         if (p.tc_engine == 1) {
                             const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
                             if (ni > 0)
-                                k_prop_t5<PS><<<ni, kT5Threads, kT5Smem, s>>>(ca, L[d], L[d - 1], tb, T, i0);
+                                k_prop_t5<PS><<<2 * ni, kT5Threads, kT5Smem, s>>>(ca, L[d], L[d - 1], tb, T, i0);
                         } else if (p.tc_engine == 2) {
                             const int i0 = T.oct_item_start[o], ni = T.oct_item_start[o + 1] - i0;
                             // persistent: as many blocks per SM as their tensor memory allows
