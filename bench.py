@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--rows", type=int, default=2000, help="direct-sum rows for the error check")
     ap.add_argument("--quick", action="store_true", help="skip the CPU legs and the FP64 timing")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-scatterer graph apply")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="with --quick: run the adaptive-octree leg too (without its direct-sum error rows)")
     ap.add_argument("--batch-orders", default="5x8", help="Ps x Pang of the 24-scatterer graph apply")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default kernel choices instead of autotuning them on this workload")
@@ -327,7 +329,7 @@ def adaptive_leg(args, timed, dev, Ps, Pang, rank, out):
         pl.close()
     res["speedup_vs_uniform_auto"] = res["uniform_auto_depth"]["ms_per_step"] / res["adaptive_leaf64_D8"]["ms_per_step"]
     res["speedup_vs_uniform_D7"] = res["uniform_D7"]["ms_per_step"] / res["adaptive_leaf64_D8"]["ms_per_step"]
-    if rank == 0:
+    if rank == 0 and not args.quick:
         import oracle
 
         oracle.build()
@@ -657,6 +659,7 @@ def run_ours(args):
                           f"orders ({Ps},{Pang},{Pang}), factor mode {args.factor_mode}; {t_cpu:.1f} s each",
                 "direct_sum_rows_per_s": len(rows) / t_direct}
         plan35.close()
+    if not args.quick or args.adaptive:
         out["adaptive_octree"] = adaptive_leg(args, timed, dev, Ps, Pang, rank, out)
     # ---- the corrected operator: rectangular-polar correction built on the GPU, applied by K5 in
     # every apply (the operator GMRES uses in the sound-soft solve) ----
