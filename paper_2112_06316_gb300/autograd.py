@@ -29,7 +29,7 @@ class IFGFApply(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_y: torch.Tensor):
         k, state = ctx.saved_tensors
-        gs, dk = ctx.plan.vjp_from_state(state, grad_y.contiguous())
+        gs, dk = ctx.plan.vjp_from_state(state, grad_y.contiguous(), with_dk=ctx.needs_input_grad[1])
         gk = torch.tensor(dk, dtype=k.dtype, device=k.device) if ctx.needs_input_grad[1] else None
         return gs if ctx.needs_input_grad[0] else None, gk, None
 

@@ -311,8 +311,9 @@ class Plan:
                                        ctypes.c_int(prec), _VP(_stream_ptr(stream))))
         return y.reshape(-1) if squeeze else y
 
-    def vjp(self, sigma, g, stream=None):
-        """(A^H g, Re <g, dA/dk sigma>) for CUDA tensors sigma, g of shape (nrhs, N) or (N,)."""
+    def vjp(self, sigma, g, stream=None, with_dk: bool = True):
+        """(A^H g, Re <g, dA/dk sigma>) for CUDA tensors sigma, g of shape (nrhs, N) or (N,); with
+        with_dk False the k-derivative is skipped (0.0 is returned in its place)."""
         import torch
 
         if sigma.dtype != g.dtype or sigma.shape != g.shape:
@@ -326,8 +327,8 @@ class Plan:
         out = torch.empty_like(s_)
         dk = ctypes.c_double(0.0)
         check(lib().ifgf_apply_vjp(self._h, _VP(s_.data_ptr()), _VP(g_.data_ptr()), _VP(out.data_ptr()),
-                                   ctypes.c_int(s_.shape[0]), ctypes.byref(dk), ctypes.c_int(prec),
-                                   _VP(_stream_ptr(stream))))
+                                   ctypes.c_int(s_.shape[0]), ctypes.byref(dk) if with_dk else None,
+                                   ctypes.c_int(prec), _VP(_stream_ptr(stream))))
         return (out.reshape(-1) if squeeze else out), float(dk.value)
 
     def workspace_bytes(self, nrhs: int, prec: int) -> int:
@@ -357,8 +358,9 @@ class Plan:
                                   ctypes.c_int(prec), _VP(ws.data_ptr()), ctypes.c_int64(nb), _VP(_stream_ptr(stream))))
         return (y.reshape(-1) if squeeze else y), ws
 
-    def vjp_from_state(self, state, g, stream=None):
-        """(A^H g, Re <g, dA/dk sigma>) from the forward state of apply_with_state(sigma)."""
+    def vjp_from_state(self, state, g, stream=None, with_dk: bool = True):
+        """(A^H g, Re <g, dA/dk sigma>) from the forward state of apply_with_state(sigma); with
+        with_dk False the k-derivative is skipped (0.0 is returned in its place)."""
         import torch
 
         prec = FP64 if g.dtype == torch.complex128 else MIXED if g.dtype == torch.complex64 else None
@@ -370,7 +372,8 @@ class Plan:
         dk = ctypes.c_double(0.0)
         check(lib().ifgf_apply_vjp_ws(self._h, _VP(state.data_ptr()), ctypes.c_int64(state.numel()),
                                       _VP(g_.data_ptr()), _VP(out.data_ptr()), ctypes.c_int(g_.shape[0]),
-                                      ctypes.byref(dk), ctypes.c_int(prec), _VP(_stream_ptr(stream))))
+                                      ctypes.byref(dk) if with_dk else None, ctypes.c_int(prec),
+                                      _VP(_stream_ptr(stream))))
         return (out.reshape(-1) if squeeze else out), float(dk.value)
 
     def apply_noalloc_ptr(self, sigma_ptr: int, y_ptr: int, nrhs: int, prec: int, stream=None):

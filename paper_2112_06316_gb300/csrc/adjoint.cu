@@ -42,11 +42,11 @@ ifgf_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
 }
 
-// The adjoint, the vector-Jacobian product and the k-gradient follow the uniform tree's level
-// structure (leaf anterpolation at level D only): adaptive plans are refused.
-ifgf_status check_uniform(const Plan &p) {
-    if (!p.adaptive) return IFGF_OK;
-    set_error("the adjoint and the k-gradient are not built for adaptive plans (leaf_max > 0)");
+// The k-gradient's leaf and near-field reductions follow the uniform tree (leaves at level D, near
+// lists of level-D boxes): it is refused for adaptive plans, whose adjoint is built.
+ifgf_status check_dk(const Plan &p, bool dk) {
+    if (!dk || !p.adaptive) return IFGF_OK;
+    set_error("the k-gradient is not built for adaptive plans (leaf_max > 0); pass no dk output");
     return IFGF_EUNSUPPORTED;
 }
 
@@ -94,7 +94,7 @@ ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
 // and level in order, to dk_partials.
 ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, int prec, cudaStream_t s, void **gs_out,
                          void **G, void *const *Fd = nullptr, double *dk_partials = nullptr) {
-    ifgf_status st = check_uniform(p);
+    ifgf_status st = check_dk(p, Fd != nullptr);
     if (st != IFGF_OK) return st;
     st = ensure_adjoint_lists(p, s);
     if (st != IFGF_OK) return st;
@@ -276,7 +276,7 @@ extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, co
     if (dk_host) *dk_host = 0.0;
     if (nrhs == 0) return IFGF_OK;
     Plan &p = plan->p;
-    st = check_uniform(p);
+    st = check_dk(p, dk_host != nullptr);
     if (st != IFGF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // forward state (a = w sigma, cone values F) in the plan workspace; gsigma is scratch here

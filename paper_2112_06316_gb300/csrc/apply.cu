@@ -274,6 +274,7 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
             for (int si = L.start[b]; si < L.start[b + 1]; si++) box_of[si] = b;
         UP(p.d_box_of[d], box_of);
         UP(p.d_alive[d], L.alive);
+        UP(p.d_leaf[d], L.leaf);
         p.nleaf_rc[d] = (int)L.leaf_rc.size();
         if (!L.leaf_rc.empty()) UP(p.d_leaf_rc[d], L.leaf_rc);
         std::vector<int4> ch;

@@ -2089,9 +2089,12 @@ __global__ void __launch_bounds__(128, MX ? (FUSE ? 4 : 6) : 4) k_ant(CommonArgs
 }
 
 // Transposed leaf evaluation: b_j += sum over the cone nodes of j's leaf box of
-// conj(W(x_n, y_j)) G_D (transpose of K1).
+// conj(W(x_n, y_j)) G (transpose of K1).  box_of == nullptr: the leaves of level D (L = LD); else the
+// level of L, for the points whose level-L box is a leaf (leaf flags), as in an adaptive tree.
 template <int PS, int PA, bool MX>
-__global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, ChebTab tb, const void *G_, void *b_) {
+__global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, ChebTab tb, const void *G_, void *b_,
+                                                  const int *__restrict__ box_of, const uint8_t *__restrict__ leaf,
+                                                  LevelArgs LD) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
     constexpr int P = PS * PA * PA;
@@ -2099,8 +2102,18 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
     C *bo = (C *)b_;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ca.N) return;
-    const int b = ca.leaf_of[j];
+    const int b = box_of ? box_of[j] : ca.leaf_of[j];
+    if (leaf && !leaf[b]) return;
     const bool split = L.split != 0;
+    // mixed: the source's offset from the box centre in leaf units (its level-D box offset plus the exact
+    // difference of the two centres; zero at level D)
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+    if constexpr (MX) {
+        const int e = ca.leaf_of[j];
+        f0 = ca.f32[3 * j] + ((LD.ijk[3 * e] + 0.5f) - (L.ijk[3 * b] + 0.5f) * L.scale);
+        f1 = ca.f32[3 * j + 1] + ((LD.ijk[3 * e + 1] + 0.5f) - (L.ijk[3 * b + 1] + 0.5f) * L.scale);
+        f2 = ca.f32[3 * j + 2] + ((LD.ijk[3 * e + 2] + 0.5f) - (L.ijk[3 * b + 2] + 0.5f) * L.scale);
+    }
     for (int q = 0; q < ca.nrhs; q++) {
         T ar = T(0), ai = T(0);
         for (int rc = L.rc_start[b]; rc < L.rc_start[b + 1]; rc++) {
@@ -2112,7 +2125,6 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
                     float s, u[3];
                     node32<PS, PA>(L, tb, cone, n, s, u);
                     const float hu = L.hu, ir = s / hu, kap = ca.kappa_hi, soh = s / (hu * ca.HDf);
-                    const float f0 = ca.f32[3 * j], f1 = ca.f32[3 * j + 1], f2 = ca.f32[3 * j + 2];
                     const float dv0 = u[0] - f0 * ir, dv1 = u[1] - f1 * ir, dv2 = u[2] - f2 * ir;
                     const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
                     const float ia = rsqrtf(a2), am = a2 * ia;
@@ -4330,9 +4342,15 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
         k_near_adj<false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], gs, bws);
         prof_mark(p, s, kStNear, D);
         if (L[D].nrc) {
-            k_leaf_adj<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], tb, G[D], bws);
+            k_leaf_adj<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[D], tb, G[D], bws, nullptr, nullptr, L[D]);
             prof_mark(p, s, kStLeaf, D);
         }
+        for (int d = 3; d < D; d++)  // adaptive tree: the leaves of the coarser levels
+            if (p.nleaf_rc[d]) {
+                k_leaf_adj<PS, PA, false><<<nblk(N), kBlock, 0, s>>>(ca, L[d], tb, G[d], bws, p.d_box_of[d],
+                                                                     p.d_leaf[d], L[D]);
+                prof_mark(p, s, kStLeaf, d);
+            }
         k_scatter_adj<double><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w64,
                                                            (const double2 *)g, (const double2 *)bws, (double2 *)out);
         prof_mark(p, s, kStScatter, 0);
@@ -4378,6 +4396,12 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
             }
             prof_mark(p, s, kStLeaf, D);
         }
+        for (int d = 3; d < D; d++)  // adaptive tree (no k-derivative): the leaves of the coarser levels
+            if (p.nleaf_rc[d]) {
+                k_leaf_adj<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], tb, G[d], bws, p.d_box_of[d],
+                                                                    p.d_leaf[d], L[D]);
+                prof_mark(p, s, kStLeaf, d);
+            }
         k_scatter_adj<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w32,
                                                           (const float2 *)g, (const float2 *)bws, (float2 *)out);
         prof_mark(p, s, kStScatter, 0);

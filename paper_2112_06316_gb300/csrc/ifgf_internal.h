@@ -167,6 +167,7 @@ struct Plan {
     float4 *d_cs_geo4[IFGF_MAXD + 1] = {};
     int *d_cs_first[IFGF_MAXD + 1] = {};  // per relevant cone: its first entry (the adjoint reuses the geometry)
     uint8_t *d_alive[IFGF_MAXD + 1] = {};  // per box: it exists (adaptive octree; all 1 otherwise)
+    uint8_t *d_leaf[IFGF_MAXD + 1] = {};   // per box: it is a leaf (level D: every existing box)
     int *d_leaf_rc[IFGF_MAXD + 1] = {};    // relevant cones of the level's source leaves (levels < D)
     int nleaf_rc[IFGF_MAXD + 1] = {};
     float2 *d_cs_geo2[IFGF_MAXD + 1] = {};

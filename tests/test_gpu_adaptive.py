@@ -11,7 +11,8 @@ the orders (3, 5) and (5, 8), the split and combined factors, the tcgen05 propag
 cousin engines and one and two right-hand sides; against the direct sum on sampled rows; a leaf budget
 above every box's count reproduces the uniform three-level plan; far field from the level-3
 interpolants and potential at targets on adaptive plans; chunks of leaves with long near-source
-lists run as one block each; the adjoint is refused.
+lists run as one block each; the adjoint (against the forward by the inner-product identity) and
+the density gradient through autograd; the k-gradient is refused.
 """
 import numpy as np
 import pytest
@@ -178,12 +179,54 @@ def test_adaptive_far_field_and_targets(B, oracle_lib, geo):
     pt.close()
 
 
-def test_adaptive_adjoint_refused(B, geo):
+ADJ_CASES = {
+    "leaf64_3x5": (dict(levels=6, leaf_max=64), None),
+    "leaf64_5x8_tc": (dict(levels=6, leaf_max=64, Ps=5, Pang=8), 0.0),
+    "leaf16_D7_split": (dict(levels=7, leaf_max=16, factor_mode=2), None),
+}
+
+
+@pytest.mark.parametrize("case", list(ADJ_CASES))
+def test_adaptive_adjoint(B, geo, case):
+    """The adjoint of an adaptive plan (anterpolation at every level, the transposed leaf evaluation
+    at every level's leaves, the transposed near field on the adaptive near lists): the FP64 adjoint
+    satisfies <A s, g> = <s, A^H g> to rounding (A is parity-checked against the oracle above), the
+    mixed adjoint matches it to 1e-5, the vector-Jacobian product without the k-derivative equals the
+    adjoint, and the k-derivative is refused."""
+    kw, fill = ADJ_CASES[case]
+    s = geo
+    plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=K, **kw))
+    if fill is not None:
+        plan.set_tc_fill(fill)
+    sig = random_density(s.N, 2, 78)
+    g = random_density(s.N, 2, 79)
+    As = apply(plan, sig, np.complex128)
+    Ahg = plan.adjoint(cu(g)).cpu().numpy()
+    lhs, rhs = np.vdot(g, As), np.vdot(Ahg, sig)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs), (lhs, rhs)
+    Ahg32 = plan.adjoint(cu(g, np.complex64)).cpu().numpy()
+    check(Ahg32, Ahg, 1e-5, "mixed adjoint")
+    gs, dk = plan.vjp(cu(sig), cu(g), with_dk=False)
+    check(gs.cpu().numpy(), Ahg, 1e-13, "vjp without dk")
+    assert dk == 0.0
+    with pytest.raises(B.IFGFError, match="EUNSUPPORTED"):
+        plan.vjp(cu(sig), cu(g))
+    assert plan.missed_lookups() == 0
+    plan.close()
+
+
+def test_adaptive_autograd_density_gradient(B, geo):
+    """torch autograd through an adaptive plan: the gradient in the density (no k-gradient asked)
+    equals A^H of the output gradient."""
+    from paper_2112_06316_gb300 import ifgf_apply
+
     s = geo
     plan = B.Plan(s.points, s.normals, s.weights, B.Params(k=K, levels=6, leaf_max=64))
-    g = cu(random_density(s.N, 1, 76))
-    with pytest.raises(B.IFGFError, match="EUNSUPPORTED"):
-        plan.adjoint(g)
-    with pytest.raises(B.IFGFError, match="EUNSUPPORTED"):
-        plan.vjp(g, g.clone())
+    sig = cu(random_density(s.N, 1, 80)[0]).requires_grad_(True)
+    w = cu(random_density(s.N, 1, 81)[0])
+    k = torch.tensor(K, dtype=torch.float64)
+    y = ifgf_apply(sig, k, plan)
+    (y * w.conj()).real.sum().backward()
+    ref = plan.adjoint(w).cpu().numpy()
+    check(sig.grad.cpu().numpy(), ref, 1e-12, "density gradient")
     plan.close()
