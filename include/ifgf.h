@@ -105,9 +105,8 @@ typedef struct {
                              and no boxes exist below it), `levels` is the maximum depth.  Points of
                              two leaves interact directly when their boxes neighbour at the coarser
                              of the two leaf levels; every other pair goes through one cousin
-                             interpolation.  The adjoint is built for adaptive plans (the
-                             transposed leaf evaluation at every level's leaves); the k-gradient
-                             is not (IFGF_EUNSUPPORTED when requested). */
+                             interpolation.  The adjoint and the k-gradient cover adaptive
+                             plans (the transposed leaf evaluation at every level's leaves). */
 } ifgf_params;
 
 /* Values of ifgf_params.layer. */
@@ -206,9 +205,7 @@ ifgf_status ifgf_apply_adjoint(ifgf_plan *plan, const void *g_dev, void *out_dev
  * stages is reduced inside the adjoint's anterpolation, that of the leaf
  * evaluation and the near field by two more passes.  Synchronises `stream` when
  * dk is requested.
- * Errors as ifgf_apply; sigma, g and gsigma must be distinct; IFGF_EUNSUPPORTED for a
- * dk request on an adaptive plan (params.leaf_max > 0), whose adjoint is built but not
- * its k-derivative. */
+ * Errors as ifgf_apply; sigma, g and gsigma must be distinct. */
 ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, const void *g_dev, void *gsigma_dev, int nrhs,
                            double *dk_host, ifgf_precision prec, void *stream);
 

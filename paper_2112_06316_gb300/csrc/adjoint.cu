@@ -42,14 +42,6 @@ ifgf_status cuda_fail(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? IFGF_ENOMEM : IFGF_ECUDA;
 }
 
-// The k-gradient's leaf and near-field reductions follow the uniform tree (leaves at level D, near
-// lists of level-D boxes): it is refused for adaptive plans, whose adjoint is built.
-ifgf_status check_dk(const Plan &p, bool dk) {
-    if (!dk || !p.adaptive) return IFGF_OK;
-    set_error("the k-gradient is not built for adaptive plans (leaf_max > 0); pass no dk output");
-    return IFGF_EUNSUPPORTED;
-}
-
 // Anterpolation lists per level (host build, then upload); once per plan.
 ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
     if (p.adj_ready) return IFGF_OK;
@@ -94,9 +86,7 @@ ifgf_status ensure_adjoint_lists(Plan &p, cudaStream_t s) {
 // and level in order, to dk_partials.
 ifgf_status adjoint_core(Plan &p, const void *g_dev, void *out_dev, int nrhs, int prec, cudaStream_t s, void **gs_out,
                          void **G, void *const *Fd = nullptr, double *dk_partials = nullptr) {
-    ifgf_status st = check_dk(p, Fd != nullptr);
-    if (st != IFGF_OK) return st;
-    st = ensure_adjoint_lists(p, s);
+    ifgf_status st = ensure_adjoint_lists(p, s);
     if (st != IFGF_OK) return st;
     const size_t cb = prec == IFGF_FP64 ? 16 : 8;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -202,6 +192,8 @@ ifgf_status vjp_core(Plan &p, const Workspace &fwd, const void *g_dev, void *gsi
         // 128 sources / per four leaf chunks)
         need = (p.N + 127) / 128 + std::max<long long>((p.lv[p.D].nrc * p.P + 127) / 128, (p.ncchunk[p.D] + 3) / 4);
         for (int d = 3; d <= p.D; d++) need += p.lv[d].nrc;
+        for (int d = 3; d < p.D; d++)  // adaptive tree: the leaves of the coarser levels (per 128 sources / nodes)
+            if (p.nleaf_rc[d]) need += std::max<long long>((p.N + 127) / 128, ((long long)p.nleaf_rc[d] * p.P + 127) / 128);
         const size_t bytes = sizeof(double) * (need + 1);
         if (bytes > p.dk_ws_bytes) {
             if (p.dk_ws) cudaFree(p.dk_ws);
@@ -228,6 +220,8 @@ ifgf_status vjp_core(Plan &p, const Workspace &fwd, const void *g_dev, void *gsi
     if (prec == IFGF_MIXED) {  // near field and leaf reduced inside the adjoint kernels
         np += (p.N + 127) / 128;
         if (p.lv[p.D].nrc) np += (p.ncchunk[p.D] + 3) / 4;
+        for (int d = 3; d < p.D; d++)
+            if (p.nleaf_rc[d]) np += (p.N + 127) / 128;
     } else {
         long long nd = 0;
         p.ws = fwd;
@@ -276,8 +270,6 @@ extern "C" ifgf_status ifgf_apply_vjp(ifgf_plan *plan, const void *sigma_dev, co
     if (dk_host) *dk_host = 0.0;
     if (nrhs == 0) return IFGF_OK;
     Plan &p = plan->p;
-    st = check_dk(p, dk_host != nullptr);
-    if (st != IFGF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     // forward state (a = w sigma, cone values F) in the plan workspace; gsigma is scratch here
     st = run_apply(p, sigma_dev, gsigma_dev, nrhs, (int)prec, s);

@@ -2091,19 +2091,25 @@ __global__ void __launch_bounds__(128, MX ? (FUSE ? 4 : 6) : 4) k_ant(CommonArgs
 // Transposed leaf evaluation: b_j += sum over the cone nodes of j's leaf box of
 // conj(W(x_n, y_j)) G (transpose of K1).  box_of == nullptr: the leaves of level D (L = LD); else the
 // level of L, for the points whose level-L box is a leaf (leaf flags), as in an adaptive tree.
-template <int PS, int PA, bool MX>
+// With DK (mixed only) the same evaluations also give the leaf's part of Re <g, dA/dk sigma>
+// (conj(dW/dk) G against the forward w sigma, as in k_leaf_adj_w), one double per block in dk_partials.
+template <int PS, int PA, bool MX, bool DK = false>
 __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, ChebTab tb, const void *G_, void *b_,
                                                   const int *__restrict__ box_of, const uint8_t *__restrict__ leaf,
-                                                  LevelArgs LD) {
+                                                  LevelArgs LD, const float2 *__restrict__ a_fwd = nullptr,
+                                                  double *dk_partials = nullptr) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
+    static_assert(!DK || MX, "the FP64 k-derivative of the leaf has its own pass (k_dk_leaf)");
     constexpr int P = PS * PA * PA;
     const C *G = (const C *)G_;
     C *bo = (C *)b_;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ca.N) return;
-    const int b = box_of ? box_of[j] : ca.leaf_of[j];
-    if (leaf && !leaf[b]) return;
+    const int jt = blockIdx.x * blockDim.x + threadIdx.x;
+    double dk = 0.0;
+    const int b = jt < ca.N ? (box_of ? box_of[jt] : ca.leaf_of[jt]) : 0;
+    const bool act = jt < ca.N && !(leaf && !leaf[b]);
+    if (!DK && !act) return;
+    const int j = act ? jt : 0;
     const bool split = L.split != 0;
     // mixed: the source's offset from the box centre in leaf units (its level-D box offset plus the exact
     // difference of the two centres; zero at level D)
@@ -2114,13 +2120,15 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
         f1 = ca.f32[3 * j + 1] + ((LD.ijk[3 * e + 1] + 0.5f) - (L.ijk[3 * b + 1] + 0.5f) * L.scale);
         f2 = ca.f32[3 * j + 2] + ((LD.ijk[3 * e + 2] + 0.5f) - (L.ijk[3 * b + 2] + 0.5f) * L.scale);
     }
-    for (int q = 0; q < ca.nrhs; q++) {
+    for (int q = 0; q < ca.nrhs && act; q++) {
         T ar = T(0), ai = T(0);
+        float dr = 0.f, di = 0.f;  // DK: sum of conj(dW/dk) G
         for (int rc = L.rc_start[b]; rc < L.rc_start[b + 1]; rc++) {
             const int cone = L.rc_cone[rc];
             const long long gb = ((long long)q * L.nrc + rc) * L.nfac;
             for (int n = 0; n < P; n++) {
                 T W0r, W0i, W1r = T(0), W1i = T(0);
+                T D0r = T(0), D0i = T(0), D1r = T(0), D1i = T(0);  // DK: dW/dk
                 if constexpr (MX) {
                     float s, u[3];
                     node32<PS, PA>(L, tb, cone, n, s, u);
@@ -2129,18 +2137,27 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
                     const float a2 = dv0 * dv0 + dv1 * dv1 + dv2 * dv2;
                     const float ia = rsqrtf(a2), am = a2 * ia;
                     const float yy = f0 * f0 + f1 * f1 + f2 * f2, uy = u[0] * f0 + u[1] * f1 + u[2] * f2;
-                    float t = kap * (s * yy / hu - 2.f * uy) / (am + 1.f);
+                    const float phl = (s * yy / hu - 2.f * uy) / (am + 1.f);  // phase distance, leaf units
+                    float t = kap * phl;
                     t -= rintf(t);
                     float sn, cs;
                     cis_cycles(t, sn, cs);
                     const float dn = dv0 * ca.n32[3 * j] + dv1 * ca.n32[3 * j + 1] + dv2 * ca.n32[3 * j + 2];
                     const float w3 = dn * ia * ia, w2 = w3 * ia, g = ca.kf * w3 + ca.etaf * ia,
                                 hr = ca.etaif * ia;
+                    const float ph0 = phl * ca.HDf;  // absolute: dW/dk = i ph0 W - i e w3 (combined, W13), i ph0 W2
                     if (split) {
                         W0r = cs * w2; W0i = sn * w2; W1r = cs * hr + sn * g; W1i = sn * hr - cs * g;
+                        if constexpr (DK) {
+                            D0r = -ph0 * W0i; D0i = ph0 * W0r;
+                            D1r = -ph0 * W1i + sn * w3; D1i = ph0 * W1r - cs * w3;
+                        }
                     } else {
                         const float a = soh * w2 + hr;
                         W0r = cs * a + sn * g; W0i = sn * a - cs * g;
+                        if constexpr (DK) {
+                            D0r = -ph0 * W0i + sn * w3; D0i = ph0 * W0r - cs * w3;
+                        }
                     }
                 } else {
                     double s, u[3], y0[3];
@@ -2168,10 +2185,18 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
                 const C g0 = G[gb * ca.Pstride + n];
                 ar += W0r * g0.x + W0i * g0.y;  // conj(W) * G
                 ai += W0r * g0.y - W0i * g0.x;
+                if constexpr (DK) {
+                    dr += D0r * g0.x + D0i * g0.y;
+                    di += D0r * g0.y - D0i * g0.x;
+                }
                 if (split) {
                     const C g1 = G[(gb + 1) * ca.Pstride + n];
                     ar += W1r * g1.x + W1i * g1.y;
                     ai += W1r * g1.y - W1i * g1.x;
+                    if constexpr (DK) {
+                        dr += D1r * g1.x + D1i * g1.y;
+                        di += D1r * g1.y - D1i * g1.x;
+                    }
                 }
             }
         }
@@ -2179,7 +2204,12 @@ __global__ void __launch_bounds__(128) k_leaf_adj(CommonArgs ca, LevelArgs L, Ch
         v.x += ar;
         v.y += ai;
         bo[(long long)q * ca.N + j] = v;
+        if constexpr (DK) {  // Re(conj(T) a_j), T = sum conj(dW) G
+            const float2 aj = a_fwd[(long long)q * ca.N + j];
+            dk += (double)dr * aj.x + (double)di * aj.y;
+        }
     }
+    if constexpr (DK) block_sum_store(dk, dk_partials);
 }
 
 // Transposed leaf evaluation (mixed), warp-cooperative: one warp per chunk of at
@@ -2506,9 +2536,11 @@ __global__ void __launch_bounds__(128) k_dk_near(CommonArgs ca, LevelArgs L, con
 
 // leaf evaluation: sum_{rc,n} conj(G_D[n]) sum_j dW/dk(x_n, y_j) a_j,
 // dW/dk = i phi0 W - i e w3 (combined or W13),  i phi0 W2 (split W2)
+// (rc_list: the relevant cones of the leaves of a coarser level of an adaptive tree, nlist of them, FP64
+// only; nullptr: every relevant cone of the level)
 template <int PS, int PA, bool MX>
 __global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, ChebTab tb, const void *a_, const void *G_,
-                                                 double *partials) {
+                                                 double *partials, const int *__restrict__ rc_list, long long nlist) {
     typedef typename std::conditional<MX, float, double>::type T;
     typedef typename CT<T>::c C;
     constexpr int P = PS * PA * PA;
@@ -2516,8 +2548,8 @@ __global__ void __launch_bounds__(128) k_dk_leaf(CommonArgs ca, LevelArgs L, Che
     const C *G = (const C *)G_;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (tid < L.nrc * P) {
-        const int rc = (int)(tid / P), n = (int)(tid % P);
+    if (tid < nlist * P) {
+        const int rc = rc_list ? rc_list[tid / P] : (int)(tid / P), n = (int)(tid % P);
         const int b = L.rc_box[rc];
         // the node's geometry, once (FP32 in leaf units, FP64 absolute)
         float s32 = 0.f, u32[3] = {0.f, 0.f, 0.f};
@@ -4394,12 +4426,19 @@ ifgf_status run_adjoint_t(Plan &p, const void *g, void *out, int nrhs, int prec,
                 if (Fd) k_leaf_adj_w<PS, PA, false, true><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, afw, dk_partials);
                 else k_leaf_adj_w<PS, PA, false, false><<<gw, 128, 0, s>>>(ca, L[D], p.d_cchunk[D], nch, tb, GD, (float2 *)bws, nullptr, nullptr);
             }
+            if (Fd) dk_partials += gw;
             prof_mark(p, s, kStLeaf, D);
         }
-        for (int d = 3; d < D; d++)  // adaptive tree (no k-derivative): the leaves of the coarser levels
+        for (int d = 3; d < D; d++)  // adaptive tree: the leaves of the coarser levels
             if (p.nleaf_rc[d]) {
-                k_leaf_adj<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], tb, G[d], bws, p.d_box_of[d],
-                                                                    p.d_leaf[d], L[D]);
+                if (Fd) {
+                    k_leaf_adj<PS, PA, true, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], tb, G[d], bws, p.d_box_of[d],
+                                                                              p.d_leaf[d], L[D], afw, dk_partials);
+                    dk_partials += nblk(N);
+                } else {
+                    k_leaf_adj<PS, PA, true><<<nblk(N), kBlock, 0, s>>>(ca, L[d], tb, G[d], bws, p.d_box_of[d],
+                                                                        p.d_leaf[d], L[D]);
+                }
                 prof_mark(p, s, kStLeaf, d);
             }
         k_scatter_adj<float><<<nblk(NT), kBlock, 0, s>>>(N, nrhs, p.d_perm, p.prm.identity_coef, p.d_w32,
@@ -4430,10 +4469,22 @@ ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs
     off += nblk(N);
     const long long nt = LD.nrc * P;
     if (nt) {
-        if (mx) k_dk_leaf<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off);
-        else k_dk_leaf<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off);
+        if (mx)
+            k_dk_leaf<PS, PA, true><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off, nullptr,
+                                                                LD.nrc);
+        else
+            k_dk_leaf<PS, PA, false><<<nblk(nt), kBlock, 0, s>>>(ca, LD, tb, p.ws.a, G[D], partials + off, nullptr,
+                                                                 LD.nrc);
         off += nblk(nt);
     }
+    for (int d = 3; d < D && !mx; d++)  // adaptive tree: the leaves of the coarser levels (FP64)
+        if (p.nleaf_rc[d]) {
+            const long long nl = p.nleaf_rc[d];
+            LevelArgs Ld = level_args(p, d, p.ws.F[d]);
+            k_dk_leaf<PS, PA, false><<<nblk(nl * P), kBlock, 0, s>>>(ca, Ld, tb, p.ws.a, G[d], partials + off,
+                                                                     p.d_leaf_rc[d], nl);
+            off += nblk(nl * P);
+        }
     *nparts = off;
     CK(cudaGetLastError());
     return IFGF_OK;
@@ -4444,6 +4495,7 @@ ifgf_status run_dk_t(Plan &p, int nrhs, int prec, cudaStream_t s, const void *gs
 inline long long dk_partials_needed(const Plan &p) {
     long long n = nblk(p.N) + nblk(p.lv[p.D].nrc * p.P);
     for (int d = 3; d <= p.D; d++) n += p.lv[d].nrc;
+    for (int d = 3; d < p.D; d++) n += std::max<long long>(nblk(p.N), nblk((long long)p.nleaf_rc[d] * p.P));
     return n;
 }
 
