@@ -8,7 +8,7 @@ import re
 import numpy as np
 import pytest
 
-from workloads import cube_sphere, ellipsoid, random_density, sphere_workload
+from workloads import cube_sphere, ellipsoid, random_density, sphere_workload, two_spheres
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -133,3 +133,36 @@ def test_entry_points_reject_a_null_plan_without_a_gpu(B):
         assert call() == -1, name
         assert lib.ifgf_last_error(), name
     lib.ifgf_plan_destroy(None)  # a no-op
+
+
+@pytest.mark.parametrize("case", ["two_spheres", "two_spheres_5x8", "ellipsoid_3to1", "cloud"])
+def test_adaptive_plan_counts_match_oracle(B, oracle_lib, case):
+    """Adaptive octree (leaf_max > 0): the library's planner builds the oracle's tree (boxes, cone grids,
+    relevant cones, cousin and propagation evaluations, leaf evaluations at every level's leaves, and
+    the near pairs of the coarser-leaf-level rule), without a GPU."""
+    rng = np.random.default_rng(2)
+    kw = {}
+    if case.startswith("two_spheres"):
+        s = two_spheres()
+        x, n, w, k, D, lm = s.points, s.normals, s.weights, 2 * np.pi, 6, 64
+        if case.endswith("5x8"):
+            kw = dict(Ps=5, Pang=8)
+    elif case == "ellipsoid_3to1":
+        s = ellipsoid(32, 8, (1.0, 1.0, 3.0))
+        x, n, w, k, D, lm = s.points, s.normals, s.weights, 2 * np.pi, 6, 32
+    else:  # a dense cluster inside a sparse cloud, random unit normals
+        x = np.concatenate([rng.normal(size=(2000, 3)) * 0.05, rng.uniform(-1, 1, (1000, 3))])
+        n = rng.normal(size=x.shape)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        w = rng.uniform(0.5, 1.5, x.shape[0])
+        k, D, lm = 9.0, 7, 16
+    sig = random_density(x.shape[0], 1, 0)
+    _, oi = oracle_lib.ifgf(x, n, w, oracle_lib.IFGFParams(k=k, levels=D, leaf_max=lm, **kw), sig)
+    pi = B.dry_run(x, n, w, B.Params(k=k, levels=D, leaf_max=lm, cone_band=0.0, **kw))
+    for key in ("nbox", "ns", "nC", "split", "nrc", "cousin_evals", "prop_evals"):
+        assert pi[key][3:] == oi[key][3:], (case, key, pi[key], oi[key])
+    assert pi["leaf_evals"] == oi["leaf_evals"]
+    assert pi["near_pairs"] == oi["near_pairs"] + x.shape[0]
+    # fewer relevant cones than the uniform tree of the same depth
+    pu = B.dry_run(x, n, w, B.Params(k=k, levels=D, cone_band=0.0, **kw))
+    assert sum(pi["nrc"]) < sum(pu["nrc"])
