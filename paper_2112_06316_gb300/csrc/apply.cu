@@ -2,7 +2,6 @@
 // compiled interpolation orders (kernels in fwd_kernels.cuh, instantiated per
 // order pair in inst_<Ps>x<Pang>.cu).
 #include <algorithm>
-#include <cstring>
 #include <cmath>
 #include <cstdio>
 
@@ -13,11 +12,6 @@ namespace ifgf {
 // level-D box coordinates packed 21 bits per axis (depth <= 20: coordinates below 2^19)
 static inline uint64_t pack_ijk(const int *q) {
     return (uint64_t)q[0] | ((uint64_t)q[1] << 21) | ((uint64_t)q[2] << 42);
-}
-static inline float bits_float(uint32_t u) {
-    float f;
-    std::memcpy(&f, &u, sizeof f);
-    return f;
 }
 
 #define CK(call)                                                                                  \
@@ -166,6 +160,7 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
         p.npairs = pstart[LDb.nbox];
         std::vector<float4> pp(4 * (size_t)p.npairs);
         std::vector<int2> psrc(p.npairs);
+        std::vector<unsigned long long> pair_ijk(p.npairs);
         for (int b = 0; b < LDb.nbox; b++)
             for (int j = LDb.start[b], m = pstart[b]; j < LDb.start[b + 1]; j += 2, m++) {
                 const bool two = j + 1 < LDb.start[b + 1];
@@ -175,12 +170,16 @@ ifgf_status upload_plan(Plan &p, const double *xyz, const double *nrm, const dou
                 pp[4 * (size_t)m] = make_float4(a0.x, a1.x, a0.y, a1.y);
                 pp[4 * (size_t)m + 1] = make_float4(a0.z, a1.z, a0.w, a1.w);
                 pp[4 * (size_t)m + 2] = make_float4(b0.x, b1.x, b0.y, b1.y);
-                // last slot: the box's coordinates packed 21 bits per axis (read by the adaptive near field)
-                const uint64_t kb = pack_ijk(&LDb.ijk[3 * b]);
-                pp[4 * (size_t)m + 3] = make_float4(b0.z, b1.z, bits_float((uint32_t)kb), bits_float((uint32_t)(kb >> 32)));
+                // last slot: f.n of each source (the leaf's |u - ir f| and (u - ir f).n from u.f and u.n)
+                auto fdotn = [](float4 f, float4 nn) {
+                    return (float)((double)f.x * nn.x + (double)f.y * nn.y + (double)f.z * nn.z);
+                };
+                pp[4 * (size_t)m + 3] = make_float4(b0.z, b1.z, fdotn(a0, b0), two ? fdotn(a1, b1) : 0.f);
+                pair_ijk[m] = pack_ijk(&LDb.ijk[3 * b]);  // read by the adaptive near field
                 psrc[m] = make_int2(j, two ? j + 1 : -1);
             }
         UP(p.d_pp32, pp);
+        if (p.adaptive) UP(p.d_pair_ijk, pair_ijk);
         UP(p.d_pstart, pstart);
         UP(p.d_pair_src, psrc);
     }

@@ -671,21 +671,21 @@ __global__ void __launch_bounds__(kBlock) k_leaf32p(CommonArgs ca, LevelArgs L, 
     for (int pm = p0; pm < p1; pm++) {
         const ulonglong2 R0 = __ldg(pp + 4 * pm), R1 = __ldg(pp + 4 * pm + 1), R2 = __ldg(pp + 4 * pm + 2),
                          R3 = __ldg(pp + 4 * pm + 3), A = __ldg(ap + pm);
-        const u64 fx = R0.x, fy = R0.y, fz = R1.x, yy = R1.y, nx = R2.x, ny = R2.y, nz = R3.x;
+        const u64 fx = R0.x, fy = R0.y, fz = R1.x, yy = R1.y, nx = R2.x, ny = R2.y, nz = R3.x, fn = R3.y;
         const u64 ax = A.x, ay = A.y;
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const Node &v = nd[k];
-            const u64 dvx = f2fma3(fx, v.mir, v.ux), dvy = f2fma3(fy, v.mir, v.uy), dvz = f2fma3(fz, v.mir, v.uz);
-            const u64 a2 = f2fma3(dvz, dvz, f2fma3(dvy, dvy, f2mul(dvx, dvx)));
+            // with u a unit vector and v = u - ir f:  |v|^2 = 1 + ir (ir |f|^2 - 2 u.f)  (>= (1 - s)^2, no
+            // cancellation: ir |f| <= s <= 1/sqrt(3)) and v.n = u.n - ir f.n (f.n stored per source)
+            const u64 uy = f2fma3(fz, v.uz, f2fma3(fy, v.uy, f2mul(fx, v.ux)));
+            const u64 num = f2fma3(uy, mtwo2, f2mul(v.ir, yy));  // ir |f|^2 - 2 u.f
+            const u64 a2 = f2fma3(v.ir, num, one2);
             float a2l, a2h;
             f2unpack(a2, a2l, a2h);
             const u64 ia = f2pack(rsqrtf(a2l), rsqrtf(a2h));
-            const u64 am = f2mul(a2, ia);
-            const u64 uy = f2fma3(fz, v.uz, f2fma3(fy, v.uy, f2mul(fx, v.ux)));
-            const u64 num = f2fma3(uy, mtwo2, f2mul(v.ir, yy));  // ir |f|^2 - 2 u.f
             float dl, dh;
-            f2unpack(f2add(am, one2), dl, dh);  // am + 1 in [1, 3]: the fast reciprocal is exact to 2 ulp
+            f2unpack(f2fma3(a2, ia, one2), dl, dh);  // |v| + 1 in [1, 3]: the fast reciprocal is exact to 2 ulp
             u64 t = f2mul(kap2, f2mul(num, f2pack(__fdividef(1.f, dl), __fdividef(1.f, dh))));
             float tl, th;
             f2unpack(t, tl, th);
@@ -695,7 +695,7 @@ __global__ void __launch_bounds__(kBlock) k_leaf32p(CommonArgs ca, LevelArgs L, 
             cis_cycles(tl, snl, csl);
             cis_cycles(th, snh, csh);
             const u64 sn = f2pack(snl, snh), cs = f2pack(csl, csh), ncs = f2pack(-csl, -csh);
-            const u64 dn = f2fma3(dvz, nz, f2fma3(dvy, ny, f2mul(dvx, nx)));
+            const u64 dn = f2fma3(v.mir, fn, f2fma3(nz, v.uz, f2fma3(ny, v.uy, f2mul(nx, v.ux))));
             const u64 w3 = f2mul(dn, f2mul(ia, ia)), w2 = f2mul(w3, ia);
             const u64 g = f2fma3(kf2, w3, f2mul(eta2, ia)), hr = f2mul(etai2, ia);
             if (SPLIT) {
@@ -975,6 +975,7 @@ __device__ __forceinline__ NearTargets near_targets(const CommonArgs &ca, const 
 // (k_near32p's arithmetic with per-pair box coordinates); accumulates (Re Kr a, Im Ki a, imag) per target
 __device__ __forceinline__ void near_pairs_acc(const CommonArgs &ca, const NearTargets &t, int p0, int p1, int step,
                                                const ulonglong2 *__restrict__ pp, const ulonglong2 *__restrict__ ap,
+                                               const unsigned long long *__restrict__ pair_ijk,
                                                u64 (&ra)[2], u64 (&rb)[2], u64 (&im)[2]) {
     const float c4 = 1.f / (4.f * kPiF * ca.HDf);
     const float tolu = (float)(ca.tol / ca.HD), tolu2 = tolu * tolu;
@@ -984,7 +985,7 @@ __device__ __forceinline__ void near_pairs_acc(const CommonArgs &ca, const NearT
         const ulonglong2 R0 = __ldg(pp + 4 * pm), R1 = __ldg(pp + 4 * pm + 1), R2 = __ldg(pp + 4 * pm + 2),
                          R3 = __ldg(pp + 4 * pm + 3), A = __ldg(ap + pm);
         int c0, c1, c2;
-        unpack_ijk(R3.y, c0, c1, c2);
+        unpack_ijk(__ldg(pair_ijk + pm), c0, c1, c2);
 #pragma unroll
         for (int k = 0; k < 2; k++) {
             const u64 dx = f2sub(f2dup((float)(t.ai[k][0] - c0) + t.fv[k].x), R0.x),
@@ -1089,12 +1090,13 @@ __global__ void __launch_bounds__(kNearWarps * 32) k_near32r(CommonArgs ca, cons
     }
 }
 
-// one warp per chunk, one right-hand side on the source pairs (the pair record's last slot holds the
-// packed coordinates of its level-D box; both sources of a pair share it)
+// one warp per chunk, one right-hand side on the source pairs (pair_ijk: the packed coordinates of each
+// pair's level-D box; both sources of a pair share it)
 __global__ void __launch_bounds__(kNearWarps * 32) k_near32pr(CommonArgs ca, const int4 *__restrict__ chunks, int nchunk,
                                                              const int *__restrict__ nr_start,
                                                              const int4 *__restrict__ nr,
                                                              const unsigned long long *__restrict__ pt_ijk,
+                                                             const unsigned long long *__restrict__ pair_ijk,
                                                              const ulonglong2 *__restrict__ pp,
                                                              const ulonglong2 *__restrict__ ap, float2 *__restrict__ u) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(kNearWarps * 32) k_near32pr(CommonArgs ca, con
     u64 ra[2] = {0ull, 0ull}, rb[2] = {0ull, 0ull}, im[2] = {0ull, 0ull};
     for (int r = nr_start[cw.w]; r < nr_start[cw.w + 1]; r++) {
         const int4 rg = __ldg(nr + r);
-        near_pairs_acc(ca, t, rg.z, rg.w, 1, pp, ap, ra, rb, im);
+        near_pairs_acc(ca, t, rg.z, rg.w, 1, pp, ap, pair_ijk, ra, rb, im);
     }
     if (v0) u[i0] = near_fold(ra[0], rb[0], im[0]);
     if (v1) u[i1] = near_fold(ra[1], rb[1], im[1]);
@@ -1119,6 +1121,7 @@ __global__ void __launch_bounds__(kNearBlkWarps * 32) k_near32pr_blk(CommonArgs 
                                                                     const int *__restrict__ nr_start,
                                                                     const int4 *__restrict__ nr,
                                                                     const unsigned long long *__restrict__ pt_ijk,
+                                                                    const unsigned long long *__restrict__ pair_ijk,
                                                                     const ulonglong2 *__restrict__ pp,
                                                                     const ulonglong2 *__restrict__ ap,
                                                                     float2 *__restrict__ u) {
@@ -1131,7 +1134,7 @@ __global__ void __launch_bounds__(kNearBlkWarps * 32) k_near32pr_blk(CommonArgs 
     u64 ra[2] = {0ull, 0ull}, rb[2] = {0ull, 0ull}, im[2] = {0ull, 0ull};
     for (int r = nr_start[cw.w]; r < nr_start[cw.w + 1]; r++) {
         const int4 rg = __ldg(nr + r);
-        near_pairs_acc(ca, t, rg.z + warp, rg.w, kNearBlkWarps, pp, ap, ra, rb, im);
+        near_pairs_acc(ca, t, rg.z + warp, rg.w, kNearBlkWarps, pp, ap, pair_ijk, ra, rb, im);
     }
     part[warp][lane] = near_fold(ra[0], rb[0], im[0]);
     part[warp][lane + 32] = near_fold(ra[1], rb[1], im[1]);
@@ -4210,10 +4213,10 @@ ifgf_status run_apply_t(Plan &p, const void *sigma, void *y, int nrhs, int prec,
                 if (nrhs == 1) {
                     if (gl)
                         k_near32pr<<<gl, kNearWarps * 32, 0, sb>>>(ca, p.d_nchunk, p.nnchunk_light, p.d_nr_start, p.d_nr,
-                                                                   p.d_pt_ijk, pp, ap, u32);
+                                                                   p.d_pt_ijk, p.d_pair_ijk, pp, ap, u32);
                     if (nh)
-                        k_near32pr_blk<<<nh, kNearBlkWarps * 32, 0, sb>>>(ca, hv, p.d_nr_start, p.d_nr, p.d_pt_ijk, pp,
-                                                                          ap, u32);
+                        k_near32pr_blk<<<nh, kNearBlkWarps * 32, 0, sb>>>(ca, hv, p.d_nr_start, p.d_nr, p.d_pt_ijk,
+                                                                          p.d_pair_ijk, pp, ap, u32);
                 } else {
                     const float2 *a32 = (const float2 *)p.ws.a;
                     if (gl && rb1)

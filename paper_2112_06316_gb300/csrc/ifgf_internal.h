@@ -192,6 +192,7 @@ struct Plan {
     int *d_nr_start = nullptr;
     int4 *d_nr = nullptr;
     unsigned long long *d_pt_ijk = nullptr;
+    unsigned long long *d_pair_ijk = nullptr;  // per source pair: its level-D box, packed the same way
     int npairs = 0;
     unsigned long long *d_missed = nullptr;
     TcLevel tc[IFGF_MAXD + 1];  // tc[d]: propagation from level d into level d-1
