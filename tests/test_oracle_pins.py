@@ -457,3 +457,36 @@ def test_adaptive_tree_converges_to_direct(oracle_lib):
     _, iu = oracle_lib.ifgf(pts, nrm, w, P(Ps=5, Pang=8), sig)
     _, ia = oracle_lib.ifgf(pts, nrm, w, P(Ps=5, Pang=8, leaf_max=64), sig)
     assert sum(ia["nrc"]) < sum(iu["nrc"]) / 5
+
+
+def test_adaptive_near_pairs_brute_force(oracle_lib):
+    """The adaptive near field visits exactly the pairs of the rule it implements: a point's leaf is its
+    first box from level 3 down holding at most leaf_max points (level D at the latest), and two points
+    interact directly when their boxes at the coarser of their two leaf levels are neighbours.  Counted
+    here by brute force over all pairs of a small two-density cloud from the root box the oracle reports;
+    a pair missing or counted twice changes the count."""
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.normal(size=(450, 3)) * 0.04 + 0.3, rng.uniform(-1, 1, (250, 3))])
+    nrm = rng.normal(size=x.shape)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    w = rng.uniform(0.5, 1.5, x.shape[0])
+    D, lm = 6, 12
+    _, info = oracle_lib.ifgf(x, nrm, w, oracle_lib.IFGFParams(k=3.0, levels=D, leaf_max=lm), random_density(len(x), 1, 6))
+    lo = np.asarray(info["root_center"]) - info["root_side"] / 2
+    cell = {d: np.clip(np.floor((x - lo) / (info["root_side"] / 2 ** (d - 1))).astype(np.int64), 0, 2 ** (d - 1) - 1)
+            for d in range(3, D + 1)}
+    lev = np.full(len(x), D)
+    done = np.zeros(len(x), bool)
+    for d in range(3, D):
+        _, inv, cnt = np.unique(cell[d], axis=0, return_inverse=True, return_counts=True)
+        m = ~done & (cnt[inv.ravel()] <= lm)
+        lev[m] = d
+        done |= m
+    assert len(set(lev.tolist())) >= 3  # leaves at several levels
+    mlev = np.minimum(lev[:, None], lev[None, :])
+    near = np.zeros((len(x), len(x)), bool)
+    for d in range(3, D + 1):
+        dd = np.abs(cell[d][:, None, :] - cell[d][None, :, :]).max(axis=2) <= 1
+        near |= (mlev == d) & dd
+    np.fill_diagonal(near, False)
+    assert info["near_pairs"] == int(near.sum())
