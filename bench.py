@@ -22,6 +22,8 @@ the 24-scatterer batch as one CUDA graph at the headline orders, the adaptive
 octree against the uniform one on a two-density point set, and the FP64 CPU
 oracle applied to the whole workload on the host cores (cpu_baseline).
 
+--quick skips the FP64, paper-orders, CPU-oracle and adaptive-octree legs; --adaptive brings the last back.
+
 --impl reference times the FP64 CPU oracle (the IFGF apply of Section 3.4, OpenMP
 on the host cores) on a bounded sample of the same workload.
 """
